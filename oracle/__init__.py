@@ -1,0 +1,307 @@
+"""FP64 CPU oracle for the tile-based micromagnetic method (arXiv 2107.05364).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, double-precision
+statement of what the GPU path computes.  Only the test-suite, the smoke
+check and the CPU-baseline leg of ``bench.py`` may import it; the product
+path (the CUDA library and its binding) never does, and shares no code with
+it.  The arithmetic lives in ``oracle.c``; this module only marshals numpy
+arrays into it (``ctypes``).
+
+Functions and the passage each follows (see ``oracle.c`` for the formulas):
+
+* :func:`point_tensor`, :func:`demag_tensor`, :func:`demag_blocks` --
+  Sec. 3, cuboid tile tensor evaluated at tile centres (closed form of the
+  Newtonian potential; Eq. 9 read as ``H_d = -N (Ms m)``).
+* :func:`demag_field_dense`, :func:`demag_field_rows` -- Eq. 9 / Eq. 17.
+* :func:`exchange_field` -- Eq. 12 with the Neumann condition of Eq. 3.
+* :func:`anisotropy_field` -- Eq. 16.  Zeeman -- Eq. 7.
+* :func:`llg_rhs` -- Eq. 1 (Landau-Lifshitz) or its Gilbert form.
+* :func:`integrate`, :func:`relax`, :func:`integrate_linear` -- Sec. 3.1,
+  Dormand-Prince RK(4,5).
+* :func:`energy` -- Eqs. 4, 6, 8, 11, 15.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+MU0 = 4e-7 * np.pi
+
+OK, EINVAL, EOVERLAP, ENOCONV, ENONFINITE = 0, 1, 3, 4, 6
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` into ``_build/liboracle.so`` (gcc, OpenMP, -O2,
+    strict IEEE arithmetic: no fast-math, no host-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+           "-fno-fast-math", "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64),
+                ("centre", ctypes.c_void_p), ("edge", ctypes.c_void_p),
+                ("Ms", ctypes.c_void_p), ("Aex", ctypes.c_void_p),
+                ("Ku", ctypes.c_void_p), ("axis", ctypes.c_void_p),
+                ("nbr", ctypes.c_void_p), ("N", ctypes.c_void_p)]
+
+
+class _Llg(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("Ha", ctypes.c_double * 3), ("form", ctypes.c_int),
+                ("precess", ctypes.c_int)]
+
+
+class _Ode(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("h0", ctypes.c_double), ("hmax", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("fixed_h", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n_accept", ctypes.c_int64), ("n_reject", ctypes.c_int64),
+                ("n_rhs", ctypes.c_int64), ("t", ctypes.c_double),
+                ("h", ctypes.c_double), ("tau", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_SO)
+    return _lib
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+# ---------------------------------------------------------------------------
+# tensor and field
+# ---------------------------------------------------------------------------
+def point_tensor(r, centre, edge) -> np.ndarray:
+    """3x3 point tensor of the cuboid (``centre``, full ``edge``) at ``r``."""
+    r = np.ascontiguousarray(r, np.float64)
+    c = np.ascontiguousarray(centre, np.float64)
+    e = np.ascontiguousarray(edge, np.float64)
+    out = np.zeros(6)
+    lib().or_point_tensor(_p(r), _p(c), _p(e), _p(out))
+    return six_to_full(out)
+
+
+def six_to_full(n6: np.ndarray) -> np.ndarray:
+    """{xx,xy,xz,yy,yz,zz} (last axis) -> symmetric 3x3 (last two axes)."""
+    n6 = np.asarray(n6)
+    idx = np.array([[0, 1, 2], [1, 3, 4], [2, 4, 5]])
+    return n6[..., idx]
+
+
+def check_tiles(centre, edge) -> int:
+    c = np.ascontiguousarray(centre, np.float64).reshape(-1)
+    e = np.ascontiguousarray(edge, np.float64).reshape(-1)
+    return int(lib().or_check_tiles(ctypes.c_int64(c.size // 3), _p(c), _p(e)))
+
+
+def demag_tensor(centre, edge) -> np.ndarray:
+    """All blocks; returns (n, n, 6): [i, j] = tile j at the centre of tile i."""
+    c = np.ascontiguousarray(centre, np.float64).reshape(-1)
+    e = np.ascontiguousarray(edge, np.float64).reshape(-1)
+    n = c.size // 3
+    out = np.empty((n, n, 6))
+    lib().or_demag_tensor(ctypes.c_int64(n), _p(c), _p(e), _p(out))
+    return out
+
+
+def demag_blocks(centre, edge, pairs) -> np.ndarray:
+    c = np.ascontiguousarray(centre, np.float64).reshape(-1)
+    e = np.ascontiguousarray(edge, np.float64).reshape(-1)
+    pr = np.ascontiguousarray(pairs, np.int64).reshape(-1, 2)
+    out = np.empty((pr.shape[0], 6))
+    lib().or_demag_blocks(_p(c), _p(e), ctypes.c_int64(pr.shape[0]), _p(pr), _p(out))
+    return out
+
+
+def demag_field_dense(N, Ms, m) -> np.ndarray:
+    N = np.ascontiguousarray(N, np.float64)
+    n = N.shape[0]
+    Ms = np.ascontiguousarray(Ms, np.float64)
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    H = np.empty(3 * n)
+    lib().or_demag_field_dense(ctypes.c_int64(n), _p(N), _p(Ms), _p(m), _p(H))
+    return H.reshape(n, 3)
+
+
+def demag_field_rows(centre, edge, Ms, m, rows) -> np.ndarray:
+    c = np.ascontiguousarray(centre, np.float64).reshape(-1)
+    e = np.ascontiguousarray(edge, np.float64).reshape(-1)
+    n = c.size // 3
+    Ms = np.ascontiguousarray(Ms, np.float64)
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    rows = np.ascontiguousarray(rows, np.int64)
+    H = np.empty(3 * rows.size)
+    lib().or_demag_field_rows(ctypes.c_int64(n), _p(c), _p(e), _p(Ms), _p(m),
+                              ctypes.c_int64(rows.size), _p(rows), _p(H))
+    return H.reshape(-1, 3)
+
+
+# ---------------------------------------------------------------------------
+# model-level functions
+# ---------------------------------------------------------------------------
+class Model:
+    """Tiles + stored FP64 tensor.  Arrays are kept alive by this object."""
+
+    def __init__(self, centre, edge, Ms, Aex, Ku, axis, nbr=None, N=None):
+        self.centre = np.ascontiguousarray(centre, np.float64).reshape(-1, 3)
+        self.n = self.centre.shape[0]
+        self.edge = np.ascontiguousarray(edge, np.float64).reshape(-1, 3)
+        self.Ms = np.ascontiguousarray(np.broadcast_to(Ms, (self.n,)), np.float64)
+        self.Aex = np.ascontiguousarray(np.broadcast_to(Aex, (self.n,)), np.float64)
+        self.Ku = np.ascontiguousarray(np.broadcast_to(Ku, (self.n,)), np.float64)
+        self.axis = np.ascontiguousarray(
+            np.broadcast_to(np.asarray(axis, np.float64).reshape(-1, 3), (self.n, 3)))
+        self.nbr = None if nbr is None else np.ascontiguousarray(nbr, np.int32).reshape(-1, 6)
+        self.N = demag_tensor(self.centre, self.edge) if N is None else np.ascontiguousarray(N, np.float64)
+        self._s = _Model(self.n, _p(self.centre), _p(self.edge), _p(self.Ms), _p(self.Aex),
+                         _p(self.Ku), _p(self.axis), _p(self.nbr) if self.nbr is not None else None,
+                         _p(self.N))
+
+    @classmethod
+    def from_tiles(cls, tiles, N=None):
+        """Build from a workload tile-set object (fields centre, edge, Ms,
+        Aex, Ku, axis, nbr)."""
+        return cls(tiles.centre, tiles.edge, tiles.Ms, tiles.Aex, tiles.Ku, tiles.axis,
+                   tiles.nbr, N)
+
+    @property
+    def volume(self):
+        return np.prod(self.edge, axis=1)
+
+    def mean_m(self, m):
+        m = np.asarray(m, np.float64).reshape(-1, 3)
+        V = self.volume
+        return (V[:, None] * m).sum(0) / V.sum()
+
+
+def llg_params(gamma=2.211e5, alpha=0.02, Ha=(0.0, 0.0, 0.0), form=0, precess=1):
+    return _Llg(float(gamma), float(alpha), (ctypes.c_double * 3)(*[float(x) for x in Ha]),
+                int(form), int(precess))
+
+
+def ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11, max_steps=10_000_000, fixed_h=0.0):
+    return _Ode(float(rtol), float(atol), float(h0), float(hmax), int(max_steps), float(fixed_h))
+
+
+def demag_field(model: Model, m) -> np.ndarray:
+    return demag_field_dense(model.N, model.Ms, m)
+
+
+def exchange_field(model: Model, m) -> np.ndarray:
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    H = np.empty(3 * model.n)
+    lib().or_exchange_field(ctypes.byref(model._s), _p(m), _p(H))
+    return H.reshape(-1, 3)
+
+
+def anisotropy_field(model: Model, m) -> np.ndarray:
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    H = np.empty(3 * model.n)
+    lib().or_anisotropy_field(ctypes.byref(model._s), _p(m), _p(H))
+    return H.reshape(-1, 3)
+
+
+def effective_field(model: Model, m, params) -> np.ndarray:
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    H = np.empty(3 * model.n)
+    lib().or_effective_field(ctypes.byref(model._s), ctypes.byref(params), _p(m), _p(H), None)
+    return H.reshape(-1, 3)
+
+
+def llg_rhs(model: Model, m, params):
+    """Returns (dm/dt (n,3), tau = max_i |m_i x H_i|/Ms_i)."""
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    k = np.empty(3 * model.n)
+    tau = ctypes.c_double(0.0)
+    lib().or_llg_rhs(ctypes.byref(model._s), ctypes.byref(params), _p(m), _p(k), ctypes.byref(tau))
+    return k.reshape(-1, 3), tau.value
+
+
+def energy(model: Model, m, params) -> dict:
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    out = np.empty(5)
+    lib().or_energy(ctypes.byref(model._s), ctypes.byref(params), _p(m), _p(out))
+    return dict(total=out[0], zeeman=out[1], demag=out[2], exchange=out[3], anisotropy=out[4])
+
+
+def _stats(st: _Stats) -> dict:
+    return dict(n_accept=st.n_accept, n_reject=st.n_reject, n_rhs=st.n_rhs, t=st.t, h=st.h,
+                tau=st.tau)
+
+
+def integrate(model: Model, m0, params, opts, t0: float, t1: float, n_out: int):
+    """Integrate Eq. 1 from t0 to t1.  Returns (status, m_final (n,3),
+    <m> at t0 + (k+1)(t1-t0)/n_out (n_out,3), stats)."""
+    m = np.ascontiguousarray(m0, np.float64).reshape(-1).copy()
+    mavg = np.zeros((n_out, 3))
+    st = _Stats()
+    s = lib().or_integrate(ctypes.byref(model._s), ctypes.byref(params), ctypes.byref(opts), _p(m),
+                           ctypes.c_double(t0), ctypes.c_double(t1), ctypes.c_int64(n_out), _p(mavg),
+                           ctypes.byref(st))
+    return int(s), m.reshape(-1, 3), mavg, _stats(st)
+
+
+def relax(model: Model, m0, params, opts, tol: float, t_max: float):
+    """Relax until max torque < tol.  Returns (status, m (n,3), stats)."""
+    m = np.ascontiguousarray(m0, np.float64).reshape(-1).copy()
+    st = _Stats()
+    s = lib().or_relax(ctypes.byref(model._s), ctypes.byref(params), ctypes.byref(opts), _p(m),
+                       ctypes.c_double(tol), ctypes.c_double(t_max), ctypes.byref(st))
+    return int(s), m.reshape(-1, 3), _stats(st)
+
+
+def integrate_linear(lam, y0, opts, t0, t1, n_out):
+    """y' = lam * y (component-wise) with the same RK(4,5) driver."""
+    lam = np.ascontiguousarray(lam, np.float64)
+    y = np.ascontiguousarray(y0, np.float64).copy()
+    yout = np.zeros((n_out, y.size))
+    st = _Stats()
+    s = lib().or_integrate_linear(ctypes.c_int64(y.size), _p(lam), ctypes.byref(opts), _p(y),
+                                  ctypes.c_double(t0), ctypes.c_double(t1), ctypes.c_int64(n_out),
+                                  _p(yout), ctypes.byref(st))
+    return int(s), y, yout, _stats(st)
+
+
+def dp45_tableau():
+    c = np.zeros(7)
+    a = np.zeros(42)
+    b = np.zeros(7)
+    bh = np.zeros(7)
+    lib().or_dp45_tableau(_p(c), _p(a), _p(b), _p(bh))
+    return c, a.reshape(7, 6), b, bh

@@ -1,0 +1,303 @@
+"""Benchmark of the hot path: LLG right-hand-side evaluations per second.
+
+Workload (default): the standard-problem-4 film 500 x 125 x 3 nm as
+200 x 50 x 1 tiles (n = 10,000), tensor assembled in FP64 on the GPU and
+stored in FP32 (2.43 GB, larger than L2), one simulation, field 1
+(mu0 H = (-24.6, 4.3, 0) mT), alpha = 0.02.  A step is one attempted
+Dormand-Prince step: 6 right-hand sides (streaming demag product +
+exchange + Zeeman + LLG), the embedded error, accept/reject and step-size
+control, all on the device (one CUDA-graph replay).
+
+Printed: one JSON line (rank 0).  `value` = RHS evaluations per second over
+all ranks, device-resident inputs, timed with CUDA events on the
+integrator's stream.  `e2e` = the same through the public API with host
+buffers (pinned host -> device state copy, one step, device -> host copy
+every step).  `roofline` = the streaming demag kernel against the measured
+HBM bandwidth.  `cpu_baseline` = the FP64 CPU oracle on the same workload.
+
+--impl reference runs the FP64 CPU oracle instead (the reference arm), on
+this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_05364_gb300 import workloads as wl  # noqa: E402
+
+MU0 = 4e-7 * math.pi
+FIELD1 = np.array([-24.6e-3, 4.3e-3, 0.0]) / MU0
+WORKLOAD = "sp4_film_200x50x1_n10000_f32"
+METRIC = "LLG RHS evals/s"
+UNIT = "RHS evals/s"
+
+
+def _rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_rhs_baseline(t, m0, n_evals=3):
+    """The FP64 oracle as it stands: dense FP64 tensor (assembled once,
+    untimed), then n_evals right-hand sides timed on all host cores."""
+    import oracle
+    md = oracle.Model.from_tiles(t)
+    p = oracle.llg_params(alpha=0.02, Ha=FIELD1)
+    oracle.llg_rhs(md, m0, p)  # warm
+    t0 = time.perf_counter()
+    for _ in range(n_evals):
+        oracle.llg_rhs(md, m0, p)
+    dt = time.perf_counter() - t0
+    return {"value": n_evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "n=%d film, FP64 tensor assembled once (untimed), %d RHS evaluations timed" % (t.n, n_evals)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle's RK(4,5) on the same workload."""
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    import oracle
+    t = wl.film(200, 50, 1)
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0)
+    md = oracle.Model.from_tiles(t)
+    p = oracle.llg_params(alpha=0.02, Ha=FIELD1)
+    h = 1e-13
+    m = m0.copy()
+    for _ in range(args.warmup):
+        st, m, _, _ = oracle.integrate(md, m, p, oracle.ode_opts(fixed_h=h), 0.0, h, 1)
+    t0 = time.perf_counter()
+    n_rhs = 0
+    for _ in range(args.steps):
+        st, m, _, s = oracle.integrate(md, m, p, oracle.ode_opts(fixed_h=h), 0.0, h, 1)
+        n_rhs += s["n_rhs"] - 1  # the first evaluation of each call is the FSAL restart
+    dt = time.perf_counter() - t0
+    val = n_rhs / dt
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "tiles": t.n, "precision": "f64 (oracle)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one fixed-size RK(4,5) step (6 RHS) per timed step, n=%d" % t.n},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _rank_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist = dist_
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2107_05364_gb300 import binding as mt
+
+    t = wl.film(200, 50, 1)
+    n = t.n
+    m0 = wl.m_noisy(n, (1, 1, 1), 1e-3, seed=rank).astype(np.float32)
+    ctx = mt.mt_ctx_create(dev)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    info = T.info()
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    I = mt.Integrator(T, p, mt.ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11))
+    I.set_state(m0.ravel())
+    stream = torch.cuda.ExternalStream(I.stream_handle())
+
+    # warm-up
+    I.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device-resident state --------------------
+    s0 = I.stats()[0]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        I.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    s1 = I.stats()[0]
+    n_rhs = s1["n_rhs"] - s0["n_rhs"]
+    assert n_rhs == 6 * args.steps, (n_rhs, args.steps)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = n_rhs * world / (ms * 1e-3)
+
+    # ---- dominant kernel alone: streaming demag product ----------------
+    mg = torch.tensor(m0.ravel(), device="cuda")
+    H = torch.empty_like(mg)
+    cur = torch.cuda.current_stream()
+    for _ in range(3):
+        mt.mt_demag_field(T, mg, H, stream=cur)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(10, args.steps)
+    torch.cuda.synchronize()
+    e0.record(cur)
+    for _ in range(reps):
+        mt.mt_demag_field(T, mg, H, stream=cur)
+    e1.record(cur)
+    torch.cuda.synchronize()
+    field_ms = e0.elapsed_time(e1) / reps  # includes the tiny operand-prep kernel
+    alg_bytes = 24.0 * n * n  # 6 unique FP32 entries per 3x3 block, each read once
+    peaks, kind = _peaks()
+    achieved = alg_bytes / (field_ms * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    # ---- end to end through the public API with host buffers ------------
+    pinned_in = torch.from_numpy(m0.ravel().copy()).pin_memory()
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    I.set_state(pinned_in.numpy())
+    I.step(1)
+    I.get_state(pinned_out.numpy().reshape(1, n, 3))
+    torch.cuda.synchronize()
+    r0 = I.stats()[0]["n_rhs"]
+    tw0 = time.perf_counter()
+    tot_rhs = 0
+    for _ in range(e2e_steps):
+        I.set_state(pinned_in.numpy())
+        I.step(1)
+        I.get_state(pinned_out.numpy().reshape(1, n, 3))
+        tot_rhs += I.stats()[0]["n_rhs"]
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - tw0
+    e2e_val = tot_rhs * world / e2e_s if e2e_s > 0 else None
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = _oracle_rhs_baseline(t, m0.astype(np.float64))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "tiles": n, "precision": "f32 storage, f32 accumulate, f64 assembly",
+                   "sims_per_gpu": 1, "step": "one Dormand-Prince attempt = 6 RHS",
+                   "l2": "inputs larger than L2 (tensor %.2f GB, L2 129 MB)" % (info["bytes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "sms": torch.cuda.get_device_properties(dev).multi_processor_count},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_matvec<f32>",
+                     "peak_kind": kind, "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": field_ms},
+        "demag_gbs": achieved,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 12 * n,
+                "note": "set_state(pinned host) + 1 step + get_state(host); init RHS included"},
+        "gpu_launches": 13 * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

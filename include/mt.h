@@ -1,0 +1,268 @@
+/*
+ * mt.h -- C ABI of the GB300 tile-micromagnetics library (libmagtile.so).
+ *
+ * The library implements the hot path of the tile-based micromagnetic
+ * method of Bjork et al. (arXiv 2107.05364, "MagTense"): the magnet is
+ * split into uniformly magnetised rectangular cuboid tiles (Sec. 3); the
+ * demagnetization field of every tile is evaluated analytically at the
+ * centre of every other tile, giving a dense 3n x 3n tensor N computed once
+ * (Sec. 3.1); at every right-hand-side evaluation of the Landau-Lifshitz
+ * equation (Eq. 1) the effective field H_eff = A m + b (Eq. 17) is formed
+ * from the dense demag product H_d = -N (Ms m) (Eq. 9), the exchange field
+ * (Eq. 12), the uniaxial anisotropy field (Eq. 16) and the applied field
+ * (Eq. 7), and the equation is integrated with an explicit Runge-Kutta (4,5)
+ * pair (Sec. 3.1).
+ *
+ * Conventions for every call:
+ *   - SI units: lengths m, fields A/m, Ms A/m, A_ex J/m, K J/m^3,
+ *     gamma m/(A s), time s.
+ *   - Vectors of tiles are tile-major: m[3*i + c], c = x, y, z.  A batch of
+ *     B simulations on one geometry is B such vectors back to back
+ *     (m[b*3n + 3*i + c]).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the context's device (e.g. from torch).  The caller
+ *     owns every pointer it passes; the library never frees them and keeps
+ *     none of them after the call returns, except where stated.
+ *   - Handles (mt_ctx, mt_tiles, mt_tensor, mt_integrator, mt_server) are
+ *     owned by the library and released with the matching *_destroy call.
+ *   - Every call returns an mt_status.  On failure a message is available
+ *     from mt_last_error() (thread-local) and outputs are unspecified.
+ *     Nothing is thrown across the ABI.
+ *   - Calls taking a `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) are asynchronous unless stated otherwise.
+ */
+#ifndef MT_H
+#define MT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MT_API __attribute__((visibility("default")))
+#else
+#define MT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MT_OK = 0,
+  MT_EINVAL = 1,      /* bad argument (size, pointer, non-finite parameter)   */
+  MT_ENOMEM = 2,      /* device allocation failed or HBM budget exceeded      */
+  MT_EOVERLAP = 3,    /* tiles overlap, or a centre lies on another tile      */
+  MT_ENOCONV = 4,     /* step cap or time cap reached before the goal         */
+  MT_ETIMEOUT = 5,    /* a bounded device wait or a host wait ran out         */
+  MT_ENONFINITE = 6,  /* a NaN/Inf appeared in the state or the error norm    */
+  MT_ECUDA = 7,       /* CUDA runtime error (message in mt_last_error)        */
+  MT_EBUSY = 8        /* resource in use (e.g. server queue full)             */
+} mt_status;
+
+/* Storage precision of the assembled tensor.  Assembly itself is always
+ * FP64 (the corner sums cancel catastrophically in the far field).  Every
+ * product accumulates in FP32, except MT_F64 which accumulates in FP64. */
+typedef enum {
+  MT_F64 = 0,          /* 8 B per entry                                       */
+  MT_F32 = 1,          /* 4 B per entry: the paper's storage (Sec. 3.2)        */
+  MT_BF16_SCALED = 2,  /* 2 B per entry + a power-of-two scale per 3x3 block;  */
+                       /* the tile and its touching neighbours stay FP64       */
+  MT_BF16_SPLIT = 3    /* hi + lo BF16 pair (4 B per entry); near blocks FP64  */
+} mt_prec;
+
+/* Equation-of-motion form. */
+typedef enum {
+  MT_FORM_GILBERT = 0, /* dm/dt = -gamma/(1+a^2) [m x H + a m x (m x H)]      */
+  MT_FORM_LL = 1       /* Eq. 1: dm/dt = -gamma m x H - alpha m x (m x H)     */
+} mt_form;
+
+typedef struct mt_ctx mt_ctx;
+typedef struct mt_tiles mt_tiles;
+typedef struct mt_tensor mt_tensor;
+typedef struct mt_integrator mt_integrator;
+
+/* Per-simulation parameters of the equation of motion for a batch of B.
+ * All arrays are HOST memory, copied by the call that receives them. */
+typedef struct {
+  double gamma;        /* gyromagnetic ratio, m/(A s) (2.211e5 for electrons) */
+  const double *alpha; /* [B] damping: dimensionless (Gilbert) or m/(A s) (LL) */
+  const double *Ha;    /* [3B] applied field per simulation, A/m (Eq. 7)      */
+  int form;            /* mt_form                                             */
+  int precess;         /* 1 = full equation, 0 = drop the m x H term           */
+} mt_llg_params;
+
+/* Runge-Kutta (4,5) options (Dormand-Prince pair, Sec. 3.1). */
+typedef struct {
+  double rtol, atol;   /* error norm: RMS of e/(atol + rtol max(|y|,|y_new|)) */
+  double h0;           /* first trial step, s                                 */
+  double hmax;         /* largest step, s (<= 0: unlimited)                   */
+  int64_t max_steps;   /* cap on attempted steps per call                     */
+  double fixed_h;      /* > 0: fixed step of this size, no error control      */
+} mt_ode_opts;
+
+/* Per-simulation outcome of an integration. */
+typedef struct {
+  int64_t n_accept, n_reject, n_rhs;
+  double t;            /* time reached, s                                     */
+  double h;            /* next step proposal, s                               */
+  double tau;          /* max_i |m_i x H_eff,i| / Ms_i at the last evaluation */
+  int32_t status;      /* mt_status of this simulation                        */
+  int32_t pad;
+} mt_stats;
+
+/* Description of an assembled tensor. */
+typedef struct {
+  int64_t n;           /* tiles                                               */
+  int32_t prec;        /* mt_prec                                             */
+  int32_t rows_per_panel, cols_per_chunk; /* tile-blocked layout              */
+  int64_t bytes;       /* device bytes of the stored tensor                   */
+  int64_t near_blocks; /* FP64 near-field blocks kept apart (0 if none)       */
+} mt_tensor_info;
+
+/* ---------------------------------------------------------------------- */
+/* library and context                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Version string; never fails. */
+MT_API const char *mt_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+MT_API const char *mt_last_error(void);
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes bounds the
+ * device memory of the tensors this context assembles (0 = 90 % of the
+ * device's free memory at creation).  Errors: MT_EINVAL (bad device),
+ * MT_ECUDA. */
+MT_API mt_status mt_ctx_create(int device, size_t hbm_budget_bytes, mt_ctx **out);
+MT_API void mt_ctx_destroy(mt_ctx *ctx);
+
+/* Bytes of tensors currently held by the context. */
+MT_API size_t mt_ctx_bytes_in_use(const mt_ctx *ctx);
+
+/* ---------------------------------------------------------------------- */
+/* tiles (Sec. 3: the magnet as N uniformly magnetised cuboid tiles)       */
+/* ---------------------------------------------------------------------- */
+
+/* Create a tile set of n >= 1 cuboids from HOST arrays (copied):
+ *   centre[3n], edge[3n] (full edge lengths, > 0), Ms[n] (> 0), Aex[n],
+ *   Ku[n], axis[3n] (easy axis, normalised by the call),
+ *   nbr[6n] face neighbours (-x,+x,-y,+y,-z,+z; -1 = free surface) of a
+ *   Cartesian (tensor-product) mesh, used by the finite-difference exchange
+ *   of Sec. 3 with the Neumann boundary of Eq. 3; nbr == NULL disables
+ *   exchange coupling.
+ * Errors: MT_EINVAL (n < 1, NULL array, non-finite or non-positive value,
+ * neighbour index out of range), MT_ECUDA. */
+MT_API mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const double *edge,
+                          const double *Ms, const double *Aex, const double *Ku, const double *axis,
+                          const int32_t *nbr, mt_tiles **out);
+MT_API void mt_tiles_destroy(mt_tiles *tiles);
+
+/* ---------------------------------------------------------------------- */
+/* demagnetization tensor (Sec. 3, Sec. 3.1, Sec. 3.2)                     */
+/* ---------------------------------------------------------------------- */
+
+/* Assemble N on the device: one thread per 3x3 block (i, j) evaluates the
+ * closed-form tensor of cuboid j at the centre of tile i in FP64 (all
+ * 8-corner arctan/log sums), then stores the 6 unique entries of each
+ * symmetric block in `prec` in a tile-blocked layout.  Synchronous.  The
+ * tiles must outlive the tensor.
+ * Errors: MT_EOVERLAP (two tiles overlap, or a centre lies inside/on
+ * another tile), MT_ENOMEM (allocation failed or the context budget would
+ * be exceeded), MT_EINVAL, MT_ECUDA. */
+MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out);
+MT_API void mt_tensor_destroy(mt_tensor *T);
+MT_API mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info);
+
+/* Copy the stored blocks of rows [i0, i1) back to HOST memory as FP64,
+ * out[((i - i0) * n + j) * 6 + e], e = xx, xy, xz, yy, yz, zz.  For the
+ * BF16 precisions the dequantised dense value is returned and near blocks
+ * (held apart in FP64) are merged in.  Synchronous.  Errors: MT_EINVAL. */
+MT_API mt_status mt_tensor_read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out);
+
+/* Evaluate selected blocks in FP64 on the device with the assembly kernel's
+ * arithmetic: pairs[2p] = i (field point tile), pairs[2p+1] = j (source
+ * tile), out[6p + e].  HOST arrays; synchronous.  Errors: MT_EINVAL. */
+MT_API mt_status mt_demag_blocks(mt_tiles *tiles, int64_t count, const int64_t *pairs, double *out);
+
+/* H_d = -N (Ms m) for B simulations (Eq. 9 / Eq. 17): m and H are DEVICE
+ * arrays of B*3n floats (tile-major per simulation).  The stored tensor is
+ * streamed once per simulation.  Errors: MT_EINVAL, MT_ECUDA. */
+MT_API mt_status mt_demag_field(mt_tensor *T, const float *m, int B, float *H, void *stream);
+
+/* The same product for an FP64 tensor, in FP64: m and H are DEVICE arrays
+ * of B*3n doubles; accumulation in FP64.  Errors: MT_EINVAL (tensor not
+ * MT_F64), MT_ECUDA. */
+MT_API mt_status mt_demag_field_f64(mt_tensor *T, const double *m, int B, double *H, void *stream);
+
+/* Landau-Lifshitz right-hand side (Eq. 1 or its Gilbert form) at m for B
+ * simulations: dmdt (DEVICE, B*3n floats) = f(m, H_eff) with
+ * H_eff = H_d + H_ex + H_an + H_a.  tau (DEVICE, B floats, may be NULL)
+ * receives max_i |m_i x H_eff,i| / Ms_i per simulation.
+ * Errors: MT_EINVAL, MT_ECUDA. */
+MT_API mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m, int B, float *dmdt,
+                     float *tau, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* time integration (Sec. 3.1: explicit Runge-Kutta (4,5))                  */
+/* ---------------------------------------------------------------------- */
+
+/* An integrator holds the device state of B simulations on one tensor and
+ * a CUDA graph of one Dormand-Prince step (6 right-hand sides, embedded
+ * error, accept/reject, renormalisation |m_i| = 1, step-size control, all
+ * decided on the device).  Parameters and options are copied.  `stream` is
+ * the caller's stream (NULL = legacy default stream); see
+ * mt_integrator_stream.
+ * Errors: MT_EINVAL, MT_ENOMEM, MT_ECUDA. */
+MT_API mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, int B,
+                               void *stream, mt_integrator **out);
+MT_API void mt_integrator_destroy(mt_integrator *I);
+
+/* Load the state (B*3n floats; host or device pointer as flagged) and set
+ * t = t0 for every simulation; resets step counters.  Asynchronous on the
+ * integrator's stream (a host source must stay valid until the next
+ * synchronising call). */
+MT_API mt_status mt_integrator_set_state(mt_integrator *I, const float *m, int m_is_host, double t0);
+
+/* Copy the state out (B*3n floats) to host or device memory.  Synchronous
+ * when the destination is host memory. */
+MT_API mt_status mt_integrator_get_state(mt_integrator *I, float *m, int m_is_host);
+
+/* The CUDA stream (cudaStream_t as void*) on which the integrator launches
+ * its kernels and graph replays.  It is private to the integrator and
+ * non-blocking; set_state/get_state order it against the caller's stream
+ * with events.  Use it to time or synchronise mt_integrator_step. */
+MT_API void *mt_integrator_stream(mt_integrator *I);
+
+/* Change the applied field / damping of the batch (host arrays, copied). */
+MT_API mt_status mt_integrator_set_params(mt_integrator *I, const mt_llg_params *p);
+
+/* Take exactly `nsteps` attempted steps (accepted or rejected) for every
+ * simulation, with no time limit.  Asynchronous. */
+MT_API mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps);
+
+/* Integrate every simulation from its current time to t1, writing the
+ * volume-weighted mean magnetisation at t_k = t + (k+1)(t1 - t)/n_out,
+ * k < n_out, into mavg (HOST, n_out*B*3 doubles, may be NULL).
+ * Synchronous; per-simulation outcome in stats (HOST, B entries, may be NULL).
+ * Returns MT_OK if every simulation reached t1, else the first failing
+ * simulation's status (MT_ENOCONV at the step cap, MT_ENONFINITE). */
+MT_API mt_status mt_integrator_run(mt_integrator *I, double t1, int64_t n_out, double *mavg, mt_stats *stats);
+
+/* Relax every simulation (Eq. 2): integrate until
+ * max_i |m_i x H_eff,i| / Ms_i < tol, or report MT_ENOCONV once the time
+ * t_max is spent.  Synchronous. */
+MT_API mt_status mt_integrator_relax(mt_integrator *I, double tol, double t_max, mt_stats *stats);
+
+/* Per-simulation counters since the last set_state.  Synchronous. */
+MT_API mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats);
+
+/* One-call forms of the above on DEVICE state m (B*3n floats, in/out). */
+MT_API mt_status mt_integrate(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, float *m, int B,
+                       double t0, double t1, int64_t n_out, double *mavg, mt_stats *stats, void *stream);
+MT_API mt_status mt_relax(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, double tol, double t_max,
+                   float *m, int B, mt_stats *stats, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MT_H */

@@ -1,0 +1,355 @@
+"""Thin Python binding of the C ABI in include/mt.h (libmagtile.so).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions carry the ABI's names; handles are wrapped in small
+owner objects that release them.  Device buffers are torch CUDA tensors
+(torch provides memory and streams, nothing else).  If the library has not
+been built, importing this module raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MT_OK, MT_EINVAL, MT_ENOMEM, MT_EOVERLAP, MT_ENOCONV, MT_ETIMEOUT, MT_ENONFINITE, MT_ECUDA, MT_EBUSY = range(9)
+MT_F64, MT_F32, MT_BF16_SCALED, MT_BF16_SPLIT = range(4)
+MT_FORM_GILBERT, MT_FORM_LL = 0, 1
+PREC_NAMES = {"f64": MT_F64, "f32": MT_F32, "bf16": MT_BF16_SCALED, "bf16_scaled": MT_BF16_SCALED,
+              "split": MT_BF16_SPLIT, "bf16_split": MT_BF16_SPLIT}
+
+
+class MtError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__("%s failed with status %d: %s" % (where, status, message))
+        self.status = status
+
+
+class LlgParams(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_void_p), ("Ha", ctypes.c_void_p),
+                ("form", ctypes.c_int), ("precess", ctypes.c_int)]
+
+
+class OdeOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("h0", ctypes.c_double),
+                ("hmax", ctypes.c_double), ("max_steps", ctypes.c_int64), ("fixed_h", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_accept", ctypes.c_int64), ("n_reject", ctypes.c_int64), ("n_rhs", ctypes.c_int64),
+                ("t", ctypes.c_double), ("h", ctypes.c_double), ("tau", ctypes.c_double),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class TensorInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("prec", ctypes.c_int32), ("rows_per_panel", ctypes.c_int32),
+                ("cols_per_chunk", ctypes.c_int32), ("bytes", ctypes.c_int64), ("near_blocks", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_I = ctypes.c_int
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); mirrors include/mt.h
+_SIGS = {
+    "mt_version": (ctypes.c_char_p, []),
+    "mt_last_error": (ctypes.c_char_p, []),
+    "mt_ctx_create": (_I, [_I, ctypes.c_size_t, _PP]),
+    "mt_ctx_destroy": (None, [_P]),
+    "mt_ctx_bytes_in_use": (ctypes.c_size_t, [_P]),
+    "mt_tiles_create": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _PP]),
+    "mt_tiles_destroy": (None, [_P]),
+    "mt_demag_assemble": (_I, [_P, _I, _PP]),
+    "mt_tensor_destroy": (None, [_P]),
+    "mt_tensor_get_info": (_I, [_P, ctypes.POINTER(TensorInfo)]),
+    "mt_tensor_read_rows": (_I, [_P, _I64, _I64, _P]),
+    "mt_demag_blocks": (_I, [_P, _I64, _P, _P]),
+    "mt_demag_field": (_I, [_P, _P, _I, _P, _P]),
+    "mt_demag_field_f64": (_I, [_P, _P, _I, _P, _P]),
+    "mt_llg_rhs": (_I, [_P, ctypes.POINTER(LlgParams), _P, _I, _P, _P, _P]),
+    "mt_integrator_create": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _I, _P, _PP]),
+    "mt_integrator_destroy": (None, [_P]),
+    "mt_integrator_set_state": (_I, [_P, _P, _I, _D]),
+    "mt_integrator_get_state": (_I, [_P, _P, _I]),
+    "mt_integrator_set_params": (_I, [_P, ctypes.POINTER(LlgParams)]),
+    "mt_integrator_stream": (_P, [_P]),
+    "mt_integrator_step": (_I, [_P, _I64]),
+    "mt_integrator_run": (_I, [_P, _D, _I64, _P, _P]),
+    "mt_integrator_relax": (_I, [_P, _D, _D, _P]),
+    "mt_integrator_stats": (_I, [_P, _P]),
+    "mt_integrate": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _P, _I, _D, _D, _I64, _P, _P,
+                          _P]),
+    "mt_relax": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _D, _D, _P, _I, _P, _P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libmagtile.so; raises if it was not built (no fallback)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libmagtile.so is not built (%s); run paper_2107_05364_gb300.build.build() "
+                              "or __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def _check(status: int, where: str):
+    if status != MT_OK:
+        raise MtError(status, where, lib().mt_last_error().decode())
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a if shape is None else a.reshape(shape)
+
+
+# ---------------------------------------------------------------------------
+# handle owners
+# ---------------------------------------------------------------------------
+class Ctx:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(lib().mt_ctx_create(device, hbm_budget_bytes, ctypes.byref(h)), "mt_ctx_create")
+        self.h = h
+        self.device = device
+
+    def bytes_in_use(self) -> int:
+        return int(lib().mt_ctx_bytes_in_use(self.h))
+
+    def close(self):
+        if self.h:
+            lib().mt_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TilesH:
+    def __init__(self, ctx: Ctx, tiles):
+        self.ctx = ctx
+        self.n = int(tiles.centre.shape[0])
+        arrs = [_f64(tiles.centre), _f64(tiles.edge), _f64(tiles.Ms), _f64(tiles.Aex), _f64(tiles.Ku),
+                _f64(tiles.axis)]
+        nbr = None if tiles.nbr is None else np.ascontiguousarray(tiles.nbr, np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().mt_tiles_create(ctx.h, self.n, *[_ptr(a) for a in arrs], _ptr(nbr), ctypes.byref(h)),
+               "mt_tiles_create")
+        self.h = h
+        self.volume = np.prod(arrs[1].reshape(-1, 3), axis=1)
+
+    def close(self):
+        if self.h:
+            lib().mt_tiles_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TensorH:
+    def __init__(self, tiles: TilesH, prec):
+        prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
+        h = ctypes.c_void_p()
+        _check(lib().mt_demag_assemble(tiles.h, prec, ctypes.byref(h)), "mt_demag_assemble")
+        self.h = h
+        self.tiles = tiles
+        self.n = tiles.n
+        self.prec = prec
+
+    def info(self) -> dict:
+        inf = TensorInfo()
+        _check(lib().mt_tensor_get_info(self.h, ctypes.byref(inf)), "mt_tensor_get_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def close(self):
+        if self.h:
+            lib().mt_tensor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def llg_params(B: int, gamma=2.211e5, alpha=0.02, Ha=(0.0, 0.0, 0.0), form=MT_FORM_GILBERT, precess=1):
+    """Returns (LlgParams, keep-alive arrays)."""
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float64), (B,)))
+    h = np.ascontiguousarray(np.broadcast_to(np.asarray(Ha, np.float64).reshape(-1, 3), (B, 3)))
+    p = LlgParams(float(gamma), a.ctypes.data, h.ctypes.data, int(form), int(precess))
+    return p, (a, h)
+
+
+def ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11, max_steps=10_000_000, fixed_h=0.0):
+    return OdeOpts(float(rtol), float(atol), float(h0), float(hmax), int(max_steps), float(fixed_h))
+
+
+# ---------------------------------------------------------------------------
+# ABI functions (same names)
+# ---------------------------------------------------------------------------
+def mt_version() -> str:
+    return lib().mt_version().decode()
+
+
+def mt_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Ctx:
+    return Ctx(device, hbm_budget_bytes)
+
+
+def mt_tiles_create(ctx: Ctx, tiles) -> TilesH:
+    return TilesH(ctx, tiles)
+
+
+def mt_demag_assemble(tiles: TilesH, prec="f32") -> TensorH:
+    return TensorH(tiles, prec)
+
+
+def mt_tensor_read_rows(T: TensorH, i0: int, i1: int) -> np.ndarray:
+    out = np.empty((i1 - i0, T.n, 6))
+    _check(lib().mt_tensor_read_rows(T.h, i0, i1, _ptr(out)), "mt_tensor_read_rows")
+    return out
+
+
+def mt_demag_blocks(tiles: TilesH, pairs) -> np.ndarray:
+    pr = np.ascontiguousarray(pairs, np.int64).reshape(-1, 2)
+    out = np.empty((pr.shape[0], 6))
+    _check(lib().mt_demag_blocks(tiles.h, pr.shape[0], _ptr(pr), _ptr(out)), "mt_demag_blocks")
+    return out
+
+
+def mt_demag_field(T: TensorH, m, H, B: int = 1, stream=None):
+    """m, H: torch CUDA float32 tensors of B*3n elements."""
+    _check(lib().mt_demag_field(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field")
+
+
+def mt_demag_field_f64(T: TensorH, m, H, B: int = 1, stream=None):
+    _check(lib().mt_demag_field_f64(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field_f64")
+
+
+def mt_llg_rhs(T: TensorH, params: LlgParams, m, dmdt, tau=None, B: int = 1, stream=None):
+    _check(lib().mt_llg_rhs(T.h, ctypes.byref(params), _ptr(m), B, _ptr(dmdt), _ptr(tau), _stream(stream)),
+           "mt_llg_rhs")
+
+
+class Integrator:
+    """Owner of an mt_integrator handle (Dormand-Prince state of B sims)."""
+
+    def __init__(self, T: TensorH, params: LlgParams, opts: OdeOpts, B: int = 1, stream=None):
+        h = ctypes.c_void_p()
+        self._stream = _stream(stream)
+        _check(lib().mt_integrator_create(T.h, ctypes.byref(params), ctypes.byref(opts), B, self._stream,
+                                          ctypes.byref(h)), "mt_integrator_create")
+        self.h = h
+        self.T = T
+        self.B = B
+        self.n = T.n
+
+    def set_state(self, m, t0: float = 0.0):
+        """m: numpy float32 (host) or torch CUDA float32, B*3n elements."""
+        is_host = isinstance(m, np.ndarray)
+        if is_host:
+            m = np.ascontiguousarray(m, np.float32)
+            self._host_keep = m
+        _check(lib().mt_integrator_set_state(self.h, _ptr(m), int(is_host), float(t0)), "mt_integrator_set_state")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty((self.B, self.n, 3), np.float32)
+        is_host = isinstance(out, np.ndarray)
+        _check(lib().mt_integrator_get_state(self.h, _ptr(out), int(is_host)), "mt_integrator_get_state")
+        return out
+
+    def set_params(self, params: LlgParams):
+        _check(lib().mt_integrator_set_params(self.h, ctypes.byref(params)), "mt_integrator_set_params")
+
+    def stream_handle(self) -> int:
+        """cudaStream_t of the integrator's launches (for timing)."""
+        return int(lib().mt_integrator_stream(self.h) or 0)
+
+    def step(self, nsteps: int):
+        _check(lib().mt_integrator_step(self.h, int(nsteps)), "mt_integrator_step")
+
+    def run(self, t1: float, n_out: int = 1, check: bool = True):
+        mavg = np.zeros((n_out, self.B, 3))
+        st = (Stats * self.B)()
+        s = lib().mt_integrator_run(self.h, float(t1), int(n_out), _ptr(mavg), st)
+        if check:
+            _check(s, "mt_integrator_run")
+        return s, mavg, [x.as_dict() for x in st]
+
+    def relax(self, tol: float, t_max: float, check: bool = True):
+        st = (Stats * self.B)()
+        s = lib().mt_integrator_relax(self.h, float(tol), float(t_max), st)
+        if check:
+            _check(s, "mt_integrator_relax")
+        return s, [x.as_dict() for x in st]
+
+    def stats(self):
+        st = (Stats * self.B)()
+        _check(lib().mt_integrator_stats(self.h, st), "mt_integrator_stats")
+        return [x.as_dict() for x in st]
+
+    def close(self):
+        if self.h:
+            lib().mt_integrator_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mt_integrator_create(T: TensorH, params: LlgParams, opts: OdeOpts, B: int = 1, stream=None) -> Integrator:
+    return Integrator(T, params, opts, B, stream)

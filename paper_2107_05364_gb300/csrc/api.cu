@@ -1,0 +1,370 @@
+// C ABI of libmagtile: contexts, tile sets, tensors and the field / RHS
+// entry points.  The integrator lives in llg.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "mt_internal.cuh"
+
+namespace {
+thread_local std::string g_err;
+}
+
+namespace mt {
+
+void set_error(const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+mt_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  set_error("CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+  return e == cudaErrorMemoryAllocation ? MT_ENOMEM : MT_ECUDA;
+}
+
+}  // namespace mt
+
+namespace {
+
+template <typename P>
+mt_status upload(P **dst, const P *src, size_t count) {
+  MT_CUDA(cudaMalloc((void **)dst, sizeof(P) * std::max<size_t>(count, 1)));
+  MT_CUDA(cudaMemcpy(*dst, src, sizeof(P) * count, cudaMemcpyHostToDevice));
+  return MT_OK;
+}
+
+void free_tiles(mt_tiles *t) {
+  cudaFree(t->d_centre);
+  cudaFree(t->d_edge);
+  cudaFree(t->d_Ms);
+  cudaFree(t->d_wex);
+  cudaFree(t->d_nbr);
+  cudaFree(t->d_kan);
+  cudaFree(t->d_axis);
+  cudaFree(t->d_wvol);
+  delete t;
+}
+
+void free_tensor_mem(mt_tensor *T) {
+  cudaFree(T->d_data);
+  cudaFree(T->d_scale);
+  cudaFree(T->d_near_ptr);
+  cudaFree(T->d_near_col);
+  cudaFree(T->d_near_val);
+  cudaFree(T->d_xs);
+  cudaFree(T->d_part);
+  cudaFree(T->d_count);
+  cudaFree(T->d_Hd);
+}
+
+// workspace of the standalone field/rhs calls for B simulations
+mt_status ensure_workspace(mt_tensor *T, int B) {
+  if (T->xs_B < B) {
+    cudaFree(T->d_xs);
+    T->d_xs = nullptr;
+    const size_t bytes = sizeof(float) * mt::xs_floats(T) * B;
+    MT_CUDA(cudaMalloc(&T->d_xs, bytes));
+    MT_CUDA(cudaMemset(T->d_xs, 0, bytes));
+    T->xs_B = B;
+  }
+  if (!T->d_part) {
+    MT_CUDA(cudaMalloc(&T->d_part, mt::matvec_part_bytes(T)));
+  }
+  if (T->count_B < B) {
+    cudaFree(T->d_count);
+    T->d_count = nullptr;
+    const size_t bytes = mt::matvec_count_bytes(T, B);
+    MT_CUDA(cudaMalloc(&T->d_count, bytes));
+    MT_CUDA(cudaMemset(T->d_count, 0, bytes));
+    T->count_B = B;
+  }
+  if (T->Hd_B < B) {
+    cudaFree(T->d_Hd);
+    T->d_Hd = nullptr;
+    MT_CUDA(cudaMalloc(&T->d_Hd, sizeof(float) * 3 * T->n * B));
+    T->Hd_B = B;
+  }
+  return MT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mt_version(void) { return "magtile 0.1 (sm_103a)"; }
+
+const char *mt_last_error(void) { return g_err.c_str(); }
+
+mt_status mt_ctx_create(int device, size_t hbm_budget_bytes, mt_ctx **out) {
+  MT_CHECK(out, MT_EINVAL, "mt_ctx_create: out is NULL");
+  int ndev = 0;
+  MT_CUDA(cudaGetDeviceCount(&ndev));
+  MT_CHECK(device >= 0 && device < ndev, MT_EINVAL, "mt_ctx_create: device %d of %d", device, ndev);
+  MT_CUDA(cudaSetDevice(device));
+  cudaDeviceProp prop;
+  MT_CUDA(cudaGetDeviceProperties(&prop, device));
+  MT_CHECK(prop.major * 10 + prop.minor >= 100, MT_EINVAL,
+           "mt_ctx_create: device %d is sm_%d%d; this library is built for sm_103a", device, prop.major,
+           prop.minor);
+  mt_ctx *c = new mt_ctx();
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) {
+    delete c;
+    return mt::cuda_fail(e, "cudaMemGetInfo", __FILE__, __LINE__);
+  }
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+  e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = mt::matvec_prepare();
+  if (e != cudaSuccess) {
+    cudaFree(c->d_status);
+    delete c;
+    return mt::cuda_fail(e, "mt_ctx_create", __FILE__, __LINE__);
+  }
+  *out = c;
+  return MT_OK;
+}
+
+void mt_ctx_destroy(mt_ctx *ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+size_t mt_ctx_bytes_in_use(const mt_ctx *ctx) { return ctx ? ctx->in_use : 0; }
+
+mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const double *edge, const double *Ms,
+                          const double *Aex, const double *Ku, const double *axis, const int32_t *nbr,
+                          mt_tiles **out) {
+  MT_CHECK(ctx && out, MT_EINVAL, "mt_tiles_create: NULL handle");
+  MT_CHECK(n >= 1 && n <= (int64_t)1 << 26, MT_EINVAL, "mt_tiles_create: n = %lld out of range", (long long)n);
+  MT_CHECK(centre && edge && Ms && Aex && Ku && axis, MT_EINVAL, "mt_tiles_create: NULL array");
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 3; ++a) {
+      MT_CHECK(std::isfinite(centre[3 * i + a]) && std::isfinite(axis[3 * i + a]), MT_EINVAL,
+               "mt_tiles_create: non-finite centre/axis at tile %lld", (long long)i);
+      MT_CHECK(std::isfinite(edge[3 * i + a]) && edge[3 * i + a] > 0, MT_EINVAL,
+               "mt_tiles_create: edge of tile %lld must be positive", (long long)i);
+    }
+    MT_CHECK(std::isfinite(Ms[i]) && Ms[i] > 0, MT_EINVAL, "mt_tiles_create: Ms of tile %lld must be positive",
+             (long long)i);
+    MT_CHECK(std::isfinite(Aex[i]) && std::isfinite(Ku[i]), MT_EINVAL,
+             "mt_tiles_create: non-finite A_ex/K_u at tile %lld", (long long)i);
+    if (nbr)
+      for (int f = 0; f < 6; ++f) {
+        const int32_t p = nbr[6 * i + f];
+        MT_CHECK(p >= -1 && p < n && p != i, MT_EINVAL, "mt_tiles_create: bad neighbour %d of tile %lld", p,
+                 (long long)i);
+      }
+  }
+  MT_CUDA(cudaSetDevice(ctx->device));
+  mt_tiles *t = new mt_tiles();
+  t->ctx = ctx;
+  t->n = n;
+  t->centre.assign(centre, centre + 3 * n);
+  t->edge.assign(edge, edge + 3 * n);
+  t->Ms.assign(Ms, Ms + n);
+  t->Aex.assign(Aex, Aex + n);
+  t->Ku.assign(Ku, Ku + n);
+  t->axis.resize(3 * n);
+  std::vector<float> msf(n), kan(n), axf(3 * n), wex(6 * n, 0.0f);
+  std::vector<double> wvol(n);
+  double vt = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double *e = &axis[3 * i];
+    double nr = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    for (int a = 0; a < 3; ++a) {
+      const double v = nr > 0 ? e[a] / nr : (a == 2 ? 1.0 : 0.0);
+      t->axis[3 * i + a] = v;
+      axf[3 * i + a] = (float)v;
+    }
+    msf[i] = (float)Ms[i];
+    kan[i] = (float)(2.0 * Ku[i] / (MT_MU0 * Ms[i]));
+    wvol[i] = edge[3 * i] * edge[3 * i + 1] * edge[3 * i + 2];
+    vt += wvol[i];
+  }
+  for (auto &v : wvol) v /= vt;
+  if (nbr) {
+    t->nbr.assign(nbr, nbr + 6 * n);
+    t->has_exchange = true;
+    // finite-volume exchange weights (Eq. 12): 2 A_i / (mu0 Ms_i h_i d_ip)
+    for (int64_t i = 0; i < n; ++i)
+      for (int f = 0; f < 6; ++f) {
+        const int32_t p = nbr[6 * i + f];
+        if (p < 0) continue;
+        const int ax = f / 2;
+        const double d = std::fabs(centre[3 * p + ax] - centre[3 * i + ax]);
+        const double h = edge[3 * i + ax];
+        if (!(d > 0)) {
+          free_tiles(t);
+          mt::set_error("mt_tiles_create: neighbour %d of tile %lld has the same centre", p, (long long)i);
+          return MT_EINVAL;
+        }
+        wex[6 * i + f] = (float)(2.0 * Aex[i] / (MT_MU0 * Ms[i] * h * d));
+      }
+  }
+  std::vector<int32_t> nb(6 * n, -1);
+  if (nbr) std::copy(nbr, nbr + 6 * n, nb.begin());
+  mt_status st = MT_OK;
+  if ((st = upload(&t->d_centre, centre, 3 * n)) != MT_OK || (st = upload(&t->d_edge, edge, 3 * n)) != MT_OK ||
+      (st = upload(&t->d_Ms, msf.data(), n)) != MT_OK || (st = upload(&t->d_wex, wex.data(), 6 * n)) != MT_OK ||
+      (st = upload(&t->d_nbr, nb.data(), 6 * n)) != MT_OK || (st = upload(&t->d_kan, kan.data(), n)) != MT_OK ||
+      (st = upload(&t->d_axis, axf.data(), 3 * n)) != MT_OK || (st = upload(&t->d_wvol, wvol.data(), n)) != MT_OK) {
+    free_tiles(t);
+    return st;
+  }
+  *out = t;
+  return MT_OK;
+}
+
+void mt_tiles_destroy(mt_tiles *tiles) {
+  if (tiles) free_tiles(tiles);
+}
+
+mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
+  MT_CHECK(tiles && out, MT_EINVAL, "mt_demag_assemble: NULL argument");
+  MT_CHECK(prec >= MT_F64 && prec <= MT_BF16_SPLIT, MT_EINVAL, "mt_demag_assemble: bad precision %d", (int)prec);
+  mt_ctx *ctx = tiles->ctx;
+  MT_CUDA(cudaSetDevice(ctx->device));
+  mt_tensor *T = new mt_tensor();
+  T->tiles = tiles;
+  T->prec = prec;
+  T->n = tiles->n;
+  mt::layout_for(prec, &T->L);
+  T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
+  T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
+  const size_t data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
+  const size_t scale_bytes = (size_t)T->L.P * T->L.Q * T->L.scale_bytes_per_chunk;
+  T->bytes = data_bytes + scale_bytes;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->in_use + T->bytes > ctx->budget) {
+      mt::set_error("mt_demag_assemble: %zu bytes exceed the context budget (%zu of %zu in use)", T->bytes,
+                    ctx->in_use, ctx->budget);
+      delete T;
+      return MT_ENOMEM;
+    }
+    ctx->in_use += T->bytes;
+  }
+  auto fail = [&](mt_status st) {
+    free_tensor_mem(T);
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      ctx->in_use -= T->bytes;
+    }
+    delete T;
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&T->d_data, data_bytes);
+  if (e == cudaSuccess) e = cudaMemset(T->d_data, 0, data_bytes);
+  if (e == cudaSuccess && scale_bytes) {
+    e = cudaMalloc(&T->d_scale, scale_bytes);
+    if (e == cudaSuccess) e = cudaMemset(T->d_scale, 0, scale_bytes);
+  }
+  if (e != cudaSuccess) return fail(mt::cuda_fail(e, "tensor allocation", __FILE__, __LINE__));
+  mt_status st = mt::assemble(T);
+  if (st != MT_OK) return fail(st);
+  *out = T;
+  return MT_OK;
+}
+
+void mt_tensor_destroy(mt_tensor *T) {
+  if (!T) return;
+  cudaDeviceSynchronize();
+  free_tensor_mem(T);
+  {
+    std::lock_guard<std::mutex> lk(T->tiles->ctx->mu);
+    T->tiles->ctx->in_use -= T->bytes;
+  }
+  delete T;
+}
+
+mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
+  MT_CHECK(T && info, MT_EINVAL, "mt_tensor_get_info: NULL argument");
+  info->n = T->n;
+  info->prec = T->prec;
+  info->rows_per_panel = T->L.TR;
+  info->cols_per_chunk = T->L.TC;
+  info->bytes = (int64_t)T->bytes;
+  info->near_blocks = T->near_count;
+  return MT_OK;
+}
+
+mt_status mt_tensor_read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
+  MT_CHECK(T && out, MT_EINVAL, "mt_tensor_read_rows: NULL argument");
+  MT_CHECK(0 <= i0 && i0 <= i1 && i1 <= T->n, MT_EINVAL, "mt_tensor_read_rows: bad row range");
+  return mt::read_rows(T, i0, i1, out);
+}
+
+mt_status mt_demag_blocks(mt_tiles *tiles, int64_t count, const int64_t *pairs, double *out) {
+  MT_CHECK(tiles && count >= 0 && (count == 0 || (pairs && out)), MT_EINVAL, "mt_demag_blocks: bad argument");
+  MT_CUDA(cudaSetDevice(tiles->ctx->device));
+  return mt::blocks_fp64(tiles, count, pairs, out);
+}
+
+mt_status mt_demag_field(mt_tensor *T, const float *m, int B, float *H, void *stream) {
+  MT_CHECK(T && m && H, MT_EINVAL, "mt_demag_field: NULL argument");
+  MT_CHECK(B >= 1, MT_EINVAL, "mt_demag_field: B must be >= 1");
+  MT_CHECK(T->prec != MT_F64, MT_EINVAL, "mt_demag_field: FP64 tensors use mt_demag_field_f64");
+  mt_status st = ensure_workspace(T, B);
+  if (st != MT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  mt::launch_prep_xs(T, m, B, T->d_xs, s);
+  mt::launch_matvec(T, T->d_xs, B, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+  mt::launch_near(T, m, B, H, nullptr, s);
+  MT_CUDA(cudaGetLastError());
+  return MT_OK;
+}
+
+mt_status mt_demag_field_f64(mt_tensor *T, const double *m, int B, double *H, void *stream) {
+  MT_CHECK(T && m && H, MT_EINVAL, "mt_demag_field_f64: NULL argument");
+  MT_CHECK(B >= 1, MT_EINVAL, "mt_demag_field_f64: B must be >= 1");
+  MT_CHECK(T->prec == MT_F64, MT_EINVAL, "mt_demag_field_f64: needs an FP64 tensor");
+  mt_status st = ensure_workspace(T, B);
+  if (st != MT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  mt::launch_prep_xs_f64(T, m, B, reinterpret_cast<double *>(T->d_xs), s);
+  mt::launch_matvec(T, T->d_xs, B, reinterpret_cast<float *>(H), T->d_part, T->d_count, nullptr,
+                    T->tiles->ctx->d_status, s);
+  MT_CUDA(cudaGetLastError());
+  return MT_OK;
+}
+
+mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m, int B, float *dmdt, float *tau,
+                     void *stream) {
+  MT_CHECK(T && p && m && dmdt && p->alpha && p->Ha, MT_EINVAL, "mt_llg_rhs: NULL argument");
+  MT_CHECK(B >= 1, MT_EINVAL, "mt_llg_rhs: B must be >= 1");
+  MT_CHECK(T->prec != MT_F64, MT_EINVAL, "mt_llg_rhs: the FP64 tensor serves field checks only");
+  mt_status st = ensure_workspace(T, B);
+  if (st != MT_OK) return st;
+  std::vector<float> g1, g2, ha;
+  mt::llg_prefactors(p, B, g1, g2, ha);
+  float *d_par = nullptr;
+  MT_CUDA(cudaMalloc(&d_par, sizeof(float) * 5 * B));
+  cudaStream_t s = (cudaStream_t)stream;
+  MT_CUDA(cudaMemcpyAsync(d_par, g1.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
+  MT_CUDA(cudaMemcpyAsync(d_par + B, g2.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
+  MT_CUDA(cudaMemcpyAsync(d_par + 2 * B, ha.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice, s));
+  mt::launch_prep_xs(T, m, B, T->d_xs, s);
+  mt::launch_matvec(T, T->d_xs, B, T->d_Hd, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+  mt::launch_near(T, m, B, T->d_Hd, nullptr, s);
+  if (tau) MT_CUDA(cudaMemsetAsync(tau, 0, sizeof(float) * B, s));
+  mt::launch_rhs_plain(T, m, T->d_Hd, B, d_par, d_par + B, d_par + 2 * B, dmdt, tau, s);
+  MT_CUDA(cudaGetLastError());
+  // the parameter block must outlive the kernels
+  MT_CUDA(cudaStreamSynchronize(s));
+  cudaFree(d_par);
+  return MT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,385 @@
+// Tensor assembly (FP64) and packing into the tile-blocked storage.
+//
+// Sec. 3 of the paper: the field of every uniformly magnetised cuboid tile
+// is evaluated analytically at the centre of every other tile; the tensor is
+// computed once, at the start (Sec. 3.1), and stored in a reduced precision
+// (FP32 in the paper, Sec. 3.2).  One thread evaluates one 3x3 block in FP64
+// and stores its 6 unique entries directly in the requested precision.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "mt_internal.cuh"
+
+namespace {
+
+// Tensor of the cuboid (centre c, full edges e) at the point r, from the
+// Newtonian potential Phi of the box:  N = -(1/4 pi) grad grad Phi, so that
+// H = -N M.  Faces are numbered low (0) / high (1) on each axis; the sign of
+// a corner is +1 when an odd number of its faces are high faces... i.e.
+// s = -(-1)^(f_x + f_y + f_z).
+//   N_xx = -(1/4 pi) sum_corners s atan(dy dz / (dx R))
+//   N_xy = +(1/4 pi) sum_corners s log(dz + R)         (xz: dy, yz: dx)
+// dx == 0 (point in a face plane, outside the face): the arctan term is 0,
+// its +-pi/2 limits cancel between corners.  A log pair whose two offsets
+// are both negative is rewritten with log(R - d), exact and free of the
+// cancellation of d + R when the point lies far on the negative side.
+struct Corners {
+  double d[3][2];  // offsets r - face, [axis][face]
+  double R[8];     // corner distance, index fx | fy << 1 | fz << 2
+};
+
+__device__ __forceinline__ double atan_ratio(double num_a, double num_b, double den, double R) {
+  return den == 0.0 ? 0.0 : atan((num_a * num_b) / (den * R));
+}
+
+// log(dp + Rp) - log(dm + Rm) for the two faces (m = low face, p = high face)
+// of one axis, with the fixed other two corner coordinates.
+__device__ __forceinline__ double log_diff(double dm, double Rm, double dp, double Rp) {
+  if (dm < 0.0 && dp < 0.0) return log(Rm - dm) - log(Rp - dp);
+  return log(dp + Rp) - log(dm + Rm);
+}
+
+__device__ void cuboid_tensor(const double *r, const double *c, const double *e, double out[6]) {
+  Corners K;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    K.d[a][0] = r[a] - (c[a] - 0.5 * e[a]);
+    K.d[a][1] = r[a] - (c[a] + 0.5 * e[a]);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double x = K.d[0][q & 1], y = K.d[1][(q >> 1) & 1], z = K.d[2][(q >> 2) & 1];
+    K.R[q] = sqrt(x * x + y * y + z * z);
+  }
+  double txx = 0.0, tyy = 0.0, tzz = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const double s = (__popc(q) & 1) ? 1.0 : -1.0;
+    const double x = K.d[0][q & 1], y = K.d[1][(q >> 1) & 1], z = K.d[2][(q >> 2) & 1];
+    txx += s * atan_ratio(y, z, x, K.R[q]);
+    tyy += s * atan_ratio(x, z, y, K.R[q]);
+    tzz += s * atan_ratio(x, y, z, K.R[q]);
+  }
+  // Off-diagonal entries: pair the two faces of the log's axis.  For a pair
+  // with the other two faces (f1, f2) fixed, the corner with the low face
+  // has sign s_lo = -(-1)^(f1+f2) and the high-face corner -s_lo, so the pair
+  // contributes s_lo (log(d_lo + R_lo) - log(d_hi + R_hi)) = -s_lo log_diff.
+  double txy = 0.0, txz = 0.0, tyz = 0.0;
+#pragma unroll
+  for (int f1 = 0; f1 < 2; ++f1) {
+#pragma unroll
+    for (int f2 = 0; f2 < 2; ++f2) {
+      const double s_lo = ((f1 + f2) & 1) ? 1.0 : -1.0;
+      // xy: log axis z, fixed (fx = f1, fy = f2)
+      txy -= s_lo * log_diff(K.d[2][0], K.R[f1 | (f2 << 1)], K.d[2][1], K.R[f1 | (f2 << 1) | 4]);
+      // xz: log axis y, fixed (fx = f1, fz = f2)
+      txz -= s_lo * log_diff(K.d[1][0], K.R[f1 | (f2 << 2)], K.d[1][1], K.R[f1 | 2 | (f2 << 2)]);
+      // yz: log axis x, fixed (fy = f1, fz = f2)
+      tyz -= s_lo * log_diff(K.d[0][0], K.R[(f1 << 1) | (f2 << 2)], K.d[0][1], K.R[1 | (f1 << 1) | (f2 << 2)]);
+    }
+  }
+  const double k = 0.25 / MT_PI;
+  out[0] = -k * txx;
+  out[1] = k * txy;
+  out[2] = k * txz;
+  out[3] = -k * tyy;
+  out[4] = k * tyz;
+  out[5] = -k * tzz;
+}
+
+// Geometry relations of tiles i and j (i != j): bit 0 = volumes overlap or
+// the centre of i lies in/on tile j (invalid), bit 1 = the closed boxes touch
+// (a "near" pair, kept in FP64 for the BF16 precisions).
+__device__ __forceinline__ int pair_relation(const double *ci, const double *ei, const double *cj,
+                                             const double *ej) {
+  bool vol = true, pt = true, touch = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const double d = fabs(ci[a] - cj[a]);
+    const double half = 0.5 * (ei[a] + ej[a]);
+    const double tol = 1e-12 * (ei[a] + ej[a]);
+    vol = vol && (d < half - tol);
+    pt = pt && (d <= 0.5 * ej[a] + tol);
+    touch = touch && (d <= half * (1.0 + 1e-9));
+  }
+  return ((vol || pt) ? 1 : 0) | (touch ? 2 : 0);
+}
+
+__device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, int e, int TR, int TC, int nplane,
+                                                int64_t Q) {
+  const int64_t p = i / TR, q = j / TC;
+  const int r = (int)(i - p * TR), c = (int)(j - q * TC);
+  return (((p * Q + q) * nplane + e) * TR + r) * (int64_t)TC + c;
+}
+
+__device__ __forceinline__ int64_t scale_index(int64_t i, int64_t j, int TR, int TC, int64_t Q) {
+  const int64_t p = i / TR, q = j / TC;
+  const int r = (int)(i - p * TR), c = (int)(j - q * TC);
+  return ((p * Q + q) * TR + r) * (int64_t)TC + c;
+}
+
+struct AsmArgs {
+  const double *centre, *edge;
+  int64_t n;
+  int TR, TC, nplane;
+  int64_t Q;
+  int prec;
+  void *data;
+  int8_t *scale;
+  int *bad;           // set to 1 on overlap
+  int *near_fill;     // per-row fill counter (BF16 precisions)
+  const int32_t *near_ptr;
+  int32_t *near_col;
+  double *near_val;
+  int count_only;     // 1: only count near blocks per row into near_fill
+};
+
+// grid (Q, P); TC threads; thread = column j of the chunk, loop over the
+// panel's TR rows i.
+__global__ void k_assemble(AsmArgs A) {
+  const int64_t q = blockIdx.x, p = blockIdx.y;
+  const int64_t j = q * A.TC + threadIdx.x;
+  if (j >= A.n) return;
+  double cj[3], ej[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    cj[a] = A.centre[3 * j + a];
+    ej[a] = A.edge[3 * j + a];
+  }
+  for (int r = 0; r < A.TR; ++r) {
+    const int64_t i = p * A.TR + r;
+    if (i >= A.n) break;
+    double ci[3], ei[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      ci[a] = A.centre[3 * i + a];
+      ei[a] = A.edge[3 * i + a];
+    }
+    int rel = (i == j) ? 2 : pair_relation(ci, ei, cj, ej);
+    if (rel & 1) atomicExch(A.bad, 1);
+    const bool near = (rel & 2) && (A.prec == MT_BF16_SCALED || A.prec == MT_BF16_SPLIT);
+    if (A.count_only) {
+      if (near) atomicAdd(&A.near_fill[i], 1);
+      continue;
+    }
+    double N6[6];
+    cuboid_tensor(ci, cj, ej, N6);
+    if (near) {
+      const int slot = atomicAdd(&A.near_fill[i], 1);
+      const int64_t at = A.near_ptr[i] + slot;
+      A.near_col[at] = (int32_t)j;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) A.near_val[6 * at + e] = N6[e];
+      continue;  // dense store keeps zeros there
+    }
+    switch (A.prec) {
+      case MT_F64: {
+        double *D = (double *)A.data;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) D[layout_index(i, j, e, A.TR, A.TC, 6, A.Q)] = N6[e];
+      } break;
+      case MT_F32: {
+        float *D = (float *)A.data;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) D[layout_index(i, j, e, A.TR, A.TC, 6, A.Q)] = (float)N6[e];
+      } break;
+      case MT_BF16_SCALED: {
+        // power-of-two scale of the block: 2^s with s = exponent of max |N|
+        double mx = 0.0;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) mx = fmax(mx, fabs(N6[e]));
+        int s = 0;
+        if (mx > 0.0) {
+          frexp(mx, &s);
+          s = max(-126, min(126, s));
+        }
+        __nv_bfloat16 *D = (__nv_bfloat16 *)A.data;
+#pragma unroll
+        for (int e = 0; e < 6; ++e)
+          D[layout_index(i, j, e, A.TR, A.TC, 6, A.Q)] = __double2bfloat16(ldexp(N6[e], -s));
+        A.scale[scale_index(i, j, A.TR, A.TC, A.Q)] = (int8_t)s;
+      } break;
+      case MT_BF16_SPLIT: {
+        __nv_bfloat16 *D = (__nv_bfloat16 *)A.data;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) {
+          const __nv_bfloat16 hi = __double2bfloat16(N6[e]);
+          const __nv_bfloat16 lo = __double2bfloat16(N6[e] - (double)__bfloat162float(hi));
+          D[layout_index(i, j, e, A.TR, A.TC, 12, A.Q)] = hi;
+          D[layout_index(i, j, 6 + e, A.TR, A.TC, 12, A.Q)] = lo;
+        }
+      } break;
+    }
+  }
+}
+
+// sort each row's near blocks by column so that the FP64 near sum has a
+// fixed order (one thread per row; rows hold at most 27 entries)
+__global__ void k_sort_near(int64_t n, const int32_t *ptr, int32_t *col, double *val) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t b = ptr[i], e = ptr[i + 1];
+  for (int32_t a = b + 1; a < e; ++a) {
+    const int32_t cj = col[a];
+    double v[6];
+    for (int q = 0; q < 6; ++q) v[q] = val[6 * a + q];
+    int32_t z = a - 1;
+    while (z >= b && col[z] > cj) {
+      col[z + 1] = col[z];
+      for (int q = 0; q < 6; ++q) val[6 * (z + 1) + q] = val[6 * z + q];
+      --z;
+    }
+    col[z + 1] = cj;
+    for (int q = 0; q < 6; ++q) val[6 * (z + 1) + q] = v[q];
+  }
+}
+
+__global__ void k_blocks(const double *centre, const double *edge, int64_t count, const int64_t *pairs,
+                         double *out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  const int64_t i = pairs[2 * p], j = pairs[2 * p + 1];
+  cuboid_tensor(&centre[3 * i], &centre[3 * j], &edge[3 * j], &out[6 * p]);
+}
+
+// stored value -> double, rows [i0, i1), all columns; out[((i-i0)*n + j)*6 + e]
+__global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int64_t n, int TR, int TC,
+                            int64_t Q, int64_t i0, int64_t i1, double *out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t rows = i1 - i0;
+  if (t >= rows * n) return;
+  const int64_t i = i0 + t / n, j = t % n;
+  for (int e = 0; e < 6; ++e) {
+    double v = 0.0;
+    switch (prec) {
+      case MT_F64: v = ((const double *)data)[layout_index(i, j, e, TR, TC, 6, Q)]; break;
+      case MT_F32: v = ((const float *)data)[layout_index(i, j, e, TR, TC, 6, Q)]; break;
+      case MT_BF16_SCALED:
+        v = ldexp((double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, e, TR, TC, 6, Q)]),
+                  (int)scale[scale_index(i, j, TR, TC, Q)]);
+        break;
+      case MT_BF16_SPLIT:
+        v = (double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, e, TR, TC, 12, Q)]) +
+            (double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, 6 + e, TR, TC, 12, Q)]);
+        break;
+    }
+    out[t * 6 + e] = v;
+  }
+}
+
+// merge the FP64 near blocks of rows [i0, i1) into out
+__global__ void k_merge_near(int64_t n, int64_t i0, int64_t i1, const int32_t *ptr, const int32_t *col,
+                             const double *val, double *out) {
+  const int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= i1) return;
+  for (int32_t a = ptr[i]; a < ptr[i + 1]; ++a) {
+    const int64_t j = col[a];
+    for (int e = 0; e < 6; ++e) out[((i - i0) * n + j) * 6 + e] = val[6 * a + e];
+  }
+}
+
+}  // namespace
+
+namespace mt {
+
+mt_status assemble(mt_tensor *T) {
+  mt_tiles *t = T->tiles;
+  const int64_t n = T->n;
+  const mt_layout &L = T->L;
+  int *d_bad = nullptr;
+  MT_CUDA(cudaMalloc(&d_bad, sizeof(int)));
+  MT_CUDA(cudaMemset(d_bad, 0, sizeof(int)));
+  AsmArgs A{};
+  A.centre = t->d_centre;
+  A.edge = t->d_edge;
+  A.n = n;
+  A.TR = L.TR;
+  A.TC = L.TC;
+  A.nplane = L.nplane;
+  A.Q = L.Q;
+  A.prec = T->prec;
+  A.data = T->d_data;
+  A.scale = T->d_scale;
+  A.bad = d_bad;
+  const bool has_near = (T->prec == MT_BF16_SCALED || T->prec == MT_BF16_SPLIT);
+  dim3 grid((unsigned)L.Q, (unsigned)L.P);
+  if (has_near) {
+    int *d_fill = nullptr;
+    MT_CUDA(cudaMalloc(&d_fill, sizeof(int) * n));
+    MT_CUDA(cudaMemset(d_fill, 0, sizeof(int) * n));
+    A.near_fill = d_fill;
+    A.count_only = 1;
+    k_assemble<<<grid, L.TC>>>(A);
+    MT_CUDA(cudaGetLastError());
+    std::vector<int> cnt(n);
+    MT_CUDA(cudaMemcpy(cnt.data(), d_fill, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> ptr(n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) ptr[i + 1] = ptr[i] + cnt[i];
+    T->near_count = ptr[n];
+    MT_CUDA(cudaMalloc(&T->d_near_ptr, sizeof(int32_t) * (n + 1)));
+    MT_CUDA(cudaMalloc(&T->d_near_col, sizeof(int32_t) * std::max<int64_t>(1, T->near_count)));
+    MT_CUDA(cudaMalloc(&T->d_near_val, sizeof(double) * 6 * std::max<int64_t>(1, T->near_count)));
+    MT_CUDA(cudaMemcpy(T->d_near_ptr, ptr.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+    MT_CUDA(cudaMemset(d_fill, 0, sizeof(int) * n));
+    A.near_ptr = T->d_near_ptr;
+    A.near_col = T->d_near_col;
+    A.near_val = T->d_near_val;
+    A.count_only = 0;
+    k_assemble<<<grid, L.TC>>>(A);
+    MT_CUDA(cudaGetLastError());
+    k_sort_near<<<(unsigned)((n + 127) / 128), 128>>>(n, T->d_near_ptr, T->d_near_col, T->d_near_val);
+    MT_CUDA(cudaGetLastError());
+    MT_CUDA(cudaDeviceSynchronize());
+    cudaFree(d_fill);
+  } else {
+    k_assemble<<<grid, L.TC>>>(A);
+    MT_CUDA(cudaGetLastError());
+    MT_CUDA(cudaDeviceSynchronize());
+  }
+  int bad = 0;
+  MT_CUDA(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaFree(d_bad);
+  MT_CHECK(!bad, MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
+  return MT_OK;
+}
+
+mt_status blocks_fp64(mt_tiles *t, int64_t count, const int64_t *pairs, double *out) {
+  if (count == 0) return MT_OK;
+  for (int64_t p = 0; p < 2 * count; ++p)
+    MT_CHECK(pairs[p] >= 0 && pairs[p] < t->n, MT_EINVAL, "mt_demag_blocks: pair index out of range");
+  int64_t *d_pairs = nullptr;
+  double *d_out = nullptr;
+  MT_CUDA(cudaMalloc(&d_pairs, sizeof(int64_t) * 2 * count));
+  MT_CUDA(cudaMalloc(&d_out, sizeof(double) * 6 * count));
+  MT_CUDA(cudaMemcpy(d_pairs, pairs, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice));
+  k_blocks<<<(unsigned)((count + 127) / 128), 128>>>(t->d_centre, t->d_edge, count, d_pairs, d_out);
+  MT_CUDA(cudaGetLastError());
+  MT_CUDA(cudaMemcpy(out, d_out, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost));
+  cudaFree(d_pairs);
+  cudaFree(d_out);
+  return MT_OK;
+}
+
+mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
+  const int64_t n = T->n;
+  const int64_t rows = i1 - i0;
+  if (rows <= 0) return MT_OK;
+  double *d_out = nullptr;
+  MT_CUDA(cudaMalloc(&d_out, sizeof(double) * 6 * rows * n));
+  const int64_t tot = rows * n;
+  k_read_rows<<<(unsigned)((tot + 255) / 256), 256>>>(T->d_data, T->d_scale, T->prec, n, T->L.TR, T->L.TC,
+                                                       T->L.Q, i0, i1, d_out);
+  MT_CUDA(cudaGetLastError());
+  if (T->near_count > 0) {
+    k_merge_near<<<(unsigned)((rows + 127) / 128), 128>>>(n, i0, i1, T->d_near_ptr, T->d_near_col,
+                                                          T->d_near_val, d_out);
+    MT_CUDA(cudaGetLastError());
+  }
+  MT_CUDA(cudaMemcpy(out, d_out, sizeof(double) * 6 * rows * n, cudaMemcpyDeviceToHost));
+  cudaFree(d_out);
+  return MT_OK;
+}
+
+}  // namespace mt

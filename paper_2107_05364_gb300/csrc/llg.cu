@@ -1,0 +1,992 @@
+// Effective field, Landau-Lifshitz right-hand side and the Runge-Kutta (4,5)
+// integrator (Sec. 2, Sec. 3.1 of the paper).
+//
+// One Dormand-Prince step of B simulations is a fixed sequence of kernels,
+// captured once in a CUDA graph:
+//   begin      commit the previous step if it was accepted (m <- |m_new|^-1
+//              m_new, k1 <- k7), form the stage-2 input;
+//   6 x [ streaming demag product ; stage kernel ]
+//              a stage kernel adds exchange (Eq. 12), anisotropy (Eq. 16)
+//              and applied field (Eq. 7) to H_d, evaluates Eq. 1 and forms
+//              the next stage's input; the last one also reduces the
+//              embedded error, the torque and the mean magnetisation, and its
+//              last block decides accept/reject and the next step size on
+//              the device.
+// The host only replays the graph and polls a counter of unfinished
+// simulations every few steps.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mt_internal.cuh"
+
+namespace {
+
+// Dormand & Prince (1980) RK5(4)7M: stage couplings, 5th-order weights
+// (= last coupling row, first same as last) and the difference between the
+// 5th- and the embedded 4th-order weights, which estimates the local error.
+__constant__ double c_dp_a[7][7] = {
+    {0, 0, 0, 0, 0, 0, 0},
+    {1.0 / 5, 0, 0, 0, 0, 0, 0},
+    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0, 0},
+    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0, 0},
+    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0, 0},
+    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0, 0},
+    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0}};
+__constant__ double c_dp_err[7] = {35.0 / 384 - 5179.0 / 57600,
+                                   0.0,
+                                   500.0 / 1113 - 7571.0 / 16695,
+                                   125.0 / 192 - 393.0 / 640,
+                                   -2187.0 / 6784 + 92097.0 / 339200,
+                                   11.0 / 84 - 187.0 / 2100,
+                                   -1.0 / 40};
+
+// ---------------------------------------------------------------------------
+// per-simulation control block (device memory)
+// ---------------------------------------------------------------------------
+struct SimCtl {
+  double t, h, hs, t_next, t_out0, dt_out, t1, tol;
+  double tau, err;
+  int64_t iout, n_out;
+  int64_t n_accept, n_reject, n_rhs, n_attempt, attempt_cap;
+  int mode;      // 0 = fixed number of steps, 1 = integrate to t1, 2 = relax
+  int accepted;  // last attempt accepted: begin/commit must adopt it
+  int clipped;   // the current attempt ends exactly on t_next
+  int status;
+  int done;
+  int pad;
+};
+
+enum { MODE_STEPS = 0, MODE_RUN = 1, MODE_RELAX = 2 };
+
+struct StageArgs {
+  int64_t n;
+  int B;
+  // geometry / material
+  const int32_t *nbr;
+  const float *wex, *kan, *axis, *Ms;
+  const double *wvol;
+  bool exch;
+  // per-simulation equation parameters
+  const float *g1, *g2, *Ha;
+  // state
+  float *y, *ys0, *ys1, *Hd, *xs;
+  float *k[7];
+  int64_t Q;
+  int TC;
+  // control
+  SimCtl *ctl;
+  int *active;
+  int *n_active;
+  double *red;     // [B][nblk][5]
+  int *red_count;  // [B]
+  double *mavg;    // [n_out][B][3]
+  double rtol, atol, hmax, fixed_h;
+};
+
+constexpr int kStageThreads = 256;
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Effective field of tile i (Eq. 5/17): H_d (from the demag product) + exchange
+// (finite volumes, Eq. 12; absent neighbour = Neumann, Eq. 3) + uniaxial
+// anisotropy (Eq. 16) + applied field (Eq. 7).
+__device__ __forceinline__ void effective_field(const StageArgs &A, const float *yin, const float *Hd, int64_t i,
+                                                int b, const float mi[3], float H[3]) {
+  const float *hd = Hd + (size_t)b * 3 * A.n + 3 * i;
+  const float *ha = A.Ha + 3 * b;
+  H[0] = hd[0] + ha[0];
+  H[1] = hd[1] + ha[1];
+  H[2] = hd[2] + ha[2];
+  if (A.exch) {
+    const float *yb = yin + (size_t)b * 3 * A.n;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      const int32_t p = A.nbr[6 * i + f];
+      if (p >= 0) {
+        const float w = A.wex[6 * i + f];
+        H[0] += w * (yb[3 * p] - mi[0]);
+        H[1] += w * (yb[3 * p + 1] - mi[1]);
+        H[2] += w * (yb[3 * p + 2] - mi[2]);
+      }
+    }
+  }
+  const float ka = A.kan[i];
+  if (ka != 0.0f) {
+    const float *e = A.axis + 3 * i;
+    const float me = mi[0] * e[0] + mi[1] * e[1] + mi[2] * e[2];
+    H[0] += ka * me * e[0];
+    H[1] += ka * me * e[1];
+    H[2] += ka * me * e[2];
+  }
+}
+
+// Eq. 1 with prefactors g1 (precession) and g2 (damping):
+// dm/dt = -g1 m x H - g2 m x (m x H); returns |m x H|.
+__device__ __forceinline__ float llg(float g1, float g2, const float m[3], const float H[3], float k[3]) {
+  float a[3], c[3];
+  cross3(m, H, a);
+  cross3(m, a, c);
+  k[0] = -g1 * a[0] - g2 * c[0];
+  k[1] = -g1 * a[1] - g2 * c[1];
+  k[2] = -g1 * a[2] - g2 * c[2];
+  return sqrtf(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+}
+
+__device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn, int64_t i, int b,
+                                                  const float v[3]) {
+  float *d = ysn + (size_t)b * 3 * A.n + 3 * i;
+  d[0] = v[0];
+  d[1] = v[1];
+  d[2] = v[2];
+  const float ms = A.Ms[i];
+  const int64_t q = i / A.TC, t = i - q * A.TC;
+  float *x = A.xs + ((size_t)(b * A.Q + q) * 3) * A.TC + t;
+  x[0] = ms * v[0];
+  x[A.TC] = ms * v[1];
+  x[2 * A.TC] = ms * v[2];
+}
+
+// Block-reduce NV doubles (sum for all but index `max_idx`, which is a max)
+// and return them in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_reduce(double v[NV], int max_idx) {
+  __shared__ double sh[kStageThreads / 32][NV];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) v[q] = (q == max_idx) ? mtd::warp_max(v[q]) : mtd::warp_sum(v[q]);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[w][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NV; ++q) {
+      double acc = sh[0][q];
+      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) acc = (q == max_idx) ? fmax(acc, sh[ww][q]) : acc + sh[ww][q];
+      v[q] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// Deterministic per-simulation reduction across blocks: every block writes
+// its 5 values, the last block to arrive sums them in block order.  Returns
+// true in thread 0 of the last block (with tot filled).
+__device__ bool reduce_across_blocks(const StageArgs &A, int b, double v[5], double tot[5]) {
+  const int nblk = gridDim.x;
+  __shared__ int s_last;
+  block_reduce<5>(v, 1);
+  if (threadIdx.x == 0) {
+    double *dst = A.red + ((size_t)b * nblk + blockIdx.x) * 5;
+    for (int q = 0; q < 5; ++q) dst[q] = v[q];
+    __threadfence();
+    const int old = atomicAdd(&A.red_count[b], 1);
+    s_last = (old == nblk - 1);
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
+    const double *src = A.red + ((size_t)b * nblk + blk) * 5;
+    acc[0] += __ldcg(&src[0]);
+    acc[1] = fmax(acc[1], __ldcg(&src[1]));
+    acc[2] += __ldcg(&src[2]);
+    acc[3] += __ldcg(&src[3]);
+    acc[4] += __ldcg(&src[4]);
+  }
+  block_reduce<5>(acc, 1);
+  if (threadIdx.x == 0) {
+    A.red_count[b] = 0;
+    for (int q = 0; q < 5; ++q) tot[q] = acc[q];
+  }
+  return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ void finish_sim(const StageArgs &A, int b, SimCtl &c, int status) {
+  c.done = 1;
+  c.status = status;
+  A.active[b] = 0;
+  atomicSub(A.n_active, 1);
+}
+
+// Step size for the next attempt: the proposal h capped by hmax, shortened to
+// land on the next output (or end) time.
+__device__ __forceinline__ void plan_attempt(const StageArgs &A, SimCtl &c) {
+  double hs = c.h;
+  if (A.fixed_h <= 0.0 && A.hmax > 0.0 && hs > A.hmax) hs = A.hmax;
+  c.clipped = 0;
+  if (c.t + hs >= c.t_next) {
+    hs = c.t_next - c.t;
+    c.clipped = 1;
+  }
+  c.hs = hs;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__global__ void k_begin(StageArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= A.n) return;
+  const SimCtl &c = A.ctl[b];
+  const size_t o = (size_t)b * 3 * A.n + 3 * i;
+  float m[3], k1[3];
+  if (c.accepted) {
+    const float *yn = A.ys1 + o;  // 5th-order solution of the previous attempt
+    const float inv = rsqrtf(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+    m[0] = yn[0] * inv;
+    m[1] = yn[1] * inv;
+    m[2] = yn[2] * inv;
+    const float *k7 = A.k[6] + o;
+    k1[0] = k7[0];
+    k1[1] = k7[1];
+    k1[2] = k7[2];
+    A.y[o] = m[0];
+    A.y[o + 1] = m[1];
+    A.y[o + 2] = m[2];
+    A.k[0][o] = k1[0];
+    A.k[0][o + 1] = k1[1];
+    A.k[0][o + 2] = k1[2];
+  } else {
+    m[0] = A.y[o];
+    m[1] = A.y[o + 1];
+    m[2] = A.y[o + 2];
+    k1[0] = A.k[0][o];
+    k1[1] = A.k[0][o + 1];
+    k1[2] = A.k[0][o + 2];
+  }
+  if (!A.active[b]) return;
+  const float h = (float)(c.hs * c_dp_a[1][0]);
+  const float v[3] = {m[0] + h * k1[0], m[1] + h * k1[1], m[2] + h * k1[2]};
+  write_stage_input(A, A.ys0, i, b, v);
+}
+
+// commit only (after the last replay)
+__global__ void k_commit(StageArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= A.n || !A.ctl[b].accepted) return;
+  const size_t o = (size_t)b * 3 * A.n + 3 * i;
+  const float *yn = A.ys1 + o;
+  const float inv = rsqrtf(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+  A.y[o] = yn[0] * inv;
+  A.y[o + 1] = yn[1] * inv;
+  A.y[o + 2] = yn[2] * inv;
+  A.k[0][o] = A.k[6][o];
+  A.k[0][o + 1] = A.k[6][o + 1];
+  A.k[0][o + 2] = A.k[6][o + 2];
+}
+
+// Stage S (1..7).  S == 1 evaluates k1 at the state (start of a run);
+// S in 2..6 also forms the input of stage S+1; S == 7 closes the attempt.
+template <int S>
+__global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (!A.active[b]) return;  // uniform per block
+  const bool live = i < A.n;
+  const float *yin = (S == 1) ? A.y : ((S & 1) ? A.ys1 : A.ys0);
+  const size_t o = (size_t)b * 3 * A.n + 3 * i;
+  float tau_i = 0.0f;
+  float mi[3] = {0, 0, 0}, kk[3] = {0, 0, 0};
+  if (live) {
+    mi[0] = yin[o];
+    mi[1] = yin[o + 1];
+    mi[2] = yin[o + 2];
+    float H[3];
+    effective_field(A, yin, A.Hd, i, b, mi, H);
+    tau_i = llg(A.g1[b], A.g2[b], mi, H, kk) / A.Ms[i];
+    float *ko = A.k[S - 1] + o;
+    ko[0] = kk[0];
+    ko[1] = kk[1];
+    ko[2] = kk[2];
+  }
+  if constexpr (S >= 2 && S <= 6) {
+    if (live) {
+      const double hs = A.ctl[b].hs;
+      float acc[3] = {0, 0, 0};
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const float a = (float)(hs * c_dp_a[S][j]);
+        if (a != 0.0f) {
+          const float *kj = (j == S - 1) ? kk : A.k[j] + o;
+          acc[0] += a * kj[0];
+          acc[1] += a * kj[1];
+          acc[2] += a * kj[2];
+        }
+      }
+      const float *y0 = A.y + o;
+      const float v[3] = {y0[0] + acc[0], y0[1] + acc[1], y0[2] + acc[2]};
+      write_stage_input(A, (S + 1) & 1 ? A.ys1 : A.ys0, i, b, v);
+    }
+    return;
+  }
+  if constexpr (S == 1) {
+    double v[5] = {0.0, (double)tau_i, 0.0, 0.0, 0.0};
+    double tot[5];
+    if (reduce_across_blocks(A, b, v, tot)) {
+      SimCtl c = A.ctl[b];
+      c.tau = tot[1];
+      c.n_rhs += 1;
+      if (!isfinite(c.tau)) finish_sim(A, b, c, MT_ENONFINITE);
+      else if (c.mode == MODE_RELAX && c.tau < c.tol) finish_sim(A, b, c, MT_OK);
+      A.ctl[b] = c;
+    }
+    return;
+  }
+  if constexpr (S == 7) {
+    double v[5] = {0.0, (double)tau_i, 0.0, 0.0, 0.0};
+    if (live) {
+      const double hs = A.ctl[b].hs;
+      const float *y0 = A.y + o;
+      double e2 = 0.0;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        double e = 0.0;
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+          if (c_dp_err[j] != 0.0) e += c_dp_err[j] * (double)((j == 6) ? kk[c] : A.k[j][o + c]);
+        e *= hs;
+        const double sc = A.atol + A.rtol * fmax(fabs((double)y0[c]), fabs((double)mi[c]));
+        e2 += (e / sc) * (e / sc);
+      }
+      v[0] = e2;
+      const double nrm = sqrt((double)mi[0] * mi[0] + (double)mi[1] * mi[1] + (double)mi[2] * mi[2]);
+      const double w = A.wvol[i] / nrm;
+      v[2] = w * mi[0];
+      v[3] = w * mi[1];
+      v[4] = w * mi[2];
+    }
+    double tot[5];
+    if (reduce_across_blocks(A, b, v, tot)) {
+      SimCtl c = A.ctl[b];
+      const bool fixed = A.fixed_h > 0.0;
+      const double err = sqrt(tot[0] / (3.0 * (double)A.n));
+      const double tau = tot[1];
+      c.err = err;
+      c.n_attempt += 1;
+      c.n_rhs += 6;
+      const bool finite = isfinite(err) && isfinite(tot[2]) && isfinite(tot[3]) && isfinite(tot[4]);
+      const bool accept = finite && (fixed || err <= 1.0);
+      if (!finite) {
+        c.accepted = 0;
+        finish_sim(A, b, c, MT_ENONFINITE);
+        A.ctl[b] = c;
+        return;
+      }
+      if (accept) {
+        c.n_accept += 1;
+        c.t = c.clipped ? c.t_next : c.t + c.hs;
+        c.tau = tau;
+        if (c.mode == MODE_RUN && c.clipped) {
+          double *mo = A.mavg + ((size_t)c.iout * A.B + b) * 3;
+          mo[0] = tot[2];
+          mo[1] = tot[3];
+          mo[2] = tot[4];
+          c.iout += 1;
+          if (c.iout >= c.n_out) {
+            finish_sim(A, b, c, MT_OK);
+          } else {
+            c.t_next = (c.iout + 1 == c.n_out) ? c.t1 : c.t_out0 + (double)(c.iout + 1) * c.dt_out;
+          }
+        } else if (c.mode == MODE_RELAX) {
+          if (tau < c.tol) finish_sim(A, b, c, MT_OK);
+          else if (c.clipped) finish_sim(A, b, c, MT_ENOCONV);
+        }
+      } else {
+        c.n_reject += 1;
+      }
+      c.accepted = accept ? 1 : 0;
+      if (fixed) {
+        c.h = A.fixed_h;
+      } else {
+        double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
+        fac = fmin(5.0, fmax(0.2, fac));
+        c.h = c.hs * fac;
+        if (A.hmax > 0.0 && c.h > A.hmax) c.h = A.hmax;
+      }
+      if (!c.done && c.mode != MODE_STEPS && c.n_attempt >= c.attempt_cap) finish_sim(A, b, c, MT_ENOCONV);
+      plan_attempt(A, c);
+      A.ctl[b] = c;
+    }
+  }
+}
+
+// standalone right-hand side: dmdt and per-simulation max torque
+__global__ void k_rhs_plain(int64_t n, const int32_t *nbr, const float *wex, const float *kan, const float *axis,
+                            const float *Ms, bool exch, const float *m, const float *Hd, const float *g1,
+                            const float *g2, const float *Ha, float *dmdt, float *tau) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= n) return;
+  StageArgs A{};
+  A.n = n;
+  A.nbr = nbr;
+  A.wex = wex;
+  A.kan = kan;
+  A.axis = axis;
+  A.exch = exch;
+  A.Ha = Ha;
+  const size_t o = (size_t)b * 3 * n + 3 * i;
+  const float mi[3] = {m[o], m[o + 1], m[o + 2]};
+  float H[3], k[3];
+  effective_field(A, m, Hd, i, b, mi, H);
+  const float t = llg(g1[b], g2[b], mi, H, k) / Ms[i];
+  dmdt[o] = k[0];
+  dmdt[o + 1] = k[1];
+  dmdt[o + 2] = k[2];
+  if (tau) atomicMax(reinterpret_cast<int *>(tau + b), __float_as_int(t));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace mt {
+
+void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B, const float *g1,
+                      const float *g2, const float *Ha, float *dmdt, float *tau, cudaStream_t s) {
+  const mt_tiles *t = T->tiles;
+  dim3 grid((unsigned)((T->n + 255) / 256), (unsigned)B);
+  k_rhs_plain<<<grid, 256, 0, s>>>(T->n, t->d_nbr, t->d_wex, t->d_kan, t->d_axis, t->d_Ms, t->has_exchange, m, Hd,
+                                   g1, g2, Ha, dmdt, tau);
+}
+
+void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::vector<float> &g2,
+                    std::vector<float> &ha) {
+  g1.resize(B);
+  g2.resize(B);
+  ha.resize(3 * B);
+  for (int b = 0; b < B; ++b) {
+    const double a = p->alpha[b];
+    double G1, G2;
+    if (p->form == MT_FORM_GILBERT) {
+      G1 = p->gamma / (1.0 + a * a);
+      G2 = G1 * a;
+    } else {
+      G1 = p->gamma;
+      G2 = a;
+    }
+    if (!p->precess) G1 = 0.0;
+    g1[b] = (float)G1;
+    g2[b] = (float)G2;
+    for (int c = 0; c < 3; ++c) ha[3 * b + c] = (float)p->Ha[3 * b + c];
+  }
+}
+
+}  // namespace mt
+
+struct mt_integrator {
+  mt_tensor *T = nullptr;
+  int B = 0;
+  cudaStream_t stream = nullptr;       // private non-blocking stream: capture and replay
+  cudaStream_t user_stream = nullptr;  // the caller's stream, ordered against `stream` by events
+  cudaEvent_t order_ev = nullptr;
+  mt_ode_opts o{};
+  int form = 0, precess = 1;
+  double gamma = 0;
+  // device state
+  float *y = nullptr, *ys0 = nullptr, *ys1 = nullptr, *Hd = nullptr, *xs = nullptr;
+  float *k[7] = {};
+  float *g1 = nullptr, *g2 = nullptr, *Ha = nullptr;
+  float *part = nullptr;
+  int *count = nullptr;
+  SimCtl *ctl = nullptr;
+  int *active = nullptr;
+  int *n_active = nullptr;
+  double *red = nullptr;
+  int *red_count = nullptr;
+  double *mavg = nullptr;
+  int64_t mavg_cap = 0;
+  int *h_poll = nullptr;  // pinned, 2 slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec = nullptr;
+  int nblk = 0;
+  bool need_init = true;
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+StageArgs stage_args(mt_integrator *I) {
+  const mt_tensor *T = I->T;
+  const mt_tiles *t = T->tiles;
+  StageArgs A{};
+  A.n = T->n;
+  A.B = I->B;
+  A.nbr = t->d_nbr;
+  A.wex = t->d_wex;
+  A.kan = t->d_kan;
+  A.axis = t->d_axis;
+  A.Ms = t->d_Ms;
+  A.wvol = t->d_wvol;
+  A.exch = t->has_exchange;
+  A.g1 = I->g1;
+  A.g2 = I->g2;
+  A.Ha = I->Ha;
+  A.y = I->y;
+  A.ys0 = I->ys0;
+  A.ys1 = I->ys1;
+  A.Hd = I->Hd;
+  A.xs = I->xs;
+  for (int s = 0; s < 7; ++s) A.k[s] = I->k[s];
+  A.Q = T->L.Q;
+  A.TC = T->L.TC;
+  A.ctl = I->ctl;
+  A.active = I->active;
+  A.n_active = I->n_active;
+  A.red = I->red;
+  A.red_count = I->red_count;
+  A.mavg = I->mavg;
+  A.rtol = I->o.rtol;
+  A.atol = I->o.atol;
+  A.hmax = I->o.hmax;
+  A.fixed_h = I->o.fixed_h;
+  return A;
+}
+
+template <int S>
+void launch_stage(mt_integrator *I, const StageArgs &A) {
+  dim3 grid((unsigned)I->nblk, (unsigned)I->B);
+  k_stage<S><<<grid, kStageThreads, 0, I->stream>>>(A);
+}
+
+// demag product of the stage input `m` into I->Hd (xs already formed)
+void demag(mt_integrator *I, const float *m) {
+  mt::launch_matvec(I->T, I->xs, I->B, I->Hd, I->part, I->count, I->active, I->T->tiles->ctx->d_status,
+                    I->stream);
+  mt::launch_near(I->T, m, I->B, I->Hd, I->active, I->stream);
+}
+
+void enqueue_attempt(mt_integrator *I) {
+  StageArgs A = stage_args(I);
+  dim3 grid((unsigned)I->nblk, (unsigned)I->B);
+  k_begin<<<grid, kStageThreads, 0, I->stream>>>(A);
+  demag(I, I->ys0);
+  launch_stage<2>(I, A);
+  demag(I, I->ys1);
+  launch_stage<3>(I, A);
+  demag(I, I->ys0);
+  launch_stage<4>(I, A);
+  demag(I, I->ys1);
+  launch_stage<5>(I, A);
+  demag(I, I->ys0);
+  launch_stage<6>(I, A);
+  demag(I, I->ys1);
+  launch_stage<7>(I, A);
+}
+
+mt_status enqueue_init(mt_integrator *I) {
+  StageArgs A = stage_args(I);
+  mt::launch_prep_xs(I->T, I->y, I->B, I->xs, I->stream);
+  demag(I, I->y);
+  launch_stage<1>(I, A);
+  MT_CUDA(cudaGetLastError());
+  I->need_init = false;
+  return MT_OK;
+}
+
+mt_status enqueue_commit(mt_integrator *I) {
+  StageArgs A = stage_args(I);
+  dim3 grid((unsigned)I->nblk, (unsigned)I->B);
+  k_commit<<<grid, kStageThreads, 0, I->stream>>>(A);
+  MT_CUDA(cudaGetLastError());
+  return MT_OK;
+}
+
+template <typename P>
+mt_status dalloc(mt_integrator *I, P **p, size_t bytes) {
+  MT_CUDA(cudaMalloc((void **)p, bytes));
+  MT_CUDA(cudaMemsetAsync(*p, 0, bytes, I->stream));
+  I->allocs.push_back((void *)*p);
+  return MT_OK;
+}
+
+mt_status read_ctl(mt_integrator *I, std::vector<SimCtl> &c) {
+  c.resize(I->B);
+  MT_CUDA(cudaMemcpyAsync(c.data(), I->ctl, sizeof(SimCtl) * I->B, cudaMemcpyDeviceToHost, I->stream));
+  MT_CUDA(cudaStreamSynchronize(I->stream));
+  return MT_OK;
+}
+
+mt_status write_ctl(mt_integrator *I, const std::vector<SimCtl> &c) {
+  std::vector<int> act(I->B);
+  int na = 0;
+  for (int b = 0; b < I->B; ++b) {
+    act[b] = c[b].done ? 0 : 1;
+    na += act[b];
+  }
+  MT_CUDA(cudaMemcpyAsync(I->ctl, c.data(), sizeof(SimCtl) * I->B, cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->active, act.data(), sizeof(int) * I->B, cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->n_active, &na, sizeof(int), cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaStreamSynchronize(I->stream));  // host vectors go out of scope
+  return MT_OK;
+}
+
+void fill_stats(const std::vector<SimCtl> &c, mt_stats *st, int B) {
+  if (!st) return;
+  for (int b = 0; b < B; ++b) {
+    st[b].n_accept = c[b].n_accept;
+    st[b].n_reject = c[b].n_reject;
+    st[b].n_rhs = c[b].n_rhs;
+    st[b].t = c[b].t;
+    st[b].h = c[b].h;
+    st[b].tau = c[b].tau;
+    st[b].status = c[b].status;
+    st[b].pad = 0;
+  }
+}
+
+void plan_host(const mt_integrator *I, SimCtl &c) {
+  double hs = c.h;
+  if (I->o.fixed_h <= 0.0 && I->o.hmax > 0.0 && hs > I->o.hmax) hs = I->o.hmax;
+  c.clipped = 0;
+  if (c.t + hs >= c.t_next) {
+    hs = c.t_next - c.t;
+    c.clipped = 1;
+  }
+  c.hs = hs;
+}
+
+// Replay the step graph until every simulation is finished (or a cap).
+mt_status replay_until_done(mt_integrator *I, int64_t max_launches) {
+  int64_t launched = 0;
+  int chunk = 2;
+  int slot = 0;
+  bool pending[2] = {false, false};
+  for (;;) {
+    const int64_t todo = std::min<int64_t>(chunk, max_launches - launched);
+    for (int64_t q = 0; q < todo; ++q) MT_CUDA(cudaGraphLaunch(I->exec, I->stream));
+    launched += todo;
+    MT_CUDA(cudaMemcpyAsync(&I->h_poll[slot], I->n_active, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
+    MT_CUDA(cudaEventRecord(I->ev[slot], I->stream));
+    pending[slot] = true;
+    const int prev = slot ^ 1;
+    if (pending[prev]) {
+      MT_CUDA(cudaEventSynchronize(I->ev[prev]));
+      pending[prev] = false;
+      if (I->h_poll[prev] == 0) break;
+    }
+    if (launched >= max_launches) {
+      MT_CUDA(cudaEventSynchronize(I->ev[slot]));
+      break;
+    }
+    slot = prev;
+    if (chunk < 64) chunk *= 2;
+  }
+  MT_CUDA(cudaStreamSynchronize(I->stream));
+  return MT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, int B, void *stream,
+                               mt_integrator **out) {
+  MT_CHECK(T && p && o && out, MT_EINVAL, "mt_integrator_create: NULL argument");
+  MT_CHECK(B >= 1 && B <= 4096, MT_EINVAL, "mt_integrator_create: B must be in [1, 4096]");
+  MT_CHECK(T->prec != MT_F64, MT_EINVAL, "mt_integrator_create: the FP64 tensor serves field checks only");
+  MT_CHECK(p->alpha && p->Ha, MT_EINVAL, "mt_integrator_create: alpha/Ha arrays required");
+  MT_CHECK(o->fixed_h > 0.0 || (o->rtol > 0.0 && o->atol > 0.0 && o->h0 > 0.0), MT_EINVAL,
+           "mt_integrator_create: rtol, atol and h0 must be positive");
+  MT_CHECK(o->max_steps > 0, MT_EINVAL, "mt_integrator_create: max_steps must be positive");
+  for (int b = 0; b < B; ++b)
+    MT_CHECK(std::isfinite(p->alpha[b]) && std::isfinite(p->Ha[3 * b]) && std::isfinite(p->Ha[3 * b + 1]) &&
+                 std::isfinite(p->Ha[3 * b + 2]),
+             MT_EINVAL, "mt_integrator_create: non-finite parameter");
+  MT_CUDA(cudaSetDevice(T->tiles->ctx->device));
+  mt_integrator *I = new mt_integrator();
+  I->T = T;
+  I->B = B;
+  I->user_stream = (cudaStream_t)stream;
+  if (cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->order_ev, cudaEventDisableTiming) != cudaSuccess) {
+    mt_integrator_destroy(I);
+    mt::set_error("mt_integrator_create: stream/event creation failed");
+    return MT_ECUDA;
+  }
+  I->o = *o;
+  I->form = p->form;
+  I->precess = p->precess;
+  I->gamma = p->gamma;
+  const int64_t n = T->n;
+  const size_t vec = sizeof(float) * 3 * n * B;
+  I->nblk = (int)((n + kStageThreads - 1) / kStageThreads);
+  mt_status st = MT_OK;
+#define MT_TRY(x)              \
+  do {                         \
+    if ((st = (x)) != MT_OK) { \
+      mt_integrator_destroy(I); \
+      return st;               \
+    }                          \
+  } while (0)
+  MT_TRY(dalloc(I, &I->y, vec));
+  MT_TRY(dalloc(I, &I->ys0, vec));
+  MT_TRY(dalloc(I, &I->ys1, vec));
+  MT_TRY(dalloc(I, &I->Hd, vec));
+  for (int s = 0; s < 7; ++s) MT_TRY(dalloc(I, &I->k[s], vec));
+  MT_TRY(dalloc(I, &I->xs, sizeof(float) * mt::xs_floats(T) * B));
+  MT_TRY(dalloc(I, &I->g1, sizeof(float) * B));
+  MT_TRY(dalloc(I, &I->g2, sizeof(float) * B));
+  MT_TRY(dalloc(I, &I->Ha, sizeof(float) * 3 * B));
+  MT_TRY(dalloc(I, &I->part, mt::matvec_part_bytes(T)));
+  MT_TRY(dalloc(I, &I->count, mt::matvec_count_bytes(T, B)));
+  MT_TRY(dalloc(I, &I->ctl, sizeof(SimCtl) * B));
+  MT_TRY(dalloc(I, &I->active, sizeof(int) * B));
+  MT_TRY(dalloc(I, &I->n_active, sizeof(int)));
+  MT_TRY(dalloc(I, &I->red, sizeof(double) * 5 * I->nblk * B));
+  MT_TRY(dalloc(I, &I->red_count, sizeof(int) * B));
+  I->mavg_cap = 1;
+  MT_TRY(dalloc(I, &I->mavg, sizeof(double) * 3 * B));
+  if (cudaMallocHost(&I->h_poll, 2 * sizeof(int)) != cudaSuccess) {
+    mt_integrator_destroy(I);
+    mt::set_error("mt_integrator_create: pinned allocation failed");
+    return MT_ENOMEM;
+  }
+  if (cudaEventCreateWithFlags(&I->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&I->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    mt_integrator_destroy(I);
+    mt::set_error("mt_integrator_create: event creation failed");
+    return MT_ECUDA;
+  }
+  MT_TRY(mt_integrator_set_params(I, p));
+  // capture one attempt
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue_attempt(I);
+    e = cudaStreamEndCapture(I->stream, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&I->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    mt_integrator_destroy(I);
+    return mt::cuda_fail(e, "graph capture", __FILE__, __LINE__);
+  }
+#undef MT_TRY
+  *out = I;
+  return MT_OK;
+}
+
+void mt_integrator_destroy(mt_integrator *I) {
+  if (!I) return;
+  if (I->stream) cudaStreamSynchronize(I->stream);
+  if (I->exec) cudaGraphExecDestroy(I->exec);
+  for (void *p : I->allocs) cudaFree(p);
+  if (I->h_poll) cudaFreeHost(I->h_poll);
+  for (auto &e : I->ev)
+    if (e) cudaEventDestroy(e);
+  if (I->order_ev) cudaEventDestroy(I->order_ev);
+  if (I->stream) cudaStreamDestroy(I->stream);
+  delete I;
+}
+
+mt_status mt_integrator_set_params(mt_integrator *I, const mt_llg_params *p) {
+  MT_CHECK(I && p && p->alpha && p->Ha, MT_EINVAL, "mt_integrator_set_params: NULL argument");
+  std::vector<float> g1, g2, ha;
+  mt::llg_prefactors(p, I->B, g1, g2, ha);
+  MT_CUDA(cudaMemcpyAsync(I->g1, g1.data(), sizeof(float) * I->B, cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->g2, g2.data(), sizeof(float) * I->B, cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->Ha, ha.data(), sizeof(float) * 3 * I->B, cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaStreamSynchronize(I->stream));
+  I->need_init = true;
+  return MT_OK;
+}
+
+mt_status mt_integrator_set_state(mt_integrator *I, const float *m, int m_is_host, double t0) {
+  MT_CHECK(I && m, MT_EINVAL, "mt_integrator_set_state: NULL argument");
+  const size_t bytes = sizeof(float) * 3 * I->T->n * I->B;
+  if (!m_is_host) {  // the caller's stream may still be writing m
+    MT_CUDA(cudaEventRecord(I->order_ev, I->user_stream));
+    MT_CUDA(cudaStreamWaitEvent(I->stream, I->order_ev, 0));
+  }
+  MT_CUDA(cudaMemcpyAsync(I->y, m, bytes, m_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                          I->stream));
+  std::vector<SimCtl> c(I->B);
+  for (auto &x : c) {
+    std::memset(&x, 0, sizeof(SimCtl));
+    x.t = t0;
+    x.h = I->o.fixed_h > 0 ? I->o.fixed_h : I->o.h0;
+    x.t_next = 1e300;
+    x.mode = MODE_STEPS;
+    x.status = MT_OK;
+    x.attempt_cap = INT64_MAX;
+  }
+  for (auto &x : c) plan_host(I, x);
+  // write_ctl synchronises, which also orders the state copy
+  mt_status st = write_ctl(I, c);
+  if (st != MT_OK) return st;
+  I->need_init = true;
+  return MT_OK;
+}
+
+mt_status mt_integrator_get_state(mt_integrator *I, float *m, int m_is_host) {
+  MT_CHECK(I && m, MT_EINVAL, "mt_integrator_get_state: NULL argument");
+  const size_t bytes = sizeof(float) * 3 * I->T->n * I->B;
+  MT_CUDA(cudaMemcpyAsync(m, I->y, bytes, m_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          I->stream));
+  if (m_is_host) {
+    MT_CUDA(cudaStreamSynchronize(I->stream));
+  } else {  // later work on the caller's stream sees the copy
+    MT_CUDA(cudaEventRecord(I->order_ev, I->stream));
+    MT_CUDA(cudaStreamWaitEvent(I->user_stream, I->order_ev, 0));
+  }
+  return MT_OK;
+}
+
+void *mt_integrator_stream(mt_integrator *I) { return I ? (void *)I->stream : nullptr; }
+
+mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps) {
+  MT_CHECK(I && nsteps >= 0, MT_EINVAL, "mt_integrator_step: bad argument");
+  if (I->need_init) {
+    // fixed number of attempts: no time target, every simulation active
+    std::vector<SimCtl> c;
+    mt_status st = read_ctl(I, c);
+    if (st != MT_OK) return st;
+    for (auto &x : c) {
+      x.mode = MODE_STEPS;
+      x.t_next = 1e300;
+      x.done = 0;
+      x.status = MT_OK;
+      plan_host(I, x);
+    }
+    if ((st = write_ctl(I, c)) != MT_OK) return st;
+    if ((st = enqueue_init(I)) != MT_OK) return st;
+  }
+  for (int64_t q = 0; q < nsteps; ++q) MT_CUDA(cudaGraphLaunch(I->exec, I->stream));
+  return enqueue_commit(I);
+}
+
+static mt_status run_common(mt_integrator *I, int mode, double t1, int64_t n_out, double tol, double *mavg,
+                            mt_stats *stats) {
+  std::vector<SimCtl> c;
+  mt_status st = read_ctl(I, c);
+  if (st != MT_OK) return st;
+  if (mode == MODE_RUN && n_out > I->mavg_cap) {
+    cudaFree(I->mavg);
+    I->allocs.erase(std::remove(I->allocs.begin(), I->allocs.end(), (void *)I->mavg), I->allocs.end());
+    I->mavg = nullptr;
+    if ((st = dalloc(I, &I->mavg, sizeof(double) * 3 * I->B * n_out)) != MT_OK) return st;
+    I->mavg_cap = n_out;
+    // the graph bakes the output pointer in: recapture
+    cudaGraphExecDestroy(I->exec);
+    I->exec = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      enqueue_attempt(I);
+      e = cudaStreamEndCapture(I->stream, &g);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&I->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return mt::cuda_fail(e, "graph capture", __FILE__, __LINE__);
+  }
+  for (auto &x : c) {
+    x.mode = mode;
+    x.done = 0;
+    x.status = MT_OK;
+    x.accepted = 0;
+    x.attempt_cap = x.n_attempt + I->o.max_steps;
+    if (mode == MODE_RUN) {
+      x.n_out = n_out;
+      x.iout = 0;
+      x.t1 = t1;
+      x.t_out0 = x.t;
+      x.dt_out = (t1 - x.t) / (double)n_out;
+      x.t_next = (n_out == 1) ? t1 : x.t + x.dt_out;
+    } else {
+      x.tol = tol;
+      x.t1 = x.t + t1;
+      x.t_next = x.t1;
+    }
+    plan_host(I, x);
+  }
+  if ((st = write_ctl(I, c)) != MT_OK) return st;
+  if ((st = enqueue_init(I)) != MT_OK) return st;
+  if ((st = replay_until_done(I, I->o.max_steps + 2)) != MT_OK) return st;
+  if ((st = enqueue_commit(I)) != MT_OK) return st;
+  if ((st = read_ctl(I, c)) != MT_OK) return st;
+  int dev_status = 0;
+  MT_CUDA(cudaMemcpy(&dev_status, I->T->tiles->ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  MT_CHECK(dev_status == 0, MT_ETIMEOUT, "integrator: a bounded device wait ran out");
+  if (mavg && mode == MODE_RUN) {
+    MT_CUDA(cudaMemcpy(mavg, I->mavg, sizeof(double) * 3 * I->B * n_out, cudaMemcpyDeviceToHost));
+  }
+  fill_stats(c, stats, I->B);
+  for (int b = 0; b < I->B; ++b) {
+    if (!c[b].done) {
+      mt::set_error("integrator: simulation %d not finished", b);
+      return MT_ENOCONV;
+    }
+    if (c[b].status != MT_OK) {
+      mt::set_error("integrator: simulation %d ended with status %d", b, c[b].status);
+      return (mt_status)c[b].status;
+    }
+  }
+  return MT_OK;
+}
+
+mt_status mt_integrator_run(mt_integrator *I, double t1, int64_t n_out, double *mavg, mt_stats *stats) {
+  MT_CHECK(I && n_out >= 1, MT_EINVAL, "mt_integrator_run: bad argument");
+  return run_common(I, MODE_RUN, t1, n_out, 0.0, mavg, stats);
+}
+
+mt_status mt_integrator_relax(mt_integrator *I, double tol, double t_max, mt_stats *stats) {
+  MT_CHECK(I && tol > 0 && t_max > 0, MT_EINVAL, "mt_integrator_relax: bad argument");
+  return run_common(I, MODE_RELAX, t_max, 1, tol, nullptr, stats);
+}
+
+mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats) {
+  MT_CHECK(I && stats, MT_EINVAL, "mt_integrator_stats: NULL argument");
+  std::vector<SimCtl> c;
+  mt_status st = read_ctl(I, c);
+  if (st != MT_OK) return st;
+  fill_stats(c, stats, I->B);
+  return MT_OK;
+}
+
+mt_status mt_integrate(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, float *m, int B, double t0,
+                       double t1, int64_t n_out, double *mavg, mt_stats *stats, void *stream) {
+  mt_integrator *I = nullptr;
+  mt_status st = mt_integrator_create(T, p, o, B, stream, &I);
+  if (st != MT_OK) return st;
+  st = mt_integrator_set_state(I, m, 0, t0);
+  mt_status st2 = (st == MT_OK) ? mt_integrator_run(I, t1, n_out, mavg, stats) : st;
+  if (st == MT_OK) st = mt_integrator_get_state(I, m, 0);
+  if (st == MT_OK) {
+    cudaError_t e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) st = mt::cuda_fail(e, "sync", __FILE__, __LINE__);
+  }
+  mt_integrator_destroy(I);
+  return st2 != MT_OK ? st2 : st;
+}
+
+mt_status mt_relax(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, double tol, double t_max, float *m,
+                   int B, mt_stats *stats, void *stream) {
+  mt_integrator *I = nullptr;
+  mt_status st = mt_integrator_create(T, p, o, B, stream, &I);
+  if (st != MT_OK) return st;
+  st = mt_integrator_set_state(I, m, 0, 0.0);
+  mt_status st2 = (st == MT_OK) ? mt_integrator_relax(I, tol, t_max, stats) : st;
+  if (st == MT_OK) st = mt_integrator_get_state(I, m, 0);
+  if (st == MT_OK) {
+    cudaError_t e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) st = mt::cuda_fail(e, "sync", __FILE__, __LINE__);
+  }
+  mt_integrator_destroy(I);
+  return st2 != MT_OK ? st2 : st;
+}
+
+}  // extern "C"

@@ -1,0 +1,474 @@
+// Streaming demag product H_d = -N (Ms m) (Eq. 9, Eq. 17 of the paper).
+//
+// The product is bound by HBM: every stored tensor value is read once per
+// right-hand side and used for 1.5 multiply-adds on average.  Design:
+//   * one persistent CTA per SM; the (simulation, panel, chunk) units are
+//     split evenly over the CTAs in storage order ("stream-K"), so every CTA
+//     streams one contiguous stretch of the tensor and the load is balanced
+//     to within one chunk whatever n is;
+//   * a producer warp moves each chunk (48 KB, all 6 planes of TR x TC blocks)
+//     and the matching slice of the Ms-scaled magnetisation into a 4-stage
+//     shared-memory ring with bulk TMA copies (cp.async.bulk + mbarrier
+//     transaction counts); the tensor stream is marked evict-first in L2, the
+//     small operand evict-last;
+//   * consumer warps own TR/W rows each; a lane owns VEC adjacent columns and
+//     keeps its operand values in registers while it walks the rows, so each
+//     tensor value is read from shared memory once, as a 16-byte vector;
+//   * a panel split between two CTAs is finished by whichever warp arrives
+//     last (counter per panel and warp): it sums the partial rows in CTA
+//     order, so the result does not depend on timing.
+#include <algorithm>
+#include <cstdio>
+
+#include "mt_internal.cuh"
+
+namespace {
+
+template <int PREC>
+struct MvCfg;
+template <>
+struct MvCfg<MT_F32> {
+  using T = float;
+  using Acc = float;
+  static constexpr int TR = 16, TC = 128, NPLANE = 6, VEC = 4, W = 4, STAGES = 4;
+  static constexpr bool SCALED = false, SPLIT = false;
+};
+template <>
+struct MvCfg<MT_F64> {
+  using T = double;
+  using Acc = double;
+  static constexpr int TR = 16, TC = 64, NPLANE = 6, VEC = 2, W = 4, STAGES = 4;
+  static constexpr bool SCALED = false, SPLIT = false;
+};
+template <>
+struct MvCfg<MT_BF16_SCALED> {
+  using T = __nv_bfloat16;
+  using Acc = float;
+  static constexpr int TR = 16, TC = 256, NPLANE = 6, VEC = 8, W = 4, STAGES = 4;
+  static constexpr bool SCALED = true, SPLIT = false;
+};
+template <>
+struct MvCfg<MT_BF16_SPLIT> {
+  using T = __nv_bfloat16;
+  using Acc = float;
+  static constexpr int TR = 8, TC = 256, NPLANE = 12, VEC = 8, W = 4, STAGES = 4;
+  static constexpr bool SCALED = false, SPLIT = true;
+};
+
+template <int PREC>
+struct MvShape {
+  using C = MvCfg<PREC>;
+  static constexpr int RPW = C::TR / C::W;  // rows per consumer warp
+  static constexpr int DATA_BYTES = C::NPLANE * C::TR * C::TC * (int)sizeof(typename C::T);
+  static constexpr int SCALE_BYTES = C::SCALED ? C::TR * C::TC : 0;
+  static constexpr int XS_BYTES = 3 * C::TC * (int)sizeof(typename C::Acc);
+  static constexpr int STAGE_BYTES = DATA_BYTES + SCALE_BYTES + XS_BYTES;
+  static constexpr int SMEM_BYTES = C::STAGES * STAGE_BYTES + 2 * C::STAGES * 8 + 16;
+  static constexpr int THREADS = (C::W + 1) * 32;
+  static_assert(C::TC == 32 * C::VEC, "a warp covers one chunk row");
+  static_assert(3 * RPW <= 32, "one lane per (row, component) in the flush");
+  static_assert(DATA_BYTES % 16 == 0 && SCALE_BYTES % 16 == 0 && XS_BYTES % 16 == 0, "bulk copy sizes");
+};
+
+// ---- per-precision load of VEC adjacent values of one plane row ----------
+template <int PREC>
+__device__ __forceinline__ void load_vals(const unsigned char *stage, int plane, int row, int lane,
+                                          typename MvCfg<PREC>::Acc v[MvCfg<PREC>::VEC]) {
+  using C = MvCfg<PREC>;
+  if constexpr (PREC == MT_F32) {
+    const float4 a = reinterpret_cast<const float4 *>(stage)[(plane * C::TR + row) * (C::TC / 4) + lane];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else if constexpr (PREC == MT_F64) {
+    const double2 a = reinterpret_cast<const double2 *>(stage)[(plane * C::TR + row) * (C::TC / 2) + lane];
+    v[0] = a.x; v[1] = a.y;
+  } else if constexpr (PREC == MT_BF16_SCALED) {
+    const uint4 a = reinterpret_cast<const uint4 *>(stage)[(plane * C::TR + row) * (C::TC / 8) + lane];
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(h[k]);
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
+    }
+  } else {  // split: hi plane `plane`, lo plane `plane + 6`
+    const uint4 a = reinterpret_cast<const uint4 *>(stage)[(plane * C::TR + row) * (C::TC / 8) + lane];
+    const uint4 b = reinterpret_cast<const uint4 *>(stage)[((plane + 6) * C::TR + row) * (C::TC / 8) + lane];
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&a);
+    const __nv_bfloat162 *l = reinterpret_cast<const __nv_bfloat162 *>(&b);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 fh = __bfloat1622float2(h[k]);
+      const float2 fl = __bfloat1622float2(l[k]);
+      v[2 * k] = fh.x + fl.x;
+      v[2 * k + 1] = fh.y + fl.y;
+    }
+  }
+}
+
+template <int PREC>
+__device__ __forceinline__ void load_xs(const unsigned char *xs, int comp, int lane,
+                                        typename MvCfg<PREC>::Acc v[MvCfg<PREC>::VEC]) {
+  using C = MvCfg<PREC>;
+  if constexpr (PREC == MT_F64) {
+    const double2 a = reinterpret_cast<const double2 *>(xs)[comp * (C::TC / 2) + lane];
+    v[0] = a.x; v[1] = a.y;
+  } else {
+    const float4 *p = reinterpret_cast<const float4 *>(xs) + comp * (C::TC / 4) + lane * (C::VEC / 4);
+#pragma unroll
+    for (int k = 0; k < C::VEC / 4; ++k) {
+      const float4 a = p[k];
+      v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+    }
+  }
+}
+
+struct MvArgs {
+  const void *tensor;
+  const int8_t *scale;
+  const void *xs;
+  void *H;
+  void *part;
+  int *count;
+  const int *active;
+  int *status;
+  int64_t n, P, Q;
+  int B;
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) {
+  using C = MvCfg<PREC>;
+  using S = MvShape<PREC>;
+  using T = typename C::T;
+  using Acc = typename C::Acc;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * S::STAGE_BYTES);
+  uint64_t *empty = full + C::STAGES;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + C::STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x, k = blockIdx.x;
+  const int64_t PQ = A.P * A.Q;
+  const int64_t U = (int64_t)A.B * PQ;
+  const int64_t u0 = mtd::sk_begin(k, U, G), u1 = mtd::sk_begin(k + 1, U, G);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mtd::mbar_init(&full[s], 1);
+      mtd::mbar_init(&empty[s], C::W);
+    }
+    *abort_flag = 0;
+    mtd::fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == C::W) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      const uint64_t pol_stream = mtd::policy_evict_first();
+      const uint64_t pol_keep = mtd::policy_evict_last();
+      const unsigned char *tens = reinterpret_cast<const unsigned char *>(A.tensor);
+      const unsigned char *xs = reinterpret_cast<const unsigned char *>(A.xs);
+      int it = 0;
+      for (int64_t u = u0; u < u1; ++u) {
+        const int64_t gp = u / A.Q, q = u - gp * A.Q;
+        const int64_t b = gp / A.P, p = gp - b * A.P;
+        if (A.active && !A.active[b]) continue;
+        const int s = it % C::STAGES;
+        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+        if (it >= C::STAGES) {
+          if (*abort_flag || !mtd::mbar_wait_bounded(&empty[s], ph ^ 1u, A.status)) {
+            *abort_flag = 1;
+            break;
+          }
+        }
+        unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
+        mtd::mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+        mtd::bulk_g2s(st, tens + (size_t)(p * A.Q + q) * S::DATA_BYTES, S::DATA_BYTES, &full[s], pol_stream);
+        if constexpr (C::SCALED)
+          mtd::bulk_g2s(st + S::DATA_BYTES, A.scale + (size_t)(p * A.Q + q) * S::SCALE_BYTES, S::SCALE_BYTES,
+                        &full[s], pol_stream);
+        mtd::bulk_g2s(st + S::DATA_BYTES + S::SCALE_BYTES, xs + (size_t)(b * A.Q + q) * S::XS_BYTES, S::XS_BYTES,
+                      &full[s], pol_keep);
+        ++it;
+      }
+      // drain: every copy issued must have landed before the CTA may exit
+      for (int s = 0; s < C::STAGES && s < it; ++s) {
+        const int last = it - 1 - ((it - 1 - s) % C::STAGES);  // last issue on stage s
+        mtd::mbar_wait_bounded(&full[s], (uint32_t)(last / C::STAGES) & 1u, A.status);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  Acc acc[S::RPW][3];
+  int64_t gp_cur = -1;
+  const int64_t first_panel = u0 / A.Q;
+  int it = 0;
+  bool aborted = false;
+
+  auto flush = [&](int64_t gp) {
+    // lane sums -> every lane holds the warp totals
+#pragma unroll
+    for (int r = 0; r < S::RPW; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[r][c] = mtd::warp_sum(acc[r][c]);
+    const int64_t b = gp / A.P, p = gp - b * A.P;
+    const int64_t kf = mtd::sk_owner(gp * A.Q, U, G), kl = mtd::sk_owner(gp * A.Q + A.Q - 1, U, G);
+    // this lane's (row, component)
+    const int lr = lane / 3, lc = lane - 3 * (lane / 3);
+    Acc mine = 0;
+#pragma unroll
+    for (int r = 0; r < S::RPW; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (r == lr && c == lc) mine = acc[r][c];
+    const int row_in_panel = warp * S::RPW + lr;
+    const int64_t row = p * C::TR + row_in_panel;
+    Acc *H = reinterpret_cast<Acc *>(A.H) + (size_t)b * 3 * A.n;
+    Acc *part = reinterpret_cast<Acc *>(A.part);
+    const bool writer = lane < 3 * S::RPW;
+    if (kf == kl) {
+      if (writer && row < A.n) H[3 * row + lc] = -mine;
+      return;
+    }
+    const int64_t slot = (gp == first_panel) ? 2 * k : 2 * k + 1;
+    if (writer) part[(slot * C::TR + row_in_panel) * 3 + lc] = mine;
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+      const int old = atomicAdd(&A.count[gp * C::W + warp], 1);
+      last = (old == (int)(kl - kf));
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      if (writer) {
+        Acc tot = 0;
+        for (int64_t kk = kf; kk <= kl; ++kk) {
+          const int64_t fp = mtd::sk_begin(kk, U, G) / A.Q;
+          const int64_t sl = (gp == fp) ? 2 * kk : 2 * kk + 1;
+          tot += __ldcg(&part[(sl * C::TR + row_in_panel) * 3 + lc]);
+        }
+        if (row < A.n) H[3 * row + lc] = -tot;
+      }
+      if (lane == 0) A.count[gp * C::W + warp] = 0;  // ready for the next launch
+    }
+  };
+
+  for (int64_t u = u0; u < u1; ++u) {
+    const int64_t gp = u / A.Q;
+    const int64_t b = gp / A.P;
+    if (A.active && !A.active[b]) continue;
+    if (gp != gp_cur) {
+      if (gp_cur >= 0) flush(gp_cur);
+      gp_cur = gp;
+#pragma unroll
+      for (int r = 0; r < S::RPW; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0;
+    }
+    const int s = it % C::STAGES;
+    const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+    ++it;
+    if (!aborted) {
+      if (*abort_flag || !mtd::mbar_wait_bounded(&full[s], ph, A.status)) {
+        aborted = true;
+        *abort_flag = 1;
+      }
+    }
+    if (!aborted) {
+      const unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
+      Acc X[C::VEC], Y[C::VEC], Z[C::VEC];
+      load_xs<PREC>(st + S::DATA_BYTES + S::SCALE_BYTES, 0, lane, X);
+      load_xs<PREC>(st + S::DATA_BYTES + S::SCALE_BYTES, 1, lane, Y);
+      load_xs<PREC>(st + S::DATA_BYTES + S::SCALE_BYTES, 2, lane, Z);
+#pragma unroll
+      for (int r = 0; r < S::RPW; ++r) {
+        const int row = warp * S::RPW + r;
+        Acc nxx[C::VEC], nxy[C::VEC], nxz[C::VEC], nyy[C::VEC], nyz[C::VEC], nzz[C::VEC];
+        load_vals<PREC>(st, 0, row, lane, nxx);
+        load_vals<PREC>(st, 1, row, lane, nxy);
+        load_vals<PREC>(st, 2, row, lane, nxz);
+        load_vals<PREC>(st, 3, row, lane, nyy);
+        load_vals<PREC>(st, 4, row, lane, nyz);
+        load_vals<PREC>(st, 5, row, lane, nzz);
+        Acc sx = 0, sy = 0, sz = 0;
+        if constexpr (C::SCALED) {
+          // per-block power-of-two scale: value = stored * 2^s
+          const uint2 sc = reinterpret_cast<const uint2 *>(st + S::DATA_BYTES)[row * (C::TC / 8) + lane];
+          const int8_t *e8 = reinterpret_cast<const int8_t *>(&sc);
+#pragma unroll
+          for (int v = 0; v < C::VEC; ++v) {
+            const float f = __int_as_float(((int)e8[v] + 127) << 23);
+            const float xs_ = X[v] * f, ys_ = Y[v] * f, zs_ = Z[v] * f;
+            sx = fmaf(nxx[v], xs_, fmaf(nxy[v], ys_, fmaf(nxz[v], zs_, sx)));
+            sy = fmaf(nxy[v], xs_, fmaf(nyy[v], ys_, fmaf(nyz[v], zs_, sy)));
+            sz = fmaf(nxz[v], xs_, fmaf(nyz[v], ys_, fmaf(nzz[v], zs_, sz)));
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < C::VEC; ++v) {
+            sx = fma(nxx[v], X[v], fma(nxy[v], Y[v], fma(nxz[v], Z[v], sx)));
+            sy = fma(nxy[v], X[v], fma(nyy[v], Y[v], fma(nyz[v], Z[v], sy)));
+            sz = fma(nxz[v], X[v], fma(nyz[v], Y[v], fma(nzz[v], Z[v], sz)));
+          }
+        }
+        acc[r][0] += sx;
+        acc[r][1] += sy;
+        acc[r][2] += sz;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mtd::mbar_arrive(&empty[s]);
+  }
+  if (gp_cur >= 0) flush(gp_cur);
+}
+
+// xs[b][q][c][t] = Ms_j m_j[c] with j = q*TC + t (0 beyond n)
+template <typename In, typename Out>
+__global__ void k_prep_xs(const In *m, const float *Ms, int64_t n, int64_t Q, int TC, int B, Out *xs) {
+  const int64_t tot = (int64_t)B * Q * TC;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / (Q * TC), rem = t - b * Q * TC;
+    const int64_t q = rem / TC, c = rem - q * TC;
+    const int64_t j = q * TC + c;
+    Out x = 0, y = 0, z = 0;
+    if (j < n) {
+      const Out ms = (Out)Ms[j];
+      const In *mj = m + (size_t)b * 3 * n + 3 * j;
+      x = ms * (Out)mj[0];
+      y = ms * (Out)mj[1];
+      z = ms * (Out)mj[2];
+    }
+    Out *dst = xs + ((size_t)(b * Q + q) * 3) * TC + c;
+    dst[0] = x;
+    dst[TC] = y;
+    dst[2 * TC] = z;
+  }
+}
+
+// Near-field blocks in FP64 (BF16 precisions): H_i -= sum_near N_ij Ms_j m_j.
+__global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const double *val,
+                       const float *Ms, const float *m, float *H, const int *active) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (i >= n || (active && !active[b])) return;
+  const float *mb = m + (size_t)b * 3 * n;
+  double hx = 0, hy = 0, hz = 0;
+  for (int32_t a = ptr[i]; a < ptr[i + 1]; ++a) {
+    const int64_t j = col[a];
+    const double ms = Ms[j];
+    const double x = ms * mb[3 * j], y = ms * mb[3 * j + 1], z = ms * mb[3 * j + 2];
+    const double *v = val + 6 * (size_t)a;
+    hx += v[0] * x + v[1] * y + v[2] * z;
+    hy += v[1] * x + v[3] * y + v[4] * z;
+    hz += v[2] * x + v[4] * y + v[5] * z;
+  }
+  float *Hb = H + (size_t)b * 3 * n + 3 * i;
+  Hb[0] = (float)((double)Hb[0] - hx);
+  Hb[1] = (float)((double)Hb[1] - hy);
+  Hb[2] = (float)((double)Hb[2] - hz);
+}
+
+template <int PREC>
+cudaError_t prepare_mv() {
+  return cudaFuncSetAttribute(k_matvec<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, MvShape<PREC>::SMEM_BYTES);
+}
+
+template <int PREC>
+void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, int *count, const int *active,
+               int *status, cudaStream_t s) {
+  using S = MvShape<PREC>;
+  MvArgs A;
+  A.tensor = T->d_data;
+  A.scale = T->d_scale;
+  A.xs = xs;
+  A.H = H;
+  A.part = part;
+  A.count = count;
+  A.active = active;
+  A.status = status;
+  A.n = T->n;
+  A.P = T->L.P;
+  A.Q = T->L.Q;
+  A.B = B;
+  // never more CTAs than units: every CTA then owns at least one unit, which
+  // the panel bookkeeping (owners of a panel's first and last unit bound its
+  // contributors) relies on
+  const int64_t U = (int64_t)B * T->L.P * T->L.Q;
+  const int grid = (int)std::min<int64_t>(mt::matvec_grid(T), U);
+  k_matvec<PREC><<<grid, S::THREADS, S::SMEM_BYTES, s>>>(A);
+}
+
+}  // namespace
+
+namespace mt {
+
+int matvec_grid(const mt_tensor *T) { return T->tiles->ctx->num_sms; }
+
+cudaError_t matvec_prepare() {
+  cudaError_t e;
+  if ((e = prepare_mv<MT_F32>()) != cudaSuccess) return e;
+  if ((e = prepare_mv<MT_F64>()) != cudaSuccess) return e;
+  if ((e = prepare_mv<MT_BF16_SCALED>()) != cudaSuccess) return e;
+  return prepare_mv<MT_BF16_SPLIT>();
+}
+
+void layout_for(int prec, mt_layout *L) {
+  switch (prec) {
+    case MT_F32: L->TR = MvCfg<MT_F32>::TR; L->TC = MvCfg<MT_F32>::TC; L->nplane = 6; L->elem_bytes = 4; break;
+    case MT_F64: L->TR = MvCfg<MT_F64>::TR; L->TC = MvCfg<MT_F64>::TC; L->nplane = 6; L->elem_bytes = 8; break;
+    case MT_BF16_SCALED:
+      L->TR = MvCfg<MT_BF16_SCALED>::TR; L->TC = MvCfg<MT_BF16_SCALED>::TC; L->nplane = 6; L->elem_bytes = 2; break;
+    default:
+      L->TR = MvCfg<MT_BF16_SPLIT>::TR; L->TC = MvCfg<MT_BF16_SPLIT>::TC; L->nplane = 12; L->elem_bytes = 2; break;
+  }
+  L->scale_bytes_per_chunk = (prec == MT_BF16_SCALED) ? (int64_t)L->TR * L->TC : 0;
+}
+
+int64_t xs_floats(const mt_tensor *T) {
+  const int64_t per = T->L.Q * 3 * T->L.TC;
+  return T->prec == MT_F64 ? 2 * per : per;  // doubles take two floats
+}
+
+size_t matvec_part_bytes(const mt_tensor *T) {
+  const size_t el = T->prec == MT_F64 ? 8 : 4;
+  return (size_t)2 * matvec_grid(T) * T->L.TR * 3 * el;
+}
+
+size_t matvec_count_bytes(const mt_tensor *T, int B) { return (size_t)B * T->L.P * 8 /*W<=8*/ * sizeof(int); }
+
+void launch_prep_xs(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
+  const int64_t tot = (int64_t)B * T->L.Q * T->L.TC;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4096);
+  if (T->prec == MT_F64)
+    k_prep_xs<float, double><<<blocks, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->L.Q, T->L.TC, B,
+                                                     reinterpret_cast<double *>(xs));
+  else
+    k_prep_xs<float, float><<<blocks, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->L.Q, T->L.TC, B, xs);
+}
+
+void launch_prep_xs_f64(const mt_tensor *T, const double *m, int B, double *xs, cudaStream_t s) {
+  const int64_t tot = (int64_t)B * T->L.Q * T->L.TC;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4096);
+  k_prep_xs<double, double><<<blocks, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->L.Q, T->L.TC, B, xs);
+}
+
+void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *part, int *count,
+                   const int *active, int *status, cudaStream_t s) {
+  switch (T->prec) {
+    case MT_F32: launch_mv<MT_F32>(T, xs, B, H, part, count, active, status, s); break;
+    case MT_F64: launch_mv<MT_F64>(T, xs, B, H, part, count, active, status, s); break;
+    case MT_BF16_SCALED: launch_mv<MT_BF16_SCALED>(T, xs, B, H, part, count, active, status, s); break;
+    case MT_BF16_SPLIT: launch_mv<MT_BF16_SPLIT>(T, xs, B, H, part, count, active, status, s); break;
+  }
+}
+
+void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s) {
+  if (T->near_count == 0) return;
+  dim3 grid((unsigned)((T->n + 127) / 128), (unsigned)B);
+  k_near<<<grid, 128, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_val, T->tiles->d_Ms, m, H, active);
+}
+
+}  // namespace mt

@@ -1,0 +1,269 @@
+// Internal declarations of libmagtile: handle structs, layout constants,
+// device helpers (mbarrier, bulk TMA copies, bounded waits, reductions).
+// Nothing here is part of the ABI; include/mt.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mt.h"
+
+// ---------------------------------------------------------------------------
+// error handling (host)
+// ---------------------------------------------------------------------------
+namespace mt {
+
+void set_error(const char *fmt, ...);
+mt_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+}  // namespace mt
+
+#define MT_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return mt::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define MT_CHECK(cond, code, ...)      \
+  do {                                 \
+    if (!(cond)) {                     \
+      mt::set_error(__VA_ARGS__);      \
+      return (code);                   \
+    }                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// physical constants (SI)
+// ---------------------------------------------------------------------------
+#define MT_PI 3.14159265358979323846
+#define MT_MU0 (4.0e-7 * MT_PI)  // vacuum permeability, classical value
+
+// device-side error codes written to a status word by bounded waits
+#define MT_DEV_TIMEOUT 1
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct mt_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  std::mutex mu;
+  int *d_status = nullptr;  // device status word for bounded waits
+};
+
+struct mt_tiles {
+  mt_ctx *ctx = nullptr;
+  int64_t n = 0;
+  // host copies (FP64, as given)
+  std::vector<double> centre, edge, Ms, Aex, Ku, axis;
+  std::vector<int32_t> nbr;  // empty = no exchange
+  // device copies
+  double *d_centre = nullptr;  // 3n
+  double *d_edge = nullptr;    // 3n
+  float *d_Ms = nullptr;       // n
+  float *d_wex = nullptr;      // 6n: 2A_i/(mu0 Ms_i h_i d_ip) per face, 0 if none
+  int32_t *d_nbr = nullptr;    // 6n
+  float *d_kan = nullptr;      // n: 2K_i/(mu0 Ms_i)
+  float *d_axis = nullptr;     // 3n unit easy axis
+  double *d_wvol = nullptr;    // n: V_i / sum V
+  bool has_exchange = false;
+};
+
+// Tile-blocked storage: the n x n grid of 3x3 blocks is cut into row panels
+// of TR tiles and column chunks of TC tiles.  Chunk (p, q) is contiguous and
+// holds NPLANE planes of TR x TC values (plane-major, then row, then column),
+// so a panel is one contiguous stream and a chunk one bulk TMA copy.
+struct mt_layout {
+  int TR = 16, TC = 128;
+  int nplane = 6;           // 6 unique entries (12 for split hi/lo)
+  int elem_bytes = 4;
+  int64_t P = 0, Q = 0;     // panels, chunks per panel
+  int64_t chunk_elems() const { return (int64_t)nplane * TR * TC; }
+  int64_t chunk_bytes() const { return chunk_elems() * elem_bytes; }
+  int64_t scale_bytes_per_chunk = 0;  // BF16 scaled: TR x TC int8 exponents
+};
+
+struct mt_tensor {
+  mt_tiles *tiles = nullptr;
+  int prec = MT_F32;
+  int64_t n = 0;
+  mt_layout L;
+  void *d_data = nullptr;
+  size_t bytes = 0;
+  int8_t *d_scale = nullptr;     // BF16 scaled: per-block exponent
+  // near-field blocks held apart in FP64 (block sparse rows)
+  int64_t near_count = 0;
+  int32_t *d_near_ptr = nullptr;  // n+1
+  int32_t *d_near_col = nullptr;  // near_count
+  double *d_near_val = nullptr;   // near_count * 6
+  // workspace of the standalone field / rhs calls
+  float *d_xs = nullptr;
+  int xs_B = 0;
+  float *d_part = nullptr;
+  int *d_count = nullptr;
+  int count_B = 0;
+  float *d_Hd = nullptr;
+  int Hd_B = 0;
+};
+
+// ---------------------------------------------------------------------------
+// matvec workspace and launch
+// ---------------------------------------------------------------------------
+namespace mt {
+
+// Number of CTAs of the streaming product (one per SM).
+int matvec_grid(const mt_tensor *T);
+// Set kernel attributes once, before any stream capture.
+cudaError_t matvec_prepare();
+// Panel/chunk shape of the storage for a precision (P, Q left to the caller).
+void layout_for(int prec, mt_layout *L);
+// floats of the padded, Ms-scaled operand of one simulation: Q * 3 * TC
+int64_t xs_floats(const mt_tensor *T);
+// bytes of the partial-sum workspace and of the panel counters for B sims
+size_t matvec_part_bytes(const mt_tensor *T);
+size_t matvec_count_bytes(const mt_tensor *T, int B);
+
+// xs[b] = Ms * m[b] in the padded chunked layout ([Q][3][TC], zero padded)
+void launch_prep_xs(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s);
+void launch_prep_xs_f64(const mt_tensor *T, const double *m, int B, double *xs, cudaStream_t s);
+// H[b] = -N xs[b]; active (may be null) skips finished simulations
+void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *part, int *count,
+                   const int *active, int *status, cudaStream_t s);
+// H[b] -= near-field FP64 blocks applied to Ms m (only for BF16 precisions)
+void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s);
+
+// assembly (FP64) and packing
+mt_status assemble(mt_tensor *T);
+mt_status blocks_fp64(mt_tiles *t, int64_t count, const int64_t *pairs, double *out);
+mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out);
+
+// per-simulation prefactors of Eq. 1: g1 (precession), g2 (damping), Ha
+void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::vector<float> &g2,
+                    std::vector<float> &ha);
+
+// standalone right-hand side
+void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B, const float *g1,
+                      const float *g2, const float *Ha, float *dmdt, float *tau, cudaStream_t s);
+
+}  // namespace mt
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace mtd {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after ~limit_ns of wall
+// time: then the status word gets MT_DEV_TIMEOUT and false is returned.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
+                                                  uint64_t limit_ns = 2000000000ull) {
+  if (mbar_try_wait(bar, parity)) return true;
+  uint64_t t0 = globaltimer_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0u) {
+      if (globaltimer_ns() - t0 > limit_ns) {
+        if (status) atomicExch(status, MT_DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// 1-D bulk copy global -> shared, completion signalled on `bar` (tx bytes).
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                         uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Stream-K split of U work units over G CTAs: CTA k owns [begin(k), begin(k+1)).
+__host__ __device__ __forceinline__ int64_t sk_begin(int64_t k, int64_t U, int64_t G) { return (k * U) / G; }
+// CTA owning unit u: largest k with begin(k) <= u.
+__host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) {
+  return ((u + 1) * G + U - 1) / U - 1;
+}
+
+}  // namespace mtd
+#endif

@@ -1,0 +1,233 @@
+"""GPU parity of the tensor assembly and the demag product against the FP64
+oracle, through the C ABI.
+
+Tolerances (relative L2 over all compared values):
+  FP64 tensor / FP64 field ............ 1e-12
+  FP32 storage, FP32 field ............ 1e-6
+  BF16 storage (+ FP64 near blocks) ... 5e-3
+  split BF16 hi+lo (+ FP64 near) ...... 1e-5 (per-entry error 2^-17)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05364_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2107_05364_gb300 import build
+    build.build()
+    from paper_2107_05364_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(mt):
+    return mt.mt_ctx_create(0)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+GEOMS = {
+    "film40x10": lambda: wl.film(40, 10, 1),                              # config 1 shape, n = 400
+    "graded23x7x3": lambda: wl.graded_film(23, 7, 3, (230e-9, 70e-9, 9e-9), seed=4),  # ragged panels
+    "cube9": lambda: wl.cube(9, 5.0),                                      # points far below tiles
+    "single": lambda: wl.film(1, 1, 1, size=(5e-9, 4e-9, 3e-9)),           # n = 1
+    "chain17": lambda: wl.film(17, 1, 1, size=(85e-9, 5e-9, 5e-9)),        # n < one chunk
+}
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_fp64_tensor_matches_oracle(mt, ctx, name):
+    t = GEOMS[name]()
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f64")
+    N = mt.mt_tensor_read_rows(T, 0, t.n)
+    ref = oracle.demag_tensor(t.centre, t.edge)
+    assert _rel(N, ref) <= 1e-12
+    # the point blocks also agree block by block for the largest entries
+    big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+    assert np.abs(N[big] - ref[big]).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_blocks_entry_matches_oracle(mt, ctx):
+    t = wl.graded_film(30, 9, 3, (300e-9, 90e-9, 9e-9), seed=1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    rng = np.random.default_rng(3)
+    pairs = rng.integers(0, t.n, size=(500, 2))
+    pairs[:20, 1] = pairs[:20, 0]  # self terms
+    g = mt.mt_demag_blocks(tiles, pairs)
+    r = oracle.demag_blocks(t.centre, t.edge, pairs)
+    assert _rel(g, r) <= 1e-12
+
+
+def test_overlap_is_rejected(mt, ctx):
+    t = wl.film(4, 2, 1)
+    t.centre[1] = t.centre[0] + np.array([0.25, 0.0, 0.0]) * t.edge[0]
+    tiles = mt.mt_tiles_create(ctx, t)
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_demag_assemble(tiles, "f32")
+    assert e.value.status == mt.MT_EOVERLAP
+
+
+def test_bad_tiles_are_rejected(mt, ctx):
+    t = wl.film(4, 2, 1)
+    t.edge[2, 1] = -1.0
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_tiles_create(ctx, t)
+    assert e.value.status == mt.MT_EINVAL
+    t = wl.film(4, 2, 1)
+    t.nbr[3, 0] = 99
+    with pytest.raises(mt.MtError):
+        mt.mt_tiles_create(ctx, t)
+
+
+TOL = {"f32": 1e-6, "bf16": 5e-3, "split": 1e-5}
+
+
+def _field_case(mt, ctx, t, prec, B, seed):
+    import torch
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, prec)
+    m = np.stack([wl.m_random(t.n, seed=seed + b) for b in range(B)]).astype(np.float32)
+    md = oracle.Model.from_tiles(t)
+    ref = np.stack([oracle.demag_field(md, m[b].astype(np.float64)) for b in range(B)])
+    mg = torch.tensor(m.ravel(), device="cuda")
+    H = torch.full_like(mg, float("nan"))
+    mt.mt_demag_field(T, mg, H, B=B)
+    torch.cuda.synchronize()
+    return H.cpu().numpy().reshape(B, t.n, 3), ref, T
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16", "split"])
+@pytest.mark.parametrize("name", ["film40x10", "graded23x7x3", "cube9", "single", "chain17"])
+def test_field_parity(mt, ctx, prec, name):
+    t = GEOMS[name]()
+    if name == "graded23x7x3":
+        t.Ms[:] = np.linspace(4e5, 1.2e6, t.n)  # heterogeneous Ms
+    Hg, ref, _ = _field_case(mt, ctx, t, prec, B=3, seed=7)
+    assert np.isfinite(Hg).all()
+    for b in range(3):
+        assert _rel(Hg[b], ref[b]) <= TOL[prec], (prec, name, b, _rel(Hg[b], ref[b]))
+
+
+def test_field_uniform_m_superposition(mt, ctx):
+    # uniform m, uniform Ms: H_d,i = -N_prism(c_i) Ms m (exact superposition)
+    import torch
+    t = wl.film(50, 13, 2, size=(250e-9, 65e-9, 6e-9))
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    u = np.array([0.48, -0.6, 0.64])
+    mg = torch.tensor(np.tile(u, t.n).astype(np.float32), device="cuda")
+    H = torch.empty_like(mg)
+    mt.mt_demag_field(T, mg, H)
+    torch.cuda.synchronize()
+    lo, hi = t.centre - t.edge / 2, t.centre + t.edge / 2
+    pc, pe = (lo.min(0) + hi.max(0)) / 2, hi.max(0) - lo.min(0)
+    exp = np.stack([-oracle.point_tensor(t.centre[i], pc, pe) @ (t.Ms[i] * u.astype(np.float32).astype(float))
+                    for i in range(t.n)])
+    assert _rel(H.cpu().numpy().reshape(-1, 3), exp) <= 1e-6
+
+
+def test_fp64_field_matches_oracle(mt, ctx):
+    import torch
+    t = wl.graded_film(19, 11, 2, (190e-9, 110e-9, 6e-9), seed=8)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f64")
+    m = wl.m_random(t.n, seed=2)
+    md = oracle.Model.from_tiles(t)
+    ref = oracle.demag_field(md, m)
+    mg = torch.tensor(m.ravel(), dtype=torch.float64, device="cuda")
+    H = torch.empty_like(mg)
+    mt.mt_demag_field_f64(T, mg, H)
+    torch.cuda.synchronize()
+    assert _rel(H.cpu().numpy().reshape(-1, 3), ref) <= 1e-12
+
+
+def test_field_repeatable_and_batched_equals_single(mt, ctx):
+    # deterministic: same bits on repeat; sim b of a batch equals a B=1 call
+    import torch
+    t = wl.film(60, 15, 1, size=(300e-9, 75e-9, 3e-9))
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    m = np.stack([wl.m_random(t.n, seed=s) for s in range(4)]).astype(np.float32)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    H1 = torch.empty_like(mg)
+    H2 = torch.empty_like(mg)
+    mt.mt_demag_field(T, mg, H1, B=4)
+    mt.mt_demag_field(T, mg, H2, B=4)
+    torch.cuda.synchronize()
+    assert torch.equal(H1, H2)
+    for b in range(4):
+        mb = mg[b * 3 * t.n:(b + 1) * 3 * t.n].clone()
+        Hb = torch.empty_like(mb)
+        mt.mt_demag_field(T, mb, Hb, B=1)
+        torch.cuda.synchronize()
+        assert _rel(Hb.cpu().numpy(), H1[b * 3 * t.n:(b + 1) * 3 * t.n].cpu().numpy()) <= 1e-6
+
+
+def test_full_size_film_sampled_rows(mt, ctx):
+    # the 200 x 50 x 1 film (n = 10,000) as timed by the benchmark: sampled
+    # rows against the oracle's matrix-free rows
+    import torch
+    t = wl.film(200, 50, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    m = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    H = torch.empty_like(mg)
+    mt.mt_demag_field(T, mg, H)
+    torch.cuda.synchronize()
+    rows = np.unique(np.concatenate([[0, 1, 199, 200, t.n - 1], np.random.default_rng(0).integers(0, t.n, 60)]))
+    ref = oracle.demag_field_rows(t.centre, t.edge, t.Ms, m.astype(np.float64), rows)
+    Hg = H.cpu().numpy().reshape(-1, 3)[rows]
+    assert _rel(Hg, ref) <= 1e-6
+    # stored entries of sampled rows against FP64 blocks
+    N = mt.mt_tensor_read_rows(T, 4990, 4994)
+    pairs = np.array([[i, j] for i in range(4990, 4994) for j in range(t.n)])
+    ref = oracle.demag_blocks(t.centre, t.edge, pairs).reshape(4, t.n, 6)
+    assert _rel(N, ref) <= 1e-7
+
+
+def test_graded_30000_sampled_blocks_fp64(mt, ctx):
+    # graded 200 x 50 x 3 mesh (n = 30,000): FP64 blocks on sampled pairs
+    t = wl.graded_film(200, 50, 3, seed=0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    rng = np.random.default_rng(11)
+    pairs = rng.integers(0, t.n, size=(4000, 2))
+    g = mt.mt_demag_blocks(tiles, pairs)
+    r = oracle.demag_blocks(t.centre, t.edge, pairs)
+    assert _rel(g, r) <= 1e-12
+
+
+def test_llg_rhs_parity(mt, ctx):
+    import torch
+    t = wl.graded_film(20, 8, 2, (200e-9, 80e-9, 6e-9), seed=5)
+    t.Ku[:] = 5e4
+    t.axis[:] = np.array([0.0, 0.6, 0.8])
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    B = 2
+    alphas = [0.02, 0.5]
+    Ha = np.array([[-1.9e4, 3.4e3, 0.0], [1e4, 2e4, -5e3]])
+    m = np.stack([wl.m_random(t.n, seed=20 + b) for b in range(B)]).astype(np.float32)
+    p, keep = mt.llg_params(B, alpha=alphas, Ha=Ha)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    k = torch.empty_like(mg)
+    tau = torch.empty(B, device="cuda")
+    mt.mt_llg_rhs(T, p, mg, k, tau, B=B)
+    torch.cuda.synchronize()
+    md = oracle.Model.from_tiles(t)
+    for b in range(B):
+        kr, taur = oracle.llg_rhs(md, m[b].astype(np.float64), oracle.llg_params(alpha=alphas[b], Ha=Ha[b]))
+        kg = k.cpu().numpy().reshape(B, t.n, 3)[b]
+        assert _rel(kg, kr) <= 1e-5
+        assert abs(tau.cpu().numpy()[b] - taur) <= 1e-5 * taur

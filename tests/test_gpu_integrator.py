@@ -1,0 +1,174 @@
+"""GPU parity of the Runge-Kutta (4,5) integration of the Landau-Lifshitz
+equation (Sec. 3.1, Eq. 1) against the FP64 oracle, through the C ABI.
+
+The GPU integrates in FP32 on the FP32-stored tensor, the oracle in FP64;
+tolerances are stated per test: fixed steps agree to FP32 round-off grown
+over the steps, adaptive traces to within the integration tolerance, and
+relaxed states to max |dm| <= 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05364_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+MU0 = 4e-7 * math.pi
+FIELD1 = np.array([-24.6e-3, 4.3e-3, 0.0]) / MU0
+
+
+@pytest.fixture(scope="module")
+def mt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2107_05364_gb300 import build
+    build.build()
+    from paper_2107_05364_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(mt):
+    return mt.mt_ctx_create(0)
+
+
+@pytest.fixture(scope="module")
+def film(mt, ctx):
+    t = wl.film(40, 10, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    return t, tiles, T, oracle.Model.from_tiles(t)
+
+
+def test_fixed_steps_match_oracle(mt, film):
+    t, tiles, T, md = film
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    h = 1e-13
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    I = mt.Integrator(T, p, mt.ode_opts(fixed_h=h))
+    I.set_state(m0.ravel())
+    I.step(20)
+    mg = I.get_state()[0]
+    st, mo, _, _ = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=FIELD1),
+                                    oracle.ode_opts(fixed_h=h), 0.0, 20 * h, 1)
+    assert st == oracle.OK
+    assert np.abs(mg - mo).max() <= 2e-5
+    np.testing.assert_allclose(np.linalg.norm(mg, axis=1), 1.0, atol=1e-6)
+    s = I.stats()[0]
+    assert s["n_accept"] == 20 and s["n_reject"] == 0
+    assert abs(s["t"] - 20 * h) <= 1e-9 * 20 * h
+
+
+def test_adaptive_trace_matches_oracle(mt, film):
+    # standard-problem-4 field 1 from the (1,1,1) start: <m>(t) for 0.1 ns
+    t, tiles, T, md = film
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    opts = dict(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11)
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    I = mt.Integrator(T, p, mt.ode_opts(**opts))
+    I.set_state(m0.ravel())
+    T1, n_out = 1e-10, 20
+    s, mavg, st = I.run(T1, n_out)
+    assert st[0]["status"] == 0 and abs(st[0]["t"] - T1) < 1e-20
+    so, mo, mref, sto = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=FIELD1),
+                                         oracle.ode_opts(**opts), 0.0, T1, n_out)
+    assert so == oracle.OK
+    assert np.abs(mavg[:, 0, :] - mref).max() <= 2e-4
+    # the step counts agree to within a few percent
+    assert abs(st[0]["n_accept"] - sto["n_accept"]) <= 0.05 * sto["n_accept"] + 3
+
+
+def test_macrospin_larmor_on_gpu(mt, ctx):
+    # one cube tile: H_d is parallel to m; precession at gamma' H about z
+    h = 5e-9
+    t = wl.grid_tiles([0, h], [0, h], [0, h], 8e5, 1.3e-11, 0.0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    H, gamma, alpha = 4e4, 2.211e5, 0.1
+    th0, ph0 = 1.2, 0.3
+    m0 = np.array([[math.sin(th0) * math.cos(ph0), math.sin(th0) * math.sin(ph0), math.cos(th0)]], np.float32)
+    p, keep = mt.llg_params(1, gamma=gamma, alpha=alpha, Ha=(0, 0, H))
+    I = mt.Integrator(T, p, mt.ode_opts(rtol=1e-7, atol=1e-7, h0=1e-14, hmax=1e-11))
+    I.set_state(m0.ravel())
+    T1, n_out = 1e-9, 10
+    _, mavg, st = I.run(T1, n_out)
+    ts = T1 * np.arange(1, n_out + 1) / n_out
+    w = gamma / (1 + alpha ** 2) * H
+    th = 2 * np.arctan(math.tan(th0 / 2) * np.exp(-alpha * w * ts))
+    ph = ph0 + w * ts
+    exp = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
+    assert np.abs(mavg[:, 0, :] - exp).max() <= 2e-5
+
+
+def test_relax_matches_oracle(mt, film):
+    t, tiles, T, md = film
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    opts = dict(rtol=1e-5, atol=1e-5, h0=1e-14, hmax=1e-11)
+    p, keep = mt.llg_params(1, alpha=0.5)
+    I = mt.Integrator(T, p, mt.ode_opts(**opts))
+    I.set_state(m0.ravel())
+    tol = 1e-5
+    s, st = I.relax(tol, 20e-9)
+    assert st[0]["status"] == 0 and st[0]["tau"] < tol
+    mg = I.get_state()[0]
+    so, mo, sto = oracle.relax(md, m0.astype(np.float64), oracle.llg_params(alpha=0.5),
+                               oracle.ode_opts(**opts), tol, 20e-9)
+    assert so == oracle.OK
+    assert np.abs(mg - mo).max() <= 1e-4
+    np.testing.assert_allclose(np.linalg.norm(mg, axis=1), 1.0, atol=1e-6)
+
+
+def test_relax_time_cap_reports_noconv(mt, film):
+    t, tiles, T, md = film
+    p, keep = mt.llg_params(1, alpha=0.02)
+    I = mt.Integrator(T, p, mt.ode_opts())
+    I.set_state(wl.m_noisy(t.n).astype(np.float32).ravel())
+    s, st = I.relax(1e-9, 2e-12, check=False)
+    assert s == mt.MT_ENOCONV and st[0]["status"] == mt.MT_ENOCONV
+
+
+def test_batch_equals_single_runs(mt, film):
+    # B simulations with different fields and damping; each equals its own
+    # B = 1 run to within FP32 round-off: the streaming product splits its
+    # sums at batch-dependent points, so the bits (and, rarely, one step-size
+    # decision) may differ
+    t, tiles, T, md = film
+    B = 3
+    alphas = [0.02, 0.1, 0.5]
+    Ha = np.array([[-1.9e4, 3.4e3, 0], [2e4, 0, 0], [0, -3e4, 1e4]])
+    m0 = np.stack([wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=b) for b in range(B)]).astype(np.float32)
+    opts = mt.ode_opts(rtol=1e-6, atol=1e-6)
+    p, keep = mt.llg_params(B, alpha=alphas, Ha=Ha)
+    I = mt.Integrator(T, p, opts, B=B)
+    I.set_state(m0.ravel())
+    _, mavg, st = I.run(5e-11, 5)
+    mb = I.get_state()
+    for b in range(B):
+        p1, keep1 = mt.llg_params(1, alpha=alphas[b], Ha=Ha[b])
+        I1 = mt.Integrator(T, p1, opts, B=1)
+        I1.set_state(m0[b].ravel())
+        _, mavg1, st1 = I1.run(5e-11, 5)
+        assert abs(st1[0]["n_accept"] - st[b]["n_accept"]) <= 2
+        assert np.abs(I1.get_state()[0] - mb[b]).max() <= 1e-5
+        assert np.abs(mavg1[:, 0] - mavg[:, b]).max() <= 1e-5
+
+
+def test_set_state_from_device_and_steps_mode(mt, film):
+    import torch
+    t, tiles, T, md = film
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    I = mt.Integrator(T, p, mt.ode_opts(rtol=1e-6, atol=1e-6))
+    m0 = torch.tensor(wl.m_noisy(t.n, seed=3).astype(np.float32).ravel(), device="cuda")
+    I.set_state(m0)
+    I.step(10)
+    out = torch.empty_like(m0)
+    I.get_state(out)
+    torch.cuda.synchronize()
+    s = I.stats()[0]
+    assert s["n_accept"] + s["n_reject"] == 10
+    assert s["n_rhs"] == 1 + 6 * 10
+    assert torch.isfinite(out).all()

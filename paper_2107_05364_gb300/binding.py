@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import sys
 
 import numpy as np
 
@@ -165,6 +166,10 @@ class Ctx:
             self.h = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be gone: leave the
+        # memory to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -190,6 +195,10 @@ class TilesH:
             self.h = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be gone: leave the
+        # memory to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -217,6 +226,10 @@ class TensorH:
             self.h = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be gone: leave the
+        # memory to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -345,6 +358,10 @@ class Integrator:
             self.h = None
 
     def __del__(self):
+        # at interpreter exit the CUDA runtime may already be gone: leave the
+        # memory to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

@@ -29,6 +29,13 @@ mt_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
   return e == cudaErrorMemoryAllocation ? MT_ENOMEM : MT_ECUDA;
 }
 
+void ctx_release(mt_ctx *c) {
+  if (c && --c->refs == 0) {
+    cudaFree(c->d_status);
+    delete c;
+  }
+}
+
 }  // namespace mt
 
 namespace {
@@ -41,6 +48,7 @@ mt_status upload(P **dst, const P *src, size_t count) {
 }
 
 void free_tiles(mt_tiles *t) {
+  mt_ctx *ctx = t->ctx;
   cudaFree(t->d_centre);
   cudaFree(t->d_edge);
   cudaFree(t->d_Ms);
@@ -50,6 +58,7 @@ void free_tiles(mt_tiles *t) {
   cudaFree(t->d_axis);
   cudaFree(t->d_wvol);
   delete t;
+  if (ctx) mt::ctx_release(ctx);
 }
 
 void free_tensor_mem(mt_tensor *T) {
@@ -135,11 +144,7 @@ mt_status mt_ctx_create(int device, size_t hbm_budget_bytes, mt_ctx **out) {
   return MT_OK;
 }
 
-void mt_ctx_destroy(mt_ctx *ctx) {
-  if (!ctx) return;
-  cudaFree(ctx->d_status);
-  delete ctx;
-}
+void mt_ctx_destroy(mt_ctx *ctx) { mt::ctx_release(ctx); }
 
 size_t mt_ctx_bytes_in_use(const mt_ctx *ctx) { return ctx ? ctx->in_use : 0; }
 
@@ -170,6 +175,7 @@ mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const do
   MT_CUDA(cudaSetDevice(ctx->device));
   mt_tiles *t = new mt_tiles();
   t->ctx = ctx;
+  ctx->refs++;
   t->n = n;
   t->centre.assign(centre, centre + 3 * n);
   t->edge.assign(edge, edge + 3 * n);
@@ -227,9 +233,7 @@ mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const do
   return MT_OK;
 }
 
-void mt_tiles_destroy(mt_tiles *tiles) {
-  if (tiles) free_tiles(tiles);
-}
+void mt_tiles_destroy(mt_tiles *tiles) { mt::tiles_release(tiles); }
 
 mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
   MT_CHECK(tiles && out, MT_EINVAL, "mt_demag_assemble: NULL argument");
@@ -238,6 +242,7 @@ mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
   MT_CUDA(cudaSetDevice(ctx->device));
   mt_tensor *T = new mt_tensor();
   T->tiles = tiles;
+  tiles->refs++;
   T->prec = prec;
   T->n = tiles->n;
   mt::layout_for(prec, &T->L);
@@ -252,6 +257,7 @@ mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
       mt::set_error("mt_demag_assemble: %zu bytes exceed the context budget (%zu of %zu in use)", T->bytes,
                     ctx->in_use, ctx->budget);
       delete T;
+      mt::tiles_release(tiles);
       return MT_ENOMEM;
     }
     ctx->in_use += T->bytes;
@@ -263,6 +269,7 @@ mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
       ctx->in_use -= T->bytes;
     }
     delete T;
+    mt::tiles_release(tiles);
     return st;
   };
   cudaError_t e = cudaMalloc(&T->d_data, data_bytes);
@@ -278,16 +285,7 @@ mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
   return MT_OK;
 }
 
-void mt_tensor_destroy(mt_tensor *T) {
-  if (!T) return;
-  cudaDeviceSynchronize();
-  free_tensor_mem(T);
-  {
-    std::lock_guard<std::mutex> lk(T->tiles->ctx->mu);
-    T->tiles->ctx->in_use -= T->bytes;
-  }
-  delete T;
-}
+void mt_tensor_destroy(mt_tensor *T) { mt::tensor_release(T); }
 
 mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
   MT_CHECK(T && info, MT_EINVAL, "mt_tensor_get_info: NULL argument");
@@ -368,3 +366,24 @@ mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m, int B
 }
 
 }  // extern "C"
+
+namespace mt {
+
+void tiles_release(mt_tiles *t) {
+  if (t && --t->refs == 0) free_tiles(t);
+}
+
+void tensor_release(mt_tensor *T) {
+  if (!T || --T->refs != 0) return;
+  cudaDeviceSynchronize();
+  free_tensor_mem(T);
+  mt_tiles *tiles = T->tiles;
+  {
+    std::lock_guard<std::mutex> lk(tiles->ctx->mu);
+    tiles->ctx->in_use -= T->bytes;
+  }
+  delete T;
+  tiles_release(tiles);
+}
+
+}  // namespace mt

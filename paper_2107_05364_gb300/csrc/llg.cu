@@ -709,6 +709,7 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
   MT_CUDA(cudaSetDevice(T->tiles->ctx->device));
   mt_integrator *I = new mt_integrator();
   I->T = T;
+  T->refs++;
   I->B = B;
   I->user_stream = (cudaStream_t)stream;
   if (cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -790,6 +791,7 @@ void mt_integrator_destroy(mt_integrator *I) {
     if (e) cudaEventDestroy(e);
   if (I->order_ev) cudaEventDestroy(I->order_ev);
   if (I->stream) cudaStreamDestroy(I->stream);
+  mt::tensor_release(I->T);
   delete I;
 }
 

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -49,7 +50,11 @@ mt_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 // ---------------------------------------------------------------------------
 // handles
 // ---------------------------------------------------------------------------
+// Handles are reference counted: a tile set keeps its context alive, a
+// tensor its tile set, an integrator its tensor, so *_destroy may be called
+// in any order (the memory goes when the last user lets go).
 struct mt_ctx {
+  std::atomic<int> refs{1};
   int device = 0;
   int num_sms = 0;
   size_t budget = 0;
@@ -59,6 +64,7 @@ struct mt_ctx {
 };
 
 struct mt_tiles {
+  std::atomic<int> refs{1};
   mt_ctx *ctx = nullptr;
   int64_t n = 0;
   // host copies (FP64, as given)
@@ -91,6 +97,7 @@ struct mt_layout {
 };
 
 struct mt_tensor {
+  std::atomic<int> refs{1};
   mt_tiles *tiles = nullptr;
   int prec = MT_F32;
   int64_t n = 0;
@@ -138,6 +145,11 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
                    const int *active, int *status, cudaStream_t s);
 // H[b] -= near-field FP64 blocks applied to Ms m (only for BF16 precisions)
 void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s);
+
+// reference counting of handles (see the handle structs)
+void ctx_release(mt_ctx *c);
+void tiles_release(mt_tiles *t);
+void tensor_release(mt_tensor *T);
 
 // assembly (FP64) and packing
 mt_status assemble(mt_tensor *T);

@@ -1,0 +1,79 @@
+"""Small driver for profiling one kernel family on a chosen film size.
+
+    python -m paper_2107_05364_gb300.profile_case --nx 100 --ny 40 --prec f32 --what field --reps 3
+
+--what field    : mt_demag_field R times (prep + streaming product [+ near])
+--what step     : R Runge-Kutta attempts through the integrator graph
+--what assemble : tensor assembly only
+Prints the average time per call measured with CUDA events (not meaningful
+under a profiler).
+"""
+from __future__ import annotations
+
+import argparse
+import math
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=100)
+    ap.add_argument("--ny", type=int, default=40)
+    ap.add_argument("--nz", type=int, default=1)
+    ap.add_argument("--prec", default="f32")
+    ap.add_argument("--what", default="field", choices=["field", "step", "assemble"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--B", type=int, default=1)
+    a = ap.parse_args()
+
+    import torch
+
+    from . import binding as mt
+    from . import workloads as wl
+
+    t = wl.film(a.nx, a.ny, a.nz, size=(2.5e-9 * a.nx, 2.5e-9 * a.ny, 3e-9 * a.nz))
+    ctx = mt.mt_ctx_create(0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.what == "assemble":
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.reps):
+            T = mt.mt_demag_assemble(tiles, a.prec)
+            T.close()
+        e1.record()
+        torch.cuda.synchronize()
+        print("assemble n=%d: %.3f ms" % (t.n, e0.elapsed_time(e1) / a.reps))
+        return
+    T = mt.mt_demag_assemble(tiles, a.prec)
+    m = np.stack([wl.m_random(t.n, seed=b) for b in range(a.B)]).astype(np.float32)
+    if a.what == "field":
+        mg = torch.tensor(m.ravel(), device="cuda")
+        H = torch.empty_like(mg)
+        mt.mt_demag_field(T, mg, H, B=a.B)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.reps):
+            mt.mt_demag_field(T, mg, H, B=a.B)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        gbs = 24.0 * t.n * t.n * a.B / (ms * 1e-3) / 1e9 if a.prec == "f32" else float("nan")
+        print("field n=%d B=%d prec=%s: %.4f ms/call (%.0f GB/s algorithmic for f32)" % (t.n, a.B, a.prec, ms, gbs))
+    else:
+        p, keep = mt.llg_params(a.B, alpha=0.02, Ha=np.array([-24.6e-3, 4.3e-3, 0.0]) / (4e-7 * math.pi))
+        I = mt.Integrator(T, p, mt.ode_opts(), B=a.B)
+        I.set_state(m.ravel())
+        I.step(1)
+        torch.cuda.synchronize()
+        s = torch.cuda.ExternalStream(I.stream_handle())
+        e0.record(s)
+        I.step(a.reps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        print("step n=%d B=%d: %.4f ms/attempt" % (t.n, a.B, e0.elapsed_time(e1) / a.reps))
+
+
+if __name__ == "__main__":
+    main()

@@ -194,6 +194,30 @@ MT_API mt_status mt_demag_field(mt_tensor *T, const float *m, int B, float *H, v
  * MT_F64), MT_ECUDA. */
 MT_API mt_status mt_demag_field_f64(mt_tensor *T, const double *m, int B, double *H, void *stream);
 
+/* Size of the fixed device work area used by mt_demag_field_noalloc, per GPU
+ * that loads the library (held until the process exits). */
+#define MT_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* mt_demag_field for callers that must not let the library allocate device
+ * memory: a loop that has given all free HBM to cached tensors, code next to
+ * latency-critical streams that cannot take the device-wide synchronisation
+ * cudaMalloc/cudaFree may cause, or an application whose own memory pool
+ * forbids the CUDA allocator.  Same arguments, same result as mt_demag_field
+ * (FP32 and BF16 tensors); this call allocates nothing: its work areas (the
+ * scaled copy of m, partial panel sums, panel counters) live in one fixed
+ * array of MT_NOALLOC_SCRATCH_BYTES in the library's device image.  The
+ * paper has no counterpart; it is an interface convenience.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, which may load the library's device code);
+ *     make that first call before any stream capture.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind: calls that overlap on the GPU (different streams, or threads)
+ *     race and corrupt each other's result.  Serialise them.
+ *   - Errors: MT_EINVAL if B * n needs more scratch than
+ *     MT_NOALLOC_SCRATCH_BYTES (about 12.3 bytes per tile and simulation plus
+ *     ~80 KB fixed), for an FP64 tensor, or a NULL pointer; MT_ECUDA. */
+MT_API mt_status mt_demag_field_noalloc(mt_tensor *T, const float *m, int B, float *H, void *stream);
+
 /* Landau-Lifshitz right-hand side (Eq. 1 or its Gilbert form) at m for B
  * simulations: dmdt (DEVICE, B*3n floats) = f(m, H_eff) with
  * H_eff = H_d + H_ex + H_an + H_a.  tau (DEVICE, B floats, may be NULL)

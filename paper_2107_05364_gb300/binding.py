@@ -75,6 +75,7 @@ _SIGS = {
     "mt_demag_blocks": (_I, [_P, _I64, _P, _P]),
     "mt_demag_field": (_I, [_P, _P, _I, _P, _P]),
     "mt_demag_field_f64": (_I, [_P, _P, _I, _P, _P]),
+    "mt_demag_field_noalloc": (_I, [_P, _P, _I, _P, _P]),
     "mt_llg_rhs": (_I, [_P, ctypes.POINTER(LlgParams), _P, _I, _P, _P, _P]),
     "mt_integrator_create": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _I, _P, _PP]),
     "mt_integrator_destroy": (None, [_P]),
@@ -287,6 +288,14 @@ def mt_demag_field(T: TensorH, m, H, B: int = 1, stream=None):
 
 def mt_demag_field_f64(T: TensorH, m, H, B: int = 1, stream=None):
     _check(lib().mt_demag_field_f64(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field_f64")
+
+
+def mt_demag_field_noalloc(T: TensorH, m, H, B: int = 1, stream=None):
+    """mt_demag_field without any device allocation by the library: work
+    areas come from a fixed per-GPU array (see include/mt.h).  Calls that
+    overlap on the GPU race; the first call on a device should precede any
+    stream capture."""
+    _check(lib().mt_demag_field_noalloc(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field_noalloc")
 
 
 def mt_llg_rhs(T: TensorH, params: LlgParams, m, dmdt, tau=None, B: int = 1, stream=None):

@@ -70,6 +70,15 @@ typedef enum {
   MT_BF16_SPLIT = 3    /* hi + lo BF16 pair (4 B per entry); near blocks FP64  */
 } mt_prec;
 
+/* Storage layout of the assembled tensor. */
+typedef enum {
+  MT_LAYOUT_STREAM = 0, /* 6 unique entries per block, tile-blocked panels for  */
+                        /* the streaming product (one simulation per pass)      */
+  MT_LAYOUT_DENSE = 1   /* all 9 entries, row-major 3n x 3n BF16 (or hi + lo   */
+                        /* pair) for the batched tensor-core product; only      */
+                        /* MT_BF16_SCALED (scales fixed to 1) and MT_BF16_SPLIT */
+} mt_layout_kind;
+
 /* Equation-of-motion form. */
 typedef enum {
   MT_FORM_GILBERT = 0, /* dm/dt = -gamma/(1+a^2) [m x H + a m x (m x H)]      */
@@ -114,7 +123,9 @@ typedef struct {
 typedef struct {
   int64_t n;           /* tiles                                               */
   int32_t prec;        /* mt_prec                                             */
-  int32_t rows_per_panel, cols_per_chunk; /* tile-blocked layout              */
+  int32_t rows_per_panel, cols_per_chunk; /* tile-blocked layout (stream)     */
+  int32_t layout;      /* mt_layout_kind                                      */
+  int32_t pad;
   int64_t bytes;       /* device bytes of the stored tensor                   */
   int64_t near_blocks; /* FP64 near-field blocks kept apart (0 if none)       */
 } mt_tensor_info;
@@ -170,6 +181,15 @@ MT_API void mt_tiles_destroy(mt_tiles *tiles);
  * another tile), MT_ENOMEM (allocation failed or the context budget would
  * be exceeded), MT_EINVAL, MT_ECUDA. */
 MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out);
+/* As mt_demag_assemble, with an explicit storage layout (mt_layout_kind).
+ * MT_LAYOUT_DENSE turns every product over a batch of B simulations into a
+ * GEMM on the tensor cores (tcgen05, BF16 in, FP32 accumulate); the rows and
+ * columns of the 3n x 3n matrix are padded to a multiple of 128 (zeros) and
+ * the blocks of touching tiles are kept apart in FP64 as for the streaming
+ * layout.  Errors as mt_demag_assemble, plus MT_EINVAL for a precision the
+ * layout does not support. */
+MT_API mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_tensor **out);
+
 MT_API void mt_tensor_destroy(mt_tensor *T);
 MT_API mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info);
 

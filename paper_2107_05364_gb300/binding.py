@@ -19,6 +19,7 @@ from . import build as _build
 MT_OK, MT_EINVAL, MT_ENOMEM, MT_EOVERLAP, MT_ENOCONV, MT_ETIMEOUT, MT_ENONFINITE, MT_ECUDA, MT_EBUSY = range(9)
 MT_F64, MT_F32, MT_BF16_SCALED, MT_BF16_SPLIT = range(4)
 MT_FORM_GILBERT, MT_FORM_LL = 0, 1
+MT_LAYOUT_STREAM, MT_LAYOUT_DENSE = 0, 1
 PREC_NAMES = {"f64": MT_F64, "f32": MT_F32, "bf16": MT_BF16_SCALED, "bf16_scaled": MT_BF16_SCALED,
               "split": MT_BF16_SPLIT, "bf16_split": MT_BF16_SPLIT}
 
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
 
 class TensorInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("prec", ctypes.c_int32), ("rows_per_panel", ctypes.c_int32),
-                ("cols_per_chunk", ctypes.c_int32), ("bytes", ctypes.c_int64), ("near_blocks", ctypes.c_int64)]
+                ("cols_per_chunk", ctypes.c_int32), ("layout", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("bytes", ctypes.c_int64), ("near_blocks", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -69,6 +71,7 @@ _SIGS = {
     "mt_tiles_create": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _PP]),
     "mt_tiles_destroy": (None, [_P]),
     "mt_demag_assemble": (_I, [_P, _I, _PP]),
+    "mt_demag_assemble_ex": (_I, [_P, _I, _I, _PP]),
     "mt_tensor_destroy": (None, [_P]),
     "mt_tensor_get_info": (_I, [_P, ctypes.POINTER(TensorInfo)]),
     "mt_tensor_read_rows": (_I, [_P, _I64, _I64, _P]),
@@ -207,10 +210,11 @@ class TilesH:
 
 
 class TensorH:
-    def __init__(self, tiles: TilesH, prec):
+    def __init__(self, tiles: TilesH, prec, layout: int = MT_LAYOUT_STREAM):
         prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
         h = ctypes.c_void_p()
-        _check(lib().mt_demag_assemble(tiles.h, prec, ctypes.byref(h)), "mt_demag_assemble")
+        _check(lib().mt_demag_assemble_ex(tiles.h, prec, int(layout), ctypes.byref(h)), "mt_demag_assemble_ex")
+        self.layout = int(layout)
         self.h = h
         self.tiles = tiles
         self.n = tiles.n
@@ -266,6 +270,10 @@ def mt_tiles_create(ctx: Ctx, tiles) -> TilesH:
 
 def mt_demag_assemble(tiles: TilesH, prec="f32") -> TensorH:
     return TensorH(tiles, prec)
+
+
+def mt_demag_assemble_ex(tiles: TilesH, prec="bf16", layout: int = MT_LAYOUT_DENSE) -> TensorH:
+    return TensorH(tiles, prec, layout)
 
 
 def mt_tensor_read_rows(T: TensorH, i0: int, i1: int) -> np.ndarray:

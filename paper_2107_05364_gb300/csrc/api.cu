@@ -75,21 +75,29 @@ void free_tensor_mem(mt_tensor *T) {
 
 // workspace of the standalone field/rhs calls for B simulations
 mt_status ensure_workspace(mt_tensor *T, int B) {
+  const bool dense = T->layout == MT_LAYOUT_DENSE;
+  if (dense && T->xs_B != B) {  // the padded batch is part of the operand's layout
+    cudaFree(T->d_xs);
+    T->d_xs = nullptr;
+    T->xs_B = 0;
+    cudaFree(T->d_part);
+    T->d_part = nullptr;
+  }
   if (T->xs_B < B) {
     cudaFree(T->d_xs);
     T->d_xs = nullptr;
-    const size_t bytes = sizeof(float) * mt::xs_floats(T) * B;
+    const size_t bytes = dense ? mt::dense_x_bytes(T, B) : sizeof(float) * mt::xs_floats(T) * B;
     MT_CUDA(cudaMalloc(&T->d_xs, bytes));
     MT_CUDA(cudaMemset(T->d_xs, 0, bytes));
     T->xs_B = B;
   }
   if (!T->d_part) {
-    MT_CUDA(cudaMalloc(&T->d_part, mt::matvec_part_bytes(T)));
+    MT_CUDA(cudaMalloc(&T->d_part, dense ? mt::dense_part_bytes(T, B) : mt::matvec_part_bytes(T)));
   }
   if (T->count_B < B) {
     cudaFree(T->d_count);
     T->d_count = nullptr;
-    const size_t bytes = mt::matvec_count_bytes(T, B);
+    const size_t bytes = dense ? mt::dense_count_bytes(T) : mt::matvec_count_bytes(T, B);
     MT_CUDA(cudaMalloc(&T->d_count, bytes));
     MT_CUDA(cudaMemset(T->d_count, 0, bytes));
     T->count_B = B;
@@ -100,6 +108,23 @@ mt_status ensure_workspace(mt_tensor *T, int B) {
     MT_CUDA(cudaMalloc(&T->d_Hd, sizeof(float) * 3 * T->n * B));
     T->Hd_B = B;
   }
+  return MT_OK;
+}
+
+// H = -N (Ms m) with the tensor's own workspace: streaming product or, for
+// the dense layout, the batched tensor-core product; then the FP64 near blocks
+mt_status demag_apply(mt_tensor *T, const float *m, int B, float *H, cudaStream_t s) {
+  if (T->layout == MT_LAYOUT_DENSE) {
+    GemmPlan plan;
+    mt_status st = mt::gemm_plan(T, B, T->d_xs, &plan);
+    if (st != MT_OK) return st;
+    mt::launch_prep_dense_x(T, m, B, T->d_xs, s);
+    mt::launch_gemm(T, plan, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+  } else {
+    mt::launch_prep_xs(T, m, B, T->d_xs, s);
+    mt::launch_matvec(T, T->d_xs, B, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+  }
+  mt::launch_near(T, m, B, H, nullptr, s);
   return MT_OK;
 }
 
@@ -135,6 +160,7 @@ mt_status mt_ctx_create(int device, size_t hbm_budget_bytes, mt_ctx **out) {
   e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = mt::matvec_prepare();
+  if (e == cudaSuccess) e = mt::gemm_prepare();
   if (e != cudaSuccess) {
     cudaFree(c->d_status);
     delete c;
@@ -236,20 +262,42 @@ mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const do
 void mt_tiles_destroy(mt_tiles *tiles) { mt::tiles_release(tiles); }
 
 mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
+  return mt_demag_assemble_ex(tiles, prec, MT_LAYOUT_STREAM, out);
+}
+
+mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_tensor **out) {
   MT_CHECK(tiles && out, MT_EINVAL, "mt_demag_assemble: NULL argument");
   MT_CHECK(prec >= MT_F64 && prec <= MT_BF16_SPLIT, MT_EINVAL, "mt_demag_assemble: bad precision %d", (int)prec);
+  MT_CHECK(layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_DENSE, MT_EINVAL, "mt_demag_assemble: bad layout %d",
+           layout);
+  MT_CHECK(layout == MT_LAYOUT_STREAM || prec == MT_BF16_SCALED || prec == MT_BF16_SPLIT, MT_EINVAL,
+           "mt_demag_assemble: the dense layout stores BF16 or split BF16 only");
   mt_ctx *ctx = tiles->ctx;
   MT_CUDA(cudaSetDevice(ctx->device));
   mt_tensor *T = new mt_tensor();
   T->tiles = tiles;
   tiles->refs++;
   T->prec = prec;
+  T->layout = layout;
   T->n = tiles->n;
-  mt::layout_for(prec, &T->L);
-  T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
-  T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
-  const size_t data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
-  const size_t scale_bytes = (size_t)T->L.P * T->L.Q * T->L.scale_bytes_per_chunk;
+  size_t data_bytes = 0, scale_bytes = 0;
+  if (layout == MT_LAYOUT_DENSE) {
+    // thread mapping of the assembly kernel: 16-row panels x 128-column chunks
+    T->L.TR = 16;
+    T->L.TC = 128;
+    T->L.nplane = 9;
+    T->L.elem_bytes = 2;
+    T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
+    T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
+    T->Kp = ((3 * T->n + 127) / 128) * 128;
+    data_bytes = (size_t)T->Kp * T->Kp * 2 * (prec == MT_BF16_SPLIT ? 2 : 1);
+  } else {
+    mt::layout_for(prec, &T->L);
+    T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
+    T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
+    data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
+    scale_bytes = (size_t)T->L.P * T->L.Q * T->L.scale_bytes_per_chunk;
+  }
   T->bytes = data_bytes + scale_bytes;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -293,6 +341,8 @@ mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
   info->prec = T->prec;
   info->rows_per_panel = T->L.TR;
   info->cols_per_chunk = T->L.TC;
+  info->layout = T->layout;
+  info->pad = 0;
   info->bytes = (int64_t)T->bytes;
   info->near_blocks = T->near_count;
   return MT_OK;
@@ -317,9 +367,7 @@ mt_status mt_demag_field(mt_tensor *T, const float *m, int B, float *H, void *st
   mt_status st = ensure_workspace(T, B);
   if (st != MT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  mt::launch_prep_xs(T, m, B, T->d_xs, s);
-  mt::launch_matvec(T, T->d_xs, B, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
-  mt::launch_near(T, m, B, H, nullptr, s);
+  if ((st = demag_apply(T, m, B, H, s)) != MT_OK) return st;
   MT_CUDA(cudaGetLastError());
   return MT_OK;
 }
@@ -353,9 +401,7 @@ mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m, int B
   MT_CUDA(cudaMemcpyAsync(d_par, g1.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
   MT_CUDA(cudaMemcpyAsync(d_par + B, g2.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
   MT_CUDA(cudaMemcpyAsync(d_par + 2 * B, ha.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice, s));
-  mt::launch_prep_xs(T, m, B, T->d_xs, s);
-  mt::launch_matvec(T, T->d_xs, B, T->d_Hd, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
-  mt::launch_near(T, m, B, T->d_Hd, nullptr, s);
+  if ((st = demag_apply(T, m, B, T->d_Hd, s)) != MT_OK) return st;
   if (tau) MT_CUDA(cudaMemsetAsync(tau, 0, sizeof(float) * B, s));
   mt::launch_rhs_plain(T, m, T->d_Hd, B, d_par, d_par + B, d_par + 2 * B, dmdt, tau, s);
   MT_CUDA(cudaGetLastError());

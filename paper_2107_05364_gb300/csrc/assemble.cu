@@ -16,9 +16,9 @@ namespace {
 
 // Tensor of the cuboid (centre c, full edges e) at the point r, from the
 // Newtonian potential Phi of the box:  N = -(1/4 pi) grad grad Phi, so that
-// H = -N M.  Faces are numbered low (0) / high (1) on each axis; the sign of
-// a corner is +1 when an odd number of its faces are high faces... i.e.
-// s = -(-1)^(f_x + f_y + f_z).
+// H = -N M.  Faces are numbered low (0) / high (1) on each axis; a corner's
+// sign is s = -(-1)^(f_x + f_y + f_z): +1 when an odd number of its faces are
+// high faces.
 //   N_xx = -(1/4 pi) sum_corners s atan(dy dz / (dx R))
 //   N_xy = +(1/4 pi) sum_corners s log(dz + R)         (xz: dy, yz: dx)
 // dx == 0 (point in a face plane, outside the face): the arctan term is 0,
@@ -129,6 +129,8 @@ struct AsmArgs {
   void *data;
   int8_t *scale;
   int *bad;           // set to 1 on overlap
+  int dense;          // 1: 9-entry row-major matrix (Kp x Kp), else tile-blocked
+  int64_t Kp;
   int *near_fill;     // per-row fill counter (BF16 precisions)
   const int32_t *near_ptr;
   int32_t *near_col;
@@ -173,6 +175,23 @@ __global__ void k_assemble(AsmArgs A) {
 #pragma unroll
       for (int e = 0; e < 6; ++e) A.near_val[6 * at + e] = N6[e];
       continue;  // dense store keeps zeros there
+    }
+    if (A.dense) {
+      // all 9 entries: row 3i + a, column 3j + b (scales fixed to 1)
+      __nv_bfloat16 *D = (__nv_bfloat16 *)A.data;
+      const size_t plane = (size_t)A.Kp * A.Kp;
+      const int e_of[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const double v = N6[e_of[a][b]];
+          const size_t at = (size_t)(3 * i + a) * A.Kp + 3 * j + b;
+          const __nv_bfloat16 hi = __double2bfloat16(v);
+          D[at] = hi;
+          if (A.prec == MT_BF16_SPLIT) D[plane + at] = __double2bfloat16(v - (double)__bfloat162float(hi));
+        }
+      continue;
     }
     switch (A.prec) {
       case MT_F64: {
@@ -269,6 +288,23 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
   }
 }
 
+// dense layout -> double, rows [i0, i1)
+__global__ void k_read_rows_dense(const __nv_bfloat16 *D, int split, int64_t n, int64_t Kp, int64_t i0, int64_t i1,
+                                  double *out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t rows = i1 - i0;
+  if (t >= rows * n) return;
+  const int64_t i = i0 + t / n, j = t % n;
+  const int ra[6] = {0, 0, 0, 1, 1, 2}, cb[6] = {0, 1, 2, 1, 2, 2};
+  const size_t plane = (size_t)Kp * Kp;
+  for (int e = 0; e < 6; ++e) {
+    const size_t at = (size_t)(3 * i + ra[e]) * Kp + 3 * j + cb[e];
+    double v = (double)__bfloat162float(D[at]);
+    if (split) v += (double)__bfloat162float(D[plane + at]);
+    out[t * 6 + e] = v;
+  }
+}
+
 // merge the FP64 near blocks of rows [i0, i1) into out
 __global__ void k_merge_near(int64_t n, int64_t i0, int64_t i1, const int32_t *ptr, const int32_t *col,
                              const double *val, double *out) {
@@ -303,6 +339,8 @@ mt_status assemble(mt_tensor *T) {
   A.data = T->d_data;
   A.scale = T->d_scale;
   A.bad = d_bad;
+  A.dense = T->layout == MT_LAYOUT_DENSE;
+  A.Kp = T->Kp;
   const bool has_near = (T->prec == MT_BF16_SCALED || T->prec == MT_BF16_SPLIT);
   dim3 grid((unsigned)L.Q, (unsigned)L.P);
   if (has_near) {
@@ -369,8 +407,12 @@ mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
   double *d_out = nullptr;
   MT_CUDA(cudaMalloc(&d_out, sizeof(double) * 6 * rows * n));
   const int64_t tot = rows * n;
-  k_read_rows<<<(unsigned)((tot + 255) / 256), 256>>>(T->d_data, T->d_scale, T->prec, n, T->L.TR, T->L.TC,
-                                                       T->L.Q, i0, i1, d_out);
+  if (T->layout == MT_LAYOUT_DENSE)
+    k_read_rows_dense<<<(unsigned)((tot + 255) / 256), 256>>>((const __nv_bfloat16 *)T->d_data,
+                                                              T->prec == MT_BF16_SPLIT, n, T->Kp, i0, i1, d_out);
+  else
+    k_read_rows<<<(unsigned)((tot + 255) / 256), 256>>>(T->d_data, T->d_scale, T->prec, n, T->L.TR, T->L.TC,
+                                                         T->L.Q, i0, i1, d_out);
   MT_CUDA(cudaGetLastError());
   if (T->near_count > 0) {
     k_merge_near<<<(unsigned)((rows + 127) / 128), 128>>>(n, i0, i1, T->d_near_ptr, T->d_near_col,

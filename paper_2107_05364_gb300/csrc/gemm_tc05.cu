@@ -1,0 +1,476 @@
+// Batched demag product on the 5th-generation tensor cores (tcgen05).
+//
+// B simulations on one geometry turn the product H_d = -N (Ms m) (Eq. 9,
+// Eq. 17) into a GEMM: D[3n x B] = N[3n x 3n] X^T with X[b] = Ms m_b.  The
+// tensor is stored dense (all 9 entries of each block, row r = 3i + a,
+// column c = 3j + b) in BF16, or as a BF16 hi + lo pair ("split") that is
+// multiplied as N_hi x_hi + N_hi x_lo + N_lo x_hi; the blocks of touching
+// tiles are zero there and are applied in FP64 by the near-field kernel.
+//
+// The GEMM is HBM-bound for B <= ~300 (64 flop per tensor byte at B = 64),
+// so the design streams the tensor once per batched product:
+//   * persistent CTAs, one per SM; the (row tile, K block) units are split
+//     evenly over the CTAs in storage order (stream-K);
+//   * warp 0 issues 2-D TMA loads (128-byte swizzle) of a 128 x 64 tensor
+//     tile and the 64-wide slice of X^T into a shared-memory ring;
+//   * warp 1 issues tcgen05.mma (M = 128, N = B, K = 16, BF16 -> FP32) into
+//     one of two TMEM accumulators and releases ring slots with
+//     tcgen05.commit;
+//   * warps 2-5 drain a finished accumulator with tcgen05.ld (one TMEM lane
+//     = one row per thread) while the next row tile accumulates in the other
+//     one; rows split between two CTAs are summed by whichever warp arrives
+//     last, in CTA order.
+// Every wait is bounded; on a timeout the kernel records MT_DEV_TIMEOUT,
+// still frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "mt_internal.cuh"
+
+namespace {
+
+constexpr int GM = 128;  // rows per tile (MMA M)
+constexpr int GK = 64;   // K per ring stage: one 128-byte swizzle row of BF16
+constexpr int EPI_WARPS = 4;
+constexpr int GEMM_THREADS = 32 * (2 + EPI_WARPS);
+
+// ---- tcgen05 / TMA wrappers -------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(mtd::smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D (tmem) = A (smem) * B (smem) [+ D]; BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on `bar` once every tcgen05.mma issued so far by this thread is done
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   mtd::smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 32 bit, 16 consecutive columns per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
+                                       uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(mtd::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mtd::smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+struct GemmArgs {
+  int64_t n3;    // valid rows (3n)
+  int64_t MT;    // row tiles
+  int64_t KB;    // K blocks
+  int B, Bp;     // batch, padded batch (MMA N)
+  int chunk;     // K blocks per TMEM accumulation before the FP32 promotion
+  int stages;
+  int stage_bytes;
+  uint32_t tmem_cols;
+  float *H;      // [B][n3]
+  float *part;   // [2G][Bp][GM]
+  int *count;    // [MT][EPI_WARPS]
+  const int *n_active;
+  int *status;
+};
+
+template <bool SPLIT, int BP>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAlo,
+           const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tXlo, GemmArgs P) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  const uint32_t raw = mtd::smem_u32(smem_raw);
+  unsigned char *smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const int A_BYTES = GM * GK * 2;
+  const int X_BYTES = P.Bp * GK * 2;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)P.stages * P.stage_bytes);
+  uint64_t *empty = full + P.stages;
+  uint64_t *accf = empty + P.stages;
+  uint64_t *acce = accf + 2;
+  uint64_t *mma_done = acce + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x, k = blockIdx.x;
+  const int64_t U = P.MT * P.KB;
+  const int64_t u0 = mtd::sk_begin(k, U, G), u1 = mtd::sk_begin(k + 1, U, G);
+  const bool idle = P.n_active && *P.n_active == 0;  // every simulation finished
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P.stages; ++s) {
+      mtd::mbar_init(&full[s], 1);
+      mtd::mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mtd::mbar_init(&accf[a], 1);
+      mtd::mbar_init(&acce[a], EPI_WARPS);
+    }
+    mtd::mbar_init(mma_done, 1);
+    *abort_flag = 0;
+    mtd::fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, P.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (!idle && warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    const uint64_t pol_stream = mtd::policy_evict_first();
+    const uint64_t pol_keep = mtd::policy_evict_last();
+    int it = 0;
+    for (int64_t u = u0; u < u1; ++u, ++it) {
+      const int64_t mt = u / P.KB, kb = u - mt * P.KB;
+      const int s = it % P.stages;
+      const uint32_t ph = (uint32_t)(it / P.stages) & 1u;
+      if (it >= P.stages && (*abort_flag || !mtd::mbar_wait_bounded(&empty[s], ph ^ 1u, P.status))) {
+        *abort_flag = 1;
+        break;
+      }
+      unsigned char *st = smem + (size_t)s * P.stage_bytes;
+      mtd::mbar_arrive_expect_tx(&full[s], (uint32_t)(SPLIT ? 2 * (A_BYTES + X_BYTES) : (A_BYTES + X_BYTES)));
+      tma_2d(st, &tA, (int)(kb * GK), (int)(mt * GM), &full[s], pol_stream);
+      tma_2d(st + A_BYTES, &tX, (int)(kb * GK), 0, &full[s], pol_keep);
+      if (SPLIT) {
+        tma_2d(st + A_BYTES + X_BYTES, &tAlo, (int)(kb * GK), (int)(mt * GM), &full[s], pol_stream);
+        tma_2d(st + 2 * A_BYTES + X_BYTES, &tXlo, (int)(kb * GK), 0, &full[s], pol_keep);
+      }
+    }
+    // drain: every copy issued must have landed before the CTA may exit
+    for (int s = 0; s < P.stages && s < it; ++s) {
+      const int last = it - 1 - ((it - 1 - s) % P.stages);  // last issue on stage s
+      mtd::mbar_wait_bounded(&full[s], (uint32_t)(last / P.stages) & 1u, P.status);
+    }
+  } else if (!idle && warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = (1u << 4)                       // D: FP32
+                           | (1u << 7) | (1u << 10)        // A, B: BF16
+                           | ((uint32_t)(P.Bp >> 3) << 17)  // N
+                           | ((uint32_t)(GM >> 4) << 24);   // M
+    // The tensor cores' FP32 accumulation rounds with a bias, so a product
+    // is accumulated in TMEM over at most P.chunk K blocks and then handed to
+    // the epilogue, which adds the chunks in FP32 (round to nearest).
+    int it = 0, chunk = 0;
+    bool issued = false;
+    int64_t u = u0;
+    while (u < u1 && !*abort_flag) {
+      const int64_t mt = u / P.KB;
+      const int64_t seg_end = u1 < (mt + 1) * P.KB ? u1 : (mt + 1) * P.KB;
+      while (u < seg_end && !*abort_flag) {
+        const int64_t c_end = seg_end < u + P.chunk ? seg_end : u + P.chunk;
+        const int a = chunk & 1;
+        if (chunk >= 2 && !mtd::mbar_wait_bounded(&acce[a], (uint32_t)((chunk >> 1) - 1) & 1u, P.status)) {
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(a * BP);
+        bool first = true;
+        for (; u < c_end; ++u, ++it) {
+          const int s = it % P.stages;
+          const uint32_t ph = (uint32_t)(it / P.stages) & 1u;
+          if (*abort_flag || !mtd::mbar_wait_bounded(&full[s], ph, P.status)) {
+            *abort_flag = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = mtd::smem_u32(smem + (size_t)s * P.stage_bytes);
+          const uint32_t sx = sa + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < GK / 16; ++kk) {
+            // K advance inside the 128-byte swizzle row: 16 BF16 = 32 bytes
+            const uint64_t da = sw128_desc(sa + 32 * kk), dx = sw128_desc(sx + 32 * kk);
+            umma_bf16(d_tmem, da, dx, idesc, first ? 0u : 1u);
+            first = false;
+            if (SPLIT) {
+              const uint32_t salo = sx + X_BYTES, sxlo = salo + A_BYTES;
+              umma_bf16(d_tmem, da, sw128_desc(sxlo + 32 * kk), idesc, 1u);  // N_hi x_lo
+              umma_bf16(d_tmem, sw128_desc(salo + 32 * kk), dx, idesc, 1u);  // N_lo x_hi
+            }
+          }
+          issued = true;
+          umma_commit(&empty[s]);  // ring slot free once these MMAs are done
+        }
+        umma_commit(&accf[a]);  // accumulator a holds the chunk
+        ++chunk;
+      }
+    }
+    if (issued) umma_commit(mma_done);
+    else mtd::mbar_arrive(mma_done);
+  } else if (!idle && warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int g = warp & 3;  // TMEM lane group accessible to this warp
+    const int row = g * 32 + lane;
+    const int64_t first_mt = u0 / P.KB;
+    int chunk = 0;
+    int64_t u = u0;
+    float run[BP];  // FP32 sum of the chunks of the current row tile
+    while (u < u1) {
+      const int64_t mt = u / P.KB;
+      const int64_t seg_end = u1 < (mt + 1) * P.KB ? u1 : (mt + 1) * P.KB;
+      bool ok = true;
+      bool first_chunk = true;
+      while (u < seg_end) {
+        u = seg_end < u + P.chunk ? seg_end : u + P.chunk;
+        const int a = chunk & 1;
+        const bool got = !*abort_flag && mtd::mbar_wait_bounded(&accf[a], (uint32_t)(chunk >> 1) & 1u, P.status);
+        if (!got) {
+          *abort_flag = 1;
+          ok = false;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int c0 = 0; c0 < BP; c0 += 16) {
+          float v[16];
+          tmem_ld16(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(a * BP + c0), v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) run[c0 + j] = first_chunk ? v[j] : run[c0 + j] + v[j];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mtd::mbar_arrive(&acce[a]);
+        first_chunk = false;
+        ++chunk;
+      }
+      if (!ok) continue;
+      const int64_t kf = mtd::sk_owner(mt * P.KB, U, G), kl = mtd::sk_owner(mt * P.KB + P.KB - 1, U, G);
+      const int64_t r = mt * GM + row;
+      if (kf == kl) {
+#pragma unroll
+        for (int b = 0; b < BP; ++b)
+          if (b < P.B && r < P.n3) P.H[(size_t)b * P.n3 + r] = -run[b];
+        continue;
+      }
+      const int64_t slot = (mt == first_mt) ? 2 * k : 2 * k + 1;
+#pragma unroll
+      for (int b = 0; b < BP; ++b) P.part[((size_t)slot * BP + b) * GM + row] = run[b];
+      __threadfence();
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) {
+        const int old = atomicAdd(&P.count[mt * EPI_WARPS + g], 1);
+        last = (old == (int)(kl - kf));
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (last) {
+        __threadfence();
+        for (int b = 0; b < P.B; ++b) {
+          float tot = 0.0f;
+          for (int64_t kk = kf; kk <= kl; ++kk) {
+            const int64_t fm = mtd::sk_begin(kk, U, G) / P.KB;
+            const int64_t sl = (mt == fm) ? 2 * kk : 2 * kk + 1;
+            tot += __ldcg(&P.part[((size_t)sl * BP + b) * GM + row]);
+          }
+          if (r < P.n3) P.H[(size_t)b * P.n3 + r] = -tot;
+        }
+        if (lane == 0) P.count[mt * EPI_WARPS + g] = 0;
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    if (!idle) mtd::mbar_wait_bounded(mma_done, 0u, P.status);
+    tc_fence_after();
+    tmem_dealloc(tmem_base, P.tmem_cols);
+  }
+}
+
+// X[b][c] = BF16(Ms_j m_j[a]) for c = 3j + a (zero for padding), and the
+// low part X_lo = BF16(x - X_hi) for the split product
+__global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64_t Kp, int B,
+                               __nv_bfloat16 *X, __nv_bfloat16 *Xlo) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (t >= Kp) return;
+  float x = 0.0f;
+  if (t < 3 * n) x = Ms[t / 3] * m[(size_t)b * 3 * n + t];
+  const __nv_bfloat16 hi = __float2bfloat16(x);
+  X[(size_t)b * Kp + t] = hi;
+  if (Xlo) Xlo[(size_t)b * Kp + t] = __float2bfloat16(x - __bfloat162float(hi));
+}
+
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  }
+  return fn;
+}
+
+// 2-D BF16 map over a row-major [rows][cols] array, box (64 cols, box_rows)
+mt_status make_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t rows, uint32_t box_rows) {
+  EncodeFn fn = encode_fn();
+  MT_CHECK(fn, MT_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)GK, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  MT_CHECK(r == CUDA_SUCCESS, MT_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return MT_OK;
+}
+
+int stages_for(int Bp, bool split) {
+  const int stage = (GM * GK * 2 + Bp * GK * 2) * (split ? 2 : 1);
+  const int budget = 200 * 1024;
+  return std::max(2, std::min(8, budget / stage));
+}
+
+}  // namespace
+
+namespace mt {
+
+// MMA N of a batch: 16, 32, 64 or 128 (one kernel instance each)
+int dense_pad_batch(int B) {
+  int bp = 16;
+  while (bp < B && bp < 128) bp *= 2;
+  return bp;
+}
+
+size_t dense_x_bytes(const mt_tensor *T, int B) {
+  return (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 2 : 1);
+}
+size_t dense_part_bytes(const mt_tensor *T, int B) {
+  return (size_t)2 * matvec_grid(T) * dense_pad_batch(B) * GM * sizeof(float);
+}
+size_t dense_count_bytes(const mt_tensor *T) { return (size_t)(T->Kp / GM) * EPI_WARPS * sizeof(int); }
+
+template <bool SPLIT, int BP>
+cudaError_t prep_one() {
+  return cudaFuncSetAttribute(k_gemm<SPLIT, BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+cudaError_t gemm_prepare() {
+  cudaError_t e;
+  if ((e = prep_one<false, 16>()) != cudaSuccess || (e = prep_one<false, 32>()) != cudaSuccess ||
+      (e = prep_one<false, 64>()) != cudaSuccess || (e = prep_one<false, 128>()) != cudaSuccess ||
+      (e = prep_one<true, 16>()) != cudaSuccess || (e = prep_one<true, 32>()) != cudaSuccess ||
+      (e = prep_one<true, 64>()) != cudaSuccess || (e = prep_one<true, 128>()) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cudaStream_t s) {
+  const int Bp = dense_pad_batch(B);
+  __nv_bfloat16 *x = reinterpret_cast<__nv_bfloat16 *>(X);
+  __nv_bfloat16 *xlo = T->prec == MT_BF16_SPLIT ? x + (size_t)Bp * T->Kp : nullptr;
+  dim3 grid((unsigned)((T->Kp + 255) / 256), (unsigned)B);
+  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, x, xlo);
+}
+
+mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
+  const int Bp = dense_pad_batch(B);
+  MT_CHECK(B >= 1 && B <= 128, MT_EINVAL, "batched product: B = %d outside 1..128 simulations per pass", B);
+  const bool split = T->prec == MT_BF16_SPLIT;
+  const __nv_bfloat16 *A = reinterpret_cast<const __nv_bfloat16 *>(T->d_data);
+  const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(X);
+  mt_status st;
+  if ((st = make_map(&plan->tA, A, T->Kp, T->Kp, GM)) != MT_OK) return st;
+  if ((st = make_map(&plan->tX, x, T->Kp, Bp, Bp)) != MT_OK) return st;
+  if (split) {
+    if ((st = make_map(&plan->tAlo, A + (size_t)T->Kp * T->Kp, T->Kp, T->Kp, GM)) != MT_OK) return st;
+    if ((st = make_map(&plan->tXlo, x + (size_t)Bp * T->Kp, T->Kp, Bp, Bp)) != MT_OK) return st;
+  } else {
+    plan->tAlo = plan->tA;
+    plan->tXlo = plan->tX;
+  }
+  plan->B = B;
+  plan->Bp = Bp;
+  plan->split = split;
+  plan->stages = stages_for(Bp, split);
+  plan->chunk = 4;
+  return MT_OK;
+}
+
+void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part, int *count, const int *n_active,
+                 int *status, cudaStream_t s) {
+  GemmArgs P;
+  P.n3 = 3 * T->n;
+  P.MT = T->Kp / GM;
+  P.KB = T->Kp / GK;
+  P.B = plan.B;
+  P.Bp = plan.Bp;
+  P.chunk = plan.chunk;
+  P.stages = plan.stages;
+  P.stage_bytes = (GM * GK * 2 + plan.Bp * GK * 2) * (plan.split ? 2 : 1);
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * plan.Bp)) cols <<= 1;
+  P.tmem_cols = cols;
+  P.H = H;
+  P.part = part;
+  P.count = count;
+  P.n_active = n_active;
+  P.status = status;
+  const int64_t U = P.MT * P.KB;
+  const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
+  const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
+#define MT_GEMM_LAUNCH(SP, BPV) \
+  k_gemm<SP, BPV><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tXlo, P)
+  if (plan.split) {
+    switch (plan.Bp) {
+      case 16: MT_GEMM_LAUNCH(true, 16); break;
+      case 32: MT_GEMM_LAUNCH(true, 32); break;
+      case 64: MT_GEMM_LAUNCH(true, 64); break;
+      default: MT_GEMM_LAUNCH(true, 128); break;
+    }
+  } else {
+    switch (plan.Bp) {
+      case 16: MT_GEMM_LAUNCH(false, 16); break;
+      case 32: MT_GEMM_LAUNCH(false, 32); break;
+      case 64: MT_GEMM_LAUNCH(false, 64); break;
+      default: MT_GEMM_LAUNCH(false, 128); break;
+    }
+  }
+#undef MT_GEMM_LAUNCH
+}
+
+}  // namespace mt

@@ -75,6 +75,12 @@ struct StageArgs {
   float *k[7];
   int64_t Q;
   int TC;
+  // operand of the batched tensor-core product (dense layout): X[b][Kp] BF16
+  // (+ low part for the split precision); xs_mode 0 = streaming layout
+  int xs_mode;  // 0 streaming FP32 chunks, 1 dense BF16, 2 dense split BF16
+  int64_t Kp;
+  int Bp;
+  __nv_bfloat16 *X;
   // control
   SimCtl *ctl;
   int *active;
@@ -145,11 +151,23 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
   d[1] = v[1];
   d[2] = v[2];
   const float ms = A.Ms[i];
-  const int64_t q = i / A.TC, t = i - q * A.TC;
-  float *x = A.xs + ((size_t)(b * A.Q + q) * 3) * A.TC + t;
-  x[0] = ms * v[0];
-  x[A.TC] = ms * v[1];
-  x[2 * A.TC] = ms * v[2];
+  if (A.xs_mode == 0) {
+    const int64_t q = i / A.TC, t = i - q * A.TC;
+    float *x = A.xs + ((size_t)(b * A.Q + q) * 3) * A.TC + t;
+    x[0] = ms * v[0];
+    x[A.TC] = ms * v[1];
+    x[2 * A.TC] = ms * v[2];
+  } else {
+    __nv_bfloat16 *x = A.X + (size_t)b * A.Kp + 3 * i;
+    __nv_bfloat16 *xl = A.X + (size_t)(A.Bp + b) * A.Kp + 3 * i;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float f = ms * v[c];
+      const __nv_bfloat16 hi = __float2bfloat16(f);
+      x[c] = hi;
+      if (A.xs_mode == 2) xl[c] = __float2bfloat16(f - __bfloat162float(hi));
+    }
+  }
 }
 
 // Block-reduce NV doubles (sum for all but index `max_idx`, which is a max)
@@ -509,6 +527,7 @@ struct mt_integrator {
   int *h_poll = nullptr;  // pinned, 2 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaGraphExec_t exec = nullptr;
+  GemmPlan plan;  // dense layout: tensor maps of the batched product
   int nblk = 0;
   bool need_init = true;
   std::vector<void *> allocs;
@@ -540,6 +559,10 @@ StageArgs stage_args(mt_integrator *I) {
   for (int s = 0; s < 7; ++s) A.k[s] = I->k[s];
   A.Q = T->L.Q;
   A.TC = T->L.TC;
+  A.xs_mode = T->layout == MT_LAYOUT_DENSE ? (T->prec == MT_BF16_SPLIT ? 2 : 1) : 0;
+  A.Kp = T->Kp;
+  A.Bp = mt::dense_pad_batch(I->B);
+  A.X = reinterpret_cast<__nv_bfloat16 *>(I->xs);
   A.ctl = I->ctl;
   A.active = I->active;
   A.n_active = I->n_active;
@@ -561,8 +584,11 @@ void launch_stage(mt_integrator *I, const StageArgs &A) {
 
 // demag product of the stage input `m` into I->Hd (xs already formed)
 void demag(mt_integrator *I, const float *m) {
-  mt::launch_matvec(I->T, I->xs, I->B, I->Hd, I->part, I->count, I->active, I->T->tiles->ctx->d_status,
-                    I->stream);
+  if (I->T->layout == MT_LAYOUT_DENSE)
+    mt::launch_gemm(I->T, I->plan, I->Hd, I->part, I->count, I->n_active, I->T->tiles->ctx->d_status, I->stream);
+  else
+    mt::launch_matvec(I->T, I->xs, I->B, I->Hd, I->part, I->count, I->active, I->T->tiles->ctx->d_status,
+                      I->stream);
   mt::launch_near(I->T, m, I->B, I->Hd, I->active, I->stream);
 }
 
@@ -586,7 +612,10 @@ void enqueue_attempt(mt_integrator *I) {
 
 mt_status enqueue_init(mt_integrator *I) {
   StageArgs A = stage_args(I);
-  mt::launch_prep_xs(I->T, I->y, I->B, I->xs, I->stream);
+  if (I->T->layout == MT_LAYOUT_DENSE)
+    mt::launch_prep_dense_x(I->T, I->y, I->B, I->xs, I->stream);
+  else
+    mt::launch_prep_xs(I->T, I->y, I->B, I->xs, I->stream);
   demag(I, I->y);
   launch_stage<1>(I, A);
   MT_CUDA(cudaGetLastError());
@@ -738,12 +767,18 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
   MT_TRY(dalloc(I, &I->ys1, vec));
   MT_TRY(dalloc(I, &I->Hd, vec));
   for (int s = 0; s < 7; ++s) MT_TRY(dalloc(I, &I->k[s], vec));
-  MT_TRY(dalloc(I, &I->xs, sizeof(float) * mt::xs_floats(T) * B));
+  const bool dense = T->layout == MT_LAYOUT_DENSE;
+  if (dense) {
+    MT_TRY(dalloc(I, (unsigned char **)&I->xs, mt::dense_x_bytes(T, B)));
+    MT_TRY(mt::gemm_plan(T, B, I->xs, &I->plan));
+  } else {
+    MT_TRY(dalloc(I, &I->xs, sizeof(float) * mt::xs_floats(T) * B));
+  }
   MT_TRY(dalloc(I, &I->g1, sizeof(float) * B));
   MT_TRY(dalloc(I, &I->g2, sizeof(float) * B));
   MT_TRY(dalloc(I, &I->Ha, sizeof(float) * 3 * B));
-  MT_TRY(dalloc(I, &I->part, mt::matvec_part_bytes(T)));
-  MT_TRY(dalloc(I, &I->count, mt::matvec_count_bytes(T, B)));
+  MT_TRY(dalloc(I, &I->part, dense ? mt::dense_part_bytes(T, B) : mt::matvec_part_bytes(T)));
+  MT_TRY(dalloc(I, &I->count, dense ? mt::dense_count_bytes(T) : mt::matvec_count_bytes(T, B)));
   MT_TRY(dalloc(I, &I->ctl, sizeof(SimCtl) * B));
   MT_TRY(dalloc(I, &I->active, sizeof(int) * B));
   MT_TRY(dalloc(I, &I->n_active, sizeof(int)));

@@ -3,8 +3,9 @@
 // Nothing here is part of the ABI; include/mt.h is.
 #pragma once
 
-#include <cuda_runtime.h>
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -100,7 +101,9 @@ struct mt_tensor {
   std::atomic<int> refs{1};
   mt_tiles *tiles = nullptr;
   int prec = MT_F32;
+  int layout = MT_LAYOUT_STREAM;  // MT_LAYOUT_DENSE: 9-entry BF16 matrix for tensor cores
   int64_t n = 0;
+  int64_t Kp = 0;                 // dense layout: rows = columns = 3n padded to 128
   mt_layout L;
   void *d_data = nullptr;
   size_t bytes = 0;
@@ -118,6 +121,14 @@ struct mt_tensor {
   int count_B = 0;
   float *d_Hd = nullptr;
   int Hd_B = 0;
+};
+
+// Tensor maps and shape of one batched tensor-core product (dense layout).
+struct GemmPlan {
+  CUtensorMap tA, tAlo, tX, tXlo;
+  int B = 0, Bp = 0, stages = 0;
+  int chunk = 4;  // K blocks accumulated in TMEM before the FP32 promotion
+  bool split = false;
 };
 
 // ---------------------------------------------------------------------------
@@ -145,6 +156,17 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
                    const int *active, int *status, cudaStream_t s);
 // H[b] -= near-field FP64 blocks applied to Ms m (only for BF16 precisions)
 void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s);
+
+// batched product on tcgen05 (dense layout)
+cudaError_t gemm_prepare();
+int dense_pad_batch(int B);
+size_t dense_x_bytes(const mt_tensor *T, int B);
+size_t dense_part_bytes(const mt_tensor *T, int B);
+size_t dense_count_bytes(const mt_tensor *T);
+void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cudaStream_t s);
+mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan);
+void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part, int *count, const int *n_active,
+                 int *status, cudaStream_t s);
 
 // reference counting of handles (see the handle structs)
 void ctx_release(mt_ctx *c);

@@ -5,7 +5,7 @@ Tolerances (relative L2 over all compared values):
   FP64 tensor / FP64 field ............ 1e-12
   FP32 storage, FP32 field ............ 1e-6
   BF16 storage (+ FP64 near blocks) ... 5e-3
-  split BF16 hi+lo (+ FP64 near) ...... 1e-5 (per-entry error 2^-17)
+  split BF16 hi+lo (+ FP64 near) ...... 1e-6
 """
 import numpy as np
 import pytest
@@ -90,7 +90,7 @@ def test_bad_tiles_are_rejected(mt, ctx):
         mt.mt_tiles_create(ctx, t)
 
 
-TOL = {"f32": 1e-6, "bf16": 5e-3, "split": 1e-5}
+TOL = {"f32": 1e-6, "bf16": 5e-3, "split": 1e-6}
 
 
 def _field_case(mt, ctx, t, prec, B, seed):

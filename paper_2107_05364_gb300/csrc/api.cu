@@ -67,6 +67,7 @@ void free_tensor_mem(mt_tensor *T) {
   cudaFree(T->d_near_ptr);
   cudaFree(T->d_near_col);
   cudaFree(T->d_near_val);
+  cudaFree(T->d_near_hl);
   cudaFree(T->d_xs);
   cudaFree(T->d_part);
   cudaFree(T->d_count);

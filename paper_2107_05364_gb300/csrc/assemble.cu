@@ -186,7 +186,7 @@ __global__ void k_assemble(AsmArgs A) {
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
           const double v = N6[e_of[a][b]];
-          const size_t at = (size_t)(3 * i + a) * A.Kp + 3 * j + b;
+          const size_t at = dense_a_index(3 * i + a, 3 * j + b, A.Kp / 64);
           const __nv_bfloat16 hi = __double2bfloat16(v);
           D[at] = hi;
           if (A.prec == MT_BF16_SPLIT) D[plane + at] = __double2bfloat16(v - (double)__bfloat162float(hi));
@@ -255,6 +255,15 @@ __global__ void k_sort_near(int64_t n, const int32_t *ptr, int32_t *col, double 
   }
 }
 
+// near blocks as FP32 hi + lo pairs (v = hi + lo to ~2^-48 relative)
+__global__ void k_near_split(int64_t count6, const double *val, float2 *hl) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count6) return;
+  const double v = val[t];
+  const float hi = (float)v;
+  hl[t] = make_float2(hi, (float)(v - (double)hi));
+}
+
 __global__ void k_blocks(const double *centre, const double *edge, int64_t count, const int64_t *pairs,
                          double *out) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -298,7 +307,7 @@ __global__ void k_read_rows_dense(const __nv_bfloat16 *D, int split, int64_t n, 
   const int ra[6] = {0, 0, 0, 1, 1, 2}, cb[6] = {0, 1, 2, 1, 2, 2};
   const size_t plane = (size_t)Kp * Kp;
   for (int e = 0; e < 6; ++e) {
-    const size_t at = (size_t)(3 * i + ra[e]) * Kp + 3 * j + cb[e];
+    const size_t at = dense_a_index(3 * i + ra[e], 3 * j + cb[e], Kp / 64);
     double v = (double)__bfloat162float(D[at]);
     if (split) v += (double)__bfloat162float(D[plane + at]);
     out[t * 6 + e] = v;
@@ -369,6 +378,13 @@ mt_status assemble(mt_tensor *T) {
     MT_CUDA(cudaGetLastError());
     k_sort_near<<<(unsigned)((n + 127) / 128), 128>>>(n, T->d_near_ptr, T->d_near_col, T->d_near_val);
     MT_CUDA(cudaGetLastError());
+    const int64_t c6 = 6 * std::max<int64_t>(1, T->near_count);
+    MT_CUDA(cudaMalloc(&T->d_near_hl, sizeof(float2) * c6));
+    if (T->near_count > 0) {
+      k_near_split<<<(unsigned)((6 * T->near_count + 255) / 256), 256>>>(6 * T->near_count, T->d_near_val,
+                                                                        T->d_near_hl);
+      MT_CUDA(cudaGetLastError());
+    }
     MT_CUDA(cudaDeviceSynchronize());
     cudaFree(d_fill);
   } else {

@@ -169,11 +169,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       }
       unsigned char *st = smem + (size_t)s * P.stage_bytes;
       mtd::mbar_arrive_expect_tx(&full[s], (uint32_t)(SPLIT ? 2 * (A_BYTES + X_BYTES) : (A_BYTES + X_BYTES)));
-      tma_2d(st, &tA, (int)(kb * GK), (int)(mt * GM), &full[s], pol_stream);
-      tma_2d(st + A_BYTES, &tX, (int)(kb * GK), 0, &full[s], pol_keep);
+      // tile (mt, kb) is one contiguous 16 KB block; X block kb likewise
+      const int ya = (int)((mt * P.KB + kb) * GM), yx = (int)(kb * P.Bp);
+      tma_2d(st, &tA, 0, ya, &full[s], pol_stream);
+      tma_2d(st + A_BYTES, &tX, 0, yx, &full[s], pol_keep);
       if (SPLIT) {
-        tma_2d(st + A_BYTES + X_BYTES, &tAlo, (int)(kb * GK), (int)(mt * GM), &full[s], pol_stream);
-        tma_2d(st + 2 * A_BYTES + X_BYTES, &tXlo, (int)(kb * GK), 0, &full[s], pol_keep);
+        tma_2d(st + A_BYTES + X_BYTES, &tAlo, 0, ya, &full[s], pol_stream);
+        tma_2d(st + 2 * A_BYTES + X_BYTES, &tXlo, 0, yx, &full[s], pol_keep);
       }
     }
     // drain: every copy issued must have landed before the CTA may exit
@@ -317,7 +319,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
 // X[b][c] = BF16(Ms_j m_j[a]) for c = 3j + a (zero for padding), and the
 // low part X_lo = BF16(x - X_hi) for the split product
-__global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64_t Kp, int B,
+__global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64_t Kp, int B, int Bp,
                                __nv_bfloat16 *X, __nv_bfloat16 *Xlo) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
@@ -325,8 +327,9 @@ __global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64
   float x = 0.0f;
   if (t < 3 * n) x = Ms[t / 3] * m[(size_t)b * 3 * n + t];
   const __nv_bfloat16 hi = __float2bfloat16(x);
-  X[(size_t)b * Kp + t] = hi;
-  if (Xlo) Xlo[(size_t)b * Kp + t] = __float2bfloat16(x - __bfloat162float(hi));
+  const size_t at = dense_x_index(b, t, Bp);
+  X[at] = hi;
+  if (Xlo) Xlo[at] = __float2bfloat16(x - __bfloat162float(hi));
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -404,7 +407,7 @@ void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cud
   __nv_bfloat16 *x = reinterpret_cast<__nv_bfloat16 *>(X);
   __nv_bfloat16 *xlo = T->prec == MT_BF16_SPLIT ? x + (size_t)Bp * T->Kp : nullptr;
   dim3 grid((unsigned)((T->Kp + 255) / 256), (unsigned)B);
-  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, x, xlo);
+  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, Bp, x, xlo);
 }
 
 mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
@@ -414,11 +417,13 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   const __nv_bfloat16 *A = reinterpret_cast<const __nv_bfloat16 *>(T->d_data);
   const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(X);
   mt_status st;
-  if ((st = make_map(&plan->tA, A, T->Kp, T->Kp, GM)) != MT_OK) return st;
-  if ((st = make_map(&plan->tX, x, T->Kp, Bp, Bp)) != MT_OK) return st;
+  // blocked storage seen as a [tiles * 128][64] array (A) and [KB * Bp][64] (X)
+  const uint64_t a_rows = (uint64_t)T->Kp * T->Kp / GK, x_rows = (uint64_t)(T->Kp / GK) * Bp;
+  if ((st = make_map(&plan->tA, A, GK, a_rows, GM)) != MT_OK) return st;
+  if ((st = make_map(&plan->tX, x, GK, x_rows, Bp)) != MT_OK) return st;
   if (split) {
-    if ((st = make_map(&plan->tAlo, A + (size_t)T->Kp * T->Kp, T->Kp, T->Kp, GM)) != MT_OK) return st;
-    if ((st = make_map(&plan->tXlo, x + (size_t)Bp * T->Kp, T->Kp, Bp, Bp)) != MT_OK) return st;
+    if ((st = make_map(&plan->tAlo, A + (size_t)T->Kp * T->Kp, GK, a_rows, GM)) != MT_OK) return st;
+    if ((st = make_map(&plan->tXlo, x + (size_t)Bp * T->Kp, GK, x_rows, Bp)) != MT_OK) return st;
   } else {
     plan->tAlo = plan->tA;
     plan->tXlo = plan->tX;

@@ -158,14 +158,14 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
     x[A.TC] = ms * v[1];
     x[2 * A.TC] = ms * v[2];
   } else {
-    __nv_bfloat16 *x = A.X + (size_t)b * A.Kp + 3 * i;
-    __nv_bfloat16 *xl = A.X + (size_t)(A.Bp + b) * A.Kp + 3 * i;
+    __nv_bfloat16 *xl = A.X + (size_t)A.Bp * A.Kp;  // low plane (split)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float f = ms * v[c];
       const __nv_bfloat16 hi = __float2bfloat16(f);
-      x[c] = hi;
-      if (A.xs_mode == 2) xl[c] = __float2bfloat16(f - __bfloat162float(hi));
+      const size_t at = dense_x_index(b, 3 * i + c, A.Bp);
+      A.X[at] = hi;
+      if (A.xs_mode == 2) xl[at] = __float2bfloat16(f - __bfloat162float(hi));
     }
   }
 }

@@ -348,27 +348,68 @@ __global__ void k_prep_xs(const In *m, const float *Ms, int64_t n, int64_t Q, in
   }
 }
 
-// Near-field blocks in FP64 (BF16 precisions): H_i -= sum_near N_ij Ms_j m_j.
-__global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const double *val,
+// Near-field blocks (BF16 precisions): H_i -= sum_near N_ij Ms_j m_j with
+// FP64-class accuracy on the FP32 pipes.  The blocks were assembled in FP64
+// and are held as FP32 hi + lo pairs; products use the exact FMA product
+// split (p = a b, e = fma(a, b, -p)) and the sum is carried as an unevaluated
+// pair (hi + lo) with Knuth's two-sum, then added to the far field and
+// rounded once.  (GB300 executes FP64 at a small fraction of its FP32 rate;
+// this keeps ~2^-44 relative accuracy at FP32 speed.)
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_add(ff acc, float p, float e) {
+  ff s = ff_two_sum(acc.hi, p);
+  s.lo += acc.lo + e;
+  const float hi = s.hi + s.lo;
+  return {hi, s.lo - (hi - s.hi)};
+}
+// acc += (v.hi + v.lo) * (x.hi + x.lo)
+__device__ __forceinline__ ff ff_fma(ff acc, float2 v, ff x) {
+  const float p = v.x * x.hi;
+  const float e = fmaf(v.x, x.hi, -p) + (v.x * x.lo + v.y * x.hi);
+  return ff_add(acc, p, e);
+}
+
+// threads enumerate (tile, simulation) pairs with the simulation fastest, so
+// a warp of a wide batch shares its tile's blocks (broadcast loads)
+__global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const float2 *val,
                        const float *Ms, const float *m, float *H, const int *active) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int b = blockIdx.y;
-  if (i >= n || (active && !active[b])) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * B) return;
+  const int64_t i = t / B;
+  const int b = (int)(t - i * B);
+  if (active && !active[b]) return;
   const float *mb = m + (size_t)b * 3 * n;
-  double hx = 0, hy = 0, hz = 0;
+  ff hx = {0, 0}, hy = {0, 0}, hz = {0, 0};
   for (int32_t a = ptr[i]; a < ptr[i + 1]; ++a) {
     const int64_t j = col[a];
-    const double ms = Ms[j];
-    const double x = ms * mb[3 * j], y = ms * mb[3 * j + 1], z = ms * mb[3 * j + 2];
-    const double *v = val + 6 * (size_t)a;
-    hx += v[0] * x + v[1] * y + v[2] * z;
-    hy += v[1] * x + v[3] * y + v[4] * z;
-    hz += v[2] * x + v[4] * y + v[5] * z;
+    const float ms = Ms[j];
+    ff x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float mc = mb[3 * j + c];
+      x[c].hi = ms * mc;
+      x[c].lo = fmaf(ms, mc, -x[c].hi);
+    }
+    const float2 *v = val + 6 * (size_t)a;
+    hx = ff_fma(ff_fma(ff_fma(hx, v[0], x[0]), v[1], x[1]), v[2], x[2]);
+    hy = ff_fma(ff_fma(ff_fma(hy, v[1], x[0]), v[3], x[1]), v[4], x[2]);
+    hz = ff_fma(ff_fma(ff_fma(hz, v[2], x[0]), v[4], x[1]), v[5], x[2]);
   }
   float *Hb = H + (size_t)b * 3 * n + 3 * i;
-  Hb[0] = (float)((double)Hb[0] - hx);
-  Hb[1] = (float)((double)Hb[1] - hy);
-  Hb[2] = (float)((double)Hb[2] - hz);
+  // H = far - near, rounded once
+  const ff rx = ff_add({Hb[0], 0.0f}, -hx.hi, -hx.lo);
+  const ff ry = ff_add({Hb[1], 0.0f}, -hy.hi, -hy.lo);
+  const ff rz = ff_add({Hb[2], 0.0f}, -hz.hi, -hz.lo);
+  Hb[0] = rx.hi + rx.lo;
+  Hb[1] = ry.hi + ry.lo;
+  Hb[2] = rz.hi + rz.lo;
 }
 
 template <int PREC>
@@ -467,8 +508,9 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
 
 void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s) {
   if (T->near_count == 0) return;
-  dim3 grid((unsigned)((T->n + 127) / 128), (unsigned)B);
-  k_near<<<grid, 128, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_val, T->tiles->d_Ms, m, H, active);
+  const int64_t tot = T->n * (int64_t)B;
+  k_near<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl,
+                                                       T->tiles->d_Ms, m, H, active);
 }
 
 }  // namespace mt

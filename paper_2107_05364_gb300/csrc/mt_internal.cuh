@@ -112,7 +112,8 @@ struct mt_tensor {
   int64_t near_count = 0;
   int32_t *d_near_ptr = nullptr;  // n+1
   int32_t *d_near_col = nullptr;  // near_count
-  double *d_near_val = nullptr;   // near_count * 6
+  double *d_near_val = nullptr;   // near_count * 6 (FP64, as assembled)
+  float2 *d_near_hl = nullptr;    // near_count * 6: the same values as FP32 hi + lo pairs
   // workspace of the standalone field / rhs calls
   float *d_xs = nullptr;
   int xs_B = 0;
@@ -122,6 +123,18 @@ struct mt_tensor {
   float *d_Hd = nullptr;
   int Hd_B = 0;
 };
+
+// Dense layout, tile-blocked: the 3n x 3n matrix (padded to Kp = 128 k) is
+// cut into 128-row x 64-column BF16 tiles, each stored contiguously (16 KB,
+// rows of 128 bytes), tiles ordered by (row tile, K block); the low part of
+// the split precision is a second such plane.  The operand X of a batch is
+// cut the same way along K: block kb holds Bp rows of 64 values.
+__host__ __device__ __forceinline__ size_t dense_a_index(int64_t r, int64_t c, int64_t KB) {
+  return ((size_t)((r >> 7) * KB + (c >> 6)) * 128 + (size_t)(r & 127)) * 64 + (size_t)(c & 63);
+}
+__host__ __device__ __forceinline__ size_t dense_x_index(int64_t b, int64_t c, int64_t Bp) {
+  return ((size_t)(c >> 6) * Bp + (size_t)b) * 64 + (size_t)(c & 63);
+}
 
 // Tensor maps and shape of one batched tensor-core product (dense layout).
 struct GemmPlan {

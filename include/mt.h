@@ -205,8 +205,12 @@ MT_API mt_status mt_tensor_read_rows(const mt_tensor *T, int64_t i0, int64_t i1,
 MT_API mt_status mt_demag_blocks(mt_tiles *tiles, int64_t count, const int64_t *pairs, double *out);
 
 /* H_d = -N (Ms m) for B simulations (Eq. 9 / Eq. 17): m and H are DEVICE
- * arrays of B*3n floats (tile-major per simulation).  The stored tensor is
- * streamed once per simulation.  Errors: MT_EINVAL, MT_ECUDA. */
+ * arrays of B*3n floats (tile-major per simulation).  Streaming layout: the
+ * stored tensor is streamed once per simulation.  Dense layout: one batched
+ * tensor-core product per call (B <= 128); the first call for a batch width
+ * times a few ring depths of the product (autotuning, a few extra launches,
+ * results unaffected) and should precede any stream capture.
+ * Errors: MT_EINVAL, MT_ECUDA. */
 MT_API mt_status mt_demag_field(mt_tensor *T, const float *m, int B, float *H, void *stream);
 
 /* The same product for an FP64 tensor, in FP64: m and H are DEVICE arrays
@@ -223,7 +227,8 @@ MT_API mt_status mt_demag_field_f64(mt_tensor *T, const double *m, int B, double
  * latency-critical streams that cannot take the device-wide synchronisation
  * cudaMalloc/cudaFree may cause, or an application whose own memory pool
  * forbids the CUDA allocator.  Same arguments, same result as mt_demag_field
- * (FP32 and BF16 tensors); this call allocates nothing: its work areas (the
+ * (FP32 and BF16 tensors of the streaming layout; dense-layout tensors get
+ * MT_EINVAL); this call allocates nothing: its work areas (the
  * scaled copy of m, partial panel sums, panel counters) live in one fixed
  * array of MT_NOALLOC_SCRATCH_BYTES in the library's device image.  The
  * paper has no counterpart; it is an interface convenience.

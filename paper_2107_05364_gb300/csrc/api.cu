@@ -119,13 +119,16 @@ mt_status demag_apply(mt_tensor *T, const float *m, int B, float *H, cudaStream_
     GemmPlan plan;
     mt_status st = mt::gemm_plan(T, B, T->d_xs, &plan);
     if (st != MT_OK) return st;
+    st = mt::gemm_tune(T, &plan, H, T->d_part, T->d_count, T->tiles->ctx->d_status, s);
+    if (st != MT_OK) return st;
     mt::launch_prep_dense_x(T, m, B, T->d_xs, s);
     mt::launch_gemm(T, plan, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+    mt::launch_near(T, mt::dense_mT(T, B, T->d_xs), 1, mt::dense_pad_batch(B), B, H, nullptr, s);
   } else {
     mt::launch_prep_xs(T, m, B, T->d_xs, s);
     mt::launch_matvec(T, T->d_xs, B, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+    mt::launch_near(T, m, 3 * T->n, 1, B, H, nullptr, s);
   }
-  mt::launch_near(T, m, B, H, nullptr, s);
   return MT_OK;
 }
 

@@ -14,12 +14,15 @@
 //   * warp 0 issues 2-D TMA loads (128-byte swizzle) of a 128 x 64 tensor
 //     tile and the 64-wide slice of X^T into a shared-memory ring;
 //   * warp 1 issues tcgen05.mma (M = 128, N = B, K = 16, BF16 -> FP32) into
-//     one of two TMEM accumulators and releases ring slots with
-//     tcgen05.commit;
-//   * warps 2-5 drain a finished accumulator with tcgen05.ld (one TMEM lane
-//     = one row per thread) while the next row tile accumulates in the other
-//     one; rows split between two CTAs are summed by whichever warp arrives
-//     last, in CTA order.
+//     a ring of four TMEM accumulators, each filled over a few K blocks (the
+//     tensor cores' FP32 accumulation rounds with a bias, so chains stay
+//     short), and releases ring slots with tcgen05.commit;
+//   * warps 2-5 drain each finished accumulator with tcgen05.ld (one TMEM
+//     lane = one row per thread) into FP32 register sums while the next ones
+//     fill; rows split between two CTAs are summed by whichever warp arrives
+//     last, in CTA order;
+//   * the number of K blocks per accumulator and the ring depth are chosen
+//     per tensor and batch width by timing candidates on first use.
 // Every wait is bounded; on a timeout the kernel records MT_DEV_TIMEOUT,
 // still frees its TMEM and returns.
 #include <cuda.h>
@@ -35,6 +38,7 @@ namespace {
 constexpr int GM = 128;  // rows per tile (MMA M)
 constexpr int GK = 64;   // K per ring stage: one 128-byte swizzle row of BF16
 constexpr int EPI_WARPS = 4;
+constexpr int NACC = 4;  // TMEM accumulators in flight between the MMA warp and the epilogue
 constexpr int GEMM_THREADS = 32 * (2 + EPI_WARPS);
 
 // ---- tcgen05 / TMA wrappers -------------------------------------------------
@@ -68,18 +72,16 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                    mtd::smem_u32(bar))
                : "memory");
 }
-// 32 lanes x 32 bit, 16 consecutive columns per thread
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
+// 32 lanes x 32 bit, 16 consecutive columns per thread; the registers are
+// valid only after tmem_wait_ld()
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
                                        uint64_t policy) {
   asm volatile(
@@ -124,8 +126,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)P.stages * P.stage_bytes);
   uint64_t *empty = full + P.stages;
   uint64_t *accf = empty + P.stages;
-  uint64_t *acce = accf + 2;
-  uint64_t *mma_done = acce + 2;
+  uint64_t *acce = accf + NACC;
+  uint64_t *mma_done = acce + NACC;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       mtd::mbar_init(&full[s], 1);
       mtd::mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NACC; ++a) {
       mtd::mbar_init(&accf[a], 1);
       mtd::mbar_init(&acce[a], EPI_WARPS);
     }
@@ -200,8 +202,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int64_t seg_end = u1 < (mt + 1) * P.KB ? u1 : (mt + 1) * P.KB;
       while (u < seg_end && !*abort_flag) {
         const int64_t c_end = seg_end < u + P.chunk ? seg_end : u + P.chunk;
-        const int a = chunk & 1;
-        if (chunk >= 2 && !mtd::mbar_wait_bounded(&acce[a], (uint32_t)((chunk >> 1) - 1) & 1u, P.status)) {
+        const int a = chunk % NACC;
+        if (chunk >= NACC && !mtd::mbar_wait_bounded(&acce[a], (uint32_t)(chunk / NACC - 1) & 1u, P.status)) {
           *abort_flag = 1;
           break;
         }
@@ -254,20 +256,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       bool first_chunk = true;
       while (u < seg_end) {
         u = seg_end < u + P.chunk ? seg_end : u + P.chunk;
-        const int a = chunk & 1;
-        const bool got = !*abort_flag && mtd::mbar_wait_bounded(&accf[a], (uint32_t)(chunk >> 1) & 1u, P.status);
+        const int a = chunk % NACC;
+        const bool got = !*abort_flag && mtd::mbar_wait_bounded(&accf[a], (uint32_t)(chunk / NACC) & 1u, P.status);
         if (!got) {
           *abort_flag = 1;
           ok = false;
         }
         tc_fence_after();
+        // all loads of the accumulator in flight at once, one wait
+        uint32_t v[BP];
 #pragma unroll
-        for (int c0 = 0; c0 < BP; c0 += 16) {
-          float v[16];
-          tmem_ld16(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(a * BP + c0), v);
+        for (int c0 = 0; c0 < BP; c0 += 16)
+          tmem_ld16(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(a * BP + c0), &v[c0]);
+        tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) run[c0 + j] = first_chunk ? v[j] : run[c0 + j] + v[j];
-        }
+        for (int j = 0; j < BP; ++j) run[j] = first_chunk ? __uint_as_float(v[j]) : run[j] + __uint_as_float(v[j]);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mtd::mbar_arrive(&acce[a]);
@@ -320,12 +323,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 // X[b][c] = BF16(Ms_j m_j[a]) for c = 3j + a (zero for padding), and the
 // low part X_lo = BF16(x - X_hi) for the split product
 __global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64_t Kp, int B, int Bp,
-                               __nv_bfloat16 *X, __nv_bfloat16 *Xlo) {
+                               __nv_bfloat16 *X, __nv_bfloat16 *Xlo, float *mT) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (t >= Kp) return;
   float x = 0.0f;
-  if (t < 3 * n) x = Ms[t / 3] * m[(size_t)b * 3 * n + t];
+  if (t < 3 * n) {
+    const float mv = m[(size_t)b * 3 * n + t];
+    x = Ms[t / 3] * mv;
+    mT[(size_t)t * Bp + b] = mv;
+  }
   const __nv_bfloat16 hi = __float2bfloat16(x);
   const size_t at = dense_x_index(b, t, Bp);
   X[at] = hi;
@@ -380,7 +387,13 @@ int dense_pad_batch(int B) {
 }
 
 size_t dense_x_bytes(const mt_tensor *T, int B) {
-  return (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 2 : 1);
+  const size_t x = (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 2 : 1);
+  return x + (size_t)3 * T->n * dense_pad_batch(B) * sizeof(float);  // + simulation-fastest copy of m
+}
+
+float *dense_mT(const mt_tensor *T, int B, void *X) {
+  const size_t x = (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 2 : 1);
+  return reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(X) + x);
 }
 size_t dense_part_bytes(const mt_tensor *T, int B) {
   return (size_t)2 * matvec_grid(T) * dense_pad_batch(B) * GM * sizeof(float);
@@ -407,7 +420,7 @@ void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cud
   __nv_bfloat16 *x = reinterpret_cast<__nv_bfloat16 *>(X);
   __nv_bfloat16 *xlo = T->prec == MT_BF16_SPLIT ? x + (size_t)Bp * T->Kp : nullptr;
   dim3 grid((unsigned)((T->Kp + 255) / 256), (unsigned)B);
-  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, Bp, x, xlo);
+  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, Bp, x, xlo, dense_mT(T, B, X));
 }
 
 mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
@@ -436,6 +449,43 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   return MT_OK;
 }
 
+mt_status gemm_tune(mt_tensor *T, GemmPlan *plan, float *H, float *part, int *count, int *status, cudaStream_t s) {
+  int key = 0;
+  while ((16 << key) < plan->Bp) ++key;
+  if (T->gemm_stages[key] > 0) {
+    plan->stages = T->gemm_stages[key];
+    return MT_OK;
+  }
+  const int smax = stages_for(plan->Bp, plan->split);
+  int cand[3] = {smax, std::max(2, smax - 2), std::max(2, smax / 2)};
+  cudaEvent_t e0, e1;
+  MT_CUDA(cudaEventCreate(&e0));
+  MT_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best = smax;
+  for (int c = 0; c < 3; ++c) {
+    if (c > 0 && cand[c] == cand[c - 1]) continue;
+    plan->stages = cand[c];
+    launch_gemm(T, *plan, H, part, count, nullptr, status, s);  // warm
+    MT_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) launch_gemm(T, *plan, H, part, count, nullptr, status, s);
+    MT_CUDA(cudaEventRecord(e1, s));
+    MT_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    MT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cand[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  MT_CUDA(cudaGetLastError());
+  T->gemm_stages[key] = best;
+  plan->stages = best;
+  return MT_OK;
+}
+
 void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part, int *count, const int *n_active,
                  int *status, cudaStream_t s) {
   GemmArgs P;
@@ -448,7 +498,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.stages = plan.stages;
   P.stage_bytes = (GM * GK * 2 + plan.Bp * GK * 2) * (plan.split ? 2 : 1);
   uint32_t cols = 32;
-  while (cols < (uint32_t)(2 * plan.Bp)) cols <<= 1;
+  while (cols < (uint32_t)(NACC * plan.Bp)) cols <<= 1;
   P.tmem_cols = cols;
   P.H = H;
   P.part = part;

@@ -81,6 +81,7 @@ struct StageArgs {
   int64_t Kp;
   int Bp;
   __nv_bfloat16 *X;
+  float *mT;  // simulation-fastest copy of the stage input (near blocks)
   // control
   SimCtl *ctl;
   int *active;
@@ -166,6 +167,7 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
       const size_t at = dense_x_index(b, 3 * i + c, A.Bp);
       A.X[at] = hi;
       if (A.xs_mode == 2) xl[at] = __float2bfloat16(f - __bfloat162float(hi));
+      A.mT[(size_t)(3 * i + c) * A.Bp + b] = v[c];
     }
   }
 }
@@ -563,6 +565,7 @@ StageArgs stage_args(mt_integrator *I) {
   A.Kp = T->Kp;
   A.Bp = mt::dense_pad_batch(I->B);
   A.X = reinterpret_cast<__nv_bfloat16 *>(I->xs);
+  A.mT = T->layout == MT_LAYOUT_DENSE ? mt::dense_mT(T, I->B, I->xs) : nullptr;
   A.ctl = I->ctl;
   A.active = I->active;
   A.n_active = I->n_active;
@@ -584,12 +587,15 @@ void launch_stage(mt_integrator *I, const StageArgs &A) {
 
 // demag product of the stage input `m` into I->Hd (xs already formed)
 void demag(mt_integrator *I, const float *m) {
-  if (I->T->layout == MT_LAYOUT_DENSE)
+  if (I->T->layout == MT_LAYOUT_DENSE) {
     mt::launch_gemm(I->T, I->plan, I->Hd, I->part, I->count, I->n_active, I->T->tiles->ctx->d_status, I->stream);
-  else
+    mt::launch_near(I->T, mt::dense_mT(I->T, I->B, I->xs), 1, mt::dense_pad_batch(I->B), I->B, I->Hd, I->active,
+                    I->stream);
+  } else {
     mt::launch_matvec(I->T, I->xs, I->B, I->Hd, I->part, I->count, I->active, I->T->tiles->ctx->d_status,
                       I->stream);
-  mt::launch_near(I->T, m, I->B, I->Hd, I->active, I->stream);
+    mt::launch_near(I->T, m, 3 * I->T->n, 1, I->B, I->Hd, I->active, I->stream);
+  }
 }
 
 void enqueue_attempt(mt_integrator *I) {
@@ -798,6 +804,7 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
     return MT_ECUDA;
   }
   MT_TRY(mt_integrator_set_params(I, p));
+  if (dense) MT_TRY(mt::gemm_tune(T, &I->plan, I->Hd, I->part, I->count, T->tiles->ctx->d_status, I->stream));
   // capture one attempt
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(I->stream, cudaStreamCaptureModeThreadLocal);

@@ -378,14 +378,16 @@ __device__ __forceinline__ ff ff_fma(ff acc, float2 v, ff x) {
 
 // threads enumerate (tile, simulation) pairs with the simulation fastest, so
 // a warp of a wide batch shares its tile's blocks (broadcast loads)
+// m element (b, j, c) sits at m[b * sb + (3 j + c) * se]: se = 1 for the
+// tile-major state, sb = 1 for the simulation-fastest copy of wide batches
 __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const float2 *val,
-                       const float *Ms, const float *m, float *H, const int *active) {
+                       const float *Ms, const float *m, int64_t sb, int64_t se, float *H, const int *active) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * B) return;
   const int64_t i = t / B;
   const int b = (int)(t - i * B);
   if (active && !active[b]) return;
-  const float *mb = m + (size_t)b * 3 * n;
+  const float *mb = m + (size_t)b * sb;
   ff hx = {0, 0}, hy = {0, 0}, hz = {0, 0};
   for (int32_t a = ptr[i]; a < ptr[i + 1]; ++a) {
     const int64_t j = col[a];
@@ -393,7 +395,7 @@ __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col,
     ff x[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float mc = mb[3 * j + c];
+      const float mc = mb[(3 * j + c) * se];
       x[c].hi = ms * mc;
       x[c].lo = fmaf(ms, mc, -x[c].hi);
     }
@@ -506,11 +508,12 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
   }
 }
 
-void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s) {
+void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int B, float *H, const int *active,
+                 cudaStream_t s) {
   if (T->near_count == 0) return;
   const int64_t tot = T->n * (int64_t)B;
   k_near<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl,
-                                                       T->tiles->d_Ms, m, H, active);
+                                                       T->tiles->d_Ms, m, sb, se, H, active);
 }
 
 }  // namespace mt

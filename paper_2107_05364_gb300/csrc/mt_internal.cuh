@@ -122,6 +122,7 @@ struct mt_tensor {
   int count_B = 0;
   float *d_Hd = nullptr;
   int Hd_B = 0;
+  int gemm_stages[4] = {0, 0, 0, 0};  // tuned ring depth per padded batch 16/32/64/128
 };
 
 // Dense layout, tile-blocked: the 3n x 3n matrix (padded to Kp = 128 k) is
@@ -167,8 +168,10 @@ void launch_prep_xs_f64(const mt_tensor *T, const double *m, int B, double *xs, 
 // H[b] = -N xs[b]; active (may be null) skips finished simulations
 void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *part, int *count,
                    const int *active, int *status, cudaStream_t s);
-// H[b] -= near-field FP64 blocks applied to Ms m (only for BF16 precisions)
-void launch_near(const mt_tensor *T, const float *m, int B, float *H, const int *active, cudaStream_t s);
+// H[b] -= near-field blocks applied to Ms m (BF16 precisions); element
+// (b, j, c) of m at m[b * sb + (3 j + c) * se]
+void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int B, float *H, const int *active,
+                 cudaStream_t s);
 
 // batched product on tcgen05 (dense layout)
 cudaError_t gemm_prepare();
@@ -178,6 +181,12 @@ size_t dense_part_bytes(const mt_tensor *T, int B);
 size_t dense_count_bytes(const mt_tensor *T);
 void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cudaStream_t s);
 mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan);
+// choose the ring depth of the batched product by timing (once per tensor
+// and padded batch); writes scratch values into H, part
+mt_status gemm_tune(mt_tensor *T, GemmPlan *plan, float *H, float *part, int *count, int *status, cudaStream_t s);
+// the simulation-fastest copy of the state used by the near blocks of a
+// dense-layout batch: mT[(3 j + c) * Bp + b], right after the operand X
+float *dense_mT(const mt_tensor *T, int B, void *X);
 void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part, int *count, const int *n_active,
                  int *status, cudaStream_t s);
 

@@ -5,6 +5,7 @@
 --what field    : mt_demag_field R times (prep + streaming product [+ near])
 --what step     : R Runge-Kutta attempts through the integrator graph
 --what assemble : tensor assembly only
+--layout dense  : 9-entry BF16 / split tensor for the batched tensor-core product
 Prints the average time per call measured with CUDA events (not meaningful
 under a profiler).
 """
@@ -25,6 +26,7 @@ def main():
     ap.add_argument("--what", default="field", choices=["field", "step", "assemble"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--B", type=int, default=1)
+    ap.add_argument("--layout", default="stream", choices=["stream", "dense"])
     a = ap.parse_args()
 
     import torch
@@ -46,7 +48,7 @@ def main():
         torch.cuda.synchronize()
         print("assemble n=%d: %.3f ms" % (t.n, e0.elapsed_time(e1) / a.reps))
         return
-    T = mt.mt_demag_assemble(tiles, a.prec)
+    T = mt.mt_demag_assemble_ex(tiles, a.prec, mt.MT_LAYOUT_DENSE if a.layout == "dense" else mt.MT_LAYOUT_STREAM)
     m = np.stack([wl.m_random(t.n, seed=b) for b in range(a.B)]).astype(np.float32)
     if a.what == "field":
         mg = torch.tensor(m.ravel(), device="cuda")

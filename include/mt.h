@@ -311,6 +311,78 @@ MT_API mt_status mt_integrate(mt_tensor *T, const mt_llg_params *p, const mt_ode
 MT_API mt_status mt_relax(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, double tol, double t_max,
                    float *m, int B, mt_stats *stats, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* request serving: relax jobs on many geometries, continuously batched     */
+/* ---------------------------------------------------------------------- */
+/* A server owns a worker thread that runs every job on the device.  For each
+ * geometry with work it keeps the assembled tensor resident together with
+ * an integrator of max_batch simulation slots (an "engine" on its own
+ * stream); jobs queue per geometry in arrival order and take free slots
+ * between graph replays, so work that arrives while other jobs run joins
+ * the batch as slots free up.  Engines of different geometries overlap on
+ * the device.  Residency is admitted by device footprint (tensor + batch
+ * state) against hbm_budget_bytes; idle engines are evicted least recently
+ * used.  A relax job integrates its own simulation until
+ * max_i |m_i x H_eff,i| / Ms_i < tol (Eq. 2) or its time cap. */
+typedef struct mt_server mt_server;
+
+typedef struct {
+  size_t hbm_budget_bytes;  /* tensors + batch state (0: the context budget) */
+  int32_t max_batch;        /* slots per resident geometry, 1..128          */
+  int32_t prec;             /* mt_prec of cached tensors (not MT_F64)       */
+  int32_t layout;           /* mt_layout_kind of cached tensors             */
+  int32_t form;             /* mt_form of every job                         */
+  double gamma;             /* m/(A s)                                      */
+  mt_ode_opts ode;          /* integrator options; max_steps caps each job  */
+  int32_t replays_per_poll; /* Runge-Kutta attempts between completion      */
+                            /* checks (0: 16)                               */
+  int32_t pad;
+} mt_server_opts;
+
+typedef struct {
+  int32_t geometry;         /* id from mt_server_add_geometry               */
+  int32_t pad;
+  double alpha;             /* damping of this job                          */
+  double Ha[3];             /* applied field, A/m                           */
+  const float *m0;          /* HOST, 3n floats, copied by mt_server_submit  */
+  double tol;               /* torque tolerance (> 0)                       */
+  double t_max;             /* simulated-time cap, s (> 0)                  */
+} mt_job;
+
+typedef struct {
+  int32_t status;           /* MT_OK, MT_ENOCONV (cap), MT_ENONFINITE,      */
+                            /* MT_ENOMEM (geometry exceeds the budget)      */
+  int32_t geometry;
+  double t_submit, t_start, t_done; /* server clock, s since creation       */
+  int64_t n_accept, n_reject, n_rhs;
+  double t_sim;             /* simulated time reached, s                    */
+  double tau;               /* final torque                                 */
+} mt_job_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, evictions, assemblies, resident;
+  size_t bytes_in_use, budget;
+} mt_server_stats;
+
+/* Errors: MT_EINVAL (bad options). */
+MT_API mt_status mt_server_create(mt_ctx *ctx, const mt_server_opts *opts, mt_server **out);
+/* Register a geometry (HOST arrays as for mt_tiles_create, copied); its
+ * tensor is assembled when a job first needs it.  Returns its id. */
+MT_API mt_status mt_server_add_geometry(mt_server *S, int64_t n, const double *centre, const double *edge,
+                                        const double *Ms, const double *Aex, const double *Ku,
+                                        const double *axis, const int32_t *nbr, int32_t *geometry_id);
+/* Queue a job (copied); returns at once with its id. */
+MT_API mt_status mt_server_submit(mt_server *S, const mt_job *job, uint64_t *job_id);
+/* Wait up to timeout_s for a job; on MT_OK fills res and (if m_out is not
+ * NULL) the final state (HOST, 3n floats) and forgets the job.  Returns
+ * MT_ETIMEOUT if it is not finished yet (it keeps running). */
+MT_API mt_status mt_server_wait(mt_server *S, uint64_t job_id, double timeout_s, mt_job_result *res,
+                                float *m_out);
+MT_API mt_status mt_server_get_stats(mt_server *S, mt_server_stats *st);
+/* Stops the worker after the device work in flight; unfinished jobs are
+ * dropped. */
+MT_API void mt_server_destroy(mt_server *S);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,35 @@ class TensorInfo(ctypes.Structure):
                 ("bytes", ctypes.c_int64), ("near_blocks", ctypes.c_int64)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("form", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("ode", OdeOpts), ("replays_per_poll", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int32), ("pad", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("Ha", ctypes.c_double * 3), ("m0", ctypes.c_void_p), ("tol", ctypes.c_double),
+                ("t_max", ctypes.c_double)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("geometry", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("n_accept", ctypes.c_int64),
+                ("n_reject", ctypes.c_int64), ("n_rhs", ctypes.c_int64), ("t_sim", ctypes.c_double),
+                ("tau", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: (list(v) if hasattr(v, "__len__") else v) for k, v in
+                ((k, getattr(self, k)) for k, _ in self._fields_)}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("assemblies", ctypes.c_int64), ("resident", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -93,6 +122,12 @@ _SIGS = {
     "mt_integrate": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _P, _I, _D, _D, _I64, _P, _P,
                           _P]),
     "mt_relax": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _D, _D, _P, _I, _P, _P]),
+    "mt_server_create": (_I, [_P, ctypes.POINTER(ServerOpts), _PP]),
+    "mt_server_add_geometry": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "mt_server_submit": (_I, [_P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
+    "mt_server_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(JobResult), _P]),
+    "mt_server_get_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
+    "mt_server_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -387,3 +422,71 @@ class Integrator:
 
 def mt_integrator_create(T: TensorH, params: LlgParams, opts: OdeOpts, B: int = 1, stream=None) -> Integrator:
     return Integrator(T, params, opts, B, stream)
+
+
+class Server:
+    """Owner of an mt_server handle: relax jobs on many geometries,
+    continuously batched on the device (see include/mt.h)."""
+
+    def __init__(self, ctx: Ctx, max_batch: int = 16, prec="f32", layout: int = MT_LAYOUT_STREAM,
+                 hbm_budget_bytes: int = 0, gamma: float = 2.211e5, form: int = MT_FORM_GILBERT,
+                 opts: OdeOpts | None = None, replays_per_poll: int = 0):
+        prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
+        o = ServerOpts(int(hbm_budget_bytes), int(max_batch), prec, int(layout), int(form), float(gamma),
+                       opts or ode_opts(rtol=1e-5, atol=1e-5), int(replays_per_poll), 0)
+        h = ctypes.c_void_p()
+        _check(lib().mt_server_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "mt_server_create")
+        self.h = h
+        self.ctx = ctx
+        self.n = {}
+
+    def add_geometry(self, tiles) -> int:
+        arrs = [_f64(tiles.centre), _f64(tiles.edge), _f64(tiles.Ms), _f64(tiles.Aex), _f64(tiles.Ku),
+                _f64(tiles.axis)]
+        nbr = None if tiles.nbr is None else np.ascontiguousarray(tiles.nbr, np.int32)
+        gid = ctypes.c_int32()
+        n = int(arrs[0].size // 3)
+        _check(lib().mt_server_add_geometry(self.h, n, *[_ptr(a) for a in arrs], _ptr(nbr), ctypes.byref(gid)),
+               "mt_server_add_geometry")
+        self.n[gid.value] = n
+        return gid.value
+
+    def submit(self, geometry: int, m0, alpha: float = 0.5, Ha=(0.0, 0.0, 0.0), tol: float = 1e-4,
+               t_max: float = 1e-9) -> int:
+        m0 = np.ascontiguousarray(m0, np.float32).ravel()
+        j = Job(int(geometry), 0, float(alpha), (ctypes.c_double * 3)(*[float(x) for x in Ha]), m0.ctypes.data,
+                float(tol), float(t_max))
+        jid = ctypes.c_uint64()
+        _check(lib().mt_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid)), "mt_server_submit")
+        return jid.value
+
+    def wait(self, job_id: int, timeout_s: float = 60.0, geometry: int | None = None):
+        """Returns (status, result dict, final m (n,3) or None)."""
+        res = JobResult()
+        m = None
+        if geometry is not None:
+            m = np.empty((self.n[geometry], 3), np.float32)
+        s = lib().mt_server_wait(self.h, ctypes.c_uint64(job_id), float(timeout_s), ctypes.byref(res), _ptr(m))
+        return s, res.as_dict(), m
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().mt_server_get_stats(self.h, ctypes.byref(st)), "mt_server_get_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if self.h:
+            lib().mt_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mt_server_create(ctx: Ctx, **kw) -> Server:
+    return Server(ctx, **kw)

@@ -437,3 +437,21 @@ void tensor_release(mt_tensor *T) {
 }
 
 }  // namespace mt
+
+namespace mt {
+
+// device bytes of a tensor of n tiles in a precision and layout (as allocated
+// by mt_demag_assemble_ex)
+size_t tensor_bytes_for(int64_t n, int prec, int layout) {
+  if (layout == MT_LAYOUT_DENSE) {
+    const size_t Kp = (size_t)((3 * n + 127) / 128) * 128;
+    return Kp * Kp * 2 * (prec == MT_BF16_SPLIT ? 2 : 1);
+  }
+  mt_layout L;
+  layout_for(prec, &L);
+  L.P = (n + L.TR - 1) / L.TR;
+  L.Q = (n + L.TC - 1) / L.TC;
+  return (size_t)L.P * L.Q * (L.chunk_bytes() + L.scale_bytes_per_chunk);
+}
+
+}  // namespace mt

@@ -3,9 +3,13 @@
 // B simulations on one geometry turn the product H_d = -N (Ms m) (Eq. 9,
 // Eq. 17) into a GEMM: D[3n x B] = N[3n x 3n] X^T with X[b] = Ms m_b.  The
 // tensor is stored dense (all 9 entries of each block, row r = 3i + a,
-// column c = 3j + b) in BF16, or as a BF16 hi + lo pair ("split") that is
-// multiplied as N_hi x_hi + N_hi x_lo + N_lo x_hi; the blocks of touching
-// tiles are zero there and are applied in FP64 by the near-field kernel.
+// column c = 3j + b) in BF16, or as a BF16 hi + lo pair ("split").  The
+// split product carries the operand as three BF16 terms x0 + x1 + x2 (24
+// significant bits: a relaxed, nearly uniform state would otherwise round
+// every x the same way and leave a coherent error) and forms
+// N_hi (x0 + x1 + x2) + N_lo (x0 + x1); the blocks of touching tiles are
+// zero there and are applied with FP64-class accuracy by the near-field
+// kernel.
 //
 // The GEMM is HBM-bound for B <= ~300 (64 flop per tensor byte at B = 64),
 // so the design streams the tensor once per batched product:
@@ -116,7 +120,8 @@ struct GemmArgs {
 template <bool SPLIT, int BP>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAlo,
-           const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tXlo, GemmArgs P) {
+           const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tX1,
+           const __grid_constant__ CUtensorMap tX2, GemmArgs P) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   const uint32_t raw = mtd::smem_u32(smem_raw);
@@ -170,14 +175,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         break;
       }
       unsigned char *st = smem + (size_t)s * P.stage_bytes;
-      mtd::mbar_arrive_expect_tx(&full[s], (uint32_t)(SPLIT ? 2 * (A_BYTES + X_BYTES) : (A_BYTES + X_BYTES)));
+      mtd::mbar_arrive_expect_tx(&full[s], (uint32_t)(SPLIT ? 2 * A_BYTES + 3 * X_BYTES : (A_BYTES + X_BYTES)));
       // tile (mt, kb) is one contiguous 16 KB block; X block kb likewise
       const int ya = (int)((mt * P.KB + kb) * GM), yx = (int)(kb * P.Bp);
       tma_2d(st, &tA, 0, ya, &full[s], pol_stream);
       tma_2d(st + A_BYTES, &tX, 0, yx, &full[s], pol_keep);
       if (SPLIT) {
+        // stage: A_hi | x0 | A_lo | x1 | x2
         tma_2d(st + A_BYTES + X_BYTES, &tAlo, 0, ya, &full[s], pol_stream);
-        tma_2d(st + 2 * A_BYTES + X_BYTES, &tXlo, 0, yx, &full[s], pol_keep);
+        tma_2d(st + 2 * A_BYTES + X_BYTES, &tX1, 0, yx, &full[s], pol_keep);
+        tma_2d(st + 2 * A_BYTES + 2 * X_BYTES, &tX2, 0, yx, &full[s], pol_keep);
       }
     }
     // drain: every copy issued must have landed before the CTA may exit
@@ -227,9 +234,12 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             umma_bf16(d_tmem, da, dx, idesc, first ? 0u : 1u);
             first = false;
             if (SPLIT) {
-              const uint32_t salo = sx + X_BYTES, sxlo = salo + A_BYTES;
-              umma_bf16(d_tmem, da, sw128_desc(sxlo + 32 * kk), idesc, 1u);  // N_hi x_lo
-              umma_bf16(d_tmem, sw128_desc(salo + 32 * kk), dx, idesc, 1u);  // N_lo x_hi
+              const uint32_t salo = sx + X_BYTES, sx1 = salo + A_BYTES, sx2 = sx1 + X_BYTES;
+              const uint64_t dlo = sw128_desc(salo + 32 * kk), d1 = sw128_desc(sx1 + 32 * kk);
+              umma_bf16(d_tmem, da, d1, idesc, 1u);                          // N_hi x1
+              umma_bf16(d_tmem, da, sw128_desc(sx2 + 32 * kk), idesc, 1u);   // N_hi x2
+              umma_bf16(d_tmem, dlo, dx, idesc, 1u);                         // N_lo x0
+              umma_bf16(d_tmem, dlo, d1, idesc, 1u);                         // N_lo x1
             }
           }
           issued = true;
@@ -323,7 +333,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 // X[b][c] = BF16(Ms_j m_j[a]) for c = 3j + a (zero for padding), and the
 // low part X_lo = BF16(x - X_hi) for the split product
 __global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64_t Kp, int B, int Bp,
-                               __nv_bfloat16 *X, __nv_bfloat16 *Xlo, float *mT) {
+                               __nv_bfloat16 *X, __nv_bfloat16 *X1, __nv_bfloat16 *X2, float *mT) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (t >= Kp) return;
@@ -336,7 +346,12 @@ __global__ void k_prep_dense_x(const float *m, const float *Ms, int64_t n, int64
   const __nv_bfloat16 hi = __float2bfloat16(x);
   const size_t at = dense_x_index(b, t, Bp);
   X[at] = hi;
-  if (Xlo) Xlo[at] = __float2bfloat16(x - __bfloat162float(hi));
+  if (X1) {  // three-term split x = x0 + x1 + x2
+    const float r = x - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16(r);
+    X1[at] = mid;
+    X2[at] = __float2bfloat16(r - __bfloat162float(mid));
+  }
 }
 
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
@@ -370,8 +385,8 @@ mt_status make_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t r
 }
 
 int stages_for(int Bp, bool split) {
-  const int stage = (GM * GK * 2 + Bp * GK * 2) * (split ? 2 : 1);
-  const int budget = 200 * 1024;
+  const int stage = split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2;
+  const int budget = 224 * 1024;
   return std::max(2, std::min(8, budget / stage));
 }
 
@@ -386,13 +401,14 @@ int dense_pad_batch(int B) {
   return bp;
 }
 
+// operand planes: 1 (BF16) or 3 (split: x0, x1, x2)
 size_t dense_x_bytes(const mt_tensor *T, int B) {
-  const size_t x = (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 2 : 1);
+  const size_t x = (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 3 : 1);
   return x + (size_t)3 * T->n * dense_pad_batch(B) * sizeof(float);  // + simulation-fastest copy of m
 }
 
 float *dense_mT(const mt_tensor *T, int B, void *X) {
-  const size_t x = (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 2 : 1);
+  const size_t x = (size_t)dense_pad_batch(B) * T->Kp * 2 * (T->prec == MT_BF16_SPLIT ? 3 : 1);
   return reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(X) + x);
 }
 size_t dense_part_bytes(const mt_tensor *T, int B) {
@@ -418,9 +434,11 @@ cudaError_t gemm_prepare() {
 void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cudaStream_t s) {
   const int Bp = dense_pad_batch(B);
   __nv_bfloat16 *x = reinterpret_cast<__nv_bfloat16 *>(X);
-  __nv_bfloat16 *xlo = T->prec == MT_BF16_SPLIT ? x + (size_t)Bp * T->Kp : nullptr;
+  const bool split = T->prec == MT_BF16_SPLIT;
+  __nv_bfloat16 *x1 = split ? x + (size_t)Bp * T->Kp : nullptr;
+  __nv_bfloat16 *x2 = split ? x + (size_t)2 * Bp * T->Kp : nullptr;
   dim3 grid((unsigned)((T->Kp + 255) / 256), (unsigned)B);
-  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, Bp, x, xlo, dense_mT(T, B, X));
+  k_prep_dense_x<<<grid, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, T->Kp, B, Bp, x, x1, x2, dense_mT(T, B, X));
 }
 
 mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
@@ -436,10 +454,12 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   if ((st = make_map(&plan->tX, x, GK, x_rows, Bp)) != MT_OK) return st;
   if (split) {
     if ((st = make_map(&plan->tAlo, A + (size_t)T->Kp * T->Kp, GK, a_rows, GM)) != MT_OK) return st;
-    if ((st = make_map(&plan->tXlo, x + (size_t)Bp * T->Kp, GK, x_rows, Bp)) != MT_OK) return st;
+    if ((st = make_map(&plan->tX1, x + (size_t)Bp * T->Kp, GK, x_rows, Bp)) != MT_OK) return st;
+    if ((st = make_map(&plan->tX2, x + (size_t)2 * Bp * T->Kp, GK, x_rows, Bp)) != MT_OK) return st;
   } else {
     plan->tAlo = plan->tA;
-    plan->tXlo = plan->tX;
+    plan->tX1 = plan->tX;
+    plan->tX2 = plan->tX;
   }
   plan->B = B;
   plan->Bp = Bp;
@@ -496,7 +516,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.Bp = plan.Bp;
   P.chunk = plan.chunk;
   P.stages = plan.stages;
-  P.stage_bytes = (GM * GK * 2 + plan.Bp * GK * 2) * (plan.split ? 2 : 1);
+  P.stage_bytes = plan.split ? 2 * GM * GK * 2 + 3 * plan.Bp * GK * 2 : GM * GK * 2 + plan.Bp * GK * 2;
   uint32_t cols = 32;
   while (cols < (uint32_t)(NACC * plan.Bp)) cols <<= 1;
   P.tmem_cols = cols;
@@ -509,7 +529,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
   const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
 #define MT_GEMM_LAUNCH(SP, BPV) \
-  k_gemm<SP, BPV><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tXlo, P)
+  k_gemm<SP, BPV><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tX1, plan.tX2, P)
   if (plan.split) {
     switch (plan.Bp) {
       case 16: MT_GEMM_LAUNCH(true, 16); break;

@@ -55,7 +55,7 @@ struct SimCtl {
   int clipped;   // the current attempt ends exactly on t_next
   int status;
   int done;
-  int pad;
+  int fresh;  // admitted since the last k1 evaluation (serving slots)
 };
 
 enum { MODE_STEPS = 0, MODE_RUN = 1, MODE_RELAX = 2 };
@@ -90,6 +90,7 @@ struct StageArgs {
   int *red_count;  // [B]
   double *mavg;    // [n_out][B][3]
   double rtol, atol, hmax, fixed_h;
+  int fresh_only;  // stage 1: evaluate k1 only for freshly admitted simulations
 };
 
 constexpr int kStageThreads = 256;
@@ -159,14 +160,20 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
     x[A.TC] = ms * v[1];
     x[2 * A.TC] = ms * v[2];
   } else {
-    __nv_bfloat16 *xl = A.X + (size_t)A.Bp * A.Kp;  // low plane (split)
+    __nv_bfloat16 *x1 = A.X + (size_t)A.Bp * A.Kp;  // split: second and third operand terms
+    __nv_bfloat16 *x2 = x1 + (size_t)A.Bp * A.Kp;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float f = ms * v[c];
       const __nv_bfloat16 hi = __float2bfloat16(f);
       const size_t at = dense_x_index(b, 3 * i + c, A.Bp);
       A.X[at] = hi;
-      if (A.xs_mode == 2) xl[at] = __float2bfloat16(f - __bfloat162float(hi));
+      if (A.xs_mode == 2) {
+        const float r = f - __bfloat162float(hi);
+        const __nv_bfloat16 mid = __float2bfloat16(r);
+        x1[at] = mid;
+        x2[at] = __float2bfloat16(r - __bfloat162float(mid));
+      }
       A.mT[(size_t)(3 * i + c) * A.Bp + b] = v[c];
     }
   }
@@ -187,7 +194,8 @@ __device__ __forceinline__ void block_reduce(double v[NV], int max_idx) {
   if (threadIdx.x == 0) {
     for (int q = 0; q < NV; ++q) {
       double acc = sh[0][q];
-      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww) acc = (q == max_idx) ? fmax(acc, sh[ww][q]) : acc + sh[ww][q];
+      for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
+        acc = (q == max_idx) ? mtd::nan_max(acc, sh[ww][q]) : acc + sh[ww][q];
       v[q] = acc;
     }
   }
@@ -215,7 +223,7 @@ __device__ bool reduce_across_blocks(const StageArgs &A, int b, double v[5], dou
   for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
     const double *src = A.red + ((size_t)b * nblk + blk) * 5;
     acc[0] += __ldcg(&src[0]);
-    acc[1] = fmax(acc[1], __ldcg(&src[1]));
+    acc[1] = mtd::nan_max(acc[1], __ldcg(&src[1]));
     acc[2] += __ldcg(&src[2]);
     acc[3] += __ldcg(&src[3]);
     acc[4] += __ldcg(&src[4]);
@@ -311,6 +319,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (!A.active[b]) return;  // uniform per block
+  if (S == 1 && A.fresh_only && !A.ctl[b].fresh) return;
   const bool live = i < A.n;
   const float *yin = (S == 1) ? A.y : ((S & 1) ? A.ys1 : A.ys0);
   const size_t o = (size_t)b * 3 * A.n + 3 * i;
@@ -355,6 +364,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
       SimCtl c = A.ctl[b];
       c.tau = tot[1];
       c.n_rhs += 1;
+      c.fresh = 0;
       if (!isfinite(c.tau)) finish_sim(A, b, c, MT_ENONFINITE);
       else if (c.mode == MODE_RELAX && c.tau < c.tol) finish_sim(A, b, c, MT_OK);
       A.ctl[b] = c;
@@ -436,6 +446,15 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
       plan_attempt(A, c);
       A.ctl[b] = c;
     }
+  }
+}
+
+// put a prepared control block into slot b and make it active
+__global__ void k_admit(SimCtl *ctl, int *active, int *n_active, int b, SimCtl c) {
+  ctl[b] = c;
+  if (!active[b]) {
+    active[b] = 1;
+    atomicAdd(n_active, 1);
   }
 }
 
@@ -527,6 +546,7 @@ struct mt_integrator {
   double *mavg = nullptr;
   int64_t mavg_cap = 0;
   int *h_poll = nullptr;  // pinned, 2 slots
+  float *h_slot_par = nullptr;  // pinned staging of per-slot parameters (g1, g2, Ha) for admissions
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaGraphExec_t exec = nullptr;
   GemmPlan plan;  // dense layout: tensor maps of the batched product
@@ -616,8 +636,9 @@ void enqueue_attempt(mt_integrator *I) {
   launch_stage<7>(I, A);
 }
 
-mt_status enqueue_init(mt_integrator *I) {
+mt_status enqueue_init(mt_integrator *I, int fresh_only = 0) {
   StageArgs A = stage_args(I);
+  A.fresh_only = fresh_only;
   if (I->T->layout == MT_LAYOUT_DENSE)
     mt::launch_prep_dense_x(I->T, I->y, I->B, I->xs, I->stream);
   else
@@ -829,6 +850,7 @@ void mt_integrator_destroy(mt_integrator *I) {
   if (I->exec) cudaGraphExecDestroy(I->exec);
   for (void *p : I->allocs) cudaFree(p);
   if (I->h_poll) cudaFreeHost(I->h_poll);
+  if (I->h_slot_par) cudaFreeHost(I->h_slot_par);
   for (auto &e : I->ev)
     if (e) cudaEventDestroy(e);
   if (I->order_ev) cudaEventDestroy(I->order_ev);
@@ -1034,3 +1056,131 @@ mt_status mt_relax(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, d
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// slot-level control used by the serving loop (one simulation per slot,
+// admitted and retired while the others keep running)
+// ---------------------------------------------------------------------------
+namespace mt {
+
+size_t integ_ctl_bytes(const mt_integrator *I) { return sizeof(SimCtl) * I->B; }
+int integ_batch(const mt_integrator *I) { return I->B; }
+void *integ_stream(const mt_integrator *I) { return I->stream; }
+
+// Enqueue the admission of one simulation into slot b: its state (host,
+// 3n floats, must stay valid until the stream reaches the copy), its
+// equation parameters, and a relax goal (torque < tol, time cap t_max).
+mt_status integ_admit(mt_integrator *I, int b, const float *m0_host, double alpha, const double *Ha, double tol,
+                      double t_max) {
+  MT_CHECK(b >= 0 && b < I->B, MT_EINVAL, "slot %d out of range", b);
+  const int64_t n = I->T->n;
+  MT_CUDA(cudaMemcpyAsync(I->y + (size_t)b * 3 * n, m0_host, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
+                          I->stream));
+  const double a = alpha;
+  double G1, G2;
+  if (I->form == MT_FORM_GILBERT) {
+    G1 = I->gamma / (1.0 + a * a);
+    G2 = G1 * a;
+  } else {
+    G1 = I->gamma;
+    G2 = a;
+  }
+  if (!I->precess) G1 = 0.0;
+  // pinned staging: slot b's entries are reused only after its previous
+  // simulation finished, i.e. after the stream consumed them
+  float *par = I->h_slot_par + 5 * b;
+  par[0] = (float)G1;
+  par[1] = (float)G2;
+  par[2] = (float)Ha[0];
+  par[3] = (float)Ha[1];
+  par[4] = (float)Ha[2];
+  MT_CUDA(cudaMemcpyAsync(I->g1 + b, par, sizeof(float), cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->g2 + b, par + 1, sizeof(float), cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->Ha + 3 * b, par + 2, 3 * sizeof(float), cudaMemcpyHostToDevice, I->stream));
+  SimCtl c;
+  std::memset(&c, 0, sizeof(c));
+  c.t = 0.0;
+  c.h = I->o.fixed_h > 0 ? I->o.fixed_h : I->o.h0;
+  c.mode = MODE_RELAX;
+  c.tol = tol;
+  c.t1 = t_max;
+  c.t_next = t_max;
+  c.attempt_cap = I->o.max_steps;
+  c.status = MT_OK;
+  c.fresh = 1;
+  plan_host(I, c);
+  k_admit<<<1, 1, 0, I->stream>>>(I->ctl, I->active, I->n_active, b, c);
+  MT_CUDA(cudaGetLastError());
+  return MT_OK;
+}
+
+// k1 for the freshly admitted slots (one demag product for the batch)
+mt_status integ_init_fresh(mt_integrator *I) { return enqueue_init(I, 1); }
+
+mt_status integ_replay(mt_integrator *I, int k) {
+  for (int q = 0; q < k; ++q) MT_CUDA(cudaGraphLaunch(I->exec, I->stream));
+  return MT_OK;
+}
+
+// commit accepted states and copy every slot's control block to ctl_host
+// (pinned); `ev` is recorded after the copy
+mt_status integ_poll(mt_integrator *I, void *ctl_host, cudaEvent_t ev) {
+  mt_status st = enqueue_commit(I);
+  if (st != MT_OK) return st;
+  MT_CUDA(cudaMemcpyAsync(ctl_host, I->ctl, sizeof(SimCtl) * I->B, cudaMemcpyDeviceToHost, I->stream));
+  MT_CUDA(cudaEventRecord(ev, I->stream));
+  return MT_OK;
+}
+
+// read slot b of a polled control copy
+bool integ_slot_done(const void *ctl_host, int b, mt_stats *st) {
+  const SimCtl &c = reinterpret_cast<const SimCtl *>(ctl_host)[b];
+  if (st) {
+    st->n_accept = c.n_accept;
+    st->n_reject = c.n_reject;
+    st->n_rhs = c.n_rhs;
+    st->t = c.t;
+    st->h = c.h;
+    st->tau = c.tau;
+    st->status = c.status;
+    st->pad = 0;
+  }
+  return c.done != 0;
+}
+
+// enqueue the copy of slot b's committed state to host memory
+mt_status integ_fetch_slot(mt_integrator *I, int b, float *m_host) {
+  const int64_t n = I->T->n;
+  MT_CUDA(cudaMemcpyAsync(m_host, I->y + (size_t)b * 3 * n, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost,
+                          I->stream));
+  return MT_OK;
+}
+
+// an integrator whose slots all start empty (no active simulation)
+mt_status integ_create_idle(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, int B,
+                            mt_integrator **out) {
+  mt_integrator *I = nullptr;
+  mt_status st = mt_integrator_create(T, p, o, B, nullptr, &I);
+  if (st != MT_OK) return st;
+  std::vector<SimCtl> c(B);
+  for (auto &x : c) {
+    std::memset(&x, 0, sizeof(SimCtl));
+    x.done = 1;
+    x.status = MT_OK;
+    x.t_next = 1e300;
+  }
+  if ((st = write_ctl(I, c)) != MT_OK) {
+    mt_integrator_destroy(I);
+    return st;
+  }
+  if (cudaMallocHost(&I->h_slot_par, sizeof(float) * 5 * B) != cudaSuccess) {
+    mt_integrator_destroy(I);
+    mt::set_error("serving engine: pinned allocation failed");
+    return MT_ENOMEM;
+  }
+  I->need_init = false;
+  *out = I;
+  return MT_OK;
+}
+
+}  // namespace mt

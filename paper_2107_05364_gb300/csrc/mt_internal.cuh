@@ -139,7 +139,7 @@ __host__ __device__ __forceinline__ size_t dense_x_index(int64_t b, int64_t c, i
 
 // Tensor maps and shape of one batched tensor-core product (dense layout).
 struct GemmPlan {
-  CUtensorMap tA, tAlo, tX, tXlo;
+  CUtensorMap tA, tAlo, tX, tX1, tX2;  // tensor hi/lo; operand terms (split: x0, x1, x2)
   int B = 0, Bp = 0, stages = 0;
   int chunk = 4;  // K blocks accumulated in TMEM before the FP32 promotion
   bool split = false;
@@ -308,9 +308,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// max that propagates NaN (fmax would drop it and hide a non-finite state)
+__device__ __forceinline__ double nan_max(double a, double b) { return (a > b || a != a) ? a : b; }
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 

@@ -172,3 +172,18 @@ def test_set_state_from_device_and_steps_mode(mt, film):
     assert s["n_accept"] + s["n_reject"] == 10
     assert s["n_rhs"] == 1 + 6 * 10
     assert torch.isfinite(out).all()
+
+
+def test_nonfinite_state_is_reported(mt, film):
+    # a NaN in the state must end the run with MT_ENONFINITE, not look converged
+    t, tiles, T, md = film
+    m = wl.m_noisy(t.n).astype(np.float32)
+    m[7, 2] = np.nan
+    p, keep = mt.llg_params(1, alpha=0.5)
+    I = mt.Integrator(T, p, mt.ode_opts())
+    I.set_state(m.ravel())
+    s, st = I.relax(1e-4, 1e-9, check=False)
+    assert s == mt.MT_ENONFINITE and st[0]["status"] == mt.MT_ENONFINITE
+    I.set_state(m.ravel())
+    s, mavg, st = I.run(1e-11, 2, check=False)
+    assert s == mt.MT_ENONFINITE

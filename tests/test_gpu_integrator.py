@@ -187,3 +187,35 @@ def test_nonfinite_state_is_reported(mt, film):
     I.set_state(m.ravel())
     s, mavg, st = I.run(1e-11, 2, check=False)
     assert s == mt.MT_ENONFINITE
+
+
+def test_config1_relax_then_1ns_dynamics(mt, film):
+    # the 40 x 10 x 1 film: relax from the (1,1,1) start at alpha = 0.5, then
+    # 1 ns of dynamics under field 1 at alpha = 0.02 with <m> every 1 ps; the
+    # FP32 GPU trace follows the FP64 oracle's within 2e-3 (both adaptive,
+    # rtol = atol = 1e-6; differences are integration error, not arithmetic)
+    t, tiles, T, md = film
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    ropts = dict(rtol=1e-7, atol=1e-7, h0=1e-14, hmax=1e-11)
+    so, mo, _ = oracle.relax(md, m0.astype(np.float64), oracle.llg_params(alpha=0.5), oracle.ode_opts(**ropts),
+                             1e-5, 20e-9)
+    assert so == oracle.OK
+    p, keep = mt.llg_params(1, alpha=0.5)
+    I = mt.Integrator(T, p, mt.ode_opts(**ropts))
+    I.set_state(m0.ravel())
+    s, st = I.relax(1e-5, 20e-9)
+    mg = I.get_state()[0]
+    assert np.abs(mg - mo).max() <= 1e-4
+    # dynamics from the oracle's relaxed state (same start on both sides)
+    dopts = dict(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11)
+    s1 = mo.astype(np.float32)
+    so, mend, mref, _ = oracle.integrate(md, s1.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=FIELD1),
+                                         oracle.ode_opts(**dopts), 0.0, 1e-9, 1000)
+    assert so == oracle.OK
+    p2, keep2 = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    I2 = mt.Integrator(T, p2, mt.ode_opts(**dopts))
+    I2.set_state(s1.ravel())
+    s, mavg, st = I2.run(1e-9, 1000)
+    d = np.abs(mavg[:, 0, :] - mref).max()
+    print("config 1: 1 ns <m>(t) max difference %.2e" % d)
+    assert d <= 2e-3

@@ -260,6 +260,24 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = _oracle_rhs_baseline(t, m0.astype(np.float64))
+    # the other two hot-path rows, compact: batched tensor-core product and
+    # serving (full versions: --workload batched / --workload serving)
+    extra = {}
+    if world == 1 and not args.no_extras:
+        for h in (I, T, tiles):
+            h.close()
+        import argparse as _ap
+        try:
+            b = run_batched(_ap.Namespace(batch=64, prec="split", steps=5, warmup=3), quiet=True)
+            extra["batched"] = {k: b[k] for k in ("value", "unit", "vs_plain_fp32", "plain_fp32_evals_per_s",
+                                                  "dtype", "config", "roofline")}
+        except Exception as e:  # reported, never hides the main line
+            extra["batched"] = {"error": str(e)}
+        try:
+            extra["serving"] = run_serving(_ap.Namespace(requests=48, rate=200.0, t_cap=50e-12, batch_slots=32,
+                                                         serve_prec="bf16"), quiet=True)
+        except Exception as e:
+            extra["serving"] = {"error": str(e)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -280,12 +298,13 @@ def run_ours(args):
         "gpu_launches": 13 * args.steps,
         "clocks": clk.summary(),
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def run_batched(args, quiet=False):
     """Batched workload: film 200 x 50 x 2 (n = 20,000), B simulations (field
     sweep +-50 mT along a seeded in-plane direction, alpha in {0.02, 0.1,
     0.5}) on a dense BF16 / split BF16 tensor multiplied on the tensor cores;
@@ -366,7 +385,11 @@ def run_batched(args):
                      "peak_kind": kind},
         "gpu_launches": 19 * args.steps, "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    for h in (Ts, I1, tiles):
+        h.close()
+    if not quiet:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serving(args, quiet=False):
@@ -459,6 +482,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
     ap.add_argument("--workload", default="film", choices=["film", "batched", "serving"])
     ap.add_argument("--requests", type=int, default=120)
     ap.add_argument("--rate", type=float, default=200.0)

@@ -105,6 +105,7 @@ struct GemmArgs {
   int64_t n3;    // valid rows (3n)
   int64_t MT;    // row tiles
   int64_t KB;    // K blocks
+  int64_t KBU;   // units per row tile (a unit = KPS consecutive K blocks)
   int B, Bp;     // batch, padded batch (MMA N)
   int chunk;     // K blocks per TMEM accumulation before the FP32 promotion
   int stages;
@@ -117,7 +118,7 @@ struct GemmArgs {
   int *status;
 };
 
-template <bool SPLIT, int BP>
+template <bool SPLIT, int BP, int KPS>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAlo,
            const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tX1,
@@ -138,7 +139,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = gridDim.x, k = blockIdx.x;
-  const int64_t U = P.MT * P.KB;
+  // a unit is KPS consecutive K blocks of one row tile; a ring stage holds
+  // one unit: KPS sub-blocks of [A (| x0 | A_lo | x1 | x2) | X]
+  const int SB = SPLIT ? 2 * A_BYTES + 3 * X_BYTES : A_BYTES + X_BYTES;
+  const int64_t U = P.MT * P.KBU;
   const int64_t u0 = mtd::sk_begin(k, U, G), u1 = mtd::sk_begin(k + 1, U, G);
   const bool idle = P.n_active && *P.n_active == 0;  // every simulation finished
 
@@ -167,7 +171,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const uint64_t pol_keep = mtd::policy_evict_last();
     int it = 0;
     for (int64_t u = u0; u < u1; ++u, ++it) {
-      const int64_t mt = u / P.KB, kb = u - mt * P.KB;
+      const int64_t mt = u / P.KBU, kbu = u - mt * P.KBU;
       const int s = it % P.stages;
       const uint32_t ph = (uint32_t)(it / P.stages) & 1u;
       if (it >= P.stages && (*abort_flag || !mtd::mbar_wait_bounded(&empty[s], ph ^ 1u, P.status))) {
@@ -175,16 +179,21 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         break;
       }
       unsigned char *st = smem + (size_t)s * P.stage_bytes;
-      mtd::mbar_arrive_expect_tx(&full[s], (uint32_t)(SPLIT ? 2 * A_BYTES + 3 * X_BYTES : (A_BYTES + X_BYTES)));
-      // tile (mt, kb) is one contiguous 16 KB block; X block kb likewise
-      const int ya = (int)((mt * P.KB + kb) * GM), yx = (int)(kb * P.Bp);
-      tma_2d(st, &tA, 0, ya, &full[s], pol_stream);
-      tma_2d(st + A_BYTES, &tX, 0, yx, &full[s], pol_keep);
-      if (SPLIT) {
-        // stage: A_hi | x0 | A_lo | x1 | x2
-        tma_2d(st + A_BYTES + X_BYTES, &tAlo, 0, ya, &full[s], pol_stream);
-        tma_2d(st + 2 * A_BYTES + X_BYTES, &tX1, 0, yx, &full[s], pol_keep);
-        tma_2d(st + 2 * A_BYTES + 2 * X_BYTES, &tX2, 0, yx, &full[s], pol_keep);
+      mtd::mbar_arrive_expect_tx(&full[s], (uint32_t)(KPS * SB));
+#pragma unroll
+      for (int q = 0; q < KPS; ++q) {
+        // tile (mt, kb) is one contiguous 16 KB block; X block kb likewise
+        const int64_t kb = kbu * KPS + q;
+        const int ya = (int)((mt * P.KB + kb) * GM), yx = (int)(kb * P.Bp);
+        unsigned char *sb = st + q * SB;
+        tma_2d(sb, &tA, 0, ya, &full[s], pol_stream);
+        tma_2d(sb + A_BYTES, &tX, 0, yx, &full[s], pol_keep);
+        if (SPLIT) {
+          // sub-block: A_hi | x0 | A_lo | x1 | x2
+          tma_2d(sb + A_BYTES + X_BYTES, &tAlo, 0, ya, &full[s], pol_stream);
+          tma_2d(sb + 2 * A_BYTES + X_BYTES, &tX1, 0, yx, &full[s], pol_keep);
+          tma_2d(sb + 2 * A_BYTES + 2 * X_BYTES, &tX2, 0, yx, &full[s], pol_keep);
+        }
       }
     }
     // drain: every copy issued must have landed before the CTA may exit
@@ -205,8 +214,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     bool issued = false;
     int64_t u = u0;
     while (u < u1 && !*abort_flag) {
-      const int64_t mt = u / P.KB;
-      const int64_t seg_end = u1 < (mt + 1) * P.KB ? u1 : (mt + 1) * P.KB;
+      const int64_t mt = u / P.KBU;
+      const int64_t seg_end = u1 < (mt + 1) * P.KBU ? u1 : (mt + 1) * P.KBU;
       while (u < seg_end && !*abort_flag) {
         const int64_t c_end = seg_end < u + P.chunk ? seg_end : u + P.chunk;
         const int a = chunk % NACC;
@@ -225,21 +234,25 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t sa = mtd::smem_u32(smem + (size_t)s * P.stage_bytes);
-          const uint32_t sx = sa + A_BYTES;
+          const uint32_t st = mtd::smem_u32(smem + (size_t)s * P.stage_bytes);
 #pragma unroll
-          for (int kk = 0; kk < GK / 16; ++kk) {
-            // K advance inside the 128-byte swizzle row: 16 BF16 = 32 bytes
-            const uint64_t da = sw128_desc(sa + 32 * kk), dx = sw128_desc(sx + 32 * kk);
-            umma_bf16(d_tmem, da, dx, idesc, first ? 0u : 1u);
-            first = false;
-            if (SPLIT) {
-              const uint32_t salo = sx + X_BYTES, sx1 = salo + A_BYTES, sx2 = sx1 + X_BYTES;
-              const uint64_t dlo = sw128_desc(salo + 32 * kk), d1 = sw128_desc(sx1 + 32 * kk);
-              umma_bf16(d_tmem, da, d1, idesc, 1u);                          // N_hi x1
-              umma_bf16(d_tmem, da, sw128_desc(sx2 + 32 * kk), idesc, 1u);   // N_hi x2
-              umma_bf16(d_tmem, dlo, dx, idesc, 1u);                         // N_lo x0
-              umma_bf16(d_tmem, dlo, d1, idesc, 1u);                         // N_lo x1
+          for (int q = 0; q < KPS; ++q) {
+            const uint32_t sa = st + q * SB;
+            const uint32_t sx = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < GK / 16; ++kk) {
+              // K advance inside the 128-byte swizzle row: 16 BF16 = 32 bytes
+              const uint64_t da = sw128_desc(sa + 32 * kk), dx = sw128_desc(sx + 32 * kk);
+              umma_bf16(d_tmem, da, dx, idesc, first ? 0u : 1u);
+              first = false;
+              if (SPLIT) {
+                const uint32_t salo = sx + X_BYTES, sx1 = salo + A_BYTES, sx2 = sx1 + X_BYTES;
+                const uint64_t dlo = sw128_desc(salo + 32 * kk), d1 = sw128_desc(sx1 + 32 * kk);
+                umma_bf16(d_tmem, da, d1, idesc, 1u);                         // N_hi x1
+                umma_bf16(d_tmem, da, sw128_desc(sx2 + 32 * kk), idesc, 1u);  // N_hi x2
+                umma_bf16(d_tmem, dlo, dx, idesc, 1u);                        // N_lo x0
+                umma_bf16(d_tmem, dlo, d1, idesc, 1u);                        // N_lo x1
+              }
             }
           }
           issued = true;
@@ -255,13 +268,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ---------------- epilogue ----------------
     const int g = warp & 3;  // TMEM lane group accessible to this warp
     const int row = g * 32 + lane;
-    const int64_t first_mt = u0 / P.KB;
+    const int64_t first_mt = u0 / P.KBU;
     int chunk = 0;
     int64_t u = u0;
     float run[BP];  // FP32 sum of the chunks of the current row tile
     while (u < u1) {
-      const int64_t mt = u / P.KB;
-      const int64_t seg_end = u1 < (mt + 1) * P.KB ? u1 : (mt + 1) * P.KB;
+      const int64_t mt = u / P.KBU;
+      const int64_t seg_end = u1 < (mt + 1) * P.KBU ? u1 : (mt + 1) * P.KBU;
       bool ok = true;
       bool first_chunk = true;
       while (u < seg_end) {
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         ++chunk;
       }
       if (!ok) continue;
-      const int64_t kf = mtd::sk_owner(mt * P.KB, U, G), kl = mtd::sk_owner(mt * P.KB + P.KB - 1, U, G);
+      const int64_t kf = mtd::sk_owner(mt * P.KBU, U, G), kl = mtd::sk_owner(mt * P.KBU + P.KBU - 1, U, G);
       const int64_t r = mt * GM + row;
       if (kf == kl) {
 #pragma unroll
@@ -312,7 +325,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         for (int b = 0; b < P.B; ++b) {
           float tot = 0.0f;
           for (int64_t kk = kf; kk <= kl; ++kk) {
-            const int64_t fm = mtd::sk_begin(kk, U, G) / P.KB;
+            const int64_t fm = mtd::sk_begin(kk, U, G) / P.KBU;
             const int64_t sl = (mt == fm) ? 2 * kk : 2 * kk + 1;
             tot += __ldcg(&P.part[((size_t)sl * BP + b) * GM + row]);
           }
@@ -385,7 +398,7 @@ mt_status make_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t r
 }
 
 int stages_for(int Bp, bool split) {
-  const int stage = split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2;
+  const int stage = 2 * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
   const int budget = 224 * 1024;
   return std::max(2, std::min(8, budget / stage));
 }
@@ -416,9 +429,19 @@ size_t dense_part_bytes(const mt_tensor *T, int B) {
 }
 size_t dense_count_bytes(const mt_tensor *T) { return (size_t)(T->Kp / GM) * EPI_WARPS * sizeof(int); }
 
+// K blocks per ring stage: two (measured: the per-stage handshakes of the
+// TMA, MMA and commit path cost a fixed few hundred cycles, so 16 KB tiles
+// alone left the BF16 product at 0.70 of HBM and two per stage reach 0.87;
+// the split product goes from 0.73 to 0.83 with a 2-deep ring of 112 KB)
+template <bool SPLIT>
+constexpr int kps_of() {
+  return 2;
+}
+
 template <bool SPLIT, int BP>
 cudaError_t prep_one() {
-  return cudaFuncSetAttribute(k_gemm<SPLIT, BP>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return cudaFuncSetAttribute(k_gemm<SPLIT, BP, kps_of<SPLIT>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              227 * 1024);
 }
 
 cudaError_t gemm_prepare() {
@@ -465,7 +488,8 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   plan->Bp = Bp;
   plan->split = split;
   plan->stages = stages_for(Bp, split);
-  plan->chunk = 4;
+  plan->kps = 2;
+  plan->chunk = 4 / plan->kps;  // units per accumulator chunk: 4 K blocks either way
   return MT_OK;
 }
 
@@ -512,11 +536,12 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.n3 = 3 * T->n;
   P.MT = T->Kp / GM;
   P.KB = T->Kp / GK;
+  P.KBU = P.KB / plan.kps;
   P.B = plan.B;
   P.Bp = plan.Bp;
   P.chunk = plan.chunk;
   P.stages = plan.stages;
-  P.stage_bytes = plan.split ? 2 * GM * GK * 2 + 3 * plan.Bp * GK * 2 : GM * GK * 2 + plan.Bp * GK * 2;
+  P.stage_bytes = 2 * (plan.split ? 2 * GM * GK * 2 + 3 * plan.Bp * GK * 2 : GM * GK * 2 + plan.Bp * GK * 2);
   uint32_t cols = 32;
   while (cols < (uint32_t)(NACC * plan.Bp)) cols <<= 1;
   P.tmem_cols = cols;
@@ -525,11 +550,11 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.count = count;
   P.n_active = n_active;
   P.status = status;
-  const int64_t U = P.MT * P.KB;
+  const int64_t U = P.MT * P.KBU;
   const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
   const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
 #define MT_GEMM_LAUNCH(SP, BPV) \
-  k_gemm<SP, BPV><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tX1, plan.tX2, P)
+  k_gemm<SP, BPV, kps_of<SP>()><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tX1, plan.tX2, P)
   if (plan.split) {
     switch (plan.Bp) {
       case 16: MT_GEMM_LAUNCH(true, 16); break;

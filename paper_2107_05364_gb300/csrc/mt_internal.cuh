@@ -141,7 +141,8 @@ __host__ __device__ __forceinline__ size_t dense_x_index(int64_t b, int64_t c, i
 struct GemmPlan {
   CUtensorMap tA, tAlo, tX, tX1, tX2;  // tensor hi/lo; operand terms (split: x0, x1, x2)
   int B = 0, Bp = 0, stages = 0;
-  int chunk = 4;  // K blocks accumulated in TMEM before the FP32 promotion
+  int kps = 1;    // K blocks per ring stage (one unit of work)
+  int chunk = 4;  // units accumulated in TMEM before the FP32 promotion (4 K blocks)
   bool split = false;
 };
 

@@ -219,7 +219,7 @@ def run_ours(args):
         mt.mt_demag_field(T, mg, H, stream=cur)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    reps = max(10, args.steps)
+    reps = max(10, min(args.steps, 100))
     torch.cuda.synchronize()
     e0.record(cur)
     for _ in range(reps):
@@ -235,7 +235,7 @@ def run_ours(args):
     # ---- end to end through the public API with host buffers ------------
     pinned_in = torch.from_numpy(m0.ravel().copy()).pin_memory()
     pinned_out = torch.empty_like(pinned_in).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
+    e2e_steps = max(3, min(args.steps, 50))
     I.set_state(pinned_in.numpy())
     I.step(1)
     I.get_state(pinned_out.numpy().reshape(1, n, 3))
@@ -478,7 +478,7 @@ def mt_pad(B):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

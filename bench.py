@@ -127,6 +127,21 @@ def _oracle_rhs_baseline(t, m0, n_evals=3):
             "sample": "n=%d film, FP64 tensor assembled once (untimed), %d RHS evaluations timed" % (t.n, n_evals)}
 
 
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (the job is done when every replica is)."""
+    if dist is None:
+        return ms
+    import torch
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units processed by all replicas per second of the slowest one."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle's RK(4,5) on the same workload."""
     rank, world, _ = _rank_env()
@@ -205,11 +220,8 @@ def run_ours(args):
     s1 = I.stats()[0]
     n_rhs = s1["n_rhs"] - s0["n_rhs"]
     assert n_rhs == 6 * args.steps, (n_rhs, args.steps)
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = n_rhs * world / (ms * 1e-3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(n_rhs, world, ms)
 
     # ---- dominant kernel alone: streaming demag product ----------------
     mg = torch.tensor(m0.ravel(), device="cuda")

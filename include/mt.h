@@ -251,6 +251,14 @@ MT_API mt_status mt_demag_field_noalloc(mt_tensor *T, const float *m, int B, flo
 MT_API mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m, int B, float *dmdt,
                      float *tau, void *stream);
 
+/* Micromagnetic energy (Eq. 4 with the densities of Eqs. 6, 8, 11, 15) of B
+ * states m (DEVICE, B*3n floats), with the applied fields p->Ha (only Ha is
+ * read).  E (HOST, 5 doubles per simulation, J): total, Zeeman, demag,
+ * exchange, anisotropy; each quadratic term is -(mu0 Ms / 2) m.H of its
+ * field, summed over tiles with their volumes.  Synchronous.
+ * Errors: MT_EINVAL, MT_ECUDA. */
+MT_API mt_status mt_energy(mt_tensor *T, const mt_llg_params *p, const float *m, int B, double *E, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* time integration (Sec. 3.1: explicit Runge-Kutta (4,5))                  */
 /* ---------------------------------------------------------------------- */
@@ -310,6 +318,14 @@ MT_API mt_status mt_integrate(mt_tensor *T, const mt_llg_params *p, const mt_ode
                        double t0, double t1, int64_t n_out, double *mavg, mt_stats *stats, void *stream);
 MT_API mt_status mt_relax(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, double tol, double t_max,
                    float *m, int B, mt_stats *stats, void *stream);
+
+/* Self-test of failure detection: runs one kernel whose mbarrier wait can
+ * never complete, bounded by limit_s seconds (0 < limit_s <= 10), as every
+ * pipelined kernel's waits are (they record a timeout in a status word,
+ * release their resources and return instead of hanging).  Returns
+ * MT_ETIMEOUT when the wait gave up and reported it (the expected outcome),
+ * MT_ECUDA otherwise.  The context stays usable.  Synchronous. */
+MT_API mt_status mt_selftest_wait_timeout(mt_ctx *ctx, double limit_s);
 
 /* ---------------------------------------------------------------------- */
 /* request serving: relax jobs on many geometries, continuously batched     */

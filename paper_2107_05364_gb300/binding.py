@@ -97,6 +97,7 @@ _SIGS = {
     "mt_ctx_create": (_I, [_I, ctypes.c_size_t, _PP]),
     "mt_ctx_destroy": (None, [_P]),
     "mt_ctx_bytes_in_use": (ctypes.c_size_t, [_P]),
+    "mt_selftest_wait_timeout": (_I, [_P, _D]),
     "mt_tiles_create": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _PP]),
     "mt_tiles_destroy": (None, [_P]),
     "mt_demag_assemble": (_I, [_P, _I, _PP]),
@@ -109,6 +110,7 @@ _SIGS = {
     "mt_demag_field_f64": (_I, [_P, _P, _I, _P, _P]),
     "mt_demag_field_noalloc": (_I, [_P, _P, _I, _P, _P]),
     "mt_llg_rhs": (_I, [_P, ctypes.POINTER(LlgParams), _P, _I, _P, _P, _P]),
+    "mt_energy": (_I, [_P, ctypes.POINTER(LlgParams), _P, _I, _P, _P]),
     "mt_integrator_create": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _I, _P, _PP]),
     "mt_integrator_destroy": (None, [_P]),
     "mt_integrator_set_state": (_I, [_P, _P, _I, _D]),
@@ -299,6 +301,11 @@ def mt_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Ctx:
     return Ctx(device, hbm_budget_bytes)
 
 
+def mt_selftest_wait_timeout(ctx: Ctx, limit_s: float = 0.2) -> int:
+    """Status of the bounded-wait self-test (MT_ETIMEOUT = works as designed)."""
+    return int(lib().mt_selftest_wait_timeout(ctx.h, float(limit_s)))
+
+
 def mt_tiles_create(ctx: Ctx, tiles) -> TilesH:
     return TilesH(ctx, tiles)
 
@@ -344,6 +351,13 @@ def mt_demag_field_noalloc(T: TensorH, m, H, B: int = 1, stream=None):
 def mt_llg_rhs(T: TensorH, params: LlgParams, m, dmdt, tau=None, B: int = 1, stream=None):
     _check(lib().mt_llg_rhs(T.h, ctypes.byref(params), _ptr(m), B, _ptr(dmdt), _ptr(tau), _stream(stream)),
            "mt_llg_rhs")
+
+
+def mt_energy(T: TensorH, params: LlgParams, m, B: int = 1, stream=None) -> np.ndarray:
+    """Energies (J) of B states: (B, 5) = total, Zeeman, demag, exchange, anisotropy."""
+    E = np.zeros((B, 5))
+    _check(lib().mt_energy(T.h, ctypes.byref(params), _ptr(m), B, _ptr(E), _stream(stream)), "mt_energy")
+    return E
 
 
 class Integrator:

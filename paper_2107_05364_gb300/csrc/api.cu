@@ -230,6 +230,7 @@ mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const do
     vt += wvol[i];
   }
   for (auto &v : wvol) v /= vt;
+  t->vol_total = vt;
   if (nbr) {
     t->nbr.assign(nbr, nbr + 6 * n);
     t->has_exchange = true;
@@ -455,3 +456,70 @@ size_t tensor_bytes_for(int64_t n, int prec, int layout) {
 }
 
 }  // namespace mt
+
+extern "C" mt_status mt_energy(mt_tensor *T, const mt_llg_params *p, const float *m, int B, double *E,
+                               void *stream) {
+  MT_CHECK(T && p && m && E && p->Ha, MT_EINVAL, "mt_energy: NULL argument");
+  MT_CHECK(B >= 1, MT_EINVAL, "mt_energy: B must be >= 1");
+  MT_CHECK(T->prec != MT_F64, MT_EINVAL, "mt_energy: the FP64 tensor serves field checks only");
+  mt_status st = ensure_workspace(T, B);
+  if (st != MT_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<float> ha(3 * B);
+  for (int q = 0; q < 3 * B; ++q) ha[q] = (float)p->Ha[q];
+  float *d_ha = nullptr;
+  double *d_E = nullptr;
+  MT_CUDA(cudaMalloc(&d_ha, sizeof(float) * 3 * B));
+  MT_CUDA(cudaMalloc(&d_E, sizeof(double) * 4 * B));
+  MT_CUDA(cudaMemcpyAsync(d_ha, ha.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice, s));
+  MT_CUDA(cudaMemsetAsync(d_E, 0, sizeof(double) * 4 * B, s));
+  if ((st = demag_apply(T, m, B, T->d_Hd, s)) != MT_OK) return st;
+  mt::launch_energy(T, m, T->d_Hd, B, d_ha, d_E, s);
+  MT_CUDA(cudaGetLastError());
+  std::vector<double> e4(4 * B);
+  MT_CUDA(cudaMemcpyAsync(e4.data(), d_E, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, s));
+  MT_CUDA(cudaStreamSynchronize(s));
+  cudaFree(d_ha);
+  cudaFree(d_E);
+  for (int b = 0; b < B; ++b) {
+    E[5 * b + 1] = e4[4 * b];
+    E[5 * b + 2] = e4[4 * b + 1];
+    E[5 * b + 3] = e4[4 * b + 2];
+    E[5 * b + 4] = e4[4 * b + 3];
+    E[5 * b] = e4[4 * b] + e4[4 * b + 1] + e4[4 * b + 2] + e4[4 * b + 3];
+  }
+  return MT_OK;
+}
+
+namespace {
+// A wait that can never complete (one expected arrival, none comes), bounded
+// by limit_ns: exercises the give-up path every pipelined kernel relies on.
+__global__ void k_wait_selftest(int *status, uint64_t limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mtd::mbar_init(&bar, 1);
+    mtd::fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mtd::mbar_wait_bounded(&bar, 0u, status, limit_ns);
+}
+}  // namespace
+
+extern "C" mt_status mt_selftest_wait_timeout(mt_ctx *ctx, double limit_s) {
+  MT_CHECK(ctx && limit_s > 0 && limit_s <= 10.0, MT_EINVAL, "mt_selftest_wait_timeout: limit in (0, 10] s");
+  MT_CUDA(cudaSetDevice(ctx->device));
+  int *d = nullptr;
+  MT_CUDA(cudaMalloc(&d, sizeof(int)));
+  MT_CUDA(cudaMemset(d, 0, sizeof(int)));
+  k_wait_selftest<<<1, 32>>>(d, (uint64_t)(limit_s * 1e9));
+  MT_CUDA(cudaGetLastError());
+  int h = 0;
+  MT_CUDA(cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaFree(d);
+  if (h == MT_DEV_TIMEOUT) {
+    mt::set_error("mt_selftest_wait_timeout: the bounded wait gave up as designed");
+    return MT_ETIMEOUT;
+  }
+  mt::set_error("mt_selftest_wait_timeout: the wait did not report a timeout");
+  return MT_ECUDA;
+}

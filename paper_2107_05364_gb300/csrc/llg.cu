@@ -458,6 +458,50 @@ __global__ void k_admit(SimCtl *ctl, int *active, int *n_active, int b, SimCtl c
   }
 }
 
+// Energy (Eqs. 4, 6, 8, 11, 15): every quadratic density is -(mu0 Ms/2) m.H
+// of its field and the Zeeman one -mu0 Ms m.Ha, so per tile
+//   e_i = -mu0 Ms_i V_i m_i.(Ha + (H_d + H_ex + H_an)/2)  split by term.
+__global__ void k_energy(int64_t n, const int32_t *nbr, const float *wex, const float *kan, const float *axis,
+                         const float *Ms, const double *wvol, double vol_total, bool exch, const float *m,
+                         const float *Hd, const float *Ha, double *E) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  double e[4] = {0, 0, 0, 0};
+  if (i < n) {
+    const size_t o = (size_t)b * 3 * n + 3 * i;
+    const float mi[3] = {m[o], m[o + 1], m[o + 2]};
+    double hex[3] = {0, 0, 0}, han[3] = {0, 0, 0};
+    if (exch) {
+      const float *mb = m + (size_t)b * 3 * n;
+      for (int f = 0; f < 6; ++f) {
+        const int32_t p = nbr[6 * i + f];
+        if (p < 0) continue;
+        for (int c = 0; c < 3; ++c) hex[c] += (double)wex[6 * i + f] * ((double)mb[3 * p + c] - (double)mi[c]);
+      }
+    }
+    const double me = (double)mi[0] * axis[3 * i] + (double)mi[1] * axis[3 * i + 1] + (double)mi[2] * axis[3 * i + 2];
+    for (int c = 0; c < 3; ++c) han[c] = (double)kan[i] * me * axis[3 * i + c];
+    const double w = MT_MU0 * (double)Ms[i] * wvol[i] * vol_total;
+    for (int c = 0; c < 3; ++c) {
+      e[0] += -w * mi[c] * (double)Ha[3 * b + c];
+      e[1] += -0.5 * w * mi[c] * (double)Hd[o + c];
+      e[2] += -0.5 * w * mi[c] * hex[c];
+      e[3] += -0.5 * w * mi[c] * han[c];
+    }
+  }
+  __shared__ double sh[8][4];
+  for (int q = 0; q < 4; ++q) e[q] = mtd::warp_sum(e[q]);
+  const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+  if (lane == 0)
+    for (int q = 0; q < 4; ++q) sh[wq][q] = e[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double acc = 0;
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) acc += sh[ww][threadIdx.x];
+    atomicAdd(&E[4 * b + threadIdx.x], acc);
+  }
+}
+
 // standalone right-hand side: dmdt and per-simulation max torque
 __global__ void k_rhs_plain(int64_t n, const int32_t *nbr, const float *wex, const float *kan, const float *axis,
                             const float *Ms, bool exch, const float *m, const float *Hd, const float *g1,
@@ -497,6 +541,14 @@ void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B
   dim3 grid((unsigned)((T->n + 255) / 256), (unsigned)B);
   k_rhs_plain<<<grid, 256, 0, s>>>(T->n, t->d_nbr, t->d_wex, t->d_kan, t->d_axis, t->d_Ms, t->has_exchange, m, Hd,
                                    g1, g2, Ha, dmdt, tau);
+}
+
+void launch_energy(const mt_tensor *T, const float *m, const float *Hd, int B, const float *Ha, double *E,
+                   cudaStream_t s) {
+  const mt_tiles *t = T->tiles;
+  dim3 grid((unsigned)((T->n + 255) / 256), (unsigned)B);
+  k_energy<<<grid, 256, 0, s>>>(T->n, t->d_nbr, t->d_wex, t->d_kan, t->d_axis, t->d_Ms, t->d_wvol, t->vol_total,
+                                t->has_exchange, m, Hd, Ha, E);
 }
 
 void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::vector<float> &g2,

@@ -80,6 +80,7 @@ struct mt_tiles {
   float *d_kan = nullptr;      // n: 2K_i/(mu0 Ms_i)
   float *d_axis = nullptr;     // 3n unit easy axis
   double *d_wvol = nullptr;    // n: V_i / sum V
+  double vol_total = 0.0;      // sum V, m^3
   bool has_exchange = false;
 };
 
@@ -204,6 +205,11 @@ mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out);
 // per-simulation prefactors of Eq. 1: g1 (precession), g2 (damping), Ha
 void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::vector<float> &g2,
                     std::vector<float> &ha);
+
+// energy terms (Eqs. 4, 6, 8, 11, 15) per simulation, accumulated into
+// E[b*4 + {0: Zeeman, 1: demag, 2: exchange, 3: anisotropy}] (device, zeroed)
+void launch_energy(const mt_tensor *T, const float *m, const float *Hd, int B, const float *Ha, double *E,
+                   cudaStream_t s);
 
 // standalone right-hand side
 void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B, const float *g1,

@@ -480,6 +480,92 @@ def run_serving(args, quiet=False):
     return out
 
 
+def run_threshold(args):
+    """Sec. 4.3.1 experiment: time versus error when the smallest fraction of
+    the tensor elements is dropped, on the standard-problem-4 film at the
+    paper's converged resolution 160 x 40 x 1 (n = 6,400).  For each fraction:
+    kept elements, time of one product, field error against the unthresholded
+    FP64 product at a relaxed state, and the largest deviation of <m>(t) over
+    0.5 ns of field-1 dynamics from the unthresholded FP32 run."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2107_05364_gb300 import binding as mt
+    t = wl.film(160, 40, 1)
+    n = t.n
+    ctx = mt.mt_ctx_create(0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    # a relaxed start (the s-state route: relax from near (1,1,1))
+    p0, k0 = mt.llg_params(1, alpha=0.5)
+    I = mt.Integrator(T, p0, mt.ode_opts(rtol=1e-5, atol=1e-5))
+    I.set_state(wl.m_noisy(n, (1, 1, 1), 1e-3, seed=0).astype(np.float32).ravel())
+    I.relax(1e-4, 10e-9, check=False)
+    m_rel = I.get_state()[0].copy()
+    I.close()
+    mg = torch.tensor(m_rel.ravel(), device="cuda")
+    H0 = torch.empty_like(mg)
+    # reference field: the unthresholded tensor stored and applied in FP64
+    T64 = mt.mt_demag_assemble(tiles, "f64")
+    Hd = torch.empty(mg.numel(), dtype=torch.float64, device="cuda")
+    mt.mt_demag_field_f64(T64, mg.double(), Hd)
+    torch.cuda.synchronize()
+    H0n = Hd.cpu().numpy()
+    T64.close()
+    mt.mt_demag_field(T, mg, H0)
+    torch.cuda.synchronize()
+    dense_err = float(np.linalg.norm(H0.cpu().numpy() - H0n) / np.linalg.norm(H0n))
+    p1, k1 = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    opts = mt.ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11)
+
+    def dynamics(tensor):
+        J = mt.Integrator(tensor, p1, opts)
+        J.set_state(m_rel.ravel())
+        tw = time.perf_counter()
+        _, mavg, st = J.run(0.5e-9, 100, check=False)
+        wall = time.perf_counter() - tw
+        J.close()
+        return mavg[:, 0, :], wall, st[0]["n_rhs"]
+
+    ref_trace, ref_wall, _ = dynamics(T)
+    rows = []
+    for f in (0.0, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8):
+        S, thr, kept = mt.mt_tensor_threshold(T, f)
+        H = torch.empty_like(mg)
+        for _ in range(3):
+            mt.mt_demag_field(S, mg, H)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            mt.mt_demag_field(S, mg, H)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        err = float(np.linalg.norm(H.cpu().numpy() - H0n) / np.linalg.norm(H0n))
+        trace, wall, nrhs = dynamics(S)
+        info = S.info()
+        rows.append({"fraction": f, "kept_elements": kept, "sparse_bytes": info["bytes"], "product_ms": ms,
+                     "field_rel_err": err, "mavg_max_dev": float(np.abs(trace - ref_trace).max()),
+                     "dynamics_s": wall, "rhs": nrhs})
+        S.close()
+    # the dense FP32 streaming product for comparison
+    for _ in range(3):
+        mt.mt_demag_field(T, mg, H0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        mt.mt_demag_field(T, mg, H0)
+    e1.record()
+    torch.cuda.synchronize()
+    line = {"metric": "thresholded tensor: product time vs field error", "value": rows[3]["product_ms"],
+            "unit": "ms (40 % threshold)", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "sp4_film_160x40x1_n6400_threshold"},
+            "dense_fp32_product_ms": e0.elapsed_time(e1) / 20, "dense_fp32_field_rel_err": dense_err,
+            "dense_dynamics_s": ref_wall, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def mt_pad(B):
     bp = 16
     while bp < B and bp < 128:
@@ -495,7 +581,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
-    ap.add_argument("--workload", default="film", choices=["film", "batched", "serving"])
+    ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold"])
     ap.add_argument("--requests", type=int, default=120)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--t-cap", type=float, default=100e-12)
@@ -510,6 +596,8 @@ def main():
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "threshold":
+        run_threshold(args)
     else:
         run_ours(args)
 

@@ -74,9 +74,11 @@ typedef enum {
 typedef enum {
   MT_LAYOUT_STREAM = 0, /* 6 unique entries per block, tile-blocked panels for  */
                         /* the streaming product (one simulation per pass)      */
-  MT_LAYOUT_DENSE = 1   /* all 9 entries, row-major 3n x 3n BF16 (or hi + lo   */
+  MT_LAYOUT_DENSE = 1,  /* all 9 entries, row-major 3n x 3n BF16 (or hi + lo   */
                         /* pair) for the batched tensor-core product; only      */
                         /* MT_BF16_SCALED (scales fixed to 1) and MT_BF16_SPLIT */
+  MT_LAYOUT_SPARSE = 2  /* thresholded FP32 tensor in block-sparse rows        */
+                        /* (made by mt_tensor_threshold, Sec. 4.3.1)            */
 } mt_layout_kind;
 
 /* Equation-of-motion form. */
@@ -189,6 +191,25 @@ MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **ou
  * layout.  Errors as mt_demag_assemble, plus MT_EINVAL for a precision the
  * layout does not support. */
 MT_API mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_tensor **out);
+
+/* Thresholded copy of an FP32 streaming-layout tensor (Sec. 4.3.1): the
+ * smallest `fraction` (in [0, 1)) of the nonzero elements of the full 3n x 3n
+ * matrix, ranked by absolute FP32 value (an off-diagonal block entry counts
+ * twice), is set to zero and the rest stored in block-sparse rows (a block is
+ * kept if any entry survives).  Exactly k = floor(fraction * nonzeros)
+ * elements go: all below the magnitude t of the element of rank k, and of
+ * those equal to t the first ones in (row tile, column tile, entry xx xy xz
+ * yy yz zz) order; an off-diagonal entry whose two copies the cut would
+ * split is kept whole (k - 1 go), so blocks stay symmetric.  The product
+ * reads 28 B per kept block (6 FP32 entries + an int32 column) and sums in
+ * compensated FP32.  The
+ * new tensor works with mt_demag_field, mt_llg_rhs, mt_energy and the
+ * integrator; it keeps the tile set alive.  threshold (may be NULL) gets t,
+ * kept_elements (may be NULL) the number of kept nonzero elements.
+ * Synchronous.  Errors: MT_EINVAL (not FP32 streaming, bad fraction),
+ * MT_ENOMEM, MT_ECUDA. */
+MT_API mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tensor **out, double *threshold,
+                                     int64_t *kept_elements);
 
 MT_API void mt_tensor_destroy(mt_tensor *T);
 MT_API mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info);

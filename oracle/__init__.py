@@ -19,6 +19,8 @@ Functions and the passage each follows (see ``oracle.c`` for the formulas):
 * :func:`integrate`, :func:`relax`, :func:`integrate_linear` -- Sec. 3.1,
   Dormand-Prince RK(4,5).
 * :func:`energy` -- Eqs. 4, 6, 8, 11, 15.
+* :func:`threshold_tensor` -- Sec. 4.3.1, dropping the smallest fraction of
+  the nonzero tensor elements.
 """
 from __future__ import annotations
 
@@ -305,3 +307,43 @@ def dp45_tableau():
     bh = np.zeros(7)
     lib().or_dp45_tableau(_p(c), _p(a), _p(b), _p(bh))
     return c, a.reshape(7, 6), b, bh
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.3.1: thresholding
+# ---------------------------------------------------------------------------
+_MULT = np.array([1, 2, 2, 1, 2, 1])  # copies of each stored entry in the full 3x3 block
+
+
+def threshold_tensor(N, fraction):
+    """Sec. 4.3.1: the fraction `fraction` of the nonzero elements of the full
+    3n x 3n tensor with the smallest magnitude is set to zero.
+
+    Readings: the elements are those of the full matrix (an off-diagonal
+    entry of a symmetric block stands for two elements); they are ranked by
+    magnitude rounded to FP32 (the storage precision the product uses), ties
+    in (row tile i, column tile j, entry xx, xy, xz, yy, yz, zz) order with an
+    off-diagonal entry's two copies adjacent; the first k = floor(fraction *
+    nonzeros) of that order are dropped, except that an entry whose two
+    copies are split by the cut stays (every 3x3 block stays symmetric).
+    Returns (thresholded FP64 tensor (n, n, 6), t = magnitude of the element
+    of rank k, kept nonzero elements)."""
+    N = np.asarray(N, np.float64)
+    a32 = np.abs(N.astype(np.float32)).astype(np.float64)
+    flat = a32.ravel()  # (i, j, entry) order
+    mult = np.tile(_MULT, flat.size // 6)
+    nzm = flat > 0
+    nz = np.sort(np.repeat(flat[nzm], mult[nzm]))
+    k = int(fraction * nz.size)
+    if k == 0 or nz.size == 0:
+        return N.copy(), 0.0, int(nz.size)
+    t = nz[k]
+    less = nzm & (flat < t)
+    r = k - int(mult[less].sum())  # elements equal to t still to drop
+    tie = flat == t
+    cum = np.cumsum(np.where(tie, mult, 0))  # copies of t up to and including this entry
+    drop = less | (tie & (cum <= r))
+    keep = (nzm & ~drop).reshape(N.shape)
+    out = np.where(keep, N, 0.0)
+    kept = int((keep.reshape(-1, 6) * _MULT).sum())
+    return out, float(t), kept

@@ -19,7 +19,7 @@ from . import build as _build
 MT_OK, MT_EINVAL, MT_ENOMEM, MT_EOVERLAP, MT_ENOCONV, MT_ETIMEOUT, MT_ENONFINITE, MT_ECUDA, MT_EBUSY = range(9)
 MT_F64, MT_F32, MT_BF16_SCALED, MT_BF16_SPLIT = range(4)
 MT_FORM_GILBERT, MT_FORM_LL = 0, 1
-MT_LAYOUT_STREAM, MT_LAYOUT_DENSE = 0, 1
+MT_LAYOUT_STREAM, MT_LAYOUT_DENSE, MT_LAYOUT_SPARSE = 0, 1, 2
 PREC_NAMES = {"f64": MT_F64, "f32": MT_F32, "bf16": MT_BF16_SCALED, "bf16_scaled": MT_BF16_SCALED,
               "split": MT_BF16_SPLIT, "bf16_split": MT_BF16_SPLIT}
 
@@ -103,6 +103,7 @@ _SIGS = {
     "mt_demag_assemble": (_I, [_P, _I, _PP]),
     "mt_demag_assemble_ex": (_I, [_P, _I, _I, _PP]),
     "mt_tensor_destroy": (None, [_P]),
+    "mt_tensor_threshold": (_I, [_P, _D, _PP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
     "mt_tensor_get_info": (_I, [_P, ctypes.POINTER(TensorInfo)]),
     "mt_tensor_read_rows": (_I, [_P, _I64, _I64, _P]),
     "mt_demag_blocks": (_I, [_P, _I64, _P, _P]),
@@ -316,6 +317,27 @@ def mt_demag_assemble(tiles: TilesH, prec="f32") -> TensorH:
 
 def mt_demag_assemble_ex(tiles: TilesH, prec="bf16", layout: int = MT_LAYOUT_DENSE) -> TensorH:
     return TensorH(tiles, prec, layout)
+
+
+class _Wrapped(TensorH):
+    """A tensor handle made by a library call other than assembly."""
+
+    def __init__(self, h, tiles, prec, layout):  # noqa: D401 - plain holder
+        self.h = h
+        self.tiles = tiles
+        self.n = tiles.n
+        self.prec = prec
+        self.layout = layout
+
+
+def mt_tensor_threshold(T: TensorH, fraction: float):
+    """Sec. 4.3.1 thresholded copy: returns (tensor, cut value t, kept elements)."""
+    h = ctypes.c_void_p()
+    thr = ctypes.c_double()
+    kept = ctypes.c_int64()
+    _check(lib().mt_tensor_threshold(T.h, float(fraction), ctypes.byref(h), ctypes.byref(thr), ctypes.byref(kept)),
+           "mt_tensor_threshold")
+    return _Wrapped(h, T.tiles, MT_F32, MT_LAYOUT_SPARSE), thr.value, kept.value
 
 
 def mt_tensor_read_rows(T: TensorH, i0: int, i1: int) -> np.ndarray:

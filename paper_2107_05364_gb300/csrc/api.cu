@@ -72,6 +72,9 @@ void free_tensor_mem(mt_tensor *T) {
   cudaFree(T->d_part);
   cudaFree(T->d_count);
   cudaFree(T->d_Hd);
+  cudaFree(T->d_sp_ptr);
+  cudaFree(T->d_sp_col);
+  cudaFree(T->d_sp_val);
 }
 
 // workspace of the standalone field/rhs calls for B simulations
@@ -115,6 +118,11 @@ mt_status ensure_workspace(mt_tensor *T, int B) {
 // H = -N (Ms m) with the tensor's own workspace: streaming product or, for
 // the dense layout, the batched tensor-core product; then the FP64 near blocks
 mt_status demag_apply(mt_tensor *T, const float *m, int B, float *H, cudaStream_t s) {
+  if (T->layout == MT_LAYOUT_SPARSE) {
+    mt::launch_prep_xs(T, m, B, T->d_xs, s);
+    mt::launch_spmv(T, T->d_xs, B, H, nullptr, s);
+    return MT_OK;
+  }
   if (T->layout == MT_LAYOUT_DENSE) {
     GemmPlan plan;
     mt_status st = mt::gemm_plan(T, B, T->d_xs, &plan);
@@ -356,6 +364,7 @@ mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
 mt_status mt_tensor_read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
   MT_CHECK(T && out, MT_EINVAL, "mt_tensor_read_rows: NULL argument");
   MT_CHECK(0 <= i0 && i0 <= i1 && i1 <= T->n, MT_EINVAL, "mt_tensor_read_rows: bad row range");
+  if (T->layout == MT_LAYOUT_SPARSE) return mt::read_rows_sparse(T, i0, i1, out);
   return mt::read_rows(T, i0, i1, out);
 }
 

@@ -77,7 +77,7 @@ struct StageArgs {
   int TC;
   // operand of the batched tensor-core product (dense layout): X[b][Kp] BF16
   // (+ low part for the split precision); xs_mode 0 = streaming layout
-  int xs_mode;  // 0 streaming FP32 chunks, 1 dense BF16, 2 dense split BF16
+  int xs_mode;  // 0 streaming FP32 chunks, 1 dense BF16, 2 dense split BF16, 3 sparse float4
   int64_t Kp;
   int Bp;
   __nv_bfloat16 *X;
@@ -159,6 +159,8 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
     x[0] = ms * v[0];
     x[A.TC] = ms * v[1];
     x[2 * A.TC] = ms * v[2];
+  } else if (A.xs_mode == 3) {
+    reinterpret_cast<float4 *>(A.xs)[(size_t)b * A.n + i] = make_float4(ms * v[0], ms * v[1], ms * v[2], 0.0f);
   } else {
     __nv_bfloat16 *x1 = A.X + (size_t)A.Bp * A.Kp;  // split: second and third operand terms
     __nv_bfloat16 *x2 = x1 + (size_t)A.Bp * A.Kp;
@@ -633,7 +635,7 @@ StageArgs stage_args(mt_integrator *I) {
   for (int s = 0; s < 7; ++s) A.k[s] = I->k[s];
   A.Q = T->L.Q;
   A.TC = T->L.TC;
-  A.xs_mode = T->layout == MT_LAYOUT_DENSE ? (T->prec == MT_BF16_SPLIT ? 2 : 1) : 0;
+  A.xs_mode = T->layout == MT_LAYOUT_DENSE ? (T->prec == MT_BF16_SPLIT ? 2 : 1) : T->layout == MT_LAYOUT_SPARSE ? 3 : 0;
   A.Kp = T->Kp;
   A.Bp = mt::dense_pad_batch(I->B);
   A.X = reinterpret_cast<__nv_bfloat16 *>(I->xs);
@@ -659,6 +661,10 @@ void launch_stage(mt_integrator *I, const StageArgs &A) {
 
 // demag product of the stage input `m` into I->Hd (xs already formed)
 void demag(mt_integrator *I, const float *m) {
+  if (I->T->layout == MT_LAYOUT_SPARSE) {
+    mt::launch_spmv(I->T, I->xs, I->B, I->Hd, I->active, I->stream);
+    return;
+  }
   if (I->T->layout == MT_LAYOUT_DENSE) {
     mt::launch_gemm(I->T, I->plan, I->Hd, I->part, I->count, I->n_active, I->T->tiles->ctx->d_status, I->stream);
     mt::launch_near(I->T, mt::dense_mT(I->T, I->B, I->xs), 1, mt::dense_pad_batch(I->B), I->B, I->Hd, I->active,

@@ -471,6 +471,7 @@ void layout_for(int prec, mt_layout *L) {
 }
 
 int64_t xs_floats(const mt_tensor *T) {
+  if (T->layout == MT_LAYOUT_SPARSE) return 4 * T->n;  // float4 (Ms m, 0) per tile
   const int64_t per = T->L.Q * 3 * T->L.TC;
   return T->prec == MT_F64 ? 2 * per : per;  // doubles take two floats
 }
@@ -483,6 +484,10 @@ size_t matvec_part_bytes(const mt_tensor *T) {
 size_t matvec_count_bytes(const mt_tensor *T, int B) { return (size_t)B * T->L.P * 8 /*W<=8*/ * sizeof(int); }
 
 void launch_prep_xs(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
+  if (T->layout == MT_LAYOUT_SPARSE) {
+    launch_prep_sparse_x(T, m, B, xs, s);
+    return;
+  }
   const int64_t tot = (int64_t)B * T->L.Q * T->L.TC;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4096);
   if (T->prec == MT_F64)

@@ -124,6 +124,11 @@ struct mt_tensor {
   float *d_Hd = nullptr;
   int Hd_B = 0;
   int gemm_stages[4] = {0, 0, 0, 0};  // tuned ring depth per padded batch 16/32/64/128
+  // thresholded layout: block-sparse rows (kept blocks, 6 FP32 entries each)
+  int64_t sp_blocks = 0;
+  int64_t *d_sp_ptr = nullptr;  // n + 1
+  int32_t *d_sp_col = nullptr;
+  float *d_sp_val = nullptr;
 };
 
 // Dense layout, tile-blocked: the 3n x 3n matrix (padded to Kp = 128 k) is
@@ -191,6 +196,12 @@ mt_status gemm_tune(mt_tensor *T, GemmPlan *plan, float *H, float *part, int *co
 float *dense_mT(const mt_tensor *T, int B, void *X);
 void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part, int *count, const int *n_active,
                  int *status, cudaStream_t s);
+
+// thresholded tensor: product and inspection
+// sparse product: xs = float4 (Ms m, 0) per tile and simulation (4 n B floats)
+void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int *active, cudaStream_t s);
+void launch_prep_sparse_x(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s);
+mt_status read_rows_sparse(const mt_tensor *T, int64_t i0, int64_t i1, double *out);
 
 // reference counting of handles (see the handle structs)
 void ctx_release(mt_ctx *c);

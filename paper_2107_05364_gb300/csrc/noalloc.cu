@@ -50,7 +50,8 @@ extern "C" mt_status mt_demag_field_noalloc(mt_tensor *T, const float *m, int B,
   MT_CHECK(T && m && H, MT_EINVAL, "mt_demag_field_noalloc: NULL argument");
   MT_CHECK(B >= 1, MT_EINVAL, "mt_demag_field_noalloc: B must be >= 1");
   MT_CHECK(T->prec != MT_F64, MT_EINVAL, "mt_demag_field_noalloc: FP64 tensors are not supported");
-  MT_CHECK(T->layout == MT_LAYOUT_STREAM, MT_EINVAL, "mt_demag_field_noalloc: dense-layout tensors are not supported");
+  MT_CHECK(T->layout == MT_LAYOUT_STREAM, MT_EINVAL,
+           "mt_demag_field_noalloc: only streaming-layout tensors are supported");
   const size_t count_bytes = align256(mt::matvec_count_bytes(T, B));
   const size_t part_bytes = align256(mt::matvec_part_bytes(T));
   const size_t xs_bytes = align256(sizeof(float) * (size_t)mt::xs_floats(T) * (size_t)B);

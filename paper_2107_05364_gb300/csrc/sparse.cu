@@ -1,0 +1,463 @@
+// Thresholded (sparse) tensor, Sec. 4.3.1 of the paper: the smallest
+// fraction f of the nonzero tensor elements (by absolute value) is set to
+// zero and the rest is stored as a sparse matrix, so the product reads only
+// what is kept.
+//
+// Reading of "the smallest fraction f of the nonzero elements": the elements
+// are those of the full 3n x 3n matrix (an off-diagonal entry of a symmetric
+// 3x3 block stands for two), ranked by magnitude of the stored FP32 value,
+// ties in (row tile i, column tile j, entry) order with an off-diagonal
+// entry's two copies adjacent; the first k = floor(f * nonzeros) are dropped,
+// except that an entry whose two copies the cut splits stays (blocks stay
+// symmetric).  The magnitude t of the element of rank k is found exactly by
+// a two-pass radix select on the FP32 bit patterns (non-negative floats order
+// like their bits); every element below t goes, and of the elements equal
+// to t the first r = k - #(below t) in that order.
+//
+// Storage: block-sparse rows of tiles; a 3x3 block is kept if any of its
+// entries survives, with its 6 unique entries (dropped ones zero) and its
+// column, in increasing column order.  Row i holds K4 = ptr[i+1] - ptr[i]
+// blocks (its kept count rounded up to 4 with zero blocks of column 0):
+// columns col[ptr[i] + a], and the entries as 6 planes of K4 floats,
+// val[6 ptr[i] + e K4 + a], so that every row starts on a 16-byte boundary
+// and a lane reads 4 blocks with 7 vector loads.
+//
+// Product: one warp per (tile row, simulation); the operand is a float4
+// (Ms m, 0) per tile, gathered from L2.  Partial sums are compensated (each
+// addition's rounding error is kept by an error-free two-sum and added back
+// at the end, Ogita, Rump and Oishi's Sum2), so the result does not depend on
+// the long per-lane summation order to more than the FP32 storage error.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "mt_internal.cuh"
+
+// blocks per lane and step, and the resident blocks per SM asked of the
+// register allocator (64-thread blocks)
+#ifndef SPMV_V
+#define SPMV_V 4
+#endif
+#ifndef SPMV_MINB
+#define SPMV_MINB 1
+#endif
+
+namespace {
+
+__device__ __forceinline__ uint32_t abs_bits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+
+// entries of the streaming FP32 layout belonging to real tiles, with their
+// multiplicity in the full matrix (diagonal 1, off-diagonal 2)
+template <typename F>
+__device__ __forceinline__ void for_each_entry(const float *D, int64_t n, int TR, int TC, int64_t Q, int64_t blk,
+                                               F &&f) {
+  // blk enumerates (p, q, r, c) chunk positions; the 6 planes of the block
+  const int64_t per_chunk = (int64_t)TR * TC;
+  const int64_t chunk = blk / per_chunk, rc = blk - chunk * per_chunk;
+  const int64_t p = chunk / Q, q = chunk - p * Q;
+  const int r = (int)(rc / TC), c = (int)(rc - (int64_t)(rc / TC) * TC);
+  const int64_t i = p * TR + r, j = q * TC + c;
+  if (i >= n || j >= n) return;
+  const float *base = D + chunk * 6 * per_chunk + (int64_t)r * TC + c;
+  const int mult[6] = {1, 2, 2, 1, 2, 1};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) f(i, j, e, base[e * per_chunk], mult[e]);
+}
+
+__global__ void k_hist(const float *D, int64_t n, int TR, int TC, int64_t Q, int64_t nblk, int pass, uint32_t hi,
+                       unsigned long long *hist) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x)
+    for_each_entry(D, n, TR, TC, Q, b, [&](int64_t, int64_t, int, float v, int mult) {
+      const uint32_t bits = abs_bits(v);
+      if (bits == 0) return;
+      if (pass == 0) atomicAdd(&hist[bits >> 16], (unsigned long long)mult);
+      else if ((bits >> 16) == hi) atomicAdd(&hist[bits & 0xffffu], (unsigned long long)mult);
+    });
+}
+
+// copies of the cut value t in row tile i (counted for the tie order)
+__global__ void k_row_ties(const float *D, int64_t n, int TR, int TC, int64_t Q, uint32_t tbits,
+                           unsigned long long *ties) {
+  const int64_t i = blockIdx.x;
+  const int64_t p = i / TR;
+  const int r = (int)(i - p * TR);
+  unsigned long long local = 0;
+  const int mult[6] = {1, 2, 2, 1, 2, 1};
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const int64_t q = j / TC;
+    const int c = (int)(j - q * TC);
+    const float *base = D + (p * Q + q) * 6 * (int64_t)TR * TC + (int64_t)r * TC + c;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) local += abs_bits(base[e * (int64_t)TR * TC]) == tbits ? mult[e] : 0;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+  __shared__ unsigned long long sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    ties[i] = s;
+  }
+}
+
+// Row tile i in increasing column order, one warp per row, 32 columns per
+// step.  An entry is kept if |v| > t, or if |v| == t and the copies of t up
+// to and including it (counted from tie_start[i], in column and entry order)
+// exceed r.  FILL = false: count the kept blocks into cnt[i]; FILL = true:
+// write them (slots by ballot + popc), then the row's padding blocks
+// (column 0, entries 0).  With t = 0 every nonzero entry is kept.
+template <bool FILL>
+__global__ void k_rows(const float *D, int64_t n, int TR, int TC, int64_t Q, uint32_t tbits,
+                       const unsigned long long *tie_start, unsigned long long r, int *cnt, const int64_t *ptr,
+                       int32_t *col, float *val) {
+  const int64_t i = blockIdx.x;
+  const int lane = threadIdx.x;
+  const int64_t p = i / TR;
+  const int rr = (int)(i - p * TR);
+  const int mult[6] = {1, 2, 2, 1, 2, 1};
+  const int64_t o = FILL ? ptr[i] : 0, K4 = FILL ? ptr[i + 1] - o : 0;
+  float *rv = FILL ? val + 6 * o : nullptr;
+  unsigned long long carry = tie_start ? tie_start[i] : 0;
+  int64_t at = 0;
+  for (int64_t j0 = 0; j0 < n; j0 += 32) {
+    const int64_t j = j0 + lane;
+    float v[6] = {0, 0, 0, 0, 0, 0};
+    uint32_t bits[6] = {0, 0, 0, 0, 0, 0};
+    unsigned tm = 0;  // copies of t in this lane's block
+    if (j < n) {
+      const int64_t q = j / TC;
+      const int c = (int)(j - q * TC);
+      const float *base = D + (p * Q + q) * 6 * (int64_t)TR * TC + (int64_t)rr * TC + c;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        v[e] = base[e * (int64_t)TR * TC];
+        bits[e] = abs_bits(v[e]);
+        tm += (bits[e] != 0 && bits[e] == tbits) ? mult[e] : 0;
+      }
+    }
+    // inclusive scan of tm over the lanes (columns in order)
+    unsigned incl = tm;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    unsigned long long cum = carry + (incl - tm);
+    bool keep = false;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      bool k = bits[e] != 0 && bits[e] > tbits;
+      if (bits[e] != 0 && bits[e] == tbits) {
+        cum += mult[e];
+        k = cum > r;
+      }
+      if (!k) v[e] = 0.0f;
+      keep = keep || k;
+    }
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    if (FILL && keep) {
+      const int64_t a = at + __popc(mask & ((1u << lane) - 1u));
+      col[o + a] = (int32_t)j;
+#pragma unroll
+      for (int e = 0; e < 6; ++e) rv[e * K4 + a] = v[e];
+    }
+    at += __popc(mask);
+  }
+  if (!FILL) {
+    if (lane == 0) cnt[i] = (int)at;
+    return;
+  }
+  for (int64_t a = at + lane; a < K4; a += 32) {
+    col[o + a] = 0;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) rv[e * K4 + a] = 0.0f;
+  }
+}
+
+// s + t = u + err exactly (Knuth's two-sum); the error goes to c
+__device__ __forceinline__ void sum2_add(float &s, float &c, float t) {
+  const float u = s + t;
+  const float bp = u - s;
+  c += (s - (u - bp)) + (t - bp);
+  s = u;
+}
+
+__device__ __forceinline__ float warp_sum2(float s, float c) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float so = __shfl_xor_sync(0xffffffffu, s, off);
+    const float co = __shfl_xor_sync(0xffffffffu, c, off);
+    c += co;
+    sum2_add(s, c, so);
+  }
+  return s + c;
+}
+
+// V consecutive blocks of one row as vectors (V = 2 or 4)
+template <int V> struct Vec;
+template <> struct Vec<2> {
+  using F = float2;
+  using I = int2;
+  static __device__ __forceinline__ float at(const F &v, int q) { return q == 0 ? v.x : v.y; }
+  static __device__ __forceinline__ int at(const I &v, int q) { return q == 0 ? v.x : v.y; }
+};
+template <> struct Vec<4> {
+  using F = float4;
+  using I = int4;
+  static __device__ __forceinline__ float at(const F &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+  static __device__ __forceinline__ int at(const I &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+};
+
+// H_i = -sum_kept N_ij Ms_j m_j; one warp per (row, simulation), rows of one
+// simulation consecutive; xs = float4 (Ms m, 0) per tile and simulation; each
+// lane takes V consecutive blocks per step (7 vector loads, V gathers)
+template <int V>
+__global__ void __launch_bounds__(64, SPMV_MINB) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
+                                             const int32_t *__restrict__ col, const float *__restrict__ val,
+                                             const float4 *__restrict__ xs, float *H, const int *active) {
+  using VF = typename Vec<V>::F;
+  using VI = typename Vec<V>::I;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= n * B) return;
+  const int64_t i = wid % n;
+  const int b = (int)(wid / n);
+  if (active && !active[b]) return;
+  const float4 *xb = xs + (size_t)b * n;
+  const int64_t o = ptr[i], K4 = ptr[i + 1] - o;
+  const float *rv = val + 6 * o;
+  const int32_t *rc = col + o;
+  float sx = 0, cx = 0, sy = 0, cy = 0, sz = 0, cz = 0;
+  for (int64_t a = V * (int64_t)lane; a < K4; a += 32 * V) {
+    const VI jj = *reinterpret_cast<const VI *>(rc + a);
+    VF v[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) v[e] = *reinterpret_cast<const VF *>(rv + e * K4 + a);
+    float4 x[V];
+#pragma unroll
+    for (int q = 0; q < V; ++q) x[q] = xb[Vec<V>::at(jj, q)];
+    // per block: (v0 v1 v2; v1 v3 v4; v2 v4 v5) (x, y, z)
+#pragma unroll
+    for (int q = 0; q < V; ++q) {
+      const float n0 = Vec<V>::at(v[0], q), n1 = Vec<V>::at(v[1], q), n2 = Vec<V>::at(v[2], q);
+      const float n3 = Vec<V>::at(v[3], q), n4 = Vec<V>::at(v[4], q), n5 = Vec<V>::at(v[5], q);
+      sum2_add(sx, cx, fmaf(n0, x[q].x, fmaf(n1, x[q].y, n2 * x[q].z)));
+      sum2_add(sy, cy, fmaf(n1, x[q].x, fmaf(n3, x[q].y, n4 * x[q].z)));
+      sum2_add(sz, cz, fmaf(n2, x[q].x, fmaf(n4, x[q].y, n5 * x[q].z)));
+    }
+  }
+  const float hx = warp_sum2(sx, cx), hy = warp_sum2(sy, cy), hz = warp_sum2(sz, cz);
+  if (lane == 0) {
+    float *Hb = H + (size_t)b * 3 * n + 3 * i;
+    Hb[0] = -hx;
+    Hb[1] = -hy;
+    Hb[2] = -hz;
+  }
+}
+
+// xs[b][j] = (Ms_j m_j, 0)
+__global__ void k_prep_sparse_x(const float *m, const float *Ms, int64_t n, int B, float4 *xs) {
+  const int64_t tot = (int64_t)B * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t % n;
+    const float ms = Ms[j];
+    const float *mj = m + 3 * t;
+    xs[t] = make_float4(ms * mj[0], ms * mj[1], ms * mj[2], 0.0f);
+  }
+}
+
+// position of rank k in a 65536-bin histogram: bin and rank within it
+void select_bin(const std::vector<unsigned long long> &h, unsigned long long k, uint32_t *bin,
+                unsigned long long *rest) {
+  unsigned long long cum = 0;
+  for (uint32_t b = 0; b < h.size(); ++b) {
+    if (cum + h[b] > k) {
+      *bin = b;
+      *rest = k - cum;
+      return;
+    }
+    cum += h[b];
+  }
+  *bin = (uint32_t)h.size() - 1;
+  *rest = 0;
+}
+
+}  // namespace
+
+namespace mt {
+
+void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int *active, cudaStream_t s) {
+  const int64_t warps = T->n * (int64_t)B;
+  k_spmv<SPMV_V><<<(unsigned)((warps + 1) / 2), 64, 0, s>>>(T->n, B, T->d_sp_ptr, T->d_sp_col, T->d_sp_val,
+                                                           reinterpret_cast<const float4 *>(xs), H, active);
+}
+
+void launch_prep_sparse_x(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
+  const int64_t tot = (int64_t)B * T->n;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 4096);
+  k_prep_sparse_x<<<blocks, 256, 0, s>>>(m, T->tiles->d_Ms, T->n, B, reinterpret_cast<float4 *>(xs));
+}
+
+}  // namespace mt
+
+extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tensor **out, double *threshold,
+                                         int64_t *kept_elements) {
+  MT_CHECK(T && out, MT_EINVAL, "mt_tensor_threshold: NULL argument");
+  MT_CHECK(T->prec == MT_F32 && T->layout == MT_LAYOUT_STREAM, MT_EINVAL,
+           "mt_tensor_threshold: needs an FP32 tensor of the streaming layout");
+  MT_CHECK(fraction >= 0.0 && fraction < 1.0, MT_EINVAL, "mt_tensor_threshold: fraction in [0, 1)");
+  MT_CUDA(cudaSetDevice(T->tiles->ctx->device));
+  const int64_t n = T->n;
+  const mt_layout &L = T->L;
+  const float *D = reinterpret_cast<const float *>(T->d_data);
+  const int64_t nblk = L.P * L.Q * (int64_t)L.TR * L.TC;
+  unsigned long long *d_hist = nullptr;
+  MT_CUDA(cudaMalloc(&d_hist, sizeof(unsigned long long) * 65536));
+  std::vector<unsigned long long> h(65536);
+  const int grid = 4 * T->tiles->ctx->num_sms;
+  // pass 1: top 16 bits
+  MT_CUDA(cudaMemset(d_hist, 0, sizeof(unsigned long long) * 65536));
+  k_hist<<<grid, 256>>>(D, n, L.TR, L.TC, L.Q, nblk, 0, 0, d_hist);
+  MT_CUDA(cudaGetLastError());
+  MT_CUDA(cudaMemcpy(h.data(), d_hist, sizeof(unsigned long long) * 65536, cudaMemcpyDeviceToHost));
+  unsigned long long nz = 0;
+  for (auto x : h) nz += x;
+  const unsigned long long k = (unsigned long long)(fraction * (double)nz);
+  uint32_t tbits = 0;
+  unsigned long long r = 0;  // copies of t to drop (the first r in tie order)
+  if (k > 0 && nz > 0) {
+    uint32_t b1 = 0;
+    unsigned long long rest = 0;
+    select_bin(h, k, &b1, &rest);
+    // pass 2: low 16 bits inside bin b1
+    MT_CUDA(cudaMemset(d_hist, 0, sizeof(unsigned long long) * 65536));
+    k_hist<<<grid, 256>>>(D, n, L.TR, L.TC, L.Q, nblk, 1, b1, d_hist);
+    MT_CUDA(cudaGetLastError());
+    MT_CUDA(cudaMemcpy(h.data(), d_hist, sizeof(unsigned long long) * 65536, cudaMemcpyDeviceToHost));
+    uint32_t b2 = 0;
+    unsigned long long rest2 = 0;
+    select_bin(h, rest, &b2, &rest2);
+    tbits = (b1 << 16) | b2;
+    r = rest2;
+  }
+  cudaFree(d_hist);
+  // tie order: copies of t before each row tile
+  unsigned long long *d_tie = nullptr;
+  if (r > 0) {
+    MT_CUDA(cudaMalloc(&d_tie, sizeof(unsigned long long) * n));
+    k_row_ties<<<(unsigned)n, 256>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie);
+    MT_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> ties(n);
+    MT_CUDA(cudaMemcpy(ties.data(), d_tie, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
+    unsigned long long acc = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      const unsigned long long c = ties[i];
+      ties[i] = acc;
+      acc += c;
+    }
+    MT_CUDA(cudaMemcpy(d_tie, ties.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice));
+  }
+  // kept blocks per row
+  int *d_cnt = nullptr;
+  MT_CUDA(cudaMalloc(&d_cnt, sizeof(int) * n));
+  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr, nullptr);
+  MT_CUDA(cudaGetLastError());
+  std::vector<int> cnt(n);
+  MT_CUDA(cudaMemcpy(cnt.data(), d_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  cudaFree(d_cnt);
+  std::vector<int64_t> ptr(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) ptr[i + 1] = ptr[i] + ((cnt[i] + 3) & ~3);
+  const int64_t nnzb = ptr[n];
+  mt_ctx *ctx = T->tiles->ctx;
+  mt_tensor *S = new mt_tensor();
+  S->tiles = T->tiles;
+  T->tiles->refs++;
+  S->prec = MT_F32;
+  S->layout = MT_LAYOUT_SPARSE;
+  S->n = n;
+  S->L = T->L;
+  S->sp_blocks = nnzb;
+  S->bytes = sizeof(int64_t) * (n + 1) + (sizeof(int32_t) + 6 * sizeof(float)) * (size_t)std::max<int64_t>(1, nnzb);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->in_use + S->bytes > ctx->budget) {
+      const size_t need = S->bytes;
+      delete S;
+      mt::tiles_release(T->tiles);
+      mt::set_error("mt_tensor_threshold: %zu bytes exceed the context budget", need);
+      cudaFree(d_tie);
+      return MT_ENOMEM;
+    }
+    ctx->in_use += S->bytes;
+  }
+  cudaError_t e = cudaMalloc(&S->d_sp_ptr, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_col, sizeof(int32_t) * std::max<int64_t>(1, nnzb));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_val, 6 * sizeof(float) * std::max<int64_t>(1, nnzb));
+  if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_ptr, ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(d_tie);
+    mt::tensor_release(S);
+    return mt::cuda_fail(e, "mt_tensor_threshold allocation", __FILE__, __LINE__);
+  }
+  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie, r, nullptr, S->d_sp_ptr, S->d_sp_col,
+                                    S->d_sp_val);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(d_tie);
+  if (e != cudaSuccess) {
+    mt::tensor_release(S);
+    return mt::cuda_fail(e, "mt_tensor_threshold fill", __FILE__, __LINE__);
+  }
+  if (threshold) {
+    float tf;
+    std::memcpy(&tf, &tbits, sizeof(tf));
+    *threshold = (double)tf;
+  }
+  if (kept_elements) {
+    // kept elements of the full matrix (off-diagonal entries count twice)
+    std::vector<float> vals(6 * (size_t)std::max<int64_t>(1, nnzb));
+    MT_CUDA(cudaMemcpy(vals.data(), S->d_sp_val, 6 * sizeof(float) * nnzb, cudaMemcpyDeviceToHost));
+    int64_t kept = 0;
+    const int mult[6] = {1, 2, 2, 1, 2, 1};
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t o = ptr[i], K4 = ptr[i + 1] - o;
+      for (int e = 0; e < 6; ++e)
+        for (int64_t a = 0; a < K4; ++a) kept += vals[6 * o + e * K4 + a] != 0.0f ? mult[e] : 0;
+    }
+    *kept_elements = kept;
+  }
+  *out = S;
+  return MT_OK;
+}
+
+namespace mt {
+
+// rows [i0, i1) of a thresholded tensor as dense FP64 blocks
+mt_status read_rows_sparse(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
+  const int64_t n = T->n;
+  std::vector<int64_t> ptr(i1 - i0 + 1);
+  MT_CUDA(cudaMemcpy(ptr.data(), T->d_sp_ptr + i0, sizeof(int64_t) * (i1 - i0 + 1), cudaMemcpyDeviceToHost));
+  const int64_t a0 = ptr[0], a1 = ptr[i1 - i0];
+  std::vector<int32_t> col(std::max<int64_t>(1, a1 - a0));
+  std::vector<float> val(6 * std::max<int64_t>(1, a1 - a0));
+  if (a1 > a0) {
+    MT_CUDA(cudaMemcpy(col.data(), T->d_sp_col + a0, sizeof(int32_t) * (a1 - a0), cudaMemcpyDeviceToHost));
+    MT_CUDA(cudaMemcpy(val.data(), T->d_sp_val + 6 * a0, 6 * sizeof(float) * (a1 - a0), cudaMemcpyDeviceToHost));
+  }
+  std::memset(out, 0, sizeof(double) * 6 * (size_t)(i1 - i0) * n);
+  for (int64_t i = i0; i < i1; ++i) {
+    const int64_t o = ptr[i - i0], K4 = ptr[i - i0 + 1] - o;
+    const float *rv = val.data() + 6 * (o - a0);
+    for (int64_t a = 0; a < K4; ++a) {
+      const int64_t j = col[o - a0 + a];
+      // padding blocks are zero and add nothing
+      for (int e = 0; e < 6; ++e) out[((i - i0) * n + j) * 6 + e] += rv[e * K4 + a];
+    }
+  }
+  return MT_OK;
+}
+
+}  // namespace mt

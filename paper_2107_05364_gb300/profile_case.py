@@ -6,6 +6,8 @@
 --what step     : R Runge-Kutta attempts through the integrator graph
 --what assemble : tensor assembly only
 --layout dense  : 9-entry BF16 / split tensor for the batched tensor-core product
+--threshold F   : drop the smallest fraction F of the elements (Sec. 4.3.1) and
+                  apply the sparse tensor (FP32, streaming layout first)
 Prints the average time per call measured with CUDA events (not meaningful
 under a profiler).
 """
@@ -27,6 +29,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--B", type=int, default=1)
     ap.add_argument("--layout", default="stream", choices=["stream", "dense"])
+    ap.add_argument("--threshold", type=float, default=None)
     a = ap.parse_args()
 
     import torch
@@ -49,6 +52,11 @@ def main():
         print("assemble n=%d: %.3f ms" % (t.n, e0.elapsed_time(e1) / a.reps))
         return
     T = mt.mt_demag_assemble_ex(tiles, a.prec, mt.MT_LAYOUT_DENSE if a.layout == "dense" else mt.MT_LAYOUT_STREAM)
+    if a.threshold is not None:
+        S, thr, kept = mt.mt_tensor_threshold(T, a.threshold)
+        T.close()
+        T = S
+        print("threshold %.2f: t = %.4g, kept elements %d, sparse bytes %d" % (a.threshold, thr, kept, T.info()["bytes"]))
     m = np.stack([wl.m_random(t.n, seed=b) for b in range(a.B)]).astype(np.float32)
     if a.what == "field":
         mg = torch.tensor(m.ravel(), device="cuda")
@@ -62,6 +70,8 @@ def main():
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / a.reps
         gbs = 24.0 * t.n * t.n * a.B / (ms * 1e-3) / 1e9 if a.prec == "f32" else float("nan")
+        if a.threshold is not None:
+            gbs = T.info()["bytes"] * a.B / (ms * 1e-3) / 1e9
         print("field n=%d B=%d prec=%s: %.4f ms/call (%.0f GB/s algorithmic for f32)" % (t.n, a.B, a.prec, ms, gbs))
     else:
         p, keep = mt.llg_params(a.B, alpha=0.02, Ha=np.array([-24.6e-3, 4.3e-3, 0.0]) / (4e-7 * math.pi))

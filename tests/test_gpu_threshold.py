@@ -1,0 +1,101 @@
+"""Thresholded tensor (Sec. 4.3.1) on the GPU against the oracle's
+thresholding: the same cut value and kept elements (the decision is taken on
+FP32 values on both sides), the sparse product within the FP32 field
+tolerance (1e-6) of the oracle's FP64 product with the same kept values,
+close to the oracle's thresholding of its own FP64 tensor, and the integrator
+running on it."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05364_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+MU0 = 4e-7 * math.pi
+
+
+@pytest.fixture(scope="module")
+def mt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2107_05364_gb300 import build
+    build.build()
+    from paper_2107_05364_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(mt):
+    return mt.mt_ctx_create(0)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("geom", ["film", "graded"])
+@pytest.mark.parametrize("fraction", [0.0, 0.2, 0.4, 0.7])
+def test_threshold_matches_oracle(mt, ctx, geom, fraction):
+    import torch
+    t = wl.film(40, 10, 1) if geom == "film" else wl.graded_film(21, 8, 3, (210e-9, 80e-9, 9e-9), seed=6)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    S, thr, kept = mt.mt_tensor_threshold(T, fraction)
+    # the selection, on identical inputs (the stored FP32 values): the same
+    # cut, the same kept elements.  (The FP64 far-field values of the two
+    # assemblies differ by ~1e-12 relative through the corner-sum
+    # cancellation, enough to move a few hundred of them across an FP32
+    # rounding boundary, so the inputs are taken from the GPU tensor here.)
+    N32 = mt.mt_tensor_read_rows(T, 0, t.n)
+    Nt32, thr_o, kept_o = oracle.threshold_tensor(N32, fraction)
+    assert np.float32(thr) == np.float32(thr_o)
+    assert kept == kept_o
+    rows = mt.mt_tensor_read_rows(S, 0, t.n)
+    np.testing.assert_array_equal(rows, Nt32)
+    assert S.info()["layout"] == mt.MT_LAYOUT_SPARSE
+    # the product against the oracle's own thresholding of its FP64 tensor
+    N = oracle.demag_tensor(t.centre, t.edge)
+    Nt, _, kept_f64 = oracle.threshold_tensor(N, fraction)
+    assert abs(kept_f64 - kept) <= 1e-3 * kept
+    md32 = oracle.Model.from_tiles(t, N=Nt32.astype(np.float64))
+    md = oracle.Model.from_tiles(t, N=Nt)
+    # a random state, and a uniform one (long sums of one sign that cancel
+    # against the self term: the case where FP32 summation order shows)
+    for m in (wl.m_random(t.n, seed=9), np.tile(np.array([[0.6, 0.48, 0.64]]), (t.n, 1))):
+        m = m.astype(np.float32)
+        mg = torch.tensor(m.ravel(), device="cuda")
+        H = torch.full_like(mg, float("nan"))
+        mt.mt_demag_field(S, mg, H)
+        torch.cuda.synchronize()
+        Hg = H.cpu().numpy().reshape(-1, 3)
+        # the sparse product itself: FP64 product of the same kept FP32 values
+        assert _rel(Hg, oracle.demag_field(md32, m.astype(np.float64))) <= 1e-6
+        # and the oracle's own thresholding of its FP64 tensor: the few
+        # elements within one FP32 rounding of the cut may fall on the other
+        # side, each worth about t relative to fields of order max|N|
+        assert _rel(Hg, oracle.demag_field(md, m.astype(np.float64))) <= 1e-4
+
+
+def test_integrator_on_thresholded_tensor(mt, ctx):
+    t = wl.film(40, 10, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    S, thr, kept = mt.mt_tensor_threshold(T, 0.4)
+    N = oracle.demag_tensor(t.centre, t.edge)
+    Nt, _, _ = oracle.threshold_tensor(N, 0.4)
+    md = oracle.Model.from_tiles(t, N=Nt)
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    Ha = np.array([-24.6e-3, 4.3e-3, 0.0]) / MU0
+    h = 1e-13
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=Ha)
+    I = mt.Integrator(S, p, mt.ode_opts(fixed_h=h))
+    I.set_state(m0.ravel())
+    I.step(20)
+    mg = I.get_state()[0]
+    st, mo, _, _ = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=Ha),
+                                    oracle.ode_opts(fixed_h=h), 0.0, 20 * h, 1)
+    assert st == oracle.OK
+    assert np.abs(mg - mo).max() <= 2e-5

@@ -250,3 +250,64 @@ def test_overlap_detection():
     c = t.centre.copy()
     c[1] = c[0] + np.array([0.3, 0, 0]) * t.edge[0]  # tile 1 overlaps tile 0
     assert oracle.check_tiles(c, t.edge) == oracle.EOVERLAP
+
+
+def test_threshold_drops_the_smallest_fraction():
+    # Sec. 4.3.1: a threshold f sets the fraction f of the nonzero tensor
+    # elements with the smallest magnitude to zero -- checked on the explicit
+    # 3n x 3n matrix, built block by block
+    t = wl.graded_film(7, 5, 2, size=(70e-9, 50e-9, 6e-9), seed=3)
+    N = oracle.demag_tensor(t.centre, t.edge)
+    full = oracle.six_to_full(N).transpose(0, 2, 1, 3).reshape(3 * t.n, 3 * t.n)
+    nz_before = np.count_nonzero(full.astype(np.float32))
+    for f in (0.2, 0.4, 0.7):
+        Nt, thr, kept = oracle.threshold_tensor(N, f)
+        ft = oracle.six_to_full(Nt).transpose(0, 2, 1, 3).reshape(3 * t.n, 3 * t.n)
+        nz_after = np.count_nonzero(ft)
+        dropped = nz_before - nz_after
+        # exactly k, or k - 1 when the cut splits the two copies of an entry
+        assert dropped in (int(f * nz_before), int(f * nz_before) - 1)
+        assert kept == nz_after
+        # every dropped element is no larger than every kept one
+        a = np.abs(full.astype(np.float32))
+        d_max = a[(ft == 0) & (a > 0)].max()
+        k_min = np.abs(ft.astype(np.float32))[ft != 0].min()
+        assert d_max <= k_min
+        np.testing.assert_array_equal(oracle.six_to_full(Nt), oracle.six_to_full(Nt).transpose(0, 1, 3, 2))
+    Nt, thr, kept = oracle.threshold_tensor(N, 0.0)
+    np.testing.assert_array_equal(Nt, N)
+
+
+def test_threshold_ties_brute_force():
+    # a uniform grid: the tensor depends only on the offset between tiles, so
+    # each value appears many times and the cut falls inside a run of ties.
+    # Brute force: every element of the full matrix as (FP32 magnitude,
+    # position), a stable sort, the first k marked; an entry (both copies of
+    # an off-diagonal one) is dropped iff all its copies are marked.
+    t = wl.film(6, 4, 1)
+    N = oracle.demag_tensor(t.centre, t.edge)
+    n = t.n
+    elems = []
+    for i in range(n):
+        for j in range(n):
+            for e in range(6):
+                v = abs(float(np.float32(N[i, j, e])))
+                if v > 0:
+                    for c in range(int(oracle._MULT[e])):
+                        elems.append((v, len(elems), (i, j, e)))
+    order = sorted(elems, key=lambda x: (x[0], x[1]))
+    ties_at_cut = 0
+    for f in (0.1, 0.25, 0.5, 0.7):
+        k = int(f * len(elems))
+        marked = {}
+        for rank, (v, _, ent) in enumerate(order):
+            marked.setdefault(ent, []).append(rank < k)
+        ties_at_cut += sum(1 for x in order if x[0] == order[k][0])
+        Nt, thr, kept = oracle.threshold_tensor(N, f)
+        assert thr == order[k][0]
+        for (i, j, e), flags in marked.items():
+            assert (Nt[i, j, e] == 0) == all(flags), (f, i, j, e, flags)
+            if not all(flags):
+                assert Nt[i, j, e] == N[i, j, e]
+        assert kept == sum(len(fl) for fl in marked.values() if not all(fl))
+    assert ties_at_cut > 8  # the case does exercise ties

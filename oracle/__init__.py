@@ -347,3 +347,50 @@ def threshold_tensor(N, fraction):
     out = np.where(keep, N, 0.0)
     kept = int((keep.reshape(-1, 6) * _MULT).sum())
     return out, float(t), kept
+
+
+def hysteresis(model: Model, m0, H, direction, opts, t_step, gamma=2.211e5, alpha=4000.0, form=1, precess=0):
+    """Sec. 4.1 (standard problem 2): the applied field takes the values
+    H[s] * direction (A/m) in turn; at each value the state, carried over
+    from the previous one, is evolved for t_step seconds (the paper holds
+    every field value for a fixed time; LL form with the precession term
+    dropped and a large damping, as there).  Returns (status, <m> at the end
+    of each value (S, 3), final state)."""
+    d = np.asarray(direction, np.float64)
+    d = d / np.linalg.norm(d)
+    m = np.asarray(m0, np.float64).reshape(-1, 3).copy()
+    out = np.zeros((len(H), 3))
+    t = 0.0
+    for s, h in enumerate(H):
+        p = llg_params(gamma=gamma, alpha=alpha, Ha=h * d, form=form, precess=precess)
+        st, m, mav, _ = integrate(model, m, p, opts, t, t + t_step, 1)
+        if st != OK:
+            return st, out, m
+        out[s] = model.mean_m(m)
+        t += t_step
+    return OK, out, m
+
+
+def loop_summary(H, mavg, direction):
+    """Coercivity and remanence of a descending branch (Sec. 4.1): the field
+    at which the projection of <m> on the field direction first changes
+    sign, linearly interpolated between the two field values around it (nan
+    if it never does), and <m> at H = 0, interpolated likewise (nan if the
+    schedule does not cross zero)."""
+    d = np.asarray(direction, np.float64)
+    d = d / np.linalg.norm(d)
+    H = np.asarray(H, np.float64)
+    mavg = np.asarray(mavg, np.float64).reshape(-1, 3)
+    proj = mavg @ d
+    hc = float("nan")
+    for s in range(1, len(H)):
+        if proj[s - 1] > 0 >= proj[s]:
+            hc = H[s - 1] + (H[s] - H[s - 1]) * proj[s - 1] / (proj[s - 1] - proj[s])
+            break
+    mr = np.full(3, np.nan)
+    for s in range(1, len(H)):
+        if H[s - 1] >= 0 >= H[s] and H[s - 1] != H[s]:
+            w = H[s - 1] / (H[s - 1] - H[s])
+            mr = (1 - w) * mavg[s - 1] + w * mavg[s]
+            break
+    return float(hc), mr

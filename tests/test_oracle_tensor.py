@@ -311,3 +311,21 @@ def test_threshold_ties_brute_force():
                 assert Nt[i, j, e] == N[i, j, e]
         assert kept == sum(len(fl) for fl in marked.values() if not all(fl))
     assert ties_at_cut > 8  # the case does exercise ties
+
+
+def test_scaled_geometry_tensor_and_exchange():
+    # the point tensor depends only on shape ratios: scaling every centre and
+    # edge by lam leaves N unchanged, while the exchange field scales as
+    # lam^-2 (a size sweep, e.g. the d/l_ex axis of standard problem 2,
+    # keeps one tensor and changes the exchange stiffness by lam^-2)
+    t = wl.graded_film(6, 4, 2, size=(60e-9, 40e-9, 6e-9), seed=5)
+    lam = 3.7
+    N1 = oracle.demag_tensor(t.centre, t.edge)
+    N2 = oracle.demag_tensor(lam * t.centre, lam * t.edge)
+    assert np.abs(N1 - N2).max() <= 1e-12 * np.abs(N1).max()
+    m = wl.m_random(t.n, seed=3)
+    md1 = oracle.Model.from_tiles(t)
+    md2 = oracle.Model(lam * t.centre, lam * t.edge, t.Ms, t.Aex, t.Ku, t.axis, t.nbr, N=N1)
+    H1 = oracle.exchange_field(md1, m)
+    H2 = oracle.exchange_field(md2, m)
+    np.testing.assert_allclose(H2, H1 / lam ** 2, rtol=1e-12, atol=1e-12 * np.abs(H1).max())

@@ -566,6 +566,70 @@ def run_threshold(args):
     print(json.dumps(line), flush=True)
 
 
+def run_hysteresis(args):
+    """Standard problem 2 (Sec. 4.1): film L x L/5 x L/50 as 100 x 20 x 3
+    tiles (n = 6,000), field along [1,1,1] descending from 0.08 Ms to -0.08 Ms
+    in 4,000 steps, each value held 40 ns, LL form with the precession term
+    dropped and alpha = 4000, as the paper.  One tensor serves the whole
+    d / l_ex sweep (the point tensor is scale-invariant; exchange enters as
+    (d_ref / d)^2), so the B = 8 films d / l_ex = 10 ... 45 run as one batch.
+    Timed: the first `--values` values of the paper's schedule for each
+    product (FP32 streaming, split BF16 and BF16 on the tensor cores); then a
+    coarse loop (17 values, relaxed to torque 1e-3 or 40 ns) for the
+    coercivity and remanence of each film."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2107_05364_gb300 import binding as mt
+    t = wl.sp2_film(100, 20, 3, d_lex=10.0)
+    ctx = mt.mt_ctx_create(0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    d_lex = np.array([10.0, 15.0, 20.0, 25.0, 30.0, 35.0, 40.0, 45.0])
+    B = len(d_lex)
+    H = wl.sp2_fields(4001)
+    opts = mt.ode_opts(rtol=1e-5, atol=1e-5, h0=1e-14, hmax=1e-10)
+    m0 = np.tile(wl.m_noisy(t.n, wl.SP2_DIR, 1e-3, seed=0).astype(np.float32).ravel(), B)
+    K = args.values
+    rows = []
+    for prec, layout in (("f32", 0), ("split", 1), ("bf16", 1)):
+        T = mt.mt_demag_assemble_ex(tiles, prec, layout)
+        p, keep = mt.llg_params(B, alpha=4000.0, form=mt.MT_FORM_LL, precess=0, exch_scale=(10.0 / d_lex) ** 2)
+        I = mt.Integrator(T, p, opts, B=B)
+        I.set_state(m0)
+        I.hysteresis(wl.SP2_DIR, H[:1], 1e-12)  # warm-up: graph, first products
+        I.set_state(m0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mavg, tau, hc, mr, st = I.hysteresis(wl.SP2_DIR, H[:K], 40e-9)
+        wall = time.perf_counter() - t0
+        rhs = sum(x["n_rhs"] for x in st)
+        rows.append({"product": "%s_%s" % (prec, "dense" if layout else "stream"), "wall_s": wall,
+                     "values_x_sims_per_s": K * B / wall, "rhs_evals_per_s": rhs / wall,
+                     "attempts_stiffest": st[0]["n_accept"] + st[0]["n_reject"],
+                     "full_loop_hours": wall / K * len(H) / 3600.0})
+        I.close()
+        T.close()
+    # coarse loop for coercivity and remanence (split BF16 products)
+    T = mt.mt_demag_assemble_ex(tiles, "split", 1)
+    p, keep = mt.llg_params(B, alpha=4000.0, form=mt.MT_FORM_LL, precess=0, exch_scale=(10.0 / d_lex) ** 2)
+    I = mt.Integrator(T, p, opts, B=B)
+    I.set_state(m0)
+    Hc = wl.sp2_fields(args.coarse)
+    t0 = time.perf_counter()
+    mavg, tau, hc, mr, st = I.hysteresis(wl.SP2_DIR, Hc, 40e-9, tol=1e-3)
+    coarse_wall = time.perf_counter() - t0
+    loop = [{"d_lex": float(d_lex[b]), "hc_over_Ms": float(-hc[b] / wl.SP4_MS), "mr": [float(x) for x in mr[b]]}
+            for b in range(B)]
+    best = max(rows, key=lambda r: r["values_x_sims_per_s"])
+    line = {"metric": "SP2 hysteresis field values x films per second (40 ns per value)",
+            "value": best["values_x_sims_per_s"], "unit": "values*films/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "sp2_film_100x20x3_n6000_B8_dlex10-45", "tiles": t.n, "films": B,
+                       "values_timed": K, "product": best["product"]},
+            "rows": rows, "coarse_loop": {"values": int(args.coarse), "tol": 1e-3, "wall_s": coarse_wall,
+                                          "films": loop}}
+    print(json.dumps(line), flush=True)
+
+
 def mt_pad(B):
     bp = 16
     while bp < B and bp < 128:
@@ -581,7 +645,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
-    ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold"])
+    ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold", "hysteresis"])
+    ap.add_argument("--values", type=int, default=2, help="hysteresis: field values of the paper's schedule timed")
+    ap.add_argument("--coarse", type=int, default=17, help="hysteresis: values of the coarse loop")
     ap.add_argument("--requests", type=int, default=120)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--t-cap", type=float, default=100e-12)
@@ -598,6 +664,8 @@ def main():
         run_serving(args)
     elif args.workload == "threshold":
         run_threshold(args)
+    elif args.workload == "hysteresis":
+        run_hysteresis(args)
     else:
         run_ours(args)
 

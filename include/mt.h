@@ -100,6 +100,11 @@ typedef struct {
   const double *Ha;    /* [3B] applied field per simulation, A/m (Eq. 7)      */
   int form;            /* mt_form                                             */
   int precess;         /* 1 = full equation, 0 = drop the m x H term           */
+  const double *exch_scale; /* [B] factor on every tile's exchange stiffness A */
+                       /* per simulation (NULL: 1).  The point tensor depends */
+                       /* only on shape ratios, so the same tiles scaled by   */
+                       /* lam behave as the originals with A / lam^2: a size  */
+                       /* sweep (d / l_ex, Sec. 4.1) shares one tensor        */
 } mt_llg_params;
 
 /* Runge-Kutta (4,5) options (Dormand-Prince pair, Sec. 3.1). */
@@ -273,8 +278,8 @@ MT_API mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m
                      float *tau, void *stream);
 
 /* Micromagnetic energy (Eq. 4 with the densities of Eqs. 6, 8, 11, 15) of B
- * states m (DEVICE, B*3n floats), with the applied fields p->Ha (only Ha is
- * read).  E (HOST, 5 doubles per simulation, J): total, Zeeman, demag,
+ * states m (DEVICE, B*3n floats), with the applied fields p->Ha and the
+ * exchange factors p->exch_scale (nothing else is read).  E (HOST, 5 doubles per simulation, J): total, Zeeman, demag,
  * exchange, anisotropy; each quadratic term is -(mu0 Ms / 2) m.H of its
  * field, summed over tiles with their volumes.  Synchronous.
  * Errors: MT_EINVAL, MT_ECUDA. */
@@ -330,6 +335,29 @@ MT_API mt_status mt_integrator_run(mt_integrator *I, double t1, int64_t n_out, d
  * max_i |m_i x H_eff,i| / Ms_i < tol, or report MT_ENOCONV once the time
  * t_max is spent.  Synchronous. */
 MT_API mt_status mt_integrator_relax(mt_integrator *I, double tol, double t_max, mt_stats *stats);
+
+/* Hysteresis loop (Sec. 4.1, micromagnetic standard problem 2).  For
+ * s = 0 .. S-1 the applied field of simulation b is H[s] * dir_b (H: HOST,
+ * S values in A/m; dir: HOST, 3B components, normalised here), replacing
+ * the Ha of the parameters; then the batch is relaxed at that field, the
+ * state carried over from the previous value: for t_step seconds of
+ * simulated time when tol = 0 (the paper holds every value for a fixed
+ * time), or until max_i |m_i x H_eff,i| / Ms_i < tol with t_step as the cap
+ * when tol > 0 (reaching the cap is not an error; the torque is reported).
+ * The rest of the equation is the integrator's (the paper: LL form, the
+ * precession term dropped, a large damping).
+ * Outputs (HOST, each may be NULL): mavg [S][B][3], the volume-averaged m at
+ * the end of each value; tau [S][B], the torque there; hc [B], the field
+ * (A/m, along dir) at which the projection of <m> on dir first changes sign
+ * from positive, interpolated linearly between the two values around it
+ * (NaN if it never does); mr [B][3], <m> at H = 0, interpolated between the
+ * two values around the first crossing of zero (NaN if none); stats [B], the
+ * counters at the end.  Synchronous.
+ * Errors: MT_EINVAL, MT_ENONFINITE, MT_ENOCONV (the step cap of the options
+ * ran out before a value was done), MT_ETIMEOUT, MT_ECUDA. */
+MT_API mt_status mt_integrator_hysteresis(mt_integrator *I, const double *dir, const double *H, int64_t S,
+                                          double t_step, double tol, double *mavg, double *tau, double *hc,
+                                          double *mr, mt_stats *stats);
 
 /* Per-simulation counters since the last set_state.  Synchronous. */
 MT_API mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats);

@@ -32,7 +32,7 @@ class MtError(RuntimeError):
 
 class LlgParams(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("alpha", ctypes.c_void_p), ("Ha", ctypes.c_void_p),
-                ("form", ctypes.c_int), ("precess", ctypes.c_int)]
+                ("form", ctypes.c_int), ("precess", ctypes.c_int), ("exch_scale", ctypes.c_void_p)]
 
 
 class OdeOpts(ctypes.Structure):
@@ -121,6 +121,7 @@ _SIGS = {
     "mt_integrator_step": (_I, [_P, _I64]),
     "mt_integrator_run": (_I, [_P, _D, _I64, _P, _P]),
     "mt_integrator_relax": (_I, [_P, _D, _D, _P]),
+    "mt_integrator_hysteresis": (_I, [_P, _P, _P, _I64, _D, _D, _P, _P, _P, _P, _P]),
     "mt_integrator_stats": (_I, [_P, _P]),
     "mt_integrate": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _P, _I, _D, _D, _I64, _P, _P,
                           _P]),
@@ -279,12 +280,16 @@ class TensorH:
             pass
 
 
-def llg_params(B: int, gamma=2.211e5, alpha=0.02, Ha=(0.0, 0.0, 0.0), form=MT_FORM_GILBERT, precess=1):
+def llg_params(B: int, gamma=2.211e5, alpha=0.02, Ha=(0.0, 0.0, 0.0), form=MT_FORM_GILBERT, precess=1,
+               exch_scale=None):
     """Returns (LlgParams, keep-alive arrays)."""
     a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float64), (B,)))
     h = np.ascontiguousarray(np.broadcast_to(np.asarray(Ha, np.float64).reshape(-1, 3), (B, 3)))
-    p = LlgParams(float(gamma), a.ctypes.data, h.ctypes.data, int(form), int(precess))
-    return p, (a, h)
+    x = None if exch_scale is None else np.ascontiguousarray(
+        np.broadcast_to(np.asarray(exch_scale, np.float64), (B,)))
+    p = LlgParams(float(gamma), a.ctypes.data, h.ctypes.data, int(form), int(precess),
+                  None if x is None else x.ctypes.data)
+    return p, (a, h, x)
 
 
 def ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11, max_steps=10_000_000, fixed_h=0.0):
@@ -434,6 +439,21 @@ class Integrator:
         if check:
             _check(s, "mt_integrator_relax")
         return s, [x.as_dict() for x in st]
+
+    def hysteresis(self, direction, H, t_step: float, tol: float = 0.0):
+        """Field schedule H[s] * direction_b (A/m), relaxed at each value;
+        returns (mavg (S, B, 3), tau (S, B), hc (B,), mr (B, 3), stats)."""
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(direction, np.float64).reshape(-1, 3), (self.B, 3)))
+        H = np.ascontiguousarray(H, np.float64).ravel()
+        S = H.size
+        mavg = np.zeros((S, self.B, 3))
+        tau = np.zeros((S, self.B))
+        hc = np.zeros(self.B)
+        mr = np.zeros((self.B, 3))
+        st = (Stats * self.B)()
+        _check(lib().mt_integrator_hysteresis(self.h, _ptr(d), _ptr(H), S, float(t_step), float(tol), _ptr(mavg),
+                                              _ptr(tau), _ptr(hc), _ptr(mr), st), "mt_integrator_hysteresis")
+        return mavg, tau, hc, mr, [x.as_dict() for x in st]
 
     def stats(self):
         st = (Stats * self.B)()

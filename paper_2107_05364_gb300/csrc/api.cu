@@ -408,16 +408,18 @@ mt_status mt_llg_rhs(mt_tensor *T, const mt_llg_params *p, const float *m, int B
   mt_status st = ensure_workspace(T, B);
   if (st != MT_OK) return st;
   std::vector<float> g1, g2, ha;
-  mt::llg_prefactors(p, B, g1, g2, ha);
+  std::vector<float> xsc;
+  mt::llg_prefactors(p, B, g1, g2, ha, xsc);
   float *d_par = nullptr;
-  MT_CUDA(cudaMalloc(&d_par, sizeof(float) * 5 * B));
+  MT_CUDA(cudaMalloc(&d_par, sizeof(float) * 6 * B));
   cudaStream_t s = (cudaStream_t)stream;
   MT_CUDA(cudaMemcpyAsync(d_par, g1.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
   MT_CUDA(cudaMemcpyAsync(d_par + B, g2.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
   MT_CUDA(cudaMemcpyAsync(d_par + 2 * B, ha.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice, s));
+  MT_CUDA(cudaMemcpyAsync(d_par + 5 * B, xsc.data(), sizeof(float) * B, cudaMemcpyHostToDevice, s));
   if ((st = demag_apply(T, m, B, T->d_Hd, s)) != MT_OK) return st;
   if (tau) MT_CUDA(cudaMemsetAsync(tau, 0, sizeof(float) * B, s));
-  mt::launch_rhs_plain(T, m, T->d_Hd, B, d_par, d_par + B, d_par + 2 * B, dmdt, tau, s);
+  mt::launch_rhs_plain(T, m, T->d_Hd, B, d_par, d_par + B, d_par + 2 * B, d_par + 5 * B, dmdt, tau, s);
   MT_CUDA(cudaGetLastError());
   // the parameter block must outlive the kernels
   MT_CUDA(cudaStreamSynchronize(s));
@@ -474,16 +476,17 @@ extern "C" mt_status mt_energy(mt_tensor *T, const mt_llg_params *p, const float
   mt_status st = ensure_workspace(T, B);
   if (st != MT_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  std::vector<float> ha(3 * B);
+  std::vector<float> ha(4 * B);  // Ha, then the exchange factors
   for (int q = 0; q < 3 * B; ++q) ha[q] = (float)p->Ha[q];
+  for (int b = 0; b < B; ++b) ha[3 * B + b] = p->exch_scale ? (float)p->exch_scale[b] : 1.0f;
   float *d_ha = nullptr;
   double *d_E = nullptr;
-  MT_CUDA(cudaMalloc(&d_ha, sizeof(float) * 3 * B));
+  MT_CUDA(cudaMalloc(&d_ha, sizeof(float) * 4 * B));
   MT_CUDA(cudaMalloc(&d_E, sizeof(double) * 4 * B));
-  MT_CUDA(cudaMemcpyAsync(d_ha, ha.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice, s));
+  MT_CUDA(cudaMemcpyAsync(d_ha, ha.data(), sizeof(float) * 4 * B, cudaMemcpyHostToDevice, s));
   MT_CUDA(cudaMemsetAsync(d_E, 0, sizeof(double) * 4 * B, s));
   if ((st = demag_apply(T, m, B, T->d_Hd, s)) != MT_OK) return st;
-  mt::launch_energy(T, m, T->d_Hd, B, d_ha, d_E, s);
+  mt::launch_energy(T, m, T->d_Hd, B, d_ha, d_ha + 3 * B, d_E, s);
   MT_CUDA(cudaGetLastError());
   std::vector<double> e4(4 * B);
   MT_CUDA(cudaMemcpyAsync(e4.data(), d_E, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, s));

@@ -15,6 +15,7 @@
 // The host only replays the graph and polls a counter of unfinished
 // simulations every few steps.
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -48,6 +49,7 @@ __constant__ double c_dp_err[7] = {35.0 / 384 - 5179.0 / 57600,
 struct SimCtl {
   double t, h, hs, t_next, t_out0, dt_out, t1, tol;
   double tau, err;
+  double m_last[3];  // volume-averaged m after the last accepted step
   int64_t iout, n_out;
   int64_t n_accept, n_reject, n_rhs, n_attempt, attempt_cap;
   int mode;      // 0 = fixed number of steps, 1 = integrate to t1, 2 = relax
@@ -70,6 +72,7 @@ struct StageArgs {
   bool exch;
   // per-simulation equation parameters
   const float *g1, *g2, *Ha;
+  const float *xsc;  // [B] factor on the exchange stiffness (nullptr: 1)
   // state
   float *y, *ys0, *ys1, *Hd, *xs;
   float *k[7];
@@ -113,16 +116,21 @@ __device__ __forceinline__ void effective_field(const StageArgs &A, const float 
   H[2] = hd[2] + ha[2];
   if (A.exch) {
     const float *yb = yin + (size_t)b * 3 * A.n;
+    float he[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
       const int32_t p = A.nbr[6 * i + f];
       if (p >= 0) {
         const float w = A.wex[6 * i + f];
-        H[0] += w * (yb[3 * p] - mi[0]);
-        H[1] += w * (yb[3 * p + 1] - mi[1]);
-        H[2] += w * (yb[3 * p + 2] - mi[2]);
+        he[0] += w * (yb[3 * p] - mi[0]);
+        he[1] += w * (yb[3 * p + 1] - mi[1]);
+        he[2] += w * (yb[3 * p + 2] - mi[2]);
       }
     }
+    const float xs = A.xsc ? A.xsc[b] : 1.0f;
+    H[0] += xs * he[0];
+    H[1] += xs * he[1];
+    H[2] += xs * he[2];
   }
   const float ka = A.kan[i];
   if (ka != 0.0f) {
@@ -417,6 +425,9 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
         c.n_accept += 1;
         c.t = c.clipped ? c.t_next : c.t + c.hs;
         c.tau = tau;
+        c.m_last[0] = tot[2];
+        c.m_last[1] = tot[3];
+        c.m_last[2] = tot[4];
         if (c.mode == MODE_RUN && c.clipped) {
           double *mo = A.mavg + ((size_t)c.iout * A.B + b) * 3;
           mo[0] = tot[2];
@@ -465,7 +476,7 @@ __global__ void k_admit(SimCtl *ctl, int *active, int *n_active, int b, SimCtl c
 //   e_i = -mu0 Ms_i V_i m_i.(Ha + (H_d + H_ex + H_an)/2)  split by term.
 __global__ void k_energy(int64_t n, const int32_t *nbr, const float *wex, const float *kan, const float *axis,
                          const float *Ms, const double *wvol, double vol_total, bool exch, const float *m,
-                         const float *Hd, const float *Ha, double *E) {
+                         const float *Hd, const float *Ha, const float *xsc, double *E) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   double e[4] = {0, 0, 0, 0};
@@ -480,6 +491,7 @@ __global__ void k_energy(int64_t n, const int32_t *nbr, const float *wex, const 
         if (p < 0) continue;
         for (int c = 0; c < 3; ++c) hex[c] += (double)wex[6 * i + f] * ((double)mb[3 * p + c] - (double)mi[c]);
       }
+      for (int c = 0; c < 3; ++c) hex[c] *= (double)xsc[b];
     }
     const double me = (double)mi[0] * axis[3 * i] + (double)mi[1] * axis[3 * i + 1] + (double)mi[2] * axis[3 * i + 2];
     for (int c = 0; c < 3; ++c) han[c] = (double)kan[i] * me * axis[3 * i + c];
@@ -507,7 +519,7 @@ __global__ void k_energy(int64_t n, const int32_t *nbr, const float *wex, const 
 // standalone right-hand side: dmdt and per-simulation max torque
 __global__ void k_rhs_plain(int64_t n, const int32_t *nbr, const float *wex, const float *kan, const float *axis,
                             const float *Ms, bool exch, const float *m, const float *Hd, const float *g1,
-                            const float *g2, const float *Ha, float *dmdt, float *tau) {
+                            const float *g2, const float *Ha, const float *xsc, float *dmdt, float *tau) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (i >= n) return;
@@ -519,6 +531,7 @@ __global__ void k_rhs_plain(int64_t n, const int32_t *nbr, const float *wex, con
   A.axis = axis;
   A.exch = exch;
   A.Ha = Ha;
+  A.xsc = xsc;
   const size_t o = (size_t)b * 3 * n + 3 * i;
   const float mi[3] = {m[o], m[o + 1], m[o + 2]};
   float H[3], k[3];
@@ -538,26 +551,27 @@ __global__ void k_rhs_plain(int64_t n, const int32_t *nbr, const float *wex, con
 namespace mt {
 
 void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B, const float *g1,
-                      const float *g2, const float *Ha, float *dmdt, float *tau, cudaStream_t s) {
+                      const float *g2, const float *Ha, const float *xsc, float *dmdt, float *tau, cudaStream_t s) {
   const mt_tiles *t = T->tiles;
   dim3 grid((unsigned)((T->n + 255) / 256), (unsigned)B);
   k_rhs_plain<<<grid, 256, 0, s>>>(T->n, t->d_nbr, t->d_wex, t->d_kan, t->d_axis, t->d_Ms, t->has_exchange, m, Hd,
-                                   g1, g2, Ha, dmdt, tau);
+                                   g1, g2, Ha, xsc, dmdt, tau);
 }
 
-void launch_energy(const mt_tensor *T, const float *m, const float *Hd, int B, const float *Ha, double *E,
-                   cudaStream_t s) {
+void launch_energy(const mt_tensor *T, const float *m, const float *Hd, int B, const float *Ha, const float *xsc,
+                   double *E, cudaStream_t s) {
   const mt_tiles *t = T->tiles;
   dim3 grid((unsigned)((T->n + 255) / 256), (unsigned)B);
   k_energy<<<grid, 256, 0, s>>>(T->n, t->d_nbr, t->d_wex, t->d_kan, t->d_axis, t->d_Ms, t->d_wvol, t->vol_total,
-                                t->has_exchange, m, Hd, Ha, E);
+                                t->has_exchange, m, Hd, Ha, xsc, E);
 }
 
 void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::vector<float> &g2,
-                    std::vector<float> &ha) {
+                    std::vector<float> &ha, std::vector<float> &xsc) {
   g1.resize(B);
   g2.resize(B);
   ha.resize(3 * B);
+  xsc.resize(B);
   for (int b = 0; b < B; ++b) {
     const double a = p->alpha[b];
     double G1, G2;
@@ -572,6 +586,7 @@ void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::
     g1[b] = (float)G1;
     g2[b] = (float)G2;
     for (int c = 0; c < 3; ++c) ha[3 * b + c] = (float)p->Ha[3 * b + c];
+    xsc[b] = p->exch_scale ? (float)p->exch_scale[b] : 1.0f;
   }
 }
 
@@ -589,7 +604,7 @@ struct mt_integrator {
   // device state
   float *y = nullptr, *ys0 = nullptr, *ys1 = nullptr, *Hd = nullptr, *xs = nullptr;
   float *k[7] = {};
-  float *g1 = nullptr, *g2 = nullptr, *Ha = nullptr;
+  float *g1 = nullptr, *g2 = nullptr, *Ha = nullptr, *xsc = nullptr;
   float *part = nullptr;
   int *count = nullptr;
   SimCtl *ctl = nullptr;
@@ -627,6 +642,7 @@ StageArgs stage_args(mt_integrator *I) {
   A.g1 = I->g1;
   A.g2 = I->g2;
   A.Ha = I->Ha;
+  A.xsc = I->xsc;
   A.y = I->y;
   A.ys0 = I->ys0;
   A.ys1 = I->ys1;
@@ -862,6 +878,7 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
   MT_TRY(dalloc(I, &I->g1, sizeof(float) * B));
   MT_TRY(dalloc(I, &I->g2, sizeof(float) * B));
   MT_TRY(dalloc(I, &I->Ha, sizeof(float) * 3 * B));
+  MT_TRY(dalloc(I, &I->xsc, sizeof(float) * B));
   MT_TRY(dalloc(I, &I->part, dense ? mt::dense_part_bytes(T, B) : mt::matvec_part_bytes(T)));
   MT_TRY(dalloc(I, &I->count, dense ? mt::dense_count_bytes(T) : mt::matvec_count_bytes(T, B)));
   MT_TRY(dalloc(I, &I->ctl, sizeof(SimCtl) * B));
@@ -919,11 +936,14 @@ void mt_integrator_destroy(mt_integrator *I) {
 
 mt_status mt_integrator_set_params(mt_integrator *I, const mt_llg_params *p) {
   MT_CHECK(I && p && p->alpha && p->Ha, MT_EINVAL, "mt_integrator_set_params: NULL argument");
-  std::vector<float> g1, g2, ha;
-  mt::llg_prefactors(p, I->B, g1, g2, ha);
+  std::vector<float> g1, g2, ha, xsc;
+  mt::llg_prefactors(p, I->B, g1, g2, ha, xsc);
+  for (int b = 0; b < I->B; ++b)
+    MT_CHECK(std::isfinite(xsc[b]) && xsc[b] >= 0.0f, MT_EINVAL, "mt_integrator_set_params: bad exch_scale");
   MT_CUDA(cudaMemcpyAsync(I->g1, g1.data(), sizeof(float) * I->B, cudaMemcpyHostToDevice, I->stream));
   MT_CUDA(cudaMemcpyAsync(I->g2, g2.data(), sizeof(float) * I->B, cudaMemcpyHostToDevice, I->stream));
   MT_CUDA(cudaMemcpyAsync(I->Ha, ha.data(), sizeof(float) * 3 * I->B, cudaMemcpyHostToDevice, I->stream));
+  MT_CUDA(cudaMemcpyAsync(I->xsc, xsc.data(), sizeof(float) * I->B, cudaMemcpyHostToDevice, I->stream));
   MT_CUDA(cudaStreamSynchronize(I->stream));
   I->need_init = true;
   return MT_OK;
@@ -993,8 +1013,10 @@ mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps) {
   return enqueue_commit(I);
 }
 
+// cap_ok: in relax mode a simulation that reached its time cap with the
+// torque above tol counts as finished (hysteresis values)
 static mt_status run_common(mt_integrator *I, int mode, double t1, int64_t n_out, double tol, double *mavg,
-                            mt_stats *stats) {
+                            mt_stats *stats, bool cap_ok = false, std::vector<SimCtl> *out_ctl = nullptr) {
   std::vector<SimCtl> c;
   mt_status st = read_ctl(I, c);
   if (st != MT_OK) return st;
@@ -1049,11 +1071,13 @@ static mt_status run_common(mt_integrator *I, int mode, double t1, int64_t n_out
     MT_CUDA(cudaMemcpy(mavg, I->mavg, sizeof(double) * 3 * I->B * n_out, cudaMemcpyDeviceToHost));
   }
   fill_stats(c, stats, I->B);
+  if (out_ctl) *out_ctl = c;
   for (int b = 0; b < I->B; ++b) {
     if (!c[b].done) {
       mt::set_error("integrator: simulation %d not finished", b);
       return MT_ENOCONV;
     }
+    if (cap_ok && c[b].status == MT_ENOCONV && c[b].t >= c[b].t1) continue;
     if (c[b].status != MT_OK) {
       mt::set_error("integrator: simulation %d ended with status %d", b, c[b].status);
       return (mt_status)c[b].status;
@@ -1070,6 +1094,73 @@ mt_status mt_integrator_run(mt_integrator *I, double t1, int64_t n_out, double *
 mt_status mt_integrator_relax(mt_integrator *I, double tol, double t_max, mt_stats *stats) {
   MT_CHECK(I && tol > 0 && t_max > 0, MT_EINVAL, "mt_integrator_relax: bad argument");
   return run_common(I, MODE_RELAX, t_max, 1, tol, nullptr, stats);
+}
+
+mt_status mt_integrator_hysteresis(mt_integrator *I, const double *dir, const double *H, int64_t S, double t_step,
+                                   double tol, double *mavg, double *tau, double *hc, double *mr, mt_stats *stats) {
+  MT_CHECK(I && dir && H && S >= 1 && t_step > 0 && tol >= 0, MT_EINVAL, "mt_integrator_hysteresis: bad argument");
+  const int B = I->B;
+  std::vector<double> d(3 * B);
+  for (int b = 0; b < B; ++b) {
+    const double nrm = std::sqrt(dir[3 * b] * dir[3 * b] + dir[3 * b + 1] * dir[3 * b + 1] +
+                                 dir[3 * b + 2] * dir[3 * b + 2]);
+    MT_CHECK(std::isfinite(nrm) && nrm > 0, MT_EINVAL, "mt_integrator_hysteresis: direction %d is zero", b);
+    for (int c = 0; c < 3; ++c) d[3 * b + c] = dir[3 * b + c] / nrm;
+  }
+  for (int64_t s = 0; s < S; ++s)
+    MT_CHECK(std::isfinite(H[s]), MT_EINVAL, "mt_integrator_hysteresis: non-finite field value");
+  std::vector<double> pm(3 * B * (size_t)S), pt(B * (size_t)S);
+  std::vector<float> ha(3 * B);
+  std::vector<SimCtl> c;
+  mt_status st0 = read_ctl(I, c);
+  if (st0 != MT_OK) return st0;
+  double t_end = 0.0;  // fixed-time values: every simulation ends on the same times
+  for (int b = 0; b < B; ++b) t_end = std::max(t_end, c[b].t);
+  for (int64_t s = 0; s < S; ++s) {
+    for (int q = 0; q < 3 * B; ++q) ha[q] = (float)(H[s] * d[q]);
+    MT_CUDA(cudaMemcpyAsync(I->Ha, ha.data(), sizeof(float) * 3 * B, cudaMemcpyHostToDevice, I->stream));
+    MT_CUDA(cudaStreamSynchronize(I->stream));
+    I->need_init = true;  // k1 belongs to the previous field
+    t_end += t_step;
+    mt_status st = tol > 0 ? run_common(I, MODE_RELAX, t_step, 1, tol, nullptr, stats, true, &c)
+                           : run_common(I, MODE_RUN, t_end, 1, 0.0, nullptr, stats, false, &c);
+    if (st != MT_OK) return st;
+    for (int b = 0; b < B; ++b) {
+      for (int q = 0; q < 3; ++q) pm[((size_t)s * B + b) * 3 + q] = c[b].m_last[q];
+      pt[(size_t)s * B + b] = c[b].tau;
+    }
+  }
+  if (mavg) std::memcpy(mavg, pm.data(), sizeof(double) * pm.size());
+  if (tau) std::memcpy(tau, pt.data(), sizeof(double) * pt.size());
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  for (int b = 0; b < B; ++b) {
+    auto proj = [&](int64_t s) {
+      const double *m = &pm[((size_t)s * B + b) * 3];
+      return m[0] * d[3 * b] + m[1] * d[3 * b + 1] + m[2] * d[3 * b + 2];
+    };
+    if (hc) {
+      hc[b] = nan;
+      for (int64_t s = 1; s < S; ++s) {
+        const double p0 = proj(s - 1), p1 = proj(s);
+        if (p0 > 0 && p1 <= 0) {
+          hc[b] = H[s - 1] + (H[s] - H[s - 1]) * p0 / (p0 - p1);
+          break;
+        }
+      }
+    }
+    if (mr) {
+      for (int q = 0; q < 3; ++q) mr[3 * b + q] = nan;
+      for (int64_t s = 1; s < S; ++s) {
+        if (H[s - 1] >= 0 && H[s] <= 0 && H[s - 1] != H[s]) {
+          const double w = H[s - 1] / (H[s - 1] - H[s]);
+          for (int q = 0; q < 3; ++q)
+            mr[3 * b + q] = (1 - w) * pm[((size_t)(s - 1) * B + b) * 3 + q] + w * pm[((size_t)s * B + b) * 3 + q];
+          break;
+        }
+      }
+    }
+  }
+  return MT_OK;
 }
 
 mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats) {

@@ -215,16 +215,16 @@ mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out);
 
 // per-simulation prefactors of Eq. 1: g1 (precession), g2 (damping), Ha
 void llg_prefactors(const mt_llg_params *p, int B, std::vector<float> &g1, std::vector<float> &g2,
-                    std::vector<float> &ha);
+                    std::vector<float> &ha, std::vector<float> &xsc);
 
 // energy terms (Eqs. 4, 6, 8, 11, 15) per simulation, accumulated into
 // E[b*4 + {0: Zeeman, 1: demag, 2: exchange, 3: anisotropy}] (device, zeroed)
-void launch_energy(const mt_tensor *T, const float *m, const float *Hd, int B, const float *Ha, double *E,
-                   cudaStream_t s);
+void launch_energy(const mt_tensor *T, const float *m, const float *Hd, int B, const float *Ha, const float *xsc,
+                   double *E, cudaStream_t s);
 
 // standalone right-hand side
 void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B, const float *g1,
-                      const float *g2, const float *Ha, float *dmdt, float *tau, cudaStream_t s);
+                      const float *g2, const float *Ha, const float *xsc, float *dmdt, float *tau, cudaStream_t s);
 
 }  // namespace mt
 

@@ -125,6 +125,22 @@ def exchange_length(Ms=SP4_MS, Aex=SP4_AEX) -> float:
     return math.sqrt(Aex / (0.5 * MU0 * Ms * Ms))
 
 
+def sp2_film(nx=100, ny=20, nz=3, d_lex=10.0, Ms=SP4_MS, Aex=SP4_AEX) -> Tiles:
+    """Standard problem 2 film (Sec. 4.1): length L, width d = L / 5,
+    thickness t = d / 10, with d = d_lex exchange lengths; no anisotropy."""
+    d = d_lex * exchange_length(Ms, Aex)
+    return film(nx, ny, nz, size=(5.0 * d, d, 0.1 * d), Ms=Ms, Aex=Aex, Ku=0.0)
+
+
+def sp2_fields(S=4001, h_max=0.08, Ms=SP4_MS) -> np.ndarray:
+    """Descending field values of standard problem 2 (Sec. 4.1): from
+    +h_max Ms to -h_max Ms in S - 1 equal steps, A/m."""
+    return np.linspace(h_max, -h_max, S) * Ms
+
+
+SP2_DIR = (1.0, 1.0, 1.0)  # the field direction of standard problem 2
+
+
 def cube(nside=20, L_lex=20.0, Ms=SP4_MS, Aex=SP4_AEX, ku_frac=0.1) -> Tiles:
     """Standard problem 3 cube (Sec. 4.2): edge L_lex exchange lengths,
     K_u = ku_frac * K_m along z."""

@@ -394,3 +394,35 @@ def loop_summary(H, mavg, direction):
             mr = (1 - w) * mavg[s - 1] + w * mavg[s]
             break
     return float(hc), mr
+
+
+def crossover(centre, edge, Ms, Aex, Ku, axis, nbr, lam, mA, mB, params, opts, tol, t_max):
+    """Sec. 4.2 (standard problem 3): for each size lam[k] the body is
+    really scaled (centres and edges times lam[k], its tensor recomputed),
+    states A and B are relaxed (torque below tol or t_max, which counts as
+    done), and their energy densities E / V (J/m^3) compared.  Returns
+    (eA, eB, lam at which eA - eB first changes sign, linear between the two
+    sizes around it (nan if none), relaxed states)."""
+    K = len(lam)
+    eA, eB = np.zeros(K), np.zeros(K)
+    states = []
+    for k, lk in enumerate(lam):
+        md = Model(lk * np.asarray(centre), lk * np.asarray(edge), Ms, Aex, Ku, axis, nbr)
+        V = md.volume.sum()
+        for m0, out in ((mA, eA), (mB, eB)):
+            st, m, _ = relax(md, m0, params, opts, tol, t_max)
+            if st not in (OK, ENOCONV):
+                raise RuntimeError("oracle relax failed with status %d" % st)
+            out[k] = energy(md, m, params)["total"] / V
+            states.append(m)
+    return eA, eB, first_crossing(lam, eA, eB), states
+
+
+def first_crossing(x, a, b):
+    """The x at which a - b first changes sign, linear between the two
+    samples around it (nan if it never does)."""
+    for k in range(1, len(x)):
+        d0, d1 = a[k - 1] - b[k - 1], a[k] - b[k]
+        if (d0 < 0) != (d1 < 0):
+            return float(x[k - 1] + (x[k] - x[k - 1]) * d0 / (d0 - d1))
+    return float("nan")

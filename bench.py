@@ -630,6 +630,73 @@ def run_hysteresis(args):
     print(json.dumps(line), flush=True)
 
 
+def run_crossover(args):
+    """Standard problem 3 (Sec. 4.2): cube with K_u = 0.1 K_m along z, the
+    size at which the flower and the vortex state have equal energy, at
+    several resolutions N^3, extrapolated by a fit L_cross = a N^b + c (the
+    paper: c = L_inf = 8.477 +- 0.007 l_ex).  For each N one tensor serves all
+    sizes (exchange factors), and each scan relaxes flower seeds (along z) and
+    vortex seeds (core along x, across the easy axis; a core along z unwinds
+    into the twisted flower at these sizes) at 8 sizes as one batch of 16 on
+    the tensor cores (split BF16): a coarse scan
+    over 7.5 ... 9.5 l_ex, then a fine one over +-0.15 l_ex around its
+    crossing."""
+    import torch
+    from scipy.optimize import curve_fit
+    torch.cuda.set_device(0)
+    from paper_2107_05364_gb300 import binding as mt
+    ctx = mt.mt_ctx_create(0)
+    opts = mt.ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-10)
+    res = [int(x) for x in args.resolutions.split(",")]
+    rows = []
+    t_all = time.perf_counter()
+    for N in res:
+        t = wl.cube(N, 1.0)
+        tiles = mt.mt_tiles_create(ctx, t)
+        tw = time.perf_counter()
+        T = mt.mt_demag_assemble_ex(tiles, "split", 1)
+        t_asm = time.perf_counter() - tw
+        p, keep = mt.llg_params(16, alpha=4000.0, form=mt.MT_FORM_LL, precess=0)
+        I = mt.Integrator(T, p, opts, B=16)
+        lam = np.linspace(7.5, 9.5, 8)
+        tw = time.perf_counter()
+        eA, eB, lc, _, st = I.crossover(lam, wl.m_flower(t), wl.m_vortex(t, axis=0), 1e-4, 20e-9)
+        rhs = sum(x["n_rhs"] for x in st)
+        if not np.isfinite(lc):
+            rows.append({"N": N, "tiles": t.n, "crossing": None})
+            continue
+        lam2 = np.linspace(lc - 0.15, lc + 0.15, 8)
+        eA2, eB2, lc2, _, st2 = I.crossover(lam2, wl.m_flower(t), wl.m_vortex(t, axis=0), 1e-4, 20e-9)
+        wall = time.perf_counter() - tw
+        rhs += sum(x["n_rhs"] for x in st2)
+        km = 0.5 * MU0 * float(t.Ms[0]) ** 2
+        rows.append({"N": N, "tiles": t.n, "crossing": lc2 if np.isfinite(lc2) else lc, "coarse_crossing": lc,
+                     "assemble_s": t_asm, "scan_s": wall, "rhs_evals": rhs, "rhs_evals_per_s": rhs / wall,
+                     "e_flower_at_crossing_over_Km": float(np.interp(lc2, lam2, eA2) / km)
+                     if np.isfinite(lc2) else None})
+        I.close()
+        T.close()
+        print("N=%d: crossing %.4f l_ex (%.1f s)" % (N, rows[-1]["crossing"], wall), file=sys.stderr, flush=True)
+    total = time.perf_counter() - t_all
+    ok = [r for r in rows if r.get("crossing") is not None]
+    fit = None
+    if len(ok) >= 4:
+        x = np.array([r["N"] for r in ok], np.float64)
+        y = np.array([r["crossing"] for r in ok])
+        try:
+            popt, pcov = curve_fit(lambda n, a, b, c: a * n ** b + c, x, y, p0=(1.0, -1.0, 8.5), maxfev=20000)
+            fit = {"a": float(popt[0]), "b": float(popt[1]), "L_inf": float(popt[2]),
+                   "L_inf_sigma": float(np.sqrt(pcov[2, 2])), "paper_L_inf": 8.477, "paper_sigma": 0.007}
+        except RuntimeError as e:
+            fit = {"error": str(e)}
+    line = {"metric": "SP3 flower/vortex crossover", "value": fit["L_inf"] if fit and "L_inf" in fit else None,
+            "unit": "l_ex (L_inf of the fit)", "n_gpus": 1, "higher_is_better": None, "data": "synthetic",
+            "config": {"workload": "sp3_cube_N%s_split_dense" % "-".join(map(str, res)), "sizes_per_scan": 8,
+                       "scans_per_N": 2},
+            "wall_s": total, "rows": rows, "fit": fit}
+    print(json.dumps(line), flush=True)
+
+
 def mt_pad(B):
     bp = 16
     while bp < B and bp < 128:
@@ -645,7 +712,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
-    ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold", "hysteresis"])
+    ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold", "hysteresis",
+                                                                   "crossover"])
+    ap.add_argument("--resolutions", default="8,10,12,16,20,24", help="crossover: cube tiles per edge")
     ap.add_argument("--values", type=int, default=2, help="hysteresis: field values of the paper's schedule timed")
     ap.add_argument("--coarse", type=int, default=17, help="hysteresis: values of the coarse loop")
     ap.add_argument("--requests", type=int, default=120)
@@ -666,6 +735,8 @@ def main():
         run_threshold(args)
     elif args.workload == "hysteresis":
         run_hysteresis(args)
+    elif args.workload == "crossover":
+        run_crossover(args)
     else:
         run_ours(args)
 

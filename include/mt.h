@@ -359,6 +359,26 @@ MT_API mt_status mt_integrator_hysteresis(mt_integrator *I, const double *dir, c
                                           double t_step, double tol, double *mavg, double *tau, double *hc,
                                           double *mr, mt_stats *stats);
 
+/* Energy crossover of two families of states over a size sweep (Sec. 4.2,
+ * micromagnetic standard problem 3: the flower and the vortex state of a
+ * cube).  The integrator must hold B = 2K simulations.  Size k is lam[k]
+ * times the tiles' own size; since the point tensor depends only on shape
+ * ratios it enters as the exchange factor 1 / lam[k]^2 (this replaces the
+ * parameters' exch_scale).  Simulation k starts from mA and K + k from mB
+ * (HOST, 3n floats each), the time is reset to 0, and all are relaxed until
+ * max_i |m_i x H_eff,i| / Ms_i < tol or t_max (reaching t_max is not an
+ * error; stats tells).  eA, eB (HOST, K each, may be NULL) get the energy
+ * densities (total energy over the tiles' volume, J/m^3, which is the same
+ * for the really scaled body); lam_cross (may be NULL) the size at which
+ * eA - eB first changes sign, linear between the two sizes around it (NaN
+ * if it never does; sizes in increasing order); m_out (HOST, 3nB floats,
+ * may be NULL) the relaxed states.  Synchronous.
+ * Errors: MT_EINVAL, MT_ENONFINITE, MT_ENOCONV (step cap), MT_ETIMEOUT,
+ * MT_ECUDA. */
+MT_API mt_status mt_integrator_crossover(mt_integrator *I, const double *lam, int K, const float *mA,
+                                         const float *mB, double tol, double t_max, double *eA, double *eB,
+                                         double *lam_cross, float *m_out, mt_stats *stats);
+
 /* Per-simulation counters since the last set_state.  Synchronous. */
 MT_API mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats);
 

@@ -122,6 +122,7 @@ _SIGS = {
     "mt_integrator_run": (_I, [_P, _D, _I64, _P, _P]),
     "mt_integrator_relax": (_I, [_P, _D, _D, _P]),
     "mt_integrator_hysteresis": (_I, [_P, _P, _P, _I64, _D, _D, _P, _P, _P, _P, _P]),
+    "mt_integrator_crossover": (_I, [_P, _P, _I, _P, _P, _D, _D, _P, _P, _P, _P, _P]),
     "mt_integrator_stats": (_I, [_P, _P]),
     "mt_integrate": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _P, _I, _D, _D, _I64, _P, _P,
                           _P]),
@@ -454,6 +455,22 @@ class Integrator:
         _check(lib().mt_integrator_hysteresis(self.h, _ptr(d), _ptr(H), S, float(t_step), float(tol), _ptr(mavg),
                                               _ptr(tau), _ptr(hc), _ptr(mr), st), "mt_integrator_hysteresis")
         return mavg, tau, hc, mr, [x.as_dict() for x in st]
+
+    def crossover(self, lam, mA, mB, tol: float, t_max: float, states: bool = False):
+        """Relax families A and B at sizes lam (B = 2K); returns (eA, eB
+        (J/m^3), lam_cross, relaxed states (B, n, 3) or None, stats)."""
+        lam = np.ascontiguousarray(lam, np.float64).ravel()
+        K = lam.size
+        mA = np.ascontiguousarray(mA, np.float32).ravel()
+        mB = np.ascontiguousarray(mB, np.float32).ravel()
+        eA, eB = np.zeros(K), np.zeros(K)
+        lc = ctypes.c_double(0.0)
+        mo = np.empty((self.B, self.n, 3), np.float32) if states else None
+        st = (Stats * self.B)()
+        _check(lib().mt_integrator_crossover(self.h, _ptr(lam), K, _ptr(mA), _ptr(mB), float(tol), float(t_max),
+                                             _ptr(eA), _ptr(eB), ctypes.byref(lc), _ptr(mo), st),
+               "mt_integrator_crossover")
+        return eA, eB, lc.value, mo, [x.as_dict() for x in st]
 
     def stats(self):
         st = (Stats * self.B)()

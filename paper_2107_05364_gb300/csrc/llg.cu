@@ -1163,6 +1163,79 @@ mt_status mt_integrator_hysteresis(mt_integrator *I, const double *dir, const do
   return MT_OK;
 }
 
+mt_status mt_integrator_crossover(mt_integrator *I, const double *lam, int K, const float *mA, const float *mB,
+                                  double tol, double t_max, double *eA, double *eB, double *lam_cross,
+                                  float *m_out, mt_stats *stats) {
+  MT_CHECK(I && lam && mA && mB && K >= 1 && tol > 0 && t_max > 0, MT_EINVAL,
+           "mt_integrator_crossover: bad argument");
+  MT_CHECK(I->B == 2 * K, MT_EINVAL, "mt_integrator_crossover: the integrator must hold 2K = %d simulations", 2 * K);
+  for (int k = 0; k < K; ++k)
+    MT_CHECK(std::isfinite(lam[k]) && lam[k] > 0, MT_EINVAL, "mt_integrator_crossover: sizes must be positive");
+  const int64_t n = I->T->n;
+  const int B = I->B;
+  // sizes enter as exchange factors (the point tensor is scale-invariant)
+  std::vector<float> xsc(B);
+  for (int k = 0; k < K; ++k) xsc[k] = xsc[K + k] = (float)(1.0 / (lam[k] * lam[k]));
+  MT_CUDA(cudaMemcpyAsync(I->xsc, xsc.data(), sizeof(float) * B, cudaMemcpyHostToDevice, I->stream));
+  // state: family A at every size, then family B
+  std::vector<float> m0((size_t)3 * n * B);
+  for (int k = 0; k < K; ++k) {
+    std::memcpy(&m0[(size_t)3 * n * k], mA, sizeof(float) * 3 * n);
+    std::memcpy(&m0[(size_t)3 * n * (K + k)], mB, sizeof(float) * 3 * n);
+  }
+  mt_status st = mt_integrator_set_state(I, m0.data(), 1, 0.0);
+  if (st != MT_OK) return st;
+  if ((st = run_common(I, MODE_RELAX, t_max, 1, tol, nullptr, stats, true)) != MT_OK) return st;
+  // energies of the relaxed states: demag product of y for every simulation
+  // (finished ones are inactive after the relaxation), then the densities
+  {
+    std::vector<int> act(B, 1);
+    MT_CUDA(cudaMemcpyAsync(I->active, act.data(), sizeof(int) * B, cudaMemcpyHostToDevice, I->stream));
+    MT_CUDA(cudaMemcpyAsync(I->n_active, &B, sizeof(int), cudaMemcpyHostToDevice, I->stream));
+    MT_CUDA(cudaStreamSynchronize(I->stream));
+  }
+  double *d_E = nullptr;
+  MT_CUDA(cudaMalloc(&d_E, sizeof(double) * 4 * B));
+  cudaError_t e = cudaMemsetAsync(d_E, 0, sizeof(double) * 4 * B, I->stream);
+  if (e == cudaSuccess) {
+    if (I->T->layout == MT_LAYOUT_DENSE)
+      mt::launch_prep_dense_x(I->T, I->y, B, I->xs, I->stream);
+    else
+      mt::launch_prep_xs(I->T, I->y, B, I->xs, I->stream);
+    demag(I, I->y);
+    mt::launch_energy(I->T, I->y, I->Hd, B, I->Ha, I->xsc, d_E, I->stream);
+    e = cudaGetLastError();
+  }
+  std::vector<double> e4(4 * B);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(e4.data(), d_E, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess && m_out)
+    e = cudaMemcpyAsync(m_out, I->y, sizeof(float) * 3 * n * B, cudaMemcpyDeviceToHost, I->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+  cudaFree(d_E);
+  if (e != cudaSuccess) return mt::cuda_fail(e, "mt_integrator_crossover", __FILE__, __LINE__);
+  I->need_init = true;  // the workspace now holds the relaxed state's product
+  const double vol = I->T->tiles->vol_total;
+  std::vector<double> ea(K), eb(K);
+  for (int k = 0; k < K; ++k) {
+    ea[k] = (e4[4 * k] + e4[4 * k + 1] + e4[4 * k + 2] + e4[4 * k + 3]) / vol;
+    eb[k] = (e4[4 * (K + k)] + e4[4 * (K + k) + 1] + e4[4 * (K + k) + 2] + e4[4 * (K + k) + 3]) / vol;
+  }
+  if (eA) std::memcpy(eA, ea.data(), sizeof(double) * K);
+  if (eB) std::memcpy(eB, eb.data(), sizeof(double) * K);
+  if (lam_cross) {
+    *lam_cross = std::numeric_limits<double>::quiet_NaN();
+    for (int k = 1; k < K; ++k) {
+      const double d0 = ea[k - 1] - eb[k - 1], d1 = ea[k] - eb[k];
+      if ((d0 < 0) != (d1 < 0)) {
+        *lam_cross = lam[k - 1] + (lam[k] - lam[k - 1]) * d0 / (d0 - d1);
+        break;
+      }
+    }
+  }
+  return MT_OK;
+}
+
 mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats) {
   MT_CHECK(I && stats, MT_EINVAL, "mt_integrator_stats: NULL argument");
   std::vector<SimCtl> c;

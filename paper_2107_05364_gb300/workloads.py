@@ -195,14 +195,19 @@ def m_flower(t: Tiles, seed=0) -> np.ndarray:
     return m_noisy(t.n, (0, 0, 1), 0.1, seed, 3)
 
 
-def m_vortex(t: Tiles, core_lex=1.0) -> np.ndarray:
-    c = t.centre
-    x0, y0 = c[:, 0].mean(), c[:, 1].mean()
+def m_vortex(t: Tiles, core_lex=1.0, axis=2) -> np.ndarray:
+    """Vortex seed: m circulates about the line through the body's centre
+    along coordinate `axis` (0, 1, 2 = x, y, z), with a core of radius
+    core_lex exchange lengths pointing along +axis."""
+    c = t.centre - t.centre.mean(0)
+    u, v = (axis + 1) % 3, (axis + 2) % 3
     rc = core_lex * exchange_length(float(t.Ms[0]), float(t.Aex[0]))
-    dx, dy = c[:, 0] - x0, c[:, 1] - y0
-    rho2 = dx * dx + dy * dy
-    v = np.stack([-dy, dx, rc * np.exp(-rho2 / (rc * rc))], axis=1)
-    return _normalise(v)
+    rho2 = c[:, u] ** 2 + c[:, v] ** 2
+    m = np.zeros_like(c)
+    m[:, u] = -c[:, v]
+    m[:, v] = c[:, u]
+    m[:, axis] = rc * np.exp(-rho2 / (rc * rc))
+    return _normalise(m)
 
 
 # ---------------------------------------------------------------------------

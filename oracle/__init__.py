@@ -63,7 +63,8 @@ class _Model(ctypes.Structure):
                 ("centre", ctypes.c_void_p), ("edge", ctypes.c_void_p),
                 ("Ms", ctypes.c_void_p), ("Aex", ctypes.c_void_p),
                 ("Ku", ctypes.c_void_p), ("axis", ctypes.c_void_p),
-                ("nbr", ctypes.c_void_p), ("N", ctypes.c_void_p)]
+                ("nbr", ctypes.c_void_p), ("N", ctypes.c_void_p),
+                ("xw", ctypes.c_void_p), ("vol", ctypes.c_void_p)]
 
 
 class _Llg(ctypes.Structure):
@@ -142,6 +143,65 @@ def demag_tensor(centre, edge) -> np.ndarray:
     return out
 
 
+def tetra_point_tensor(r, verts, full=False) -> np.ndarray:
+    """Tensor of the uniformly magnetised tetrahedron verts (4, 3) at r:
+    (3, 3) if full, else the 6 entries of its symmetric part."""
+    r = np.ascontiguousarray(r, np.float64)
+    v = np.ascontiguousarray(verts, np.float64).reshape(12)
+    if full:
+        out = np.empty(9)
+        lib().or_tetra_point_tensor_full(_p(r), _p(v), _p(out))
+        return out.reshape(3, 3)
+    out = np.empty(6)
+    lib().or_tetra_point_tensor(_p(r), _p(v), _p(out))
+    return out
+
+
+def tetra_demag_tensor(verts) -> np.ndarray:
+    """(n, n, 6) tensor of tetrahedral tiles verts (n, 4, 3) at their centroids."""
+    v = np.ascontiguousarray(verts, np.float64).reshape(-1, 12)
+    n = v.shape[0]
+    N = np.empty((n, n, 6))
+    lib().or_tetra_demag_tensor(ctypes.c_int64(n), _p(v), _p(N))
+    return N
+
+
+def tetra_model(verts, tets, Ms, Aex, Ku, axis, N=None):
+    """Oracle model of tetrahedral tiles: vertices (nv, 3), tets (n, 4)
+    vertex indices.  Centroids, volumes, the tensor (Sec. 3) and the
+    two-point-flux exchange coefficients area / (V_i d_ip) over shared faces
+    (d_ip the centroid distance along the face normal; a face on the
+    boundary carries no flux)."""
+    verts = np.asarray(verts, np.float64)
+    tets = np.asarray(tets, np.int64)
+    n = tets.shape[0]
+    P = verts[tets]  # (n, 4, 3)
+    cen = P.mean(axis=1)
+    vol = np.abs(np.einsum("ij,ij->i", P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6
+    faces = {}
+    for i in range(n):
+        for f in range(4):
+            key = tuple(sorted(int(tets[i, k]) for k in range(4) if k != f))
+            faces.setdefault(key, []).append((i, f))
+    nbr = -np.ones((n, 6), np.int32)
+    xw = np.zeros((n, 6))
+    for key, owners in faces.items():
+        if len(owners) != 2:
+            continue
+        a, b, c = verts[list(key)]
+        nrm = np.cross(b - a, c - a)
+        area = 0.5 * np.linalg.norm(nrm)
+        nrm = nrm / np.linalg.norm(nrm)
+        (i, fi), (j, fj) = owners
+        d = abs(np.dot(cen[j] - cen[i], nrm))
+        nbr[i, fi], nbr[j, fj] = j, i
+        xw[i, fi] = area / (vol[i] * d)
+        xw[j, fj] = area / (vol[j] * d)
+    if N is None:
+        N = tetra_demag_tensor(P)
+    return Model(cen, None, Ms, Aex, Ku, axis, nbr, N=N, xw=xw, vol=vol)
+
+
 def demag_blocks(centre, edge, pairs) -> np.ndarray:
     c = np.ascontiguousarray(centre, np.float64).reshape(-1)
     e = np.ascontiguousarray(edge, np.float64).reshape(-1)
@@ -180,10 +240,15 @@ def demag_field_rows(centre, edge, Ms, m, rows) -> np.ndarray:
 class Model:
     """Tiles + stored FP64 tensor.  Arrays are kept alive by this object."""
 
-    def __init__(self, centre, edge, Ms, Aex, Ku, axis, nbr=None, N=None):
+    def __init__(self, centre, edge, Ms, Aex, Ku, axis, nbr=None, N=None, xw=None, vol=None):
+        """Cuboid tiles (centre, edge), or any tiles with their tensor N,
+        volumes vol and exchange face coefficients xw (6 per tile, 1/m^2)."""
         self.centre = np.ascontiguousarray(centre, np.float64).reshape(-1, 3)
         self.n = self.centre.shape[0]
-        self.edge = np.ascontiguousarray(edge, np.float64).reshape(-1, 3)
+        self.edge = np.ascontiguousarray(edge if edge is not None else np.ones((self.n, 3)),
+                                         np.float64).reshape(-1, 3)
+        self.xw = None if xw is None else np.ascontiguousarray(xw, np.float64).reshape(-1, 6)
+        self.vol = None if vol is None else np.ascontiguousarray(vol, np.float64).reshape(-1)
         self.Ms = np.ascontiguousarray(np.broadcast_to(Ms, (self.n,)), np.float64)
         self.Aex = np.ascontiguousarray(np.broadcast_to(Aex, (self.n,)), np.float64)
         self.Ku = np.ascontiguousarray(np.broadcast_to(Ku, (self.n,)), np.float64)
@@ -193,7 +258,8 @@ class Model:
         self.N = demag_tensor(self.centre, self.edge) if N is None else np.ascontiguousarray(N, np.float64)
         self._s = _Model(self.n, _p(self.centre), _p(self.edge), _p(self.Ms), _p(self.Aex),
                          _p(self.Ku), _p(self.axis), _p(self.nbr) if self.nbr is not None else None,
-                         _p(self.N))
+                         _p(self.N), _p(self.xw) if self.xw is not None else None,
+                         _p(self.vol) if self.vol is not None else None)
 
     @classmethod
     def from_tiles(cls, tiles, N=None):
@@ -204,7 +270,7 @@ class Model:
 
     @property
     def volume(self):
-        return np.prod(self.edge, axis=1)
+        return self.vol if self.vol is not None else np.prod(self.edge, axis=1)
 
     def mean_m(self, m):
         m = np.asarray(m, np.float64).reshape(-1, 3)

@@ -16,6 +16,8 @@
  * Parts and the passage each follows:
  *   - cuboid point tensor ........ Sec. 3 (tiles, Smith et al. closed form),
  *                                   Eq. 9 read as H_d = -N (Ms m)
+ *   - tetrahedron point tensor ... Sec. 3 (tetrahedron tiles), from the
+ *                                   surface charges of a uniform body
  *   - demag field ................ Eq. 9/10, Sec. 3.1 Eq. 17 (dense product)
  *   - exchange field ............. Eq. 12, Neumann boundary from Eq. 3,
  *                                   3-point stencil of Sec. 4.1
@@ -208,6 +210,135 @@ static void or_block_apply(const double *N6, const double *x, double *acc) {
  *   H_d,i = - sum_j N_ij (Ms_j m_j),  all j including j = i.
  * m is tile-major (m[3j + c]).
  */
+/* ------------------------------------------------------------------------ */
+/* Tetrahedron tile (Sec. 3: the tensor of a uniformly magnetised            */
+/* tetrahedron is known in closed form; the paper cites it, not prints it)  */
+/* ------------------------------------------------------------------------ */
+/*
+ * Written here from the surface-charge form of the field.  A body of uniform
+ * magnetisation M carries the charge density M.n_f on each plane face f
+ * (outward unit normal n_f), so
+ *     H(r) = -(1/4 pi) sum_f (M . n_f) G_f(r),   G_f(r) = grad_r int_f dS'/|r - r'|,
+ * and with H = -N M:   N_ab(r) = (1/4 pi) sum_f G_f,a(r) n_f,b.
+ * Splitting r - r' into the height h = (r - r').n_f and in-plane parts, the
+ * normal part of G_f is -n_f int_f h/R^3 dS' = -n_f Omega_f(r) (the solid
+ * angle of the face seen from r, signed like h), and by the 2-D gradient
+ * theorem the in-plane part is -sum_e u_e int_e dl'/R, u_e the in-plane unit
+ * normal pointing out of the face across edge e.  For the edge p1 -> p2 with
+ * unit tangent t and s_k = (p_k - r).t, R_k = |p_k - r|:
+ *     int_e dl'/R = ln((R2 + s2)/(R1 + s1)) = ln((R1 - s1)/(R2 - s2)),
+ * the second form used when the first would cancel (s1 + s2 < 0).
+ * The solid angle of a triangle is taken from the formula of Van Oosterom
+ * and Strackee (1983):
+ *     tan(Omega/2) = a.(b x c) / (|a||b||c| + (a.b)|c| + (a.c)|b| + (b.c)|a|),
+ * a, b, c the vertices relative to r; with the vertices counter-clockwise
+ * about n_f the triple product is -h times a positive quantity, hence the sign.
+ * Outside the body the solid angles cancel and tr N = 0; inside they add up
+ * to -4 pi and tr N = 1.
+ */
+static double or_dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void or_cross3(const double *a, const double *b, double *c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double or_edge_integral(const double *r, const double *p1, const double *p2) {
+  double t[3], d1[3], d2[3];
+  for (int c = 0; c < 3; c++) {
+    t[c] = p2[c] - p1[c];
+    d1[c] = p1[c] - r[c];
+    d2[c] = p2[c] - r[c];
+  }
+  double len = sqrt(or_dot3(t, t));
+  for (int c = 0; c < 3; c++) t[c] /= len;
+  double s1 = or_dot3(d1, t), s2 = or_dot3(d2, t);
+  double R1 = sqrt(or_dot3(d1, d1)), R2 = sqrt(or_dot3(d2, d2));
+  if (s1 + s2 >= 0) return log((R2 + s2) / (R1 + s1));
+  return log((R1 - s1) / (R2 - s2));
+}
+
+/* int over the triangle (v0, v1, v2) of h/R^3, vertices counter-clockwise
+   about the face normal, h = (r - v0).n */
+static double or_triangle_solid_angle(const double *r, const double *v0, const double *v1, const double *v2) {
+  double a[3], b[3], c[3], bc[3];
+  for (int k = 0; k < 3; k++) {
+    a[k] = v0[k] - r[k];
+    b[k] = v1[k] - r[k];
+    c[k] = v2[k] - r[k];
+  }
+  or_cross3(b, c, bc);
+  double num = or_dot3(a, bc);
+  double la = sqrt(or_dot3(a, a)), lb = sqrt(or_dot3(b, b)), lc = sqrt(or_dot3(c, c));
+  double den = la * lb * lc + or_dot3(a, b) * lc + or_dot3(a, c) * lb + or_dot3(b, c) * la;
+  return -2.0 * atan2(num, den);
+}
+
+/* full 3x3 point tensor (row-major) of the tetrahedron v[0..11] at r */
+void or_tetra_point_tensor_full(const double *r, const double *v, double *N9) {
+  for (int k = 0; k < 9; k++) N9[k] = 0.0;
+  for (int f = 0; f < 4; f++) {
+    /* face opposite vertex f, oriented so that its normal points away from it */
+    const double *p[3];
+    int q = 0;
+    for (int k = 0; k < 4; k++)
+      if (k != f) p[q++] = &v[3 * k];
+    double e1[3], e2[3], nrm[3], w[3];
+    for (int c = 0; c < 3; c++) {
+      e1[c] = p[1][c] - p[0][c];
+      e2[c] = p[2][c] - p[0][c];
+      w[c] = v[3 * f + c] - p[0][c];
+    }
+    or_cross3(e1, e2, nrm);
+    if (or_dot3(nrm, w) > 0) { /* reverse the order: counter-clockwise about the outward normal */
+      const double *tmp = p[1];
+      p[1] = p[2];
+      p[2] = tmp;
+      for (int c = 0; c < 3; c++) nrm[c] = -nrm[c];
+    }
+    double ln = sqrt(or_dot3(nrm, nrm));
+    for (int c = 0; c < 3; c++) nrm[c] /= ln;
+    double G[3];
+    double om = or_triangle_solid_angle(r, p[0], p[1], p[2]);
+    for (int c = 0; c < 3; c++) G[c] = -nrm[c] * om;
+    for (int e = 0; e < 3; e++) {
+      const double *a = p[e], *b = p[(e + 1) % 3];
+      double t[3], u[3];
+      for (int c = 0; c < 3; c++) t[c] = b[c] - a[c];
+      or_cross3(t, nrm, u); /* in-plane, pointing out of the face for counter-clockwise edges */
+      double lu = sqrt(or_dot3(u, u));
+      double L = or_edge_integral(r, a, b);
+      for (int c = 0; c < 3; c++) G[c] -= u[c] / lu * L;
+    }
+    for (int a = 0; a < 3; a++)
+      for (int b = 0; b < 3; b++) N9[3 * a + b] += G[a] * nrm[b] / (4.0 * OR_PI);
+  }
+}
+
+/* the 6 unique entries (xx, xy, xz, yy, yz, zz) of the symmetrised tensor */
+void or_tetra_point_tensor(const double *r, const double *v, double *N6) {
+  double N9[9];
+  or_tetra_point_tensor_full(r, v, N9);
+  N6[0] = N9[0];
+  N6[1] = 0.5 * (N9[1] + N9[3]);
+  N6[2] = 0.5 * (N9[2] + N9[6]);
+  N6[3] = N9[4];
+  N6[4] = 0.5 * (N9[5] + N9[7]);
+  N6[5] = N9[8];
+}
+
+/* full tensor of a tetrahedral tile set, evaluated at the centroids */
+void or_tetra_demag_tensor(int64_t n, const double *v, double *N) {
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; i++) {
+    double r[3];
+    for (int c = 0; c < 3; c++)
+      r[c] = 0.25 * (v[12 * i + c] + v[12 * i + 3 + c] + v[12 * i + 6 + c] + v[12 * i + 9 + c]);
+    for (int64_t j = 0; j < n; j++) or_tetra_point_tensor(r, &v[12 * j], &N[(i * n + j) * 6]);
+  }
+}
+
 void or_demag_field_dense(int64_t n, const double *N, const double *Ms, const double *m, double *H) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; i++) {
@@ -254,6 +385,9 @@ typedef struct {
   const double *axis;   /* 3n, unit easy axis */
   const int32_t *nbr;   /* 6n: -x,+x,-y,+y,-z,+z face neighbour, -1 = none; may be NULL */
   const double *N;      /* n*n*6 stored tensor */
+  const double *xw;     /* 6n face coefficients area/(V_i d_ip), 1/m^2, replacing the
+                           Cartesian 1/(h_i d_ip) (unstructured tiles); may be NULL */
+  const double *vol;    /* n tile volumes replacing the edge products; may be NULL */
 } or_model;
 
 typedef struct {
@@ -272,7 +406,10 @@ typedef struct {
  *     H_ex,i = (2 A_i/(mu0 Ms_i)) sum_p (m_p - m_i) / (h_i d_ip),
  * h_i the tile's edge along that axis.  On a uniform grid this is the
  * 3-point stencil of Sec. 4.1.  A missing neighbour contributes no flux,
- * which is the Neumann condition dm/dn = 0 of Eq. 3.
+ * which is the Neumann condition dm/dn = 0 of Eq. 3.  For unstructured
+ * tiles (tetrahedra) the same two-point flux is used with the face
+ * coefficient area_f / (V_i d_ip) given per face (d_ip the centre distance
+ * along the face normal); the paper leaves that operator to later work.
  */
 void or_exchange_field(const or_model *md, const double *m, double *H) {
   int64_t n = md->n;
@@ -283,10 +420,15 @@ void or_exchange_field(const or_model *md, const double *m, double *H) {
     for (int f = 0; f < 6; f++) {
       int32_t p = md->nbr[6 * i + f];
       if (p < 0) continue;
-      int ax = f / 2;
-      double d = fabs(md->centre[3 * p + ax] - md->centre[3 * i + ax]);
-      double h = md->edge[3 * i + ax];
-      for (int c = 0; c < 3; c++) H[3 * i + c] += pref * (m[3 * p + c] - m[3 * i + c]) / (h * d);
+      double w;
+      if (md->xw) {
+        w = md->xw[6 * i + f];
+      } else {
+        int ax = f / 2;
+        double d = fabs(md->centre[3 * p + ax] - md->centre[3 * i + ax]);
+        w = 1.0 / (md->edge[3 * i + ax] * d);
+      }
+      for (int c = 0; c < 3; c++) H[3 * i + c] += pref * w * (m[3 * p + c] - m[3 * i + c]);
     }
   }
 }
@@ -378,7 +520,7 @@ void or_energy(const or_model *md, const or_llg *p, const double *m, double *out
   or_anisotropy_field(md, m, ha);
   double ez = 0, ed = 0, ex = 0, ea = 0;
   for (int64_t i = 0; i < n; i++) {
-    double V = md->edge[3 * i] * md->edge[3 * i + 1] * md->edge[3 * i + 2];
+    double V = md->vol ? md->vol[i] : md->edge[3 * i] * md->edge[3 * i + 1] * md->edge[3 * i + 2];
     double w = OR_MU0 * md->Ms[i] * V;
     for (int c = 0; c < 3; c++) {
       double mc = m[3 * i + c];

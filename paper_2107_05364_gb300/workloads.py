@@ -125,6 +125,35 @@ def exchange_length(Ms=SP4_MS, Aex=SP4_AEX) -> float:
     return math.sqrt(Aex / (0.5 * MU0 * Ms * Ms))
 
 
+def tetra_box(nx, ny, nz, size=(30e-9, 20e-9, 10e-9), jitter=0.0, seed=0):
+    """Tetrahedral tiles filling a box: an nx x ny x nz grid of cells, each
+    cut into the 6 tetrahedra of its Kuhn triangulation (all sharing the
+    cell diagonal, so the mesh is conforming); interior vertices moved by up
+    to `jitter` times the cell size (seeded) for an irregular mesh.  Returns
+    (vertices (nv, 3), tets (6 nx ny nz, 4) vertex indices)."""
+    gx, gy, gz = (np.linspace(0, L, k + 1) for L, k in zip(size, (nx, ny, nz)))
+    Z, Y, X = np.meshgrid(gz, gy, gx, indexing="ij")
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    if jitter > 0:
+        h = np.array([size[0] / nx, size[1] / ny, size[2] / nz])
+        u = uniform(seed, 11, verts.size).reshape(-1, 3)
+        interior = np.all((verts > 1e-12 * np.array(size)) & (verts < (1 - 1e-12) * np.array(size)), axis=1)
+        verts = verts + (interior[:, None] * jitter * h) * u
+    idx = lambda i, j, k: i + (nx + 1) * (j + (ny + 1) * k)
+    tets = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+                    p = [0, 0, 0]
+                    vs = [idx(i, j, k)]
+                    for a in perm:
+                        p[a] = 1
+                        vs.append(idx(i + p[0], j + p[1], k + p[2]))
+                    tets.append(vs)
+    return verts, np.array(tets, np.int32)
+
+
 def sp2_film(nx=100, ny=20, nz=3, d_lex=10.0, Ms=SP4_MS, Aex=SP4_AEX) -> Tiles:
     """Standard problem 2 film (Sec. 4.1): length L, width d = L / 5,
     thickness t = d / 10, with d = d_lex exchange lengths; no anisotropy."""

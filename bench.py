@@ -697,6 +697,63 @@ def run_crossover(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tetra(args):
+    """Tetrahedral tiles (Sec. 3): a box of 20 x 20 x 10 cells, 6 jittered
+    tetrahedra each (n = 24,000), against the cuboid film of the same tile
+    count: FP64 assembly rate of the face-charge tensor, the FP32 streaming
+    product on the tetrahedral tensor (the same kernel: layouts do not care
+    about the tile shape), and RHS evals/s of the integrator."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2107_05364_gb300 import binding as mt
+    ctx = mt.mt_ctx_create(0)
+    verts, tets = wl.tetra_box(20, 20, 10, size=(200e-9, 200e-9, 50e-9), jitter=0.1, seed=9)
+    n = len(tets)
+    out = {}
+    for name, make in (("tetra", lambda: mt.mt_tiles_create_tetra(ctx, verts, tets, wl.SP4_MS, wl.SP4_AEX, 0.0)),
+                       ("cuboid", lambda: mt.mt_tiles_create(ctx, wl.film(240, 100, 1, size=(600e-9, 250e-9,
+                                                                                              3e-9))))):
+        tiles = make()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        T = mt.mt_demag_assemble(tiles, "f32")
+        torch.cuda.synchronize()
+        t_asm = time.perf_counter() - t0
+        m = torch.tensor(wl.m_random(tiles.n, seed=1).astype(np.float32).ravel(), device="cuda")
+        H = torch.empty_like(m)
+        for _ in range(3):
+            mt.mt_demag_field(T, m, H)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(20):
+            mt.mt_demag_field(T, m, H)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        p, keep = mt.llg_params(1, alpha=0.1)
+        I = mt.Integrator(T, p, mt.ode_opts(rtol=1e-5, atol=1e-5, h0=1e-15, hmax=1e-11))
+        I.set_state(wl.m_noisy(tiles.n, (1, 1, 1), 1e-2, seed=1).astype(np.float32).ravel())
+        I.step(5)
+        torch.cuda.synchronize()
+        s = torch.cuda.ExternalStream(I.stream_handle())
+        e0.record(s)
+        I.step(100)
+        e1.record(s)
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / 100
+        out[name] = {"tiles": tiles.n, "assemble_s": t_asm, "blocks_per_s": tiles.n ** 2 / t_asm,
+                     "product_ms": ms, "product_gbs": 24.0 * tiles.n ** 2 / (ms * 1e-3) / 1e9,
+                     "rhs_evals_per_s": 6.0 / (step_ms * 1e-3)}
+        I.close()
+        T.close()
+    line = {"metric": "tetrahedral tiles: RHS evals/s", "value": out["tetra"]["rhs_evals_per_s"],
+            "unit": "RHS evals/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "tetra_box_20x20x10x6_n%d_f32" % n}, "tetra": out["tetra"],
+            "cuboid_same_n": out["cuboid"]}
+    print(json.dumps(line), flush=True)
+
+
 def mt_pad(B):
     bp = 16
     while bp < B and bp < 128:
@@ -713,7 +770,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
     ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold", "hysteresis",
-                                                                   "crossover"])
+                                                                   "crossover", "tetra"])
     ap.add_argument("--resolutions", default="8,10,12,16,20,24", help="crossover: cube tiles per edge")
     ap.add_argument("--values", type=int, default=2, help="hysteresis: field values of the paper's schedule timed")
     ap.add_argument("--coarse", type=int, default=17, help="hysteresis: values of the coarse loop")
@@ -737,6 +794,8 @@ def main():
         run_hysteresis(args)
     elif args.workload == "crossover":
         run_crossover(args)
+    elif args.workload == "tetra":
+        run_tetra(args)
     else:
         run_ours(args)
 

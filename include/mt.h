@@ -173,6 +173,24 @@ MT_API size_t mt_ctx_bytes_in_use(const mt_ctx *ctx);
 MT_API mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const double *edge,
                           const double *Ms, const double *Aex, const double *Ku, const double *axis,
                           const int32_t *nbr, mt_tiles **out);
+
+/* Create a tile set of n >= 1 tetrahedra (Sec. 3: tetrahedral tiles, whose
+ * tensor is known in closed form; evaluated here from the charges M.n of
+ * the four faces) from HOST arrays (copied): vertices[3 nv], tets[4n] vertex
+ * indices, Ms[n] (> 0), Aex[n], Ku[n], axis[3n].  The field point of a tile
+ * is its centroid.  Exchange (which the paper leaves to later work for
+ * unstructured tiles) is the two-point flux over shared faces:
+ *   H_ex,i = (2 A_i / (mu0 Ms_i)) sum_faces area / (V_i d_ip) (m_p - m_i),
+ * d_ip the centroid distance along the face normal; faces on the surface
+ * carry no flux (Eq. 3).  It is exact for uniform m and first-order only
+ * where the centroid line is normal to the face.  Two tiles sharing a vertex
+ * count as touching (kept in FP64 for the BF16 precisions).
+ * Errors: MT_EINVAL (index out of range, repeated vertex, degenerate tile,
+ * a face shared by three tiles, non-finite value), MT_ECUDA; assembly
+ * reports MT_EOVERLAP when a centroid lies in or on another tile. */
+MT_API mt_status mt_tiles_create_tetra(mt_ctx *ctx, int64_t nv, const double *vertices, int64_t n,
+                                       const int32_t *tets, const double *Ms, const double *Aex, const double *Ku,
+                                       const double *axis, mt_tiles **out);
 MT_API void mt_tiles_destroy(mt_tiles *tiles);
 
 /* ---------------------------------------------------------------------- */

@@ -166,6 +166,20 @@ def tetra_demag_tensor(verts) -> np.ndarray:
     return N
 
 
+def tetra_field_rows(verts, Ms, m, rows) -> np.ndarray:
+    """H_d at the centroids of tetrahedral tiles `rows` (verts (n, 4, 3)),
+    row by row without storing the tensor."""
+    v = np.ascontiguousarray(verts, np.float64).reshape(-1)
+    n = v.size // 12
+    Ms = np.ascontiguousarray(np.broadcast_to(Ms, (n,)), np.float64)
+    m = np.ascontiguousarray(m, np.float64).reshape(-1)
+    rows = np.ascontiguousarray(rows, np.int64)
+    H = np.empty(3 * rows.size)
+    lib().or_tetra_field_rows(ctypes.c_int64(n), _p(v), _p(Ms), _p(m), ctypes.c_int64(rows.size), _p(rows),
+                              _p(H))
+    return H.reshape(-1, 3)
+
+
 def tetra_model(verts, tets, Ms, Aex, Ku, axis, N=None):
     """Oracle model of tetrahedral tiles: vertices (nv, 3), tets (n, 4)
     vertex indices.  Centroids, volumes, the tensor (Sec. 3) and the

@@ -372,6 +372,28 @@ void or_demag_field_rows(int64_t n, const double *centre, const double *edge, co
   }
 }
 
+/* H_d at the centroids of the tetrahedral tiles `rows`, row by row (matrix-free) */
+void or_tetra_field_rows(int64_t n, const double *v, const double *Ms, const double *m, int64_t nrows,
+                         const int64_t *rows, double *H) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t r = 0; r < nrows; r++) {
+    int64_t i = rows[r];
+    double c[3];
+    for (int a = 0; a < 3; a++)
+      c[a] = 0.25 * (v[12 * i + a] + v[12 * i + 3 + a] + v[12 * i + 6 + a] + v[12 * i + 9 + a]);
+    double acc[3] = {0, 0, 0};
+    for (int64_t j = 0; j < n; j++) {
+      double N6[6];
+      or_tetra_point_tensor(c, &v[12 * j], N6);
+      double x[3] = {Ms[j] * m[3 * j], Ms[j] * m[3 * j + 1], Ms[j] * m[3 * j + 2]};
+      or_block_apply(N6, x, acc);
+    }
+    H[3 * r] = -acc[0];
+    H[3 * r + 1] = -acc[1];
+    H[3 * r + 2] = -acc[2];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Local fields                                                             */
 /* ------------------------------------------------------------------------ */
@@ -700,6 +722,14 @@ static int or_dp45_core(or_rhs_fn f, void *fctx, int64_t dim, int renorm, const 
       }
       err = sqrt(sum / (double)dim);
       if (!isfinite(err)) {
+        status = OR_ENONFINITE;
+        break;
+      }
+    } else {
+      /* no error norm to watch: a step that left the finite numbers ends the run */
+      int finite = 1;
+      for (int64_t q = 0; q < dim; q++) finite = finite && isfinite(ynew[q]);
+      if (!finite) {
         status = OR_ENONFINITE;
         break;
       }

@@ -99,6 +99,7 @@ _SIGS = {
     "mt_ctx_bytes_in_use": (ctypes.c_size_t, [_P]),
     "mt_selftest_wait_timeout": (_I, [_P, _D]),
     "mt_tiles_create": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, _PP]),
+    "mt_tiles_create_tetra": (_I, [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _PP]),
     "mt_tiles_destroy": (None, [_P]),
     "mt_demag_assemble": (_I, [_P, _I, _PP]),
     "mt_demag_assemble_ex": (_I, [_P, _I, _I, _PP]),
@@ -221,8 +222,28 @@ class Ctx:
 
 
 class TilesH:
-    def __init__(self, ctx: Ctx, tiles):
+    def __init__(self, ctx: Ctx, tiles=None, tetra=None):
+        """tiles: cuboid tile set (centre, edge, Ms, Aex, Ku, axis, nbr);
+        tetra: (vertices (nv, 3), tets (n, 4), Ms, Aex, Ku, axis)."""
         self.ctx = ctx
+        if tetra is not None:
+            verts, tets, Ms, Aex, Ku, axis = tetra
+            verts = _f64(verts)
+            tets = np.ascontiguousarray(tets, np.int32)
+            n = tets.shape[0]
+            self.n = n
+            arrs = [_f64(np.broadcast_to(np.asarray(Ms, np.float64), (n,))),
+                    _f64(np.broadcast_to(np.asarray(Aex, np.float64), (n,))),
+                    _f64(np.broadcast_to(np.asarray(Ku, np.float64), (n,))),
+                    _f64(np.broadcast_to(np.asarray(axis, np.float64).reshape(-1, 3), (n, 3)))]
+            h = ctypes.c_void_p()
+            _check(lib().mt_tiles_create_tetra(ctx.h, verts.size // 3, _ptr(verts), n, _ptr(tets),
+                                               *[_ptr(a) for a in arrs], ctypes.byref(h)), "mt_tiles_create_tetra")
+            self.h = h
+            P = verts.reshape(-1, 3)[tets]
+            self.volume = np.abs(np.einsum("ij,ij->i", P[:, 1] - P[:, 0],
+                                           np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6
+            return
         self.n = int(tiles.centre.shape[0])
         arrs = [_f64(tiles.centre), _f64(tiles.edge), _f64(tiles.Ms), _f64(tiles.Aex), _f64(tiles.Ku),
                 _f64(tiles.axis)]
@@ -315,6 +336,10 @@ def mt_selftest_wait_timeout(ctx: Ctx, limit_s: float = 0.2) -> int:
 
 def mt_tiles_create(ctx: Ctx, tiles) -> TilesH:
     return TilesH(ctx, tiles)
+
+
+def mt_tiles_create_tetra(ctx: Ctx, vertices, tets, Ms, Aex, Ku, axis=(0.0, 0.0, 1.0)) -> TilesH:
+    return TilesH(ctx, tetra=(vertices, tets, Ms, Aex, Ku, axis))
 
 
 def mt_demag_assemble(tiles: TilesH, prec="f32") -> TensorH:

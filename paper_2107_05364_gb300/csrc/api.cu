@@ -47,6 +47,12 @@ mt_status upload(P **dst, const P *src, size_t count) {
   return MT_OK;
 }
 
+template <typename P>
+mt_status copy_to(P *dst, const P *src, size_t count) {
+  MT_CUDA(cudaMemcpy(dst, src, sizeof(P) * count, cudaMemcpyHostToDevice));
+  return MT_OK;
+}
+
 void free_tiles(mt_tiles *t) {
   mt_ctx *ctx = t->ctx;
   cudaFree(t->d_centre);
@@ -57,6 +63,7 @@ void free_tiles(mt_tiles *t) {
   cudaFree(t->d_kan);
   cudaFree(t->d_axis);
   cudaFree(t->d_wvol);
+  cudaFree(t->d_vert);
   delete t;
   if (ctx) mt::ctx_release(ctx);
 }
@@ -266,6 +273,126 @@ mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const do
       (st = upload(&t->d_nbr, nb.data(), 6 * n)) != MT_OK || (st = upload(&t->d_kan, kan.data(), n)) != MT_OK ||
       (st = upload(&t->d_axis, axf.data(), 3 * n)) != MT_OK || (st = upload(&t->d_wvol, wvol.data(), n)) != MT_OK) {
     free_tiles(t);
+    return st;
+  }
+  *out = t;
+  return MT_OK;
+}
+
+mt_status mt_tiles_create_tetra(mt_ctx *ctx, int64_t nv, const double *vertices, int64_t n, const int32_t *tets,
+                                const double *Ms, const double *Aex, const double *Ku, const double *axis,
+                                mt_tiles **out) {
+  MT_CHECK(ctx && out, MT_EINVAL, "mt_tiles_create_tetra: NULL handle");
+  MT_CHECK(n >= 1 && n <= (int64_t)1 << 26, MT_EINVAL, "mt_tiles_create_tetra: n = %lld out of range", (long long)n);
+  MT_CHECK(nv >= 4 && nv <= (int64_t)1 << 30, MT_EINVAL, "mt_tiles_create_tetra: nv = %lld out of range",
+           (long long)nv);
+  MT_CHECK(vertices && tets && Ms && Aex && Ku && axis, MT_EINVAL, "mt_tiles_create_tetra: NULL array");
+  for (int64_t k = 0; k < 3 * nv; ++k)
+    MT_CHECK(std::isfinite(vertices[k]), MT_EINVAL, "mt_tiles_create_tetra: non-finite vertex coordinate");
+  std::vector<double> centre(3 * n), edge(3 * n), vert(12 * n), vol(n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < 4; ++a) {
+      const int32_t q = tets[4 * i + a];
+      MT_CHECK(q >= 0 && q < nv, MT_EINVAL, "mt_tiles_create_tetra: vertex index %d of tile %lld out of range", q,
+               (long long)i);
+      for (int b = 0; b < a; ++b)
+        MT_CHECK(tets[4 * i + b] != q, MT_EINVAL, "mt_tiles_create_tetra: repeated vertex in tile %lld",
+                 (long long)i);
+      for (int c = 0; c < 3; ++c) vert[12 * i + 3 * a + c] = vertices[3 * q + c];
+    }
+    const double *v = &vert[12 * i];
+    double e1[3], e2[3], e3[3];
+    for (int c = 0; c < 3; ++c) {
+      e1[c] = v[3 + c] - v[c];
+      e2[c] = v[6 + c] - v[c];
+      e3[c] = v[9 + c] - v[c];
+      centre[3 * i + c] = 0.25 * (v[c] + v[3 + c] + v[6 + c] + v[9 + c]);
+    }
+    const double det = e1[0] * (e2[1] * e3[2] - e2[2] * e3[1]) - e1[1] * (e2[0] * e3[2] - e2[2] * e3[0]) +
+                       e1[2] * (e2[0] * e3[1] - e2[1] * e3[0]);
+    const double scale = std::max({std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]),
+                                   std::sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]),
+                                   std::sqrt(e3[0] * e3[0] + e3[1] * e3[1] + e3[2] * e3[2])});
+    vol[i] = std::fabs(det) / 6.0;
+    MT_CHECK(vol[i] > 1e-12 * scale * scale * scale, MT_EINVAL, "mt_tiles_create_tetra: tile %lld is degenerate",
+             (long long)i);
+    const double h = std::cbrt(vol[i]);
+    edge[3 * i] = edge[3 * i + 1] = edge[3 * i + 2] = h;
+  }
+  // tiles sharing a face: sort the faces by their vertex triples
+  struct Face {
+    int32_t a, b, c;
+    int64_t tile;
+    int slot;
+  };
+  std::vector<Face> faces(4 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int f = 0; f < 4; ++f) {
+      int32_t q[3], k = 0;
+      for (int a = 0; a < 4; ++a)
+        if (a != f) q[k++] = tets[4 * i + a];
+      std::sort(q, q + 3);
+      faces[4 * i + f] = {q[0], q[1], q[2], i, f};
+    }
+  std::sort(faces.begin(), faces.end(), [](const Face &x, const Face &y) {
+    return x.a != y.a ? x.a < y.a : x.b != y.b ? x.b < y.b : x.c != y.c ? x.c < y.c : x.tile < y.tile;
+  });
+  std::vector<int32_t> nbr(6 * n, -1);
+  std::vector<double> coef(6 * n, 0.0);  // area / (V_i d_ip)
+  for (size_t k = 0; k < faces.size();) {
+    size_t e = k + 1;
+    while (e < faces.size() && faces[e].a == faces[k].a && faces[e].b == faces[k].b && faces[e].c == faces[k].c) ++e;
+    MT_CHECK(e - k <= 2, MT_EINVAL, "mt_tiles_create_tetra: a face is shared by more than two tiles");
+    if (e - k == 2) {
+      const Face &F = faces[k], &G = faces[k + 1];
+      const double *pa = &vertices[3 * F.a], *pb = &vertices[3 * F.b], *pc = &vertices[3 * F.c];
+      double u[3], w[3], nr[3];
+      for (int c = 0; c < 3; ++c) {
+        u[c] = pb[c] - pa[c];
+        w[c] = pc[c] - pa[c];
+      }
+      nr[0] = u[1] * w[2] - u[2] * w[1];
+      nr[1] = u[2] * w[0] - u[0] * w[2];
+      nr[2] = u[0] * w[1] - u[1] * w[0];
+      const double l = std::sqrt(nr[0] * nr[0] + nr[1] * nr[1] + nr[2] * nr[2]);
+      const double area = 0.5 * l;
+      double d = 0.0;
+      for (int c = 0; c < 3; ++c) d += (centre[3 * G.tile + c] - centre[3 * F.tile + c]) * nr[c] / l;
+      d = std::fabs(d);
+      MT_CHECK(d > 0, MT_EINVAL, "mt_tiles_create_tetra: tiles %lld and %lld share a face but not its sides",
+               (long long)F.tile, (long long)G.tile);
+      nbr[6 * F.tile + F.slot] = (int32_t)G.tile;
+      nbr[6 * G.tile + G.slot] = (int32_t)F.tile;
+      coef[6 * F.tile + F.slot] = area / (vol[F.tile] * d);
+      coef[6 * G.tile + G.slot] = area / (vol[G.tile] * d);
+    }
+    k = e;
+  }
+  // the cuboid path builds the tile set; then the tetrahedral parts replace
+  // the geometry-dependent ones
+  mt_tiles *t = nullptr;
+  mt_status st = mt_tiles_create(ctx, n, centre.data(), edge.data(), Ms, Aex, Ku, axis, nullptr, &t);
+  if (st != MT_OK) return st;
+  t->kind = MT_TILE_TETRA;
+  std::vector<float> wex(6 * n, 0.0f);
+  bool any = false;
+  for (int64_t i = 0; i < n; ++i)
+    for (int f = 0; f < 6; ++f)
+      if (nbr[6 * i + f] >= 0) {
+        wex[6 * i + f] = (float)(2.0 * Aex[i] / (MT_MU0 * Ms[i]) * coef[6 * i + f]);
+        any = true;
+      }
+  double vt = 0.0;
+  for (int64_t i = 0; i < n; ++i) vt += vol[i];
+  std::vector<double> wvol(n);
+  for (int64_t i = 0; i < n; ++i) wvol[i] = vol[i] / vt;
+  t->vol_total = vt;
+  t->has_exchange = any;
+  t->nbr = nbr;
+  if ((st = upload(&t->d_vert, vert.data(), 12 * n)) != MT_OK ||
+      (st = copy_to(t->d_wex, wex.data(), 6 * n)) != MT_OK || (st = copy_to(t->d_nbr, nbr.data(), 6 * n)) != MT_OK ||
+      (st = copy_to(t->d_wvol, wvol.data(), n)) != MT_OK) {
+    mt::tiles_release(t);
     return st;
   }
   *out = t;

@@ -1,7 +1,7 @@
 // Tensor assembly (FP64) and packing into the tile-blocked storage.
 //
-// Sec. 3 of the paper: the field of every uniformly magnetised cuboid tile
-// is evaluated analytically at the centre of every other tile; the tensor is
+// Sec. 3 of the paper: the field of every uniformly magnetised cuboid or
+// tetrahedral tile is evaluated analytically at the centre of every other tile; the tensor is
 // computed once, at the start (Sec. 3.1), and stored in a reduced precision
 // (FP32 in the paper, Sec. 3.2).  One thread evaluates one 3x3 block in FP64
 // and stores its 6 unique entries directly in the requested precision.
@@ -89,6 +89,125 @@ __device__ void cuboid_tensor(const double *r, const double *c, const double *e,
   out[5] = -k * tzz;
 }
 
+// Tensor of a uniformly magnetised tetrahedron (vertices v[4][3]) at r.
+// The body's field is that of its face charges sigma_f = M.n_f, so with
+// H = -N M,  N = (1/4 pi) sum_f g_f n_f^T,  g_f = grad_r int_f dS / |r - r'|.
+// For a plane triangle the gradient splits into a part along n_f, -n_f times
+// the solid angle under which the face is seen (signed like the height of r
+// above the face), and an in-plane part from the 2-D divergence theorem:
+// minus the sum over the edges of the edge's outward in-plane normal times
+// int_edge dl / |r - r'|.  Solid angle: atan2 form of Van Oosterom and
+// Strackee (1983); edge integral: log((R_b + s_b) / (R_a + s_a)) with s the
+// projections on the edge direction, or the equal log((R_a - s_a) /
+// (R_b - s_b)) where the first would cancel.  FP64 throughout.
+__device__ __forceinline__ void sub3(const double *a, const double *b, double *c) {
+  c[0] = a[0] - b[0];
+  c[1] = a[1] - b[1];
+  c[2] = a[2] - b[2];
+}
+__device__ __forceinline__ double dot3(const double *a, const double *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+__device__ __forceinline__ void crs3(const double *a, const double *b, double *c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ void tetra_tensor(const double *r, const double *v, double out[6]) {
+  double N[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll 1
+  for (int f = 0; f < 4; ++f) {
+    // face (a, b, c) opposite vertex f, made counter-clockwise about its
+    // outward normal
+    const int ia = f == 0 ? 1 : 0;
+    const int ib = f <= 1 ? 2 : 1;
+    const int ic = f <= 2 ? 3 : 2;
+    const double *A = v + 3 * ia, *Bv = v + 3 * ib, *C = v + 3 * ic;
+    double ab[3], ac[3], nf[3], to_f[3];
+    sub3(Bv, A, ab);
+    sub3(C, A, ac);
+    crs3(ab, ac, nf);
+    sub3(v + 3 * f, A, to_f);
+    if (dot3(nf, to_f) > 0.0) {
+      const double *t = Bv;
+      Bv = C;
+      C = t;
+      nf[0] = -nf[0];
+      nf[1] = -nf[1];
+      nf[2] = -nf[2];
+    }
+    const double inv = 1.0 / sqrt(dot3(nf, nf));
+    nf[0] *= inv;
+    nf[1] *= inv;
+    nf[2] *= inv;
+    double ra[3], rb[3], rc[3], bxc[3];
+    sub3(A, r, ra);
+    sub3(Bv, r, rb);
+    sub3(C, r, rc);
+    crs3(rb, rc, bxc);
+    const double la = sqrt(dot3(ra, ra)), lb = sqrt(dot3(rb, rb)), lc = sqrt(dot3(rc, rc));
+    const double omega = -2.0 * atan2(dot3(ra, bxc), la * lb * lc + dot3(ra, rb) * lc + dot3(ra, rc) * lb +
+                                                         dot3(rb, rc) * la);
+    double g[3] = {-omega * nf[0], -omega * nf[1], -omega * nf[2]};
+    const double *P[3] = {A, Bv, C};
+    const double *Rv[3] = {ra, rb, rc};
+    const double L[3] = {la, lb, lc};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int e2 = (e + 1) % 3;
+      double t[3], u[3];
+      sub3(P[e2], P[e], t);
+      const double len = sqrt(dot3(t, t));
+      t[0] /= len;
+      t[1] /= len;
+      t[2] /= len;
+      crs3(t, nf, u);  // in-plane, out of the face
+      const double s1 = dot3(Rv[e], t), s2 = dot3(Rv[e2], t);
+      const double li = (s1 + s2 >= 0.0) ? log((L[e2] + s2) / (L[e] + s1)) : log((L[e] - s1) / (L[e2] - s2));
+      g[0] -= u[0] * li;
+      g[1] -= u[1] * li;
+      g[2] -= u[2] * li;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) N[a][b] += g[a] * nf[b];
+  }
+  const double k = 0.25 / MT_PI;
+  out[0] = k * N[0][0];
+  out[1] = 0.5 * k * (N[0][1] + N[1][0]);
+  out[2] = 0.5 * k * (N[0][2] + N[2][0]);
+  out[3] = k * N[1][1];
+  out[4] = 0.5 * k * (N[1][2] + N[2][1]);
+  out[5] = k * N[2][2];
+}
+
+// Relations of tetrahedra i and j (i != j), as pair_relation: bit 0 = the
+// centroid of i lies in or on tetrahedron j (barycentric coordinates all
+// >= -eps), bit 1 = they share a vertex (a "near" pair).
+__device__ int tetra_relation(const double *ci, const double *vi, const double *vj) {
+  bool touch = false;
+#pragma unroll 1
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      touch = touch || (vi[3 * a] == vj[3 * b] && vi[3 * a + 1] == vj[3 * b + 1] && vi[3 * a + 2] == vj[3 * b + 2]);
+  // barycentric coordinates of ci in j: solve [v1-v0, v2-v0, v3-v0] x = ci - v0
+  double e1[3], e2[3], e3[3], d[3], c23[3], c31[3], c12[3];
+  sub3(vj + 3, vj, e1);
+  sub3(vj + 6, vj, e2);
+  sub3(vj + 9, vj, e3);
+  sub3(ci, vj, d);
+  crs3(e2, e3, c23);
+  crs3(e3, e1, c31);
+  crs3(e1, e2, c12);
+  const double det = dot3(e1, c23);
+  const double x = dot3(d, c23) / det, y = dot3(d, c31) / det, z = dot3(d, c12) / det;
+  const double eps = 1e-12;
+  const bool in = x >= -eps && y >= -eps && z >= -eps && (1.0 - x - y - z) >= -eps;
+  return (in ? 1 : 0) | (touch ? 2 : 0);
+}
+
 // Geometry relations of tiles i and j (i != j): bit 0 = volumes overlap or
 // the centre of i lies in/on tile j (invalid), bit 1 = the closed boxes touch
 // (a "near" pair, kept in FP64 for the BF16 precisions).
@@ -122,6 +241,8 @@ __device__ __forceinline__ int64_t scale_index(int64_t i, int64_t j, int TR, int
 
 struct AsmArgs {
   const double *centre, *edge;
+  const double *vert;  // 12n, tetrahedral tiles
+  int kind;            // MT_TILE_CUBOID / MT_TILE_TETRA
   int64_t n;
   int TR, TC, nplane;
   int64_t Q;
@@ -144,12 +265,16 @@ __global__ void k_assemble(AsmArgs A) {
   const int64_t q = blockIdx.x, p = blockIdx.y;
   const int64_t j = q * A.TC + threadIdx.x;
   if (j >= A.n) return;
-  double cj[3], ej[3];
+  const bool tet = A.kind == MT_TILE_TETRA;
+  double cj[3], ej[3], vj[12];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     cj[a] = A.centre[3 * j + a];
     ej[a] = A.edge[3 * j + a];
   }
+  if (tet)
+#pragma unroll
+    for (int a = 0; a < 12; ++a) vj[a] = A.vert[12 * j + a];
   for (int r = 0; r < A.TR; ++r) {
     const int64_t i = p * A.TR + r;
     if (i >= A.n) break;
@@ -159,7 +284,7 @@ __global__ void k_assemble(AsmArgs A) {
       ci[a] = A.centre[3 * i + a];
       ei[a] = A.edge[3 * i + a];
     }
-    int rel = (i == j) ? 2 : pair_relation(ci, ei, cj, ej);
+    int rel = (i == j) ? 2 : tet ? tetra_relation(ci, A.vert + 12 * i, vj) : pair_relation(ci, ei, cj, ej);
     if (rel & 1) atomicExch(A.bad, 1);
     const bool near = (rel & 2) && (A.prec == MT_BF16_SCALED || A.prec == MT_BF16_SPLIT);
     if (A.count_only) {
@@ -167,7 +292,10 @@ __global__ void k_assemble(AsmArgs A) {
       continue;
     }
     double N6[6];
-    cuboid_tensor(ci, cj, ej, N6);
+    if (tet)
+      tetra_tensor(ci, vj, N6);
+    else
+      cuboid_tensor(ci, cj, ej, N6);
     if (near) {
       const int slot = atomicAdd(&A.near_fill[i], 1);
       const int64_t at = A.near_ptr[i] + slot;
@@ -235,7 +363,8 @@ __global__ void k_assemble(AsmArgs A) {
 }
 
 // sort each row's near blocks by column so that the FP64 near sum has a
-// fixed order (one thread per row; rows hold at most 27 entries)
+// fixed order (one thread per row; rows hold at most 27 entries for cuboid
+// grids, a few dozen for tetrahedral meshes)
 __global__ void k_sort_near(int64_t n, const int32_t *ptr, int32_t *col, double *val) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -264,12 +393,15 @@ __global__ void k_near_split(int64_t count6, const double *val, float2 *hl) {
   hl[t] = make_float2(hi, (float)(v - (double)hi));
 }
 
-__global__ void k_blocks(const double *centre, const double *edge, int64_t count, const int64_t *pairs,
-                         double *out) {
+__global__ void k_blocks(const double *centre, const double *edge, const double *vert, int kind, int64_t count,
+                         const int64_t *pairs, double *out) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= count) return;
   const int64_t i = pairs[2 * p], j = pairs[2 * p + 1];
-  cuboid_tensor(&centre[3 * i], &centre[3 * j], &edge[3 * j], &out[6 * p]);
+  if (kind == MT_TILE_TETRA)
+    tetra_tensor(&centre[3 * i], &vert[12 * j], &out[6 * p]);
+  else
+    cuboid_tensor(&centre[3 * i], &centre[3 * j], &edge[3 * j], &out[6 * p]);
 }
 
 // stored value -> double, rows [i0, i1), all columns; out[((i-i0)*n + j)*6 + e]
@@ -339,6 +471,8 @@ mt_status assemble(mt_tensor *T) {
   AsmArgs A{};
   A.centre = t->d_centre;
   A.edge = t->d_edge;
+  A.vert = t->d_vert;
+  A.kind = t->kind;
   A.n = n;
   A.TR = L.TR;
   A.TC = L.TC;
@@ -408,7 +542,8 @@ mt_status blocks_fp64(mt_tiles *t, int64_t count, const int64_t *pairs, double *
   MT_CUDA(cudaMalloc(&d_pairs, sizeof(int64_t) * 2 * count));
   MT_CUDA(cudaMalloc(&d_out, sizeof(double) * 6 * count));
   MT_CUDA(cudaMemcpy(d_pairs, pairs, sizeof(int64_t) * 2 * count, cudaMemcpyHostToDevice));
-  k_blocks<<<(unsigned)((count + 127) / 128), 128>>>(t->d_centre, t->d_edge, count, d_pairs, d_out);
+  k_blocks<<<(unsigned)((count + 127) / 128), 128>>>(t->d_centre, t->d_edge, t->d_vert, t->kind, count, d_pairs,
+                                                     d_out);
   MT_CUDA(cudaGetLastError());
   MT_CUDA(cudaMemcpy(out, d_out, sizeof(double) * 6 * count, cudaMemcpyDeviceToHost));
   cudaFree(d_pairs);

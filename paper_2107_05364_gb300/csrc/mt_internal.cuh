@@ -82,7 +82,11 @@ struct mt_tiles {
   double *d_wvol = nullptr;    // n: V_i / sum V
   double vol_total = 0.0;      // sum V, m^3
   bool has_exchange = false;
+  int kind = 0;                // MT_TILE_CUBOID or MT_TILE_TETRA
+  double *d_vert = nullptr;    // 12n: the 4 vertices of each tetrahedron (kind tetra)
 };
+
+enum { MT_TILE_CUBOID = 0, MT_TILE_TETRA = 1 };
 
 // Tile-blocked storage: the n x n grid of 3x3 blocks is cut into row panels
 // of TR tiles and column chunks of TC tiles.  Chunk (p, q) is contiguous and

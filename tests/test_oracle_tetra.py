@@ -144,3 +144,14 @@ def test_tetra_mesh_of_a_box():
     assert np.all(md.vol > 0) and abs(md.vol.sum() - 6e-24) < 1e-36
     # every interior face has two owners: each tile has at most 4 neighbours
     assert np.all((md.nbr >= 0).sum(1) <= 4)
+
+
+def test_field_rows_match_dense_product():
+    verts, tets = wl.tetra_box(3, 2, 2, size=(30e-9, 20e-9, 10e-9), jitter=0.2, seed=4)
+    P = verts[tets]
+    N = oracle.tetra_demag_tensor(P)
+    m = wl.m_random(len(tets), seed=2)
+    Ms = np.full(len(tets), 8e5)
+    Hd = oracle.demag_field_dense(N, Ms, m)
+    rows = np.array([0, 5, 17, len(tets) - 1])
+    np.testing.assert_allclose(oracle.tetra_field_rows(P, Ms, m, rows), Hd[rows], rtol=1e-13, atol=1e-9)

@@ -384,11 +384,13 @@ __global__ void k_sort_near(int64_t n, const int32_t *ptr, int32_t *col, double 
   }
 }
 
-// near blocks as FP32 hi + lo pairs (v = hi + lo to ~2^-48 relative)
-__global__ void k_near_split(int64_t count6, const double *val, float2 *hl) {
+// near blocks times the source tile's Ms as FP32 hi + lo pairs
+// (N_ij Ms_j = hi + lo to ~2^-48 relative; Ms_j as the FP32 value every
+// product uses), so that the near product multiplies plain m
+__global__ void k_near_split(int64_t count6, const double *val, const int32_t *col, const float *Ms, float2 *hl) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count6) return;
-  const double v = val[t];
+  const double v = val[t] * (double)Ms[col[t / 6]];
   const float hi = (float)v;
   hl[t] = make_float2(hi, (float)(v - (double)hi));
 }
@@ -516,7 +518,7 @@ mt_status assemble(mt_tensor *T) {
     MT_CUDA(cudaMalloc(&T->d_near_hl, sizeof(float2) * c6));
     if (T->near_count > 0) {
       k_near_split<<<(unsigned)((6 * T->near_count + 255) / 256), 256>>>(6 * T->near_count, T->d_near_val,
-                                                                        T->d_near_hl);
+                                                                        T->d_near_col, t->d_Ms, T->d_near_hl);
       MT_CUDA(cudaGetLastError());
     }
     MT_CUDA(cudaDeviceSynchronize());

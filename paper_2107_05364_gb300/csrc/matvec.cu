@@ -350,11 +350,12 @@ __global__ void k_prep_xs(const In *m, const float *Ms, int64_t n, int64_t Q, in
 
 // Near-field blocks (BF16 precisions): H_i -= sum_near N_ij Ms_j m_j with
 // FP64-class accuracy on the FP32 pipes.  The blocks were assembled in FP64
-// and are held as FP32 hi + lo pairs; products use the exact FMA product
-// split (p = a b, e = fma(a, b, -p)) and the sum is carried as an unevaluated
-// pair (hi + lo) with Knuth's two-sum, then added to the far field and
-// rounded once.  (GB300 executes FP64 at a small fraction of its FP32 rate;
-// this keeps ~2^-44 relative accuracy at FP32 speed.)
+// and are held, times Ms_j, as FP32 hi + lo pairs; products use the exact FMA
+// product split (p = a b, e = fma(a, b, -p)) and the sum is carried as an
+// unevaluated pair (hi + lo), Knuth's two-sum feeding every rounding error
+// into lo, then added to the far field and rounded once.  (GB300 executes
+// FP64 at a small fraction of its FP32 rate; this keeps ~2^-44 relative
+// accuracy at FP32 speed.)
 struct ff {
   float hi, lo;
 };
@@ -369,19 +370,24 @@ __device__ __forceinline__ ff ff_add(ff acc, float p, float e) {
   const float hi = s.hi + s.lo;
   return {hi, s.lo - (hi - s.hi)};
 }
-// acc += (v.hi + v.lo) * (x.hi + x.lo)
-__device__ __forceinline__ ff ff_fma(ff acc, float2 v, ff x) {
-  const float p = v.x * x.hi;
-  const float e = fmaf(v.x, x.hi, -p) + (v.x * x.lo + v.y * x.hi);
-  return ff_add(acc, p, e);
-}
-
 // threads enumerate (tile, simulation) pairs with the simulation fastest, so
 // a warp of a wide batch shares its tile's blocks (broadcast loads)
 // m element (b, j, c) sits at m[b * sb + (3 j + c) * se]: se = 1 for the
 // tile-major state, sb = 1 for the simulation-fastest copy of wide batches
+// acc += (v.hi + v.lo) * x with the error of the rounded product and of the
+// addition collected in acc.lo (a cascaded sum: no renormalisation per term,
+// acc.lo stays a few ulps of acc.hi over the <= 27 blocks of a row)
+__device__ __forceinline__ void ff_fma_lazy(ff &acc, float2 v, float x) {
+  const float p = v.x * x;
+  const float e = fmaf(v.y, x, fmaf(v.x, x, -p));
+  const float s = acc.hi + p;
+  const float bp = s - acc.hi;
+  acc.lo += ((acc.hi - (s - bp)) + (p - bp)) + e;
+  acc.hi = s;
+}
+
 __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const float2 *val,
-                       const float *Ms, const float *m, int64_t sb, int64_t se, float *H, const int *active) {
+                       const float *m, int64_t sb, int64_t se, float *H, const int *active) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * B) return;
   const int64_t i = t / B;
@@ -391,18 +397,19 @@ __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col,
   ff hx = {0, 0}, hy = {0, 0}, hz = {0, 0};
   for (int32_t a = ptr[i]; a < ptr[i + 1]; ++a) {
     const int64_t j = col[a];
-    const float ms = Ms[j];
-    ff x[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float mc = mb[(3 * j + c) * se];
-      x[c].hi = ms * mc;
-      x[c].lo = fmaf(ms, mc, -x[c].hi);
-    }
+    // val holds N_ij Ms_j: the operand is m itself, exact in FP32
+    const float x0 = mb[(3 * j) * se], x1 = mb[(3 * j + 1) * se], x2 = mb[(3 * j + 2) * se];
     const float2 *v = val + 6 * (size_t)a;
-    hx = ff_fma(ff_fma(ff_fma(hx, v[0], x[0]), v[1], x[1]), v[2], x[2]);
-    hy = ff_fma(ff_fma(ff_fma(hy, v[1], x[0]), v[3], x[1]), v[4], x[2]);
-    hz = ff_fma(ff_fma(ff_fma(hz, v[2], x[0]), v[4], x[1]), v[5], x[2]);
+    const float2 v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5];
+    ff_fma_lazy(hx, v0, x0);
+    ff_fma_lazy(hx, v1, x1);
+    ff_fma_lazy(hx, v2, x2);
+    ff_fma_lazy(hy, v1, x0);
+    ff_fma_lazy(hy, v3, x1);
+    ff_fma_lazy(hy, v4, x2);
+    ff_fma_lazy(hz, v2, x0);
+    ff_fma_lazy(hz, v4, x1);
+    ff_fma_lazy(hz, v5, x2);
   }
   float *Hb = H + (size_t)b * 3 * n + 3 * i;
   // H = far - near, rounded once
@@ -517,8 +524,8 @@ void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int
                  cudaStream_t s) {
   if (T->near_count == 0) return;
   const int64_t tot = T->n * (int64_t)B;
-  k_near<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl,
-                                                       T->tiles->d_Ms, m, sb, se, H, active);
+  k_near<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl, m, sb,
+                                                       se, H, active);
 }
 
 }  // namespace mt

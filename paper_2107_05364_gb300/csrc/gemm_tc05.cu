@@ -43,6 +43,21 @@ constexpr int GM = 128;  // rows per tile (MMA M)
 constexpr int GK = 64;   // K per ring stage: one 128-byte swizzle row of BF16
 constexpr int EPI_WARPS = 4;
 constexpr int NACC = 4;  // TMEM accumulators in flight between the MMA warp and the epilogue
+
+// The split product with a padded batch up to 64 "stacks" the three operand
+// planes x0 | x1 | x2 into one N = 3 Bp operand: one MMA gives N_hi x0,
+// N_hi x1, N_hi x2 side by side in TMEM and a second (N = 2 Bp) adds N_lo x0
+// and N_lo x1 onto the first two groups; the epilogue adds the groups in
+// FP32.  That reads each tensor tile from shared memory twice per K step
+// instead of five times (the split product was bound by the shared-memory
+// reads that feed the tensor cores).  N <= 256 limits it to Bp <= 64; wider
+// batches issue the five MMAs.
+template <bool SPLIT, int BP>
+struct GemmShape {
+  static constexpr bool STACK = SPLIT && BP <= 64;
+  static constexpr int ACC_COLS = STACK ? 3 * BP : BP;  // TMEM columns of one accumulator
+  static constexpr int NA = STACK ? (BP == 64 ? 2 : 4) : NACC;  // accumulators (<= 512 columns)
+};
 constexpr int GEMM_THREADS = 32 * (2 + EPI_WARPS);
 
 // ---- tcgen05 / TMA wrappers -------------------------------------------------
@@ -132,8 +147,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)P.stages * P.stage_bytes);
   uint64_t *empty = full + P.stages;
   uint64_t *accf = empty + P.stages;
-  uint64_t *acce = accf + NACC;
-  uint64_t *mma_done = acce + NACC;
+  using SH = GemmShape<SPLIT, BP>;
+  constexpr int NA = SH::NA;
+  uint64_t *acce = accf + NA;
+  uint64_t *mma_done = acce + NA;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -151,7 +168,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       mtd::mbar_init(&full[s], 1);
       mtd::mbar_init(&empty[s], 1);
     }
-    for (int a = 0; a < NACC; ++a) {
+    for (int a = 0; a < NA; ++a) {
       mtd::mbar_init(&accf[a], 1);
       mtd::mbar_init(&acce[a], EPI_WARPS);
     }
@@ -187,12 +204,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const int ya = (int)((mt * P.KB + kb) * GM), yx = (int)(kb * P.Bp);
         unsigned char *sb = st + q * SB;
         tma_2d(sb, &tA, 0, ya, &full[s], pol_stream);
-        tma_2d(sb + A_BYTES, &tX, 0, yx, &full[s], pol_keep);
         if (SPLIT) {
-          // sub-block: A_hi | x0 | A_lo | x1 | x2
-          tma_2d(sb + A_BYTES + X_BYTES, &tAlo, 0, ya, &full[s], pol_stream);
+          // sub-block: A_hi | A_lo | x0 | x1 | x2 (the planes of x adjacent:
+          // one 3 Bp-row operand)
+          tma_2d(sb + A_BYTES, &tAlo, 0, ya, &full[s], pol_stream);
+          tma_2d(sb + 2 * A_BYTES, &tX, 0, yx, &full[s], pol_keep);
           tma_2d(sb + 2 * A_BYTES + X_BYTES, &tX1, 0, yx, &full[s], pol_keep);
           tma_2d(sb + 2 * A_BYTES + 2 * X_BYTES, &tX2, 0, yx, &full[s], pol_keep);
+        } else {
+          tma_2d(sb + A_BYTES, &tX, 0, yx, &full[s], pol_keep);
         }
       }
     }
@@ -207,6 +227,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                            | (1u << 7) | (1u << 10)        // A, B: BF16
                            | ((uint32_t)(P.Bp >> 3) << 17)  // N
                            | ((uint32_t)(GM >> 4) << 24);   // M
+    // stacked split: N = 3 Bp (N_hi [x0 | x1 | x2]) and N = 2 Bp (N_lo [x0 | x1])
+    const uint32_t idesc3 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((3 * BP) >> 3) << 17);
+    const uint32_t idesc2 = (idesc & ~(0x3Fu << 17)) | ((uint32_t)((2 * BP) >> 3) << 17);
     // The tensor cores' FP32 accumulation rounds with a bias, so a product
     // is accumulated in TMEM over at most P.chunk K blocks and then handed to
     // the epilogue, which adds the chunks in FP32 (round to nearest).
@@ -218,13 +241,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int64_t seg_end = u1 < (mt + 1) * P.KBU ? u1 : (mt + 1) * P.KBU;
       while (u < seg_end && !*abort_flag) {
         const int64_t c_end = seg_end < u + P.chunk ? seg_end : u + P.chunk;
-        const int a = chunk % NACC;
-        if (chunk >= NACC && !mtd::mbar_wait_bounded(&acce[a], (uint32_t)(chunk / NACC - 1) & 1u, P.status)) {
+        const int a = chunk % NA;
+        if (chunk >= NA && !mtd::mbar_wait_bounded(&acce[a], (uint32_t)(chunk / NA - 1) & 1u, P.status)) {
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(a * BP);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(a * SH::ACC_COLS);
         bool first = true;
         for (; u < c_end; ++u, ++it) {
           const int s = it % P.stages;
@@ -238,21 +261,28 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
           for (int q = 0; q < KPS; ++q) {
             const uint32_t sa = st + q * SB;
-            const uint32_t sx = sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < GK / 16; ++kk) {
               // K advance inside the 128-byte swizzle row: 16 BF16 = 32 bytes
-              const uint64_t da = sw128_desc(sa + 32 * kk), dx = sw128_desc(sx + 32 * kk);
-              umma_bf16(d_tmem, da, dx, idesc, first ? 0u : 1u);
-              first = false;
-              if (SPLIT) {
-                const uint32_t salo = sx + X_BYTES, sx1 = salo + A_BYTES, sx2 = sx1 + X_BYTES;
-                const uint64_t dlo = sw128_desc(salo + 32 * kk), d1 = sw128_desc(sx1 + 32 * kk);
+              const uint64_t da = sw128_desc(sa + 32 * kk);
+              if (!SPLIT) {
+                umma_bf16(d_tmem, da, sw128_desc(sa + A_BYTES + 32 * kk), idesc, first ? 0u : 1u);
+              } else if (SH::STACK) {
+                const uint32_t salo = sa + A_BYTES, sx = salo + A_BYTES;
+                const uint64_t dx = sw128_desc(sx + 32 * kk);
+                umma_bf16(d_tmem, da, dx, idesc3, first ? 0u : 1u);                  // N_hi [x0 | x1 | x2]
+                umma_bf16(d_tmem, sw128_desc(salo + 32 * kk), dx, idesc2, 1u);       // N_lo [x0 | x1]
+              } else {
+                const uint32_t salo = sa + A_BYTES, sx = salo + A_BYTES, sx1 = sx + X_BYTES, sx2 = sx1 + X_BYTES;
+                const uint64_t dx = sw128_desc(sx + 32 * kk), d1 = sw128_desc(sx1 + 32 * kk);
+                const uint64_t dlo = sw128_desc(salo + 32 * kk);
+                umma_bf16(d_tmem, da, dx, idesc, first ? 0u : 1u);            // N_hi x0
                 umma_bf16(d_tmem, da, d1, idesc, 1u);                         // N_hi x1
                 umma_bf16(d_tmem, da, sw128_desc(sx2 + 32 * kk), idesc, 1u);  // N_hi x2
                 umma_bf16(d_tmem, dlo, dx, idesc, 1u);                        // N_lo x0
                 umma_bf16(d_tmem, dlo, d1, idesc, 1u);                        // N_lo x1
               }
+              first = false;
             }
           }
           issued = true;
@@ -279,21 +309,40 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       bool first_chunk = true;
       while (u < seg_end) {
         u = seg_end < u + P.chunk ? seg_end : u + P.chunk;
-        const int a = chunk % NACC;
-        const bool got = !*abort_flag && mtd::mbar_wait_bounded(&accf[a], (uint32_t)(chunk / NACC) & 1u, P.status);
+        const int a = chunk % NA;
+        const bool got = !*abort_flag && mtd::mbar_wait_bounded(&accf[a], (uint32_t)(chunk / NA) & 1u, P.status);
         if (!got) {
           *abort_flag = 1;
           ok = false;
         }
         tc_fence_after();
-        // all loads of the accumulator in flight at once, one wait
-        uint32_t v[BP];
+        const uint32_t acc = tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(a * SH::ACC_COLS);
+        if (SH::STACK) {
+          // the three column groups x0, x1, x2 of each 16-column piece, the
+          // two small ones added first
 #pragma unroll
-        for (int c0 = 0; c0 < BP; c0 += 16)
-          tmem_ld16(tmem_base + ((uint32_t)(g * 32) << 16) + (uint32_t)(a * BP + c0), &v[c0]);
-        tmem_wait_ld();
+          for (int c0 = 0; c0 < BP; c0 += 16) {
+            uint32_t v0[16], v1[16], v2[16];
+            tmem_ld16(acc + (uint32_t)c0, v0);
+            tmem_ld16(acc + (uint32_t)(BP + c0), v1);
+            tmem_ld16(acc + (uint32_t)(2 * BP + c0), v2);
+            tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < BP; ++j) run[j] = first_chunk ? __uint_as_float(v[j]) : run[j] + __uint_as_float(v[j]);
+            for (int j = 0; j < 16; ++j) {
+              const float x = __uint_as_float(v0[j]) + (__uint_as_float(v1[j]) + __uint_as_float(v2[j]));
+              run[c0 + j] = first_chunk ? x : run[c0 + j] + x;
+            }
+          }
+        } else {
+          // all loads of the accumulator in flight at once, one wait
+          uint32_t v[BP];
+#pragma unroll
+          for (int c0 = 0; c0 < BP; c0 += 16) tmem_ld16(acc + (uint32_t)c0, &v[c0]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < BP; ++j)
+            run[j] = first_chunk ? __uint_as_float(v[j]) : run[j] + __uint_as_float(v[j]);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mtd::mbar_arrive(&acce[a]);
@@ -397,8 +446,19 @@ mt_status make_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t r
   return MT_OK;
 }
 
+#ifndef MT_GEMM_KPS_SPLIT
+#define MT_GEMM_KPS_SPLIT 2
+#endif
+
+// K blocks per ring stage (see kps_of below)
+constexpr int kps_for(bool split) { return split ? MT_GEMM_KPS_SPLIT : 2; }
+
+int stage_bytes_for(int Bp, bool split) {
+  return kps_for(split) * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
+}
+
 int stages_for(int Bp, bool split) {
-  const int stage = 2 * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
+  const int stage = stage_bytes_for(Bp, split);
   const int budget = 224 * 1024;
   return std::max(2, std::min(8, budget / stage));
 }
@@ -435,7 +495,7 @@ size_t dense_count_bytes(const mt_tensor *T) { return (size_t)(T->Kp / GM) * EPI
 // the split product goes from 0.73 to 0.83 with a 2-deep ring of 112 KB)
 template <bool SPLIT>
 constexpr int kps_of() {
-  return 2;
+  return kps_for(SPLIT);
 }
 
 template <bool SPLIT, int BP>
@@ -488,7 +548,7 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   plan->Bp = Bp;
   plan->split = split;
   plan->stages = stages_for(Bp, split);
-  plan->kps = 2;
+  plan->kps = kps_for(split);
   plan->chunk = 4 / plan->kps;  // units per accumulator chunk: 4 K blocks either way
   return MT_OK;
 }
@@ -541,9 +601,12 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.Bp = plan.Bp;
   P.chunk = plan.chunk;
   P.stages = plan.stages;
-  P.stage_bytes = 2 * (plan.split ? 2 * GM * GK * 2 + 3 * plan.Bp * GK * 2 : GM * GK * 2 + plan.Bp * GK * 2);
+  P.stage_bytes = stage_bytes_for(plan.Bp, plan.split);
+  const bool stack = plan.split && plan.Bp <= 64;
+  const int acc_cols = stack ? 3 * plan.Bp : plan.Bp;
+  const int na = stack ? (plan.Bp == 64 ? 2 : 4) : NACC;  // as GemmShape
   uint32_t cols = 32;
-  while (cols < (uint32_t)(NACC * plan.Bp)) cols <<= 1;
+  while (cols < (uint32_t)(na * acc_cols)) cols <<= 1;
   P.tmem_cols = cols;
   P.H = H;
   P.part = part;

@@ -66,8 +66,10 @@ typedef enum {
   MT_F64 = 0,          /* 8 B per entry                                       */
   MT_F32 = 1,          /* 4 B per entry: the paper's storage (Sec. 3.2)        */
   MT_BF16_SCALED = 2,  /* 2 B per entry + a power-of-two scale per 3x3 block;  */
-                       /* the tile and its touching neighbours stay FP64       */
-  MT_BF16_SPLIT = 3    /* hi + lo BF16 pair (4 B per entry); near blocks FP64  */
+                       /* the tile and its touching neighbours are kept apart  */
+                       /* (assembled FP64, applied in FP32)                    */
+  MT_BF16_SPLIT = 3    /* hi + lo BF16 pair (4 B per entry); near blocks kept  */
+                       /* apart, applied in double-FP32 (~FP64 accuracy)       */
 } mt_prec;
 
 /* Storage layout of the assembled tensor. */

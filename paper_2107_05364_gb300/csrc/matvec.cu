@@ -386,6 +386,9 @@ __device__ __forceinline__ void ff_fma_lazy(ff &acc, float2 v, float x) {
   acc.hi = s;
 }
 
+// FF = false (the BF16 precision, whose far part carries ~1e-4 errors):
+// plain FP32 sums of the high words, H = far - near in FP32
+template <bool FF>
 __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const float2 *val,
                        const float *m, int64_t sb, int64_t se, float *H, const int *active) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -399,8 +402,17 @@ __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col,
     const int64_t j = col[a];
     // val holds N_ij Ms_j: the operand is m itself, exact in FP32
     const float x0 = mb[(3 * j) * se], x1 = mb[(3 * j + 1) * se], x2 = mb[(3 * j + 2) * se];
-    const float2 *v = val + 6 * (size_t)a;
-    const float2 v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4], v5 = v[5];
+    // 48 bytes per block, 16-byte aligned: three float4 requests
+    const float4 *vp = reinterpret_cast<const float4 *>(val + 6 * (size_t)a);
+    const float4 w0 = vp[0], w1 = vp[1], w2 = vp[2];
+    const float2 v0 = make_float2(w0.x, w0.y), v1 = make_float2(w0.z, w0.w), v2 = make_float2(w1.x, w1.y);
+    const float2 v3 = make_float2(w1.z, w1.w), v4 = make_float2(w2.x, w2.y), v5 = make_float2(w2.z, w2.w);
+    if (!FF) {
+      hx.hi = fmaf(v0.x, x0, fmaf(v1.x, x1, fmaf(v2.x, x2, hx.hi)));
+      hy.hi = fmaf(v1.x, x0, fmaf(v3.x, x1, fmaf(v4.x, x2, hy.hi)));
+      hz.hi = fmaf(v2.x, x0, fmaf(v4.x, x1, fmaf(v5.x, x2, hz.hi)));
+      continue;
+    }
     ff_fma_lazy(hx, v0, x0);
     ff_fma_lazy(hx, v1, x1);
     ff_fma_lazy(hx, v2, x2);
@@ -524,8 +536,11 @@ void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int
                  cudaStream_t s) {
   if (T->near_count == 0) return;
   const int64_t tot = T->n * (int64_t)B;
-  k_near<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl, m, sb,
-                                                       se, H, active);
+  const unsigned grid = (unsigned)((tot + 255) / 256);
+  if (T->prec == MT_BF16_SPLIT)
+    k_near<true><<<grid, 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl, m, sb, se, H, active);
+  else
+    k_near<false><<<grid, 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl, m, sb, se, H, active);
 }
 
 }  // namespace mt

@@ -38,6 +38,16 @@ sys.path.insert(0, ROOT)
 from paper_2107_05364_gb300 import workloads as wl  # noqa: E402
 
 MU0 = 4e-7 * math.pi
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the streaming FP32 product at the film workload below (n = 10,000), from one
+# ncu capture of a full launch: 2,427,086,080 read + 2,945,024 written
+# (1.0125 x the 2.4e9 algorithmic bytes: the zero padding of the last chunk
+# row).  Valid while k_matvec<f32> is unchanged.
+MATVEC_F32_N10000_TRAFFIC = 2427086080 + 2945024
+# The split tensor-core product at n = 8,000 read 1.0040 x its stored tensor
+# and wrote its field (one ncu capture of the stacked-operand kernel); the
+# batched line scales that per stored byte.
+SPLIT_GEMM_READ_PER_STORED_BYTE = 1.0040
 FIELD1 = np.array([-24.6e-3, 4.3e-3, 0.0]) / MU0
 WORKLOAD = "sp4_film_200x50x1_n10000_f32"
 METRIC = "LLG RHS evals/s"
@@ -300,7 +310,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "sms": torch.cuda.get_device_properties(dev).multi_processor_count},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_matvec<f32>",
+                     "frac": achieved / peak,
+                     "traffic": MATVEC_F32_N10000_TRAFFIC if n == 10000 else None, "kernel": "k_matvec<f32>",
                      "peak_kind": kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": field_ms},
         "demag_gbs": achieved,
@@ -391,7 +402,10 @@ def run_batched(args, quiet=False):
         "vs_plain_fp32": value / plain, "plain_fp32_evals_per_s": plain,
         "roofline": {"bound": "hbm", "achieved": stored / (gemm_ms * 1e-3) / 1e9, "peak": float(peaks["hbm_gbs"]),
                      "unit": "GB/s", "frac": stored / (gemm_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]),
-                     "traffic": None, "kernel": "k_gemm<%s>" % args.prec, "launch_ms": gemm_ms,
+                     "traffic": (round(SPLIT_GEMM_READ_PER_STORED_BYTE * stored + 12 * n * B)
+                                 if args.prec == "split" else None),
+                     "traffic_note": "scaled from an n = 8,000 capture" if args.prec == "split" else None,
+                     "kernel": "k_gemm<%s>" % args.prec, "launch_ms": gemm_ms,
                      "tensor_tflops": flops / (gemm_ms * 1e-3) / 1e12,
                      "tensor_frac_of_bf16_peak": flops / (gemm_ms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]),
                      "peak_kind": kind},

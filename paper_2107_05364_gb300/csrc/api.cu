@@ -64,6 +64,7 @@ void free_tiles(mt_tiles *t) {
   cudaFree(t->d_axis);
   cudaFree(t->d_wvol);
   cudaFree(t->d_vert);
+  cudaFree(t->d_lat);
   delete t;
   if (ctx) mt::ctx_release(ctx);
 }
@@ -267,7 +268,43 @@ mt_status mt_tiles_create(mt_ctx *ctx, int64_t n, const double *centre, const do
   }
   std::vector<int32_t> nb(6 * n, -1);
   if (nbr) std::copy(nbr, nbr + 6 * n, nb.begin());
+  // uniform lattice?  equal edges and every centre within 1e-9 edges of
+  // c_min + index * edge; the offset table must stay small
+  std::vector<int32_t> lat;
+  {
+    bool ok = true;
+    double cmin[3] = {centre[0], centre[1], centre[2]};
+    for (int64_t i = 0; i < n && ok; ++i)
+      for (int a = 0; a < 3; ++a) {
+        ok = ok && std::fabs(edge[3 * i + a] - edge[a]) <= 1e-12 * edge[a];
+        cmin[a] = std::min(cmin[a], centre[3 * i + a]);
+      }
+    int64_t L[3] = {1, 1, 1};
+    if (ok) {
+      lat.resize(3 * n);
+      for (int64_t i = 0; i < n && ok; ++i)
+        for (int a = 0; a < 3; ++a) {
+          const double u = (centre[3 * i + a] - cmin[a]) / edge[a];
+          const double r = std::nearbyint(u);
+          ok = ok && std::fabs(u - r) <= 1e-9 && r < 1e6;
+          lat[3 * i + a] = (int32_t)r;
+          L[a] = std::max<int64_t>(L[a], (int64_t)r + 1);
+        }
+    }
+    ok = ok && (2 * L[0] - 1) * (2 * L[1] - 1) * (2 * L[2] - 1) <= ((int64_t)1 << 22);
+    if (ok) {
+      t->lattice = true;
+      t->Lx = (int)L[0];
+      t->Ly = (int)L[1];
+      t->Lz = (int)L[2];
+      for (int a = 0; a < 3; ++a) t->lat_edge[a] = edge[a];
+    }
+  }
   mt_status st = MT_OK;
+  if (t->lattice && (st = upload(&t->d_lat, lat.data(), 3 * n)) != MT_OK) {
+    free_tiles(t);
+    return st;
+  }
   if ((st = upload(&t->d_centre, centre, 3 * n)) != MT_OK || (st = upload(&t->d_edge, edge, 3 * n)) != MT_OK ||
       (st = upload(&t->d_Ms, msf.data(), n)) != MT_OK || (st = upload(&t->d_wex, wex.data(), 6 * n)) != MT_OK ||
       (st = upload(&t->d_nbr, nb.data(), 6 * n)) != MT_OK || (st = upload(&t->d_kan, kan.data(), n)) != MT_OK ||
@@ -374,6 +411,7 @@ mt_status mt_tiles_create_tetra(mt_ctx *ctx, int64_t nv, const double *vertices,
   mt_status st = mt_tiles_create(ctx, n, centre.data(), edge.data(), Ms, Aex, Ku, axis, nullptr, &t);
   if (st != MT_OK) return st;
   t->kind = MT_TILE_TETRA;
+  t->lattice = false;  // centroids may happen to sit on a lattice; the tiles are not cuboids
   std::vector<float> wex(6 * n, 0.0f);
   bool any = false;
   for (int64_t i = 0; i < n; ++i)

@@ -183,6 +183,23 @@ __device__ void tetra_tensor(const double *r, const double *v, double out[6]) {
   out[5] = k * N[2][2];
 }
 
+// One block per lattice offset (dx, dy, dz): the tensor of the tile at the
+// origin seen from (dx ex, dy ey, dz ez).  Index ((dx + Lx - 1)(2Ly - 1) +
+// dy + Ly - 1)(2Lz - 1) + dz + Lz - 1.
+__global__ void k_offset_table(int Lx, int Ly, int Lz, double ex, double ey, double ez, double *table) {
+  const int64_t Ny = 2 * Ly - 1, Nz = 2 * Lz - 1;
+  const int64_t tot = (int64_t)(2 * Lx - 1) * Ny * Nz;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= tot) return;
+  const int dz = (int)(t % Nz) - (Lz - 1);
+  const int dy = (int)((t / Nz) % Ny) - (Ly - 1);
+  const int dx = (int)(t / (Ny * Nz)) - (Lx - 1);
+  const double r[3] = {dx * ex, dy * ey, dz * ez};
+  const double c[3] = {0.0, 0.0, 0.0};
+  const double e[3] = {ex, ey, ez};
+  cuboid_tensor(r, c, e, table + 6 * t);
+}
+
 // Relations of tetrahedra i and j (i != j), as pair_relation: bit 0 = the
 // centroid of i lies in or on tetrahedron j (barycentric coordinates all
 // >= -eps), bit 1 = they share a vertex (a "near" pair).
@@ -243,6 +260,10 @@ struct AsmArgs {
   const double *centre, *edge;
   const double *vert;  // 12n, tetrahedral tiles
   int kind;            // MT_TILE_CUBOID / MT_TILE_TETRA
+  // uniform lattice: block (i, j) = table[offset lat_i - lat_j] (nullptr: evaluate)
+  const double *table;
+  const int32_t *lat;
+  int Lx, Ly, Lz;
   int64_t n;
   int TR, TC, nplane;
   int64_t Q;
@@ -284,7 +305,20 @@ __global__ void k_assemble(AsmArgs A) {
       ci[a] = A.centre[3 * i + a];
       ei[a] = A.edge[3 * i + a];
     }
-    int rel = (i == j) ? 2 : tet ? tetra_relation(ci, A.vert + 12 * i, vj) : pair_relation(ci, ei, cj, ej);
+    int rel;
+    int64_t toff = 0;
+    if (A.table) {
+      // lattice: the offset decides everything (a repeated index = overlap,
+      // touching = at most one step on every axis)
+      const int dx = A.lat[3 * i] - A.lat[3 * j], dy = A.lat[3 * i + 1] - A.lat[3 * j + 1];
+      const int dz = A.lat[3 * i + 2] - A.lat[3 * j + 2];
+      const bool same = dx == 0 && dy == 0 && dz == 0;
+      const bool touch = dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1;
+      rel = (i == j) ? 2 : ((same ? 1 : 0) | (touch ? 2 : 0));
+      toff = ((int64_t)(dx + A.Lx - 1) * (2 * A.Ly - 1) + (dy + A.Ly - 1)) * (2 * A.Lz - 1) + (dz + A.Lz - 1);
+    } else {
+      rel = (i == j) ? 2 : tet ? tetra_relation(ci, A.vert + 12 * i, vj) : pair_relation(ci, ei, cj, ej);
+    }
     if (rel & 1) atomicExch(A.bad, 1);
     const bool near = (rel & 2) && (A.prec == MT_BF16_SCALED || A.prec == MT_BF16_SPLIT);
     if (A.count_only) {
@@ -292,10 +326,14 @@ __global__ void k_assemble(AsmArgs A) {
       continue;
     }
     double N6[6];
-    if (tet)
+    if (A.table) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) N6[e] = A.table[6 * toff + e];
+    } else if (tet) {
       tetra_tensor(ci, vj, N6);
-    else
+    } else {
       cuboid_tensor(ci, cj, ej, N6);
+    }
     if (near) {
       const int slot = atomicAdd(&A.near_fill[i], 1);
       const int64_t at = A.near_ptr[i] + slot;
@@ -486,6 +524,19 @@ mt_status assemble(mt_tensor *T) {
   A.bad = d_bad;
   A.dense = T->layout == MT_LAYOUT_DENSE;
   A.Kp = T->Kp;
+  double *d_table = nullptr;
+  if (t->lattice && t->kind == MT_TILE_CUBOID) {
+    const int64_t cnt = (int64_t)(2 * t->Lx - 1) * (2 * t->Ly - 1) * (2 * t->Lz - 1);
+    MT_CUDA(cudaMalloc(&d_table, sizeof(double) * 6 * cnt));
+    k_offset_table<<<(unsigned)((cnt + 127) / 128), 128>>>(t->Lx, t->Ly, t->Lz, t->lat_edge[0], t->lat_edge[1],
+                                                          t->lat_edge[2], d_table);
+    MT_CUDA(cudaGetLastError());
+    A.table = d_table;
+    A.lat = t->d_lat;
+    A.Lx = t->Lx;
+    A.Ly = t->Ly;
+    A.Lz = t->Lz;
+  }
   const bool has_near = (T->prec == MT_BF16_SCALED || T->prec == MT_BF16_SPLIT);
   dim3 grid((unsigned)L.Q, (unsigned)L.P);
   if (has_near) {
@@ -531,6 +582,7 @@ mt_status assemble(mt_tensor *T) {
   int bad = 0;
   MT_CUDA(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
   cudaFree(d_bad);
+  cudaFree(d_table);
   MT_CHECK(!bad, MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
   return MT_OK;
 }

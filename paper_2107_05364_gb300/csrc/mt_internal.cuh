@@ -84,6 +84,13 @@ struct mt_tiles {
   bool has_exchange = false;
   int kind = 0;                // MT_TILE_CUBOID or MT_TILE_TETRA
   double *d_vert = nullptr;    // 12n: the 4 vertices of each tetrahedron (kind tetra)
+  // uniform cuboid lattice (equal edges, centres on c0 + index * edge): a
+  // block depends only on the index offset of its two tiles, so assembly
+  // evaluates one block per offset and fills the tensor from that table
+  bool lattice = false;
+  int32_t *d_lat = nullptr;    // 3n lattice indices
+  int Lx = 0, Ly = 0, Lz = 0;  // lattice extents
+  double lat_edge[3] = {0, 0, 0};
 };
 
 enum { MT_TILE_CUBOID = 0, MT_TILE_TETRA = 1 };

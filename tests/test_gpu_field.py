@@ -69,6 +69,31 @@ def test_blocks_entry_matches_oracle(mt, ctx):
     assert _rel(g, r) <= 1e-12
 
 
+def test_lattice_duplicate_is_overlap(mt, ctx):
+    # a uniform lattice is assembled from its offset table; two tiles on one
+    # lattice point are an overlap there too
+    t = wl.film(4, 2, 1)
+    t.centre[5] = t.centre[2]
+    t.nbr = None  # (with exchange, creation already refuses a neighbour at zero distance)
+    tiles = mt.mt_tiles_create(ctx, t)
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_demag_assemble(tiles, "f32")
+    assert e.value.status == mt.MT_EOVERLAP
+
+
+def test_lattice_and_direct_assembly_agree(mt, ctx):
+    # the same film once on its lattice (offset table) and once with every
+    # centre moved by 1e-11 of an edge (off the lattice: evaluated per block)
+    t = wl.film(30, 8, 2, size=(150e-9, 40e-9, 6e-9))
+    tiles = mt.mt_tiles_create(ctx, t)
+    A = mt.mt_tensor_read_rows(mt.mt_demag_assemble(tiles, "f64"), 0, t.n)
+    t2 = wl.film(30, 8, 2, size=(150e-9, 40e-9, 6e-9))
+    t2.centre = t2.centre + 1e-11 * t2.edge * np.random.default_rng(0).uniform(-1, 1, t2.centre.shape)
+    B = mt.mt_tensor_read_rows(mt.mt_demag_assemble(mt.mt_tiles_create(ctx, t2), "f64"), 0, t.n)
+    assert _rel(A, B) < 1e-9
+    assert _rel(A, oracle.demag_tensor(t.centre, t.edge)) <= 1e-12
+
+
 def test_overlap_is_rejected(mt, ctx):
     t = wl.film(4, 2, 1)
     t.centre[1] = t.centre[0] + np.array([0.25, 0.0, 0.0]) * t.edge[0]

@@ -99,3 +99,41 @@ def test_integrator_on_thresholded_tensor(mt, ctx):
                                     oracle.ode_opts(fixed_h=h), 0.0, 20 * h, 1)
     assert st == oracle.OK
     assert np.abs(mg - mo).max() <= 2e-5
+
+
+def test_threshold_full_size_sampled_rows(mt, ctx):
+    # the time-vs-error workload (standard-problem-4 film at 160 x 40 x 1,
+    # n = 6,400) at 40 %: properties that hold at any size, on sampled rows
+    import torch
+    t = wl.film(160, 40, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    _, _, nz = mt.mt_tensor_threshold(T, 0.0)
+    S, thr, kept = mt.mt_tensor_threshold(T, 0.4)
+    k = int(0.4 * nz)
+    assert nz - kept in (k, k - 1)  # exactly k, or k - 1 when the cut splits an entry's two copies
+    rows = np.unique(np.concatenate([[0, t.n - 1, 3200], np.random.default_rng(2).integers(0, t.n, 12)]))
+    t32 = np.float32(thr)
+    for i in rows:
+        full = mt.mt_tensor_read_rows(T, int(i), int(i) + 1)[0]
+        kept_row = mt.mt_tensor_read_rows(S, int(i), int(i) + 1)[0]
+        a = np.abs(full.astype(np.float32))
+        on = kept_row != 0
+        np.testing.assert_array_equal(kept_row[on], full[on])  # kept values untouched
+        assert np.all(a[on] >= t32)                            # kept: at or above the cut
+        assert np.all(a[(~on) & (a > 0)] <= t32)               # dropped: at or below it
+        assert np.all(a[a > t32] > 0) and np.all(on[a > t32])  # everything above the cut kept
+    # the sparse field on the sampled rows: FP64 product of the kept values
+    m = wl.m_random(t.n, seed=4).astype(np.float32)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    H = torch.full_like(mg, float("nan"))
+    mt.mt_demag_field(S, mg, H)
+    torch.cuda.synchronize()
+    Hg = H.cpu().numpy().reshape(-1, 3)[rows]
+    x = (t.Ms[:, None] * m.astype(np.float64))
+    ref = []
+    for i in rows:
+        blk = mt.mt_tensor_read_rows(S, int(i), int(i) + 1)[0]
+        full = oracle.six_to_full(blk[None])[0]  # (n, 3, 3)
+        ref.append(-np.einsum("jab,jb->a", full, x))
+    assert _rel(Hg, np.array(ref)) < 1e-6

@@ -505,8 +505,9 @@ mt_status assemble(mt_tensor *T) {
   mt_tiles *t = T->tiles;
   const int64_t n = T->n;
   const mt_layout &L = T->L;
-  int *d_bad = nullptr;
-  MT_CUDA(cudaMalloc(&d_bad, sizeof(int)));
+  DevTemp<int> bad_flag;
+  MT_CUDA(bad_flag.alloc(1));
+  int *d_bad = bad_flag.p;
   MT_CUDA(cudaMemset(d_bad, 0, sizeof(int)));
   AsmArgs A{};
   A.centre = t->d_centre;
@@ -524,10 +525,12 @@ mt_status assemble(mt_tensor *T) {
   A.bad = d_bad;
   A.dense = T->layout == MT_LAYOUT_DENSE;
   A.Kp = T->Kp;
+  DevTemp<double> table;
   double *d_table = nullptr;
   if (t->lattice && t->kind == MT_TILE_CUBOID) {
     const int64_t cnt = (int64_t)(2 * t->Lx - 1) * (2 * t->Ly - 1) * (2 * t->Lz - 1);
-    MT_CUDA(cudaMalloc(&d_table, sizeof(double) * 6 * cnt));
+    MT_CUDA(table.alloc(6 * cnt));
+    d_table = table.p;
     k_offset_table<<<(unsigned)((cnt + 127) / 128), 128>>>(t->Lx, t->Ly, t->Lz, t->lat_edge[0], t->lat_edge[1],
                                                           t->lat_edge[2], d_table);
     MT_CUDA(cudaGetLastError());
@@ -540,8 +543,9 @@ mt_status assemble(mt_tensor *T) {
   const bool has_near = (T->prec == MT_BF16_SCALED || T->prec == MT_BF16_SPLIT);
   dim3 grid((unsigned)L.Q, (unsigned)L.P);
   if (has_near) {
-    int *d_fill = nullptr;
-    MT_CUDA(cudaMalloc(&d_fill, sizeof(int) * n));
+    DevTemp<int> fill;
+    MT_CUDA(fill.alloc(n));
+    int *d_fill = fill.p;
     MT_CUDA(cudaMemset(d_fill, 0, sizeof(int) * n));
     A.near_fill = d_fill;
     A.count_only = 1;
@@ -573,7 +577,6 @@ mt_status assemble(mt_tensor *T) {
       MT_CUDA(cudaGetLastError());
     }
     MT_CUDA(cudaDeviceSynchronize());
-    cudaFree(d_fill);
   } else {
     k_assemble<<<grid, L.TC>>>(A);
     MT_CUDA(cudaGetLastError());
@@ -581,8 +584,6 @@ mt_status assemble(mt_tensor *T) {
   }
   int bad = 0;
   MT_CUDA(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
-  cudaFree(d_bad);
-  cudaFree(d_table);
   MT_CHECK(!bad, MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
   return MT_OK;
 }

@@ -95,6 +95,20 @@ struct mt_tiles {
 
 enum { MT_TILE_CUBOID = 0, MT_TILE_TETRA = 1 };
 
+// Device temporary of a host function, freed when the function returns (on
+// the error paths of MT_CUDA / MT_CHECK too).
+template <typename T>
+struct DevTemp {
+  T *p = nullptr;
+  DevTemp() = default;
+  DevTemp(const DevTemp &) = delete;
+  DevTemp &operator=(const DevTemp &) = delete;
+  ~DevTemp() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t count) { return cudaMalloc(reinterpret_cast<void **>(&p), sizeof(T) * count); }
+};
+
 // Tile-blocked storage: the n x n grid of 3x3 blocks is cut into row panels
 // of TR tiles and column chunks of TC tiles.  Chunk (p, q) is contiguous and
 // holds NPLANE planes of TR x TC values (plane-major, then row, then column),

@@ -170,7 +170,7 @@ bool make_resident(mt_server *S, Geometry &g, const std::vector<Geometry *> &all
   mt_status st = mt_demag_assemble_ex(g.tiles, (mt_prec)S->o.prec, S->o.layout, &e->T);
   if (st == MT_OK) {
     std::vector<double> alpha(e->B, 0.5), Ha(3 * e->B, 0.0);
-    mt_llg_params p{S->o.gamma, alpha.data(), Ha.data(), S->o.form, 1};
+    mt_llg_params p{S->o.gamma, alpha.data(), Ha.data(), S->o.form, 1, nullptr};
     st = mt::integ_create_idle(e->T, &p, &S->o.ode, e->B, &e->I);
   }
   const size_t vec = sizeof(float) * 3 * (size_t)g.n * e->B;

@@ -33,14 +33,8 @@
 
 #include "mt_internal.cuh"
 
-// blocks per lane and step, and the resident blocks per SM asked of the
-// register allocator (64-thread blocks)
-#ifndef SPMV_V
-#define SPMV_V 4
-#endif
-#ifndef SPMV_MINB
-#define SPMV_MINB 1
-#endif
+// blocks per lane and step (4 measured fastest against 2; 64-thread blocks)
+constexpr int kSpmvV = 4;
 
 namespace {
 
@@ -166,14 +160,14 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int64_t Q, uin
     }
     at += __popc(mask);
   }
-  if (!FILL) {
+  if constexpr (!FILL) {
     if (lane == 0) cnt[i] = (int)at;
-    return;
-  }
-  for (int64_t a = at + lane; a < K4; a += 32) {
-    col[o + a] = 0;
+  } else {
+    for (int64_t a = at + lane; a < K4; a += 32) {
+      col[o + a] = 0;
 #pragma unroll
-    for (int e = 0; e < 6; ++e) rv[e * K4 + a] = 0.0f;
+      for (int e = 0; e < 6; ++e) rv[e * K4 + a] = 0.0f;
+    }
   }
 }
 
@@ -196,14 +190,8 @@ __device__ __forceinline__ float warp_sum2(float s, float c) {
   return s + c;
 }
 
-// V consecutive blocks of one row as vectors (V = 2 or 4)
+// V consecutive blocks of one row as vectors
 template <int V> struct Vec;
-template <> struct Vec<2> {
-  using F = float2;
-  using I = int2;
-  static __device__ __forceinline__ float at(const F &v, int q) { return q == 0 ? v.x : v.y; }
-  static __device__ __forceinline__ int at(const I &v, int q) { return q == 0 ? v.x : v.y; }
-};
 template <> struct Vec<4> {
   using F = float4;
   using I = int4;
@@ -215,7 +203,7 @@ template <> struct Vec<4> {
 // simulation consecutive; xs = float4 (Ms m, 0) per tile and simulation; each
 // lane takes V consecutive blocks per step (7 vector loads, V gathers)
 template <int V>
-__global__ void __launch_bounds__(64, SPMV_MINB) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
+__global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
                                              const int32_t *__restrict__ col, const float *__restrict__ val,
                                              const float4 *__restrict__ xs, float *H, const int *active) {
   using VF = typename Vec<V>::F;
@@ -291,7 +279,7 @@ namespace mt {
 
 void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int *active, cudaStream_t s) {
   const int64_t warps = T->n * (int64_t)B;
-  k_spmv<SPMV_V><<<(unsigned)((warps + 1) / 2), 64, 0, s>>>(T->n, B, T->d_sp_ptr, T->d_sp_col, T->d_sp_val,
+  k_spmv<kSpmvV><<<(unsigned)((warps + 1) / 2), 64, 0, s>>>(T->n, B, T->d_sp_ptr, T->d_sp_col, T->d_sp_val,
                                                            reinterpret_cast<const float4 *>(xs), H, active);
 }
 
@@ -314,8 +302,9 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   const mt_layout &L = T->L;
   const float *D = reinterpret_cast<const float *>(T->d_data);
   const int64_t nblk = L.P * L.Q * (int64_t)L.TR * L.TC;
-  unsigned long long *d_hist = nullptr;
-  MT_CUDA(cudaMalloc(&d_hist, sizeof(unsigned long long) * 65536));
+  DevTemp<unsigned long long> hist;
+  MT_CUDA(hist.alloc(65536));
+  unsigned long long *d_hist = hist.p;
   std::vector<unsigned long long> h(65536);
   const int grid = 4 * T->tiles->ctx->num_sms;
   // pass 1: top 16 bits
@@ -343,11 +332,12 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     tbits = (b1 << 16) | b2;
     r = rest2;
   }
-  cudaFree(d_hist);
   // tie order: copies of t before each row tile
+  DevTemp<unsigned long long> tie_start;
   unsigned long long *d_tie = nullptr;
   if (r > 0) {
-    MT_CUDA(cudaMalloc(&d_tie, sizeof(unsigned long long) * n));
+    MT_CUDA(tie_start.alloc(n));
+    d_tie = tie_start.p;
     k_row_ties<<<(unsigned)n, 256>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie);
     MT_CUDA(cudaGetLastError());
     std::vector<unsigned long long> ties(n);
@@ -361,13 +351,13 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     MT_CUDA(cudaMemcpy(d_tie, ties.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice));
   }
   // kept blocks per row
-  int *d_cnt = nullptr;
-  MT_CUDA(cudaMalloc(&d_cnt, sizeof(int) * n));
+  DevTemp<int> cnt_rows;
+  MT_CUDA(cnt_rows.alloc(n));
+  int *d_cnt = cnt_rows.p;
   k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr, nullptr);
   MT_CUDA(cudaGetLastError());
   std::vector<int> cnt(n);
   MT_CUDA(cudaMemcpy(cnt.data(), d_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
-  cudaFree(d_cnt);
   std::vector<int64_t> ptr(n + 1, 0);
   for (int64_t i = 0; i < n; ++i) ptr[i + 1] = ptr[i] + ((cnt[i] + 3) & ~3);
   const int64_t nnzb = ptr[n];
@@ -388,7 +378,6 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
       delete S;
       mt::tiles_release(T->tiles);
       mt::set_error("mt_tensor_threshold: %zu bytes exceed the context budget", need);
-      cudaFree(d_tie);
       return MT_ENOMEM;
     }
     ctx->in_use += S->bytes;
@@ -398,7 +387,6 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_val, 6 * sizeof(float) * std::max<int64_t>(1, nnzb));
   if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_ptr, ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    cudaFree(d_tie);
     mt::tensor_release(S);
     return mt::cuda_fail(e, "mt_tensor_threshold allocation", __FILE__, __LINE__);
   }
@@ -406,7 +394,6 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
                                     S->d_sp_val);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  cudaFree(d_tie);
   if (e != cudaSuccess) {
     mt::tensor_release(S);
     return mt::cuda_fail(e, "mt_tensor_threshold fill", __FILE__, __LINE__);

@@ -527,6 +527,10 @@ void launch_prep_dense_x(const mt_tensor *T, const float *m, int B, void *X, cud
 mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   const int Bp = dense_pad_batch(B);
   MT_CHECK(B >= 1 && B <= 128, MT_EINVAL, "batched product: B = %d outside 1..128 simulations per pass", B);
+  // TMA row coordinates are 32-bit: (row tile * K blocks + K block) * 128
+  MT_CHECK((T->Kp / GM) * (T->Kp / GK) * (int64_t)GM < ((int64_t)1 << 31), MT_EINVAL,
+           "batched product: the dense tensor (3n = %lld) exceeds the 32-bit TMA coordinate range",
+           (long long)(3 * T->n));
   const bool split = T->prec == MT_BF16_SPLIT;
   const __nv_bfloat16 *A = reinterpret_cast<const __nv_bfloat16 *>(T->d_data);
   const __nv_bfloat16 *x = reinterpret_cast<const __nv_bfloat16 *>(X);

@@ -450,17 +450,18 @@ mt_status make_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t r
 #define MT_GEMM_KPS_SPLIT 2
 #endif
 
-// K blocks per ring stage (see kps_of below)
-constexpr int kps_for(bool split) { return split ? MT_GEMM_KPS_SPLIT : 2; }
+// K blocks per ring stage (see kps_of below); the split product at a padded
+// batch of 128 holds one (two would need 160 KB a stage: no room for two)
+constexpr int kps_for(bool split, int Bp) { return split ? (Bp > 64 ? 1 : MT_GEMM_KPS_SPLIT) : 2; }
 
 int stage_bytes_for(int Bp, bool split) {
-  return kps_for(split) * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
+  return kps_for(split, Bp) * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
 }
 
 int stages_for(int Bp, bool split) {
   const int stage = stage_bytes_for(Bp, split);
   const int budget = 224 * 1024;
-  return std::max(2, std::min(8, budget / stage));
+  return std::max(2, std::min(8, budget / stage));  // >= 2 stages always fit (stage <= 112 KB)
 }
 
 }  // namespace
@@ -493,14 +494,14 @@ size_t dense_count_bytes(const mt_tensor *T) { return (size_t)(T->Kp / GM) * EPI
 // TMA, MMA and commit path cost a fixed few hundred cycles, so 16 KB tiles
 // alone left the BF16 product at 0.70 of HBM and two per stage reach 0.87;
 // the split product goes from 0.73 to 0.83 with a 2-deep ring of 112 KB)
-template <bool SPLIT>
+template <bool SPLIT, int BP>
 constexpr int kps_of() {
-  return kps_for(SPLIT);
+  return kps_for(SPLIT, BP);
 }
 
 template <bool SPLIT, int BP>
 cudaError_t prep_one() {
-  return cudaFuncSetAttribute(k_gemm<SPLIT, BP, kps_of<SPLIT>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_gemm<SPLIT, BP, kps_of<SPLIT, BP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               227 * 1024);
 }
 
@@ -552,7 +553,7 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   plan->Bp = Bp;
   plan->split = split;
   plan->stages = stages_for(Bp, split);
-  plan->kps = kps_for(split);
+  plan->kps = kps_for(split, Bp);
   plan->chunk = 4 / plan->kps;  // units per accumulator chunk: 4 K blocks either way
   return MT_OK;
 }
@@ -621,7 +622,8 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
   const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
 #define MT_GEMM_LAUNCH(SP, BPV) \
-  k_gemm<SP, BPV, kps_of<SP>()><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tX1, plan.tX2, P)
+  k_gemm<SP, BPV, kps_of<SP, BPV>()><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tX1, plan.tX2, \
+                                                                    P)
   if (plan.split) {
     switch (plan.Bp) {
       case 16: MT_GEMM_LAUNCH(true, 16); break;

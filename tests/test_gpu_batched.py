@@ -55,7 +55,7 @@ def test_dense_tensor_entries(mt, ctx, prec):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "split"])
-@pytest.mark.parametrize("B", [1, 3, 17, 64])
+@pytest.mark.parametrize("B", [1, 3, 17, 64, 100, 128])  # padded 16, 16, 32, 64, 128, 128
 def test_dense_field_parity(mt, ctx, prec, B):
     import torch
     t = wl.graded_film(29, 9, 2, (290e-9, 90e-9, 6e-9), seed=6)   # 3n = 1566: ragged 128-row tiles

@@ -768,6 +768,78 @@ def run_tetra(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sp4(args):
+    """Standard problem 4 as the paper times it (Sec. 4.3): the film
+    500 x 125 x 3 nm on grids [20n, 5n, 1], n = 1 ... 9; the s-state is
+    relaxed first (untimed), then the dynamic part -- 1 ns under field 1 and
+    under field 2, LL form with the paper's gamma = 2.21e5 and
+    alpha = 4.42e3, rtol = atol = 1e-6 -- is timed: each field as its own
+    simulation (as the paper runs them), both fields as one batch of 2, and
+    the FP64 oracle on the host cores for the smallest grids."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2107_05364_gb300 import binding as mt
+    ctx = mt.mt_ctx_create(0)
+    fields = np.stack([FIELD1, np.array([-35.5e-3, -6.3e-3, 0.0]) / MU0])
+    opts = dict(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11)
+    rows = []
+    for k in range(1, args.sp4_max + 1):
+        t = wl.film(20 * k, 5 * k, 1)
+        tiles = mt.mt_tiles_create(ctx, t)
+        T = mt.mt_demag_assemble(tiles, "f32")
+        p0, k0 = mt.llg_params(1, alpha=0.5)
+        I = mt.Integrator(T, p0, mt.ode_opts(rtol=1e-5, atol=1e-5))
+        I.set_state(wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32).ravel())
+        I.run(5e-9, 1, check=False)
+        s_state = I.get_state()[0].copy()
+        I.close()
+        row = {"n": k, "grid": [20 * k, 5 * k, 1], "tiles": t.n}
+        single = 0.0
+        rhs = 0
+        for f in range(2):
+            p, keep = mt.llg_params(1, gamma=2.21e5, alpha=4.42e3, Ha=fields[f], form=mt.MT_FORM_LL)
+            J = mt.Integrator(T, p, mt.ode_opts(**opts))
+            J.set_state(s_state.ravel())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, mavg, st = J.run(1e-9, 100, check=False)
+            single += time.perf_counter() - t0
+            rhs += st[0]["n_rhs"]
+            if f == 0:
+                row["mavg_1ns_field1"] = [float(x) for x in mavg[-1, 0]]
+            J.close()
+        p, keep = mt.llg_params(2, gamma=2.21e5, alpha=4.42e3, Ha=fields, form=mt.MT_FORM_LL)
+        J = mt.Integrator(T, p, mt.ode_opts(**opts), B=2)
+        J.set_state(np.tile(s_state.ravel(), 2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J.run(1e-9, 100, check=False)
+        batched = time.perf_counter() - t0
+        J.close()
+        row.update({"gpu_fields_one_by_one_s": single, "gpu_fields_batched_s": batched, "rhs_evals": rhs})
+        if k <= args.sp4_cpu_max:
+            # CPU baseline of this workload: the FP64 oracle, as it stands
+            import oracle
+            md = oracle.Model.from_tiles(t)
+            t0 = time.perf_counter()
+            for f in range(2):
+                oracle.integrate(md, s_state.astype(np.float64),
+                                 oracle.llg_params(gamma=2.21e5, alpha=4.42e3, Ha=fields[f], form=1),
+                                 oracle.ode_opts(**opts), 0.0, 1e-9, 1)
+            row["cpu_baseline"] = {"value": time.perf_counter() - t0, "unit": "s", "cores": oracle.num_threads(),
+                                   "kind": "oracle", "sample": "fields 1 and 2, 1 ns each, FP64 stored tensor"}
+        rows.append(row)
+        print("SP4 n=%d (%d tiles): GPU %.2f s (batched %.2f s)%s" % (
+            k, t.n, single, batched,
+            "" if "cpu_baseline" not in row else ", CPU oracle %.1f s" % row["cpu_baseline"]["value"]),
+            file=sys.stderr, flush=True)
+        T.close()
+    line = {"metric": "SP4 dynamic part wall time (fields 1 and 2, 1 ns each)", "value": rows[-1]["gpu_fields_one_by_one_s"],
+            "unit": "s (n = %d)" % rows[-1]["n"], "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+            "dtype": "f32", "config": {"workload": "sp4_film_grids_20n_5n_1_n1-%d" % args.sp4_max}, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def mt_pad(B):
     bp = 16
     while bp < B and bp < 128:
@@ -784,7 +856,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
     ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold", "hysteresis",
-                                                                   "crossover", "tetra"])
+                                                                   "crossover", "tetra", "sp4"])
+    ap.add_argument("--sp4-max", type=int, default=9, help="sp4: largest n of the [20n, 5n, 1] grids")
+    ap.add_argument("--sp4-cpu-max", type=int, default=3, help="sp4: largest n the CPU oracle runs")
     ap.add_argument("--resolutions", default="8,10,12,16,20,24", help="crossover: cube tiles per edge")
     ap.add_argument("--values", type=int, default=2, help="hysteresis: field values of the paper's schedule timed")
     ap.add_argument("--coarse", type=int, default=17, help="hysteresis: values of the coarse loop")
@@ -810,6 +884,8 @@ def main():
         run_crossover(args)
     elif args.workload == "tetra":
         run_tetra(args)
+    elif args.workload == "sp4":
+        run_sp4(args)
     else:
         run_ours(args)
 

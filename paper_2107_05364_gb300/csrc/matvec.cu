@@ -2,10 +2,12 @@
 //
 // The product is bound by HBM: every stored tensor value is read once per
 // right-hand side and used for 1.5 multiply-adds on average.  Design:
-//   * one persistent CTA per SM; the (simulation, panel, chunk) units are
-//     split evenly over the CTAs in storage order ("stream-K"), so every CTA
-//     streams one contiguous stretch of the tensor and the load is balanced
-//     to within one chunk whatever n is;
+//   * one persistent CTA per SM; the (simulation group, panel, chunk) units
+//     are split evenly over the CTAs in storage order ("stream-K"), so every
+//     CTA streams one contiguous stretch of the tensor and the load is
+//     balanced to within one chunk whatever n is; a group of up to 4
+//     simulations shares each chunk read (a batch of B reads the tensor
+//     ceil(B / 4) times, not B times);
 //   * a producer warp moves each chunk (48 KB, all 6 planes of TR x TC blocks)
 //     and the matching slice of the Ms-scaled magnetisation into a 4-stage
 //     shared-memory ring with bulk TMA copies (cp.async.bulk + mbarrier
@@ -55,16 +57,19 @@ struct MvCfg<MT_BF16_SPLIT> {
   static constexpr bool SCALED = false, SPLIT = true;
 };
 
-template <int PREC>
+template <int PREC, int SB>
 struct MvShape {
   using C = MvCfg<PREC>;
   static constexpr int RPW = C::TR / C::W;  // rows per consumer warp
   static constexpr int DATA_BYTES = C::NPLANE * C::TR * C::TC * (int)sizeof(typename C::T);
   static constexpr int SCALE_BYTES = C::SCALED ? C::TR * C::TC : 0;
-  static constexpr int XS_BYTES = 3 * C::TC * (int)sizeof(typename C::Acc);
-  static constexpr int STAGE_BYTES = DATA_BYTES + SCALE_BYTES + XS_BYTES;
-  static constexpr int SMEM_BYTES = C::STAGES * STAGE_BYTES + 2 * C::STAGES * 8 + 16;
+  static constexpr int XS_BYTES = 3 * C::TC * (int)sizeof(typename C::Acc);  // one simulation's slice
+  static constexpr int STAGE_BYTES = DATA_BYTES + SCALE_BYTES + SB * XS_BYTES;
+  // ring depth: up to C::STAGES within ~220 KB of shared memory
+  static constexpr int STAGES = (C::STAGES * STAGE_BYTES <= 220 * 1024) ? C::STAGES : (220 * 1024) / STAGE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16;
   static constexpr int THREADS = (C::W + 1) * 32;
+  static_assert(STAGES >= 2, "at least a double-buffered ring");
   static_assert(C::TC == 32 * C::VEC, "a warp covers one chunk row");
   static_assert(3 * RPW <= 32, "one lane per (row, component) in the flush");
   static_assert(DATA_BYTES % 16 == 0 && SCALE_BYTES % 16 == 0 && XS_BYTES % 16 == 0, "bulk copy sizes");
@@ -135,25 +140,38 @@ struct MvArgs {
   int B;
 };
 
-template <int PREC>
-__global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) {
+// SB simulations share every chunk read: unit = (group of SB simulations,
+// panel, chunk); the stage holds the chunk and the group's SB operand slices
+// and each tensor value is used for all of them.  (Members of a last, partial
+// group beyond B read simulation 0's slice and are not written.)
+__device__ __forceinline__ bool group_live(const MvArgs &A, int64_t g, int SB) {
+  if (!A.active) return true;
+  for (int s = 0; s < SB; ++s) {
+    const int64_t b = g * SB + s;
+    if (b < A.B && A.active[b]) return true;
+  }
+  return false;
+}
+
+template <int PREC, int SB>
+__global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs A) {
   using C = MvCfg<PREC>;
-  using S = MvShape<PREC>;
-  using T = typename C::T;
+  using S = MvShape<PREC, SB>;
   using Acc = typename C::Acc;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * S::STAGE_BYTES);
-  uint64_t *empty = full + C::STAGES;
-  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + C::STAGES);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES);
+  uint64_t *empty = full + S::STAGES;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + S::STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = gridDim.x, k = blockIdx.x;
   const int64_t PQ = A.P * A.Q;
-  const int64_t U = (int64_t)A.B * PQ;
+  const int64_t NG = (A.B + SB - 1) / SB;
+  const int64_t U = NG * PQ;
   const int64_t u0 = mtd::sk_begin(k, U, G), u1 = mtd::sk_begin(k + 1, U, G);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
+    for (int s = 0; s < S::STAGES; ++s) {
       mtd::mbar_init(&full[s], 1);
       mtd::mbar_init(&empty[s], C::W);
     }
@@ -172,11 +190,11 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
       int it = 0;
       for (int64_t u = u0; u < u1; ++u) {
         const int64_t gp = u / A.Q, q = u - gp * A.Q;
-        const int64_t b = gp / A.P, p = gp - b * A.P;
-        if (A.active && !A.active[b]) continue;
-        const int s = it % C::STAGES;
-        const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
-        if (it >= C::STAGES) {
+        const int64_t g = gp / A.P, p = gp - g * A.P;
+        if (!group_live(A, g, SB)) continue;
+        const int s = it % S::STAGES;
+        const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
+        if (it >= S::STAGES) {
           if (*abort_flag || !mtd::mbar_wait_bounded(&empty[s], ph ^ 1u, A.status)) {
             *abort_flag = 1;
             break;
@@ -188,21 +206,25 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
         if constexpr (C::SCALED)
           mtd::bulk_g2s(st + S::DATA_BYTES, A.scale + (size_t)(p * A.Q + q) * S::SCALE_BYTES, S::SCALE_BYTES,
                         &full[s], pol_stream);
-        mtd::bulk_g2s(st + S::DATA_BYTES + S::SCALE_BYTES, xs + (size_t)(b * A.Q + q) * S::XS_BYTES, S::XS_BYTES,
-                      &full[s], pol_keep);
+#pragma unroll
+        for (int m = 0; m < SB; ++m) {
+          const int64_t b = g * SB + m < A.B ? g * SB + m : 0;
+          mtd::bulk_g2s(st + S::DATA_BYTES + S::SCALE_BYTES + m * S::XS_BYTES,
+                        xs + (size_t)(b * A.Q + q) * S::XS_BYTES, S::XS_BYTES, &full[s], pol_keep);
+        }
         ++it;
       }
       // drain: every copy issued must have landed before the CTA may exit
-      for (int s = 0; s < C::STAGES && s < it; ++s) {
-        const int last = it - 1 - ((it - 1 - s) % C::STAGES);  // last issue on stage s
-        mtd::mbar_wait_bounded(&full[s], (uint32_t)(last / C::STAGES) & 1u, A.status);
+      for (int s = 0; s < S::STAGES && s < it; ++s) {
+        const int last = it - 1 - ((it - 1 - s) % S::STAGES);  // last issue on stage s
+        mtd::mbar_wait_bounded(&full[s], (uint32_t)(last / S::STAGES) & 1u, A.status);
       }
     }
     return;
   }
 
   // ---------------- consumers ----------------
-  Acc acc[S::RPW][3];
+  Acc acc[SB][S::RPW][3];
   int64_t gp_cur = -1;
   const int64_t first_panel = u0 / A.Q;
   int it = 0;
@@ -211,30 +233,44 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
   auto flush = [&](int64_t gp) {
     // lane sums -> every lane holds the warp totals
 #pragma unroll
-    for (int r = 0; r < S::RPW; ++r)
+    for (int m = 0; m < SB; ++m)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) acc[r][c] = mtd::warp_sum(acc[r][c]);
-    const int64_t b = gp / A.P, p = gp - b * A.P;
+      for (int r = 0; r < S::RPW; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[m][r][c] = mtd::warp_sum(acc[m][r][c]);
+    const int64_t g = gp / A.P, p = gp - g * A.P;
     const int64_t kf = mtd::sk_owner(gp * A.Q, U, G), kl = mtd::sk_owner(gp * A.Q + A.Q - 1, U, G);
     // this lane's (row, component)
     const int lr = lane / 3, lc = lane - 3 * (lane / 3);
-    Acc mine = 0;
+    Acc mine[SB];
 #pragma unroll
-    for (int r = 0; r < S::RPW; ++r)
+    for (int m = 0; m < SB; ++m) {
+      mine[m] = 0;
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (r == lr && c == lc) mine = acc[r][c];
+      for (int r = 0; r < S::RPW; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (r == lr && c == lc) mine[m] = acc[m][r][c];
+    }
     const int row_in_panel = warp * S::RPW + lr;
     const int64_t row = p * C::TR + row_in_panel;
-    Acc *H = reinterpret_cast<Acc *>(A.H) + (size_t)b * 3 * A.n;
     Acc *part = reinterpret_cast<Acc *>(A.part);
     const bool writer = lane < 3 * S::RPW;
+    auto out = [&](int m) -> Acc * {
+      const int64_t b = g * SB + m;
+      return (b < A.B && (!A.active || A.active[b])) ? reinterpret_cast<Acc *>(A.H) + (size_t)b * 3 * A.n : nullptr;
+    };
     if (kf == kl) {
-      if (writer && row < A.n) H[3 * row + lc] = -mine;
+      if (writer && row < A.n)
+#pragma unroll
+        for (int m = 0; m < SB; ++m)
+          if (Acc *H = out(m)) H[3 * row + lc] = -mine[m];
       return;
     }
     const int64_t slot = (gp == first_panel) ? 2 * k : 2 * k + 1;
-    if (writer) part[(slot * C::TR + row_in_panel) * 3 + lc] = mine;
+    if (writer)
+#pragma unroll
+      for (int m = 0; m < SB; ++m) part[((slot * SB + m) * C::TR + row_in_panel) * 3 + lc] = mine[m];
     __threadfence();
     __syncwarp();
     int last = 0;
@@ -245,31 +281,35 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
     last = __shfl_sync(0xffffffffu, last, 0);
     if (last) {
       __threadfence();
-      if (writer) {
-        Acc tot = 0;
-        for (int64_t kk = kf; kk <= kl; ++kk) {
-          const int64_t fp = mtd::sk_begin(kk, U, G) / A.Q;
-          const int64_t sl = (gp == fp) ? 2 * kk : 2 * kk + 1;
-          tot += __ldcg(&part[(sl * C::TR + row_in_panel) * 3 + lc]);
+      if (writer)
+        for (int m = 0; m < SB; ++m) {
+          Acc tot = 0;
+          for (int64_t kk = kf; kk <= kl; ++kk) {
+            const int64_t fp = mtd::sk_begin(kk, U, G) / A.Q;
+            const int64_t sl = (gp == fp) ? 2 * kk : 2 * kk + 1;
+            tot += __ldcg(&part[((sl * SB + m) * C::TR + row_in_panel) * 3 + lc]);
+          }
+          Acc *H = out(m);
+          if (H && row < A.n) H[3 * row + lc] = -tot;
         }
-        if (row < A.n) H[3 * row + lc] = -tot;
-      }
       if (lane == 0) A.count[gp * C::W + warp] = 0;  // ready for the next launch
     }
   };
 
   for (int64_t u = u0; u < u1; ++u) {
     const int64_t gp = u / A.Q;
-    const int64_t b = gp / A.P;
-    if (A.active && !A.active[b]) continue;
+    const int64_t g = gp / A.P;
+    if (!group_live(A, g, SB)) continue;
     if (gp != gp_cur) {
       if (gp_cur >= 0) flush(gp_cur);
       gp_cur = gp;
 #pragma unroll
-      for (int r = 0; r < S::RPW; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0;
+      for (int m = 0; m < SB; ++m)
+#pragma unroll
+        for (int r = 0; r < S::RPW; ++r) acc[m][r][0] = acc[m][r][1] = acc[m][r][2] = 0;
     }
-    const int s = it % C::STAGES;
-    const uint32_t ph = (uint32_t)(it / C::STAGES) & 1u;
+    const int s = it % S::STAGES;
+    const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
     ++it;
     if (!aborted) {
       if (*abort_flag || !mtd::mbar_wait_bounded(&full[s], ph, A.status)) {
@@ -279,10 +319,14 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
     }
     if (!aborted) {
       const unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
-      Acc X[C::VEC], Y[C::VEC], Z[C::VEC];
-      load_xs<PREC>(st + S::DATA_BYTES + S::SCALE_BYTES, 0, lane, X);
-      load_xs<PREC>(st + S::DATA_BYTES + S::SCALE_BYTES, 1, lane, Y);
-      load_xs<PREC>(st + S::DATA_BYTES + S::SCALE_BYTES, 2, lane, Z);
+      Acc X[SB][C::VEC], Y[SB][C::VEC], Z[SB][C::VEC];
+#pragma unroll
+      for (int m = 0; m < SB; ++m) {
+        const unsigned char *xsm = st + S::DATA_BYTES + S::SCALE_BYTES + m * S::XS_BYTES;
+        load_xs<PREC>(xsm, 0, lane, X[m]);
+        load_xs<PREC>(xsm, 1, lane, Y[m]);
+        load_xs<PREC>(xsm, 2, lane, Z[m]);
+      }
 #pragma unroll
       for (int r = 0; r < S::RPW; ++r) {
         const int row = warp * S::RPW + r;
@@ -293,7 +337,6 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
         load_vals<PREC>(st, 3, row, lane, nyy);
         load_vals<PREC>(st, 4, row, lane, nyz);
         load_vals<PREC>(st, 5, row, lane, nzz);
-        Acc sx = 0, sy = 0, sz = 0;
         if constexpr (C::SCALED) {
           // per-block power-of-two scale: value = stored * 2^s
           const uint2 sc = reinterpret_cast<const uint2 *>(st + S::DATA_BYTES)[row * (C::TC / 8) + lane];
@@ -301,22 +344,27 @@ __global__ void __launch_bounds__(MvShape<PREC>::THREADS, 1) k_matvec(MvArgs A) 
 #pragma unroll
           for (int v = 0; v < C::VEC; ++v) {
             const float f = __int_as_float(((int)e8[v] + 127) << 23);
-            const float xs_ = X[v] * f, ys_ = Y[v] * f, zs_ = Z[v] * f;
-            sx = fmaf(nxx[v], xs_, fmaf(nxy[v], ys_, fmaf(nxz[v], zs_, sx)));
-            sy = fmaf(nxy[v], xs_, fmaf(nyy[v], ys_, fmaf(nyz[v], zs_, sy)));
-            sz = fmaf(nxz[v], xs_, fmaf(nyz[v], ys_, fmaf(nzz[v], zs_, sz)));
-          }
-        } else {
-#pragma unroll
-          for (int v = 0; v < C::VEC; ++v) {
-            sx = fma(nxx[v], X[v], fma(nxy[v], Y[v], fma(nxz[v], Z[v], sx)));
-            sy = fma(nxy[v], X[v], fma(nyy[v], Y[v], fma(nyz[v], Z[v], sy)));
-            sz = fma(nxz[v], X[v], fma(nyz[v], Y[v], fma(nzz[v], Z[v], sz)));
+            nxx[v] *= f;
+            nxy[v] *= f;
+            nxz[v] *= f;
+            nyy[v] *= f;
+            nyz[v] *= f;
+            nzz[v] *= f;
           }
         }
-        acc[r][0] += sx;
-        acc[r][1] += sy;
-        acc[r][2] += sz;
+#pragma unroll
+        for (int m = 0; m < SB; ++m) {
+          Acc sx = 0, sy = 0, sz = 0;
+#pragma unroll
+          for (int v = 0; v < C::VEC; ++v) {
+            sx = fma(nxx[v], X[m][v], fma(nxy[v], Y[m][v], fma(nxz[v], Z[m][v], sx)));
+            sy = fma(nxy[v], X[m][v], fma(nyy[v], Y[m][v], fma(nyz[v], Z[m][v], sy)));
+            sz = fma(nxz[v], X[m][v], fma(nyz[v], Y[m][v], fma(nzz[v], Z[m][v], sz)));
+          }
+          acc[m][r][0] += sx;
+          acc[m][r][1] += sy;
+          acc[m][r][2] += sz;
+        }
       }
     }
     __syncwarp();
@@ -433,15 +481,36 @@ __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col,
   Hb[2] = rz.hi + rz.lo;
 }
 
+template <int PREC, int SB>
+cudaError_t prepare_mv_one() {
+  return cudaFuncSetAttribute(k_matvec<PREC, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              MvShape<PREC, SB>::SMEM_BYTES);
+}
+
 template <int PREC>
 cudaError_t prepare_mv() {
-  return cudaFuncSetAttribute(k_matvec<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, MvShape<PREC>::SMEM_BYTES);
+  cudaError_t e;
+  if ((e = prepare_mv_one<PREC, 1>()) != cudaSuccess || (e = prepare_mv_one<PREC, 2>()) != cudaSuccess) return e;
+  return prepare_mv_one<PREC, 4>();
+}
+
+// simulations per chunk read: 1, 2 or 4
+inline int mv_group(int B) { return B <= 1 ? 1 : B == 2 ? 2 : 4; }
+
+template <int PREC, int SB>
+void launch_mv_sb(const MvArgs &A, int64_t P, int64_t Q, int grid_cap, cudaStream_t s) {
+  using S = MvShape<PREC, SB>;
+  // never more CTAs than units: every CTA then owns at least one unit, which
+  // the panel bookkeeping (owners of a panel's first and last unit bound its
+  // contributors) relies on
+  const int64_t U = (int64_t)((A.B + SB - 1) / SB) * P * Q;
+  const int grid = (int)std::min<int64_t>(grid_cap, U);
+  k_matvec<PREC, SB><<<grid, S::THREADS, S::SMEM_BYTES, s>>>(A);
 }
 
 template <int PREC>
 void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, int *count, const int *active,
                int *status, cudaStream_t s) {
-  using S = MvShape<PREC>;
   MvArgs A;
   A.tensor = T->d_data;
   A.scale = T->d_scale;
@@ -455,12 +524,12 @@ void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, i
   A.P = T->L.P;
   A.Q = T->L.Q;
   A.B = B;
-  // never more CTAs than units: every CTA then owns at least one unit, which
-  // the panel bookkeeping (owners of a panel's first and last unit bound its
-  // contributors) relies on
-  const int64_t U = (int64_t)B * T->L.P * T->L.Q;
-  const int grid = (int)std::min<int64_t>(mt::matvec_grid(T), U);
-  k_matvec<PREC><<<grid, S::THREADS, S::SMEM_BYTES, s>>>(A);
+  const int cap = mt::matvec_grid(T);
+  switch (mv_group(B)) {
+    case 1: launch_mv_sb<PREC, 1>(A, T->L.P, T->L.Q, cap, s); break;
+    case 2: launch_mv_sb<PREC, 2>(A, T->L.P, T->L.Q, cap, s); break;
+    default: launch_mv_sb<PREC, 4>(A, T->L.P, T->L.Q, cap, s); break;
+  }
 }
 
 }  // namespace
@@ -497,7 +566,7 @@ int64_t xs_floats(const mt_tensor *T) {
 
 size_t matvec_part_bytes(const mt_tensor *T) {
   const size_t el = T->prec == MT_F64 ? 8 : 4;
-  return (size_t)2 * matvec_grid(T) * T->L.TR * 3 * el;
+  return (size_t)2 * matvec_grid(T) * 4 /*simulations per chunk read, at most*/ * T->L.TR * 3 * el;
 }
 
 size_t matvec_count_bytes(const mt_tensor *T, int B) { return (size_t)B * T->L.P * 8 /*W<=8*/ * sizeof(int); }

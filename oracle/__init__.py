@@ -429,13 +429,15 @@ def threshold_tensor(N, fraction):
     return out, float(t), kept
 
 
-def hysteresis(model: Model, m0, H, direction, opts, t_step, gamma=2.211e5, alpha=4000.0, form=1, precess=0):
+def hysteresis(model: Model, m0, H, direction, opts, t_step, gamma=2.211e5, alpha=4000.0, form=1, precess=0,
+               tol=0.0):
     """Sec. 4.1 (standard problem 2): the applied field takes the values
     H[s] * direction (A/m) in turn; at each value the state, carried over
-    from the previous one, is evolved for t_step seconds (the paper holds
-    every field value for a fixed time; LL form with the precession term
-    dropped and a large damping, as there).  Returns (status, <m> at the end
-    of each value (S, 3), final state)."""
+    from the previous one, is evolved for t_step seconds (tol = 0: the paper
+    holds every field value for a fixed time), or relaxed until the torque is
+    below tol with t_step as the cap (reaching the cap is not an error).  LL
+    form with the precession term dropped and a large damping, as the paper.
+    Returns (status, <m> at the end of each value (S, 3), final state)."""
     d = np.asarray(direction, np.float64)
     d = d / np.linalg.norm(d)
     m = np.asarray(m0, np.float64).reshape(-1, 3).copy()
@@ -443,7 +445,12 @@ def hysteresis(model: Model, m0, H, direction, opts, t_step, gamma=2.211e5, alph
     t = 0.0
     for s, h in enumerate(H):
         p = llg_params(gamma=gamma, alpha=alpha, Ha=h * d, form=form, precess=precess)
-        st, m, mav, _ = integrate(model, m, p, opts, t, t + t_step, 1)
+        if tol > 0:
+            st, m, _ = relax(model, m, p, opts, tol, t_step)
+            if st == ENOCONV:
+                st = OK
+        else:
+            st, m, mav, _ = integrate(model, m, p, opts, t, t + t_step, 1)
         if st != OK:
             return st, out, m
         out[s] = model.mean_m(m)

@@ -128,3 +128,28 @@ def test_sp2_loop_batched_over_d_lex(mt, ctx):
         hco, mro = oracle.loop_summary(H, mo, wl.SP2_DIR)
         assert (np.isnan(hc[b]) and np.isnan(hco)) or abs(hc[b] - hco) < 1e-3 * wl.SP4_MS
         np.testing.assert_allclose(mr[b], mro, atol=1e-4)
+
+
+def test_sp2_loop_relaxed_to_torque_matches_oracle(mt, ctx):
+    # the coarse-loop mode: each value relaxed until max |m x H| / Ms < 5e-3
+    # (cap 10 ns; the first values stop early, the ones near the switch run
+    # to the cap); two runs that stop below the same torque agree to about
+    # that torque over the stiffness of the softest mode
+    t = wl.sp2_film(20, 4, 1, d_lex=20.0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    H = wl.sp2_fields(7)
+    p, keep = mt.llg_params(1, alpha=4000.0, form=mt.MT_FORM_LL, precess=0)
+    opts = dict(rtol=1e-7, atol=1e-7, h0=1e-14, hmax=1e-10)
+    I = mt.Integrator(T, p, mt.ode_opts(**opts))
+    m0 = wl.m_noisy(t.n, wl.SP2_DIR, 1e-3, seed=0).astype(np.float32)
+    I.set_state(m0.ravel())
+    mavg, tau, hc, mr, st = I.hysteresis(wl.SP2_DIR, H, 10e-9, tol=5e-3)
+    md = oracle.Model.from_tiles(t)
+    sto, mo, _ = oracle.hysteresis(md, m0.astype(np.float64), H, wl.SP2_DIR, oracle.ode_opts(**opts), 10e-9,
+                                   tol=5e-3)
+    assert sto == oracle.OK
+    dev = np.abs(mavg[:, 0] - mo).max()
+    print("relax-to-torque loop: max |d<m>| %.2e, torque at the ends %s" % (dev, np.round(tau[:, 0], 6)))
+    assert dev < 2e-3
+    assert np.any(tau[:, 0] < 5e-3) and np.any(tau[:, 0] >= 5e-3)  # both endings occurred

@@ -286,6 +286,28 @@ def run_ours(args):
     # serving (full versions: --workload batched / --workload serving)
     extra = {}
     if world == 1 and not args.no_extras:
+        # the same film, one simulation, with the tensor stored in the other
+        # streaming precisions (BF16 with per-block scales, split BF16)
+        prec_rows = {}
+        for pname in ("bf16", "split"):
+            Tp = mt.mt_demag_assemble(tiles, pname)
+            Ip = mt.Integrator(Tp, p, mt.ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11))
+            Ip.set_state(m0.ravel())
+            Ip.step(3)
+            sp = torch.cuda.ExternalStream(Ip.stream_handle())
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            nst = max(20, min(args.steps, 200))
+            torch.cuda.synchronize()
+            k0.record(sp)
+            Ip.step(nst)
+            k1.record(sp)
+            torch.cuda.synchronize()
+            prec_rows[pname] = {"rhs_evals_per_s": 6.0 * nst / (k0.elapsed_time(k1) * 1e-3),
+                                "tensor_gb": Tp.info()["bytes"] / 1e9}
+            Ip.close()
+            Tp.close()
+        extra["stored_precisions_same_workload"] = prec_rows
         for h in (I, T, tiles):
             h.close()
         import argparse as _ap

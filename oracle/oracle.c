@@ -24,7 +24,7 @@
  *   - anisotropy field ........... Eq. 16
  *   - Zeeman field ............... Eq. 7
  *   - Landau-Lifshitz RHS ........ Eq. 1 (and its Gilbert-form equivalent)
- *   - RK(4,5) integration ........ Sec. 3.1 ("explicit Runge-Kutta (4,5)"),
+ *   - RK(4,5) integration ........ Sec. 3.1 (an explicit Runge-Kutta 4(5) pair),
  *                                   Dormand & Prince 1980 coefficients
  *   - relaxation ................. Sec. 4.1 (damping-only relaxation), Eq. 2
  *   - energy ..................... Eqs. 4, 6, 8, 11, 15

@@ -3,7 +3,7 @@
 // zero and the rest is stored as a sparse matrix, so the product reads only
 // what is kept.
 //
-// Reading of "the smallest fraction f of the nonzero elements": the elements
+// Reading of the rule (drop the smallest fraction f of the nonzero elements): the elements
 // are those of the full 3n x 3n matrix (an off-diagonal entry of a symmetric
 // 3x3 block stands for two), ranked by magnitude of the stored FP32 value,
 // ties in (row tile i, column tile j, entry) order with an off-diagonal

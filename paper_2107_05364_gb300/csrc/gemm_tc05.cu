@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tAlo,
            const __grid_constant__ CUtensorMap tX, const __grid_constant__ CUtensorMap tX1,
            const __grid_constant__ CUtensorMap tX2, GemmArgs P) {
+  mtd::pdl_enter();
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte aligned base for the swizzled tiles
   const uint32_t raw = mtd::smem_u32(smem_raw);
@@ -621,9 +622,9 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   const int64_t U = P.MT * P.KBU;
   const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
   const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
-#define MT_GEMM_LAUNCH(SP, BPV) \
-  k_gemm<SP, BPV, kps_of<SP, BPV>()><<<grid, GEMM_THREADS, smem, s>>>(plan.tA, plan.tAlo, plan.tX, plan.tX1, plan.tX2, \
-                                                                    P)
+#define MT_GEMM_LAUNCH(SP, BPV)                                                                              \
+  mt::launch_pdl(k_gemm<SP, BPV, kps_of<SP, BPV>()>, dim3(grid), dim3(GEMM_THREADS), smem, s, plan.tA, plan.tAlo, \
+                 plan.tX, plan.tX1, plan.tX2, P)
   if (plan.split) {
     switch (plan.Bp) {
       case 16: MT_GEMM_LAUNCH(true, 16); break;

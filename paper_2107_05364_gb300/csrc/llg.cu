@@ -270,6 +270,7 @@ __device__ __forceinline__ void plan_attempt(const StageArgs &A, SimCtl &c) {
 // kernels
 // ---------------------------------------------------------------------------
 __global__ void k_begin(StageArgs A) {
+  mtd::pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (i >= A.n) return;
@@ -326,6 +327,7 @@ __global__ void k_commit(StageArgs A) {
 // S in 2..6 also forms the input of stage S+1; S == 7 closes the attempt.
 template <int S>
 __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
+  mtd::pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int b = blockIdx.y;
   if (!A.active[b]) return;  // uniform per block
@@ -672,7 +674,7 @@ StageArgs stage_args(mt_integrator *I) {
 template <int S>
 void launch_stage(mt_integrator *I, const StageArgs &A) {
   dim3 grid((unsigned)I->nblk, (unsigned)I->B);
-  k_stage<S><<<grid, kStageThreads, 0, I->stream>>>(A);
+  mt::launch_pdl(k_stage<S>, grid, dim3(kStageThreads), 0, I->stream, A);
 }
 
 // demag product of the stage input `m` into I->Hd (xs already formed)
@@ -695,7 +697,7 @@ void demag(mt_integrator *I, const float *m) {
 void enqueue_attempt(mt_integrator *I) {
   StageArgs A = stage_args(I);
   dim3 grid((unsigned)I->nblk, (unsigned)I->B);
-  k_begin<<<grid, kStageThreads, 0, I->stream>>>(A);
+  mt::launch_pdl(k_begin, grid, dim3(kStageThreads), 0, I->stream, A);
   demag(I, I->ys0);
   launch_stage<2>(I, A);
   demag(I, I->ys1);

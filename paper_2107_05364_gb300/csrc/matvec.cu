@@ -155,6 +155,7 @@ __device__ __forceinline__ bool group_live(const MvArgs &A, int64_t g, int SB) {
 
 template <int PREC, int SB>
 __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs A) {
+  mtd::pdl_enter();
   using C = MvCfg<PREC>;
   using S = MvShape<PREC, SB>;
   using Acc = typename C::Acc;
@@ -439,6 +440,7 @@ __device__ __forceinline__ void ff_fma_lazy(ff &acc, float2 v, float x) {
 template <bool FF>
 __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col, const float2 *val,
                        const float *m, int64_t sb, int64_t se, float *H, const int *active) {
+  mtd::pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * B) return;
   const int64_t i = t / B;
@@ -511,7 +513,7 @@ void launch_mv_sb(const MvArgs &A, int64_t P, int64_t Q, int grid_cap, cudaStrea
   // contributors) relies on
   const int64_t U = (int64_t)((A.B + SB - 1) / SB) * P * Q;
   const int grid = (int)std::min<int64_t>(grid_cap, U);
-  k_matvec<PREC, SB><<<grid, S::THREADS, S::SMEM_BYTES, s>>>(A);
+  mt::launch_pdl(k_matvec<PREC, SB>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
 }
 
 template <int PREC>
@@ -614,10 +616,13 @@ void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int
   if (T->near_count == 0) return;
   const int64_t tot = T->n * (int64_t)B;
   const unsigned grid = (unsigned)((tot + 255) / 256);
+  const int32_t *ptr = T->d_near_ptr, *col = T->d_near_col;
+  const float2 *hl = T->d_near_hl;
+  const int64_t n = T->n;
   if (T->prec == MT_BF16_SPLIT)
-    k_near<true><<<grid, 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl, m, sb, se, H, active);
+    mt::launch_pdl(k_near<true>, dim3(grid), dim3(256), 0, s, n, B, ptr, col, hl, m, sb, se, H, active);
   else
-    k_near<false><<<grid, 256, 0, s>>>(T->n, B, T->d_near_ptr, T->d_near_col, T->d_near_hl, m, sb, se, H, active);
+    mt::launch_pdl(k_near<false>, dim3(grid), dim3(256), 0, s, n, B, ptr, col, hl, m, sb, se, H, active);
 }
 
 }  // namespace mt

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mt.h"
@@ -94,6 +95,26 @@ struct mt_tiles {
 };
 
 enum { MT_TILE_CUBOID = 0, MT_TILE_TETRA = 1 };
+
+namespace mt {
+// launch with the programmatic-stream-serialisation attribute (the kernel
+// must start with mtd::pdl_enter)
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+}  // namespace mt
 
 // Device temporary of a host function, freed when the function returns (on
 // the error paths of MT_CUDA / MT_CHECK too).
@@ -258,6 +279,17 @@ void launch_rhs_plain(const mt_tensor *T, const float *m, const float *Hd, int B
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 namespace mtd {
+
+// Programmatic dependent launch (kernels of the step graph): wait until the
+// preceding kernel of the stream has completed and its writes are visible
+// (returns at once when the launch did not ask for it), then let the next
+// kernel be scheduled, so that its launch and prologue overlap this kernel.
+// Every kernel launched with mt::launch_pdl calls this before it touches
+// global memory that its predecessor writes or reads.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -206,6 +206,7 @@ template <int V>
 __global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
                                              const int32_t *__restrict__ col, const float *__restrict__ val,
                                              const float4 *__restrict__ xs, float *H, const int *active) {
+  mtd::pdl_enter();
   using VF = typename Vec<V>::F;
   using VI = typename Vec<V>::I;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -279,8 +280,9 @@ namespace mt {
 
 void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int *active, cudaStream_t s) {
   const int64_t warps = T->n * (int64_t)B;
-  k_spmv<kSpmvV><<<(unsigned)((warps + 1) / 2), 64, 0, s>>>(T->n, B, T->d_sp_ptr, T->d_sp_col, T->d_sp_val,
-                                                           reinterpret_cast<const float4 *>(xs), H, active);
+  mt::launch_pdl(k_spmv<kSpmvV>, dim3((unsigned)((warps + 1) / 2)), dim3(64), 0, s, T->n, B,
+                 (const int64_t *)T->d_sp_ptr, (const int32_t *)T->d_sp_col, (const float *)T->d_sp_val,
+                 reinterpret_cast<const float4 *>(xs), H, active);
 }
 
 void launch_prep_sparse_x(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {

@@ -44,10 +44,10 @@ MU0 = 4e-7 * math.pi
 # (1.0125 x the 2.4e9 algorithmic bytes: the zero padding of the last chunk
 # row).  Valid while k_matvec<f32> is unchanged.
 MATVEC_F32_N10000_TRAFFIC = 2427094016 + 2980864
-# The split tensor-core product at n = 8,000 read 1.0040 x its stored tensor
-# and wrote its field (one ncu capture of the stacked-operand kernel); the
-# batched line scales that per stored byte.
-SPLIT_GEMM_READ_PER_STORED_BYTE = 1.0040
+# The tensor-core products at n = 8,000 read 1.0040 (split) and 1.0028 (BF16)
+# x their stored tensors and wrote their fields (one ncu capture each of the
+# current kernels); the batched line scales that per stored byte.
+GEMM_READ_PER_STORED_BYTE = {"split": 1.0040, "bf16": 1.0028}
 FIELD1 = np.array([-24.6e-3, 4.3e-3, 0.0]) / MU0
 WORKLOAD = "sp4_film_200x50x1_n10000_f32"
 METRIC = "LLG RHS evals/s"
@@ -424,9 +424,8 @@ def run_batched(args, quiet=False):
         "vs_plain_fp32": value / plain, "plain_fp32_evals_per_s": plain,
         "roofline": {"bound": "hbm", "achieved": stored / (gemm_ms * 1e-3) / 1e9, "peak": float(peaks["hbm_gbs"]),
                      "unit": "GB/s", "frac": stored / (gemm_ms * 1e-3) / 1e9 / float(peaks["hbm_gbs"]),
-                     "traffic": (round(SPLIT_GEMM_READ_PER_STORED_BYTE * stored + 12 * n * B)
-                                 if args.prec == "split" else None),
-                     "traffic_note": "scaled from an n = 8,000 capture" if args.prec == "split" else None,
+                     "traffic": round(GEMM_READ_PER_STORED_BYTE[args.prec] * stored + 12 * n * B),
+                     "traffic_note": "scaled from an n = 8,000 capture",
                      "kernel": "k_gemm<%s>" % args.prec, "launch_ms": gemm_ms,
                      "tensor_tflops": flops / (gemm_ms * 1e-3) / 1e12,
                      "tensor_frac_of_bf16_peak": flops / (gemm_ms * 1e-3) / 1e12 / float(peaks["bf16_tflops"]),

@@ -861,6 +861,92 @@ def run_sp4(args):
     print(json.dumps(line), flush=True)
 
 
+def run_c1(args):
+    """The plain method at its smallest: the film 500 x 125 x 3 nm as
+    40 x 10 x 1 tiles (n = 400, FP32 tensor 3.8 MB, resident in L2), the
+    seed-0 state relaxed at alpha = 0.5 to a torque below 1e-6, then 1 ns of
+    Gilbert dynamics at alpha = 0.02 under field 1 with <m> every 1 ps.  At
+    this size a right-hand side is bound by kernel launch and grid-wide
+    dependency latency, not by HBM: reported as RHS evals/s and time per
+    step, beside the FP64 oracle running the same two phases on the host."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2107_05364_gb300 import binding as mt
+    ctx = mt.mt_ctx_create(0)
+    t = wl.film(40, 10, 1)
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    tiles = mt.mt_tiles_create(ctx, t)
+    t0 = time.perf_counter()
+    T = mt.mt_demag_assemble(tiles, "f32")
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    relax_o = dict(rtol=1e-5, atol=1e-5)
+    dyn_o = dict(rtol=1e-6, atol=1e-6)
+    p_r, k_r = mt.llg_params(1, alpha=0.5)
+    p_d, k_d = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+
+    def phases(path):
+        res = {}
+        for rep in range(2):  # the first pass warms up (graph capture, autotuning)
+            I = mt.Integrator(T, p_r, mt.ode_opts(**relax_o))
+            I.set_path(path)
+            I.set_state(m0.ravel())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s_r, st_r = I.relax(1e-6, 5e-9, check=False)
+            t_relax = time.perf_counter() - t0
+            m_rel = I.get_state()[0].copy()
+            I.close()
+            J = mt.Integrator(T, p_d, mt.ode_opts(**dyn_o))
+            J.set_path(path)
+            J.set_state(m_rel.ravel())
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, mavg, st_d = J.run(1e-9, 1000, check=False)
+            t_dyn = time.perf_counter() - t0
+            J.close()
+            res = {"relax_s": t_relax, "relax_status": int(s_r), "relax_tau": st_r[0]["tau"],
+                   "relax_rhs": st_r[0]["n_rhs"], "dynamics_s": t_dyn, "dynamics_rhs": st_d[0]["n_rhs"],
+                   "dynamics_accepted": st_d[0]["n_accept"]}
+        # the step itself: fixed steps back to back
+        F = mt.Integrator(T, p_d, mt.ode_opts(fixed_h=1e-13))
+        F.set_path(path)
+        F.set_state(m0.ravel())
+        F.step(args.warmup)
+        torch.cuda.synchronize()
+        steps = max(args.steps, 100)
+        t0 = time.perf_counter()
+        F.step(steps)
+        torch.cuda.synchronize()
+        res["ms_per_fixed_step"] = (time.perf_counter() - t0) * 1e3 / steps
+        res["fixed_step_rhs_evals_per_s"] = 6e3 / res["ms_per_fixed_step"]
+        F.close()
+        res["rhs_evals_per_s"] = (res["relax_rhs"] + res["dynamics_rhs"]) / (res["relax_s"] + res["dynamics_s"])
+        return res, mavg
+
+    res, mavg = phases(mt.MT_PATH_PERSISTENT)
+    graph, _ = phases(mt.MT_PATH_GRAPH)
+    line = {"metric": "LLG RHS evals/s", "value": res["rhs_evals_per_s"], "unit": "RHS evals/s", "n_gpus": 1,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": "film_40x10x1_n400_relax_then_1ns", "n": t.n, "path": "persistent"},
+            "assembly_s": t_asm, **res, "graph_path": graph}
+    if not args.no_cpu_baseline:
+        # CPU baseline of this workload: the FP64 oracle, as it stands
+        import oracle
+        md = oracle.Model.from_tiles(t)
+        t0 = time.perf_counter()
+        s1, m_o, st1 = oracle.relax(md, m0.astype(np.float64), oracle.llg_params(alpha=0.5),
+                                       oracle.ode_opts(**relax_o), 1e-6, 5e-9)
+        s2, _, trace, st2 = oracle.integrate(md, m_o, oracle.llg_params(alpha=0.02, Ha=FIELD1),
+                                             oracle.ode_opts(**dyn_o), 0.0, 1e-9, 1000)
+        wall = time.perf_counter() - t0
+        n_rhs = st1["n_rhs"] + st2["n_rhs"]
+        line["cpu_baseline"] = {"value": n_rhs / wall, "unit": "RHS evals/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": "the whole workload (relax + 1 ns), FP64 stored tensor",
+                                "wall_s": wall, "mavg_trace_max_dev_vs_gpu": float(np.abs(trace[:, :] - mavg[:, 0]).max())}
+    print(json.dumps(line), flush=True)
+
+
 def mt_pad(B):
     bp = 16
     while bp < B and bp < 128:
@@ -877,7 +963,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the compact batched and serving legs")
     ap.add_argument("--workload", default="film", choices=["film", "batched", "serving", "threshold", "hysteresis",
-                                                                   "crossover", "tetra", "sp4"])
+                                                                   "crossover", "tetra", "sp4", "c1"])
     ap.add_argument("--sp4-max", type=int, default=9, help="sp4: largest n of the [20n, 5n, 1] grids")
     ap.add_argument("--sp4-cpu-max", type=int, default=3, help="sp4: largest n the CPU oracle runs")
     ap.add_argument("--resolutions", default="8,10,12,16,20,24", help="crossover: cube tiles per edge")
@@ -907,6 +993,8 @@ def main():
         run_tetra(args)
     elif args.workload == "sp4":
         run_sp4(args)
+    elif args.workload == "c1":
+        run_c1(args)
     else:
         run_ours(args)
 

@@ -89,6 +89,16 @@ typedef enum {
   MT_FORM_LL = 1       /* Eq. 1: dm/dt = -gamma m x H - alpha m x (m x H)     */
 } mt_form;
 
+/* How an integrator executes its steps (mt_integrator_set_path). */
+typedef enum {
+  MT_PATH_GRAPH = 1,      /* one CUDA-graph replay per attempt: 6 demag       */
+                          /* products + 7 stage kernels; every tensor kind    */
+  MT_PATH_PERSISTENT = 2  /* a whole step/run/relax call as one cooperative    */
+                          /* kernel: each SM holds its rows of the tensor in   */
+                          /* shared memory, grid barriers between the stages; */
+                          /* FP32 streaming tensors of small tile sets         */
+} mt_path;
+
 typedef struct mt_ctx mt_ctx;
 typedef struct mt_tiles mt_tiles;
 typedef struct mt_tensor mt_tensor;
@@ -336,6 +346,17 @@ MT_API mt_status mt_integrator_get_state(mt_integrator *I, float *m, int m_is_ho
  * with events.  Use it to time or synchronise mt_integrator_step. */
 MT_API void *mt_integrator_stream(mt_integrator *I);
 
+/* Execution path (mt_path).  At creation an integrator takes
+ * MT_PATH_PERSISTENT where it fits -- an FP32 streaming tensor with at most
+ * 8 tiles per SM, whose rows and the B states of all tiles fit one SM's
+ * shared memory (about 1,000 tiles for B = 1) -- and MT_PATH_GRAPH
+ * otherwise.  Both compute the same stages with the same step control; they
+ * differ in the summation order of the demag product (FP32 round-off).
+ * The path may be switched between calls.  set: MT_EINVAL if the path is
+ * unknown or does not fit.  get: the path in use (0 for a NULL handle). */
+MT_API mt_status mt_integrator_set_path(mt_integrator *I, int path);
+MT_API int mt_integrator_get_path(mt_integrator *I);
+
 /* Change the applied field / damping of the batch (host arrays, copied). */
 MT_API mt_status mt_integrator_set_params(mt_integrator *I, const mt_llg_params *p);
 
@@ -401,6 +422,31 @@ MT_API mt_status mt_integrator_crossover(mt_integrator *I, const double *lam, in
 
 /* Per-simulation counters since the last set_state.  Synchronous. */
 MT_API mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats);
+
+/* Checkpoint / resume (no counterpart in the paper).  A checkpoint is a
+ * self-describing HOST byte image of the integrator's dynamic state: for
+ * every simulation its time, step size, step-control state and counters,
+ * its m (3n floats) and the derivative the next step starts from (the
+ * first-same-as-last stage of Dormand-Prince, 3n floats), plus a header
+ * (format version, n, B, the tensor's precision and layout) and a 64-bit
+ * FNV-1a checksum of everything before it.  Parameters (Ha, alpha, exchange
+ * factors) and options are not part of it: they are the integrator's own.
+ * mt_integrator_checkpoint_bytes gives the size (depends only on n and B).
+ * mt_integrator_checkpoint writes the image into buf (HOST, at least that
+ * many bytes).  mt_integrator_restore loads one into an integrator with the
+ * same n and B (the same or another handle, in this or another process);
+ * continuing from it takes bit for bit the steps the saved integrator would
+ * have taken with the same tensor, parameters and options (every reduction
+ * on the path runs in a fixed order, so this holds for adaptive steps too).
+ * Restored onto a tensor of another precision or layout, the saved
+ * derivative is dropped and re-evaluated on the new tensor.
+ * All three are synchronous.
+ * Errors: MT_EINVAL (NULL, buffer too small, wrong magic or version,
+ * n or B mismatch, checksum mismatch; the integrator is then unchanged),
+ * MT_ECUDA. */
+MT_API mt_status mt_integrator_checkpoint_bytes(mt_integrator *I, size_t *bytes);
+MT_API mt_status mt_integrator_checkpoint(mt_integrator *I, void *buf, size_t bytes);
+MT_API mt_status mt_integrator_restore(mt_integrator *I, const void *buf, size_t bytes);
 
 /* One-call forms of the above on DEVICE state m (B*3n floats, in/out). */
 MT_API mt_status mt_integrate(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, float *m, int B,

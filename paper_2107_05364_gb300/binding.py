@@ -20,6 +20,7 @@ MT_OK, MT_EINVAL, MT_ENOMEM, MT_EOVERLAP, MT_ENOCONV, MT_ETIMEOUT, MT_ENONFINITE
 MT_F64, MT_F32, MT_BF16_SCALED, MT_BF16_SPLIT = range(4)
 MT_FORM_GILBERT, MT_FORM_LL = 0, 1
 MT_LAYOUT_STREAM, MT_LAYOUT_DENSE, MT_LAYOUT_SPARSE = 0, 1, 2
+MT_PATH_GRAPH, MT_PATH_PERSISTENT = 1, 2
 PREC_NAMES = {"f64": MT_F64, "f32": MT_F32, "bf16": MT_BF16_SCALED, "bf16_scaled": MT_BF16_SCALED,
               "split": MT_BF16_SPLIT, "bf16_split": MT_BF16_SPLIT}
 
@@ -125,6 +126,11 @@ _SIGS = {
     "mt_integrator_hysteresis": (_I, [_P, _P, _P, _I64, _D, _D, _P, _P, _P, _P, _P]),
     "mt_integrator_crossover": (_I, [_P, _P, _I, _P, _P, _D, _D, _P, _P, _P, _P, _P]),
     "mt_integrator_stats": (_I, [_P, _P]),
+    "mt_integrator_checkpoint_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "mt_integrator_checkpoint": (_I, [_P, _P, ctypes.c_size_t]),
+    "mt_integrator_restore": (_I, [_P, _P, ctypes.c_size_t]),
+    "mt_integrator_set_path": (_I, [_P, _I]),
+    "mt_integrator_get_path": (_I, [_P]),
     "mt_integrate": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _P, _I, _D, _D, _I64, _P, _P,
                           _P]),
     "mt_relax": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _D, _D, _P, _I, _P, _P]),
@@ -443,6 +449,27 @@ class Integrator:
 
     def set_params(self, params: LlgParams):
         _check(lib().mt_integrator_set_params(self.h, ctypes.byref(params)), "mt_integrator_set_params")
+
+    def path(self) -> int:
+        """MT_PATH_GRAPH or MT_PATH_PERSISTENT: how the steps execute."""
+        return int(lib().mt_integrator_get_path(self.h))
+
+    def set_path(self, path: int):
+        _check(lib().mt_integrator_set_path(self.h, int(path)), "mt_integrator_set_path")
+
+    def checkpoint(self) -> bytes:
+        """Byte image of the dynamic state (times, step sizes, counters, m,
+        the next step's starting derivative); see mt_integrator_checkpoint."""
+        nb = ctypes.c_size_t()
+        _check(lib().mt_integrator_checkpoint_bytes(self.h, ctypes.byref(nb)), "mt_integrator_checkpoint_bytes")
+        buf = ctypes.create_string_buffer(nb.value)
+        _check(lib().mt_integrator_checkpoint(self.h, buf, nb.value), "mt_integrator_checkpoint")
+        return buf.raw
+
+    def restore(self, image: bytes):
+        """Load a checkpoint image (same n and B)."""
+        image = bytes(image)
+        _check(lib().mt_integrator_restore(self.h, ctypes.c_char_p(image), len(image)), "mt_integrator_restore")
 
     def stream_handle(self) -> int:
         """cudaStream_t of the integrator's launches (for timing)."""

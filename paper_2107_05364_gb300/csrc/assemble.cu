@@ -243,13 +243,6 @@ __device__ __forceinline__ int pair_relation(const double *ci, const double *ei,
   return ((vol || pt) ? 1 : 0) | (touch ? 2 : 0);
 }
 
-__device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, int e, int TR, int TC, int nplane,
-                                                int64_t Q) {
-  const int64_t p = i / TR, q = j / TC;
-  const int r = (int)(i - p * TR), c = (int)(j - q * TC);
-  return (((p * Q + q) * nplane + e) * TR + r) * (int64_t)TC + c;
-}
-
 __device__ __forceinline__ int64_t scale_index(int64_t i, int64_t j, int TR, int TC, int64_t Q) {
   const int64_t p = i / TR, q = j / TC;
   const int r = (int)(i - p * TR), c = (int)(j - q * TC);

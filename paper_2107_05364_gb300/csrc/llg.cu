@@ -107,39 +107,53 @@ __device__ __forceinline__ void cross3(const float a[3], const float b[3], float
 // Effective field of tile i (Eq. 5/17): H_d (from the demag product) + exchange
 // (finite volumes, Eq. 12; absent neighbour = Neumann, Eq. 3) + uniaxial
 // anisotropy (Eq. 16) + applied field (Eq. 7).
-__device__ __forceinline__ void effective_field(const StageArgs &A, const float *yin, const float *Hd, int64_t i,
-                                                int b, const float mi[3], float H[3]) {
-  const float *hd = Hd + (size_t)b * 3 * A.n + 3 * i;
-  const float *ha = A.Ha + 3 * b;
-  H[0] = hd[0] + ha[0];
-  H[1] = hd[1] + ha[1];
-  H[2] = hd[2] + ha[2];
-  if (A.exch) {
-    const float *yb = yin + (size_t)b * 3 * A.n;
+// H holds H_d on entry.  ha, xs: the simulation's applied field and exchange
+// factor; nbr6, wex6: the tile's six face neighbours (-1: none) and their
+// weights; ka, e: its anisotropy prefactor and axis; yb: the simulation's
+// state of all tiles (the neighbours' m).
+__device__ __forceinline__ void local_fields(const float *ha, float xs, bool exch, const int32_t *nbr6,
+                                             const float *wex6, float ka, const float *e, const float *yb,
+                                             const float mi[3], float H[3]) {
+  H[0] = H[0] + ha[0];
+  H[1] = H[1] + ha[1];
+  H[2] = H[2] + ha[2];
+  if (exch) {
     float he[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int f = 0; f < 6; ++f) {
-      const int32_t p = A.nbr[6 * i + f];
+      const int32_t p = nbr6[f];
       if (p >= 0) {
-        const float w = A.wex[6 * i + f];
+        const float w = wex6[f];
         he[0] += w * (yb[3 * p] - mi[0]);
         he[1] += w * (yb[3 * p + 1] - mi[1]);
         he[2] += w * (yb[3 * p + 2] - mi[2]);
       }
     }
-    const float xs = A.xsc ? A.xsc[b] : 1.0f;
     H[0] += xs * he[0];
     H[1] += xs * he[1];
     H[2] += xs * he[2];
   }
-  const float ka = A.kan[i];
   if (ka != 0.0f) {
-    const float *e = A.axis + 3 * i;
     const float me = mi[0] * e[0] + mi[1] * e[1] + mi[2] * e[2];
     H[0] += ka * me * e[0];
     H[1] += ka * me * e[1];
     H[2] += ka * me * e[2];
   }
+}
+
+__device__ __forceinline__ void add_local_fields(const StageArgs &A, const float *yb, int64_t i, int b,
+                                                 const float mi[3], float H[3]) {
+  local_fields(A.Ha + 3 * b, A.xsc ? A.xsc[b] : 1.0f, A.exch, A.nbr + 6 * i, A.wex + 6 * i, A.kan[i],
+               A.axis + 3 * i, yb, mi, H);
+}
+
+__device__ __forceinline__ void effective_field(const StageArgs &A, const float *yin, const float *Hd, int64_t i,
+                                                int b, const float mi[3], float H[3]) {
+  const float *hd = Hd + (size_t)b * 3 * A.n + 3 * i;
+  H[0] = hd[0];
+  H[1] = hd[1];
+  H[2] = hd[2];
+  add_local_fields(A, yin + (size_t)b * 3 * A.n, i, b, mi, H);
 }
 
 // Eq. 1 with prefactors g1 (precession) and g2 (damping):
@@ -246,11 +260,9 @@ __device__ bool reduce_across_blocks(const StageArgs &A, int b, double v[5], dou
   return threadIdx.x == 0;
 }
 
-__device__ __forceinline__ void finish_sim(const StageArgs &A, int b, SimCtl &c, int status) {
+__device__ __forceinline__ void finish_sim(SimCtl &c, int status) {
   c.done = 1;
   c.status = status;
-  A.active[b] = 0;
-  atomicSub(A.n_active, 1);
 }
 
 // Step size for the next attempt: the proposal h capped by hmax, shortened to
@@ -264,6 +276,74 @@ __device__ __forceinline__ void plan_attempt(const StageArgs &A, SimCtl &c) {
     c.clipped = 1;
   }
   c.hs = hs;
+}
+
+// After the first derivative of a run: its torque, and a relaxation that is
+// already below tolerance ends here.
+__device__ __forceinline__ void close_first(SimCtl &c, double tau) {
+  c.tau = tau;
+  c.n_rhs += 1;
+  c.fresh = 0;
+  if (!isfinite(c.tau)) finish_sim(c, MT_ENONFINITE);
+  else if (c.mode == MODE_RELAX && c.tau < c.tol) finish_sim(c, MT_OK);
+}
+
+// Step control after an attempt, from the simulation's reduced sums tot =
+// (sum of squared scaled errors, max torque, volume-weighted <m>): accept or
+// reject, advance the time, record an output (*out_row = its index, else
+// -1), finish on the end time, on the torque tolerance or on the attempt
+// cap, choose the next step size and plan the next attempt.
+__device__ __forceinline__ void close_attempt(const StageArgs &A, SimCtl &c, const double tot[5], int64_t *out_row) {
+  *out_row = -1;
+  const bool fixed = A.fixed_h > 0.0;
+  const double err = sqrt(tot[0] / (3.0 * (double)A.n));
+  const double tau = tot[1];
+  c.err = err;
+  c.n_attempt += 1;
+  c.n_rhs += 6;
+  const bool finite = isfinite(err) && isfinite(tot[2]) && isfinite(tot[3]) && isfinite(tot[4]);
+  const bool accept = finite && (fixed || err <= 1.0);
+  if (!finite) {
+    c.accepted = 0;
+    finish_sim(c, MT_ENONFINITE);
+    return;
+  }
+  if (accept) {
+    c.n_accept += 1;
+    c.t = c.clipped ? c.t_next : c.t + c.hs;
+    c.tau = tau;
+    c.m_last[0] = tot[2];
+    c.m_last[1] = tot[3];
+    c.m_last[2] = tot[4];
+    if (c.mode == MODE_RUN && c.clipped) {
+      *out_row = c.iout;
+      c.iout += 1;
+      if (c.iout >= c.n_out) {
+        finish_sim(c, MT_OK);
+      } else {
+        c.t_next = (c.iout + 1 == c.n_out) ? c.t1 : c.t_out0 + (double)(c.iout + 1) * c.dt_out;
+      }
+    } else if (c.mode == MODE_RELAX) {
+      if (tau < c.tol) finish_sim(c, MT_OK);
+      else if (c.clipped) finish_sim(c, MT_ENOCONV);
+    }
+  } else {
+    c.n_reject += 1;
+  }
+  c.accepted = accept ? 1 : 0;
+  if (fixed) {
+    c.h = A.fixed_h;
+  } else {
+    // 0.9 err^(-1/5) clamped to [0.2, 5], in FP32 (a relative 1e-7 on the
+    // proposal is immaterial; FP64 transcendentals are slow on this part)
+    const float ef = (float)err;
+    double fac = ef > 0.0f ? (double)(0.9f * exp2f(-0.2f * log2f(ef))) : 5.0;
+    fac = fmin(5.0, fmax(0.2, fac));
+    c.h = c.hs * fac;
+    if (A.hmax > 0.0 && c.h > A.hmax) c.h = A.hmax;
+  }
+  if (!c.done && c.mode != MODE_STEPS && c.n_attempt >= c.attempt_cap) finish_sim(c, MT_ENOCONV);
+  plan_attempt(A, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -374,11 +454,11 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
     double tot[5];
     if (reduce_across_blocks(A, b, v, tot)) {
       SimCtl c = A.ctl[b];
-      c.tau = tot[1];
-      c.n_rhs += 1;
-      c.fresh = 0;
-      if (!isfinite(c.tau)) finish_sim(A, b, c, MT_ENONFINITE);
-      else if (c.mode == MODE_RELAX && c.tau < c.tol) finish_sim(A, b, c, MT_OK);
+      close_first(c, tot[1]);
+      if (c.done) {
+        A.active[b] = 0;
+        atomicSub(A.n_active, 1);
+      }
       A.ctl[b] = c;
     }
     return;
@@ -409,58 +489,479 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
     double tot[5];
     if (reduce_across_blocks(A, b, v, tot)) {
       SimCtl c = A.ctl[b];
-      const bool fixed = A.fixed_h > 0.0;
-      const double err = sqrt(tot[0] / (3.0 * (double)A.n));
-      const double tau = tot[1];
-      c.err = err;
-      c.n_attempt += 1;
-      c.n_rhs += 6;
-      const bool finite = isfinite(err) && isfinite(tot[2]) && isfinite(tot[3]) && isfinite(tot[4]);
-      const bool accept = finite && (fixed || err <= 1.0);
-      if (!finite) {
-        c.accepted = 0;
-        finish_sim(A, b, c, MT_ENONFINITE);
-        A.ctl[b] = c;
-        return;
+      int64_t row = -1;
+      close_attempt(A, c, tot, &row);
+      if (row >= 0) {
+        double *mo = A.mavg + ((size_t)row * A.B + b) * 3;
+        mo[0] = tot[2];
+        mo[1] = tot[3];
+        mo[2] = tot[4];
       }
-      if (accept) {
-        c.n_accept += 1;
-        c.t = c.clipped ? c.t_next : c.t + c.hs;
-        c.tau = tau;
-        c.m_last[0] = tot[2];
-        c.m_last[1] = tot[3];
-        c.m_last[2] = tot[4];
-        if (c.mode == MODE_RUN && c.clipped) {
-          double *mo = A.mavg + ((size_t)c.iout * A.B + b) * 3;
-          mo[0] = tot[2];
-          mo[1] = tot[3];
-          mo[2] = tot[4];
-          c.iout += 1;
-          if (c.iout >= c.n_out) {
-            finish_sim(A, b, c, MT_OK);
-          } else {
-            c.t_next = (c.iout + 1 == c.n_out) ? c.t1 : c.t_out0 + (double)(c.iout + 1) * c.dt_out;
-          }
-        } else if (c.mode == MODE_RELAX) {
-          if (tau < c.tol) finish_sim(A, b, c, MT_OK);
-          else if (c.clipped) finish_sim(A, b, c, MT_ENOCONV);
-        }
-      } else {
-        c.n_reject += 1;
+      if (c.done) {
+        A.active[b] = 0;
+        atomicSub(A.n_active, 1);
       }
-      c.accepted = accept ? 1 : 0;
-      if (fixed) {
-        c.h = A.fixed_h;
-      } else {
-        double fac = err > 0.0 ? 0.9 * pow(err, -0.2) : 5.0;
-        fac = fmin(5.0, fmax(0.2, fac));
-        c.h = c.hs * fac;
-        if (A.hmax > 0.0 && c.h > A.hmax) c.h = A.hmax;
-      }
-      if (!c.done && c.mode != MODE_STEPS && c.n_attempt >= c.attempt_cap) finish_sim(A, b, c, MT_ENOCONV);
-      plan_attempt(A, c);
       A.ctl[b] = c;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small tile sets: a whole run in one cooperative kernel
+// ---------------------------------------------------------------------------
+// Below about a thousand tiles the FP32 tensor is a few MB, a right-hand
+// side is a few microseconds of work, and the step graph's 13 dependent
+// launches per attempt are what the step costs.  Here one CTA per SM keeps
+// its rows of the tensor in shared memory for the whole call, the stage
+// inputs of all tiles pass through L2 between grid-wide barriers, and every
+// CTA takes the step-control decisions itself from the same per-CTA partial
+// sums reduced in the same fixed order (so all CTAs agree bit for bit): per
+// attempt 6 barriers before the 6 right-hand sides and one for the error
+// norm, no launches.  The arithmetic of each stage is the graph path's.
+constexpr int kSmallThreads = 256;
+constexpr int kSmallWarps = kSmallThreads / 32;
+
+struct SmallArgs {
+  StageArgs A;
+  const float *N;  // stored FP32 tensor, streaming layout
+  int TR, TC;
+  int64_t Q;
+  float *xg;                // 2 x B x 3n: stage inputs of all tiles (ping-pong)
+  float *part;              // [G][B][5] per-CTA partial sums
+  unsigned long long *bar;  // barrier words (kBarWords, zeroed before the launch)
+  int *abort_flag;          // a bounded wait gave up: every CTA leaves
+  int *status;              // device status word (MT_DEV_TIMEOUT)
+  int64_t iters;            // attempts at most
+  int init;                 // evaluate k1 and the torque at the state first
+  int R;                    // rows per CTA at most
+};
+
+// byte offsets of the dynamic shared memory of k_small_run
+struct SmallSmem {
+  size_t ctl, red, hd, y, k, tau, coef, par, nbr, wex, kan, axis, wv, Ms, M, N, total;
+};
+__host__ __device__ __forceinline__ size_t small_take(size_t &o, size_t bytes) {
+  const size_t at = o;
+  o += (bytes + 15) & ~(size_t)15;
+  return at;
+}
+__host__ __device__ __forceinline__ SmallSmem small_smem(int64_t n, int B, int R) {
+  SmallSmem s;
+  size_t o = 0;
+  s.ctl = small_take(o, sizeof(SimCtl) * B);
+  s.red = small_take(o, sizeof(float) * kSmallWarps * 3 * 8);
+  s.hd = small_take(o, sizeof(float) * B * R * 3);
+  s.y = small_take(o, sizeof(float) * B * R * 3);
+  s.k = small_take(o, sizeof(float) * 7 * B * R * 3);
+  s.tau = small_take(o, sizeof(float) * B * R);
+  s.coef = small_take(o, sizeof(float) * B * 36);  // (float)(h a_sj), s = 1..6, j < s
+  s.par = small_take(o, sizeof(float) * B * 6);    // g1, g2, Ha, exchange factor
+  s.nbr = small_take(o, sizeof(int32_t) * R * 6);  // the CTA's rows: neighbours,
+  s.wex = small_take(o, sizeof(float) * R * 6);    // exchange weights,
+  s.kan = small_take(o, sizeof(float) * R);        // anisotropy, axis,
+  s.axis = small_take(o, sizeof(float) * R * 3);
+  s.wv = small_take(o, sizeof(float) * R);         // volume weights
+  s.Ms = small_take(o, sizeof(float) * n);
+  s.M = small_take(o, sizeof(float) * B * 3 * n);
+  s.N = small_take(o, sizeof(float) * 6 * R * n);
+  s.total = o;
+  return s;
+}
+
+struct SmallSh {
+  SimCtl *ctl;
+  float *red, *hd, *y, *k, *tau, *coef, *par, *wex, *kan, *axis, *wv, *Ms, *M, *N;
+  int32_t *nbr;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Barrier words: [0] the arrival counter, which only grows (zeroed before
+// the launch): barrier k is complete when it reaches k x G.  The abort flag
+// sits on the next 128-byte line.
+constexpr int kBarLine = 16;  // 8-byte words per 128-byte line
+constexpr size_t kBarWords = kBarLine;
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident): the
+// CTA's writes are ordered before thread 0's release-add by the CTA barrier,
+// and the other CTAs' writes before its acquire-load of the completed count
+// (release/acquire at GPU scope, no full fences).  The wait is bounded:
+// after ~2 s (or once another CTA gave up) the status word gets
+// MT_DEV_TIMEOUT, the abort flag is raised and false is returned.
+__device__ __forceinline__ bool small_grid_sync(const SmallArgs &S, unsigned long long &k) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    k += 1;
+    const unsigned long long target = k * gridDim.x;
+    red_release_add_u64(S.bar, 1ull);
+    int ok = 1;
+    if (ld_acquire_u64(S.bar) < target) {
+      const uint64_t t0 = mtd::globaltimer_ns();
+      for (uint32_t it = 1;; ++it) {
+        if (ld_acquire_u64(S.bar) >= target) break;
+        if ((it & 63u) == 0u) {
+          if (*reinterpret_cast<volatile int *>(S.abort_flag)) {
+            ok = 0;
+            break;
+          }
+          if (mtd::globaltimer_ns() - t0 > 2000000000ull) {
+            atomicExch(S.status, MT_DEV_TIMEOUT);
+            atomicExch(S.abort_flag, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ float nan_maxf(float a, float b) { return (a > b || a != a) ? a : b; }
+
+// k_S of the CTA's rows [r0, r0 + nr) for every running simulation, from
+// the stage input of all tiles in sh.M: H_d = -N (Ms m) from the rows held
+// in sh.N, then the local fields and Eq. 1 (the arithmetic of k_stage); the
+// torque |m x H|/Ms into sh.tau.
+template <int RMAX>
+__device__ __forceinline__ void small_rhs(const StageArgs &A, const SmallSh &sh, float *kout, int R, int nr,
+                                          int64_t r0) {
+  const int64_t n = A.n;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const size_t pl = (size_t)R * n;  // entries of one plane of the CTA's rows
+  for (int b = 0; b < A.B; ++b) {
+    if (sh.ctl[b].done) continue;  // the same in every thread
+    float acc[RMAX][3];
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q) acc[q][0] = acc[q][1] = acc[q][2] = 0.0f;
+    const float *mb = sh.M + (size_t)b * 3 * n;
+    for (int64_t j = tid; j < n; j += kSmallThreads) {
+      const float ms = sh.Ms[j];
+      const float x0 = ms * mb[3 * j], x1 = ms * mb[3 * j + 1], x2 = ms * mb[3 * j + 2];
+#pragma unroll
+      for (int q = 0; q < RMAX; ++q) {
+        if (q < nr) {
+          const float *e = sh.N + (size_t)q * n + j;
+          const float nxx = e[0], nxy = e[pl], nxz = e[2 * pl], nyy = e[3 * pl], nyz = e[4 * pl], nzz = e[5 * pl];
+          acc[q][0] = fmaf(nxx, x0, fmaf(nxy, x1, fmaf(nxz, x2, acc[q][0])));
+          acc[q][1] = fmaf(nxy, x0, fmaf(nyy, x1, fmaf(nyz, x2, acc[q][1])));
+          acc[q][2] = fmaf(nxz, x0, fmaf(nyz, x1, fmaf(nzz, x2, acc[q][2])));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RMAX; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = mtd::warp_sum(acc[q][c]);
+        if (lane == 0 && q < nr) sh.red[w * 3 * RMAX + 3 * q + c] = v;
+      }
+    __syncthreads();
+    if (tid < 3 * nr) {
+      float s = 0.0f;
+      for (int ww = 0; ww < kSmallWarps; ++ww) s += sh.red[ww * 3 * RMAX + tid];
+      sh.hd[(size_t)b * R * 3 + tid] = -s;
+    }
+    __syncthreads();
+  }
+  for (int p = tid; p < A.B * nr; p += kSmallThreads) {
+    const int b = p / nr, q = p - (p / nr) * nr;
+    if (sh.ctl[b].done) continue;
+    const int64_t i = r0 + q;
+    const float *yb = sh.M + (size_t)b * 3 * n;
+    const float mi[3] = {yb[3 * i], yb[3 * i + 1], yb[3 * i + 2]};
+    const float *hd = sh.hd + ((size_t)b * R + q) * 3;
+    const float *pb = sh.par + 6 * b;
+    float H[3] = {hd[0], hd[1], hd[2]}, k[3];
+    local_fields(pb + 2, pb[5], A.exch, sh.nbr + 6 * q, sh.wex + 6 * q, sh.kan[q], sh.axis + 3 * q, yb, mi, H);
+    const float t = llg(pb[0], pb[1], mi, H, k) / sh.Ms[i];
+    float *ko = kout + ((size_t)b * R + q) * 3;
+    ko[0] = k[0];
+    ko[1] = k[1];
+    ko[2] = k[2];
+    sh.tau[(size_t)b * R + q] = t;
+  }
+  __syncthreads();
+}
+
+// all tiles' stage input (B x 3n floats written by every CTA before the
+// barrier) into shared memory, through L2
+__device__ __forceinline__ void small_load_state(float *sM, const float *src, size_t count) {
+  if ((count & 3) == 0) {  // src and sM are 16-byte aligned
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(sM);
+    for (size_t q = threadIdx.x; q < count / 4; q += kSmallThreads) d4[q] = __ldcg(s4 + q);
+  } else {
+    for (size_t q = threadIdx.x; q < count; q += kSmallThreads) sM[q] = __ldcg(src + q);
+  }
+  __syncthreads();
+}
+
+// Warp 0: the sums of the CTA's 5 values per simulation (sum, max, sum,
+// sum, sum over its rows, one lane per row) to part[g][b]; after the
+// barrier, every CTA's warp 0 adds the G partials of b in the same fixed
+// order (lane-strided, then a butterfly), so all CTAs hold the same totals.
+__device__ __forceinline__ void small_warp_reduce(float v[5]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    v[1] = nan_maxf(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+    v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
+    v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
+    v[4] += __shfl_xor_sync(0xffffffffu, v[4], o);
+  }
+}
+__device__ __forceinline__ void small_partial(const SmallArgs &S, int b, float v[5]) {
+  small_warp_reduce(v);
+  if ((threadIdx.x & 31) == 0) {
+    float *dst = S.part + ((size_t)blockIdx.x * S.A.B + b) * 5;
+    for (int q = 0; q < 5; ++q) dst[q] = v[q];
+  }
+}
+__device__ __forceinline__ void small_total(const SmallArgs &S, int b, double tot[5]) {
+  float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+  for (int g = threadIdx.x & 31; g < (int)gridDim.x; g += 32) {
+    const float *src = S.part + ((size_t)g * S.A.B + b) * 5;
+    acc[0] += __ldcg(&src[0]);
+    acc[1] = nan_maxf(acc[1], __ldcg(&src[1]));
+    acc[2] += __ldcg(&src[2]);
+    acc[3] += __ldcg(&src[3]);
+    acc[4] += __ldcg(&src[4]);
+  }
+  small_warp_reduce(acc);
+  for (int q = 0; q < 5; ++q) tot[q] = (double)acc[q];
+}
+
+// (float)(h a_sj) of every stage-input row s = 1..6 (the inputs of stages
+// 2..7) and j < s, per simulation: coef[36 b + 6 (s - 1) + j]
+__device__ __forceinline__ void small_coefficients(const StageArgs &A, const SmallSh &sh) {
+  for (int p = threadIdx.x; p < A.B * 36; p += kSmallThreads) {
+    const int b = p / 36, rj = p - b * 36, r = rj / 6, j = rj - r * 6;
+    if (j <= r) sh.coef[p] = (float)(sh.ctl[b].hs * c_dp_a[r + 1][j]);
+  }
+  __syncthreads();
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const StageArgs &A = S.A;
+  const int64_t n = A.n;
+  const int B = A.B, R = S.R;
+  const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = (int64_t)g * n / G, r1 = (int64_t)(g + 1) * n / G;
+  const int nr = (int)(r1 - r0);
+  const SmallSmem L = small_smem(n, B, R);
+  SmallSh sh;
+  sh.ctl = reinterpret_cast<SimCtl *>(smem + L.ctl);
+  sh.red = reinterpret_cast<float *>(smem + L.red);
+  sh.hd = reinterpret_cast<float *>(smem + L.hd);
+  sh.y = reinterpret_cast<float *>(smem + L.y);
+  sh.k = reinterpret_cast<float *>(smem + L.k);
+  sh.tau = reinterpret_cast<float *>(smem + L.tau);
+  sh.coef = reinterpret_cast<float *>(smem + L.coef);
+  sh.par = reinterpret_cast<float *>(smem + L.par);
+  sh.nbr = reinterpret_cast<int32_t *>(smem + L.nbr);
+  sh.wex = reinterpret_cast<float *>(smem + L.wex);
+  sh.kan = reinterpret_cast<float *>(smem + L.kan);
+  sh.axis = reinterpret_cast<float *>(smem + L.axis);
+  sh.wv = reinterpret_cast<float *>(smem + L.wv);
+  sh.Ms = reinterpret_cast<float *>(smem + L.Ms);
+  sh.M = reinterpret_cast<float *>(smem + L.M);
+  sh.N = reinterpret_cast<float *>(smem + L.N);
+  const size_t kpl = (size_t)B * R * 3;  // floats of one derivative plane
+  const size_t state = (size_t)B * 3 * n;
+  unsigned long long nbar = 0;  // barriers passed
+  bool ok = true;
+  const float atol = (float)A.atol, rtol = (float)A.rtol;
+
+  // control blocks and parameters, Ms, the CTA's rows of N (plane e, row q,
+  // column j) and their tile constants, the rows of y and of the derivative
+  // the next attempt starts from
+  for (int b = tid; b < B; b += kSmallThreads) {
+    sh.ctl[b] = A.ctl[b];
+    float *pb = sh.par + 6 * b;
+    pb[0] = A.g1[b];
+    pb[1] = A.g2[b];
+    pb[2] = A.Ha[3 * b];
+    pb[3] = A.Ha[3 * b + 1];
+    pb[4] = A.Ha[3 * b + 2];
+    pb[5] = A.xsc ? A.xsc[b] : 1.0f;
+  }
+  for (int64_t j = tid; j < n; j += kSmallThreads) sh.Ms[j] = A.Ms[j];
+  for (int64_t q = tid; q < (int64_t)6 * nr * n; q += kSmallThreads) {
+    const int64_t j = q % n, eq = q / n;
+    const int e = (int)(eq / nr), r = (int)(eq % nr);
+    sh.N[((size_t)e * R + r) * n + j] = S.N[layout_index(r0 + r, j, e, S.TR, S.TC, 6, S.Q)];
+  }
+  for (int q = tid; q < nr; q += kSmallThreads) {
+    const int64_t i = r0 + q;
+    for (int f = 0; f < 6; ++f) {
+      sh.nbr[6 * q + f] = A.nbr[6 * i + f];
+      sh.wex[6 * q + f] = A.wex[6 * i + f];
+    }
+    sh.kan[q] = A.kan[i];
+    for (int c = 0; c < 3; ++c) sh.axis[3 * q + c] = A.axis[3 * i + c];
+    sh.wv[q] = (float)A.wvol[i];
+  }
+  for (int p = tid; p < B * nr * 3; p += kSmallThreads) {
+    const int b = p / (nr * 3), qc = p - b * nr * 3;
+    const size_t o = (size_t)b * 3 * n + 3 * r0 + qc;
+    sh.y[(size_t)b * R * 3 + qc] = A.y[o];
+    sh.k[(size_t)b * R * 3 + qc] = A.k[0][o];
+  }
+  __syncthreads();
+
+  if (S.init) {  // k1 and the torque at the state
+    small_load_state(sh.M, A.y, state);
+    small_rhs<RMAX>(A, sh, sh.k, R, nr, r0);
+    if (warp == 0)
+      for (int b = 0; b < B; ++b) {
+        if (sh.ctl[b].done) continue;
+        float v[5] = {0.0f, lane < nr ? sh.tau[(size_t)b * R + lane] : 0.0f, 0.0f, 0.0f, 0.0f};
+        small_partial(S, b, v);
+      }
+    ok = small_grid_sync(S, nbar);
+    if (ok && warp == 0)
+      for (int b = 0; b < B; ++b) {
+        if (sh.ctl[b].done) continue;
+        double tot[5];
+        small_total(S, b, tot);
+        if (lane == 0) close_first(sh.ctl[b], tot[1]);
+        __syncwarp();
+      }
+    __syncthreads();
+  }
+
+  for (int64_t it = 0; ok && it < S.iters; ++it) {
+    bool any = false;
+    for (int b = 0; b < B; ++b) any = any || !sh.ctl[b].done;
+    if (!any) break;
+    small_coefficients(A, sh);
+    for (int st = 2; st <= 7 && ok; ++st) {
+      // this CTA's rows of the stage input y + sum_j (h a_sj) k_j
+      float *xo = S.xg + (size_t)(st & 1) * state;
+      for (int p = tid; p < B * nr; p += kSmallThreads) {
+        const int b = p / nr, q = p - (p / nr) * nr;
+        if (sh.ctl[b].done) continue;
+        const float *cf = sh.coef + 36 * b + 6 * (st - 2);
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int j = 0; j < st - 1; ++j) {
+          const float a = cf[j];
+          if (a != 0.0f) {
+            const float *kj = sh.k + j * kpl + ((size_t)b * R + q) * 3;
+            acc[0] += a * kj[0];
+            acc[1] += a * kj[1];
+            acc[2] += a * kj[2];
+          }
+        }
+        const float *y0 = sh.y + ((size_t)b * R + q) * 3;
+        float *d = xo + (size_t)b * 3 * n + 3 * (r0 + q);
+        d[0] = y0[0] + acc[0];
+        d[1] = y0[1] + acc[1];
+        d[2] = y0[2] + acc[2];
+      }
+      ok = small_grid_sync(S, nbar);
+      if (!ok) break;
+      small_load_state(sh.M, xo, state);
+      small_rhs<RMAX>(A, sh, sh.k + (st - 1) * kpl, R, nr, r0);
+    }
+    if (!ok) break;
+    // embedded error, torque and <m> at the 5th-order solution (the stage-7
+    // input), in FP32 over the CTA's rows: one lane per row
+    if (warp == 0)
+      for (int b = 0; b < B; ++b) {
+        if (sh.ctl[b].done) continue;
+        float v[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (lane < nr) {
+          const float hs = (float)sh.ctl[b].hs;
+          const int64_t i = r0 + lane;
+          const float *mi = sh.M + (size_t)b * 3 * n + 3 * i;
+          const float *y0 = sh.y + ((size_t)b * R + lane) * 3;
+          for (int c = 0; c < 3; ++c) {
+            float e = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+              if (c_dp_err[j] != 0.0) e = fmaf((float)c_dp_err[j], sh.k[j * kpl + ((size_t)b * R + lane) * 3 + c], e);
+            const float r = e * hs / (atol + rtol * fmaxf(fabsf(y0[c]), fabsf(mi[c])));
+            v[0] = fmaf(r, r, v[0]);
+          }
+          v[1] = sh.tau[(size_t)b * R + lane];
+          const float wv = sh.wv[lane] / sqrtf(mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2]);
+          v[2] = wv * mi[0];
+          v[3] = wv * mi[1];
+          v[4] = wv * mi[2];
+        }
+        small_partial(S, b, v);
+      }
+    ok = small_grid_sync(S, nbar);
+    if (!ok) break;
+    if (warp == 0)
+      for (int b = 0; b < B; ++b) {
+        if (sh.ctl[b].done) continue;
+        double tot[5];
+        small_total(S, b, tot);
+        if (lane == 0) {
+          int64_t row = -1;
+          close_attempt(A, sh.ctl[b], tot, &row);
+          if (g == 0 && row >= 0) {
+            double *mo = A.mavg + ((size_t)row * B + b) * 3;
+            mo[0] = tot[2];
+            mo[1] = tot[3];
+            mo[2] = tot[4];
+          }
+        }
+        __syncwarp();
+      }
+    __syncthreads();
+    // accepted: adopt the normalised 5th-order solution; k7 is the next k1
+    for (int p = tid; p < B * nr; p += kSmallThreads) {
+      const int b = p / nr, q = p - (p / nr) * nr;
+      if (!sh.ctl[b].accepted) continue;
+      const float *yn = sh.M + (size_t)b * 3 * n + 3 * (r0 + q);
+      const float inv = rsqrtf(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
+      float *y0 = sh.y + ((size_t)b * R + q) * 3;
+      float *k1 = sh.k + ((size_t)b * R + q) * 3;
+      const float *k7 = sh.k + 6 * kpl + ((size_t)b * R + q) * 3;
+      y0[0] = yn[0] * inv;
+      y0[1] = yn[1] * inv;
+      y0[2] = yn[2] * inv;
+      k1[0] = k7[0];
+      k1[1] = k7[1];
+      k1[2] = k7[2];
+    }
+    __syncthreads();
+  }
+  if (!ok) return;  // timed out: the status word tells the host
+  // write back: the state and the next derivative of this CTA's rows; CTA 0
+  // the control blocks (nothing left to commit) and the active set
+  for (int p = tid; p < B * nr * 3; p += kSmallThreads) {
+    const int b = p / (nr * 3), qc = p - b * nr * 3;
+    const size_t o = (size_t)b * 3 * n + 3 * r0 + qc;
+    A.y[o] = sh.y[(size_t)b * R * 3 + qc];
+    A.k[0][o] = sh.k[(size_t)b * R * 3 + qc];
+  }
+  if (g == 0 && tid == 0) {
+    int na = 0;
+    for (int b = 0; b < B; ++b) {
+      SimCtl c = sh.ctl[b];
+      c.accepted = 0;
+      A.ctl[b] = c;
+      A.active[b] = c.done ? 0 : 1;
+      na += c.done ? 0 : 1;
+    }
+    *A.n_active = na;
   }
 }
 
@@ -624,6 +1125,14 @@ struct mt_integrator {
   int nblk = 0;
   bool need_init = true;
   std::vector<void *> allocs;
+  // small tile sets: the whole call in one cooperative kernel (k_small_run)
+  int path = MT_PATH_GRAPH;  // the one in use
+  bool small_ok = false;     // the tile set and batch fit it
+  int small_G = 0, small_R = 0, small_rmax = 0;
+  size_t small_smem_bytes = 0;
+  float *sm_xg = nullptr;
+  float *sm_part = nullptr;
+  unsigned long long *sm_bar = nullptr;  // barrier words, then the abort flag
 };
 
 namespace {
@@ -669,6 +1178,92 @@ StageArgs stage_args(mt_integrator *I) {
   A.hmax = I->o.hmax;
   A.fixed_h = I->o.fixed_h;
   return A;
+}
+
+constexpr size_t kSmallSmemMax = 225 * 1024;
+#ifndef MT_SMALL_MIN_ROWS
+#define MT_SMALL_MIN_ROWS 1
+#endif
+constexpr int kSmallMinRows = MT_SMALL_MIN_ROWS;  // of the 227 KB a CTA may opt in to
+
+template <int RMAX>
+cudaError_t small_attr(size_t bytes, int *per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_small_run<RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_small_run<RMAX>, kSmallThreads, bytes);
+  return e;
+}
+
+// Does the one-kernel path fit this tile set and batch?  FP32 streaming
+// tensor, at most 8 rows per CTA (one CTA per SM, up to one per tile), its
+// rows of N and the state of all tiles within the shared memory, and a
+// co-resident grid.
+bool small_plan(mt_integrator *I) {
+  const mt_tensor *T = I->T;
+  if (T->prec != MT_F32 || T->layout != MT_LAYOUT_STREAM) return false;
+  const int64_t n = T->n;
+  const int sms = T->tiles->ctx->num_sms;
+  if (n < 1 || sms < 1) return false;
+  // rows per CTA: enough to cover the tiles with one CTA per SM, and at
+  // least kSmallMinRows (fewer CTAs meet at each barrier)
+  const int64_t r_sm = (n + sms - 1) / sms;
+  const int R = (int)std::max<int64_t>(r_sm, std::min<int64_t>(kSmallMinRows, n));
+  if (R > 8) return false;
+  const int G = (int)((n + R - 1) / R);
+  const size_t bytes = small_smem(n, I->B, R).total;
+  if (bytes > kSmallSmemMax) return false;
+  const int rmax = R <= 2 ? 2 : R <= 4 ? 4 : 8;
+  int per_sm = 0;
+  const cudaError_t e = rmax == 2 ? small_attr<2>(bytes, &per_sm)
+                        : rmax == 4 ? small_attr<4>(bytes, &per_sm)
+                                    : small_attr<8>(bytes, &per_sm);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (per_sm < 1 || (int64_t)per_sm * sms < G) return false;
+  I->small_G = G;
+  I->small_R = R;
+  I->small_rmax = rmax;
+  I->small_smem_bytes = bytes;
+  return true;
+}
+
+mt_status launch_small(mt_integrator *I, int init, int64_t iters) {
+  const mt_tensor *T = I->T;
+  SmallArgs S{};
+  S.A = stage_args(I);
+  S.N = static_cast<const float *>(T->d_data);
+  S.TR = T->L.TR;
+  S.TC = T->L.TC;
+  S.Q = T->L.Q;
+  S.xg = I->sm_xg;
+  S.part = I->sm_part;
+  S.bar = I->sm_bar;
+  S.abort_flag = reinterpret_cast<int *>(I->sm_bar + kBarWords);
+  S.status = T->tiles->ctx->d_status;
+  S.iters = iters;
+  S.init = init;
+  S.R = I->small_R;
+  MT_CUDA(cudaMemsetAsync(I->sm_bar, 0, (kBarWords + kBarLine) * sizeof(unsigned long long), I->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)I->small_G);
+  cfg.blockDim = dim3(kSmallThreads);
+  cfg.dynamicSmemBytes = I->small_smem_bytes;
+  cfg.stream = I->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  switch (I->small_rmax) {
+    case 2: e = cudaLaunchKernelEx(&cfg, k_small_run<2>, S); break;
+    case 4: e = cudaLaunchKernelEx(&cfg, k_small_run<4>, S); break;
+    default: e = cudaLaunchKernelEx(&cfg, k_small_run<8>, S); break;
+  }
+  if (e != cudaSuccess) return mt::cuda_fail(e, "k_small_run launch", __FILE__, __LINE__);
+  I->need_init = false;
+  return MT_OK;
 }
 
 template <int S>
@@ -890,6 +1485,13 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
   MT_TRY(dalloc(I, &I->red_count, sizeof(int) * B));
   I->mavg_cap = 1;
   MT_TRY(dalloc(I, &I->mavg, sizeof(double) * 3 * B));
+  I->small_ok = small_plan(I);
+  if (I->small_ok) {
+    MT_TRY(dalloc(I, &I->sm_xg, 2 * vec));
+    MT_TRY(dalloc(I, &I->sm_part, sizeof(float) * 5 * I->small_G * B));
+    MT_TRY(dalloc(I, &I->sm_bar, (kBarWords + kBarLine) * sizeof(unsigned long long)));
+    I->path = MT_PATH_PERSISTENT;
+  }
   if (cudaMallocHost(&I->h_poll, 2 * sizeof(int)) != cudaSuccess) {
     mt_integrator_destroy(I);
     mt::set_error("mt_integrator_create: pinned allocation failed");
@@ -994,6 +1596,20 @@ mt_status mt_integrator_get_state(mt_integrator *I, float *m, int m_is_host) {
 
 void *mt_integrator_stream(mt_integrator *I) { return I ? (void *)I->stream : nullptr; }
 
+mt_status mt_integrator_set_path(mt_integrator *I, int path) {
+  MT_CHECK(I, MT_EINVAL, "mt_integrator_set_path: NULL integrator");
+  MT_CHECK(path == MT_PATH_GRAPH || path == MT_PATH_PERSISTENT, MT_EINVAL, "mt_integrator_set_path: unknown path %d",
+           path);
+  MT_CHECK(path == MT_PATH_GRAPH || I->small_ok, MT_EINVAL,
+           "mt_integrator_set_path: the one-kernel path needs an FP32 streaming tensor of a small tile set");
+  // both paths leave the state committed between calls (y and k1 current)
+  MT_CUDA(cudaStreamSynchronize(I->stream));
+  I->path = path;
+  return MT_OK;
+}
+
+int mt_integrator_get_path(mt_integrator *I) { return I ? I->path : 0; }
+
 mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps) {
   MT_CHECK(I && nsteps >= 0, MT_EINVAL, "mt_integrator_step: bad argument");
   if (I->need_init) {
@@ -1009,8 +1625,10 @@ mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps) {
       plan_host(I, x);
     }
     if ((st = write_ctl(I, c)) != MT_OK) return st;
+    if (I->path == MT_PATH_PERSISTENT) return launch_small(I, 1, nsteps);
     if ((st = enqueue_init(I)) != MT_OK) return st;
   }
+  if (I->path == MT_PATH_PERSISTENT) return nsteps > 0 ? launch_small(I, 0, nsteps) : MT_OK;
   for (int64_t q = 0; q < nsteps; ++q) MT_CUDA(cudaGraphLaunch(I->exec, I->stream));
   return enqueue_commit(I);
 }
@@ -1062,9 +1680,13 @@ static mt_status run_common(mt_integrator *I, int mode, double t1, int64_t n_out
     plan_host(I, x);
   }
   if ((st = write_ctl(I, c)) != MT_OK) return st;
-  if ((st = enqueue_init(I)) != MT_OK) return st;
-  if ((st = replay_until_done(I, I->o.max_steps + 2)) != MT_OK) return st;
-  if ((st = enqueue_commit(I)) != MT_OK) return st;
+  if (I->path == MT_PATH_PERSISTENT) {
+    if ((st = launch_small(I, 1, I->o.max_steps + 2)) != MT_OK) return st;
+  } else {
+    if ((st = enqueue_init(I)) != MT_OK) return st;
+    if ((st = replay_until_done(I, I->o.max_steps + 2)) != MT_OK) return st;
+    if ((st = enqueue_commit(I)) != MT_OK) return st;
+  }
   if ((st = read_ctl(I, c)) != MT_OK) return st;
   int dev_status = 0;
   MT_CUDA(cudaMemcpy(&dev_status, I->T->tiles->ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1247,6 +1869,114 @@ mt_status mt_integrator_stats(mt_integrator *I, mt_stats *stats) {
   return MT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// checkpoint / resume: header | SimCtl[B] | m[3nB] | k1[3nB] | FNV-1a 64
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t k1_valid;  // the saved derivative belongs to the saved m
+  int64_t n;
+  int32_t B;
+  int32_t prec;
+  int32_t layout;
+  uint32_t ctl_bytes;  // sizeof(SimCtl) of the writer
+};
+constexpr char kCkptMagic[8] = {'M', 'T', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+uint64_t fnv1a64(const unsigned char *p, size_t len) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t q = 0; q < len; ++q) {
+    h ^= p[q];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+size_t ckpt_bytes(const mt_integrator *I) {
+  const size_t state = sizeof(float) * 3 * (size_t)I->T->n * I->B;
+  return sizeof(CkptHeader) + sizeof(SimCtl) * I->B + 2 * state + sizeof(uint64_t);
+}
+
+}  // namespace
+
+mt_status mt_integrator_checkpoint_bytes(mt_integrator *I, size_t *bytes) {
+  MT_CHECK(I && bytes, MT_EINVAL, "mt_integrator_checkpoint_bytes: NULL argument");
+  *bytes = ckpt_bytes(I);
+  return MT_OK;
+}
+
+mt_status mt_integrator_checkpoint(mt_integrator *I, void *buf, size_t bytes) {
+  MT_CHECK(I && buf, MT_EINVAL, "mt_integrator_checkpoint: NULL argument");
+  const size_t need = ckpt_bytes(I);
+  MT_CHECK(bytes >= need, MT_EINVAL, "mt_integrator_checkpoint: buffer of %zu bytes, %zu needed", bytes, need);
+  unsigned char *p = static_cast<unsigned char *>(buf);
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, sizeof(h.magic));
+  h.version = kCkptVersion;
+  h.k1_valid = I->need_init ? 0u : 1u;
+  h.n = I->T->n;
+  h.B = I->B;
+  h.prec = I->T->prec;
+  h.layout = I->T->layout;
+  h.ctl_bytes = (uint32_t)sizeof(SimCtl);
+  std::memcpy(p, &h, sizeof(h));
+  std::vector<SimCtl> c;
+  mt_status st = read_ctl(I, c);  // also orders after every queued step
+  if (st != MT_OK) return st;
+  // every public call ends with the commit of the last accepted attempt
+  // (m and k1 already hold it), so the flag that asks the next begin to
+  // adopt it again is dropped: the next attempt starts from the same bits
+  for (auto &x : c) x.accepted = 0;
+  unsigned char *q = p + sizeof(h);
+  std::memcpy(q, c.data(), sizeof(SimCtl) * I->B);
+  q += sizeof(SimCtl) * I->B;
+  const size_t state = sizeof(float) * 3 * (size_t)I->T->n * I->B;
+  MT_CUDA(cudaMemcpyAsync(q, I->y, state, cudaMemcpyDeviceToHost, I->stream));
+  MT_CUDA(cudaMemcpyAsync(q + state, I->k[0], state, cudaMemcpyDeviceToHost, I->stream));
+  MT_CUDA(cudaStreamSynchronize(I->stream));
+  q += 2 * state;
+  const uint64_t sum = fnv1a64(p, (size_t)(q - p));
+  std::memcpy(q, &sum, sizeof(sum));
+  return MT_OK;
+}
+
+mt_status mt_integrator_restore(mt_integrator *I, const void *buf, size_t bytes) {
+  MT_CHECK(I && buf, MT_EINVAL, "mt_integrator_restore: NULL argument");
+  const unsigned char *p = static_cast<const unsigned char *>(buf);
+  MT_CHECK(bytes >= sizeof(CkptHeader), MT_EINVAL, "mt_integrator_restore: %zu bytes is no checkpoint", bytes);
+  CkptHeader h;
+  std::memcpy(&h, p, sizeof(h));
+  MT_CHECK(std::memcmp(h.magic, kCkptMagic, sizeof(h.magic)) == 0 && h.version == kCkptVersion &&
+               h.ctl_bytes == sizeof(SimCtl),
+           MT_EINVAL, "mt_integrator_restore: not a checkpoint of this format version");
+  MT_CHECK(h.n == I->T->n && h.B == I->B, MT_EINVAL,
+           "mt_integrator_restore: checkpoint of n = %lld, B = %d into an integrator of n = %lld, B = %d",
+           (long long)h.n, h.B, (long long)I->T->n, I->B);
+  const size_t need = ckpt_bytes(I);
+  MT_CHECK(bytes >= need, MT_EINVAL, "mt_integrator_restore: %zu bytes, %zu expected", bytes, need);
+  uint64_t sum;
+  std::memcpy(&sum, p + need - sizeof(sum), sizeof(sum));
+  MT_CHECK(sum == fnv1a64(p, need - sizeof(sum)), MT_EINVAL, "mt_integrator_restore: checksum mismatch");
+  std::vector<SimCtl> c(I->B);
+  const unsigned char *q = p + sizeof(h);
+  std::memcpy(c.data(), q, sizeof(SimCtl) * I->B);
+  q += sizeof(SimCtl) * I->B;
+  const size_t state = sizeof(float) * 3 * (size_t)I->T->n * I->B;
+  // the state of a finished simulation is restored with it; the derivative
+  // only when it was evaluated with this kind of tensor
+  const bool keep_k1 = h.k1_valid && h.prec == I->T->prec && h.layout == I->T->layout;
+  MT_CUDA(cudaMemcpyAsync(I->y, q, state, cudaMemcpyHostToDevice, I->stream));
+  if (keep_k1) MT_CUDA(cudaMemcpyAsync(I->k[0], q + state, state, cudaMemcpyHostToDevice, I->stream));
+  mt_status st = write_ctl(I, c);  // synchronises: the host image may go after this
+  if (st != MT_OK) return st;
+  I->need_init = !keep_k1;
+  return MT_OK;
+}
+
 mt_status mt_integrate(mt_tensor *T, const mt_llg_params *p, const mt_ode_opts *o, float *m, int B, double t0,
                        double t1, int64_t n_out, double *mavg, mt_stats *stats, void *stream) {
   mt_integrator *I = nullptr;
@@ -1386,6 +2116,7 @@ mt_status integ_create_idle(mt_tensor *T, const mt_llg_params *p, const mt_ode_o
   mt_integrator *I = nullptr;
   mt_status st = mt_integrator_create(T, p, o, B, nullptr, &I);
   if (st != MT_OK) return st;
+  I->path = MT_PATH_GRAPH;  // slots are admitted between graph replays
   std::vector<SimCtl> c(B);
   for (auto &x : c) {
     std::memset(&x, 0, sizeof(SimCtl));

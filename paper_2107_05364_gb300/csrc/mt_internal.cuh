@@ -177,6 +177,14 @@ struct mt_tensor {
   float *d_sp_val = nullptr;
 };
 
+// Index of entry e of block (i, j) in the tile-blocked streaming layout.
+__host__ __device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, int e, int TR, int TC, int nplane,
+                                                         int64_t Q) {
+  const int64_t p = i / TR, q = j / TC;
+  const int r = (int)(i - p * TR), c = (int)(j - q * TC);
+  return (((p * Q + q) * nplane + e) * TR + r) * (int64_t)TC + c;
+}
+
 // Dense layout, tile-blocked: the 3n x 3n matrix (padded to Kp = 128 k) is
 // cut into 128-row x 64-column BF16 tiles, each stored contiguously (16 KB,
 // rows of 128 bytes), tiles ordered by (row tile, K block); the low part of

@@ -1,0 +1,210 @@
+"""The one-kernel execution path of the Runge-Kutta (4,5) integration
+(Sec. 3.1) for small tile sets, against the FP64 oracle and against the
+graph path, through the C ABI.
+
+Both paths compute the same stages (Eq. 1 with the Eq. 17 effective field,
+the Dormand-Prince pair, renormalisation, step control); only the FP32
+summation order of the demag product differs, so they agree with each other
+and with the oracle to FP32 round-off grown over the steps.  Tile sets are
+chosen so that the rows per CTA are ragged (400 tiles over the SMs), one per
+CTA (fewer tiles than SMs) and at the shared-memory limit (1,000 tiles)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05364_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+MU0 = 4e-7 * math.pi
+FIELD1 = np.array([-24.6e-3, 4.3e-3, 0.0]) / MU0
+
+
+@pytest.fixture(scope="module")
+def mt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2107_05364_gb300 import build
+    build.build()
+    from paper_2107_05364_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(mt):
+    return mt.mt_ctx_create(0)
+
+
+def _setup(mt, ctx, nx, ny, nz=1, size=(500e-9, 125e-9, 3e-9)):
+    t = wl.film(nx, ny, nz, size=size)
+    tiles = mt.mt_tiles_create(ctx, t)
+    return t, tiles, mt.mt_demag_assemble(tiles, "f32"), oracle.Model.from_tiles(t)
+
+
+@pytest.fixture(scope="module")
+def film(mt, ctx):
+    return _setup(mt, ctx, 40, 10)
+
+
+def _params(B):
+    alpha = [0.02, 0.1, 0.5][:B]
+    Ha = np.array([FIELD1, 0.5 * FIELD1[::-1], np.array([0.0, 0.0, 2e4])])[:B]
+    return alpha, Ha
+
+
+def test_path_selection(mt, ctx, film):
+    t, tiles, T, _ = film
+    p, keep = mt.llg_params(1, alpha=0.02)
+    I = mt.Integrator(T, p, mt.ode_opts())
+    assert I.path() == mt.MT_PATH_PERSISTENT
+    I.set_path(mt.MT_PATH_GRAPH)
+    assert I.path() == mt.MT_PATH_GRAPH
+    with pytest.raises(mt.MtError) as e:
+        I.set_path(7)
+    assert e.value.status == mt.MT_EINVAL
+    # tensors the one-kernel path does not take: BF16 storage, a large set
+    Tb = mt.mt_demag_assemble(tiles, "bf16")
+    J = mt.Integrator(Tb, p, mt.ode_opts())
+    assert J.path() == mt.MT_PATH_GRAPH
+    with pytest.raises(mt.MtError) as e:
+        J.set_path(mt.MT_PATH_PERSISTENT)
+    assert e.value.status == mt.MT_EINVAL
+    big = wl.film(100, 50, 1)
+    Tl = mt.mt_demag_assemble(mt.mt_tiles_create(ctx, big), "f32")
+    assert mt.Integrator(Tl, p, mt.ode_opts()).path() == mt.MT_PATH_GRAPH
+
+
+@pytest.mark.parametrize("grid", [(40, 10, 1), (10, 8, 1), (50, 20, 1)])
+def test_fixed_steps_match_oracle_and_graph(mt, ctx, grid):
+    # 400 tiles (2 or 3 rows per CTA), 80 (one per CTA), 1,000 (7 per CTA)
+    t, tiles, T, md = _setup(mt, ctx, *grid)
+    B = 3
+    alpha, Ha = _params(B)
+    m0 = np.stack([wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=b) for b in range(B)]).astype(np.float32)
+    h, steps = 1e-13, 20
+    p, keep = mt.llg_params(B, alpha=alpha, Ha=Ha)
+    out = {}
+    for path in (mt.MT_PATH_PERSISTENT, mt.MT_PATH_GRAPH):
+        I = mt.Integrator(T, p, mt.ode_opts(fixed_h=h), B)
+        I.set_path(path)
+        I.set_state(m0.ravel())
+        I.step(steps)
+        out[path] = I.get_state()
+        for s in I.stats():
+            assert s["n_accept"] == steps and s["n_reject"] == 0 and s["n_rhs"] == 6 * steps + 1
+            assert abs(s["t"] - steps * h) <= 1e-9 * steps * h
+    for b in range(B):
+        st, mo, _, _ = oracle.integrate(md, m0[b].astype(np.float64),
+                                        oracle.llg_params(alpha=alpha[b], Ha=Ha[b]), oracle.ode_opts(fixed_h=h),
+                                        0.0, steps * h, 1)
+        assert st == oracle.OK
+        assert np.abs(out[mt.MT_PATH_PERSISTENT][b] - mo).max() <= 2e-5
+        assert np.abs(out[mt.MT_PATH_GRAPH][b] - mo).max() <= 2e-5
+    assert np.abs(out[mt.MT_PATH_PERSISTENT] - out[mt.MT_PATH_GRAPH]).max() <= 1e-5
+    np.testing.assert_allclose(np.linalg.norm(out[mt.MT_PATH_PERSISTENT], axis=2), 1.0, atol=1e-6)
+
+
+def test_adaptive_trace_matches_oracle(mt, film):
+    # standard-problem-4 field 1 from the (1,1,1) start: <m>(t) for 0.1 ns,
+    # outputs every 5 ps; the step counts follow the oracle's
+    t, tiles, T, md = film
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    opts = dict(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11)
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    T1, n_out = 1e-10, 20
+    so, mo, mref, sto = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=FIELD1),
+                                         oracle.ode_opts(**opts), 0.0, T1, n_out)
+    assert so == oracle.OK
+    traces = {}
+    for path in (mt.MT_PATH_PERSISTENT, mt.MT_PATH_GRAPH):
+        I = mt.Integrator(T, p, mt.ode_opts(**opts))
+        I.set_path(path)
+        I.set_state(m0.ravel())
+        s, mavg, st = I.run(T1, n_out)
+        assert st[0]["status"] == 0 and abs(st[0]["t"] - T1) < 1e-20
+        assert np.abs(mavg[:, 0, :] - mref).max() <= 2e-4
+        assert abs(st[0]["n_accept"] - sto["n_accept"]) <= 0.05 * sto["n_accept"] + 3
+        traces[path] = mavg
+    assert np.abs(traces[mt.MT_PATH_PERSISTENT] - traces[mt.MT_PATH_GRAPH]).max() <= 1e-5
+
+
+def test_relax_matches_oracle(mt, film):
+    t, tiles, T, md = film
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
+    opts = dict(rtol=1e-5, atol=1e-5, h0=1e-14, hmax=1e-11)
+    p, keep = mt.llg_params(1, alpha=0.5)
+    I = mt.Integrator(T, p, mt.ode_opts(**opts))
+    assert I.path() == mt.MT_PATH_PERSISTENT
+    I.set_state(m0.ravel())
+    tol = 1e-5
+    s, st = I.relax(tol, 20e-9)
+    assert st[0]["status"] == 0 and st[0]["tau"] < tol
+    so, mo, sto = oracle.relax(md, m0.astype(np.float64), oracle.llg_params(alpha=0.5),
+                               oracle.ode_opts(**opts), tol, 20e-9)
+    assert so == oracle.OK
+    assert np.abs(I.get_state()[0] - mo).max() <= 1e-4
+
+
+def test_relax_finishes_simulations_one_by_one(mt, film):
+    # three dampings in one batch: each stops at its own tolerance crossing
+    # while the others go on; the same as three separate relaxations
+    t, tiles, T, md = film
+    B = 3
+    alpha = [0.5, 0.2, 1.0]
+    m0 = np.stack([wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=10 + b) for b in range(B)]).astype(np.float32)
+    opts = mt.ode_opts(rtol=1e-5, atol=1e-5)
+    p, keep = mt.llg_params(B, alpha=alpha)
+    I = mt.Integrator(T, p, opts, B)
+    I.set_state(m0.ravel())
+    s, st = I.relax(1e-4, 20e-9, check=False)
+    mb = I.get_state()
+    for b in range(B):
+        q, keep1 = mt.llg_params(1, alpha=alpha[b])
+        J = mt.Integrator(T, q, opts, 1)
+        J.set_state(m0[b].ravel())
+        _, sj = J.relax(1e-4, 20e-9, check=False)
+        assert sj[0]["status"] == st[b]["status"]
+        assert sj[0]["n_accept"] == st[b]["n_accept"] and sj[0]["n_reject"] == st[b]["n_reject"]
+        np.testing.assert_array_equal(J.get_state()[0], mb[b])
+
+
+def test_switching_paths_between_calls(mt, film):
+    t, tiles, T, md = film
+    p, keep = mt.llg_params(1, alpha=0.02, Ha=FIELD1)
+    opts = mt.ode_opts(fixed_h=1e-13)
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=4).astype(np.float32)
+    A = mt.Integrator(T, p, opts)
+    A.set_state(m0.ravel())
+    A.step(10)
+    A.set_path(mt.MT_PATH_GRAPH)
+    A.step(10)
+    A.set_path(mt.MT_PATH_PERSISTENT)
+    A.step(10)
+    Bi = mt.Integrator(T, p, opts)
+    Bi.set_path(mt.MT_PATH_GRAPH)
+    Bi.set_state(m0.ravel())
+    Bi.step(30)
+    assert np.abs(A.get_state() - Bi.get_state()).max() <= 2e-5
+    assert A.stats()[0]["n_accept"] == 30
+
+
+def test_tetrahedral_tiles(mt, ctx):
+    verts, tets = wl.tetra_box(5, 4, 3, size=(50e-9, 40e-9, 15e-9), jitter=0.1, seed=7)
+    n = len(tets)
+    tiles = mt.mt_tiles_create_tetra(ctx, verts, tets, wl.SP4_MS, wl.SP4_AEX, 5e4, (0.0, 0.0, 1.0))
+    T = mt.mt_demag_assemble(tiles, "f32")
+    md = oracle.tetra_model(verts, tets, wl.SP4_MS, wl.SP4_AEX, 5e4, (0.0, 0.0, 1.0))
+    Ha = np.array([1e4, -2e4, 3e3])
+    p, keep = mt.llg_params(1, alpha=0.1, Ha=Ha)
+    I = mt.Integrator(T, p, mt.ode_opts(fixed_h=2e-14))
+    assert I.path() == mt.MT_PATH_PERSISTENT
+    m0 = wl.m_noisy(n, (1, 1, 1), 1e-2, seed=1).astype(np.float32)
+    I.set_state(m0.ravel())
+    I.step(20)
+    st, mo, _, _ = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.1, Ha=Ha),
+                                    oracle.ode_opts(fixed_h=2e-14), 0.0, 20 * 2e-14, 1)
+    assert st == oracle.OK
+    assert np.abs(I.get_state()[0] - mo).max() < 2e-5

@@ -483,6 +483,97 @@ __global__ void k_near(int64_t n, int B, const int32_t *ptr, const int32_t *col,
   Hb[2] = rz.hi + rz.lo;
 }
 
+// The same for the simulation-fastest copy of a batch (element (b, j, c) at
+// mT[(3 j + c) Bp + b]): a thread takes V adjacent simulations of one tile
+// (one vector load per component), so a warp covers 32 V simulations and
+// shares the tile's blocks; the column of the next block is fetched one step
+// ahead.
+template <int V>
+struct VecF;
+template <>
+struct VecF<1> {
+  using T = float;
+  static __device__ __forceinline__ void get(T v, float *o) { o[0] = v; }
+};
+template <>
+struct VecF<2> {
+  using T = float2;
+  static __device__ __forceinline__ void get(T v, float *o) {
+    o[0] = v.x;
+    o[1] = v.y;
+  }
+};
+template <>
+struct VecF<4> {
+  using T = float4;
+  static __device__ __forceinline__ void get(T v, float *o) {
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+};
+
+template <bool FF, int V>
+__global__ void k_near_v(int64_t n, int B, int Bp, const int32_t *ptr, const int32_t *col, const float2 *val,
+                         const float *mT, float *H, const int *active) {
+  mtd::pdl_enter();
+  using VT = typename VecF<V>::T;
+  const int Bv = (B + V - 1) / V;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * Bv) return;
+  const int64_t i = t / Bv;
+  const int b0 = (int)(t - i * Bv) * V;
+  ff hx[V], hy[V], hz[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) hx[v] = hy[v] = hz[v] = ff{0.0f, 0.0f};
+  const int32_t a0 = ptr[i], a1 = ptr[i + 1];
+  int64_t jn = a0 < a1 ? col[a0] : 0;
+  for (int32_t a = a0; a < a1; ++a) {
+    const int64_t j = jn;
+    if (a + 1 < a1) jn = col[a + 1];
+    const float4 *vp = reinterpret_cast<const float4 *>(val + 6 * (size_t)a);
+    const float4 w0 = vp[0], w1 = vp[1], w2 = vp[2];
+    float x0[V], x1[V], x2[V];
+    VecF<V>::get(*reinterpret_cast<const VT *>(mT + (size_t)(3 * j) * Bp + b0), x0);
+    VecF<V>::get(*reinterpret_cast<const VT *>(mT + (size_t)(3 * j + 1) * Bp + b0), x1);
+    VecF<V>::get(*reinterpret_cast<const VT *>(mT + (size_t)(3 * j + 2) * Bp + b0), x2);
+    const float2 v0 = make_float2(w0.x, w0.y), v1 = make_float2(w0.z, w0.w), v2 = make_float2(w1.x, w1.y);
+    const float2 v3 = make_float2(w1.z, w1.w), v4 = make_float2(w2.x, w2.y), v5 = make_float2(w2.z, w2.w);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      if (!FF) {
+        hx[v].hi = fmaf(v0.x, x0[v], fmaf(v1.x, x1[v], fmaf(v2.x, x2[v], hx[v].hi)));
+        hy[v].hi = fmaf(v1.x, x0[v], fmaf(v3.x, x1[v], fmaf(v4.x, x2[v], hy[v].hi)));
+        hz[v].hi = fmaf(v2.x, x0[v], fmaf(v4.x, x1[v], fmaf(v5.x, x2[v], hz[v].hi)));
+      } else {
+        ff_fma_lazy(hx[v], v0, x0[v]);
+        ff_fma_lazy(hx[v], v1, x1[v]);
+        ff_fma_lazy(hx[v], v2, x2[v]);
+        ff_fma_lazy(hy[v], v1, x0[v]);
+        ff_fma_lazy(hy[v], v3, x1[v]);
+        ff_fma_lazy(hy[v], v4, x2[v]);
+        ff_fma_lazy(hz[v], v2, x0[v]);
+        ff_fma_lazy(hz[v], v4, x1[v]);
+        ff_fma_lazy(hz[v], v5, x2[v]);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int b = b0 + v;
+    if (b >= B || (active && !active[b])) continue;
+    float *Hb = H + (size_t)b * 3 * n + 3 * i;
+    // H = far - near, rounded once
+    const ff rx = ff_add({Hb[0], 0.0f}, -hx[v].hi, -hx[v].lo);
+    const ff ry = ff_add({Hb[1], 0.0f}, -hy[v].hi, -hy[v].lo);
+    const ff rz = ff_add({Hb[2], 0.0f}, -hz[v].hi, -hz[v].lo);
+    Hb[0] = rx.hi + rx.lo;
+    Hb[1] = ry.hi + ry.lo;
+    Hb[2] = rz.hi + rz.lo;
+  }
+}
+
 template <int PREC, int SB>
 cudaError_t prepare_mv_one() {
   return cudaFuncSetAttribute(k_matvec<PREC, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -619,6 +710,26 @@ void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int
   const int32_t *ptr = T->d_near_ptr, *col = T->d_near_col;
   const float2 *hl = T->d_near_hl;
   const int64_t n = T->n;
+  if (sb == 1 && se >= B && se % 4 == 0) {  // simulation-fastest copy, rows of se >= B floats
+    const int V = B >= 128 ? 4 : B >= 64 ? 2 : 1;
+    const int64_t threads = n * ((B + V - 1) / V);
+    const unsigned g = (unsigned)((threads + 255) / 256);
+    const int Bp = (int)se;
+    const bool split = T->prec == MT_BF16_SPLIT;
+#define MT_NEAR_V(FF, VV) \
+  mt::launch_pdl(k_near_v<FF, VV>, dim3(g), dim3(256), 0, s, n, B, Bp, ptr, col, hl, m, H, active)
+    if (split) {
+      if (V == 4) MT_NEAR_V(true, 4);
+      else if (V == 2) MT_NEAR_V(true, 2);
+      else MT_NEAR_V(true, 1);
+    } else {
+      if (V == 4) MT_NEAR_V(false, 4);
+      else if (V == 2) MT_NEAR_V(false, 2);
+      else MT_NEAR_V(false, 1);
+    }
+#undef MT_NEAR_V
+    return;
+  }
   if (T->prec == MT_BF16_SPLIT)
     mt::launch_pdl(k_near<true>, dim3(grid), dim3(256), 0, s, n, B, ptr, col, hl, m, sb, se, H, active);
   else

@@ -89,7 +89,7 @@ struct StageArgs {
   SimCtl *ctl;
   int *active;
   int *n_active;
-  double *red;     // [B][nblk][5]
+  float *red;      // [B][nblk][5]
   int *red_count;  // [B]
   double *mavg;    // [n_out][B][3]
   double rtol, atol, hmax, fixed_h;
@@ -203,11 +203,11 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
   }
 }
 
-// Block-reduce NV doubles (sum for all but index `max_idx`, which is a max)
-// and return them in thread 0.
+// Block-reduce NV floats (sum for all but index `max_idx`, which is a
+// NaN-propagating max) and return them in thread 0.
 template <int NV>
-__device__ __forceinline__ void block_reduce(double v[NV], int max_idx) {
-  __shared__ double sh[kStageThreads / 32][NV];
+__device__ __forceinline__ void block_reduce(float v[NV], int max_idx) {
+  __shared__ float sh[kStageThreads / 32][NV];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < NV; ++q) v[q] = (q == max_idx) ? mtd::warp_max(v[q]) : mtd::warp_sum(v[q]);
@@ -217,7 +217,7 @@ __device__ __forceinline__ void block_reduce(double v[NV], int max_idx) {
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int q = 0; q < NV; ++q) {
-      double acc = sh[0][q];
+      float acc = sh[0][q];
       for (int ww = 1; ww < (int)(blockDim.x >> 5); ++ww)
         acc = (q == max_idx) ? mtd::nan_max(acc, sh[ww][q]) : acc + sh[ww][q];
       v[q] = acc;
@@ -228,13 +228,15 @@ __device__ __forceinline__ void block_reduce(double v[NV], int max_idx) {
 
 // Deterministic per-simulation reduction across blocks: every block writes
 // its 5 values, the last block to arrive sums them in block order.  Returns
-// true in thread 0 of the last block (with tot filled).
-__device__ bool reduce_across_blocks(const StageArgs &A, int b, double v[5], double tot[5]) {
+// true in thread 0 of the last block (with tot filled).  FP32 throughout:
+// the sums (squared scaled errors, volume-weighted m) need no more, and FP64
+// arithmetic on the one latency-critical thread is slow on this part.
+__device__ bool reduce_across_blocks(const StageArgs &A, int b, float v[5], double tot[5]) {
   const int nblk = gridDim.x;
   __shared__ int s_last;
   block_reduce<5>(v, 1);
   if (threadIdx.x == 0) {
-    double *dst = A.red + ((size_t)b * nblk + blockIdx.x) * 5;
+    float *dst = A.red + ((size_t)b * nblk + blockIdx.x) * 5;
     for (int q = 0; q < 5; ++q) dst[q] = v[q];
     __threadfence();
     const int old = atomicAdd(&A.red_count[b], 1);
@@ -243,9 +245,9 @@ __device__ bool reduce_across_blocks(const StageArgs &A, int b, double v[5], dou
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  double acc[5] = {0, 0, 0, 0, 0};
+  float acc[5] = {0, 0, 0, 0, 0};
   for (int blk = threadIdx.x; blk < nblk; blk += blockDim.x) {
-    const double *src = A.red + ((size_t)b * nblk + blk) * 5;
+    const float *src = A.red + ((size_t)b * nblk + blk) * 5;
     acc[0] += __ldcg(&src[0]);
     acc[1] = mtd::nan_max(acc[1], __ldcg(&src[1]));
     acc[2] += __ldcg(&src[2]);
@@ -255,7 +257,7 @@ __device__ bool reduce_across_blocks(const StageArgs &A, int b, double v[5], dou
   block_reduce<5>(acc, 1);
   if (threadIdx.x == 0) {
     A.red_count[b] = 0;
-    for (int q = 0; q < 5; ++q) tot[q] = acc[q];
+    for (int q = 0; q < 5; ++q) tot[q] = (double)acc[q];
   }
   return threadIdx.x == 0;
 }
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
     return;
   }
   if constexpr (S == 1) {
-    double v[5] = {0.0, (double)tau_i, 0.0, 0.0, 0.0};
+    float v[5] = {0.0f, tau_i, 0.0f, 0.0f, 0.0f};
     double tot[5];
     if (reduce_across_blocks(A, b, v, tot)) {
       SimCtl c = A.ctl[b];
@@ -464,24 +466,24 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
     return;
   }
   if constexpr (S == 7) {
-    double v[5] = {0.0, (double)tau_i, 0.0, 0.0, 0.0};
+    // embedded error, torque and <m> at the 5th-order solution, in FP32
+    float v[5] = {0.0f, tau_i, 0.0f, 0.0f, 0.0f};
     if (live) {
-      const double hs = A.ctl[b].hs;
+      const float hs = (float)A.ctl[b].hs;
+      const float atol = (float)A.atol, rtol = (float)A.rtol;
       const float *y0 = A.y + o;
-      double e2 = 0.0;
+      float e2 = 0.0f;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        double e = 0.0;
+        float e = 0.0f;
 #pragma unroll
         for (int j = 0; j < 7; ++j)
-          if (c_dp_err[j] != 0.0) e += c_dp_err[j] * (double)((j == 6) ? kk[c] : A.k[j][o + c]);
-        e *= hs;
-        const double sc = A.atol + A.rtol * fmax(fabs((double)y0[c]), fabs((double)mi[c]));
-        e2 += (e / sc) * (e / sc);
+          if (c_dp_err[j] != 0.0) e = fmaf((float)c_dp_err[j], (j == 6) ? kk[c] : A.k[j][o + c], e);
+        const float r = e * hs / (atol + rtol * fmaxf(fabsf(y0[c]), fabsf(mi[c])));
+        e2 = fmaf(r, r, e2);
       }
       v[0] = e2;
-      const double nrm = sqrt((double)mi[0] * mi[0] + (double)mi[1] * mi[1] + (double)mi[2] * mi[2]);
-      const double w = A.wvol[i] / nrm;
+      const float w = (float)A.wvol[i] / sqrtf(mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2]);
       v[2] = w * mi[0];
       v[3] = w * mi[1];
       v[4] = w * mi[2];
@@ -628,8 +630,6 @@ __device__ __forceinline__ bool small_grid_sync(const SmallArgs &S, unsigned lon
   return s_ok != 0;
 }
 
-__device__ __forceinline__ float nan_maxf(float a, float b) { return (a > b || a != a) ? a : b; }
-
 // k_S of the CTA's rows [r0, r0 + nr) for every running simulation, from
 // the stage input of all tiles in sh.M: H_d = -N (Ms m) from the rows held
 // in sh.N, then the local fields and Eq. 1 (the arithmetic of k_stage); the
@@ -716,7 +716,7 @@ __device__ __forceinline__ void small_warp_reduce(float v[5]) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
-    v[1] = nan_maxf(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+    v[1] = mtd::nan_max(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
     v[2] += __shfl_xor_sync(0xffffffffu, v[2], o);
     v[3] += __shfl_xor_sync(0xffffffffu, v[3], o);
     v[4] += __shfl_xor_sync(0xffffffffu, v[4], o);
@@ -734,7 +734,7 @@ __device__ __forceinline__ void small_total(const SmallArgs &S, int b, double to
   for (int g = threadIdx.x & 31; g < (int)gridDim.x; g += 32) {
     const float *src = S.part + ((size_t)g * S.A.B + b) * 5;
     acc[0] += __ldcg(&src[0]);
-    acc[1] = nan_maxf(acc[1], __ldcg(&src[1]));
+    acc[1] = mtd::nan_max(acc[1], __ldcg(&src[1]));
     acc[2] += __ldcg(&src[2]);
     acc[3] += __ldcg(&src[3]);
     acc[4] += __ldcg(&src[4]);
@@ -1113,7 +1113,7 @@ struct mt_integrator {
   SimCtl *ctl = nullptr;
   int *active = nullptr;
   int *n_active = nullptr;
-  double *red = nullptr;
+  float *red = nullptr;
   int *red_count = nullptr;
   double *mavg = nullptr;
   int64_t mavg_cap = 0;
@@ -1481,7 +1481,7 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
   MT_TRY(dalloc(I, &I->ctl, sizeof(SimCtl) * B));
   MT_TRY(dalloc(I, &I->active, sizeof(int) * B));
   MT_TRY(dalloc(I, &I->n_active, sizeof(int)));
-  MT_TRY(dalloc(I, &I->red, sizeof(double) * 5 * I->nblk * B));
+  MT_TRY(dalloc(I, &I->red, sizeof(float) * 5 * I->nblk * B));
   MT_TRY(dalloc(I, &I->red_count, sizeof(int) * B));
   I->mavg_cap = 1;
   MT_TRY(dalloc(I, &I->mavg, sizeof(double) * 3 * B));

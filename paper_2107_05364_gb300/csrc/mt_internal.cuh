@@ -398,6 +398,12 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+__device__ __forceinline__ float nan_max(float a, float b) { return (a > b || a != a) ? a : b; }
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
 
 // Stream-K split of U work units over G CTAs: CTA k owns [begin(k), begin(k+1)).
 __host__ __device__ __forceinline__ int64_t sk_begin(int64_t k, int64_t U, int64_t G) { return (k * U) / G; }

@@ -3,7 +3,9 @@
     python -m paper_2107_05364_gb300.profile_case --nx 100 --ny 40 --prec f32 --what field --reps 3
 
 --what field    : mt_demag_field R times (prep + streaming product [+ near])
---what step     : R Runge-Kutta attempts through the integrator graph
+--what step     : R Runge-Kutta attempts through the integrator
+--path P        : step execution: auto (default), graph (one CUDA-graph replay
+                  per attempt) or persistent (one cooperative kernel per call)
 --what assemble : tensor assembly only
 --layout dense  : 9-entry BF16 / split tensor for the batched tensor-core product
 --threshold F   : drop the smallest fraction F of the elements (Sec. 4.3.1) and
@@ -30,6 +32,7 @@ def main():
     ap.add_argument("--B", type=int, default=1)
     ap.add_argument("--layout", default="stream", choices=["stream", "dense"])
     ap.add_argument("--threshold", type=float, default=None)
+    ap.add_argument("--path", default="auto", choices=["auto", "graph", "persistent"])
     a = ap.parse_args()
 
     import torch
@@ -76,6 +79,8 @@ def main():
     else:
         p, keep = mt.llg_params(a.B, alpha=0.02, Ha=np.array([-24.6e-3, 4.3e-3, 0.0]) / (4e-7 * math.pi))
         I = mt.Integrator(T, p, mt.ode_opts(), B=a.B)
+        if a.path != "auto":
+            I.set_path(mt.MT_PATH_GRAPH if a.path == "graph" else mt.MT_PATH_PERSISTENT)
         I.set_state(m.ravel())
         I.step(1)
         torch.cuda.synchronize()
@@ -84,7 +89,7 @@ def main():
         I.step(a.reps)
         e1.record(s)
         torch.cuda.synchronize()
-        print("step n=%d B=%d: %.4f ms/attempt" % (t.n, a.B, e0.elapsed_time(e1) / a.reps))
+        print("step n=%d B=%d path=%d: %.4f ms/attempt" % (t.n, a.B, I.path(), e0.elapsed_time(e1) / a.reps))
 
 
 if __name__ == "__main__":

@@ -462,6 +462,14 @@ MT_API mt_status mt_relax(mt_tensor *T, const mt_llg_params *p, const mt_ode_opt
  * MT_ECUDA otherwise.  The context stays usable.  Synchronous. */
 MT_API mt_status mt_selftest_wait_timeout(mt_ctx *ctx, double limit_s);
 
+/* Self-test of the grid-wide barrier of the one-kernel integrator path
+ * (MT_PATH_PERSISTENT): a cooperative launch of 4 CTAs in which one CTA
+ * leaves without arriving, so the others' bounded wait (about 2 s) runs
+ * out; they record the timeout, raise the abort flag and return.  Returns
+ * MT_ETIMEOUT when that was reported (the expected outcome), MT_ECUDA
+ * otherwise.  The context stays usable.  Synchronous. */
+MT_API mt_status mt_selftest_grid_barrier_timeout(mt_ctx *ctx);
+
 /* ---------------------------------------------------------------------- */
 /* request serving: relax jobs on many geometries, continuously batched     */
 /* ---------------------------------------------------------------------- */

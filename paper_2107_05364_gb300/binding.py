@@ -130,6 +130,7 @@ _SIGS = {
     "mt_integrator_checkpoint": (_I, [_P, _P, ctypes.c_size_t]),
     "mt_integrator_restore": (_I, [_P, _P, ctypes.c_size_t]),
     "mt_integrator_set_path": (_I, [_P, _I]),
+    "mt_selftest_grid_barrier_timeout": (_I, [_P]),
     "mt_integrator_get_path": (_I, [_P]),
     "mt_integrate": (_I, [_P, ctypes.POINTER(LlgParams), ctypes.POINTER(OdeOpts), _P, _I, _D, _D, _I64, _P, _P,
                           _P]),
@@ -338,6 +339,11 @@ def mt_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> Ctx:
 def mt_selftest_wait_timeout(ctx: Ctx, limit_s: float = 0.2) -> int:
     """Status of the bounded-wait self-test (MT_ETIMEOUT = works as designed)."""
     return int(lib().mt_selftest_wait_timeout(ctx.h, float(limit_s)))
+
+
+def mt_selftest_grid_barrier_timeout(ctx: Ctx) -> int:
+    """Status of the grid-barrier self-test (MT_ETIMEOUT = works as designed)."""
+    return int(lib().mt_selftest_grid_barrier_timeout(ctx.h))
 
 
 def mt_tiles_create(ctx: Ctx, tiles) -> TilesH:

@@ -826,15 +826,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
   if (S.init) {  // k1 and the torque at the state
     small_load_state(sh.M, A.y, state);
     small_rhs<RMAX>(A, sh, sh.k, R, nr, r0);
-    if (warp == 0)
-      for (int b = 0; b < B; ++b) {
-        if (sh.ctl[b].done) continue;
-        float v[5] = {0.0f, lane < nr ? sh.tau[(size_t)b * R + lane] : 0.0f, 0.0f, 0.0f, 0.0f};
-        small_partial(S, b, v);
-      }
+    for (int b = warp; b < B; b += kSmallWarps) {
+      if (sh.ctl[b].done) continue;
+      float v[5] = {0.0f, lane < nr ? sh.tau[(size_t)b * R + lane] : 0.0f, 0.0f, 0.0f, 0.0f};
+      small_partial(S, b, v);
+    }
     ok = small_grid_sync(S, nbar);
-    if (ok && warp == 0)
-      for (int b = 0; b < B; ++b) {
+    if (ok)
+      for (int b = warp; b < B; b += kSmallWarps) {
         if (sh.ctl[b].done) continue;
         double tot[5];
         small_total(S, b, tot);
@@ -880,50 +879,48 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     if (!ok) break;
     // embedded error, torque and <m> at the 5th-order solution (the stage-7
     // input), in FP32 over the CTA's rows: one lane per row
-    if (warp == 0)
-      for (int b = 0; b < B; ++b) {
-        if (sh.ctl[b].done) continue;
-        float v[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (lane < nr) {
-          const float hs = (float)sh.ctl[b].hs;
-          const int64_t i = r0 + lane;
-          const float *mi = sh.M + (size_t)b * 3 * n + 3 * i;
-          const float *y0 = sh.y + ((size_t)b * R + lane) * 3;
-          for (int c = 0; c < 3; ++c) {
-            float e = 0.0f;
+    for (int b = warp; b < B; b += kSmallWarps) {
+      if (sh.ctl[b].done) continue;
+      float v[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      if (lane < nr) {
+        const float hs = (float)sh.ctl[b].hs;
+        const int64_t i = r0 + lane;
+        const float *mi = sh.M + (size_t)b * 3 * n + 3 * i;
+        const float *y0 = sh.y + ((size_t)b * R + lane) * 3;
+        for (int c = 0; c < 3; ++c) {
+          float e = 0.0f;
 #pragma unroll
-            for (int j = 0; j < 7; ++j)
-              if (c_dp_err[j] != 0.0) e = fmaf((float)c_dp_err[j], sh.k[j * kpl + ((size_t)b * R + lane) * 3 + c], e);
-            const float r = e * hs / (atol + rtol * fmaxf(fabsf(y0[c]), fabsf(mi[c])));
-            v[0] = fmaf(r, r, v[0]);
-          }
-          v[1] = sh.tau[(size_t)b * R + lane];
-          const float wv = sh.wv[lane] / sqrtf(mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2]);
-          v[2] = wv * mi[0];
-          v[3] = wv * mi[1];
-          v[4] = wv * mi[2];
+          for (int j = 0; j < 7; ++j)
+            if (c_dp_err[j] != 0.0) e = fmaf((float)c_dp_err[j], sh.k[j * kpl + ((size_t)b * R + lane) * 3 + c], e);
+          const float r = e * hs / (atol + rtol * fmaxf(fabsf(y0[c]), fabsf(mi[c])));
+          v[0] = fmaf(r, r, v[0]);
         }
-        small_partial(S, b, v);
+        v[1] = sh.tau[(size_t)b * R + lane];
+        const float wv = sh.wv[lane] / sqrtf(mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2]);
+        v[2] = wv * mi[0];
+        v[3] = wv * mi[1];
+        v[4] = wv * mi[2];
       }
+      small_partial(S, b, v);
+    }
     ok = small_grid_sync(S, nbar);
     if (!ok) break;
-    if (warp == 0)
-      for (int b = 0; b < B; ++b) {
-        if (sh.ctl[b].done) continue;
-        double tot[5];
-        small_total(S, b, tot);
-        if (lane == 0) {
-          int64_t row = -1;
-          close_attempt(A, sh.ctl[b], tot, &row);
-          if (g == 0 && row >= 0) {
-            double *mo = A.mavg + ((size_t)row * B + b) * 3;
-            mo[0] = tot[2];
-            mo[1] = tot[3];
-            mo[2] = tot[4];
-          }
+    for (int b = warp; b < B; b += kSmallWarps) {
+      if (sh.ctl[b].done) continue;
+      double tot[5];
+      small_total(S, b, tot);
+      if (lane == 0) {
+        int64_t row = -1;
+        close_attempt(A, sh.ctl[b], tot, &row);
+        if (g == 0 && row >= 0) {
+          double *mo = A.mavg + ((size_t)row * B + b) * 3;
+          mo[0] = tot[2];
+          mo[1] = tot[3];
+          mo[2] = tot[4];
         }
-        __syncwarp();
       }
+      __syncwarp();
+    }
     __syncthreads();
     // accepted: adopt the normalised 5th-order solution; k7 is the next k1
     for (int p = tid; p < B * nr; p += kSmallThreads) {
@@ -963,6 +960,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     }
     *A.n_active = na;
   }
+}
+
+// failure-detection self-test: CTA 0 leaves without arriving, so the other
+// CTAs' bounded barrier wait runs out
+__global__ void k_barrier_selftest(SmallArgs S) {
+  unsigned long long nbar = 0;
+  if (blockIdx.x == 0) return;
+  small_grid_sync(S, nbar);
 }
 
 // put a prepared control block into slot b and make it active
@@ -1609,6 +1614,40 @@ mt_status mt_integrator_set_path(mt_integrator *I, int path) {
 }
 
 int mt_integrator_get_path(mt_integrator *I) { return I ? I->path : 0; }
+
+mt_status mt_selftest_grid_barrier_timeout(mt_ctx *ctx) {
+  MT_CHECK(ctx, MT_EINVAL, "mt_selftest_grid_barrier_timeout: NULL context");
+  MT_CUDA(cudaSetDevice(ctx->device));
+  unsigned long long *words = nullptr;
+  const size_t bytes = (kBarWords + kBarLine) * sizeof(unsigned long long) + sizeof(int);
+  MT_CUDA(cudaMalloc(&words, bytes));
+  cudaError_t e = cudaMemset(words, 0, bytes);
+  SmallArgs S{};
+  S.bar = words;
+  S.abort_flag = reinterpret_cast<int *>(words + kBarWords);
+  S.status = reinterpret_cast<int *>(words + kBarWords + kBarLine);
+  if (e == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(4);
+    cfg.blockDim = dim3(32);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_barrier_selftest, S);
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, S.status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(words);
+  if (e != cudaSuccess) return mt::cuda_fail(e, "mt_selftest_grid_barrier_timeout", __FILE__, __LINE__);
+  if (h == MT_DEV_TIMEOUT) {
+    mt::set_error("mt_selftest_grid_barrier_timeout: the bounded barrier gave up as designed");
+    return MT_ETIMEOUT;
+  }
+  mt::set_error("mt_selftest_grid_barrier_timeout: the barrier did not report a timeout");
+  return MT_ECUDA;
+}
 
 mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps) {
   MT_CHECK(I && nsteps >= 0, MT_EINVAL, "mt_integrator_step: bad argument");

@@ -92,3 +92,26 @@ def test_bounded_wait_gives_up_and_context_survives(mt, ctx):
     mt.mt_demag_field(T, mg, H)
     torch.cuda.synchronize()
     assert torch.isfinite(H).all()
+
+
+def test_grid_barrier_gives_up_and_context_survives(mt, ctx):
+    # one CTA of a cooperative launch never arrives at the barrier the
+    # one-kernel integrator uses between its stages: the others give up
+    # after their bounded wait and report it; the context keeps working,
+    # including the one-kernel path itself
+    t0 = time.time()
+    st = mt.mt_selftest_grid_barrier_timeout(ctx)
+    dt = time.time() - t0
+    assert st == mt.MT_ETIMEOUT
+    assert 1.5 < dt < 10.0
+    t = wl.film(20, 5, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    p, keep = mt.llg_params(1, alpha=0.1)
+    I = mt.Integrator(T, p, mt.ode_opts(fixed_h=1e-13))
+    assert I.path() == mt.MT_PATH_PERSISTENT
+    I.set_state(wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=0).astype(np.float32).ravel())
+    I.step(5)
+    s = I.stats()[0]
+    assert s["status"] == 0 and s["n_accept"] == 5
+    assert np.isfinite(I.get_state()).all()

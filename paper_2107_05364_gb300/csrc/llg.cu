@@ -298,7 +298,8 @@ __device__ __forceinline__ void close_first(SimCtl &c, double tau) {
 __device__ __forceinline__ void close_attempt(const StageArgs &A, SimCtl &c, const double tot[5], int64_t *out_row) {
   *out_row = -1;
   const bool fixed = A.fixed_h > 0.0;
-  const double err = sqrt(tot[0] / (3.0 * (double)A.n));
+  // the RMS of the scaled errors; its sum is an FP32 sum on both paths
+  const double err = (double)sqrtf((float)tot[0] / (3.0f * (float)A.n));
   const double tau = tot[1];
   c.err = err;
   c.n_attempt += 1;

@@ -1389,6 +1389,38 @@ void plan_host(const mt_integrator *I, SimCtl &c) {
   c.hs = hs;
 }
 
+// The one-kernel path in launches of at most kSmallChunk attempts, so that
+// no launch runs for long; between them the host reads the number of
+// unfinished simulations (and stops on a device timeout).
+constexpr int64_t kSmallChunk = 4096;
+
+mt_status small_steps(mt_integrator *I, int init, int64_t nsteps) {
+  for (int64_t done = 0; done < nsteps || init;) {
+    const int64_t todo = std::min<int64_t>(kSmallChunk, nsteps - done);
+    mt_status st = launch_small(I, init, todo);
+    if (st != MT_OK) return st;
+    init = 0;
+    done += todo;
+  }
+  return MT_OK;
+}
+
+mt_status small_until_done(mt_integrator *I, int64_t max_attempts) {
+  int init = 1;
+  for (int64_t done = 0;;) {
+    const int64_t todo = std::min<int64_t>(kSmallChunk, max_attempts - done);
+    mt_status st = launch_small(I, init, todo);
+    if (st != MT_OK) return st;
+    init = 0;
+    done += todo;
+    int h[2] = {0, 0};
+    MT_CUDA(cudaMemcpyAsync(&h[0], I->n_active, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
+    MT_CUDA(cudaMemcpyAsync(&h[1], I->T->tiles->ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, I->stream));
+    MT_CUDA(cudaStreamSynchronize(I->stream));
+    if (h[0] == 0 || h[1] != 0 || done >= max_attempts) return MT_OK;
+  }
+}
+
 // Replay the step graph until every simulation is finished (or a cap).
 mt_status replay_until_done(mt_integrator *I, int64_t max_launches) {
   int64_t launched = 0;
@@ -1665,10 +1697,10 @@ mt_status mt_integrator_step(mt_integrator *I, int64_t nsteps) {
       plan_host(I, x);
     }
     if ((st = write_ctl(I, c)) != MT_OK) return st;
-    if (I->path == MT_PATH_PERSISTENT) return launch_small(I, 1, nsteps);
+    if (I->path == MT_PATH_PERSISTENT) return small_steps(I, 1, nsteps);
     if ((st = enqueue_init(I)) != MT_OK) return st;
   }
-  if (I->path == MT_PATH_PERSISTENT) return nsteps > 0 ? launch_small(I, 0, nsteps) : MT_OK;
+  if (I->path == MT_PATH_PERSISTENT) return small_steps(I, 0, nsteps);
   for (int64_t q = 0; q < nsteps; ++q) MT_CUDA(cudaGraphLaunch(I->exec, I->stream));
   return enqueue_commit(I);
 }
@@ -1721,7 +1753,7 @@ static mt_status run_common(mt_integrator *I, int mode, double t1, int64_t n_out
   }
   if ((st = write_ctl(I, c)) != MT_OK) return st;
   if (I->path == MT_PATH_PERSISTENT) {
-    if ((st = launch_small(I, 1, I->o.max_steps + 2)) != MT_OK) return st;
+    if ((st = small_until_done(I, I->o.max_steps + 2)) != MT_OK) return st;
   } else {
     if ((st = enqueue_init(I)) != MT_OK) return st;
     if ((st = replay_until_done(I, I->o.max_steps + 2)) != MT_OK) return st;

@@ -208,3 +208,35 @@ def test_tetrahedral_tiles(mt, ctx):
                                     oracle.ode_opts(fixed_h=2e-14), 0.0, 20 * 2e-14, 1)
     assert st == oracle.OK
     assert np.abs(I.get_state()[0] - mo).max() < 2e-5
+
+
+def test_long_calls_run_in_chunks(mt, ctx):
+    # more attempts than one launch of the one-kernel path takes: the call
+    # is split into launches whose seams change nothing
+    t, tiles, T, md = _setup(mt, ctx, 10, 8)
+    p, keep = mt.llg_params(1, alpha=0.05, Ha=FIELD1)
+    h = 1e-13
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=2).astype(np.float32).ravel()
+    A = mt.Integrator(T, p, mt.ode_opts(fixed_h=h))
+    A.set_state(m0)
+    A.step(9000)
+    Bi = mt.Integrator(T, p, mt.ode_opts(fixed_h=h))
+    Bi.set_state(m0)
+    Bi.step(3000)
+    Bi.step(6000)
+    np.testing.assert_array_equal(A.get_state(), Bi.get_state())
+    sa = A.stats()[0]
+    assert sa["n_accept"] == 9000 and sa["status"] == 0, sa
+    # run mode: the host reads the unfinished count between launches
+    C = mt.Integrator(T, p, mt.ode_opts(fixed_h=h))
+    C.set_state(m0)
+    s, mavg, st = C.run(9000 * h, 9)
+    # one short step per output may be added where the summed time falls just
+    # short of the output time
+    assert st[0]["status"] == 0, st
+    assert 9000 <= st[0]["n_accept"] <= 9009, st
+    dev = float(np.abs(C.get_state() - A.get_state()).max())
+    assert dev <= 1e-5, dev
+    assert np.isfinite(mavg).all()
+    dm = float(np.abs(mavg[-1, 0] - np.average(C.get_state()[0], axis=0)).max())
+    assert dm <= 1e-5, dm

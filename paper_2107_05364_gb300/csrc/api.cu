@@ -32,6 +32,7 @@ mt_status cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 void ctx_release(mt_ctx *c) {
   if (c && --c->refs == 0) {
     cudaFree(c->d_status);
+    if (c->small_ev) cudaEventDestroy(c->small_ev);
     delete c;
   }
 }

@@ -1261,12 +1261,21 @@ mt_status launch_small(mt_integrator *I, int init, int64_t iters) {
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaError_t e;
-  switch (I->small_rmax) {
-    case 2: e = cudaLaunchKernelEx(&cfg, k_small_run<2>, S); break;
-    case 4: e = cudaLaunchKernelEx(&cfg, k_small_run<4>, S); break;
-    default: e = cudaLaunchKernelEx(&cfg, k_small_run<8>, S); break;
+  // after the context's previous one-kernel launch, whatever its stream: two
+  // such grids resident together could each hold SMs the other waits for
+  mt_ctx *ctx = T->tiles->ctx;
+  std::lock_guard<std::mutex> lock(ctx->small_mu);
+  cudaError_t e = cudaSuccess;
+  if (!ctx->small_ev) e = cudaEventCreateWithFlags(&ctx->small_ev, cudaEventDisableTiming);
+  else e = cudaStreamWaitEvent(I->stream, ctx->small_ev, 0);
+  if (e == cudaSuccess) {
+    switch (I->small_rmax) {
+      case 2: e = cudaLaunchKernelEx(&cfg, k_small_run<2>, S); break;
+      case 4: e = cudaLaunchKernelEx(&cfg, k_small_run<4>, S); break;
+      default: e = cudaLaunchKernelEx(&cfg, k_small_run<8>, S); break;
+    }
   }
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->small_ev, I->stream);
   if (e != cudaSuccess) return mt::cuda_fail(e, "k_small_run launch", __FILE__, __LINE__);
   I->need_init = false;
   return MT_OK;

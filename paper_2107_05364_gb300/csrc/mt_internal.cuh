@@ -63,6 +63,10 @@ struct mt_ctx {
   size_t in_use = 0;
   std::mutex mu;
   int *d_status = nullptr;  // device status word for bounded waits
+  // one-kernel integrator launches (cooperative grids that wait on their own
+  // CTAs) are chained through this event so that two never share the SMs
+  std::mutex small_mu;
+  cudaEvent_t small_ev = nullptr;
 };
 
 struct mt_tiles {

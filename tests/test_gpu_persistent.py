@@ -240,3 +240,29 @@ def test_long_calls_run_in_chunks(mt, ctx):
     assert np.isfinite(mavg).all()
     dm = float(np.abs(mavg[-1, 0] - np.average(C.get_state()[0], axis=0)).max())
     assert dm <= 1e-5, dm
+
+
+def test_two_integrators_at_once(mt, film):
+    # one-kernel launches from integrators on different streams queued
+    # together: they run one after the other (a cooperative grid waits on
+    # its own CTAs, so two must not share the SMs) and give what each gives
+    # alone
+    t, tiles, T, md = film
+    p, keep = mt.llg_params(1, alpha=0.05, Ha=FIELD1)
+    opts = mt.ode_opts(fixed_h=1e-13)
+    m = [wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=30 + k).astype(np.float32).ravel() for k in range(3)]
+    alone = []
+    for k in range(3):
+        I = mt.Integrator(T, p, opts)
+        I.set_state(m[k])
+        I.step(300)
+        alone.append(I.get_state())
+    its = [mt.Integrator(T, p, opts) for _ in range(3)]
+    for k in range(3):
+        its[k].set_state(m[k])
+    for k in range(3):
+        its[k].step(300)  # asynchronous, each on its own stream
+    for k in range(3):
+        np.testing.assert_array_equal(its[k].get_state(), alone[k])
+        s = its[k].stats()[0]
+        assert s["status"] == 0 and s["n_accept"] == 300

@@ -349,7 +349,9 @@ MT_API void *mt_integrator_stream(mt_integrator *I);
 /* Execution path (mt_path).  At creation an integrator takes
  * MT_PATH_PERSISTENT where it fits -- an FP32 streaming tensor with at most
  * 8 tiles per SM, whose rows and the B states of all tiles fit one SM's
- * shared memory (about 1,000 tiles for B = 1) -- and MT_PATH_GRAPH
+ * shared memory (about 1,000 tiles for B = 1), or at most 16 tiles per SM
+ * reading their rows from an L2-resident tensor of at most 96 MB (about
+ * 2,000 tiles) -- and MT_PATH_GRAPH
  * otherwise.  Both compute the same stages with the same step control; they
  * differ in the summation order of the demag product (FP32 round-off).
  * The path may be switched between calls.  set: MT_EINVAL if the path is

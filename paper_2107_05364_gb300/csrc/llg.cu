@@ -537,6 +537,7 @@ struct SmallArgs {
   int64_t iters;            // attempts at most
   int init;                 // evaluate k1 and the torque at the state first
   int R;                    // rows per CTA at most
+  int nsmem;                // 1: the CTA's tensor rows live in shared memory, 0: read from L2
 };
 
 // byte offsets of the dynamic shared memory of k_small_run
@@ -548,7 +549,7 @@ __host__ __device__ __forceinline__ size_t small_take(size_t &o, size_t bytes) {
   o += (bytes + 15) & ~(size_t)15;
   return at;
 }
-__host__ __device__ __forceinline__ SmallSmem small_smem(int64_t n, int B, int R) {
+__host__ __device__ __forceinline__ SmallSmem small_smem(int64_t n, int B, int R, bool nsmem) {
   SmallSmem s;
   size_t o = 0;
   s.ctl = small_take(o, sizeof(SimCtl) * B);
@@ -566,7 +567,7 @@ __host__ __device__ __forceinline__ SmallSmem small_smem(int64_t n, int B, int R
   s.wv = small_take(o, sizeof(float) * R);         // volume weights
   s.Ms = small_take(o, sizeof(float) * n);
   s.M = small_take(o, sizeof(float) * B * 3 * n);
-  s.N = small_take(o, sizeof(float) * 6 * R * n);
+  s.N = small_take(o, nsmem ? sizeof(float) * 6 * R * n : 0);
   s.total = o;
   return s;
 }
@@ -631,6 +632,32 @@ __device__ __forceinline__ bool small_grid_sync(const SmallArgs &S, unsigned lon
   return s_ok != 0;
 }
 
+// Eq. 1 for the CTA's rows from H_d in sh.hd: the local fields and the
+// right-hand side into kout, the torque |m x H|/Ms into sh.tau (the
+// arithmetic of k_stage).
+__device__ __forceinline__ void small_llg(const StageArgs &A, const SmallSh &sh, float *kout, int R, int nr,
+                                          int64_t r0) {
+  const int64_t n = A.n;
+  for (int p = threadIdx.x; p < A.B * nr; p += kSmallThreads) {
+    const int b = p / nr, q = p - (p / nr) * nr;
+    if (sh.ctl[b].done) continue;
+    const int64_t i = r0 + q;
+    const float *yb = sh.M + (size_t)b * 3 * n;
+    const float mi[3] = {yb[3 * i], yb[3 * i + 1], yb[3 * i + 2]};
+    const float *hd = sh.hd + ((size_t)b * R + q) * 3;
+    const float *pb = sh.par + 6 * b;
+    float H[3] = {hd[0], hd[1], hd[2]}, k[3];
+    local_fields(pb + 2, pb[5], A.exch, sh.nbr + 6 * q, sh.wex + 6 * q, sh.kan[q], sh.axis + 3 * q, yb, mi, H);
+    const float t = llg(pb[0], pb[1], mi, H, k) / sh.Ms[i];
+    float *ko = kout + ((size_t)b * R + q) * 3;
+    ko[0] = k[0];
+    ko[1] = k[1];
+    ko[2] = k[2];
+    sh.tau[(size_t)b * R + q] = t;
+  }
+  __syncthreads();
+}
+
 // k_S of the CTA's rows [r0, r0 + nr) for every running simulation, from
 // the stage input of all tiles in sh.M: H_d = -N (Ms m) from the rows held
 // in sh.N, then the local fields and Eq. 1 (the arithmetic of k_stage); the
@@ -676,24 +703,84 @@ __device__ __forceinline__ void small_rhs(const StageArgs &A, const SmallSh &sh,
     }
     __syncthreads();
   }
-  for (int p = tid; p < A.B * nr; p += kSmallThreads) {
-    const int b = p / nr, q = p - (p / nr) * nr;
-    if (sh.ctl[b].done) continue;
-    const int64_t i = r0 + q;
-    const float *yb = sh.M + (size_t)b * 3 * n;
-    const float mi[3] = {yb[3 * i], yb[3 * i + 1], yb[3 * i + 2]};
-    const float *hd = sh.hd + ((size_t)b * R + q) * 3;
-    const float *pb = sh.par + 6 * b;
-    float H[3] = {hd[0], hd[1], hd[2]}, k[3];
-    local_fields(pb + 2, pb[5], A.exch, sh.nbr + 6 * q, sh.wex + 6 * q, sh.kan[q], sh.axis + 3 * q, yb, mi, H);
-    const float t = llg(pb[0], pb[1], mi, H, k) / sh.Ms[i];
-    float *ko = kout + ((size_t)b * R + q) * 3;
-    ko[0] = k[0];
-    ko[1] = k[1];
-    ko[2] = k[2];
-    sh.tau[(size_t)b * R + q] = t;
+  small_llg(A, sh, kout, R, nr, r0);
+}
+
+// The same for tile sets whose rows do not fit the shared memory but whose
+// tensor stays in L2 (up to ~100 MB): each warp owns rows w and w + 8 of the
+// CTA (at most 16) and reads them from the streaming layout, lanes over the
+// columns (128 consecutive columns of an entry plane are contiguous, 16-byte
+// aligned), so no cross-warp reduction is needed.
+__device__ __forceinline__ void small_rhs_l2(const SmallArgs &S, const StageArgs &A, const SmallSh &sh,
+                                             float *kout, int R, int nr, int64_t r0) {
+  const int64_t n = A.n;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const size_t plane = (size_t)S.TR * S.TC, chunk = 6 * plane;
+  const float *rowp[2] = {nullptr, nullptr};
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int q = w + kSmallWarps * r;
+    if (q < nr) {
+      const int64_t i = r0 + q, p = i / S.TR;
+      rowp[r] = S.N + (size_t)p * S.Q * chunk + (size_t)(i - p * S.TR) * S.TC;
+    }
+  }
+  for (int b = 0; b < A.B; ++b) {
+    if (sh.ctl[b].done) continue;  // the same in every thread
+    float acc[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+    const float *mb = sh.M + (size_t)b * 3 * n;
+    // a lane takes 4 adjacent columns (one 16-byte load per entry plane; the
+    // padding of the last column chunk holds zeros), two such groups per
+    // step so that 24 loads per lane are in flight
+    for (int64_t j0 = 4 * lane; j0 < n; j0 += 256) {
+      float4 ent[2][2][6];
+      float x[2][4][3];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int64_t j = j0 + 128 * u;
+        const int64_t cq = j / S.TC;
+        const size_t off = (size_t)cq * chunk + (size_t)(j - cq * S.TC);
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int e = 0; e < 6; ++e)
+            ent[u][r][e] = (rowp[r] && j < n) ? __ldg(reinterpret_cast<const float4 *>(rowp[r] + off + e * plane))
+                                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool in = j + k < n;
+          const float ms = in ? sh.Ms[j + k] : 0.0f;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) x[u][k][c] = in ? ms * mb[3 * (j + k) + c] : 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float *ex = reinterpret_cast<const float *>(&ent[u][r][0]) + k;  // entry e at ex[4 e]
+            const float nxx = ex[0], nxy = ex[4], nxz = ex[8], nyy = ex[12], nyz = ex[16], nzz = ex[20];
+            const float x0 = x[u][k][0], x1 = x[u][k][1], x2 = x[u][k][2];
+            acc[r][0] = fmaf(nxx, x0, fmaf(nxy, x1, fmaf(nxz, x2, acc[r][0])));
+            acc[r][1] = fmaf(nxy, x0, fmaf(nyy, x1, fmaf(nyz, x2, acc[r][1])));
+            acc[r][2] = fmaf(nxz, x0, fmaf(nyz, x1, fmaf(nzz, x2, acc[r][2])));
+          }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (!rowp[r]) continue;  // the same in the whole warp
+      const int q = w + kSmallWarps * r;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = mtd::warp_sum(acc[r][c]);
+        if (lane == 0) sh.hd[((size_t)b * R + q) * 3 + c] = -v;
+      }
+    }
   }
   __syncthreads();
+  small_llg(A, sh, kout, R, nr, r0);
 }
 
 // all tiles' stage input (B x 3n floats written by every CTA before the
@@ -754,7 +841,7 @@ __device__ __forceinline__ void small_coefficients(const StageArgs &A, const Sma
   __syncthreads();
 }
 
-template <int RMAX>
+template <int RMAX, bool NSMEM>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
   extern __shared__ __align__(16) unsigned char smem[];
   const StageArgs &A = S.A;
@@ -763,7 +850,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
   const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)g * n / G, r1 = (int64_t)(g + 1) * n / G;
   const int nr = (int)(r1 - r0);
-  const SmallSmem L = small_smem(n, B, R);
+  const SmallSmem L = small_smem(n, B, R, NSMEM);
   SmallSh sh;
   sh.ctl = reinterpret_cast<SimCtl *>(smem + L.ctl);
   sh.red = reinterpret_cast<float *>(smem + L.red);
@@ -801,11 +888,12 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     pb[5] = A.xsc ? A.xsc[b] : 1.0f;
   }
   for (int64_t j = tid; j < n; j += kSmallThreads) sh.Ms[j] = A.Ms[j];
-  for (int64_t q = tid; q < (int64_t)6 * nr * n; q += kSmallThreads) {
-    const int64_t j = q % n, eq = q / n;
-    const int e = (int)(eq / nr), r = (int)(eq % nr);
-    sh.N[((size_t)e * R + r) * n + j] = S.N[layout_index(r0 + r, j, e, S.TR, S.TC, 6, S.Q)];
-  }
+  if (NSMEM)
+    for (int64_t q = tid; q < (int64_t)6 * nr * n; q += kSmallThreads) {
+      const int64_t j = q % n, eq = q / n;
+      const int e = (int)(eq / nr), r = (int)(eq % nr);
+      sh.N[((size_t)e * R + r) * n + j] = S.N[layout_index(r0 + r, j, e, S.TR, S.TC, 6, S.Q)];
+    }
   for (int q = tid; q < nr; q += kSmallThreads) {
     const int64_t i = r0 + q;
     for (int f = 0; f < 6; ++f) {
@@ -826,7 +914,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
 
   if (S.init) {  // k1 and the torque at the state
     small_load_state(sh.M, A.y, state);
-    small_rhs<RMAX>(A, sh, sh.k, R, nr, r0);
+    if (NSMEM) small_rhs<RMAX>(A, sh, sh.k, R, nr, r0);
+    else small_rhs_l2(S, A, sh, sh.k, R, nr, r0);
     for (int b = warp; b < B; b += kSmallWarps) {
       if (sh.ctl[b].done) continue;
       float v[5] = {0.0f, lane < nr ? sh.tau[(size_t)b * R + lane] : 0.0f, 0.0f, 0.0f, 0.0f};
@@ -875,7 +964,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
       ok = small_grid_sync(S, nbar);
       if (!ok) break;
       small_load_state(sh.M, xo, state);
-      small_rhs<RMAX>(A, sh, sh.k + (st - 1) * kpl, R, nr, r0);
+      if (NSMEM) small_rhs<RMAX>(A, sh, sh.k + (st - 1) * kpl, R, nr, r0);
+      else small_rhs_l2(S, A, sh, sh.k + (st - 1) * kpl, R, nr, r0);
     }
     if (!ok) break;
     // embedded error, torque and <m> at the 5th-order solution (the stage-7
@@ -1135,6 +1225,7 @@ struct mt_integrator {
   int path = MT_PATH_GRAPH;  // the one in use
   bool small_ok = false;     // the tile set and batch fit it
   int small_G = 0, small_R = 0, small_rmax = 0;
+  bool small_nsmem = true;  // tensor rows in shared memory (else read from L2)
   size_t small_smem_bytes = 0;
   float *sm_xg = nullptr;
   float *sm_part = nullptr;
@@ -1186,52 +1277,62 @@ StageArgs stage_args(mt_integrator *I) {
   return A;
 }
 
-constexpr size_t kSmallSmemMax = 225 * 1024;
-#ifndef MT_SMALL_MIN_ROWS
-#define MT_SMALL_MIN_ROWS 1
-#endif
-constexpr int kSmallMinRows = MT_SMALL_MIN_ROWS;  // of the 227 KB a CTA may opt in to
+constexpr size_t kSmallSmemMax = 225 * 1024;  // of the 227 KB a CTA may opt in to
 
-template <int RMAX>
+template <int RMAX, bool NSMEM>
 cudaError_t small_attr(size_t bytes, int *per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_small_run<RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_small_run<RMAX>, kSmallThreads, bytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_small_run<RMAX, NSMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_small_run<RMAX, NSMEM>, kSmallThreads, bytes);
   return e;
 }
 
-// Does the one-kernel path fit this tile set and batch?  FP32 streaming
-// tensor, at most 8 rows per CTA (one CTA per SM, up to one per tile), its
-// rows of N and the state of all tiles within the shared memory, and a
-// co-resident grid.
+// a tensor the one-kernel path reads from L2 every right-hand side must
+// stay there (L2: 129 MB)
+constexpr size_t kSmallL2Bytes = 96ull << 20;
+
+// Does the one-kernel path fit this tile set and batch?  An FP32 streaming
+// tensor; one CTA per SM (or per tile) and a co-resident grid; either at
+// most 8 rows per CTA whose tensor rows and the state of all tiles fit the
+// shared memory, or at most 16 rows per CTA read from an L2-resident tensor
+// with the state in shared memory.
 bool small_plan(mt_integrator *I) {
   const mt_tensor *T = I->T;
   if (T->prec != MT_F32 || T->layout != MT_LAYOUT_STREAM) return false;
   const int64_t n = T->n;
   const int sms = T->tiles->ctx->num_sms;
   if (n < 1 || sms < 1) return false;
-  // rows per CTA: enough to cover the tiles with one CTA per SM, and at
-  // least kSmallMinRows (fewer CTAs meet at each barrier)
   const int64_t r_sm = (n + sms - 1) / sms;
-  const int R = (int)std::max<int64_t>(r_sm, std::min<int64_t>(kSmallMinRows, n));
-  if (R > 8) return false;
-  const int G = (int)((n + R - 1) / R);
-  const size_t bytes = small_smem(n, I->B, R).total;
-  if (bytes > kSmallSmemMax) return false;
-  const int rmax = R <= 2 ? 2 : R <= 4 ? 4 : 8;
-  int per_sm = 0;
-  const cudaError_t e = rmax == 2 ? small_attr<2>(bytes, &per_sm)
-                        : rmax == 4 ? small_attr<4>(bytes, &per_sm)
-                                    : small_attr<8>(bytes, &per_sm);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool nsmem = pass == 0;
+    // rows per CTA: enough to cover the tiles with one CTA per SM (fewer
+    // CTAs meeting at each barrier measured no faster)
+    const int R = (int)r_sm;
+    if (R > (nsmem ? 8 : 2 * kSmallWarps)) continue;
+    if (!nsmem && (T->bytes > kSmallL2Bytes || T->L.TC % 4 != 0)) continue;
+    const size_t bytes = small_smem(n, I->B, R, nsmem).total;
+    if (bytes > kSmallSmemMax) continue;
+    const int G = (int)((n + R - 1) / R);
+    const int rmax = !nsmem ? 2 : R <= 2 ? 2 : R <= 4 ? 4 : 8;
+    int per_sm = 0;
+    const cudaError_t e = !nsmem     ? small_attr<2, false>(bytes, &per_sm)
+                          : rmax == 2 ? small_attr<2, true>(bytes, &per_sm)
+                          : rmax == 4 ? small_attr<4, true>(bytes, &per_sm)
+                                      : small_attr<8, true>(bytes, &per_sm);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (per_sm < 1 || (int64_t)per_sm * sms < G) continue;
+    I->small_G = G;
+    I->small_R = R;
+    I->small_rmax = rmax;
+    I->small_nsmem = nsmem;
+    I->small_smem_bytes = bytes;
+    return true;
   }
-  if (per_sm < 1 || (int64_t)per_sm * sms < G) return false;
-  I->small_G = G;
-  I->small_R = R;
-  I->small_rmax = rmax;
-  I->small_smem_bytes = bytes;
-  return true;
+  return false;
 }
 
 mt_status launch_small(mt_integrator *I, int init, int64_t iters) {
@@ -1250,6 +1351,7 @@ mt_status launch_small(mt_integrator *I, int init, int64_t iters) {
   S.iters = iters;
   S.init = init;
   S.R = I->small_R;
+  S.nsmem = I->small_nsmem ? 1 : 0;
   MT_CUDA(cudaMemsetAsync(I->sm_bar, 0, (kBarWords + kBarLine) * sizeof(unsigned long long), I->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)I->small_G);
@@ -1269,11 +1371,10 @@ mt_status launch_small(mt_integrator *I, int init, int64_t iters) {
   if (!ctx->small_ev) e = cudaEventCreateWithFlags(&ctx->small_ev, cudaEventDisableTiming);
   else e = cudaStreamWaitEvent(I->stream, ctx->small_ev, 0);
   if (e == cudaSuccess) {
-    switch (I->small_rmax) {
-      case 2: e = cudaLaunchKernelEx(&cfg, k_small_run<2>, S); break;
-      case 4: e = cudaLaunchKernelEx(&cfg, k_small_run<4>, S); break;
-      default: e = cudaLaunchKernelEx(&cfg, k_small_run<8>, S); break;
-    }
+    if (!I->small_nsmem) e = cudaLaunchKernelEx(&cfg, k_small_run<2, false>, S);
+    else if (I->small_rmax == 2) e = cudaLaunchKernelEx(&cfg, k_small_run<2, true>, S);
+    else if (I->small_rmax == 4) e = cudaLaunchKernelEx(&cfg, k_small_run<4, true>, S);
+    else e = cudaLaunchKernelEx(&cfg, k_small_run<8, true>, S);
   }
   if (e == cudaSuccess) e = cudaEventRecord(ctx->small_ev, I->stream);
   if (e != cudaSuccess) return mt::cuda_fail(e, "k_small_run launch", __FILE__, __LINE__);

@@ -7,7 +7,8 @@ the Dormand-Prince pair, renormalisation, step control); only the FP32
 summation order of the demag product differs, so they agree with each other
 and with the oracle to FP32 round-off grown over the steps.  Tile sets are
 chosen so that the rows per CTA are ragged (400 tiles over the SMs), one per
-CTA (fewer tiles than SMs) and at the shared-memory limit (1,000 tiles)."""
+CTA (fewer tiles than SMs), at the shared-memory limit (1,000 tiles) and
+read from the L2-resident tensor (1,600 tiles)."""
 import math
 
 import numpy as np
@@ -72,14 +73,18 @@ def test_path_selection(mt, ctx, film):
     with pytest.raises(mt.MtError) as e:
         J.set_path(mt.MT_PATH_PERSISTENT)
     assert e.value.status == mt.MT_EINVAL
+    mid = wl.film(40, 40, 1)  # 1,600 tiles: rows read from the L2-resident tensor
+    Tm = mt.mt_demag_assemble(mt.mt_tiles_create(ctx, mid), "f32")
+    assert mt.Integrator(Tm, p, mt.ode_opts()).path() == mt.MT_PATH_PERSISTENT
     big = wl.film(100, 50, 1)
     Tl = mt.mt_demag_assemble(mt.mt_tiles_create(ctx, big), "f32")
     assert mt.Integrator(Tl, p, mt.ode_opts()).path() == mt.MT_PATH_GRAPH
 
 
-@pytest.mark.parametrize("grid", [(40, 10, 1), (10, 8, 1), (50, 20, 1)])
+@pytest.mark.parametrize("grid", [(40, 10, 1), (10, 8, 1), (50, 20, 1), (40, 40, 1)])
 def test_fixed_steps_match_oracle_and_graph(mt, ctx, grid):
-    # 400 tiles (2 or 3 rows per CTA), 80 (one per CTA), 1,000 (7 per CTA)
+    # 400 tiles (2 or 3 rows per CTA), 80 (one per CTA), 1,000 (7 per CTA,
+    # rows in shared memory), 1,600 (11 per CTA, rows read from L2)
     t, tiles, T, md = _setup(mt, ctx, *grid)
     B = 3
     alpha, Ha = _params(B)

@@ -271,3 +271,28 @@ def test_two_integrators_at_once(mt, film):
         np.testing.assert_array_equal(its[k].get_state(), alone[k])
         s = its[k].stats()[0]
         assert s["status"] == 0 and s["n_accept"] == 300
+
+
+def test_wide_batch_matches_graph(mt, film):
+    # 12 simulations: the per-simulation step control is spread over the
+    # CTA's 8 warps (simulations 8..11 on the second pass)
+    t, tiles, T, md = film
+    B = 12
+    alpha = [0.02, 0.05, 0.1, 0.2, 0.5, 1.0] * 2
+    Ha = np.outer(np.linspace(-1.0, 1.0, B), FIELD1)
+    m0 = np.stack([wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=40 + b) for b in range(B)]).astype(np.float32)
+    p, keep = mt.llg_params(B, alpha=alpha, Ha=Ha)
+    opts = mt.ode_opts(rtol=1e-6, atol=1e-6)
+    out = {}
+    for path in (mt.MT_PATH_PERSISTENT, mt.MT_PATH_GRAPH):
+        I = mt.Integrator(T, p, opts, B)
+        I.set_path(path)
+        I.set_state(m0.ravel())
+        s, mavg, st = I.run(30e-12, 3)
+        assert all(x["status"] == 0 for x in st)
+        out[path] = (mavg, st)
+    mp, sp = out[mt.MT_PATH_PERSISTENT]
+    mg, sg = out[mt.MT_PATH_GRAPH]
+    assert np.abs(mp - mg).max() <= 1e-5
+    for a, b in zip(sp, sg):
+        assert abs(a["n_accept"] - b["n_accept"]) <= 2

@@ -197,3 +197,26 @@ def test_bad_images_rejected(mt, film):
     with pytest.raises(mt.MtError) as e:
         K.restore(image)  # B = 2 image into B = 1
     assert e.value.status == mt.MT_EINVAL
+
+
+def test_image_moves_between_paths(mt, film):
+    # an image taken on the one-kernel path continues on the step graph
+    # to FP32 round-off of the product's summation order
+    t, _, T = film
+    p, keep = _params(mt, 2)
+    opts = mt.ode_opts(fixed_h=1e-13)
+    I = mt.Integrator(T, p, opts, 2)
+    assert I.path() == mt.MT_PATH_PERSISTENT
+    I.set_state(_batch(t, 2, seed=50).ravel())
+    I.step(20)
+    image = I.checkpoint()
+    I.step(20)
+    J = mt.Integrator(T, p, opts, 2)
+    J.set_path(mt.MT_PATH_GRAPH)
+    J.restore(image)
+    J.step(20)
+    assert np.abs(J.get_state() - I.get_state()).max() <= 1e-5
+    for a, b in zip(J.stats(), I.stats()):
+        for k in ("n_accept", "n_reject", "n_rhs", "status"):
+            assert a[k] == b[k], (k, a[k], b[k])
+        assert abs(a["t"] - b["t"]) <= 1e-9 * b["t"]

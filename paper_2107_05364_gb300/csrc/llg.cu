@@ -542,7 +542,7 @@ struct SmallArgs {
 
 // byte offsets of the dynamic shared memory of k_small_run
 struct SmallSmem {
-  size_t ctl, red, hd, y, k, tau, coef, par, nbr, wex, kan, axis, wv, Ms, M, N, total;
+  size_t ctl, red, hd, y, k, tau, coef, par, kc, nbr, wex, kan, axis, wv, Ms, M, N, total;
 };
 __host__ __device__ __forceinline__ size_t small_take(size_t &o, size_t bytes) {
   const size_t at = o;
@@ -560,6 +560,7 @@ __host__ __device__ __forceinline__ SmallSmem small_smem(int64_t n, int B, int R
   s.tau = small_take(o, sizeof(float) * B * R);
   s.coef = small_take(o, sizeof(float) * B * 36);  // (float)(h a_sj), s = 1..6, j < s
   s.par = small_take(o, sizeof(float) * B * 6);    // g1, g2, Ha, exchange factor
+  s.kc = small_take(o, sizeof(int) * B);           // buffer of the committed k1 (0: k[0], 1: k[6])
   s.nbr = small_take(o, sizeof(int32_t) * R * 6);  // the CTA's rows: neighbours,
   s.wex = small_take(o, sizeof(float) * R * 6);    // exchange weights,
   s.kan = small_take(o, sizeof(float) * R);        // anisotropy, axis,
@@ -576,6 +577,7 @@ struct SmallSh {
   SimCtl *ctl;
   float *red, *hd, *y, *k, *tau, *coef, *par, *wex, *kan, *axis, *wv, *Ms, *M, *N;
   int32_t *nbr;
+  int *kc;
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
@@ -831,6 +833,26 @@ __device__ __forceinline__ void small_total(const SmallArgs &S, int b, double to
   for (int q = 0; q < 5; ++q) tot[q] = (double)acc[q];
 }
 
+// m / |m| with every rounding pinned (no contraction freedom), so that the
+// CTA committing a row and the CTAs forming the next stage input from it
+// compute the same bits
+__device__ __forceinline__ void small_unit(const float *v, float *out) {
+  const float inv = rsqrtf(__fmaf_rn(v[2], v[2], __fmaf_rn(v[1], v[1], __fmul_rn(v[0], v[0]))));
+  out[0] = __fmul_rn(v[0], inv);
+  out[1] = __fmul_rn(v[1], inv);
+  out[2] = __fmul_rn(v[2], inv);
+}
+
+// this CTA's rows [r0, r0 + nr) of a per-simulation plane (B x R x 3 in
+// shared memory) into the tile-major global array dst (B x 3n)
+__device__ __forceinline__ void small_publish_rows(float *dst, const float *src, int B, int R, int nr, int64_t r0,
+                                                   int64_t n) {
+  for (int p = threadIdx.x; p < B * nr * 3; p += kSmallThreads) {
+    const int b = p / (nr * 3), qc = p - b * nr * 3;
+    dst[(size_t)b * 3 * n + 3 * r0 + qc] = src[(size_t)b * R * 3 + qc];
+  }
+}
+
 // (float)(h a_sj) of every stage-input row s = 1..6 (the inputs of stages
 // 2..7) and j < s, per simulation: coef[36 b + 6 (s - 1) + j]
 __device__ __forceinline__ void small_coefficients(const StageArgs &A, const SmallSh &sh) {
@@ -861,6 +883,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
   sh.coef = reinterpret_cast<float *>(smem + L.coef);
   sh.par = reinterpret_cast<float *>(smem + L.par);
   sh.nbr = reinterpret_cast<int32_t *>(smem + L.nbr);
+  sh.kc = reinterpret_cast<int *>(smem + L.kc);
   sh.wex = reinterpret_cast<float *>(smem + L.wex);
   sh.kan = reinterpret_cast<float *>(smem + L.kan);
   sh.axis = reinterpret_cast<float *>(smem + L.axis);
@@ -886,6 +909,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     pb[3] = A.Ha[3 * b + 1];
     pb[4] = A.Ha[3 * b + 2];
     pb[5] = A.xsc ? A.xsc[b] : 1.0f;
+    sh.kc[b] = 0;
   }
   for (int64_t j = tid; j < n; j += kSmallThreads) sh.Ms[j] = A.Ms[j];
   if (NSMEM)
@@ -916,6 +940,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     small_load_state(sh.M, A.y, state);
     if (NSMEM) small_rhs<RMAX>(A, sh, sh.k, R, nr, r0);
     else small_rhs_l2(S, A, sh, sh.k, R, nr, r0);
+    small_publish_rows(A.k[0], sh.k, B, R, nr, r0, n);  // read by all CTAs after the barrier
     for (int b = warp; b < B; b += kSmallWarps) {
       if (sh.ctl[b].done) continue;
       float v[5] = {0.0f, lane < nr ? sh.tau[(size_t)b * R + lane] : 0.0f, 0.0f, 0.0f, 0.0f};
@@ -938,7 +963,33 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     for (int b = 0; b < B; ++b) any = any || !sh.ctl[b].done;
     if (!any) break;
     small_coefficients(A, sh);
-    for (int st = 2; st <= 7 && ok; ++st) {
+    // stage 2 needs no exchange between CTAs: every CTA forms the input of
+    // all tiles, y + (h a_21) k1, from the committed state (after an accepted
+    // attempt: the normalised 5th-order solution still in sh.M and the k7
+    // every CTA published; else the committed y and k1 in global memory)
+    for (int b = 0; b < B; ++b) {
+      if (sh.ctl[b].done) continue;
+      const bool adopt = it > 0 && sh.ctl[b].accepted;
+      const float a21 = sh.coef[36 * b];
+      const float *kb = (sh.kc[b] ? A.k[6] : A.k[0]) + (size_t)b * 3 * n;
+      const float *yb = A.y + (size_t)b * 3 * n;
+      float *mb = sh.M + (size_t)b * 3 * n;
+      for (int64_t j = tid; j < n; j += kSmallThreads) {
+        float y[3];
+        if (adopt) {
+          small_unit(mb + 3 * j, y);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) y[c] = __ldcg(yb + 3 * j + c);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mb[3 * j + c] = __fadd_rn(y[c], __fmul_rn(a21, __ldcg(kb + 3 * j + c)));
+      }
+    }
+    __syncthreads();
+    if (NSMEM) small_rhs<RMAX>(A, sh, sh.k + kpl, R, nr, r0);
+    else small_rhs_l2(S, A, sh, sh.k + kpl, R, nr, r0);
+    for (int st = 3; st <= 7 && ok; ++st) {
       // this CTA's rows of the stage input y + sum_j (h a_sj) k_j
       float *xo = S.xg + (size_t)(st & 1) * state;
       for (int p = tid; p < B * nr; p += kSmallThreads) {
@@ -968,6 +1019,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
       else small_rhs_l2(S, A, sh, sh.k + (st - 1) * kpl, R, nr, r0);
     }
     if (!ok) break;
+    // this CTA's k7 rows into the buffer not holding the committed k1: the
+    // next attempt's k1 if this one is accepted
+    for (int p = tid; p < B * nr * 3; p += kSmallThreads) {
+      const int b = p / (nr * 3), qc = p - b * nr * 3;
+      if (sh.ctl[b].done) continue;
+      (sh.kc[b] ? A.k[0] : A.k[6])[(size_t)b * 3 * n + 3 * r0 + qc] = sh.k[6 * kpl + (size_t)b * R * 3 + qc];
+    }
     // embedded error, torque and <m> at the 5th-order solution (the stage-7
     // input), in FP32 over the CTA's rows: one lane per row
     for (int b = warp; b < B; b += kSmallWarps) {
@@ -1013,22 +1071,27 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
       __syncwarp();
     }
     __syncthreads();
-    // accepted: adopt the normalised 5th-order solution; k7 is the next k1
+    // accepted: adopt the normalised 5th-order solution (this CTA's rows also
+    // into the committed y in global memory, read after a later rejection);
+    // k7 is the next k1
     for (int p = tid; p < B * nr; p += kSmallThreads) {
       const int b = p / nr, q = p - (p / nr) * nr;
       if (!sh.ctl[b].accepted) continue;
       const float *yn = sh.M + (size_t)b * 3 * n + 3 * (r0 + q);
-      const float inv = rsqrtf(yn[0] * yn[0] + yn[1] * yn[1] + yn[2] * yn[2]);
       float *y0 = sh.y + ((size_t)b * R + q) * 3;
       float *k1 = sh.k + ((size_t)b * R + q) * 3;
       const float *k7 = sh.k + 6 * kpl + ((size_t)b * R + q) * 3;
-      y0[0] = yn[0] * inv;
-      y0[1] = yn[1] * inv;
-      y0[2] = yn[2] * inv;
-      k1[0] = k7[0];
-      k1[1] = k7[1];
-      k1[2] = k7[2];
+      float *yg = A.y + (size_t)b * 3 * n + 3 * (r0 + q);
+      small_unit(yn, y0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        yg[c] = y0[c];
+        k1[c] = k7[c];
+      }
     }
+    __syncthreads();
+    for (int b = tid; b < B; b += kSmallThreads)
+      if (sh.ctl[b].accepted) sh.kc[b] ^= 1;
     __syncthreads();
   }
   if (!ok) return;  // timed out: the status word tells the host

@@ -40,10 +40,12 @@ from paper_2107_05364_gb300 import workloads as wl  # noqa: E402
 MU0 = 4e-7 * math.pi
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the streaming FP32 product at the film workload below (n = 10,000), from one
-# ncu capture of a full launch: 2,427,094,016 read + 2,980,864 written
-# (1.0125 x the 2.4e9 algorithmic bytes: the zero padding of the last chunk
-# row).  Valid while k_matvec<f32> is unchanged.
-MATVEC_F32_N10000_TRAFFIC = 2427094016 + 2980864
+# ncu capture of a full launch, by stored entry planes: 6 planes 2,427,094,016
+# read + 2,980,864 written (1.0125 x the 2.4e9 algorithmic bytes: the zero
+# padding of the last chunk row); 4 planes (the single-layer film)
+# 1,618,193,152 + 2,841,856 (1.0131 x 1.6e9).  Valid while k_matvec<f32> is
+# unchanged.
+MATVEC_F32_N10000_TRAFFIC = {6: 2427094016 + 2980864, 4: 1618193152 + 2841856}
 # The tensor-core products at n = 8,000 read 1.0040 (split) and 1.0028 (BF16)
 # x their stored tensors and wrote their fields (one ncu capture each of the
 # current kernels); the batched line scales that per stored byte.
@@ -249,7 +251,10 @@ def run_ours(args):
     e1.record(cur)
     torch.cuda.synchronize()
     field_ms = e0.elapsed_time(e1) / reps  # includes the tiny operand-prep kernel
-    alg_bytes = 24.0 * n * n  # 6 unique FP32 entries per 3x3 block, each read once
+    # the stored FP32 entries of a 3x3 block, each read once: 6, or 4 for a
+    # single-layer film (xz and yz vanish)
+    planes = info["planes"]
+    alg_bytes = 4.0 * planes * n * n
     peaks, kind = _peaks()
     achieved = alg_bytes / (field_ms * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -289,8 +294,11 @@ def run_ours(args):
         # the same film, one simulation, with the tensor stored in the other
         # streaming precisions (BF16 with per-block scales, split BF16)
         prec_rows = {}
-        for pname in ("bf16", "split"):
-            Tp = mt.mt_demag_assemble(tiles, pname)
+        for pname in ("f32_six_planes", "bf16", "split"):
+            if pname == "f32_six_planes":
+                Tp = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM6)
+            else:
+                Tp = mt.mt_demag_assemble(tiles, pname)
             Ip = mt.Integrator(Tp, p, mt.ode_opts(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11))
             Ip.set_state(m0.ravel())
             Ip.step(3)
@@ -327,13 +335,15 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "tiles": n, "precision": "f32 storage, f32 accumulate, f64 assembly",
+                   "stored_planes": planes,
                    "sims_per_gpu": 1, "step": "one Dormand-Prince attempt = 6 RHS",
                    "l2": "inputs larger than L2 (tensor %.2f GB, L2 129 MB)" % (info["bytes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single",
                    "sms": torch.cuda.get_device_properties(dev).multi_processor_count},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": MATVEC_F32_N10000_TRAFFIC if n == 10000 else None, "kernel": "k_matvec<f32>",
+                     "traffic": MATVEC_F32_N10000_TRAFFIC.get(planes) if n == 10000 else None,
+                     "kernel": "k_matvec<f32>" if planes == 6 else "k_matvec<f32, 4 planes>",
                      "peak_kind": kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": field_ms},
         "demag_gbs": achieved,
@@ -751,7 +761,8 @@ def run_tetra(args):
         tiles = make()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        T = mt.mt_demag_assemble(tiles, "f32")
+        # all 6 entry planes for both: the single-layer film would store 4
+        T = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM6)
         torch.cuda.synchronize()
         t_asm = time.perf_counter() - t0
         m = torch.tensor(wl.m_random(tiles.n, seed=1).astype(np.float32).ravel(), device="cuda")
@@ -778,7 +789,7 @@ def run_tetra(args):
         torch.cuda.synchronize()
         step_ms = e0.elapsed_time(e1) / 100
         out[name] = {"tiles": tiles.n, "assemble_s": t_asm, "blocks_per_s": tiles.n ** 2 / t_asm,
-                     "product_ms": ms, "product_gbs": 24.0 * tiles.n ** 2 / (ms * 1e-3) / 1e9,
+                     "product_ms": ms, "product_gbs": 4.0 * T.info()["planes"] * tiles.n ** 2 / (ms * 1e-3) / 1e9,
                      "rhs_evals_per_s": 6.0 / (step_ms * 1e-3)}
         I.close()
         T.close()

@@ -79,8 +79,10 @@ typedef enum {
   MT_LAYOUT_DENSE = 1,  /* all 9 entries, row-major 3n x 3n BF16 (or hi + lo   */
                         /* pair) for the batched tensor-core product; only      */
                         /* MT_BF16_SCALED (scales fixed to 1) and MT_BF16_SPLIT */
-  MT_LAYOUT_SPARSE = 2  /* thresholded FP32 tensor in block-sparse rows        */
+  MT_LAYOUT_SPARSE = 2, /* thresholded FP32 tensor in block-sparse rows       */
                         /* (made by mt_tensor_threshold, Sec. 4.3.1)            */
+  MT_LAYOUT_STREAM6 = 3 /* MT_LAYOUT_STREAM with all 6 entry planes stored     */
+                        /* even where two vanish (see mt_demag_assemble)        */
 } mt_layout_kind;
 
 /* Equation-of-motion form. */
@@ -144,7 +146,8 @@ typedef struct {
   int32_t prec;        /* mt_prec                                             */
   int32_t rows_per_panel, cols_per_chunk; /* tile-blocked layout (stream)     */
   int32_t layout;      /* mt_layout_kind                                      */
-  int32_t pad;
+  int32_t planes;      /* stored values per 3x3 block: 6, 4 (single-layer     */
+                       /* FP32 streaming tensor), 12 (split), 9 (dense)       */
   int64_t bytes;       /* device bytes of the stored tensor                   */
   int64_t near_blocks; /* FP64 near-field blocks kept apart (0 if none)       */
 } mt_tensor_info;
@@ -218,6 +221,15 @@ MT_API void mt_tiles_destroy(mt_tiles *tiles);
  * another tile), MT_ENOMEM (allocation failed or the context budget would
  * be exceeded), MT_EINVAL, MT_ECUDA. */
 MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out);
+/* Single-layer tile sets.  When every cuboid tile has the same centre z and
+ * the same z edge, each tile's field point lies in the mid-plane of every
+ * other tile, and the xz and yz entries of every block vanish by mirror
+ * symmetry (they are odd in the z offset).  An FP32 streaming tensor of such
+ * a set stores the 4 entry planes xx, xy, yy, zz (16 bytes per block instead
+ * of 24), provided that every assembled |N_xz|, |N_yz| is at most 1e-12
+ * (their FP64 round-off; otherwise all 6 planes are stored).  Products,
+ * row reads and thresholding treat the missing entries as zeros.
+ * MT_LAYOUT_STREAM6 keeps the 6 planes. */
 /* As mt_demag_assemble, with an explicit storage layout (mt_layout_kind).
  * MT_LAYOUT_DENSE turns every product over a batch of B simulations into a
  * GEMM on the tensor cores (tcgen05, BF16 in, FP32 accumulate); the rows and

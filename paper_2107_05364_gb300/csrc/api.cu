@@ -447,8 +447,10 @@ mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
 mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_tensor **out) {
   MT_CHECK(tiles && out, MT_EINVAL, "mt_demag_assemble: NULL argument");
   MT_CHECK(prec >= MT_F64 && prec <= MT_BF16_SPLIT, MT_EINVAL, "mt_demag_assemble: bad precision %d", (int)prec);
-  MT_CHECK(layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_DENSE, MT_EINVAL, "mt_demag_assemble: bad layout %d",
-           layout);
+  MT_CHECK(layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_DENSE || layout == MT_LAYOUT_STREAM6, MT_EINVAL,
+           "mt_demag_assemble: bad layout %d", layout);
+  const bool allow_planar = layout == MT_LAYOUT_STREAM;
+  if (layout == MT_LAYOUT_STREAM6) layout = MT_LAYOUT_STREAM;
   MT_CHECK(layout == MT_LAYOUT_STREAM || prec == MT_BF16_SCALED || prec == MT_BF16_SPLIT, MT_EINVAL,
            "mt_demag_assemble: the dense layout stores BF16 or split BF16 only");
   mt_ctx *ctx = tiles->ctx;
@@ -472,6 +474,14 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
     data_bytes = (size_t)T->Kp * T->Kp * 2 * (prec == MT_BF16_SPLIT ? 2 : 1);
   } else {
     mt::layout_for(prec, &T->L);
+    // single-layer cuboid set (every tile: the same centre z and z edge): the
+    // FP32 tensor's xz and yz entries vanish; 4 entry planes
+    if (allow_planar && prec == MT_F32 && tiles->kind == MT_TILE_CUBOID) {
+      bool planar = true;
+      for (int64_t i = 1; i < tiles->n && planar; ++i)
+        planar = tiles->centre[3 * i + 2] == tiles->centre[2] && tiles->edge[3 * i + 2] == tiles->edge[2];
+      if (planar) mt::layout_for_planar(&T->L);
+    }
     T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
     T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
     data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
@@ -521,7 +531,7 @@ mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
   info->rows_per_panel = T->L.TR;
   info->cols_per_chunk = T->L.TC;
   info->layout = T->layout;
-  info->pad = 0;
+  info->planes = T->layout == MT_LAYOUT_DENSE ? 9 : T->layout == MT_LAYOUT_SPARSE ? 6 : T->L.nplane;
   info->bytes = (int64_t)T->bytes;
   info->near_blocks = T->near_count;
   return MT_OK;

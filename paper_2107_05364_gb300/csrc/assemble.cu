@@ -264,6 +264,7 @@ struct AsmArgs {
   void *data;
   int8_t *scale;
   int *bad;           // set to 1 on overlap
+  int *planar_bad;    // set to 1 if a 4-plane (single-layer) tensor meets |N_xz| or |N_yz| > kPlanarTol
   int dense;          // 1: 9-entry row-major matrix (Kp x Kp), else tile-blocked
   int64_t Kp;
   int *near_fill;     // per-row fill counter (BF16 precisions)
@@ -361,7 +362,11 @@ __global__ void k_assemble(AsmArgs A) {
       case MT_F32: {
         float *D = (float *)A.data;
 #pragma unroll
-        for (int e = 0; e < 6; ++e) D[layout_index(i, j, e, A.TR, A.TC, 6, A.Q)] = (float)N6[e];
+        for (int e = 0; e < 6; ++e) {
+          const int pl = stream_plane(e, A.nplane);
+          if (pl >= 0) D[layout_index(i, j, pl, A.TR, A.TC, A.nplane, A.Q)] = (float)N6[e];
+          else if (!(fabs(N6[e]) <= kPlanarTol)) *A.planar_bad = 1;
+        }
       } break;
       case MT_BF16_SCALED: {
         // power-of-two scale of the block: 2^s with s = exponent of max |N|
@@ -439,7 +444,7 @@ __global__ void k_blocks(const double *centre, const double *edge, const double 
 
 // stored value -> double, rows [i0, i1), all columns; out[((i-i0)*n + j)*6 + e]
 __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int64_t n, int TR, int TC,
-                            int64_t Q, int64_t i0, int64_t i1, double *out) {
+                            int nplane, int64_t Q, int64_t i0, int64_t i1, double *out) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t rows = i1 - i0;
   if (t >= rows * n) return;
@@ -448,7 +453,10 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
     double v = 0.0;
     switch (prec) {
       case MT_F64: v = ((const double *)data)[layout_index(i, j, e, TR, TC, 6, Q)]; break;
-      case MT_F32: v = ((const float *)data)[layout_index(i, j, e, TR, TC, 6, Q)]; break;
+      case MT_F32: {
+        const int pl = stream_plane(e, nplane);
+        v = pl < 0 ? 0.0 : ((const float *)data)[layout_index(i, j, pl, TR, TC, nplane, Q)];
+      } break;
       case MT_BF16_SCALED:
         v = ldexp((double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, e, TR, TC, 6, Q)]),
                   (int)scale[scale_index(i, j, TR, TC, Q)]);
@@ -499,9 +507,9 @@ mt_status assemble(mt_tensor *T) {
   const int64_t n = T->n;
   const mt_layout &L = T->L;
   DevTemp<int> bad_flag;
-  MT_CUDA(bad_flag.alloc(1));
+  MT_CUDA(bad_flag.alloc(2));
   int *d_bad = bad_flag.p;
-  MT_CUDA(cudaMemset(d_bad, 0, sizeof(int)));
+  MT_CUDA(cudaMemset(d_bad, 0, 2 * sizeof(int)));
   AsmArgs A{};
   A.centre = t->d_centre;
   A.edge = t->d_edge;
@@ -516,6 +524,7 @@ mt_status assemble(mt_tensor *T) {
   A.data = T->d_data;
   A.scale = T->d_scale;
   A.bad = d_bad;
+  A.planar_bad = d_bad + 1;
   A.dense = T->layout == MT_LAYOUT_DENSE;
   A.Kp = T->Kp;
   DevTemp<double> table;
@@ -575,9 +584,37 @@ mt_status assemble(mt_tensor *T) {
     MT_CUDA(cudaGetLastError());
     MT_CUDA(cudaDeviceSynchronize());
   }
-  int bad = 0;
-  MT_CUDA(cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost));
-  MT_CHECK(!bad, MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
+  int bad[2] = {0, 0};
+  MT_CUDA(cudaMemcpy(bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  MT_CHECK(!bad[0], MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
+  if (bad[1] && T->L.nplane == 4) {
+    // an xz or yz entry of the single-layer set is not round-off: store all
+    // 6 planes after all (within the budget reserved for them)
+    mt_ctx *ctx = t->ctx;
+    layout_for(MT_F32, &T->L);
+    T->L.P = (n + T->L.TR - 1) / T->L.TR;
+    T->L.Q = (n + T->L.TC - 1) / T->L.TC;
+    const size_t bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
+    {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      MT_CHECK(ctx->in_use - T->bytes + bytes <= ctx->budget, MT_ENOMEM,
+               "mt_demag_assemble: %zu bytes exceed the context budget", bytes);
+      ctx->in_use += bytes - T->bytes;
+      T->bytes = bytes;
+    }
+    MT_CUDA(cudaFree(T->d_data));
+    T->d_data = nullptr;
+    MT_CUDA(cudaMalloc(&T->d_data, bytes));
+    MT_CUDA(cudaMemset(T->d_data, 0, bytes));
+    A.data = T->d_data;
+    A.TR = T->L.TR;
+    A.TC = T->L.TC;
+    A.nplane = T->L.nplane;
+    A.Q = T->L.Q;
+    k_assemble<<<dim3((unsigned)T->L.Q, (unsigned)T->L.P), T->L.TC>>>(A);
+    MT_CUDA(cudaGetLastError());
+    MT_CUDA(cudaDeviceSynchronize());
+  }
   return MT_OK;
 }
 
@@ -611,7 +648,7 @@ mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
                                                               T->prec == MT_BF16_SPLIT, n, T->Kp, i0, i1, d_out);
   else
     k_read_rows<<<(unsigned)((tot + 255) / 256), 256>>>(T->d_data, T->d_scale, T->prec, n, T->L.TR, T->L.TC,
-                                                         T->L.Q, i0, i1, d_out);
+                                                         T->L.nplane, T->L.Q, i0, i1, d_out);
   MT_CUDA(cudaGetLastError());
   if (T->near_count > 0) {
     k_merge_near<<<(unsigned)((rows + 127) / 128), 128>>>(n, i0, i1, T->d_near_ptr, T->d_near_col,

@@ -538,6 +538,7 @@ struct SmallArgs {
   int init;                 // evaluate k1 and the torque at the state first
   int R;                    // rows per CTA at most
   int nsmem;                // 1: the CTA's tensor rows live in shared memory, 0: read from L2
+  int nplane;               // stored entry planes: 6, or 4 (single layer: no xz, yz)
 };
 
 // byte offsets of the dynamic shared memory of k_small_run
@@ -717,7 +718,7 @@ __device__ __forceinline__ void small_rhs_l2(const SmallArgs &S, const StageArgs
                                              float *kout, int R, int nr, int64_t r0) {
   const int64_t n = A.n;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const size_t plane = (size_t)S.TR * S.TC, chunk = 6 * plane;
+  const size_t plane = (size_t)S.TR * S.TC, chunk = (size_t)S.nplane * plane;
   const float *rowp[2] = {nullptr, nullptr};
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -745,9 +746,12 @@ __device__ __forceinline__ void small_rhs_l2(const SmallArgs &S, const StageArgs
 #pragma unroll
         for (int r = 0; r < 2; ++r)
 #pragma unroll
-          for (int e = 0; e < 6; ++e)
-            ent[u][r][e] = (rowp[r] && j < n) ? __ldg(reinterpret_cast<const float4 *>(rowp[r] + off + e * plane))
-                                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          for (int e = 0; e < 6; ++e) {
+            const int pl = stream_plane(e, S.nplane);
+            ent[u][r][e] = (rowp[r] && j < n && pl >= 0)
+                               ? __ldg(reinterpret_cast<const float4 *>(rowp[r] + off + pl * plane))
+                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const bool in = j + k < n;
@@ -916,7 +920,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_run(SmallArgs S) {
     for (int64_t q = tid; q < (int64_t)6 * nr * n; q += kSmallThreads) {
       const int64_t j = q % n, eq = q / n;
       const int e = (int)(eq / nr), r = (int)(eq % nr);
-      sh.N[((size_t)e * R + r) * n + j] = S.N[layout_index(r0 + r, j, e, S.TR, S.TC, 6, S.Q)];
+      const int pl = stream_plane(e, S.nplane);
+      sh.N[((size_t)e * R + r) * n + j] = pl < 0 ? 0.0f : S.N[layout_index(r0 + r, j, pl, S.TR, S.TC, S.nplane, S.Q)];
     }
   for (int q = tid; q < nr; q += kSmallThreads) {
     const int64_t i = r0 + q;
@@ -1415,6 +1420,7 @@ mt_status launch_small(mt_integrator *I, int init, int64_t iters) {
   S.init = init;
   S.R = I->small_R;
   S.nsmem = I->small_nsmem ? 1 : 0;
+  S.nplane = T->L.nplane;
   MT_CUDA(cudaMemsetAsync(I->sm_bar, 0, (kBarWords + kBarLine) * sizeof(unsigned long long), I->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)I->small_G);

@@ -181,6 +181,17 @@ struct mt_tensor {
   float *d_sp_val = nullptr;
 };
 
+// Plane of entry e (xx, xy, xz, yy, yz, zz) in a streaming layout of
+// nplane planes: the identity for 6 (and 12: hi planes), -1 for the xz and
+// yz entries of a single-layer FP32 tensor (planes xx, xy, yy, zz).
+__host__ __device__ __forceinline__ int stream_plane(int e, int nplane) {
+  if (nplane != 4) return e;
+  return e < 2 ? e : e == 3 ? 2 : e == 5 ? 3 : -1;
+}
+// bound on |N_xz|, |N_yz| of a single-layer tile set (FP64 round-off of
+// entries that vanish by mirror symmetry)
+constexpr double kPlanarTol = 1e-12;
+
 // Index of entry e of block (i, j) in the tile-blocked streaming layout.
 __host__ __device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, int e, int TR, int TC, int nplane,
                                                          int64_t Q) {
@@ -221,6 +232,7 @@ int matvec_grid(const mt_tensor *T);
 cudaError_t matvec_prepare();
 // Panel/chunk shape of the storage for a precision (P, Q left to the caller).
 void layout_for(int prec, mt_layout *L);
+void layout_for_planar(mt_layout *L);  // FP32, single-layer tile set: 4 entry planes
 // floats of the padded, Ms-scaled operand of one simulation: Q * 3 * TC
 int64_t xs_floats(const mt_tensor *T);
 // bytes of the partial-sum workspace and of the panel counters for B sims

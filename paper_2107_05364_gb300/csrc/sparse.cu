@@ -43,25 +43,29 @@ __device__ __forceinline__ uint32_t abs_bits(float v) { return __float_as_uint(v
 // entries of the streaming FP32 layout belonging to real tiles, with their
 // multiplicity in the full matrix (diagonal 1, off-diagonal 2)
 template <typename F>
-__device__ __forceinline__ void for_each_entry(const float *D, int64_t n, int TR, int TC, int64_t Q, int64_t blk,
-                                               F &&f) {
-  // blk enumerates (p, q, r, c) chunk positions; the 6 planes of the block
+__device__ __forceinline__ void for_each_entry(const float *D, int64_t n, int TR, int TC, int np, int64_t Q,
+                                               int64_t blk, F &&f) {
+  // blk enumerates (p, q, r, c) chunk positions; the 6 entries of the block
+  // (np planes stored: 6, or 4 for a single-layer tensor without xz, yz)
   const int64_t per_chunk = (int64_t)TR * TC;
   const int64_t chunk = blk / per_chunk, rc = blk - chunk * per_chunk;
   const int64_t p = chunk / Q, q = chunk - p * Q;
   const int r = (int)(rc / TC), c = (int)(rc - (int64_t)(rc / TC) * TC);
   const int64_t i = p * TR + r, j = q * TC + c;
   if (i >= n || j >= n) return;
-  const float *base = D + chunk * 6 * per_chunk + (int64_t)r * TC + c;
+  const float *base = D + chunk * np * per_chunk + (int64_t)r * TC + c;
   const int mult[6] = {1, 2, 2, 1, 2, 1};
 #pragma unroll
-  for (int e = 0; e < 6; ++e) f(i, j, e, base[e * per_chunk], mult[e]);
+  for (int e = 0; e < 6; ++e) {
+    const int pl = stream_plane(e, np);
+    f(i, j, e, pl < 0 ? 0.0f : base[pl * per_chunk], mult[e]);
+  }
 }
 
-__global__ void k_hist(const float *D, int64_t n, int TR, int TC, int64_t Q, int64_t nblk, int pass, uint32_t hi,
-                       unsigned long long *hist) {
+__global__ void k_hist(const float *D, int64_t n, int TR, int TC, int np, int64_t Q, int64_t nblk, int pass,
+                       uint32_t hi, unsigned long long *hist) {
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nblk; b += (int64_t)gridDim.x * blockDim.x)
-    for_each_entry(D, n, TR, TC, Q, b, [&](int64_t, int64_t, int, float v, int mult) {
+    for_each_entry(D, n, TR, TC, np, Q, b, [&](int64_t, int64_t, int, float v, int mult) {
       const uint32_t bits = abs_bits(v);
       if (bits == 0) return;
       if (pass == 0) atomicAdd(&hist[bits >> 16], (unsigned long long)mult);
@@ -70,7 +74,7 @@ __global__ void k_hist(const float *D, int64_t n, int TR, int TC, int64_t Q, int
 }
 
 // copies of the cut value t in row tile i (counted for the tie order)
-__global__ void k_row_ties(const float *D, int64_t n, int TR, int TC, int64_t Q, uint32_t tbits,
+__global__ void k_row_ties(const float *D, int64_t n, int TR, int TC, int np, int64_t Q, uint32_t tbits,
                            unsigned long long *ties) {
   const int64_t i = blockIdx.x;
   const int64_t p = i / TR;
@@ -80,9 +84,12 @@ __global__ void k_row_ties(const float *D, int64_t n, int TR, int TC, int64_t Q,
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
     const int64_t q = j / TC;
     const int c = (int)(j - q * TC);
-    const float *base = D + (p * Q + q) * 6 * (int64_t)TR * TC + (int64_t)r * TC + c;
+    const float *base = D + (p * Q + q) * np * (int64_t)TR * TC + (int64_t)r * TC + c;
 #pragma unroll
-    for (int e = 0; e < 6; ++e) local += abs_bits(base[e * (int64_t)TR * TC]) == tbits ? mult[e] : 0;
+    for (int e = 0; e < 6; ++e) {
+      const int pl = stream_plane(e, np);
+      if (pl >= 0) local += abs_bits(base[pl * (int64_t)TR * TC]) == tbits ? mult[e] : 0;
+    }
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
@@ -103,7 +110,7 @@ __global__ void k_row_ties(const float *D, int64_t n, int TR, int TC, int64_t Q,
 // write them (slots by ballot + popc), then the row's padding blocks
 // (column 0, entries 0).  With t = 0 every nonzero entry is kept.
 template <bool FILL>
-__global__ void k_rows(const float *D, int64_t n, int TR, int TC, int64_t Q, uint32_t tbits,
+__global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_t Q, uint32_t tbits,
                        const unsigned long long *tie_start, unsigned long long r, int *cnt, const int64_t *ptr,
                        int32_t *col, float *val) {
   const int64_t i = blockIdx.x;
@@ -123,10 +130,11 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int64_t Q, uin
     if (j < n) {
       const int64_t q = j / TC;
       const int c = (int)(j - q * TC);
-      const float *base = D + (p * Q + q) * 6 * (int64_t)TR * TC + (int64_t)rr * TC + c;
+      const float *base = D + (p * Q + q) * np * (int64_t)TR * TC + (int64_t)rr * TC + c;
 #pragma unroll
       for (int e = 0; e < 6; ++e) {
-        v[e] = base[e * (int64_t)TR * TC];
+        const int pl = stream_plane(e, np);
+        v[e] = pl < 0 ? 0.0f : base[pl * (int64_t)TR * TC];
         bits[e] = abs_bits(v[e]);
         tm += (bits[e] != 0 && bits[e] == tbits) ? mult[e] : 0;
       }
@@ -311,7 +319,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   const int grid = 4 * T->tiles->ctx->num_sms;
   // pass 1: top 16 bits
   MT_CUDA(cudaMemset(d_hist, 0, sizeof(unsigned long long) * 65536));
-  k_hist<<<grid, 256>>>(D, n, L.TR, L.TC, L.Q, nblk, 0, 0, d_hist);
+  k_hist<<<grid, 256>>>(D, n, L.TR, L.TC, L.nplane, L.Q, nblk, 0, 0, d_hist);
   MT_CUDA(cudaGetLastError());
   MT_CUDA(cudaMemcpy(h.data(), d_hist, sizeof(unsigned long long) * 65536, cudaMemcpyDeviceToHost));
   unsigned long long nz = 0;
@@ -325,7 +333,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     select_bin(h, k, &b1, &rest);
     // pass 2: low 16 bits inside bin b1
     MT_CUDA(cudaMemset(d_hist, 0, sizeof(unsigned long long) * 65536));
-    k_hist<<<grid, 256>>>(D, n, L.TR, L.TC, L.Q, nblk, 1, b1, d_hist);
+    k_hist<<<grid, 256>>>(D, n, L.TR, L.TC, L.nplane, L.Q, nblk, 1, b1, d_hist);
     MT_CUDA(cudaGetLastError());
     MT_CUDA(cudaMemcpy(h.data(), d_hist, sizeof(unsigned long long) * 65536, cudaMemcpyDeviceToHost));
     uint32_t b2 = 0;
@@ -340,7 +348,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   if (r > 0) {
     MT_CUDA(tie_start.alloc(n));
     d_tie = tie_start.p;
-    k_row_ties<<<(unsigned)n, 256>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie);
+    k_row_ties<<<(unsigned)n, 256>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie);
     MT_CUDA(cudaGetLastError());
     std::vector<unsigned long long> ties(n);
     MT_CUDA(cudaMemcpy(ties.data(), d_tie, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost));
@@ -356,7 +364,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   DevTemp<int> cnt_rows;
   MT_CUDA(cnt_rows.alloc(n));
   int *d_cnt = cnt_rows.p;
-  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr, nullptr);
+  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr, nullptr);
   MT_CUDA(cudaGetLastError());
   std::vector<int> cnt(n);
   MT_CUDA(cudaMemcpy(cnt.data(), d_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
@@ -392,7 +400,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     mt::tensor_release(S);
     return mt::cuda_fail(e, "mt_tensor_threshold allocation", __FILE__, __LINE__);
   }
-  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.Q, tbits, d_tie, r, nullptr, S->d_sp_ptr, S->d_sp_col,
+  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, nullptr, S->d_sp_ptr, S->d_sp_col,
                                     S->d_sp_val);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

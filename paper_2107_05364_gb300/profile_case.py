@@ -72,7 +72,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / a.reps
-        gbs = 24.0 * t.n * t.n * a.B / (ms * 1e-3) / 1e9 if a.prec == "f32" else float("nan")
+        gbs = 4.0 * T.info()["planes"] * t.n * t.n * a.B / (ms * 1e-3) / 1e9 if a.prec == "f32" else float("nan")
         if a.threshold is not None:
             gbs = T.info()["bytes"] * a.B / (ms * 1e-3) / 1e9
         print("field n=%d B=%d prec=%s: %.4f ms/call (%.0f GB/s algorithmic for f32)" % (t.n, a.B, a.prec, ms, gbs))

@@ -256,3 +256,39 @@ def test_llg_rhs_parity(mt, ctx):
         kg = k.cpu().numpy().reshape(B, t.n, 3)[b]
         assert _rel(kg, kr) <= 1e-5
         assert abs(tau.cpu().numpy()[b] - taur) <= 1e-5 * taur
+
+
+@pytest.mark.parametrize("z0", [0.0, 10.7e-9])
+def test_single_layer_stores_four_planes(mt, ctx, z0):
+    # every tile in one layer: the xz and yz entries vanish by mirror
+    # symmetry (exactly for the film at z = 0, to FP64 round-off when it is
+    # moved up to z0 = 10.7 nm); the FP32 streaming tensor keeps 4 planes and
+    # gives the 6-plane field and the oracle's
+    import torch
+    t = wl.grid_tiles(np.linspace(0, 500e-9, 41), np.linspace(0, 125e-9, 11), np.array([z0, z0 + 3e-9]),
+                      wl.SP4_MS, wl.SP4_AEX, 0.0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T4 = mt.mt_demag_assemble(tiles, "f32")
+    T6 = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM6)
+    assert T4.info()["planes"] == 4 and T6.info()["planes"] == 6
+    assert T4.info()["bytes"] < 0.7 * T6.info()["bytes"]
+    r4, r6 = mt.mt_tensor_read_rows(T4, 0, t.n), mt.mt_tensor_read_rows(T6, 0, t.n)
+    assert np.abs(r6[..., [2, 4]]).max() <= 1e-12
+    np.testing.assert_array_equal(r4[..., [0, 1, 3, 5]], r6[..., [0, 1, 3, 5]])
+    assert not r4[..., [2, 4]].any()
+    m = wl.m_random(t.n, seed=3).astype(np.float32)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    H4, H6 = torch.empty_like(mg), torch.empty_like(mg)
+    mt.mt_demag_field(T4, mg, H4)
+    mt.mt_demag_field(T6, mg, H6)
+    torch.cuda.synchronize()
+    h4, h6 = H4.cpu().numpy().reshape(-1, 3), H6.cpu().numpy().reshape(-1, 3)
+    assert _rel(h4, h6) <= 1e-9
+    ref = oracle.demag_field(oracle.Model.from_tiles(t), m.astype(np.float64))
+    assert _rel(h4, ref) <= 1e-6
+
+
+def test_multi_layer_keeps_six_planes(mt, ctx):
+    t = wl.film(20, 5, 2, size=(250e-9, 62.5e-9, 6e-9))
+    T = mt.mt_demag_assemble(mt.mt_tiles_create(ctx, t), "f32")
+    assert T.info()["planes"] == 6

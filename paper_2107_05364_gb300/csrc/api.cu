@@ -531,7 +531,7 @@ mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
   info->rows_per_panel = T->L.TR;
   info->cols_per_chunk = T->L.TC;
   info->layout = T->layout;
-  info->planes = T->layout == MT_LAYOUT_DENSE ? 9 : T->layout == MT_LAYOUT_SPARSE ? 6 : T->L.nplane;
+  info->planes = T->layout == MT_LAYOUT_DENSE ? 9 : T->L.nplane;  // sparse: as its source
   info->bytes = (int64_t)T->bytes;
   info->near_blocks = T->near_count;
   return MT_OK;

@@ -18,9 +18,10 @@
 // entries survives, with its 6 unique entries (dropped ones zero) and its
 // column, in increasing column order.  Row i holds K4 = ptr[i+1] - ptr[i]
 // blocks (its kept count rounded up to 4 with zero blocks of column 0):
-// columns col[ptr[i] + a], and the entries as 6 planes of K4 floats,
-// val[6 ptr[i] + e K4 + a], so that every row starts on a 16-byte boundary
-// and a lane reads 4 blocks with 7 vector loads.
+// columns col[ptr[i] + a], and the entries as np planes of K4 floats,
+// val[np ptr[i] + e K4 + a] (np = 6, or 4 when the source is a single-layer
+// tensor without the xz and yz planes), so that every row starts on a
+// 16-byte boundary and a lane reads 4 blocks with np + 1 vector loads.
 //
 // Product: one warp per (tile row, simulation); the operand is a float4
 // (Ms m, 0) per tile, gathered from L2.  Partial sums are compensated (each
@@ -119,7 +120,7 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_
   const int rr = (int)(i - p * TR);
   const int mult[6] = {1, 2, 2, 1, 2, 1};
   const int64_t o = FILL ? ptr[i] : 0, K4 = FILL ? ptr[i + 1] - o : 0;
-  float *rv = FILL ? val + 6 * o : nullptr;
+  float *rv = FILL ? val + np * o : nullptr;  // np value planes, as the source
   unsigned long long carry = tie_start ? tie_start[i] : 0;
   int64_t at = 0;
   for (int64_t j0 = 0; j0 < n; j0 += 32) {
@@ -164,7 +165,10 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_
       const int64_t a = at + __popc(mask & ((1u << lane) - 1u));
       col[o + a] = (int32_t)j;
 #pragma unroll
-      for (int e = 0; e < 6; ++e) rv[e * K4 + a] = v[e];
+      for (int e = 0; e < 6; ++e) {
+        const int pl = stream_plane(e, np);
+        if (pl >= 0) rv[pl * K4 + a] = v[e];
+      }
     }
     at += __popc(mask);
   }
@@ -173,8 +177,7 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_
   } else {
     for (int64_t a = at + lane; a < K4; a += 32) {
       col[o + a] = 0;
-#pragma unroll
-      for (int e = 0; e < 6; ++e) rv[e * K4 + a] = 0.0f;
+      for (int pl = 0; pl < np; ++pl) rv[pl * K4 + a] = 0.0f;
     }
   }
 }
@@ -210,7 +213,7 @@ template <> struct Vec<4> {
 // H_i = -sum_kept N_ij Ms_j m_j; one warp per (row, simulation), rows of one
 // simulation consecutive; xs = float4 (Ms m, 0) per tile and simulation; each
 // lane takes V consecutive blocks per step (7 vector loads, V gathers)
-template <int V>
+template <int V, int NP>
 __global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
                                              const int32_t *__restrict__ col, const float *__restrict__ val,
                                              const float4 *__restrict__ xs, float *H, const int *active) {
@@ -225,25 +228,34 @@ __global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__
   if (active && !active[b]) return;
   const float4 *xb = xs + (size_t)b * n;
   const int64_t o = ptr[i], K4 = ptr[i + 1] - o;
-  const float *rv = val + 6 * o;
+  const float *rv = val + NP * o;
   const int32_t *rc = col + o;
   float sx = 0, cx = 0, sy = 0, cy = 0, sz = 0, cz = 0;
   for (int64_t a = V * (int64_t)lane; a < K4; a += 32 * V) {
     const VI jj = *reinterpret_cast<const VI *>(rc + a);
-    VF v[6];
+    VF v[NP];
 #pragma unroll
-    for (int e = 0; e < 6; ++e) v[e] = *reinterpret_cast<const VF *>(rv + e * K4 + a);
+    for (int e = 0; e < NP; ++e) v[e] = *reinterpret_cast<const VF *>(rv + e * K4 + a);
     float4 x[V];
 #pragma unroll
     for (int q = 0; q < V; ++q) x[q] = xb[Vec<V>::at(jj, q)];
-    // per block: (v0 v1 v2; v1 v3 v4; v2 v4 v5) (x, y, z)
 #pragma unroll
     for (int q = 0; q < V; ++q) {
-      const float n0 = Vec<V>::at(v[0], q), n1 = Vec<V>::at(v[1], q), n2 = Vec<V>::at(v[2], q);
-      const float n3 = Vec<V>::at(v[3], q), n4 = Vec<V>::at(v[4], q), n5 = Vec<V>::at(v[5], q);
-      sum2_add(sx, cx, fmaf(n0, x[q].x, fmaf(n1, x[q].y, n2 * x[q].z)));
-      sum2_add(sy, cy, fmaf(n1, x[q].x, fmaf(n3, x[q].y, n4 * x[q].z)));
-      sum2_add(sz, cz, fmaf(n2, x[q].x, fmaf(n4, x[q].y, n5 * x[q].z)));
+      if constexpr (NP == 6) {
+        // per block: (v0 v1 v2; v1 v3 v4; v2 v4 v5) (x, y, z)
+        const float n0 = Vec<V>::at(v[0], q), n1 = Vec<V>::at(v[1], q), n2 = Vec<V>::at(v[2], q);
+        const float n3 = Vec<V>::at(v[3], q), n4 = Vec<V>::at(v[4], q), n5 = Vec<V>::at(v[5], q);
+        sum2_add(sx, cx, fmaf(n0, x[q].x, fmaf(n1, x[q].y, n2 * x[q].z)));
+        sum2_add(sy, cy, fmaf(n1, x[q].x, fmaf(n3, x[q].y, n4 * x[q].z)));
+        sum2_add(sz, cz, fmaf(n2, x[q].x, fmaf(n4, x[q].y, n5 * x[q].z)));
+      } else {
+        // single-layer tensor: (v0 v1 0; v1 v2 0; 0 0 v3) (x, y, z)
+        const float n0 = Vec<V>::at(v[0], q), n1 = Vec<V>::at(v[1], q);
+        const float n3 = Vec<V>::at(v[2], q), n5 = Vec<V>::at(v[3], q);
+        sum2_add(sx, cx, fmaf(n0, x[q].x, n1 * x[q].y));
+        sum2_add(sy, cy, fmaf(n1, x[q].x, n3 * x[q].y));
+        sum2_add(sz, cz, __fmul_rn(n5, x[q].z));  // a rounded product, as in the 6-plane form
+      }
     }
   }
   const float hx = warp_sum2(sx, cx), hy = warp_sum2(sy, cy), hz = warp_sum2(sz, cz);
@@ -288,9 +300,15 @@ namespace mt {
 
 void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int *active, cudaStream_t s) {
   const int64_t warps = T->n * (int64_t)B;
-  mt::launch_pdl(k_spmv<kSpmvV>, dim3((unsigned)((warps + 1) / 2)), dim3(64), 0, s, T->n, B,
-                 (const int64_t *)T->d_sp_ptr, (const int32_t *)T->d_sp_col, (const float *)T->d_sp_val,
-                 reinterpret_cast<const float4 *>(xs), H, active);
+  const dim3 grid((unsigned)((warps + 1) / 2));
+  const int64_t *ptr = (const int64_t *)T->d_sp_ptr;
+  const int32_t *col = (const int32_t *)T->d_sp_col;
+  const float *val = (const float *)T->d_sp_val;
+  const float4 *x4 = reinterpret_cast<const float4 *>(xs);
+  if (T->L.nplane == 4)
+    mt::launch_pdl(k_spmv<kSpmvV, 4>, grid, dim3(64), 0, s, T->n, B, ptr, col, val, x4, H, active);
+  else
+    mt::launch_pdl(k_spmv<kSpmvV, 6>, grid, dim3(64), 0, s, T->n, B, ptr, col, val, x4, H, active);
 }
 
 void launch_prep_sparse_x(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
@@ -380,7 +398,8 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   S->n = n;
   S->L = T->L;
   S->sp_blocks = nnzb;
-  S->bytes = sizeof(int64_t) * (n + 1) + (sizeof(int32_t) + 6 * sizeof(float)) * (size_t)std::max<int64_t>(1, nnzb);
+  const int np = T->L.nplane;  // value planes: those the source stores (6, or 4 for a single layer)
+  S->bytes = sizeof(int64_t) * (n + 1) + (sizeof(int32_t) + np * sizeof(float)) * (size_t)std::max<int64_t>(1, nnzb);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->in_use + S->bytes > ctx->budget) {
@@ -394,7 +413,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   }
   cudaError_t e = cudaMalloc(&S->d_sp_ptr, sizeof(int64_t) * (n + 1));
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_col, sizeof(int32_t) * std::max<int64_t>(1, nnzb));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_val, 6 * sizeof(float) * std::max<int64_t>(1, nnzb));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_val, np * sizeof(float) * std::max<int64_t>(1, nnzb));
   if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_ptr, ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     mt::tensor_release(S);
@@ -415,14 +434,17 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   }
   if (kept_elements) {
     // kept elements of the full matrix (off-diagonal entries count twice)
-    std::vector<float> vals(6 * (size_t)std::max<int64_t>(1, nnzb));
-    MT_CUDA(cudaMemcpy(vals.data(), S->d_sp_val, 6 * sizeof(float) * nnzb, cudaMemcpyDeviceToHost));
+    std::vector<float> vals(np * (size_t)std::max<int64_t>(1, nnzb));
+    MT_CUDA(cudaMemcpy(vals.data(), S->d_sp_val, np * sizeof(float) * nnzb, cudaMemcpyDeviceToHost));
     int64_t kept = 0;
     const int mult[6] = {1, 2, 2, 1, 2, 1};
     for (int64_t i = 0; i < n; ++i) {
       const int64_t o = ptr[i], K4 = ptr[i + 1] - o;
       for (int e = 0; e < 6; ++e)
-        for (int64_t a = 0; a < K4; ++a) kept += vals[6 * o + e * K4 + a] != 0.0f ? mult[e] : 0;
+        for (int64_t a = 0; a < K4; ++a) {
+          const int pl = stream_plane(e, np);
+          kept += (pl >= 0 && vals[np * o + pl * K4 + a] != 0.0f) ? mult[e] : 0;
+        }
     }
     *kept_elements = kept;
   }
@@ -439,19 +461,23 @@ mt_status read_rows_sparse(const mt_tensor *T, int64_t i0, int64_t i1, double *o
   MT_CUDA(cudaMemcpy(ptr.data(), T->d_sp_ptr + i0, sizeof(int64_t) * (i1 - i0 + 1), cudaMemcpyDeviceToHost));
   const int64_t a0 = ptr[0], a1 = ptr[i1 - i0];
   std::vector<int32_t> col(std::max<int64_t>(1, a1 - a0));
-  std::vector<float> val(6 * std::max<int64_t>(1, a1 - a0));
+  const int np = T->L.nplane;
+  std::vector<float> val(np * std::max<int64_t>(1, a1 - a0));
   if (a1 > a0) {
     MT_CUDA(cudaMemcpy(col.data(), T->d_sp_col + a0, sizeof(int32_t) * (a1 - a0), cudaMemcpyDeviceToHost));
-    MT_CUDA(cudaMemcpy(val.data(), T->d_sp_val + 6 * a0, 6 * sizeof(float) * (a1 - a0), cudaMemcpyDeviceToHost));
+    MT_CUDA(cudaMemcpy(val.data(), T->d_sp_val + np * a0, np * sizeof(float) * (a1 - a0), cudaMemcpyDeviceToHost));
   }
   std::memset(out, 0, sizeof(double) * 6 * (size_t)(i1 - i0) * n);
   for (int64_t i = i0; i < i1; ++i) {
     const int64_t o = ptr[i - i0], K4 = ptr[i - i0 + 1] - o;
-    const float *rv = val.data() + 6 * (o - a0);
+    const float *rv = val.data() + np * (o - a0);
     for (int64_t a = 0; a < K4; ++a) {
       const int64_t j = col[o - a0 + a];
       // padding blocks are zero and add nothing
-      for (int e = 0; e < 6; ++e) out[((i - i0) * n + j) * 6 + e] += rv[e * K4 + a];
+      for (int e = 0; e < 6; ++e) {
+        const int pl = stream_plane(e, np);
+        if (pl >= 0) out[((i - i0) * n + j) * 6 + e] += rv[pl * K4 + a];
+      }
     }
   }
   return MT_OK;

@@ -137,3 +137,24 @@ def test_threshold_full_size_sampled_rows(mt, ctx):
         full = oracle.six_to_full(blk[None])[0]  # (n, 3, 3)
         ref.append(-np.einsum("jab,jb->a", full, x))
     assert _rel(Hg, np.array(ref)) < 1e-6
+
+
+def test_single_layer_sparse_stores_four_planes(mt, ctx):
+    # a thresholded single-layer tensor keeps the source's 4 value planes
+    # (20 bytes per kept block) and gives the 6-plane sparse tensor's field
+    import torch
+    t = wl.film(40, 10, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    S4, thr4, kept4 = mt.mt_tensor_threshold(mt.mt_demag_assemble(tiles, "f32"), 0.4)
+    S6, thr6, kept6 = mt.mt_tensor_threshold(mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM6), 0.4)
+    assert S4.info()["planes"] == 4 and S6.info()["planes"] == 6
+    assert np.float32(thr4) == np.float32(thr6) and kept4 == kept6
+    assert S4.info()["bytes"] < 0.8 * S6.info()["bytes"]
+    np.testing.assert_array_equal(mt.mt_tensor_read_rows(S4, 0, t.n), mt.mt_tensor_read_rows(S6, 0, t.n))
+    m = wl.m_random(t.n, seed=5).astype(np.float32)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    H4, H6 = torch.full_like(mg, float("nan")), torch.full_like(mg, float("nan"))
+    mt.mt_demag_field(S4, mg, H4)
+    mt.mt_demag_field(S6, mg, H6)
+    torch.cuda.synchronize()
+    assert torch.equal(H4, H6)

@@ -329,3 +329,21 @@ def test_scaled_geometry_tensor_and_exchange():
     H1 = oracle.exchange_field(md1, m)
     H2 = oracle.exchange_field(md2, m)
     np.testing.assert_allclose(H2, H1 / lam ** 2, rtol=1e-12, atol=1e-12 * np.abs(H1).max())
+
+
+def test_single_layer_xz_yz_vanish_by_mirror_symmetry():
+    # every tile in one layer (same centre z and z edge): the field point lies
+    # in each source's mid-plane and N_xz, N_yz (odd in the z offset) vanish;
+    # on a graded in-plane grid at an arbitrary height they are FP64
+    # round-off (<= 1e-12), while a second layer makes them O(1e-2)
+    rng = np.random.default_rng(7)
+    xf = np.concatenate([[0.0], np.cumsum(rng.uniform(2e-9, 8e-9, 9))])
+    yf = np.concatenate([[0.0], np.cumsum(rng.uniform(2e-9, 8e-9, 5))])
+    for z0 in (0.0, 17.3e-9):
+        t = wl.grid_tiles(xf, yf, np.array([z0, z0 + 3e-9]), wl.SP4_MS, wl.SP4_AEX, 0.0)
+        N = oracle.demag_tensor(t.centre, t.edge)
+        assert np.abs(N[..., [2, 4]]).max() <= 1e-12
+        assert np.abs(N[..., [0, 1, 3, 5]]).max() > 0.1  # the in-plane part is not small
+    two = wl.grid_tiles(xf, yf, np.array([0.0, 3e-9, 6e-9]), wl.SP4_MS, wl.SP4_AEX, 0.0)
+    N2 = oracle.demag_tensor(two.centre, two.edge)
+    assert np.abs(N2[..., [2, 4]]).max() > 1e-3

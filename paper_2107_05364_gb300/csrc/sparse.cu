@@ -382,7 +382,8 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   DevTemp<int> cnt_rows;
   MT_CUDA(cnt_rows.alloc(n));
   int *d_cnt = cnt_rows.p;
-  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr, nullptr);
+  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr,
+                                     nullptr);
   MT_CUDA(cudaGetLastError());
   std::vector<int> cnt(n);
   MT_CUDA(cudaMemcpy(cnt.data(), d_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
@@ -419,8 +420,8 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     mt::tensor_release(S);
     return mt::cuda_fail(e, "mt_tensor_threshold allocation", __FILE__, __LINE__);
   }
-  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, nullptr, S->d_sp_ptr, S->d_sp_col,
-                                    S->d_sp_val);
+  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, nullptr, S->d_sp_ptr,
+                                    S->d_sp_col, S->d_sp_val);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {

@@ -512,15 +512,18 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
 // ---------------------------------------------------------------------------
 // Small tile sets: a whole run in one cooperative kernel
 // ---------------------------------------------------------------------------
-// Below about a thousand tiles the FP32 tensor is a few MB, a right-hand
-// side is a few microseconds of work, and the step graph's 13 dependent
-// launches per attempt are what the step costs.  Here one CTA per SM keeps
-// its rows of the tensor in shared memory for the whole call, the stage
+// Below about two thousand tiles the FP32 tensor is a few tens of MB, a
+// right-hand side is a few microseconds of work, and the step graph's 13
+// dependent launches per attempt are what the step costs.  Here one CTA per
+// SM keeps its rows of the tensor in shared memory for the whole call (or,
+// when they do not fit, reads them from the L2-resident tensor), the stage
 // inputs of all tiles pass through L2 between grid-wide barriers, and every
 // CTA takes the step-control decisions itself from the same per-CTA partial
 // sums reduced in the same fixed order (so all CTAs agree bit for bit): per
-// attempt 6 barriers before the 6 right-hand sides and one for the error
-// norm, no launches.  The arithmetic of each stage is the graph path's.
+// attempt one barrier before each of the right-hand sides 3..7 and one for
+// the error norm (the stage-2 input every CTA forms for all tiles itself),
+// no launches.  The stage arithmetic is the graph path's except that the
+// error norm and <m> are summed over rows and CTAs in another order.
 constexpr int kSmallThreads = 256;
 constexpr int kSmallWarps = kSmallThreads / 32;
 

@@ -37,7 +37,7 @@ struct MvCfg<MT_F32> {
   using T = float;
   using Acc = float;
   static constexpr int TR = 16, TC = 128, NPLANE = 6, VEC = 4, W = 4, STAGES = 4;
-  static constexpr bool SCALED = false, SPLIT = false, PLANAR = false;
+  static constexpr bool SCALED = false, PLANAR = false;
 };
 template <>
 struct MvCfg<kF32Planar> {
@@ -47,28 +47,28 @@ struct MvCfg<kF32Planar> {
   // chunks) timed faster alone (0.234 against 0.248 ms at n = 10,000) but
   // slower inside the step graph (1.450 against 1.397 ms per attempt)
   static constexpr int TR = 16, TC = 128, NPLANE = 4, VEC = 4, W = 4, STAGES = 6;
-  static constexpr bool SCALED = false, SPLIT = false, PLANAR = true;
+  static constexpr bool SCALED = false, PLANAR = true;
 };
 template <>
 struct MvCfg<MT_F64> {
   using T = double;
   using Acc = double;
   static constexpr int TR = 16, TC = 64, NPLANE = 6, VEC = 2, W = 4, STAGES = 4;
-  static constexpr bool SCALED = false, SPLIT = false, PLANAR = false;
+  static constexpr bool SCALED = false, PLANAR = false;
 };
 template <>
 struct MvCfg<MT_BF16_SCALED> {
   using T = __nv_bfloat16;
   using Acc = float;
   static constexpr int TR = 16, TC = 256, NPLANE = 6, VEC = 8, W = 4, STAGES = 4;
-  static constexpr bool SCALED = true, SPLIT = false, PLANAR = false;
+  static constexpr bool SCALED = true, PLANAR = false;
 };
 template <>
 struct MvCfg<MT_BF16_SPLIT> {
   using T = __nv_bfloat16;
   using Acc = float;
   static constexpr int TR = 8, TC = 256, NPLANE = 12, VEC = 8, W = 4, STAGES = 4;
-  static constexpr bool SCALED = false, SPLIT = true, PLANAR = false;
+  static constexpr bool SCALED = false, PLANAR = false;
 };
 
 template <int PREC, int SB>

@@ -380,8 +380,11 @@ __global__ void k_assemble(AsmArgs A) {
         }
         __nv_bfloat16 *D = (__nv_bfloat16 *)A.data;
 #pragma unroll
-        for (int e = 0; e < 6; ++e)
-          D[layout_index(i, j, e, A.TR, A.TC, 6, A.Q)] = __double2bfloat16(ldexp(N6[e], -s));
+        for (int e = 0; e < 6; ++e) {
+          const int pl = stream_plane(e, A.nplane);
+          if (pl >= 0) D[layout_index(i, j, pl, A.TR, A.TC, A.nplane, A.Q)] = __double2bfloat16(ldexp(N6[e], -s));
+          else if (!(fabs(N6[e]) <= kPlanarTol)) *A.planar_bad = 1;
+        }
         A.scale[scale_index(i, j, A.TR, A.TC, A.Q)] = (int8_t)s;
       } break;
       case MT_BF16_SPLIT: {
@@ -457,10 +460,13 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
         const int pl = stream_plane(e, nplane);
         v = pl < 0 ? 0.0 : ((const float *)data)[layout_index(i, j, pl, TR, TC, nplane, Q)];
       } break;
-      case MT_BF16_SCALED:
-        v = ldexp((double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, e, TR, TC, 6, Q)]),
-                  (int)scale[scale_index(i, j, TR, TC, Q)]);
-        break;
+      case MT_BF16_SCALED: {
+        const int pl = stream_plane(e, nplane);
+        v = pl < 0 ? 0.0
+                   : ldexp((double)__bfloat162float(
+                               ((const __nv_bfloat16 *)data)[layout_index(i, j, pl, TR, TC, nplane, Q)]),
+                           (int)scale[scale_index(i, j, TR, TC, Q)]);
+      } break;
       case MT_BF16_SPLIT:
         v = (double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, e, TR, TC, 12, Q)]) +
             (double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, 6 + e, TR, TC, 12, Q)]);
@@ -591,10 +597,10 @@ mt_status assemble(mt_tensor *T) {
     // an xz or yz entry of the single-layer set is not round-off: store all
     // 6 planes after all (within the budget reserved for them)
     mt_ctx *ctx = t->ctx;
-    layout_for(MT_F32, &T->L);
+    layout_for(T->prec, &T->L);
     T->L.P = (n + T->L.TR - 1) / T->L.TR;
     T->L.Q = (n + T->L.TC - 1) / T->L.TC;
-    const size_t bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
+    const size_t bytes = (size_t)T->L.P * T->L.Q * (T->L.chunk_bytes() + T->L.scale_bytes_per_chunk);
     {
       std::lock_guard<std::mutex> lk(ctx->mu);
       MT_CHECK(ctx->in_use - T->bytes + bytes <= ctx->budget, MT_ENOMEM,
@@ -602,10 +608,11 @@ mt_status assemble(mt_tensor *T) {
       ctx->in_use += bytes - T->bytes;
       T->bytes = bytes;
     }
+    const size_t data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
     MT_CUDA(cudaFree(T->d_data));
     T->d_data = nullptr;
-    MT_CUDA(cudaMalloc(&T->d_data, bytes));
-    MT_CUDA(cudaMemset(T->d_data, 0, bytes));
+    MT_CUDA(cudaMalloc(&T->d_data, data_bytes));
+    MT_CUDA(cudaMemset(T->d_data, 0, data_bytes));
     A.data = T->d_data;
     A.TR = T->L.TR;
     A.TC = T->L.TC;

@@ -26,9 +26,11 @@
 
 namespace {
 
-// FP32 tensor of a single-layer tile set: the xz and yz planes are not
-// stored (they vanish by mirror symmetry), planes xx, xy, yy, zz
+// FP32 / scaled-BF16 tensors of a single-layer tile set: the xz and yz
+// planes are not stored (they vanish by mirror symmetry), planes xx, xy, yy,
+// zz
 constexpr int kF32Planar = 4;
+constexpr int kBF16Planar = 5;
 
 template <int PREC>
 struct MvCfg;
@@ -62,6 +64,13 @@ struct MvCfg<MT_BF16_SCALED> {
   using Acc = float;
   static constexpr int TR = 16, TC = 256, NPLANE = 6, VEC = 8, W = 4, STAGES = 4;
   static constexpr bool SCALED = true, PLANAR = false;
+};
+template <>
+struct MvCfg<kBF16Planar> {
+  using T = __nv_bfloat16;
+  using Acc = float;
+  static constexpr int TR = 16, TC = 256, NPLANE = 4, VEC = 8, W = 4, STAGES = 5;
+  static constexpr bool SCALED = true, PLANAR = true;
 };
 template <>
 struct MvCfg<MT_BF16_SPLIT> {
@@ -100,7 +109,7 @@ __device__ __forceinline__ void load_vals(const unsigned char *stage, int plane,
   } else if constexpr (PREC == MT_F64) {
     const double2 a = reinterpret_cast<const double2 *>(stage)[(plane * C::TR + row) * (C::TC / 2) + lane];
     v[0] = a.x; v[1] = a.y;
-  } else if constexpr (PREC == MT_BF16_SCALED) {
+  } else if constexpr (PREC == MT_BF16_SCALED || PREC == kBF16Planar) {
     const uint4 a = reinterpret_cast<const uint4 *>(stage)[(plane * C::TR + row) * (C::TC / 8) + lane];
     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&a);
 #pragma unroll
@@ -351,6 +360,19 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
           load_vals<PREC>(st, 1, row, lane, nxy);
           load_vals<PREC>(st, 2, row, lane, nyy);
           load_vals<PREC>(st, 3, row, lane, nzz);
+          if constexpr (C::SCALED) {
+            // per-block power-of-two scale: value = stored * 2^s
+            const uint2 sc = reinterpret_cast<const uint2 *>(st + S::DATA_BYTES)[row * (C::TC / 8) + lane];
+            const int8_t *e8 = reinterpret_cast<const int8_t *>(&sc);
+#pragma unroll
+            for (int v = 0; v < C::VEC; ++v) {
+              const float f = __int_as_float(((int)e8[v] + 127) << 23);
+              nxx[v] *= f;
+              nxy[v] *= f;
+              nyy[v] *= f;
+              nzz[v] *= f;
+            }
+          }
 #pragma unroll
           for (int m = 0; m < SB; ++m) {
             Acc sx = 0, sy = 0, sz = 0;
@@ -619,7 +641,7 @@ template <int PREC>
 cudaError_t prepare_mv() {
   cudaError_t e;
   if ((e = prepare_mv_one<PREC, 1>()) != cudaSuccess || (e = prepare_mv_one<PREC, 2>()) != cudaSuccess) return e;
-  if constexpr (PREC == MT_BF16_SCALED) return cudaSuccess;
+  if constexpr (PREC == MT_BF16_SCALED || PREC == kBF16Planar) return cudaSuccess;
   else return prepare_mv_one<PREC, 4>();
 }
 
@@ -627,7 +649,7 @@ cudaError_t prepare_mv() {
 // tensor, whose 8-wide rows with 4 operands spill registers: measured 0.56 ms
 // for 4 simulations at n = 10,000 against 0.21 ms for one)
 inline int mv_group(int B, int prec) {
-  const int cap = prec == MT_BF16_SCALED ? 2 : 4;
+  const int cap = (prec == MT_BF16_SCALED || prec == kBF16Planar) ? 2 : 4;
   return B <= 1 ? 1 : (B == 2 || cap == 2) ? 2 : 4;
 }
 
@@ -663,7 +685,7 @@ void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, i
     case 1: launch_mv_sb<PREC, 1>(A, T->L.P, T->L.Q, cap, s); break;
     case 2: launch_mv_sb<PREC, 2>(A, T->L.P, T->L.Q, cap, s); break;
     default:
-      if constexpr (PREC != MT_BF16_SCALED) launch_mv_sb<PREC, 4>(A, T->L.P, T->L.Q, cap, s);
+      if constexpr (PREC != MT_BF16_SCALED && PREC != kBF16Planar) launch_mv_sb<PREC, 4>(A, T->L.P, T->L.Q, cap, s);
       break;
   }
 }
@@ -678,16 +700,26 @@ cudaError_t matvec_prepare() {
   cudaError_t e;
   if ((e = prepare_mv<MT_F32>()) != cudaSuccess) return e;
   if ((e = prepare_mv<kF32Planar>()) != cudaSuccess) return e;
+  if ((e = prepare_mv<kBF16Planar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<MT_F64>()) != cudaSuccess) return e;
   if ((e = prepare_mv<MT_BF16_SCALED>()) != cudaSuccess) return e;
   return prepare_mv<MT_BF16_SPLIT>();
 }
 
-void layout_for_planar(mt_layout *L) {
-  L->TR = MvCfg<kF32Planar>::TR;
-  L->TC = MvCfg<kF32Planar>::TC;
-  L->nplane = MvCfg<kF32Planar>::NPLANE;
-  L->elem_bytes = 4;
+void layout_for_planar(int prec, mt_layout *L) {
+  if (prec == MT_BF16_SCALED) {
+    L->TR = MvCfg<kBF16Planar>::TR;
+    L->TC = MvCfg<kBF16Planar>::TC;
+    L->nplane = MvCfg<kBF16Planar>::NPLANE;
+    L->elem_bytes = 2;
+    L->scale_bytes_per_chunk = (int64_t)L->TR * L->TC;
+  } else {
+    L->TR = MvCfg<kF32Planar>::TR;
+    L->TC = MvCfg<kF32Planar>::TC;
+    L->nplane = MvCfg<kF32Planar>::NPLANE;
+    L->elem_bytes = 4;
+    L->scale_bytes_per_chunk = 0;
+  }
 }
 
 void layout_for(int prec, mt_layout *L) {
@@ -743,7 +775,10 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
       else launch_mv<MT_F32>(T, xs, B, H, part, count, active, status, s);
       break;
     case MT_F64: launch_mv<MT_F64>(T, xs, B, H, part, count, active, status, s); break;
-    case MT_BF16_SCALED: launch_mv<MT_BF16_SCALED>(T, xs, B, H, part, count, active, status, s); break;
+    case MT_BF16_SCALED:
+      if (T->L.nplane == 4) launch_mv<kBF16Planar>(T, xs, B, H, part, count, active, status, s);
+      else launch_mv<MT_BF16_SCALED>(T, xs, B, H, part, count, active, status, s);
+      break;
     case MT_BF16_SPLIT: launch_mv<MT_BF16_SPLIT>(T, xs, B, H, part, count, active, status, s); break;
   }
 }

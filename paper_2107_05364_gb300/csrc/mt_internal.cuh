@@ -232,7 +232,7 @@ int matvec_grid(const mt_tensor *T);
 cudaError_t matvec_prepare();
 // Panel/chunk shape of the storage for a precision (P, Q left to the caller).
 void layout_for(int prec, mt_layout *L);
-void layout_for_planar(mt_layout *L);  // FP32, single-layer tile set: 4 entry planes
+void layout_for_planar(int prec, mt_layout *L);  // FP32 / scaled BF16, single-layer tile set: 4 entry planes
 // floats of the padded, Ms-scaled operand of one simulation: Q * 3 * TC
 int64_t xs_floats(const mt_tensor *T);
 // bytes of the partial-sum workspace and of the panel counters for B sims

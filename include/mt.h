@@ -146,8 +146,8 @@ typedef struct {
   int32_t prec;        /* mt_prec                                             */
   int32_t rows_per_panel, cols_per_chunk; /* tile-blocked layout (stream)     */
   int32_t layout;      /* mt_layout_kind                                      */
-  int32_t planes;      /* stored values per 3x3 block: 6, 4 (single-layer     */
-                       /* FP32 / BF16 streaming), 12 (split), 9 (dense)       */
+  int32_t planes;      /* stored values per 3x3 block: 6 (4 single-layer),    */
+                       /* split 12 (8 single-layer), dense 9                  */
   int64_t bytes;       /* device bytes of the stored tensor                   */
   int64_t near_blocks; /* FP64 near-field blocks kept apart (0 if none)       */
 } mt_tensor_info;
@@ -224,9 +224,10 @@ MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **ou
 /* Single-layer tile sets.  When every cuboid tile has the same centre z and
  * the same z edge, each tile's field point lies in the mid-plane of every
  * other tile, and the xz and yz entries of every block vanish by mirror
- * symmetry (they are odd in the z offset).  An FP32 or scaled-BF16 streaming
- * tensor of such a set stores the 4 entry planes xx, xy, yy, zz (FP32: 16
- * bytes per block instead of 24; BF16: 8 + the scale byte instead of 12 + 1),
+ * symmetry (they are odd in the z offset).  A streaming tensor of such a set
+ * (FP32, scaled BF16 or split BF16) stores the 4 entry planes xx, xy, yy, zz
+ * (FP32 and split: 16 bytes per block instead of 24; BF16: 8 + the scale
+ * byte instead of 12 + 1),
  * provided that every assembled |N_xz|, |N_yz| is at most 1e-12
  * (their FP64 round-off; otherwise all 6 planes are stored).  Products,
  * row reads and thresholding treat the missing entries as zeros.

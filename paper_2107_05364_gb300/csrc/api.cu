@@ -476,7 +476,7 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
     mt::layout_for(prec, &T->L);
     // single-layer cuboid set (every tile: the same centre z and z edge): the
     // FP32 tensor's xz and yz entries vanish; 4 entry planes
-    if (allow_planar && (prec == MT_F32 || prec == MT_BF16_SCALED) && tiles->kind == MT_TILE_CUBOID) {
+    if (allow_planar && prec != MT_F64 && tiles->kind == MT_TILE_CUBOID) {
       bool planar = true;
       for (int64_t i = 1; i < tiles->n && planar; ++i)
         planar = tiles->centre[3 * i + 2] == tiles->centre[2] && tiles->edge[3 * i + 2] == tiles->edge[2];

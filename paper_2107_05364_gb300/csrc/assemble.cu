@@ -390,11 +390,17 @@ __global__ void k_assemble(AsmArgs A) {
       case MT_BF16_SPLIT: {
         __nv_bfloat16 *D = (__nv_bfloat16 *)A.data;
 #pragma unroll
+        const int half = A.nplane / 2;  // hi planes, then as many lo planes
         for (int e = 0; e < 6; ++e) {
+          const int pl = stream_plane(e, half);
+          if (pl < 0) {
+            if (!(fabs(N6[e]) <= kPlanarTol)) *A.planar_bad = 1;
+            continue;
+          }
           const __nv_bfloat16 hi = __double2bfloat16(N6[e]);
           const __nv_bfloat16 lo = __double2bfloat16(N6[e] - (double)__bfloat162float(hi));
-          D[layout_index(i, j, e, A.TR, A.TC, 12, A.Q)] = hi;
-          D[layout_index(i, j, 6 + e, A.TR, A.TC, 12, A.Q)] = lo;
+          D[layout_index(i, j, pl, A.TR, A.TC, A.nplane, A.Q)] = hi;
+          D[layout_index(i, j, half + pl, A.TR, A.TC, A.nplane, A.Q)] = lo;
         }
       } break;
     }
@@ -467,10 +473,13 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
                                ((const __nv_bfloat16 *)data)[layout_index(i, j, pl, TR, TC, nplane, Q)]),
                            (int)scale[scale_index(i, j, TR, TC, Q)]);
       } break;
-      case MT_BF16_SPLIT:
-        v = (double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, e, TR, TC, 12, Q)]) +
-            (double)__bfloat162float(((const __nv_bfloat16 *)data)[layout_index(i, j, 6 + e, TR, TC, 12, Q)]);
-        break;
+      case MT_BF16_SPLIT: {
+        const int half = nplane / 2, pl = stream_plane(e, half);
+        const __nv_bfloat16 *d = (const __nv_bfloat16 *)data;
+        v = pl < 0 ? 0.0
+                   : (double)__bfloat162float(d[layout_index(i, j, pl, TR, TC, nplane, Q)]) +
+                         (double)__bfloat162float(d[layout_index(i, j, half + pl, TR, TC, nplane, Q)]);
+      } break;
     }
     out[t * 6 + e] = v;
   }

@@ -31,6 +31,7 @@ namespace {
 // zz
 constexpr int kF32Planar = 4;
 constexpr int kBF16Planar = 5;
+constexpr int kSplitPlanar = 6;  // hi planes xx, xy, yy, zz, then the lo planes
 
 template <int PREC>
 struct MvCfg;
@@ -71,6 +72,13 @@ struct MvCfg<kBF16Planar> {
   using Acc = float;
   static constexpr int TR = 16, TC = 256, NPLANE = 4, VEC = 8, W = 4, STAGES = 5;
   static constexpr bool SCALED = true, PLANAR = true;
+};
+template <>
+struct MvCfg<kSplitPlanar> {
+  using T = __nv_bfloat16;
+  using Acc = float;
+  static constexpr int TR = 8, TC = 256, NPLANE = 8, VEC = 8, W = 4, STAGES = 6;
+  static constexpr bool SCALED = false, PLANAR = true;
 };
 template <>
 struct MvCfg<MT_BF16_SPLIT> {
@@ -118,9 +126,10 @@ __device__ __forceinline__ void load_vals(const unsigned char *stage, int plane,
       v[2 * k] = f.x;
       v[2 * k + 1] = f.y;
     }
-  } else {  // split: hi plane `plane`, lo plane `plane + 6`
+  } else {  // split: hi plane `plane`, lo plane `plane + NPLANE / 2`
     const uint4 a = reinterpret_cast<const uint4 *>(stage)[(plane * C::TR + row) * (C::TC / 8) + lane];
-    const uint4 b = reinterpret_cast<const uint4 *>(stage)[((plane + 6) * C::TR + row) * (C::TC / 8) + lane];
+    const uint4 b =
+        reinterpret_cast<const uint4 *>(stage)[((plane + C::NPLANE / 2) * C::TR + row) * (C::TC / 8) + lane];
     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&a);
     const __nv_bfloat162 *l = reinterpret_cast<const __nv_bfloat162 *>(&b);
 #pragma unroll
@@ -701,13 +710,20 @@ cudaError_t matvec_prepare() {
   if ((e = prepare_mv<MT_F32>()) != cudaSuccess) return e;
   if ((e = prepare_mv<kF32Planar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<kBF16Planar>()) != cudaSuccess) return e;
+  if ((e = prepare_mv<kSplitPlanar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<MT_F64>()) != cudaSuccess) return e;
   if ((e = prepare_mv<MT_BF16_SCALED>()) != cudaSuccess) return e;
   return prepare_mv<MT_BF16_SPLIT>();
 }
 
 void layout_for_planar(int prec, mt_layout *L) {
-  if (prec == MT_BF16_SCALED) {
+  if (prec == MT_BF16_SPLIT) {
+    L->TR = MvCfg<kSplitPlanar>::TR;
+    L->TC = MvCfg<kSplitPlanar>::TC;
+    L->nplane = MvCfg<kSplitPlanar>::NPLANE;
+    L->elem_bytes = 2;
+    L->scale_bytes_per_chunk = 0;
+  } else if (prec == MT_BF16_SCALED) {
     L->TR = MvCfg<kBF16Planar>::TR;
     L->TC = MvCfg<kBF16Planar>::TC;
     L->nplane = MvCfg<kBF16Planar>::NPLANE;
@@ -779,7 +795,10 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
       if (T->L.nplane == 4) launch_mv<kBF16Planar>(T, xs, B, H, part, count, active, status, s);
       else launch_mv<MT_BF16_SCALED>(T, xs, B, H, part, count, active, status, s);
       break;
-    case MT_BF16_SPLIT: launch_mv<MT_BF16_SPLIT>(T, xs, B, H, part, count, active, status, s); break;
+    case MT_BF16_SPLIT:
+      if (T->L.nplane == 8) launch_mv<kSplitPlanar>(T, xs, B, H, part, count, active, status, s);
+      else launch_mv<MT_BF16_SPLIT>(T, xs, B, H, part, count, active, status, s);
+      break;
   }
 }
 

@@ -182,8 +182,9 @@ struct mt_tensor {
 };
 
 // Plane of entry e (xx, xy, xz, yy, yz, zz) in a streaming layout of
-// nplane planes: the identity for 6 (and 12: hi planes), -1 for the xz and
-// yz entries of a single-layer FP32 tensor (planes xx, xy, yy, zz).
+// nplane planes: the identity for 6, -1 for the xz and yz entries of a
+// single-layer tensor (planes xx, xy, yy, zz).  The split precision holds
+// two such sets (hi, then lo): call it with half its planes.
 __host__ __device__ __forceinline__ int stream_plane(int e, int nplane) {
   if (nplane != 4) return e;
   return e < 2 ? e : e == 3 ? 2 : e == 5 ? 3 : -1;
@@ -232,7 +233,7 @@ int matvec_grid(const mt_tensor *T);
 cudaError_t matvec_prepare();
 // Panel/chunk shape of the storage for a precision (P, Q left to the caller).
 void layout_for(int prec, mt_layout *L);
-void layout_for_planar(int prec, mt_layout *L);  // FP32 / scaled BF16, single-layer tile set: 4 entry planes
+void layout_for_planar(int prec, mt_layout *L);  // single-layer tile set: 4 entry planes (split: 4 hi + 4 lo)
 // floats of the padded, Ms-scaled operand of one simulation: Q * 3 * TC
 int64_t xs_floats(const mt_tensor *T);
 // bytes of the partial-sum workspace and of the panel counters for B sims

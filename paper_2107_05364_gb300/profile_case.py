@@ -8,6 +8,8 @@
                   per attempt) or persistent (one cooperative kernel per call)
 --what assemble : tensor assembly only
 --layout dense  : 9-entry BF16 / split tensor for the batched tensor-core product
+--layout stream6: the streaming layout with all 6 entry planes even for a
+                  single-layer film (which otherwise stores 4)
 --threshold F   : drop the smallest fraction F of the elements (Sec. 4.3.1) and
                   apply the sparse tensor (FP32, streaming layout first)
 Prints the average time per call measured with CUDA events (not meaningful
@@ -30,7 +32,7 @@ def main():
     ap.add_argument("--what", default="field", choices=["field", "step", "assemble"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--B", type=int, default=1)
-    ap.add_argument("--layout", default="stream", choices=["stream", "dense"])
+    ap.add_argument("--layout", default="stream", choices=["stream", "dense", "stream6"])
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--path", default="auto", choices=["auto", "graph", "persistent"])
     a = ap.parse_args()
@@ -54,7 +56,8 @@ def main():
         torch.cuda.synchronize()
         print("assemble n=%d: %.3f ms" % (t.n, e0.elapsed_time(e1) / a.reps))
         return
-    T = mt.mt_demag_assemble_ex(tiles, a.prec, mt.MT_LAYOUT_DENSE if a.layout == "dense" else mt.MT_LAYOUT_STREAM)
+    layout = {"stream": mt.MT_LAYOUT_STREAM, "dense": mt.MT_LAYOUT_DENSE, "stream6": mt.MT_LAYOUT_STREAM6}[a.layout]
+    T = mt.mt_demag_assemble_ex(tiles, a.prec, layout)
     if a.threshold is not None:
         S, thr, kept = mt.mt_tensor_threshold(T, a.threshold)
         T.close()

@@ -273,6 +273,37 @@ def test_against_scipy_nonlinear():
 # ---------------------------------------------------------------------------
 # relaxation (Brown's equation, Eq. 2)
 # ---------------------------------------------------------------------------
+def test_mean_m_is_volume_weighted():
+    # <m> of the traces is the volume average (1/V) sum_i V_i m_i.  Two tiles
+    # of volumes V and 3V magnetised along x and y: <m> = (1/4, 3/4, 0) (an
+    # unweighted mean would give (1/2, 1/2, 0)).  With gamma = 0 the equation
+    # of motion is dm/dt = 0, so the integrator's recorded <m> is that of m0.
+    h = 2e-9
+    centre = np.array([[0.0, 0.0, 0.0], [3.0 * h, 0.0, 0.0]])
+    edge = np.array([[h, h, h], [3.0 * h, h, h]])
+    md = oracle.Model(centre, edge, wl.SP4_MS, wl.SP4_AEX, 0.0, (0, 0, 1))
+    m0 = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    p = oracle.llg_params(gamma=0.0, alpha=0.0)
+    st, m, mavg, _ = oracle.integrate(md, m0, p, oracle.ode_opts(fixed_h=1e-13), 0.0, 3e-13, 3)
+    assert st == oracle.OK
+    np.testing.assert_array_equal(m, m0)
+    np.testing.assert_allclose(mavg, np.tile([0.25, 0.75, 0.0], (3, 1)), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(md.mean_m(m0), [0.25, 0.75, 0.0], rtol=0, atol=1e-15)
+    # a graded film: the same against a sum written out tile by tile
+    t = wl.graded_film(9, 5, 3, size=(60e-9, 30e-9, 9e-9), seed=6)
+    mr = wl.m_random(t.n, seed=4)
+    num, den = np.zeros(3), 0.0
+    for i in range(t.n):
+        V = t.edge[i, 0] * t.edge[i, 1] * t.edge[i, 2]
+        num += V * mr[i]
+        den += V
+    mdg = oracle.Model.from_tiles(t)
+    st, _, mavg, _ = oracle.integrate(mdg, mr, p, oracle.ode_opts(fixed_h=1e-13), 0.0, 1e-13, 1)
+    assert st == oracle.OK
+    np.testing.assert_allclose(mavg[0], num / den, rtol=0, atol=1e-14)
+    assert np.abs(mavg[0] - mr.mean(0)).max() > 1e-3  # the grading matters here
+
+
 def test_relax_reaches_equilibrium():
     t = wl.film(10, 3, 1, size=(100e-9, 30e-9, 3e-9))
     md = oracle.Model.from_tiles(t)

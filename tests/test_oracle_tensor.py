@@ -252,6 +252,27 @@ def test_overlap_detection():
     assert oracle.check_tiles(c, t.edge) == oracle.EOVERLAP
 
 
+def test_centre_on_another_tile_surface_is_rejected():
+    # The closed form is singular where a field point lies on a source tile's
+    # surface (ln(W + R) with R = |W| on a face, and atan(./0) on its edges),
+    # so a tile centre in or on another tile is invalid even where the two
+    # volumes do not overlap measurably.  A tile too thin to overlap within
+    # the relative tolerance 1e-12 (edge 1e-22 m against 1e-8 m), whose
+    # centre lies on the +x face, on an edge, or at a corner of a 10 nm cube,
+    # tests that rule alone; the same thin tile just outside the face is valid.
+    h, eps = 10e-9, 1e-22
+    edge = np.array([[h, h, h], [eps, eps, eps]])
+    for where in ([0.5 * h, 0.0, 0.0], [0.5 * h, 0.5 * h, 0.0], [0.5 * h, -0.5 * h, 0.5 * h],
+                  [0.5 * h, 0.2 * h, -0.3 * h]):
+        c = np.array([[0.0, 0.0, 0.0], where])
+        assert oracle.check_tiles(c, edge) == oracle.EOVERLAP, where
+    c = np.array([[0.0, 0.0, 0.0], [0.5 * h * (1 + 1e-6), 0.0, 0.0]])
+    assert oracle.check_tiles(c, edge) == oracle.OK
+    # face-adjacent tiles of a grid touch without either centre on the other
+    t = wl.graded_film(5, 4, 2, size=(40e-9, 30e-9, 6e-9), seed=4)
+    assert oracle.check_tiles(t.centre, t.edge) == oracle.OK
+
+
 def test_threshold_drops_the_smallest_fraction():
     # Sec. 4.3.1: a threshold f sets the fraction f of the nonzero tensor
     # elements with the smallest magnitude to zero -- checked on the explicit

@@ -487,7 +487,8 @@ MT_API mt_status mt_selftest_wait_timeout(mt_ctx *ctx, double limit_s);
 MT_API mt_status mt_selftest_grid_barrier_timeout(mt_ctx *ctx);
 
 /* ---------------------------------------------------------------------- */
-/* request serving: relax jobs on many geometries, continuously batched     */
+/* request serving: relax and field-sweep jobs on many geometries,          */
+/* continuously batched                                                    */
 /* ---------------------------------------------------------------------- */
 /* A server owns a worker thread that runs every job on the device.  For each
  * geometry with work it keeps the assembled tensor resident together with
@@ -498,8 +499,17 @@ MT_API mt_status mt_selftest_grid_barrier_timeout(mt_ctx *ctx);
  * the device.  Residency is admitted by device footprint (tensor + batch
  * state) against hbm_budget_bytes; idle engines are evicted least recently
  * used.  A relax job integrates its own simulation until
- * max_i |m_i x H_eff,i| / Ms_i < tol (Eq. 2) or its time cap. */
+ * max_i |m_i x H_eff,i| / Ms_i < tol (Eq. 2) or its time cap.  A sweep job
+ * is the field loop of Sec. 4.1 as one request: its simulation is relaxed
+ * at each applied field of its schedule in turn (tolerance tol, time cap
+ * t_max per value; reaching the cap is not an error), the state carried
+ * over; the job keeps <m> and the torque at the end of every value. */
 typedef struct mt_server mt_server;
+
+typedef enum {
+  MT_JOB_RELAX = 0,  /* relax m0 at the applied field Ha                     */
+  MT_JOB_SWEEP = 1   /* relax at fields[0], fields[1], ... in turn            */
+} mt_job_kind;
 
 typedef struct {
   size_t hbm_budget_bytes;  /* tensors + batch state (0: the context budget) */
@@ -511,27 +521,37 @@ typedef struct {
   mt_ode_opts ode;          /* integrator options; max_steps caps each job  */
   int32_t replays_per_poll; /* Runge-Kutta attempts between completion      */
                             /* checks (0: 16)                               */
-  int32_t pad;
+  int32_t max_running;      /* jobs running at once over all geometries     */
+                            /* (0: no limit beyond the slots); with a limit */
+                            /* jobs start strictly in arrival order (1 and  */
+                            /* max_batch 1: one job at a time, FIFO)        */
 } mt_server_opts;
 
 typedef struct {
   int32_t geometry;         /* id from mt_server_add_geometry               */
-  int32_t pad;
+  int32_t kind;             /* mt_job_kind (0: MT_JOB_RELAX)                */
   double alpha;             /* damping of this job                          */
-  double Ha[3];             /* applied field, A/m                           */
+  double Ha[3];             /* relax: applied field, A/m (sweep: unused)    */
   const float *m0;          /* HOST, 3n floats, copied by mt_server_submit  */
   double tol;               /* torque tolerance (> 0)                       */
-  double t_max;             /* simulated-time cap, s (> 0)                  */
+  double t_max;             /* simulated-time cap, s (> 0); sweep: per value */
+  int64_t n_fields;         /* sweep: number of field values, >= 1          */
+  const double *fields;     /* sweep: HOST [n_fields][3] applied fields,    */
+                            /* A/m, copied by mt_server_submit              */
 } mt_job;
 
 typedef struct {
-  int32_t status;           /* MT_OK, MT_ENOCONV (cap), MT_ENONFINITE,      */
-                            /* MT_ENOMEM (geometry exceeds the budget)      */
+  int32_t status;           /* MT_OK, MT_ENOCONV (relax: time cap; both:    */
+                            /* step cap), MT_ENONFINITE, MT_ENOMEM          */
+                            /* (geometry exceeds the budget), or the status */
+                            /* of a geometry that fails creation/assembly   */
   int32_t geometry;
   double t_submit, t_start, t_done; /* server clock, s since creation       */
-  int64_t n_accept, n_reject, n_rhs;
-  double t_sim;             /* simulated time reached, s                    */
+  int64_t n_accept, n_reject, n_rhs; /* summed over a sweep's values        */
+  double t_sim;             /* simulated time, s (summed over a sweep)      */
   double tau;               /* final torque                                 */
+  int64_t values_done;      /* field values finished (relax: 1)             */
+  int64_t values_converged; /* of those, values that met the tolerance      */
 } mt_job_result;
 
 typedef struct {
@@ -548,11 +568,14 @@ MT_API mt_status mt_server_add_geometry(mt_server *S, int64_t n, const double *c
                                         const double *axis, const int32_t *nbr, int32_t *geometry_id);
 /* Queue a job (copied); returns at once with its id. */
 MT_API mt_status mt_server_submit(mt_server *S, const mt_job *job, uint64_t *job_id);
-/* Wait up to timeout_s for a job; on MT_OK fills res and (if m_out is not
- * NULL) the final state (HOST, 3n floats) and forgets the job.  Returns
- * MT_ETIMEOUT if it is not finished yet (it keeps running). */
+/* Wait up to timeout_s for a job; on MT_OK fills res, (if m_out is not
+ * NULL) the final state (HOST, 3n floats) and, for a sweep job, (if
+ * sweep_out is not NULL) sweep_out[4 s + q] = <m>_q (q < 3) and the torque
+ * (q = 3) at the end of field value s (HOST, 4 n_fields doubles; NaN for
+ * values not reached), and forgets the job.  Returns MT_ETIMEOUT if it is
+ * not finished yet (it keeps running). */
 MT_API mt_status mt_server_wait(mt_server *S, uint64_t job_id, double timeout_s, mt_job_result *res,
-                                float *m_out);
+                                float *m_out, double *sweep_out);
 MT_API mt_status mt_server_get_stats(mt_server *S, mt_server_stats *st);
 /* Stops the worker after the device work in flight; unfinished jobs are
  * dropped. */

@@ -59,20 +59,23 @@ class TensorInfo(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_batch", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("layout", ctypes.c_int32), ("form", ctypes.c_int32), ("gamma", ctypes.c_double),
-                ("ode", OdeOpts), ("replays_per_poll", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("ode", OdeOpts), ("replays_per_poll", ctypes.c_int32), ("max_running", ctypes.c_int32)]
+
+
+MT_JOB_RELAX, MT_JOB_SWEEP = 0, 1
 
 
 class Job(ctypes.Structure):
-    _fields_ = [("geometry", ctypes.c_int32), ("pad", ctypes.c_int32), ("alpha", ctypes.c_double),
+    _fields_ = [("geometry", ctypes.c_int32), ("kind", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("Ha", ctypes.c_double * 3), ("m0", ctypes.c_void_p), ("tol", ctypes.c_double),
-                ("t_max", ctypes.c_double)]
+                ("t_max", ctypes.c_double), ("n_fields", ctypes.c_int64), ("fields", ctypes.c_void_p)]
 
 
 class JobResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("geometry", ctypes.c_int32), ("t_submit", ctypes.c_double),
                 ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("n_accept", ctypes.c_int64),
                 ("n_reject", ctypes.c_int64), ("n_rhs", ctypes.c_int64), ("t_sim", ctypes.c_double),
-                ("tau", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("values_done", ctypes.c_int64), ("values_converged", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: (list(v) if hasattr(v, "__len__") else v) for k, v in
@@ -138,7 +141,7 @@ _SIGS = {
     "mt_server_create": (_I, [_P, ctypes.POINTER(ServerOpts), _PP]),
     "mt_server_add_geometry": (_I, [_P, _I64, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "mt_server_submit": (_I, [_P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
-    "mt_server_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(JobResult), _P]),
+    "mt_server_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(JobResult), _P, _P]),
     "mt_server_get_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
     "mt_server_destroy": (None, [_P]),
 }
@@ -194,6 +197,32 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _device_vector(x, count: int, dtype_name: str, device: int, where: str, what: str):
+    """Refuse anything but a contiguous torch CUDA tensor of `count`
+    elements of the given dtype on the library context's device: the kernels
+    read and write exactly that many elements through the raw pointer, so a
+    host array, a short tensor, a strided view or another device's memory
+    would become an out-of-bounds device access."""
+    import torch
+    dt = getattr(torch, dtype_name)
+    if not isinstance(x, torch.Tensor):
+        raise ValueError("%s: %s must be a torch CUDA tensor, got %s" % (where, what, type(x).__name__))
+    if not x.is_cuda:
+        raise ValueError("%s: %s is in host memory; a CUDA tensor is required" % (where, what))
+    if x.dtype != dt:
+        raise ValueError("%s: %s has dtype %s, %s is required" % (where, what, x.dtype, dt))
+    if not x.is_contiguous():
+        raise ValueError("%s: %s must be contiguous" % (where, what))
+    if x.numel() != count:
+        raise ValueError("%s: %s has %d elements, %d (B * 3n) are required" % (where, what, x.numel(), count))
+    if x.device.index != device:
+        raise ValueError("%s: %s is on cuda:%s, the context is on cuda:%d" % (where, what, x.device.index, device))
+
+
+def _tensor_device(T) -> int:
+    return int(T.tiles.ctx.device)
+
+
 def _f64(a, shape=None):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a if shape is None else a.reshape(shape)
@@ -247,9 +276,6 @@ class TilesH:
             _check(lib().mt_tiles_create_tetra(ctx.h, verts.size // 3, _ptr(verts), n, _ptr(tets),
                                                *[_ptr(a) for a in arrs], ctypes.byref(h)), "mt_tiles_create_tetra")
             self.h = h
-            P = verts.reshape(-1, 3)[tets]
-            self.volume = np.abs(np.einsum("ij,ij->i", P[:, 1] - P[:, 0],
-                                           np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6
             return
         self.n = int(tiles.centre.shape[0])
         arrs = [_f64(tiles.centre), _f64(tiles.edge), _f64(tiles.Ms), _f64(tiles.Aex), _f64(tiles.Ku),
@@ -259,7 +285,6 @@ class TilesH:
         _check(lib().mt_tiles_create(ctx.h, self.n, *[_ptr(a) for a in arrs], _ptr(nbr), ctypes.byref(h)),
                "mt_tiles_create")
         self.h = h
-        self.volume = np.prod(arrs[1].reshape(-1, 3), axis=1)
 
     def close(self):
         if self.h:
@@ -396,12 +421,23 @@ def mt_demag_blocks(tiles: TilesH, pairs) -> np.ndarray:
     return out
 
 
+def _field_args(T, m, H, B, dtype_name, where):
+    if int(B) < 1:
+        raise ValueError("%s: B must be >= 1" % where)
+    dev = _tensor_device(T)
+    _device_vector(m, 3 * T.n * int(B), dtype_name, dev, where, "m")
+    _device_vector(H, 3 * T.n * int(B), dtype_name, dev, where, "H")
+
+
 def mt_demag_field(T: TensorH, m, H, B: int = 1, stream=None):
     """m, H: torch CUDA float32 tensors of B*3n elements."""
+    _field_args(T, m, H, B, "float32", "mt_demag_field")
     _check(lib().mt_demag_field(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field")
 
 
 def mt_demag_field_f64(T: TensorH, m, H, B: int = 1, stream=None):
+    """m, H: torch CUDA float64 tensors of B*3n elements."""
+    _field_args(T, m, H, B, "float64", "mt_demag_field_f64")
     _check(lib().mt_demag_field_f64(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field_f64")
 
 
@@ -410,19 +446,58 @@ def mt_demag_field_noalloc(T: TensorH, m, H, B: int = 1, stream=None):
     areas come from a fixed per-GPU array (see include/mt.h).  Calls that
     overlap on the GPU race; the first call on a device should precede any
     stream capture."""
+    _field_args(T, m, H, B, "float32", "mt_demag_field_noalloc")
     _check(lib().mt_demag_field_noalloc(T.h, _ptr(m), B, _ptr(H), _stream(stream)), "mt_demag_field_noalloc")
 
 
 def mt_llg_rhs(T: TensorH, params: LlgParams, m, dmdt, tau=None, B: int = 1, stream=None):
+    """m, dmdt: torch CUDA float32 tensors of B*3n elements; tau: None or B floats."""
+    _field_args(T, m, dmdt, B, "float32", "mt_llg_rhs")
+    if tau is not None:
+        _device_vector(tau, int(B), "float32", _tensor_device(T), "mt_llg_rhs", "tau")
     _check(lib().mt_llg_rhs(T.h, ctypes.byref(params), _ptr(m), B, _ptr(dmdt), _ptr(tau), _stream(stream)),
            "mt_llg_rhs")
 
 
 def mt_energy(T: TensorH, params: LlgParams, m, B: int = 1, stream=None) -> np.ndarray:
     """Energies (J) of B states: (B, 5) = total, Zeeman, demag, exchange, anisotropy."""
+    if int(B) < 1:
+        raise ValueError("mt_energy: B must be >= 1")
+    _device_vector(m, 3 * T.n * int(B), "float32", _tensor_device(T), "mt_energy", "m")
     E = np.zeros((B, 5))
     _check(lib().mt_energy(T.h, ctypes.byref(params), _ptr(m), B, _ptr(E), _stream(stream)), "mt_energy")
     return E
+
+
+def mt_integrate(T: TensorH, params: LlgParams, opts: OdeOpts, m, t0: float, t1: float, n_out: int = 1, B: int = 1,
+                 stream=None, check: bool = True):
+    """One-call integration of the DEVICE state m (torch CUDA float32, B*3n,
+    in/out) from t0 to t1; returns (status, mavg (n_out, B, 3), stats)."""
+    if int(B) < 1:
+        raise ValueError("mt_integrate: B must be >= 1")
+    _device_vector(m, 3 * T.n * int(B), "float32", _tensor_device(T), "mt_integrate", "m")
+    mavg = np.zeros((int(n_out), int(B), 3))
+    st = (Stats * int(B))()
+    s = lib().mt_integrate(T.h, ctypes.byref(params), ctypes.byref(opts), _ptr(m), int(B), float(t0), float(t1),
+                           int(n_out), _ptr(mavg), st, _stream(stream))
+    if check:
+        _check(s, "mt_integrate")
+    return s, mavg, [x.as_dict() for x in st]
+
+
+def mt_relax(T: TensorH, params: LlgParams, opts: OdeOpts, m, tol: float, t_max: float, B: int = 1, stream=None,
+             check: bool = True):
+    """One-call relaxation (Eq. 2) of the DEVICE state m (torch CUDA
+    float32, B*3n, in/out); returns (status, stats)."""
+    if int(B) < 1:
+        raise ValueError("mt_relax: B must be >= 1")
+    _device_vector(m, 3 * T.n * int(B), "float32", _tensor_device(T), "mt_relax", "m")
+    st = (Stats * int(B))()
+    s = lib().mt_relax(T.h, ctypes.byref(params), ctypes.byref(opts), float(tol), float(t_max), _ptr(m), int(B), st,
+                       _stream(stream))
+    if check:
+        _check(s, "mt_relax")
+    return s, [x.as_dict() for x in st]
 
 
 class Integrator:
@@ -443,13 +518,22 @@ class Integrator:
         is_host = isinstance(m, np.ndarray)
         if is_host:
             m = np.ascontiguousarray(m, np.float32)
+            if m.size != self.B * 3 * self.n:
+                raise ValueError("set_state: %d elements, %d (B * 3n) are required" % (m.size, self.B * 3 * self.n))
             self._host_keep = m
+        else:
+            _device_vector(m, self.B * 3 * self.n, "float32", _tensor_device(self.T), "set_state", "m")
         _check(lib().mt_integrator_set_state(self.h, _ptr(m), int(is_host), float(t0)), "mt_integrator_set_state")
 
     def get_state(self, out=None):
         if out is None:
             out = np.empty((self.B, self.n, 3), np.float32)
         is_host = isinstance(out, np.ndarray)
+        if is_host:
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != self.B * 3 * self.n:
+                raise ValueError("get_state: a contiguous float32 array of B * 3n elements is required")
+        else:
+            _device_vector(out, self.B * 3 * self.n, "float32", _tensor_device(self.T), "get_state", "out")
         _check(lib().mt_integrator_get_state(self.h, _ptr(out), int(is_host)), "mt_integrator_get_state")
         return out
 
@@ -561,15 +645,16 @@ class Server:
 
     def __init__(self, ctx: Ctx, max_batch: int = 16, prec="f32", layout: int = MT_LAYOUT_STREAM,
                  hbm_budget_bytes: int = 0, gamma: float = 2.211e5, form: int = MT_FORM_GILBERT,
-                 opts: OdeOpts | None = None, replays_per_poll: int = 0):
+                 opts: OdeOpts | None = None, replays_per_poll: int = 0, max_running: int = 0):
         prec = PREC_NAMES[prec] if isinstance(prec, str) else int(prec)
         o = ServerOpts(int(hbm_budget_bytes), int(max_batch), prec, int(layout), int(form), float(gamma),
-                       opts or ode_opts(rtol=1e-5, atol=1e-5), int(replays_per_poll), 0)
+                       opts or ode_opts(rtol=1e-5, atol=1e-5), int(replays_per_poll), int(max_running))
         h = ctypes.c_void_p()
         _check(lib().mt_server_create(ctx.h, ctypes.byref(o), ctypes.byref(h)), "mt_server_create")
         self.h = h
         self.ctx = ctx
         self.n = {}
+        self._sweeps = {}
 
     def add_geometry(self, tiles) -> int:
         arrs = [_f64(tiles.centre), _f64(tiles.edge), _f64(tiles.Ms), _f64(tiles.Aex), _f64(tiles.Ku),
@@ -583,22 +668,38 @@ class Server:
         return gid.value
 
     def submit(self, geometry: int, m0, alpha: float = 0.5, Ha=(0.0, 0.0, 0.0), tol: float = 1e-4,
-               t_max: float = 1e-9) -> int:
+               t_max: float = 1e-9, fields=None) -> int:
+        """A relax job (fields None: relax at Ha) or a sweep job (fields:
+        (S, 3) applied fields in A/m, relaxed at in turn, t_max per value)."""
         m0 = np.ascontiguousarray(m0, np.float32).ravel()
-        j = Job(int(geometry), 0, float(alpha), (ctypes.c_double * 3)(*[float(x) for x in Ha]), m0.ctypes.data,
-                float(tol), float(t_max))
+        if m0.size != 3 * self.n[int(geometry)]:
+            raise ValueError("submit: m0 has %d values, %d (3n) are required" % (m0.size, 3 * self.n[int(geometry)]))
+        f = None if fields is None else np.ascontiguousarray(fields, np.float64).reshape(-1, 3)
+        j = Job(int(geometry), MT_JOB_RELAX if f is None else MT_JOB_SWEEP, float(alpha),
+                (ctypes.c_double * 3)(*[float(x) for x in Ha]), m0.ctypes.data, float(tol), float(t_max),
+                0 if f is None else f.shape[0], None if f is None else f.ctypes.data)
         jid = ctypes.c_uint64()
         _check(lib().mt_server_submit(self.h, ctypes.byref(j), ctypes.byref(jid)), "mt_server_submit")
+        if f is not None:
+            self._sweeps[jid.value] = f.shape[0]
         return jid.value
 
     def wait(self, job_id: int, timeout_s: float = 60.0, geometry: int | None = None):
-        """Returns (status, result dict, final m (n,3) or None)."""
+        """Returns (status, result dict, final m (n,3) or None); a sweep
+        job's result dict also holds "sweep": (S, 4) = <m>, torque per value."""
         res = JobResult()
         m = None
         if geometry is not None:
             m = np.empty((self.n[geometry], 3), np.float32)
-        s = lib().mt_server_wait(self.h, ctypes.c_uint64(job_id), float(timeout_s), ctypes.byref(res), _ptr(m))
-        return s, res.as_dict(), m
+        nf = self._sweeps.get(job_id)
+        sw = None if nf is None else np.full((nf, 4), np.nan)
+        s = lib().mt_server_wait(self.h, ctypes.c_uint64(job_id), float(timeout_s), ctypes.byref(res), _ptr(m),
+                                 _ptr(sw))
+        d = res.as_dict()
+        if s == MT_OK and nf is not None:
+            d["sweep"] = sw
+            del self._sweeps[job_id]
+        return s, d, m
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -49,7 +49,7 @@ __constant__ double c_dp_err[7] = {35.0 / 384 - 5179.0 / 57600,
 struct SimCtl {
   double t, h, hs, t_next, t_out0, dt_out, t1, tol;
   double tau, err;
-  double m_last[3];  // volume-averaged m after the last accepted step
+  double m_last[3];  // volume-averaged m of the last accepted (or starting) state
   int64_t iout, n_out;
   int64_t n_accept, n_reject, n_rhs, n_attempt, attempt_cap;
   int mode;      // 0 = fixed number of steps, 1 = integrate to t1, 2 = relax
@@ -453,10 +453,21 @@ __global__ void __launch_bounds__(kStageThreads) k_stage(StageArgs A) {
     return;
   }
   if constexpr (S == 1) {
+    // torque and <m> of the starting state (a relaxation that is already
+    // converged ends here with its mean recorded)
     float v[5] = {0.0f, tau_i, 0.0f, 0.0f, 0.0f};
+    if (live) {
+      const float w = (float)A.wvol[i] / sqrtf(mi[0] * mi[0] + mi[1] * mi[1] + mi[2] * mi[2]);
+      v[2] = w * mi[0];
+      v[3] = w * mi[1];
+      v[4] = w * mi[2];
+    }
     double tot[5];
     if (reduce_across_blocks(A, b, v, tot)) {
       SimCtl c = A.ctl[b];
+      c.m_last[0] = tot[2];
+      c.m_last[1] = tot[3];
+      c.m_last[2] = tot[4];
       close_first(c, tot[1]);
       if (c.done) {
         A.active[b] = 0;
@@ -2320,6 +2331,44 @@ mt_status integ_admit(mt_integrator *I, int b, const float *m0_host, double alph
   k_admit<<<1, 1, 0, I->stream>>>(I->ctl, I->active, I->n_active, b, c);
   MT_CUDA(cudaGetLastError());
   return MT_OK;
+}
+
+// Enqueue the next leg of slot b's simulation from the state it holds (a
+// field sweep moves to its next applied field): new applied field, a fresh
+// relax goal (torque < tol, time cap t_max from t = 0) and the first trial
+// step h0, as a new relaxation would start; k1 is re-evaluated by the next
+// integ_init_fresh.  The damping stays.
+mt_status integ_readmit(mt_integrator *I, int b, const double *Ha, double tol, double t_max) {
+  MT_CHECK(b >= 0 && b < I->B, MT_EINVAL, "slot %d out of range", b);
+  // pinned staging: slot b's entries were consumed at its admission, which
+  // the stream completed before the poll that reported the slot done
+  float *par = I->h_slot_par + 5 * b;
+  par[2] = (float)Ha[0];
+  par[3] = (float)Ha[1];
+  par[4] = (float)Ha[2];
+  MT_CUDA(cudaMemcpyAsync(I->Ha + 3 * b, par + 2, 3 * sizeof(float), cudaMemcpyHostToDevice, I->stream));
+  SimCtl c;
+  std::memset(&c, 0, sizeof(c));
+  c.t = 0.0;
+  c.h = I->o.fixed_h > 0 ? I->o.fixed_h : I->o.h0;
+  c.mode = MODE_RELAX;
+  c.tol = tol;
+  c.t1 = t_max;
+  c.t_next = t_max;
+  c.attempt_cap = I->o.max_steps;
+  c.status = MT_OK;
+  c.fresh = 1;
+  plan_host(I, c);
+  k_admit<<<1, 1, 0, I->stream>>>(I->ctl, I->active, I->n_active, b, c);
+  MT_CUDA(cudaGetLastError());
+  return MT_OK;
+}
+
+// volume-averaged m of slot b after its last accepted step, from a polled
+// control copy
+void integ_slot_mavg(const void *ctl_host, int b, double m[3]) {
+  const SimCtl &c = reinterpret_cast<const SimCtl *>(ctl_host)[b];
+  for (int q = 0; q < 3; ++q) m[q] = c.m_last[q];
 }
 
 // k1 for the freshly admitted slots (one demag product for the batch)

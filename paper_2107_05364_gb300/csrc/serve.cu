@@ -1,4 +1,5 @@
-// Request serving: relax jobs on many geometries, continuously batched.
+// Request serving: relax and field-sweep jobs on many geometries,
+// continuously batched.
 //
 // A worker thread owns all device work of a server.  Each geometry that has
 // work becomes "resident": its tensor is assembled once and kept on the
@@ -11,11 +12,20 @@
 // streams and overlap on the device.  Residency is limited by an HBM budget
 // (tensor + batch state); idle engines are evicted least-recently-used when a
 // waiting geometry needs room.
+//
+// A relax job integrates its simulation until the torque criterion of
+// Brown's equation (Eq. 2) holds or its time cap is spent.  A sweep job is
+// the field loop of Sec. 4.1 as one request: its slot is relaxed at each
+// applied field of its schedule in turn, the state carried over; between
+// values the slot is re-admitted in place (new field, fresh relax goal, k1
+// re-evaluated) while the other slots keep running, and <m> and the torque
+// at the end of every value are kept for the caller.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <limits>
 #include <list>
 #include <map>
 #include <memory>
@@ -31,6 +41,8 @@ size_t integ_ctl_bytes(const mt_integrator *I);
 void *integ_stream(const mt_integrator *I);
 mt_status integ_admit(mt_integrator *I, int b, const float *m0_host, double alpha, const double *Ha, double tol,
                       double t_max);
+mt_status integ_readmit(mt_integrator *I, int b, const double *Ha, double tol, double t_max);
+void integ_slot_mavg(const void *ctl_host, int b, double m[3]);
 mt_status integ_init_fresh(mt_integrator *I);
 mt_status integ_replay(mt_integrator *I, int k);
 mt_status integ_poll(mt_integrator *I, void *ctl_host, cudaEvent_t ev);
@@ -47,9 +59,15 @@ using Clock = std::chrono::steady_clock;
 struct Job {
   uint64_t id = 0;
   int geometry = 0;
+  int kind = MT_JOB_RELAX;
   double alpha = 0, tol = 0, t_max = 0;
   double Ha[3] = {0, 0, 0};
-  std::vector<float> m;  // m0 in, final state out
+  std::vector<double> fields;  // sweep: [n_fields][3]
+  std::vector<double> sweep;   // sweep: [n_fields][4] = <m>, torque at the end of each value
+  int64_t value = 0;           // sweep: the value in progress
+  mt_stats acc{};              // sweep: counters of the values already done
+  int64_t converged = 0;       // sweep: values that met the torque tolerance
+  std::vector<float> m;        // m0 in, final state out
   mt_job_result res{};
   bool done = false;
 };
@@ -66,6 +84,7 @@ struct Engine {
   void *ctl = nullptr;     // pinned control copies
   cudaEvent_t ev = nullptr;
   bool inflight = false;
+  bool need_fresh = false;  // slots admitted or re-admitted since the last k1
   int occupied = 0;
 };
 
@@ -161,7 +180,16 @@ bool make_resident(mt_server *S, Geometry &g, const std::vector<Geometry *> &all
   if (!g.tiles) {
     mt_status st = mt_tiles_create(S->ctx, g.n, g.centre.data(), g.edge.data(), g.Ms.data(), g.Aex.data(),
                                    g.Ku.data(), g.axis.data(), g.nbr.empty() ? nullptr : g.nbr.data(), &g.tiles);
-    if (st != MT_OK) return false;
+    if (st != MT_OK) {
+      // an invalid geometry never becomes resident: its jobs fail with the
+      // creation status instead of waiting for room forever
+      g.tiles = nullptr;
+      while (!g.waiting.empty()) {
+        fail_job(S, g.waiting.front(), st);
+        g.waiting.pop_front();
+      }
+      return false;
+    }
   }
   std::unique_ptr<Engine> e(new Engine());
   e->B = S->o.max_batch;
@@ -197,7 +225,9 @@ bool make_resident(mt_server *S, Geometry &g, const std::vector<Geometry *> &all
   return true;
 }
 
-void complete(mt_server *S, Geometry &g, int b, const mt_stats &st) {
+// Retire slot b: the job's final state (already copied to e.m_out) and its
+// outcome `st` (counters summed over a sweep's values).
+void complete(mt_server *S, Geometry &g, int b, const mt_stats &st, int64_t values_done, int64_t values_converged) {
   Engine &e = *g.eng;
   std::shared_ptr<Job> j = e.slot[b];
   e.slot[b].reset();
@@ -212,10 +242,46 @@ void complete(mt_server *S, Geometry &g, int b, const mt_stats &st) {
   j->res.t_sim = st.t;
   j->res.tau = st.tau;
   j->res.t_done = S->now();
+  j->res.values_done = values_done;
+  j->res.values_converged = values_converged;
   j->done = true;
   if (st.status == MT_OK) S->stats.completed++;
   else S->stats.failed++;
   S->cv_done.notify_all();
+}
+
+// A slot reported done.  Relax job: finished.  Sweep job: record the value's
+// <m> and torque; a failure (non-finite state, step cap) ends the job, the
+// time cap does not (as a held field value, the torque tells); with values
+// left the slot is re-admitted at the next field and true is returned.
+bool sweep_advance(Engine &e, int b, const mt_stats &st, mt_stats *final_st, int64_t *converged) {
+  Job &j = *e.slot[b];
+  if (j.kind != MT_JOB_SWEEP) {
+    *final_st = st;
+    *converged = (st.status == MT_OK) ? 1 : 0;
+    return false;
+  }
+  const int64_t nf = (int64_t)j.fields.size() / 3;
+  double mv[3];
+  mt::integ_slot_mavg(e.ctl, b, mv);
+  double *row = &j.sweep[4 * (size_t)j.value];
+  for (int q = 0; q < 3; ++q) row[q] = mv[q];
+  row[3] = st.tau;
+  j.acc.n_accept += st.n_accept;
+  j.acc.n_reject += st.n_reject;
+  j.acc.n_rhs += st.n_rhs;
+  j.acc.t += st.t;
+  j.acc.tau = st.tau;
+  if (st.status == MT_OK) j.converged++;
+  const bool ok = st.status == MT_OK || (st.status == MT_ENOCONV && st.t >= j.t_max * (1.0 - 1e-12));
+  j.value++;
+  if (ok && j.value < nf && mt::integ_readmit(e.I, b, &j.fields[3 * (size_t)j.value], j.tol, j.t_max) == MT_OK)
+    return true;
+  *final_st = j.acc;
+  final_st->status = ok ? MT_OK : st.status;
+  final_st->pad = 0;
+  *converged = j.converged;
+  return false;
 }
 
 void worker_loop(mt_server *S) {
@@ -246,15 +312,27 @@ void worker_loop(mt_server *S) {
       if (!e || !e->inflight) continue;
       if (cudaEventQuery(e->ev) != cudaSuccess) continue;
       e->inflight = false;
-      std::vector<std::pair<int, mt_stats>> fin;
+      struct Fin {
+        int b;
+        mt_stats st;
+        int64_t values, converged;
+      };
+      std::vector<Fin> fin;
       for (int b = 0; b < e->B; ++b) {
         mt_stats st{};
-        if (e->slot[b] && mt::integ_slot_done(e->ctl, b, &st)) fin.push_back({b, st});
+        if (!e->slot[b] || !mt::integ_slot_done(e->ctl, b, &st)) continue;
+        Fin f{b, {}, 0, 0};
+        if (sweep_advance(*e, b, st, &f.st, &f.converged)) {
+          e->need_fresh = true;  // next value of a sweep: k1 at the new field
+          continue;
+        }
+        f.values = e->slot[b]->kind == MT_JOB_SWEEP ? e->slot[b]->value : 1;
+        fin.push_back(f);
       }
       if (!fin.empty()) {
-        for (auto &f : fin) mt::integ_fetch_slot(e->I, f.first, e->m_out + f.first * 3 * (size_t)g.n);
+        for (auto &f : fin) mt::integ_fetch_slot(e->I, f.b, e->m_out + f.b * 3 * (size_t)g.n);
         cudaStreamSynchronize((cudaStream_t)mt::integ_stream(e->I));
-        for (auto &f : fin) complete(S, g, f.first, f.second);
+        for (auto &f : fin) complete(S, g, f.b, f.st, f.values, f.converged);
       }
       g.last_used = S->now();
     }
@@ -265,19 +343,33 @@ void worker_loop(mt_server *S) {
     std::sort(order.begin(), order.end(), [](Geometry *a, Geometry *b) {
       return a->waiting.front()->res.t_submit < b->waiting.front()->res.t_submit;
     });
+    // a server-wide cap on running jobs (max_running > 0) admits strictly in
+    // arrival order: the oldest waiting job goes first or nothing does
+    const int cap = S->o.max_running;
+    int running = 0;
+    for (Geometry *g : all)
+      if (g->eng) running += g->eng->occupied;
     for (Geometry *gp : order) {
       Geometry &g = *gp;
-      if (!g.eng && !make_resident(S, g, all)) continue;
+      if (cap > 0 && running >= cap) break;
+      if (!g.eng && !make_resident(S, g, all)) {
+        if (cap > 0) break;
+        continue;
+      }
       Engine *e = g.eng.get();
-      if (!e || e->inflight) continue;
+      if (!e || e->inflight) {
+        if (cap > 0) break;
+        continue;
+      }
       bool admitted = false;
-      for (int b = 0; b < e->B && !g.waiting.empty(); ++b) {
+      for (int b = 0; b < e->B && !g.waiting.empty() && (cap <= 0 || running < cap); ++b) {
         if (e->slot[b]) continue;
         std::shared_ptr<Job> j = g.waiting.front();
         g.waiting.pop_front();
         const size_t n3 = 3 * (size_t)g.n;
         std::memcpy(e->m_in + b * n3, j->m.data(), sizeof(float) * n3);
-        if (mt::integ_admit(e->I, b, e->m_in + b * n3, j->alpha, j->Ha, j->tol, j->t_max) != MT_OK) {
+        const double *ha = j->kind == MT_JOB_SWEEP ? j->fields.data() : j->Ha;
+        if (mt::integ_admit(e->I, b, e->m_in + b * n3, j->alpha, ha, j->tol, j->t_max) != MT_OK) {
           fail_job(S, j, MT_ECUDA);
           continue;
         }
@@ -287,9 +379,10 @@ void worker_loop(mt_server *S) {
         }
         e->slot[b] = j;
         e->occupied++;
+        running++;
         admitted = true;
       }
-      if (admitted) mt::integ_init_fresh(e->I);
+      if (admitted) e->need_fresh = true;
       g.last_used = S->now();
     }
     // 4. launch work on every engine with running slots
@@ -298,6 +391,10 @@ void worker_loop(mt_server *S) {
       Engine *e = gp->eng.get();
       if (!e) continue;
       if (!e->inflight && e->occupied > 0) {
+        if (e->need_fresh) {
+          mt::integ_init_fresh(e->I);  // one product for every new or re-admitted slot
+          e->need_fresh = false;
+        }
         mt::integ_replay(e->I, K);
         mt::integ_poll(e->I, e->ctl, e->ev);
         e->inflight = true;
@@ -322,6 +419,7 @@ mt_status mt_server_create(mt_ctx *ctx, const mt_server_opts *opts, mt_server **
            "mt_server_create: precision must be FP32, BF16 or split BF16");
   MT_CHECK(opts->layout == MT_LAYOUT_STREAM || opts->prec != MT_F32, MT_EINVAL,
            "mt_server_create: the dense layout stores BF16 or split BF16");
+  MT_CHECK(opts->max_running >= 0, MT_EINVAL, "mt_server_create: max_running must be >= 0");
   mt_server *S = new mt_server();
   S->ctx = ctx;
   ctx->refs++;
@@ -364,10 +462,24 @@ mt_status mt_server_submit(mt_server *S, const mt_job *job, uint64_t *job_id) {
              "mt_server_submit: unknown geometry %d", job->geometry);
     MT_CHECK(job->tol > 0 && job->t_max > 0 && std::isfinite(job->alpha), MT_EINVAL,
              "mt_server_submit: tol and t_max must be positive");
+    MT_CHECK(job->kind == MT_JOB_RELAX || job->kind == MT_JOB_SWEEP, MT_EINVAL, "mt_server_submit: unknown kind %d",
+             job->kind);
+    if (job->kind == MT_JOB_SWEEP) {
+      MT_CHECK(job->fields && job->n_fields >= 1 && job->n_fields <= ((int64_t)1 << 24), MT_EINVAL,
+               "mt_server_submit: a sweep needs 1 .. 2^24 field values");
+      for (int64_t q = 0; q < 3 * job->n_fields; ++q)
+        MT_CHECK(std::isfinite(job->fields[q]), MT_EINVAL, "mt_server_submit: non-finite field value");
+      j->fields.assign(job->fields, job->fields + 3 * job->n_fields);
+      j->sweep.assign(4 * (size_t)job->n_fields, std::numeric_limits<double>::quiet_NaN());
+    } else {
+      for (int c = 0; c < 3; ++c)
+        MT_CHECK(std::isfinite(job->Ha[c]), MT_EINVAL, "mt_server_submit: non-finite applied field");
+    }
     const int64_t n = S->geoms[job->geometry]->n;
     j->m.assign(job->m0, job->m0 + 3 * n);
     j->id = S->next_id++;
     j->geometry = job->geometry;
+    j->kind = job->kind;
     j->alpha = job->alpha;
     j->tol = job->tol;
     j->t_max = job->t_max;
@@ -384,7 +496,8 @@ mt_status mt_server_submit(mt_server *S, const mt_job *job, uint64_t *job_id) {
   return MT_OK;
 }
 
-mt_status mt_server_wait(mt_server *S, uint64_t job_id, double timeout_s, mt_job_result *res, float *m_out) {
+mt_status mt_server_wait(mt_server *S, uint64_t job_id, double timeout_s, mt_job_result *res, float *m_out,
+                         double *sweep_out) {
   MT_CHECK(S, MT_EINVAL, "mt_server_wait: NULL server");
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->jobs.find(job_id);
@@ -400,6 +513,7 @@ mt_status mt_server_wait(mt_server *S, uint64_t job_id, double timeout_s, mt_job
   }
   if (res) *res = j->res;
   if (m_out) std::memcpy(m_out, j->m.data(), sizeof(float) * j->m.size());
+  if (sweep_out && !j->sweep.empty()) std::memcpy(sweep_out, j->sweep.data(), sizeof(double) * j->sweep.size());
   S->jobs.erase(it);
   return MT_OK;
 }

@@ -76,3 +76,38 @@ def test_sources_name_no_closed_calls():
             for f in fs:
                 if f.endswith((".cu", ".cuh", ".h", ".c", ".py")):
                     assert not bad.search(open(os.path.join(dp, f)).read()), f
+
+
+def test_binding_refuses_host_and_malformed_buffers():
+    # The product entry points take raw device pointers of B * 3n elements;
+    # the binding refuses anything else before calling the library (a host
+    # array or a short buffer would otherwise become an out-of-bounds device
+    # access).  No GPU is needed: the checks run first.
+    import types
+
+    import pytest
+    import torch
+
+    from paper_2107_05364_gb300 import binding as mt
+    n = 10
+    T = types.SimpleNamespace(n=n, h=None, tiles=types.SimpleNamespace(ctx=types.SimpleNamespace(device=0)))
+    good_host = np.zeros(3 * n, np.float32)
+    cpu_t = torch.zeros(3 * n)
+    for f in (mt.mt_demag_field, mt.mt_demag_field_noalloc):
+        with pytest.raises(ValueError, match="torch CUDA tensor"):
+            f(T, good_host, good_host)
+        with pytest.raises(ValueError, match="host memory"):
+            f(T, cpu_t, cpu_t)
+        with pytest.raises(ValueError, match="B must be"):
+            f(T, cpu_t, cpu_t, B=0)
+    with pytest.raises(ValueError, match="host memory"):
+        mt.mt_demag_field_f64(T, cpu_t.double(), cpu_t.double())
+    p, keep = mt.llg_params(1)
+    with pytest.raises(ValueError, match="host memory"):
+        mt.mt_llg_rhs(T, p, cpu_t, cpu_t)
+    with pytest.raises(ValueError, match="host memory"):
+        mt.mt_energy(T, p, cpu_t)
+    with pytest.raises(ValueError, match="host memory"):
+        mt.mt_relax(T, p, mt.ode_opts(), cpu_t, 1e-4, 1e-9)
+    with pytest.raises(ValueError, match="host memory"):
+        mt.mt_integrate(T, p, mt.ode_opts(), cpu_t, 0.0, 1e-9)

@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _observe import observe
 from paper_2107_05364_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -101,6 +102,50 @@ def test_overlap_is_rejected(mt, ctx):
     with pytest.raises(mt.MtError) as e:
         mt.mt_demag_assemble(tiles, "f32")
     assert e.value.status == mt.MT_EOVERLAP
+
+
+def test_centre_on_surface_is_rejected(mt, ctx):
+    # a tile too thin to overlap measurably whose centre lies on a face, an
+    # edge or a corner of a 10 nm cube: the closed form is singular there, so
+    # assembly refuses it as the oracle does; just outside the face it is valid
+    import types
+    h, eps = 10e-9, 1e-22
+    for where, ok in (([0.5 * h, 0.0, 0.0], False), ([0.5 * h, 0.5 * h, 0.0], False),
+                      ([0.5 * h, -0.5 * h, 0.5 * h], False), ([0.5 * h * (1 + 1e-6), 0.0, 0.0], True)):
+        c = np.array([[0.0, 0.0, 0.0], where])
+        e = np.array([[h, h, h], [eps, eps, eps]])
+        assert (oracle.check_tiles(c, e) == oracle.OK) == ok
+        t = types.SimpleNamespace(centre=c, edge=e, Ms=np.full(2, 8e5), Aex=np.zeros(2), Ku=np.zeros(2),
+                                  axis=np.tile([0.0, 0.0, 1.0], (2, 1)), nbr=None)
+        tiles = mt.mt_tiles_create(ctx, t)
+        if ok:
+            mt.mt_demag_assemble(tiles, "f64").close()
+        else:
+            with pytest.raises(mt.MtError) as err:
+                mt.mt_demag_assemble(tiles, "f64")
+            assert err.value.status == mt.MT_EOVERLAP
+        tiles.close()
+
+
+def test_binding_refuses_short_strided_and_mistyped_buffers(mt, ctx):
+    import torch
+    t = wl.film(6, 3, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    good = torch.zeros(3 * t.n, device="cuda")
+    for bad, msg in ((torch.zeros(3 * t.n - 1, device="cuda"), "elements"),
+                     (torch.zeros(6 * t.n, device="cuda")[::2], "contiguous"),
+                     (torch.zeros(3 * t.n, device="cuda", dtype=torch.float64), "dtype"),
+                     (torch.zeros(3 * t.n), "host memory")):
+        for f in (mt.mt_demag_field, mt.mt_demag_field_noalloc):
+            with pytest.raises(ValueError, match=msg):
+                f(T, bad, good)
+            with pytest.raises(ValueError, match=msg):
+                f(T, good, bad)
+    with pytest.raises(ValueError, match="elements"):
+        mt.mt_demag_field(T, good, good, B=2)  # B * 3n elements are read
+    mt.mt_demag_field(T, good, good)
+    torch.cuda.synchronize()
 
 
 def test_bad_tiles_are_rejected(mt, ctx):
@@ -254,8 +299,11 @@ def test_llg_rhs_parity(mt, ctx):
     for b in range(B):
         kr, taur = oracle.llg_rhs(md, m[b].astype(np.float64), oracle.llg_params(alpha=alphas[b], Ha=Ha[b]))
         kg = k.cpu().numpy().reshape(B, t.n, 3)[b]
-        assert _rel(kg, kr) <= 1e-5
-        assert abs(tau.cpu().numpy()[b] - taur) <= 1e-5 * taur
+        # bounds ~11x the agreement observed on GB300 (9.1e-8 and 1.8e-7)
+        observe("llg_rhs_rel_l2_b%d" % b, _rel(kg, kr), 1e-6)
+        observe("llg_rhs_tau_rel_b%d" % b, abs(tau.cpu().numpy()[b] - taur) / taur, 2e-6)
+        assert _rel(kg, kr) <= 1e-6
+        assert abs(tau.cpu().numpy()[b] - taur) <= 2e-6 * taur
 
 
 @pytest.mark.parametrize("prec", ["f32", "bf16", "split"])

@@ -2,9 +2,11 @@
 equation (Sec. 3.1, Eq. 1) against the FP64 oracle, through the C ABI.
 
 The GPU integrates in FP32 on the FP32-stored tensor, the oracle in FP64;
-tolerances are stated per test: fixed steps agree to FP32 round-off grown
-over the steps, adaptive traces to within the integration tolerance, and
-relaxed states to max |dm| <= 1e-4.
+tolerances are stated per test.  Fixed steps and adaptive <m> traces are
+bounded at a stated multiple (10-16x) of the agreement observed on GB300
+(FP32 round-off grown over the steps; the runs are deterministic, so a
+regression shows as a jump); relaxed states keep the relaxed-state bound
+max |dm| <= 1e-4, and print the observed value.
 """
 import math
 
@@ -12,6 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _observe import observe
 from paper_2107_05364_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -44,6 +47,34 @@ def film(mt, ctx):
     return t, tiles, T, oracle.Model.from_tiles(t)
 
 
+@pytest.mark.parametrize("path", ["persistent", "graph"])
+def test_mean_m_is_volume_weighted(mt, ctx, path):
+    # <m> of the traces is (1/V) sum_i V_i m_i: two tiles of volumes V and 3V
+    # along x and y give (1/4, 3/4, 0); with gamma = 0 the state does not move
+    import types
+    h = 2e-9
+    t = types.SimpleNamespace(centre=np.array([[0.0, 0.0, 0.0], [3.0 * h, 0.0, 0.0]]),
+                              edge=np.array([[h, h, h], [3.0 * h, h, h]]), Ms=np.full(2, 8e5),
+                              Aex=np.zeros(2), Ku=np.zeros(2), axis=np.tile([0.0, 0.0, 1.0], (2, 1)), nbr=None)
+    g = wl.graded_film(9, 5, 3, size=(60e-9, 30e-9, 9e-9), seed=6)
+    mg = wl.m_random(g.n, seed=4)
+    for tt, m0, expect in ((t, np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]), np.array([0.25, 0.75, 0.0])),
+                           (g, mg, (g.edge.prod(1)[:, None] * mg).sum(0) / g.edge.prod(1).sum())):
+        tiles = mt.mt_tiles_create(ctx, tt)
+        T = mt.mt_demag_assemble(tiles, "f32")
+        p, keep = mt.llg_params(1, gamma=0.0, alpha=0.0)
+        I = mt.Integrator(T, p, mt.ode_opts(fixed_h=1e-13))
+        I.set_path(mt.MT_PATH_PERSISTENT if path == "persistent" else mt.MT_PATH_GRAPH)
+        I.set_state(m0.astype(np.float32).ravel())
+        s, mavg, st = I.run(3e-13, 3)
+        assert np.abs(mavg[:, 0, :] - expect).max() <= 1e-6, (mavg, expect)
+        # (an unweighted mean differs by far more on both sets)
+        assert np.abs(m0.mean(0) - expect).max() > 1e-3
+        I.close()
+        T.close()
+        tiles.close()
+
+
 def test_fixed_steps_match_oracle(mt, film):
     t, tiles, T, md = film
     m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
@@ -56,7 +87,9 @@ def test_fixed_steps_match_oracle(mt, film):
     st, mo, _, _ = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=FIELD1),
                                     oracle.ode_opts(fixed_h=h), 0.0, 20 * h, 1)
     assert st == oracle.OK
-    assert np.abs(mg - mo).max() <= 2e-5
+    # bound ~13x the 2.4e-7 observed on GB300 (FP32 round-off over 20 steps)
+    observe("fixed_steps_20", np.abs(mg - mo).max(), 3e-6)
+    assert np.abs(mg - mo).max() <= 3e-6
     np.testing.assert_allclose(np.linalg.norm(mg, axis=1), 1.0, atol=1e-6)
     s = I.stats()[0]
     assert s["n_accept"] == 20 and s["n_reject"] == 0
@@ -77,7 +110,9 @@ def test_adaptive_trace_matches_oracle(mt, film):
     so, mo, mref, sto = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.02, Ha=FIELD1),
                                          oracle.ode_opts(**opts), 0.0, T1, n_out)
     assert so == oracle.OK
-    assert np.abs(mavg[:, 0, :] - mref).max() <= 2e-4
+    # bound ~12x the 1.28e-6 observed on GB300
+    observe("adaptive_trace_0.1ns", np.abs(mavg[:, 0, :] - mref).max(), 1.5e-5)
+    assert np.abs(mavg[:, 0, :] - mref).max() <= 1.5e-5
     # the step counts agree to within a few percent
     assert abs(st[0]["n_accept"] - sto["n_accept"]) <= 0.05 * sto["n_accept"] + 3
 
@@ -101,7 +136,9 @@ def test_macrospin_larmor_on_gpu(mt, ctx):
     th = 2 * np.arctan(math.tan(th0 / 2) * np.exp(-alpha * w * ts))
     ph = ph0 + w * ts
     exp = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], 1)
-    assert np.abs(mavg[:, 0, :] - exp).max() <= 2e-5
+    # bound 16x the 1.26e-7 observed on GB300
+    observe("macrospin_larmor", np.abs(mavg[:, 0, :] - exp).max(), 2e-6)
+    assert np.abs(mavg[:, 0, :] - exp).max() <= 2e-6
 
 
 def test_relax_matches_oracle(mt, film):
@@ -118,6 +155,7 @@ def test_relax_matches_oracle(mt, film):
     so, mo, sto = oracle.relax(md, m0.astype(np.float64), oracle.llg_params(alpha=0.5),
                                oracle.ode_opts(**opts), tol, 20e-9)
     assert so == oracle.OK
+    observe("relax_c1_tol1e-5", np.abs(mg - mo).max(), 1e-4)
     assert np.abs(mg - mo).max() <= 1e-4
     np.testing.assert_allclose(np.linalg.norm(mg, axis=1), 1.0, atol=1e-6)
 
@@ -192,7 +230,7 @@ def test_nonfinite_state_is_reported(mt, film):
 def test_config1_relax_then_1ns_dynamics(mt, film):
     # the 40 x 10 x 1 film: relax from the (1,1,1) start at alpha = 0.5, then
     # 1 ns of dynamics under field 1 at alpha = 0.02 with <m> every 1 ps; the
-    # FP32 GPU trace follows the FP64 oracle's within 2e-3 (both adaptive,
+    # FP32 GPU trace follows the FP64 oracle's within 3e-6 (both adaptive,
     # rtol = atol = 1e-6; differences are integration error, not arithmetic)
     t, tiles, T, md = film
     m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-3, seed=0).astype(np.float32)
@@ -205,6 +243,7 @@ def test_config1_relax_then_1ns_dynamics(mt, film):
     I.set_state(m0.ravel())
     s, st = I.relax(1e-5, 20e-9)
     mg = I.get_state()[0]
+    observe("config1_relax", np.abs(mg - mo).max(), 1e-4)
     assert np.abs(mg - mo).max() <= 1e-4
     # dynamics from the oracle's relaxed state (same start on both sides)
     dopts = dict(rtol=1e-6, atol=1e-6, h0=1e-14, hmax=1e-11)
@@ -217,5 +256,40 @@ def test_config1_relax_then_1ns_dynamics(mt, film):
     I2.set_state(s1.ravel())
     s, mavg, st = I2.run(1e-9, 1000)
     d = np.abs(mavg[:, 0, :] - mref).max()
-    print("config 1: 1 ns <m>(t) max difference %.2e" % d)
-    assert d <= 2e-3
+    # bound 12x the 2.5e-7 observed on GB300
+    observe("config1_1ns_trace", d, 3e-6)
+    assert d <= 3e-6
+
+
+def test_config2_cube_relax_to_1e_6_converges_or_reports_torque(mt, ctx):
+    # config 2's cube (20 l_ex, 20^3 tiles, K_u = 0.1 K_m along z) relaxed
+    # from the flower seed with the one-call mt_relax on device state, asking
+    # for a torque below 1e-6: an explicit integrator in FP32 state has a
+    # torque floor near 10 x atol, so the call either converges or stops at
+    # the time cap with MT_ENOCONV and reports the torque it attained
+    import torch
+    t = wl.cube(20, 20.0)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble(tiles, "f32")
+    p, keep = mt.llg_params(1, alpha=0.5)
+    m = torch.tensor(wl.m_flower(t).astype(np.float32).ravel(), device="cuda")
+    E0 = mt.mt_energy(T, p, m)[0, 0]
+    t_max = 1e-9
+    s, st = mt.mt_relax(T, p, mt.ode_opts(rtol=1e-7, atol=1e-7, h0=1e-14, hmax=1e-11), m, 1e-6, t_max, check=False)
+    torch.cuda.synchronize()
+    tau = st[0]["tau"]
+    print("config 2 cube, tol 1e-6: status %d, tau %.2e after %.3g s" % (s, tau, st[0]["t"]))
+    assert np.isfinite(tau) and tau > 0
+    if s == mt.MT_OK:
+        assert tau < 1e-6 and st[0]["status"] == mt.MT_OK
+    else:
+        assert s == mt.MT_ENOCONV and st[0]["status"] == mt.MT_ENOCONV
+        assert tau >= 1e-6 and abs(st[0]["t"] - t_max) <= 1e-9 * t_max
+    mm = m.cpu().numpy().reshape(-1, 3)
+    np.testing.assert_allclose(np.linalg.norm(mm, axis=1), 1.0, atol=1e-5)
+    # the state moved toward equilibrium: with damping the energy of a
+    # uniform lattice decreases (after 1 ns the 20 l_ex cube is still
+    # reorganising, its torque of order 0.1)
+    assert mt.mt_energy(T, p, m)[0, 0] < E0
+    T.close()
+    tiles.close()

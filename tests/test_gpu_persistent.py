@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _observe import observe
 from paper_2107_05364_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -106,8 +107,11 @@ def test_fixed_steps_match_oracle_and_graph(mt, ctx, grid):
                                         oracle.llg_params(alpha=alpha[b], Ha=Ha[b]), oracle.ode_opts(fixed_h=h),
                                         0.0, steps * h, 1)
         assert st == oracle.OK
-        assert np.abs(out[mt.MT_PATH_PERSISTENT][b] - mo).max() <= 2e-5
-        assert np.abs(out[mt.MT_PATH_GRAPH][b] - mo).max() <= 2e-5
+        # bound ~14x the 2.9e-7 observed on GB300
+        observe("fixed_steps_persistent_b%d" % b, np.abs(out[mt.MT_PATH_PERSISTENT][b] - mo).max(), 4e-6)
+        observe("fixed_steps_graph_b%d" % b, np.abs(out[mt.MT_PATH_GRAPH][b] - mo).max(), 4e-6)
+        assert np.abs(out[mt.MT_PATH_PERSISTENT][b] - mo).max() <= 4e-6
+        assert np.abs(out[mt.MT_PATH_GRAPH][b] - mo).max() <= 4e-6
     assert np.abs(out[mt.MT_PATH_PERSISTENT] - out[mt.MT_PATH_GRAPH]).max() <= 1e-5
     np.testing.assert_allclose(np.linalg.norm(out[mt.MT_PATH_PERSISTENT], axis=2), 1.0, atol=1e-6)
 
@@ -130,7 +134,9 @@ def test_adaptive_trace_matches_oracle(mt, film):
         I.set_state(m0.ravel())
         s, mavg, st = I.run(T1, n_out)
         assert st[0]["status"] == 0 and abs(st[0]["t"] - T1) < 1e-20
-        assert np.abs(mavg[:, 0, :] - mref).max() <= 2e-4
+        # bound ~12x the 1.28e-6 observed on GB300 (either path)
+        observe("adaptive_trace_0.1ns_path%d" % path, np.abs(mavg[:, 0, :] - mref).max(), 1.5e-5)
+        assert np.abs(mavg[:, 0, :] - mref).max() <= 1.5e-5
         assert abs(st[0]["n_accept"] - sto["n_accept"]) <= 0.05 * sto["n_accept"] + 3
         traces[path] = mavg
     assert np.abs(traces[mt.MT_PATH_PERSISTENT] - traces[mt.MT_PATH_GRAPH]).max() <= 1e-5
@@ -150,6 +156,7 @@ def test_relax_matches_oracle(mt, film):
     so, mo, sto = oracle.relax(md, m0.astype(np.float64), oracle.llg_params(alpha=0.5),
                                oracle.ode_opts(**opts), tol, 20e-9)
     assert so == oracle.OK
+    observe("relax_persistent", np.abs(I.get_state()[0] - mo).max(), 1e-4)
     assert np.abs(I.get_state()[0] - mo).max() <= 1e-4
 
 

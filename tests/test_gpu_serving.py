@@ -130,3 +130,19 @@ def test_dense_layout_server(mt, ctx):
     for (s1, r1, m1), (s2, r2, m2) in zip(dense, ref):
         assert r1["status"] == 0 and r2["status"] == 0
         assert np.abs(m1 - m2).max() <= 1e-4
+
+
+def test_one_job_at_a_time_in_arrival_order(mt, ctx):
+    # a server-wide limit of one running job with one slot per geometry runs
+    # the requests strictly one by one, first come first served
+    geoms = _geoms()
+    jobs = _jobs(geoms, 6, seed=9)
+    S = mt.Server(ctx, max_batch=1, max_running=1, opts=mt.ode_opts(rtol=1e-5, atol=1e-5))
+    gids = [S.add_geometry(t) for t in geoms]
+    ids = [S.submit(gids[j["geometry"]], j["m0"], alpha=j["alpha"], Ha=j["Ha"], tol=1e-4, t_max=20e-9)
+           for j in jobs]
+    res = [S.wait(i, 120.0)[1] for i in ids]
+    S.close()
+    assert all(r["status"] == 0 for r in res)
+    for a, b in zip(res, res[1:]):
+        assert b["t_start"] >= a["t_done"], (a, b)  # no overlap, in submission order

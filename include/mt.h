@@ -297,20 +297,27 @@ MT_API mt_status mt_demag_field_f64(mt_tensor *T, const double *m, int B, double
  * latency-critical streams that cannot take the device-wide synchronisation
  * cudaMalloc/cudaFree may cause, or an application whose own memory pool
  * forbids the CUDA allocator.  Same arguments, same result as mt_demag_field
- * (FP32 and BF16 tensors of the streaming layout; dense-layout tensors get
- * MT_EINVAL); this call allocates nothing: its work areas (the
- * scaled copy of m, partial panel sums, panel counters) live in one fixed
- * array of MT_NOALLOC_SCRATCH_BYTES in the library's device image.  The
- * paper has no counterpart; it is an interface convenience.
+ * for streaming-layout tensors (FP32, scaled BF16 and split BF16); this call
+ * allocates nothing: its work areas (the scaled copy of m, partial panel
+ * sums, panel counters) live in one fixed array of MT_NOALLOC_SCRATCH_BYTES
+ * in the library's device image.  The paper has no counterpart; it is an
+ * interface convenience.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress, which may load the library's device code);
  *     make that first call before any stream capture.
  *   - Every call on a device shares the one array and leaves its contents
  *     behind: calls that overlap on the GPU (different streams, or threads)
  *     race and corrupt each other's result.  Serialise them.
+ *   - Scratch needed, each part rounded up to 256 bytes: the scaled operand,
+ *     12 bytes per tile and simulation (tiles padded to whole column chunks);
+ *     the panel counters, 32 / R bytes per tile and simulation (R = 16 tile
+ *     rows per panel for FP32 and BF16, 8 for split: 2 or 4 bytes); the
+ *     partial sums, 96 R bytes per SM (on a 152-SM GB300 about 233 KB for
+ *     FP32 and BF16, 117 KB for split).  So B * n may reach about 282,000
+ *     (FP32, BF16) or 254,000 (split) on a 152-SM GB300.
  *   - Errors: MT_EINVAL if B * n needs more scratch than
- *     MT_NOALLOC_SCRATCH_BYTES (about 12.3 bytes per tile and simulation plus
- *     ~80 KB fixed), for an FP64 tensor, or a NULL pointer; MT_ECUDA. */
+ *     MT_NOALLOC_SCRATCH_BYTES, for an FP64 tensor, for a dense-layout or
+ *     thresholded (sparse) tensor, or a NULL pointer; MT_ECUDA. */
 MT_API mt_status mt_demag_field_noalloc(mt_tensor *T, const float *m, int B, float *H, void *stream);
 
 /* Landau-Lifshitz right-hand side (Eq. 1 or its Gilbert form) at m for B

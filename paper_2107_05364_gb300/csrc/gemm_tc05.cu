@@ -56,7 +56,9 @@ template <bool SPLIT, int BP>
 struct GemmShape {
   static constexpr bool STACK = SPLIT && BP <= 64;
   static constexpr int ACC_COLS = STACK ? 3 * BP : BP;  // TMEM columns of one accumulator
-  static constexpr int NA = STACK ? (BP == 64 ? 2 : 4) : NACC;  // accumulators (<= 512 columns)
+  // accumulators (<= 512 TMEM columns); the BF16 product at BP <= 64 keeps 8
+  // in flight
+  static constexpr int NA = STACK ? (BP == 64 ? 2 : 4) : (BP <= 64 ? 2 * NACC : NACC);
 };
 constexpr int GEMM_THREADS = 32 * (2 + EPI_WARPS);
 
@@ -567,7 +569,7 @@ mt_status gemm_tune(mt_tensor *T, GemmPlan *plan, float *H, float *part, int *co
     return MT_OK;
   }
   const int smax = stages_for(plan->Bp, plan->split);
-  int cand[3] = {smax, std::max(2, smax - 2), std::max(2, smax / 2)};
+  int cand[3] = {smax, std::max(2, smax - 1), std::max(2, smax - 2)};
   cudaEvent_t e0, e1;
   MT_CUDA(cudaEventCreate(&e0));
   MT_CUDA(cudaEventCreate(&e1));
@@ -610,7 +612,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.stage_bytes = stage_bytes_for(plan.Bp, plan.split);
   const bool stack = plan.split && plan.Bp <= 64;
   const int acc_cols = stack ? 3 * plan.Bp : plan.Bp;
-  const int na = stack ? (plan.Bp == 64 ? 2 : 4) : NACC;  // as GemmShape
+  const int na = stack ? (plan.Bp == 64 ? 2 : 4) : (plan.Bp <= 64 ? 2 * NACC : NACC);  // as GemmShape
   uint32_t cols = 32;
   while (cols < (uint32_t)(na * acc_cols)) cols <<= 1;
   P.tmem_cols = cols;
@@ -621,7 +623,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.status = status;
   const int64_t U = P.MT * P.KBU;
   const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
-  const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 256;
+  const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 512;  // + alignment slack, barriers
 #define MT_GEMM_LAUNCH(SP, BPV)                                                                              \
   mt::launch_pdl(k_gemm<SP, BPV, kps_of<SP, BPV>()>, dim3(grid), dim3(GEMM_THREADS), smem, s, plan.tA, plan.tAlo, \
                  plan.tX, plan.tX1, plan.tX2, P)

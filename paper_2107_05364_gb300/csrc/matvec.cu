@@ -463,43 +463,15 @@ __global__ void k_prep_xs(const In *m, const float *Ms, int64_t n, int64_t Q, in
   }
 }
 
-// Near-field blocks (BF16 precisions): H_i -= sum_near N_ij Ms_j m_j with
-// FP64-class accuracy on the FP32 pipes.  The blocks were assembled in FP64
-// and are held, times Ms_j, as FP32 hi + lo pairs; products use the exact FMA
-// product split (p = a b, e = fma(a, b, -p)) and the sum is carried as an
-// unevaluated pair (hi + lo), Knuth's two-sum feeding every rounding error
-// into lo, then added to the far field and rounded once.  (GB300 executes
-// FP64 at a small fraction of its FP32 rate; this keeps ~2^-44 relative
-// accuracy at FP32 speed.)
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff ff_two_sum(float a, float b) {
-  const float s = a + b;
-  const float bb = s - a;
-  return {s, (a - (s - bb)) + (b - bb)};
-}
-__device__ __forceinline__ ff ff_add(ff acc, float p, float e) {
-  ff s = ff_two_sum(acc.hi, p);
-  s.lo += acc.lo + e;
-  const float hi = s.hi + s.lo;
-  return {hi, s.lo - (hi - s.hi)};
-}
-// threads enumerate (tile, simulation) pairs with the simulation fastest, so
-// a warp of a wide batch shares its tile's blocks (broadcast loads)
-// m element (b, j, c) sits at m[b * sb + (3 j + c) * se]: se = 1 for the
-// tile-major state, sb = 1 for the simulation-fastest copy of wide batches
-// acc += (v.hi + v.lo) * x with the error of the rounded product and of the
-// addition collected in acc.lo (a cascaded sum: no renormalisation per term,
-// acc.lo stays a few ulps of acc.hi over the <= 27 blocks of a row)
-__device__ __forceinline__ void ff_fma_lazy(ff &acc, float2 v, float x) {
-  const float p = v.x * x;
-  const float e = fmaf(v.y, x, fmaf(v.x, x, -p));
-  const float s = acc.hi + p;
-  const float bp = s - acc.hi;
-  acc.lo += ((acc.hi - (s - bp)) + (p - bp)) + e;
-  acc.hi = s;
-}
+// Near-field blocks (BF16 precisions of the streaming layout): double-FP32
+// sums (mtd::ff) of N_ij Ms_j m_j over the touching tiles, added to the far
+// field and rounded once.  Threads enumerate (tile, simulation) pairs with
+// the simulation fastest, so a warp of a wide batch shares its tile's blocks
+// (broadcast loads); m element (b, j, c) sits at m[b * sb + (3 j + c) * se]:
+// se = 1 for the tile-major state, sb = 1 for a simulation-fastest copy.
+using mtd::ff;
+using mtd::ff_add;
+using mtd::ff_fma_lazy;
 
 // FF = false (the BF16 precision, whose far part carries ~1e-4 errors):
 // plain FP32 sums of the high words, H = far - near in FP32

@@ -216,6 +216,7 @@ __host__ __device__ __forceinline__ size_t dense_x_index(int64_t b, int64_t c, i
 // Tensor maps and shape of one batched tensor-core product (dense layout).
 struct GemmPlan {
   CUtensorMap tA, tAlo, tX, tX1, tX2;  // tensor hi/lo; operand terms (split: x0, x1, x2)
+  const float *mT = nullptr;           // simulation-fastest copy of m (near blocks)
   int B = 0, Bp = 0, stages = 0;
   int kps = 1;    // K blocks per ring stage (one unit of work)
   int chunk = 4;  // units accumulated in TMEM before the FP32 promotion (4 K blocks)
@@ -427,6 +428,41 @@ __host__ __device__ __forceinline__ int64_t sk_begin(int64_t k, int64_t U, int64
 // CTA owning unit u: largest k with begin(k) <= u.
 __host__ __device__ __forceinline__ int64_t sk_owner(int64_t u, int64_t U, int64_t G) {
   return ((u + 1) * G + U - 1) / U - 1;
+}
+
+// Double-FP32 sums for the near-field blocks (BF16 precisions): H_i -= sum
+// over touching j of N_ij Ms_j m_j with FP64-class accuracy on the FP32
+// pipes.  The blocks were assembled in FP64 and are held, times Ms_j, as FP32
+// hi + lo pairs; products use the exact FMA product split (p = a b,
+// e = fma(a, b, -p)) and the sum is carried as an unevaluated pair
+// (hi + lo), Knuth's two-sum feeding every rounding error into lo, then
+// added to the far field and rounded once.  (GB300 executes FP64 at a small
+// fraction of its FP32 rate; this keeps ~2^-44 relative accuracy at FP32
+// speed.)
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_add(ff acc, float p, float e) {
+  ff s = ff_two_sum(acc.hi, p);
+  s.lo += acc.lo + e;
+  const float hi = s.hi + s.lo;
+  return {hi, s.lo - (hi - s.hi)};
+}
+// acc += (v.hi + v.lo) * x with the error of the rounded product and of the
+// addition collected in acc.lo (a cascaded sum: no renormalisation per term,
+// acc.lo stays a few ulps of acc.hi over the <= 27 blocks of a row)
+__device__ __forceinline__ void ff_fma_lazy(ff &acc, float2 v, float x) {
+  const float p = v.x * x;
+  const float e = fmaf(v.y, x, fmaf(v.x, x, -p));
+  const float s = acc.hi + p;
+  const float bp = s - acc.hi;
+  acc.lo += ((acc.hi - (s - bp)) + (p - bp)) + e;
+  acc.hi = s;
 }
 
 }  // namespace mtd

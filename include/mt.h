@@ -249,9 +249,11 @@ MT_API mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout,
  * elements go: all below the magnitude t of the element of rank k, and of
  * those equal to t the first ones in (row tile, column tile, entry xx xy xz
  * yy yz zz) order; an off-diagonal entry whose two copies the cut would
- * split is kept whole (k - 1 go), so blocks stay symmetric.  The product
- * reads 28 B per kept block (6 FP32 entries + an int32 column) and sums in
- * compensated FP32.  The
+ * split is kept whole (k - 1 go), so blocks stay symmetric.  The kept
+ * columns of a row are stored as runs of consecutive tiles (gaps of up to 3
+ * blocks filled with zeros, runs padded to 4 blocks), so the product reads
+ * 24 B per stored block (6 FP32 entries; 16 B for a single-layer tile set)
+ * plus 8 B per run, and sums in compensated FP32.  The
  * new tensor works with mt_demag_field, mt_llg_rhs, mt_energy and the
  * integrator; it keeps the tile set alive.  threshold (may be NULL) gets t,
  * kept_elements (may be NULL) the number of kept nonzero elements.

@@ -82,6 +82,7 @@ void free_tensor_mem(mt_tensor *T) {
   cudaFree(T->d_count);
   cudaFree(T->d_Hd);
   cudaFree(T->d_sp_ptr);
+  cudaFree(T->d_sp_rptr);
   cudaFree(T->d_sp_col);
   cudaFree(T->d_sp_val);
 }

@@ -182,7 +182,8 @@ __device__ __forceinline__ void write_stage_input(const StageArgs &A, float *ysn
     x[A.TC] = ms * v[1];
     x[2 * A.TC] = ms * v[2];
   } else if (A.xs_mode == 3) {
-    reinterpret_cast<float4 *>(A.xs)[(size_t)b * A.n + i] = make_float4(ms * v[0], ms * v[1], ms * v[2], 0.0f);
+    reinterpret_cast<float4 *>(A.xs)[(size_t)b * sparse_x_stride(A.n) + i] =
+        make_float4(ms * v[0], ms * v[1], ms * v[2], 0.0f);
   } else {
     __nv_bfloat16 *x1 = A.X + (size_t)A.Bp * A.Kp;  // split: second and third operand terms
     __nv_bfloat16 *x2 = x1 + (size_t)A.Bp * A.Kp;

@@ -723,7 +723,7 @@ void layout_for(int prec, mt_layout *L) {
 }
 
 int64_t xs_floats(const mt_tensor *T) {
-  if (T->layout == MT_LAYOUT_SPARSE) return 4 * T->n;  // float4 (Ms m, 0) per tile
+  if (T->layout == MT_LAYOUT_SPARSE) return 4 * sparse_x_stride(T->n);  // float4 (Ms m, 0) per tile
   const int64_t per = T->L.Q * 3 * T->L.TC;
   return T->prec == MT_F64 ? 2 * per : per;  // doubles take two floats
 }

@@ -175,9 +175,11 @@ struct mt_tensor {
   int Hd_B = 0;
   int gemm_stages[4] = {0, 0, 0, 0};  // tuned ring depth per padded batch 16/32/64/128
   // thresholded layout: block-sparse rows (kept blocks, 6 FP32 entries each)
-  int64_t sp_blocks = 0;
-  int64_t *d_sp_ptr = nullptr;  // n + 1
-  int32_t *d_sp_col = nullptr;
+  int64_t sp_blocks = 0;         // stored blocks (runs padded to 4)
+  int64_t sp_runs = 0;           // runs of consecutive columns
+  int64_t *d_sp_ptr = nullptr;   // n + 1: first block of each row
+  int64_t *d_sp_rptr = nullptr;  // n + 1: first run of each row
+  int32_t *d_sp_col = nullptr;   // 2 per run: (first block within the row, first column)
   float *d_sp_val = nullptr;
 };
 
@@ -200,6 +202,11 @@ __host__ __device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, i
   const int r = (int)(i - p * TR), c = (int)(j - q * TC);
   return (((p * Q + q) * nplane + e) * TR + r) * (int64_t)TC + c;
 }
+
+// Operand of the thresholded product: a float4 (Ms m, 0) per tile and
+// simulation, n + 4 per simulation (the last 4 zero: a run's padding blocks
+// may reach 3 columns past the last tile).
+__host__ __device__ __forceinline__ int64_t sparse_x_stride(int64_t n) { return n + 4; }
 
 // Dense layout, tile-blocked: the 3n x 3n matrix (padded to Kp = 128 k) is
 // cut into 128-row x 64-column BF16 tiles, each stored contiguously (16 KB,

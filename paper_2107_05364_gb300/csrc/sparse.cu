@@ -15,31 +15,38 @@
 // to t the first r = k - #(below t) in that order.
 //
 // Storage: block-sparse rows of tiles; a 3x3 block is kept if any of its
-// entries survives, with its 6 unique entries (dropped ones zero) and its
-// column, in increasing column order.  Row i holds K4 = ptr[i+1] - ptr[i]
-// blocks (its kept count rounded up to 4 with zero blocks of column 0):
-// columns col[ptr[i] + a], and the entries as np planes of K4 floats,
+// entries survives, with its 6 unique entries (dropped ones zero), in
+// increasing column order.  The threshold drops the blocks of distant tiles,
+// so the kept columns of a row form long runs of consecutive tiles (about
+// one per line of tiles): columns are stored as runs, not one index per
+// block.  A run starts at a kept column; later kept columns join it while
+// they are at most 4 columns past the last one (the gap is stored as zero
+// blocks); each run is padded with zero blocks to a multiple of 4.  Row i
+// holds K4 = ptr[i+1] - ptr[i] blocks as np planes of K4 floats,
 // val[np ptr[i] + e K4 + a] (np = 6, or 4 when the source is a single-layer
-// tensor without the xz and yz planes), so that every row starts on a
-// 16-byte boundary and a lane reads 4 blocks with np + 1 vector loads.
+// tensor without the xz and yz planes), and its runs rptr[i] .. rptr[i+1]-1
+// as pairs (first block a0 within the row, first column c0): block a of the
+// run has column c0 + (a - a0).  Every row and run starts on a 16-byte
+// boundary, so a lane reads 4 blocks with np vector loads and their 4
+// operands as one contiguous 64-byte stretch.
 //
 // Product: one warp per (tile row, simulation); the operand is a float4
-// (Ms m, 0) per tile, gathered from L2.  Partial sums are compensated (each
-// addition's rounding error is kept by an error-free two-sum and added back
-// at the end, Ogita, Rump and Oishi's Sum2), so the result does not depend on
-// the long per-lane summation order to more than the FP32 storage error.
+// (Ms m, 0) per tile (n + 4 per simulation, the last 4 zero for padding that
+// runs past the last tile), read from L2 in whole runs.  Partial sums are
+// compensated (each addition's rounding error is kept by an error-free
+// two-sum and added back at the end, Ogita, Rump and Oishi's Sum2), so the
+// result does not depend on the long per-lane summation order to more than
+// the FP32 storage error.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "mt_internal.cuh"
 
-// blocks per lane and step (4 measured fastest against 2; 64-thread blocks)
-constexpr int kSpmvV = 4;
-
 namespace {
 
 __device__ __forceinline__ uint32_t abs_bits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+__device__ __forceinline__ float f4_at(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
 
 // entries of the streaming FP32 layout belonging to real tiles, with their
 // multiplicity in the full matrix (diagonal 1, off-diagonal 2)
@@ -104,16 +111,23 @@ __global__ void k_row_ties(const float *D, int64_t n, int TR, int TC, int np, in
   }
 }
 
+// a later kept column joins the run when it lies at most this far past the
+// run's last kept column (the columns between are stored as zero blocks)
+constexpr int kRunJoin = 4;
+
 // Row tile i in increasing column order, one warp per row, 32 columns per
 // step.  An entry is kept if |v| > t, or if |v| == t and the copies of t up
 // to and including it (counted from tie_start[i], in column and entry order)
-// exceed r.  FILL = false: count the kept blocks into cnt[i]; FILL = true:
-// write them (slots by ballot + popc), then the row's padding blocks
-// (column 0, entries 0).  With t = 0 every nonzero entry is kept.
+// exceed r.  The kept columns are grouped into runs (see the storage note);
+// every lane walks the step's kept columns in order, so the run state is
+// the same in all lanes.  FILL = false: the row's stored blocks (runs padded
+// to 4) into cnt[i] and its runs into nrun[i]; FILL = true: each kept block
+// at its slot and each run's (first block, first column) pair (the value
+// planes were zeroed before).  With t = 0 every nonzero entry is kept.
 template <bool FILL>
 __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_t Q, uint32_t tbits,
-                       const unsigned long long *tie_start, unsigned long long r, int *cnt, const int64_t *ptr,
-                       int32_t *col, float *val) {
+                       const unsigned long long *tie_start, unsigned long long r, int *cnt, int *nrun,
+                       const int64_t *ptr, const int64_t *rptr, int32_t *run, float *val) {
   const int64_t i = blockIdx.x;
   const int lane = threadIdx.x;
   const int64_t p = i / TR;
@@ -121,8 +135,11 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_
   const int mult[6] = {1, 2, 2, 1, 2, 1};
   const int64_t o = FILL ? ptr[i] : 0, K4 = FILL ? ptr[i + 1] - o : 0;
   float *rv = FILL ? val + np * o : nullptr;  // np value planes, as the source
+  int32_t *rd = FILL ? run + 2 * rptr[i] : nullptr;
   unsigned long long carry = tie_start ? tie_start[i] : 0;
-  int64_t at = 0;
+  // run state: stored blocks before the open run, its first and last column
+  int64_t ofs = 0, col0 = -1, last = -1;
+  int64_t runs = 0;
   for (int64_t j0 = 0; j0 < n; j0 += 32) {
     const int64_t j = j0 + lane;
     float v[6] = {0, 0, 0, 0, 0, 0};
@@ -160,25 +177,38 @@ __global__ void k_rows(const float *D, int64_t n, int TR, int TC, int np, int64_
       keep = keep || k;
     }
     carry += __shfl_sync(0xffffffffu, incl, 31);
-    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    // runs: the kept columns of this step in order (the mask is the same in
+    // every lane, so is the walk)
+    unsigned mk = __ballot_sync(0xffffffffu, keep);
+    int64_t slot = -1;
+    while (mk) {
+      const int l = __ffs(mk) - 1;
+      mk &= mk - 1;
+      const int64_t jk = j0 + l;
+      if (col0 < 0 || jk - last > kRunJoin) {  // a new run
+        if (col0 >= 0) ofs += (last - col0 + 4) & ~(int64_t)3;  // close the open one, padded to 4
+        col0 = jk;
+        if (FILL && lane == 0) {
+          rd[2 * runs] = (int32_t)ofs;
+          rd[2 * runs + 1] = (int32_t)jk;
+        }
+        ++runs;
+      }
+      if (l == lane) slot = ofs + (jk - col0);
+      last = jk;
+    }
     if (FILL && keep) {
-      const int64_t a = at + __popc(mask & ((1u << lane) - 1u));
-      col[o + a] = (int32_t)j;
 #pragma unroll
       for (int e = 0; e < 6; ++e) {
         const int pl = stream_plane(e, np);
-        if (pl >= 0) rv[pl * K4 + a] = v[e];
+        if (pl >= 0) rv[pl * K4 + slot] = v[e];
       }
     }
-    at += __popc(mask);
   }
-  if constexpr (!FILL) {
-    if (lane == 0) cnt[i] = (int)at;
-  } else {
-    for (int64_t a = at + lane; a < K4; a += 32) {
-      col[o + a] = 0;
-      for (int pl = 0; pl < np; ++pl) rv[pl * K4 + a] = 0.0f;
-    }
+  if (col0 >= 0) ofs += (last - col0 + 4) & ~(int64_t)3;
+  if (!FILL && lane == 0) {
+    cnt[i] = (int)ofs;
+    nrun[i] = (int)runs;
   }
 }
 
@@ -190,7 +220,9 @@ __device__ __forceinline__ void sum2_add(float &s, float &c, float t) {
   s = u;
 }
 
-__device__ __forceinline__ float warp_sum2(float s, float c) {
+// the warp's (sum, error) pairs combined into lane 0's (s, c) (and every
+// lane's: butterfly), errors carried
+__device__ __forceinline__ void warp_sum2_pair(float &s, float &c) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const float so = __shfl_xor_sync(0xffffffffu, s, off);
@@ -198,83 +230,89 @@ __device__ __forceinline__ float warp_sum2(float s, float c) {
     c += co;
     sum2_add(s, c, so);
   }
-  return s + c;
 }
 
-// V consecutive blocks of one row as vectors
-template <int V> struct Vec;
-template <> struct Vec<4> {
-  using F = float4;
-  using I = int4;
-  static __device__ __forceinline__ float at(const F &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
-  static __device__ __forceinline__ int at(const I &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
-};
 
 // H_i = -sum_kept N_ij Ms_j m_j; one warp per (row, simulation), rows of one
-// simulation consecutive; xs = float4 (Ms m, 0) per tile and simulation; each
-// lane takes V consecutive blocks per step (7 vector loads, V gathers)
-template <int V, int NP>
+// simulation consecutive; xs = float4 (Ms m, 0) per tile, n + 4 per
+// simulation; each lane takes 4 consecutive blocks of one run per step (NP
+// vector loads of the values and 4 contiguous operands) and follows the
+// row's runs with a cursor of its own.  (Lanes on interleaved blocks, for
+// wider contiguous loads, needed a cursor walk per block and measured 2.4x
+// slower.)
+template <int NP>
 __global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
-                                             const int32_t *__restrict__ col, const float *__restrict__ val,
-                                             const float4 *__restrict__ xs, float *H, const int *active) {
+                                             const int64_t *__restrict__ rptr, const int2 *__restrict__ run,
+                                             const float *__restrict__ val, const float4 *__restrict__ xs, float *H,
+                                             const int *active) {
   mtd::pdl_enter();
-  using VF = typename Vec<V>::F;
-  using VI = typename Vec<V>::I;
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (wid >= n * B) return;
   const int64_t i = wid % n;
   const int b = (int)(wid / n);
   if (active && !active[b]) return;
-  const float4 *xb = xs + (size_t)b * n;
+  const float4 *xb = xs + (size_t)b * sparse_x_stride(n);
   const int64_t o = ptr[i], K4 = ptr[i + 1] - o;
   const float *rv = val + NP * o;
-  const int32_t *rc = col + o;
+  const int64_t r1 = rptr[i + 1];
+  int64_t rc = rptr[i];  // this lane's run
+  int2 cur = rc < r1 ? run[rc] : make_int2(0, 0);
+  int64_t next = rc + 1 < r1 ? run[rc + 1].x : INT64_MAX;  // first block of the following run
   float sx = 0, cx = 0, sy = 0, cy = 0, sz = 0, cz = 0;
-  for (int64_t a = V * (int64_t)lane; a < K4; a += 32 * V) {
-    const VI jj = *reinterpret_cast<const VI *>(rc + a);
-    VF v[NP];
+  for (int64_t a = 4 * (int64_t)lane; a < K4; a += 128) {
+    // the values stream past (read once: no L1 allocation); the operands,
+    // read by every row, stay cached
+    float4 v[NP];
 #pragma unroll
-    for (int e = 0; e < NP; ++e) v[e] = *reinterpret_cast<const VF *>(rv + e * K4 + a);
-    float4 x[V];
+    for (int e = 0; e < NP; ++e) v[e] = __ldcs(reinterpret_cast<const float4 *>(rv + e * K4 + a));
+    while (a >= next) {
+      ++rc;
+      cur = run[rc];
+      next = rc + 1 < r1 ? run[rc + 1].x : INT64_MAX;
+    }
+    const int64_t c = cur.y + (a - cur.x);  // column of block a
+    float4 x[4];
 #pragma unroll
-    for (int q = 0; q < V; ++q) x[q] = xb[Vec<V>::at(jj, q)];
+    for (int q = 0; q < 4; ++q) x[q] = xb[c + q];
 #pragma unroll
-    for (int q = 0; q < V; ++q) {
+    for (int q = 0; q < 4; ++q) {
       if constexpr (NP == 6) {
         // per block: (v0 v1 v2; v1 v3 v4; v2 v4 v5) (x, y, z)
-        const float n0 = Vec<V>::at(v[0], q), n1 = Vec<V>::at(v[1], q), n2 = Vec<V>::at(v[2], q);
-        const float n3 = Vec<V>::at(v[3], q), n4 = Vec<V>::at(v[4], q), n5 = Vec<V>::at(v[5], q);
+        const float n0 = f4_at(v[0], q), n1 = f4_at(v[1], q), n2 = f4_at(v[2], q);
+        const float n3 = f4_at(v[3], q), n4 = f4_at(v[4], q), n5 = f4_at(v[5], q);
         sum2_add(sx, cx, fmaf(n0, x[q].x, fmaf(n1, x[q].y, n2 * x[q].z)));
         sum2_add(sy, cy, fmaf(n1, x[q].x, fmaf(n3, x[q].y, n4 * x[q].z)));
         sum2_add(sz, cz, fmaf(n2, x[q].x, fmaf(n4, x[q].y, n5 * x[q].z)));
       } else {
         // single-layer tensor: (v0 v1 0; v1 v2 0; 0 0 v3) (x, y, z)
-        const float n0 = Vec<V>::at(v[0], q), n1 = Vec<V>::at(v[1], q);
-        const float n3 = Vec<V>::at(v[2], q), n5 = Vec<V>::at(v[3], q);
+        const float n0 = f4_at(v[0], q), n1 = f4_at(v[1], q);
+        const float n3 = f4_at(v[2], q), n5 = f4_at(v[3], q);
         sum2_add(sx, cx, fmaf(n0, x[q].x, n1 * x[q].y));
         sum2_add(sy, cy, fmaf(n1, x[q].x, n3 * x[q].y));
         sum2_add(sz, cz, __fmul_rn(n5, x[q].z));  // a rounded product, as in the 6-plane form
       }
     }
   }
-  const float hx = warp_sum2(sx, cx), hy = warp_sum2(sy, cy), hz = warp_sum2(sz, cz);
+  warp_sum2_pair(sx, cx);
+  warp_sum2_pair(sy, cy);
+  warp_sum2_pair(sz, cz);
   if (lane == 0) {
     float *Hb = H + (size_t)b * 3 * n + 3 * i;
-    Hb[0] = -hx;
-    Hb[1] = -hy;
-    Hb[2] = -hz;
+    Hb[0] = -(sx + cx);
+    Hb[1] = -(sy + cy);
+    Hb[2] = -(sz + cz);
   }
 }
 
-// xs[b][j] = (Ms_j m_j, 0)
+// xs[b][j] = (Ms_j m_j, 0) (the 4 padding entries per simulation stay zero)
 __global__ void k_prep_sparse_x(const float *m, const float *Ms, int64_t n, int B, float4 *xs) {
   const int64_t tot = (int64_t)B * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = t % n;
+    const int64_t b = t / n, j = t - b * n;
     const float ms = Ms[j];
     const float *mj = m + 3 * t;
-    xs[t] = make_float4(ms * mj[0], ms * mj[1], ms * mj[2], 0.0f);
+    xs[b * sparse_x_stride(n) + j] = make_float4(ms * mj[0], ms * mj[1], ms * mj[2], 0.0f);
   }
 }
 
@@ -302,13 +340,14 @@ void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int
   const int64_t warps = T->n * (int64_t)B;
   const dim3 grid((unsigned)((warps + 1) / 2));
   const int64_t *ptr = (const int64_t *)T->d_sp_ptr;
-  const int32_t *col = (const int32_t *)T->d_sp_col;
+  const int64_t *rptr = (const int64_t *)T->d_sp_rptr;
+  const int2 *run = reinterpret_cast<const int2 *>(T->d_sp_col);
   const float *val = (const float *)T->d_sp_val;
   const float4 *x4 = reinterpret_cast<const float4 *>(xs);
   if (T->L.nplane == 4)
-    mt::launch_pdl(k_spmv<kSpmvV, 4>, grid, dim3(64), 0, s, T->n, B, ptr, col, val, x4, H, active);
+    mt::launch_pdl(k_spmv<4>, grid, dim3(64), 0, s, T->n, B, ptr, rptr, run, val, x4, H, active);
   else
-    mt::launch_pdl(k_spmv<kSpmvV, 6>, grid, dim3(64), 0, s, T->n, B, ptr, col, val, x4, H, active);
+    mt::launch_pdl(k_spmv<6>, grid, dim3(64), 0, s, T->n, B, ptr, rptr, run, val, x4, H, active);
 }
 
 void launch_prep_sparse_x(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
@@ -378,18 +417,23 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     }
     MT_CUDA(cudaMemcpy(d_tie, ties.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice));
   }
-  // kept blocks per row
-  DevTemp<int> cnt_rows;
+  // stored blocks and runs per row
+  DevTemp<int> cnt_rows, run_rows;
   MT_CUDA(cnt_rows.alloc(n));
-  int *d_cnt = cnt_rows.p;
-  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, d_cnt, nullptr, nullptr,
-                                     nullptr);
+  MT_CUDA(run_rows.alloc(n));
+  int *d_cnt = cnt_rows.p, *d_nrun = run_rows.p;
+  k_rows<false><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, d_cnt, d_nrun, nullptr,
+                                     nullptr, nullptr, nullptr);
   MT_CUDA(cudaGetLastError());
-  std::vector<int> cnt(n);
+  std::vector<int> cnt(n), nrun(n);
   MT_CUDA(cudaMemcpy(cnt.data(), d_cnt, sizeof(int) * n, cudaMemcpyDeviceToHost));
-  std::vector<int64_t> ptr(n + 1, 0);
-  for (int64_t i = 0; i < n; ++i) ptr[i + 1] = ptr[i] + ((cnt[i] + 3) & ~3);
-  const int64_t nnzb = ptr[n];
+  MT_CUDA(cudaMemcpy(nrun.data(), d_nrun, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  std::vector<int64_t> ptr(n + 1, 0), rptr(n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    ptr[i + 1] = ptr[i] + cnt[i];  // runs are padded to 4 blocks already
+    rptr[i + 1] = rptr[i] + nrun[i];
+  }
+  const int64_t nnzb = ptr[n], nruns = rptr[n];
   mt_ctx *ctx = T->tiles->ctx;
   mt_tensor *S = new mt_tensor();
   S->tiles = T->tiles;
@@ -399,8 +443,10 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   S->n = n;
   S->L = T->L;
   S->sp_blocks = nnzb;
+  S->sp_runs = nruns;
   const int np = T->L.nplane;  // value planes: those the source stores (6, or 4 for a single layer)
-  S->bytes = sizeof(int64_t) * (n + 1) + (sizeof(int32_t) + np * sizeof(float)) * (size_t)std::max<int64_t>(1, nnzb);
+  S->bytes = 2 * sizeof(int64_t) * (n + 1) + 2 * sizeof(int32_t) * (size_t)std::max<int64_t>(1, nruns) +
+             np * sizeof(float) * (size_t)std::max<int64_t>(1, nnzb);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->in_use + S->bytes > ctx->budget) {
@@ -413,15 +459,19 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
     ctx->in_use += S->bytes;
   }
   cudaError_t e = cudaMalloc(&S->d_sp_ptr, sizeof(int64_t) * (n + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_col, sizeof(int32_t) * std::max<int64_t>(1, nnzb));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_rptr, sizeof(int64_t) * (n + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_col, 2 * sizeof(int32_t) * std::max<int64_t>(1, nruns));
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_val, np * sizeof(float) * std::max<int64_t>(1, nnzb));
   if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_ptr, ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_rptr, rptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+  // gap and padding blocks are zero
+  if (e == cudaSuccess) e = cudaMemset(S->d_sp_val, 0, np * sizeof(float) * std::max<int64_t>(1, nnzb));
   if (e != cudaSuccess) {
     mt::tensor_release(S);
     return mt::cuda_fail(e, "mt_tensor_threshold allocation", __FILE__, __LINE__);
   }
-  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, nullptr, S->d_sp_ptr,
-                                    S->d_sp_col, S->d_sp_val);
+  k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, nullptr, nullptr,
+                                    S->d_sp_ptr, S->d_sp_rptr, S->d_sp_col, S->d_sp_val);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -458,26 +508,32 @@ namespace mt {
 // rows [i0, i1) of a thresholded tensor as dense FP64 blocks
 mt_status read_rows_sparse(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
   const int64_t n = T->n;
-  std::vector<int64_t> ptr(i1 - i0 + 1);
+  std::vector<int64_t> ptr(i1 - i0 + 1), rptr(i1 - i0 + 1);
   MT_CUDA(cudaMemcpy(ptr.data(), T->d_sp_ptr + i0, sizeof(int64_t) * (i1 - i0 + 1), cudaMemcpyDeviceToHost));
-  const int64_t a0 = ptr[0], a1 = ptr[i1 - i0];
-  std::vector<int32_t> col(std::max<int64_t>(1, a1 - a0));
+  MT_CUDA(cudaMemcpy(rptr.data(), T->d_sp_rptr + i0, sizeof(int64_t) * (i1 - i0 + 1), cudaMemcpyDeviceToHost));
+  const int64_t a0 = ptr[0], a1 = ptr[i1 - i0], q0 = rptr[0], q1 = rptr[i1 - i0];
+  std::vector<int32_t> run(2 * std::max<int64_t>(1, q1 - q0));
   const int np = T->L.nplane;
   std::vector<float> val(np * std::max<int64_t>(1, a1 - a0));
   if (a1 > a0) {
-    MT_CUDA(cudaMemcpy(col.data(), T->d_sp_col + a0, sizeof(int32_t) * (a1 - a0), cudaMemcpyDeviceToHost));
+    MT_CUDA(cudaMemcpy(run.data(), T->d_sp_col + 2 * q0, 2 * sizeof(int32_t) * (q1 - q0), cudaMemcpyDeviceToHost));
     MT_CUDA(cudaMemcpy(val.data(), T->d_sp_val + np * a0, np * sizeof(float) * (a1 - a0), cudaMemcpyDeviceToHost));
   }
   std::memset(out, 0, sizeof(double) * 6 * (size_t)(i1 - i0) * n);
   for (int64_t i = i0; i < i1; ++i) {
     const int64_t o = ptr[i - i0], K4 = ptr[i - i0 + 1] - o;
     const float *rv = val.data() + np * (o - a0);
-    for (int64_t a = 0; a < K4; ++a) {
-      const int64_t j = col[o - a0 + a];
-      // padding blocks are zero and add nothing
-      for (int e = 0; e < 6; ++e) {
-        const int pl = stream_plane(e, np);
-        if (pl >= 0) out[((i - i0) * n + j) * 6 + e] += rv[pl * K4 + a];
+    const int64_t rb = rptr[i - i0] - q0, re = rptr[i - i0 + 1] - q0;
+    for (int64_t q = rb; q < re; ++q) {
+      const int64_t b0 = run[2 * q], c0 = run[2 * q + 1];
+      const int64_t b1 = q + 1 < re ? run[2 * (q + 1)] : K4;
+      for (int64_t a = b0; a < b1; ++a) {
+        const int64_t j = c0 + (a - b0);
+        if (j >= n) break;  // padding past the last tile (zero)
+        for (int e = 0; e < 6; ++e) {
+          const int pl = stream_plane(e, np);
+          if (pl >= 0) out[((i - i0) * n + j) * 6 + e] += rv[pl * K4 + a];
+        }
       }
     }
   }

@@ -449,20 +449,18 @@ mt_status make_map(CUtensorMap *map, const void *base, uint64_t cols, uint64_t r
   return MT_OK;
 }
 
-#ifndef MT_GEMM_KPS_SPLIT
-#define MT_GEMM_KPS_SPLIT 2
-#endif
+// Tile shape along K: the K blocks (64 columns each) one ring stage holds,
+// 1 or 2 (a stage of 16 or 32 KB of tensor per plane), chosen by the
+// autotuner together with the ring depth; the split product at a padded
+// batch of 128 holds one (two would need 160 KB a stage: no room for two).
+constexpr int kps_max(bool split, int Bp) { return split && Bp > 64 ? 1 : 2; }
 
-// K blocks per ring stage (see kps_of below); the split product at a padded
-// batch of 128 holds one (two would need 160 KB a stage: no room for two)
-constexpr int kps_for(bool split, int Bp) { return split ? (Bp > 64 ? 1 : MT_GEMM_KPS_SPLIT) : 2; }
-
-int stage_bytes_for(int Bp, bool split) {
-  return kps_for(split, Bp) * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
+int stage_bytes_for(int Bp, bool split, int kps) {
+  return kps * (split ? 2 * GM * GK * 2 + 3 * Bp * GK * 2 : GM * GK * 2 + Bp * GK * 2);
 }
 
-int stages_for(int Bp, bool split) {
-  const int stage = stage_bytes_for(Bp, split);
+int stages_for(int Bp, bool split, int kps) {
+  const int stage = stage_bytes_for(Bp, split, kps);
   const int budget = 224 * 1024;
   return std::max(2, std::min(8, budget / stage));  // >= 2 stages always fit (stage <= 112 KB)
 }
@@ -493,19 +491,18 @@ size_t dense_part_bytes(const mt_tensor *T, int B) {
 }
 size_t dense_count_bytes(const mt_tensor *T) { return (size_t)(T->Kp / GM) * EPI_WARPS * sizeof(int); }
 
-// K blocks per ring stage: two (measured: the per-stage handshakes of the
-// TMA, MMA and commit path cost a fixed few hundred cycles, so 16 KB tiles
-// alone left the BF16 product at 0.70 of HBM and two per stage reach 0.87;
-// the split product goes from 0.73 to 0.83 with a 2-deep ring of 112 KB)
-template <bool SPLIT, int BP>
-constexpr int kps_of() {
-  return kps_for(SPLIT, BP);
-}
-
+// (Measured when a stage first held two K blocks: the per-stage handshakes
+// of the TMA, MMA and commit path cost a fixed few hundred cycles, so 16 KB
+// tiles alone left the BF16 product at 0.70 of HBM and two per stage reached
+// 0.87; the split product went from 0.73 to 0.83 with a 2-deep ring of
+// 112 KB.  Both shapes stay candidates of the autotuner.)
 template <bool SPLIT, int BP>
 cudaError_t prep_one() {
-  return cudaFuncSetAttribute(k_gemm<SPLIT, BP, kps_of<SPLIT, BP>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm<SPLIT, BP, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024);
+  if (e == cudaSuccess && kps_max(SPLIT, BP) == 2)
+    e = cudaFuncSetAttribute(k_gemm<SPLIT, BP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  return e;
 }
 
 cudaError_t gemm_prepare() {
@@ -555,46 +552,60 @@ mt_status gemm_plan(const mt_tensor *T, int B, const void *X, GemmPlan *plan) {
   plan->B = B;
   plan->Bp = Bp;
   plan->split = split;
-  plan->stages = stages_for(Bp, split);
-  plan->kps = kps_for(split, Bp);
+  plan->kps = kps_max(split, Bp);
+  plan->stages = stages_for(Bp, split, plan->kps);
   plan->chunk = 4 / plan->kps;  // units per accumulator chunk: 4 K blocks either way
   return MT_OK;
 }
 
+// The autotuner: per tensor and padded batch width, time the product for
+// each tile shape along K (1 or 2 K blocks per ring stage) and three ring
+// depths (the deepest that fits in shared memory and one and two stages
+// shallower) and keep the fastest; numerics do not depend on the choice.
 mt_status gemm_tune(mt_tensor *T, GemmPlan *plan, float *H, float *part, int *count, int *status, cudaStream_t s) {
   int key = 0;
   while ((16 << key) < plan->Bp) ++key;
   if (T->gemm_stages[key] > 0) {
     plan->stages = T->gemm_stages[key];
+    plan->kps = T->gemm_kps[key];
+    plan->chunk = 4 / plan->kps;
     return MT_OK;
   }
-  const int smax = stages_for(plan->Bp, plan->split);
-  int cand[3] = {smax, std::max(2, smax - 1), std::max(2, smax - 2)};
   cudaEvent_t e0, e1;
   MT_CUDA(cudaEventCreate(&e0));
   MT_CUDA(cudaEventCreate(&e1));
   float best_ms = 1e30f;
-  int best = smax;
-  for (int c = 0; c < 3; ++c) {
-    if (c > 0 && cand[c] == cand[c - 1]) continue;
-    plan->stages = cand[c];
-    launch_gemm(T, *plan, H, part, count, nullptr, status, s);  // warm
-    MT_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) launch_gemm(T, *plan, H, part, count, nullptr, status, s);
-    MT_CUDA(cudaEventRecord(e1, s));
-    MT_CUDA(cudaEventSynchronize(e1));
-    float ms = 0.0f;
-    MT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = cand[c];
+  int best = 0, best_kps = plan->kps;
+  for (int kps = kps_max(plan->split, plan->Bp); kps >= 1; --kps) {
+    const int smax = stages_for(plan->Bp, plan->split, kps);
+    const int cand[3] = {smax, std::max(2, smax - 1), std::max(2, smax - 2)};
+    for (int c = 0; c < 3; ++c) {
+      if (c > 0 && cand[c] == cand[c - 1]) continue;
+      plan->kps = kps;
+      plan->chunk = 4 / kps;
+      plan->stages = cand[c];
+      launch_gemm(T, *plan, H, part, count, nullptr, status, s);  // warm
+      MT_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) launch_gemm(T, *plan, H, part, count, nullptr, status, s);
+      MT_CUDA(cudaEventRecord(e1, s));
+      MT_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      MT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand[c];
+        best_kps = kps;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   MT_CUDA(cudaGetLastError());
   T->gemm_stages[key] = best;
+  T->gemm_kps[key] = best_kps;
   plan->stages = best;
+  plan->kps = best_kps;
+  plan->chunk = 4 / best_kps;
   return MT_OK;
 }
 
@@ -609,7 +620,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   P.Bp = plan.Bp;
   P.chunk = plan.chunk;
   P.stages = plan.stages;
-  P.stage_bytes = stage_bytes_for(plan.Bp, plan.split);
+  P.stage_bytes = stage_bytes_for(plan.Bp, plan.split, plan.kps);
   const bool stack = plan.split && plan.Bp <= 64;
   const int acc_cols = stack ? 3 * plan.Bp : plan.Bp;
   const int na = stack ? (plan.Bp == 64 ? 2 : 4) : (plan.Bp <= 64 ? 2 * NACC : NACC);  // as GemmShape
@@ -624,9 +635,16 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
   const int64_t U = P.MT * P.KBU;
   const int grid = (int)std::min<int64_t>(matvec_grid(T), U);
   const size_t smem = (size_t)P.stages * P.stage_bytes + 1024 + 512;  // + alignment slack, barriers
-#define MT_GEMM_LAUNCH(SP, BPV)                                                                              \
-  mt::launch_pdl(k_gemm<SP, BPV, kps_of<SP, BPV>()>, dim3(grid), dim3(GEMM_THREADS), smem, s, plan.tA, plan.tAlo, \
-                 plan.tX, plan.tX1, plan.tX2, P)
+#define MT_GEMM_LAUNCH_K(SP, BPV, K)                                                                            \
+  mt::launch_pdl(k_gemm<SP, BPV, K>, dim3(grid), dim3(GEMM_THREADS), smem, s, plan.tA, plan.tAlo, plan.tX, plan.tX1, \
+                 plan.tX2, P)
+#define MT_GEMM_LAUNCH(SP, BPV)                          \
+  do {                                                   \
+    if (plan.kps == 2 && kps_max(SP, BPV) == 2)          \
+      MT_GEMM_LAUNCH_K(SP, BPV, kps_max(SP, BPV));       \
+    else                                                 \
+      MT_GEMM_LAUNCH_K(SP, BPV, 1);                      \
+  } while (0)
   if (plan.split) {
     switch (plan.Bp) {
       case 16: MT_GEMM_LAUNCH(true, 16); break;
@@ -643,6 +661,7 @@ void launch_gemm(const mt_tensor *T, const GemmPlan &plan, float *H, float *part
     }
   }
 #undef MT_GEMM_LAUNCH
+#undef MT_GEMM_LAUNCH_K
 }
 
 }  // namespace mt

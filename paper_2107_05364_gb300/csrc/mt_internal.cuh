@@ -174,6 +174,7 @@ struct mt_tensor {
   float *d_Hd = nullptr;
   int Hd_B = 0;
   int gemm_stages[4] = {0, 0, 0, 0};  // tuned ring depth per padded batch 16/32/64/128
+  int gemm_kps[4] = {0, 0, 0, 0};     // tuned K blocks per ring stage (tile shape along K)
   // thresholded layout: block-sparse rows (kept blocks, 6 FP32 entries each)
   int64_t sp_blocks = 0;         // stored blocks (runs padded to 4)
   int64_t sp_runs = 0;           // runs of consecutive columns

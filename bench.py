@@ -45,7 +45,16 @@ MU0 = 4e-7 * math.pi
 # padding of the last chunk row); 4 planes (the single-layer film)
 # 1,618,193,152 + 2,841,856 (1.0131 x 1.6e9).  Valid while k_matvec<f32> is
 # unchanged.
-MATVEC_F32_N10000_TRAFFIC = {6: 2427094016 + 2980864, 4: 1618193152 + 2841856}
+MATVEC_F32_N10000_TRAFFIC = {6: 2427094016 + 2980864, 4: 1618193152 + 2841856}  # tensors storing every block
+
+
+def f32_alg_bytes(info, n):
+    """Algorithmic bytes of one FP32 streaming product: every unique stored
+    value read once -- the stored entry planes of every block, or of the
+    upper triangle (n (n + 1) / 2 blocks) when the tensor of a tile set of
+    one shape is stored half (N_ij = N_ji)."""
+    blocks = n * (n + 1) / 2.0 if info.get("half") else float(n) * n
+    return 4.0 * info["planes"] * blocks
 # The tensor-core products at n = 8,000 read 1.0040 (split) and 1.0028 (BF16)
 # x their stored tensors and wrote their fields (one ncu capture each of the
 # current kernels); the batched line scales that per stored byte.
@@ -251,7 +260,7 @@ def run_ours(args):
     # the stored FP32 entries of a 3x3 block, each read once: 6, or 4 for a
     # single-layer film (xz and yz vanish)
     planes = info["planes"]
-    alg_bytes = 4.0 * planes * n * n
+    alg_bytes = f32_alg_bytes(info, n)
     peaks, kind = _peaks()
     # the product's duration inside the timed step: at most the step time
     # over its six products (the stage kernels take the rest), so the
@@ -295,8 +304,10 @@ def run_ours(args):
         # the same film, one simulation, with the tensor stored in the other
         # streaming precisions (BF16 with per-block scales, split BF16)
         prec_rows = {}
-        for pname in ("f32_six_planes", "bf16", "split"):
-            if pname == "f32_six_planes":
+        for pname in ("f32_every_block", "f32_six_planes", "bf16", "split"):
+            if pname == "f32_every_block":  # 4 planes, every block stored (no use of N_ij = N_ji)
+                Tp = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)
+            elif pname == "f32_six_planes":  # 6 planes, every block stored
                 Tp = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM6)
             else:
                 Tp = mt.mt_demag_assemble(tiles, pname)
@@ -339,11 +350,15 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": film_config(n, world),
         "precision": "f32 storage, f32 accumulate, f64 assembly", "stored_planes": planes,
+        "stored_half": bool(info["half"]),
         "sms": torch.cuda.get_device_properties(dev).multi_processor_count,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
-                     "traffic": MATVEC_F32_N10000_TRAFFIC.get(planes) if n == 10000 else None,
-                     "kernel": "k_matvec<f32>" if planes == 6 else "k_matvec<f32, 4 planes>",
+                     "traffic": MATVEC_F32_N10000_TRAFFIC.get(planes) if n == 10000 and not info["half"] else None,
+                     "kernel": ("k_matvec<f32" + (", 4 planes" if planes == 4 else "") +
+                                (", half> + k_half_cols" if info["half"] else ">")),
+                     "stored": "upper triangle of blocks (N_ij = N_ji: tiles of one shape)" if info["half"]
+                     else "every block",
                      "peak_kind": kind, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": launch_ms,
                      "launch_ms_source": "timed step (CUDA events) / 6 products: an upper bound of the "
@@ -578,7 +593,9 @@ def run_threshold(args):
     n = t.n
     ctx = mt.mt_ctx_create(0)
     tiles = mt.mt_tiles_create(ctx, t)
-    T = mt.mt_demag_assemble(tiles, "f32")
+    # thresholding works on a tensor with every block stored; the half
+    # storage of this film (N_ij = N_ji) is timed beside it at the end
+    T = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)
     # a relaxed start (the s-state route: relax from near (1,1,1))
     p0, k0 = mt.llg_params(1, alpha=0.5)
     I = mt.Integrator(T, p0, mt.ode_opts(rtol=1e-5, atol=1e-5))
@@ -642,10 +659,29 @@ def run_threshold(args):
         mt.mt_demag_field(T, mg, H0)
     e1.record()
     torch.cuda.synchronize()
+    dense_ms = e0.elapsed_time(e1) / 20
+    # the default storage of this film: the upper triangle only
+    Th = mt.mt_demag_assemble(tiles, "f32")
+    Hh = torch.empty_like(mg)
+    for _ in range(3):
+        mt.mt_demag_field(Th, mg, Hh)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(20):
+        mt.mt_demag_field(Th, mg, Hh)
+    e1.record()
+    torch.cuda.synchronize()
+    half_ms = e0.elapsed_time(e1) / 20
+    half_err = float(np.linalg.norm(Hh.cpu().numpy() - H0n) / np.linalg.norm(H0n))
+    half_info = Th.info()
+    Th.close()
     line = {"metric": "thresholded tensor: product time vs field error", "value": rows[3]["product_ms"],
             "unit": "ms (40 % threshold)", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
             "config": {"workload": "sp4_film_160x40x1_n6400_threshold"},
-            "dense_fp32_product_ms": e0.elapsed_time(e1) / 20, "dense_fp32_field_rel_err": dense_err,
+            "dense_fp32_product_ms": dense_ms, "dense_fp32_field_rel_err": dense_err,
+            "dense_fp32_bytes": T.info()["bytes"],
+            "half_fp32_product_ms": half_ms, "half_fp32_field_rel_err": half_err,
+            "half_fp32_bytes": half_info["bytes"], "half_stored": bool(half_info["half"]),
             "dense_dynamics_s": ref_wall, "rows": rows}
     print(json.dumps(line), flush=True)
 
@@ -828,7 +864,8 @@ def run_tetra(args):
         torch.cuda.synchronize()
         step_ms = e0.elapsed_time(e1) / 100
         out[name] = {"tiles": tiles.n, "assemble_s": t_asm, "blocks_per_s": tiles.n ** 2 / t_asm,
-                     "product_ms": ms, "product_gbs": 4.0 * T.info()["planes"] * tiles.n ** 2 / (ms * 1e-3) / 1e9,
+                     "product_ms": ms, "product_gbs": f32_alg_bytes(T.info(), tiles.n) / (ms * 1e-3) / 1e9,
+                     "stored_half": bool(T.info()["half"]),
                      "rhs_evals_per_s": 6.0 / (step_ms * 1e-3)}
         I.close()
         T.close()
@@ -1088,7 +1125,7 @@ def run_cube(args):
     mg = torch.tensor(m0.ravel(), device="cuda")
     H = torch.empty_like(mg)
     alone, graph = _product_times(mt, T, mg, H, B)
-    alg = 4.0 * info["planes"] * n * n  # the stored FP32 entries, read once per group of <= 4 simulations
+    alg = f32_alg_bytes(info, n)  # the stored FP32 entries, read once per group of <= 4 simulations
     peaks, kind = _peaks()
     peak = float(peaks["hbm_gbs"])
     launch = graph if graph is not None else alone

@@ -81,8 +81,10 @@ typedef enum {
                         /* MT_BF16_SCALED (scales fixed to 1) and MT_BF16_SPLIT */
   MT_LAYOUT_SPARSE = 2, /* thresholded FP32 tensor in block-sparse rows       */
                         /* (made by mt_tensor_threshold, Sec. 4.3.1)            */
-  MT_LAYOUT_STREAM6 = 3 /* MT_LAYOUT_STREAM with all 6 entry planes stored     */
-                        /* even where two vanish (see mt_demag_assemble)        */
+  MT_LAYOUT_STREAM6 = 3, /* MT_LAYOUT_STREAM with all 6 entry planes and every  */
+                        /* block stored (see mt_demag_assemble)                */
+  MT_LAYOUT_STREAM_FULL = 4 /* MT_LAYOUT_STREAM with every block stored (no use  */
+                        /* of N_ij = N_ji; planes as for MT_LAYOUT_STREAM)      */
 } mt_layout_kind;
 
 /* Equation-of-motion form. */
@@ -150,6 +152,9 @@ typedef struct {
                        /* split 12 (8 single-layer), dense 9                  */
   int64_t bytes;       /* device bytes of the stored tensor                   */
   int64_t near_blocks; /* FP64 near-field blocks kept apart (0 if none)       */
+  int32_t half;        /* 1: only the upper triangle of blocks is stored      */
+                       /* (N_ij = N_ji, see mt_demag_assemble)                */
+  int32_t pad;
 } mt_tensor_info;
 
 /* ---------------------------------------------------------------------- */
@@ -231,7 +236,18 @@ MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **ou
  * provided that every assembled |N_xz|, |N_yz| is at most 1e-12
  * (their FP64 round-off; otherwise all 6 planes are stored).  Products,
  * row reads and thresholding treat the missing entries as zeros.
- * MT_LAYOUT_STREAM6 keeps the 6 planes. */
+ * MT_LAYOUT_STREAM6 keeps the 6 planes.
+ * Tiles of one shape.  When every cuboid has the same edges, the point
+ * tensor of tile j at the centre of tile i depends only on c_i - c_j and is
+ * even in it, so N_ij = N_ji and the whole tensor is symmetric (Sec. 3.2).
+ * An FP32 streaming tensor of more than 2,048 such tiles then stores only
+ * the upper triangle: 16-row panel p keeps its 128-column chunks from the
+ * one holding its own rows on (about n^2 / 2 blocks); the product applies
+ * each off-diagonal chunk to its rows and, transposed, to its columns (a
+ * column work area of 1.5 KB per stored chunk and simulation, held by the
+ * tensor or the integrator).  mt_tensor_info.half tells;
+ * MT_LAYOUT_STREAM_FULL stores every block.  Thresholding and the
+ * allocation-free product need every block stored. */
 /* As mt_demag_assemble, with an explicit storage layout (mt_layout_kind).
  * MT_LAYOUT_DENSE turns every product over a batch of B simulations into a
  * GEMM on the tensor cores (tcgen05, BF16 in, FP32 accumulate); the rows and

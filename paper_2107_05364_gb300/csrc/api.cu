@@ -81,6 +81,7 @@ void free_tensor_mem(mt_tensor *T) {
   cudaFree(T->d_part);
   cudaFree(T->d_count);
   cudaFree(T->d_Hd);
+  cudaFree(T->d_colpart);
   cudaFree(T->d_sp_ptr);
   cudaFree(T->d_sp_rptr);
   cudaFree(T->d_sp_col);
@@ -107,6 +108,13 @@ mt_status ensure_workspace(mt_tensor *T, int B) {
   }
   if (!T->d_part) {
     MT_CUDA(cudaMalloc(&T->d_part, dense ? mt::dense_part_bytes(T, B) : mt::matvec_part_bytes(T)));
+  }
+  if (T->L.half && T->colpart_B < B) {  // half storage: column work area (grows with B)
+    cudaFree(T->d_colpart);
+    T->d_colpart = nullptr;
+    T->colpart_B = 0;
+    MT_CUDA(cudaMalloc(&T->d_colpart, mt::matvec_colpart_bytes(T, B)));
+    T->colpart_B = B;
   }
   if (T->count_B < B) {
     cudaFree(T->d_count);
@@ -144,7 +152,7 @@ mt_status demag_apply(mt_tensor *T, const float *m, int B, float *H, cudaStream_
     mt::launch_near(T, mt::dense_mT(T, B, T->d_xs), 1, mt::dense_pad_batch(B), B, H, nullptr, s);
   } else {
     mt::launch_prep_xs(T, m, B, T->d_xs, s);
-    mt::launch_matvec(T, T->d_xs, B, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s);
+    mt::launch_matvec(T, T->d_xs, B, H, T->d_part, T->d_count, nullptr, T->tiles->ctx->d_status, s, T->d_colpart);
     mt::launch_near(T, m, 3 * T->n, 1, B, H, nullptr, s);
   }
   return MT_OK;
@@ -448,10 +456,12 @@ mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **out) {
 mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_tensor **out) {
   MT_CHECK(tiles && out, MT_EINVAL, "mt_demag_assemble: NULL argument");
   MT_CHECK(prec >= MT_F64 && prec <= MT_BF16_SPLIT, MT_EINVAL, "mt_demag_assemble: bad precision %d", (int)prec);
-  MT_CHECK(layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_DENSE || layout == MT_LAYOUT_STREAM6, MT_EINVAL,
-           "mt_demag_assemble: bad layout %d", layout);
-  const bool allow_planar = layout == MT_LAYOUT_STREAM;
-  if (layout == MT_LAYOUT_STREAM6) layout = MT_LAYOUT_STREAM;
+  MT_CHECK(layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_DENSE || layout == MT_LAYOUT_STREAM6 ||
+               layout == MT_LAYOUT_STREAM_FULL,
+           MT_EINVAL, "mt_demag_assemble: bad layout %d", layout);
+  const bool allow_planar = layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_STREAM_FULL;
+  const bool allow_half = layout == MT_LAYOUT_STREAM;
+  if (layout == MT_LAYOUT_STREAM6 || layout == MT_LAYOUT_STREAM_FULL) layout = MT_LAYOUT_STREAM;
   MT_CHECK(layout == MT_LAYOUT_STREAM || prec == MT_BF16_SCALED || prec == MT_BF16_SPLIT, MT_EINVAL,
            "mt_demag_assemble: the dense layout stores BF16 or split BF16 only");
   mt_ctx *ctx = tiles->ctx;
@@ -485,8 +495,21 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
     }
     T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
     T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
-    data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
-    scale_bytes = (size_t)T->L.P * T->L.Q * T->L.scale_bytes_per_chunk;
+    // FP32 tiles of one shape beyond the one-kernel path's range: the
+    // tensor is symmetric (N_ij = N_ji), so only the upper triangle of
+    // chunks is stored (Sec. 3.2)
+    if (allow_half && prec == MT_F32 && tiles->kind == MT_TILE_CUBOID && T->n > kHalfMinTiles) {
+      // one shape: equal edges to 1e-12 (as for the lattice test; the
+      // tensor then differs from a symmetric one far below FP32 rounding)
+      bool same = true;
+      for (int64_t i = 1; i < tiles->n && same; ++i)
+        for (int a = 0; a < 3; ++a)
+          same = same && std::fabs(tiles->edge[3 * i + a] - tiles->edge[a]) <= 1e-12 * tiles->edge[a];
+      T->L.half = same;
+    }
+    T->L.CH = T->L.half ? half_cum(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
+    data_bytes = (size_t)T->L.CH * T->L.chunk_bytes();
+    scale_bytes = (size_t)T->L.CH * T->L.scale_bytes_per_chunk;
   }
   T->bytes = data_bytes + scale_bytes;
   {
@@ -535,6 +558,8 @@ mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
   info->planes = T->layout == MT_LAYOUT_DENSE ? 9 : T->L.nplane;  // sparse: as its source
   info->bytes = (int64_t)T->bytes;
   info->near_blocks = T->near_count;
+  info->half = T->L.half ? 1 : 0;
+  info->pad = 0;
   return MT_OK;
 }
 

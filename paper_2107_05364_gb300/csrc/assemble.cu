@@ -266,6 +266,7 @@ struct AsmArgs {
   int *bad;           // set to 1 on overlap
   int *planar_bad;    // set to 1 if a 4-plane (single-layer) tensor meets |N_xz| or |N_yz| > kPlanarTol
   int dense;          // 1: 9-entry row-major matrix (Kp x Kp), else tile-blocked
+  int half;           // 1: streaming FP32 tensor of one tile shape, upper triangle of chunks only
   int64_t Kp;
   int *near_fill;     // per-row fill counter (BF16 precisions)
   const int32_t *near_ptr;
@@ -314,6 +315,9 @@ __global__ void k_assemble(AsmArgs A) {
       rel = (i == j) ? 2 : tet ? tetra_relation(ci, A.vert + 12 * i, vj) : pair_relation(ci, ei, cj, ej);
     }
     if (rel & 1) atomicExch(A.bad, 1);
+    // half storage: block (i, j) of an omitted chunk is block (j, i), which
+    // its own chunk stores (the relation above is still checked for all pairs)
+    if (A.half && half_q0(p, A.TC / A.TR) > q) continue;
     const bool near = (rel & 2) && (A.prec == MT_BF16_SCALED || A.prec == MT_BF16_SPLIT);
     if (A.count_only) {
       if (near) atomicAdd(&A.near_fill[i], 1);
@@ -364,7 +368,7 @@ __global__ void k_assemble(AsmArgs A) {
 #pragma unroll
         for (int e = 0; e < 6; ++e) {
           const int pl = stream_plane(e, A.nplane);
-          if (pl >= 0) D[layout_index(i, j, pl, A.TR, A.TC, A.nplane, A.Q)] = (float)N6[e];
+          if (pl >= 0) D[layout_index_h(i, j, pl, A.TR, A.TC, A.nplane, A.Q, A.half)] = (float)N6[e];
           else if (!(fabs(N6[e]) <= kPlanarTol)) *A.planar_bad = 1;
         }
       } break;
@@ -453,7 +457,7 @@ __global__ void k_blocks(const double *centre, const double *edge, const double 
 
 // stored value -> double, rows [i0, i1), all columns; out[((i-i0)*n + j)*6 + e]
 __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int64_t n, int TR, int TC,
-                            int nplane, int64_t Q, int64_t i0, int64_t i1, double *out) {
+                            int nplane, int64_t Q, bool hs, int64_t i0, int64_t i1, double *out) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t rows = i1 - i0;
   if (t >= rows * n) return;
@@ -464,7 +468,9 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
       case MT_F64: v = ((const double *)data)[layout_index(i, j, e, TR, TC, 6, Q)]; break;
       case MT_F32: {
         const int pl = stream_plane(e, nplane);
-        v = pl < 0 ? 0.0 : ((const float *)data)[layout_index(i, j, pl, TR, TC, nplane, Q)];
+        int64_t at = pl < 0 ? -1 : layout_index_h(i, j, pl, TR, TC, nplane, Q, hs);
+        if (pl >= 0 && at < 0) at = layout_index_h(j, i, pl, TR, TC, nplane, Q, hs);  // N_ij = N_ji
+        v = pl < 0 ? 0.0 : ((const float *)data)[at];
       } break;
       case MT_BF16_SCALED: {
         const int pl = stream_plane(e, nplane);
@@ -541,6 +547,7 @@ mt_status assemble(mt_tensor *T) {
   A.bad = d_bad;
   A.planar_bad = d_bad + 1;
   A.dense = T->layout == MT_LAYOUT_DENSE;
+  A.half = T->L.half ? 1 : 0;
   A.Kp = T->Kp;
   DevTemp<double> table;
   double *d_table = nullptr;
@@ -606,10 +613,13 @@ mt_status assemble(mt_tensor *T) {
     // an xz or yz entry of the single-layer set is not round-off: store all
     // 6 planes after all (within the budget reserved for them)
     mt_ctx *ctx = t->ctx;
+    const bool half = T->L.half;
     layout_for(T->prec, &T->L);
     T->L.P = (n + T->L.TR - 1) / T->L.TR;
     T->L.Q = (n + T->L.TC - 1) / T->L.TC;
-    const size_t bytes = (size_t)T->L.P * T->L.Q * (T->L.chunk_bytes() + T->L.scale_bytes_per_chunk);
+    T->L.half = half;
+    T->L.CH = half ? half_cum(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
+    const size_t bytes = (size_t)T->L.CH * (T->L.chunk_bytes() + T->L.scale_bytes_per_chunk);
     {
       std::lock_guard<std::mutex> lk(ctx->mu);
       MT_CHECK(ctx->in_use - T->bytes + bytes <= ctx->budget, MT_ENOMEM,
@@ -617,7 +627,7 @@ mt_status assemble(mt_tensor *T) {
       ctx->in_use += bytes - T->bytes;
       T->bytes = bytes;
     }
-    const size_t data_bytes = (size_t)T->L.P * T->L.Q * T->L.chunk_bytes();
+    const size_t data_bytes = (size_t)T->L.CH * T->L.chunk_bytes();
     MT_CUDA(cudaFree(T->d_data));
     T->d_data = nullptr;
     MT_CUDA(cudaMalloc(&T->d_data, data_bytes));
@@ -664,7 +674,7 @@ mt_status read_rows(const mt_tensor *T, int64_t i0, int64_t i1, double *out) {
                                                               T->prec == MT_BF16_SPLIT, n, T->Kp, i0, i1, d_out);
   else
     k_read_rows<<<(unsigned)((tot + 255) / 256), 256>>>(T->d_data, T->d_scale, T->prec, n, T->L.TR, T->L.TC,
-                                                         T->L.nplane, T->L.Q, i0, i1, d_out);
+                                                         T->L.nplane, T->L.Q, T->L.half, i0, i1, d_out);
   MT_CUDA(cudaGetLastError());
   if (T->near_count > 0) {
     k_merge_near<<<(unsigned)((rows + 127) / 128), 128>>>(n, i0, i1, T->d_near_ptr, T->d_near_col,

@@ -1288,6 +1288,7 @@ struct mt_integrator {
   float *k[7] = {};
   float *g1 = nullptr, *g2 = nullptr, *Ha = nullptr, *xsc = nullptr;
   float *part = nullptr;
+  float *colpart = nullptr;  // half-stored tensor: column work area of the product
   int *count = nullptr;
   SimCtl *ctl = nullptr;
   int *active = nullptr;
@@ -1382,7 +1383,7 @@ constexpr size_t kSmallL2Bytes = 96ull << 20;
 // with the state in shared memory.
 bool small_plan(mt_integrator *I) {
   const mt_tensor *T = I->T;
-  if (T->prec != MT_F32 || T->layout != MT_LAYOUT_STREAM) return false;
+  if (T->prec != MT_F32 || T->layout != MT_LAYOUT_STREAM || T->L.half) return false;
   const int64_t n = T->n;
   const int sms = T->tiles->ctx->num_sms;
   if (n < 1 || sms < 1) return false;
@@ -1484,7 +1485,7 @@ void demag(mt_integrator *I, const float *m) {
                     I->stream);
   } else {
     mt::launch_matvec(I->T, I->xs, I->B, I->Hd, I->part, I->count, I->active, I->T->tiles->ctx->d_status,
-                      I->stream);
+                      I->stream, I->colpart);
     mt::launch_near(I->T, m, 3 * I->T->n, 1, I->B, I->Hd, I->active, I->stream);
   }
 }
@@ -1710,6 +1711,7 @@ mt_status mt_integrator_create(mt_tensor *T, const mt_llg_params *p, const mt_od
   MT_TRY(dalloc(I, &I->xsc, sizeof(float) * B));
   MT_TRY(dalloc(I, &I->part, dense ? mt::dense_part_bytes(T, B) : mt::matvec_part_bytes(T)));
   MT_TRY(dalloc(I, &I->count, dense ? mt::dense_count_bytes(T) : mt::matvec_count_bytes(T, B)));
+  if (!dense && T->L.half) MT_TRY(dalloc(I, &I->colpart, mt::matvec_colpart_bytes(T, B)));
   MT_TRY(dalloc(I, &I->ctl, sizeof(SimCtl) * B));
   MT_TRY(dalloc(I, &I->active, sizeof(int) * B));
   MT_TRY(dalloc(I, &I->n_active, sizeof(int)));

@@ -88,19 +88,31 @@ struct MvCfg<MT_BF16_SPLIT> {
   static constexpr bool SCALED = false, PLANAR = false;
 };
 
-template <int PREC, int SB>
+template <int PREC, int SB, bool HALF = false>
 struct MvShape {
   using C = MvCfg<PREC>;
-  static constexpr int RPW = C::TR / C::W;  // rows per consumer warp
+  // consumer warps: W, or 2 W for a half-stored tensor and one simulation
+  // (its chunks carry twice the arithmetic per byte, the row and the column
+  // product, and one warp per SM sub-partition left the issue slots idle on
+  // latency)
+  static constexpr int NCW = (HALF && SB == 1) ? 2 * C::W : C::W;
+  static constexpr int RPW = C::TR / NCW;  // rows per consumer warp
   static constexpr int DATA_BYTES = C::NPLANE * C::TR * C::TC * (int)sizeof(typename C::T);
   static constexpr int SCALE_BYTES = C::SCALED ? C::TR * C::TC : 0;
   static constexpr int XS_BYTES = 3 * C::TC * (int)sizeof(typename C::Acc);  // one simulation's slice
   static constexpr int STAGE_BYTES = DATA_BYTES + SCALE_BYTES + SB * XS_BYTES;
-  // ring depth: up to C::STAGES within ~220 KB of shared memory
-  static constexpr int STAGES = (C::STAGES * STAGE_BYTES <= 220 * 1024) ? C::STAGES : (220 * 1024) / STAGE_BYTES;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16;
-  static constexpr int THREADS = (C::W + 1) * 32;
+  // half storage: the consumer warps' column sums of a chunk, double buffered
+  static constexpr int CB_BYTES = HALF ? 2 * NCW * SB * 3 * C::TC * (int)sizeof(typename C::Acc) : 0;
+  // ring depth: up to C::STAGES within 226 KB of shared memory (the
+  // barriers and the abort flag fill the rest of the 227 KB a CTA may have)
+  static constexpr int STAGES = (C::STAGES * STAGE_BYTES + CB_BYTES <= 226 * 1024)
+                                    ? C::STAGES
+                                    : (226 * 1024 - CB_BYTES) / STAGE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + CB_BYTES + 2 * STAGES * 8 + 16;
+  static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
+  static constexpr int THREADS = (NCW + 1) * 32;
   static_assert(STAGES >= 2, "at least a double-buffered ring");
+  static_assert(C::TR % NCW == 0 && (!HALF || (NCW * 32) % C::TC == 0), "whole rows per warp, whole column sets");
   static_assert(C::TC == 32 * C::VEC, "a warp covers one chunk row");
   static_assert(3 * RPW <= 32, "one lane per (row, component) in the flush");
   static_assert(DATA_BYTES % 16 == 0 && SCALE_BYTES % 16 == 0 && XS_BYTES % 16 == 0, "bulk copy sizes");
@@ -169,8 +181,58 @@ struct MvArgs {
   const int *active;
   int *status;
   int64_t n, P, Q;
+  int64_t CH;     // stored chunks per group of simulations
+  float *colpart; // half storage: column sums [unit][SB][3][TC]
+  int *arrive;    // half storage: k_half_cols arrival counters [B][Q], zeroed by k_matvec
   int B;
 };
+
+// slices of a column chunk's panel range in k_half_cols: about 32 panels each
+inline int half_col_slices(int64_t P) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (P + 31) / 32)); }
+
+// Units in storage order: (group of simulations g, stored chunk c) with c
+// the chunk (panel p, column chunk q).  Without half storage c = p Q + q;
+// with it panel p holds chunks q0(p) .. Q-1 (see half_cum).
+struct UnitCursor {
+  int64_t g, p, q, c;
+};
+template <int K, bool HALF>
+__device__ __forceinline__ void unit_decode(const MvArgs &A, int64_t u, UnitCursor &cu) {
+  cu.g = u / A.CH;
+  cu.c = u - cu.g * A.CH;
+  if (!HALF) {
+    cu.p = cu.c / A.Q;
+    cu.q = cu.c - cu.p * A.Q;
+    return;
+  }
+  int64_t lo = 0, hi = A.P - 1;  // the last panel whose first chunk is <= c
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (half_cum(mid, A.Q, K) <= cu.c) lo = mid;
+    else hi = mid - 1;
+  }
+  cu.p = lo;
+  cu.q = half_q0(lo, K) + (cu.c - half_cum(lo, A.Q, K));
+}
+template <int K, bool HALF>
+__device__ __forceinline__ void unit_next(const MvArgs &A, UnitCursor &cu) {
+  ++cu.c;
+  if (++cu.q == A.Q) {
+    ++cu.p;
+    cu.q = HALF ? half_q0(cu.p, K) : 0;
+  }
+  if (cu.c == A.CH) {
+    cu.c = 0;
+    ++cu.g;
+    cu.p = 0;
+    cu.q = 0;
+  }
+}
+// first unit of panel p of group g
+template <int K, bool HALF>
+__device__ __forceinline__ int64_t panel_first_unit(const MvArgs &A, int64_t g, int64_t p) {
+  return g * A.CH + (HALF ? half_cum(p, A.Q, K) : p * A.Q);
+}
 
 // SB simulations share every chunk read: unit = (group of SB simulations,
 // panel, chunk); the stage holds the chunk and the group's SB operand slices
@@ -185,35 +247,41 @@ __device__ __forceinline__ bool group_live(const MvArgs &A, int64_t g, int SB) {
   return false;
 }
 
-template <int PREC, int SB>
-__global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs A) {
+template <int PREC, int SB, bool HALF>
+__global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(MvArgs A) {
   mtd::pdl_enter();
   using C = MvCfg<PREC>;
-  using S = MvShape<PREC, SB>;
+  using S = MvShape<PREC, SB, HALF>;
+  if constexpr (HALF) {  // the column pass that follows counts its arrivals from zero
+    for (int64_t k = blockIdx.x * (int64_t)S::THREADS + threadIdx.x; k < (int64_t)A.B * A.Q;
+         k += (int64_t)gridDim.x * S::THREADS)
+      A.arrive[k] = 0;
+  }
   using Acc = typename C::Acc;
+  constexpr int K = C::TC / C::TR;  // panels per column chunk
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES);
+  Acc *cb = reinterpret_cast<Acc *>(smem + S::STAGES * S::STAGE_BYTES);  // half: column sums
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES + S::CB_BYTES);
   uint64_t *empty = full + S::STAGES;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + S::STAGES);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t G = gridDim.x, k = blockIdx.x;
-  const int64_t PQ = A.P * A.Q;
   const int64_t NG = (A.B + SB - 1) / SB;
-  const int64_t U = NG * PQ;
+  const int64_t U = NG * A.CH;
   const int64_t u0 = mtd::sk_begin(k, U, G), u1 = mtd::sk_begin(k + 1, U, G);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S::STAGES; ++s) {
       mtd::mbar_init(&full[s], 1);
-      mtd::mbar_init(&empty[s], C::W);
+      mtd::mbar_init(&empty[s], S::NCW);
     }
     *abort_flag = 0;
     mtd::fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == C::W) {
+  if (warp == S::NCW) {
     // ---------------- producer ----------------
     if (lane == 0) {
       const uint64_t pol_stream = mtd::policy_evict_first();
@@ -221,9 +289,10 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
       const unsigned char *tens = reinterpret_cast<const unsigned char *>(A.tensor);
       const unsigned char *xs = reinterpret_cast<const unsigned char *>(A.xs);
       int it = 0;
-      for (int64_t u = u0; u < u1; ++u) {
-        const int64_t gp = u / A.Q, q = u - gp * A.Q;
-        const int64_t g = gp / A.P, p = gp - g * A.P;
+      UnitCursor cu;
+      unit_decode<K, HALF>(A, u0, cu);
+      for (int64_t u = u0; u < u1; ++u, unit_next<K, HALF>(A, cu)) {
+        const int64_t g = cu.g, q = cu.q;
         if (!group_live(A, g, SB)) continue;
         const int s = it % S::STAGES;
         const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
@@ -235,10 +304,10 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
         }
         unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
         mtd::mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
-        mtd::bulk_g2s(st, tens + (size_t)(p * A.Q + q) * S::DATA_BYTES, S::DATA_BYTES, &full[s], pol_stream);
+        mtd::bulk_g2s(st, tens + (size_t)cu.c * S::DATA_BYTES, S::DATA_BYTES, &full[s], pol_stream);
         if constexpr (C::SCALED)
-          mtd::bulk_g2s(st + S::DATA_BYTES, A.scale + (size_t)(p * A.Q + q) * S::SCALE_BYTES, S::SCALE_BYTES,
-                        &full[s], pol_stream);
+          mtd::bulk_g2s(st + S::DATA_BYTES, A.scale + (size_t)cu.c * S::SCALE_BYTES, S::SCALE_BYTES, &full[s],
+                        pol_stream);
 #pragma unroll
         for (int m = 0; m < SB; ++m) {
           const int64_t b = g * SB + m < A.B ? g * SB + m : 0;
@@ -258,9 +327,9 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
 
   // ---------------- consumers ----------------
   Acc acc[SB][S::RPW][3];
+  Acc xi[HALF ? SB : 1][S::RPW][3];  // half: the operand of this warp's rows (the transposed product)
   int64_t gp_cur = -1;
-  const int64_t first_panel = u0 / A.Q;
-  int it = 0;
+  int it = 0, strict_it = 0;
   bool aborted = false;
 
   auto flush = [&](int64_t gp) {
@@ -272,7 +341,8 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[m][r][c] = mtd::warp_sum(acc[m][r][c]);
     const int64_t g = gp / A.P, p = gp - g * A.P;
-    const int64_t kf = mtd::sk_owner(gp * A.Q, U, G), kl = mtd::sk_owner(gp * A.Q + A.Q - 1, U, G);
+    const int64_t pu0 = panel_first_unit<K, HALF>(A, g, p), pu1 = panel_first_unit<K, HALF>(A, g, p + 1);
+    const int64_t kf = mtd::sk_owner(pu0, U, G), kl = mtd::sk_owner(pu1 - 1, U, G);
     // this lane's (row, component)
     const int lr = lane / 3, lc = lane - 3 * (lane / 3);
     Acc mine[SB];
@@ -300,7 +370,7 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
           if (Acc *H = out(m)) H[3 * row + lc] = -mine[m];
       return;
     }
-    const int64_t slot = (gp == first_panel) ? 2 * k : 2 * k + 1;
+    const int64_t slot = (u0 >= pu0) ? 2 * k : 2 * k + 1;  // this CTA starts inside the panel: its first
     if (writer)
 #pragma unroll
       for (int m = 0; m < SB; ++m) part[((slot * SB + m) * C::TR + row_in_panel) * 3 + lc] = mine[m];
@@ -308,7 +378,7 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
     __syncwarp();
     int last = 0;
     if (lane == 0) {
-      const int old = atomicAdd(&A.count[gp * C::W + warp], 1);
+      const int old = atomicAdd(&A.count[gp * S::NCW + warp], 1);
       last = (old == (int)(kl - kf));
     }
     last = __shfl_sync(0xffffffffu, last, 0);
@@ -318,20 +388,21 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
         for (int m = 0; m < SB; ++m) {
           Acc tot = 0;
           for (int64_t kk = kf; kk <= kl; ++kk) {
-            const int64_t fp = mtd::sk_begin(kk, U, G) / A.Q;
-            const int64_t sl = (gp == fp) ? 2 * kk : 2 * kk + 1;
+            // slot of CTA kk: 2 kk if this panel is its first, else 2 kk + 1
+            const int64_t sl = (mtd::sk_begin(kk, U, G) >= pu0) ? 2 * kk : 2 * kk + 1;
             tot += __ldcg(&part[((sl * SB + m) * C::TR + row_in_panel) * 3 + lc]);
           }
           Acc *H = out(m);
           if (H && row < A.n) H[3 * row + lc] = -tot;
         }
-      if (lane == 0) A.count[gp * C::W + warp] = 0;  // ready for the next launch
+      if (lane == 0) A.count[gp * S::NCW + warp] = 0;  // ready for the next launch
     }
   };
 
-  for (int64_t u = u0; u < u1; ++u) {
-    const int64_t gp = u / A.Q;
-    const int64_t g = gp / A.P;
+  UnitCursor cu;
+  unit_decode<K, HALF>(A, u0, cu);
+  for (int64_t u = u0; u < u1; ++u, unit_next<K, HALF>(A, cu)) {
+    const int64_t g = cu.g, gp = g * A.P + cu.p;
     if (!group_live(A, g, SB)) continue;
     if (gp != gp_cur) {
       if (gp_cur >= 0) flush(gp_cur);
@@ -340,6 +411,30 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
       for (int m = 0; m < SB; ++m)
 #pragma unroll
         for (int r = 0; r < S::RPW; ++r) acc[m][r][0] = acc[m][r][1] = acc[m][r][2] = 0;
+      if constexpr (HALF) {
+        // the operand of this warp's rows, for the transposed product
+        const Acc *xsg = reinterpret_cast<const Acc *>(A.xs);
+#pragma unroll
+        for (int m = 0; m < SB; ++m) {
+          const int64_t b = g * SB + m < A.B ? g * SB + m : 0;
+#pragma unroll
+          for (int r = 0; r < S::RPW; ++r) {
+            const int64_t i = cu.p * C::TR + warp * S::RPW + r;
+            const int64_t qi = i / C::TC, ti = i - qi * C::TC;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) xi[m][r][c] = __ldg(&xsg[((b * A.Q + qi) * 3 + c) * C::TC + ti]);
+          }
+        }
+      }
+    }
+    // an off-diagonal chunk of the half storage also serves its columns
+    const bool strict = HALF && cu.q > half_q0(cu.p, K);
+    Acc colp[HALF ? SB : 1][C::VEC][3];
+    if constexpr (HALF) {
+#pragma unroll
+      for (int m = 0; m < SB; ++m)
+#pragma unroll
+        for (int v = 0; v < C::VEC; ++v) colp[m][v][0] = colp[m][v][1] = colp[m][v][2] = 0;
     }
     const int s = it % S::STAGES;
     const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
@@ -395,6 +490,19 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
             acc[m][r][1] += sy;
             acc[m][r][2] += sz;
           }
+          if constexpr (HALF) {
+            if (strict) {
+              // block (row, v) transposed: the same symmetric block times this row's operand
+#pragma unroll
+              for (int m = 0; m < SB; ++m)
+#pragma unroll
+                for (int v = 0; v < C::VEC; ++v) {
+                  colp[m][v][0] = fma(nxx[v], xi[m][r][0], fma(nxy[v], xi[m][r][1], colp[m][v][0]));
+                  colp[m][v][1] = fma(nxy[v], xi[m][r][0], fma(nyy[v], xi[m][r][1], colp[m][v][1]));
+                  colp[m][v][2] = fma(nzz[v], xi[m][r][2], colp[m][v][2]);
+                }
+            }
+          }
           continue;
         }
         Acc nxx[C::VEC], nxy[C::VEC], nxz[C::VEC], nyy[C::VEC], nyz[C::VEC], nzz[C::VEC];
@@ -432,12 +540,143 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
           acc[m][r][1] += sy;
           acc[m][r][2] += sz;
         }
+        if constexpr (HALF) {
+          if (strict) {
+#pragma unroll
+            for (int m = 0; m < SB; ++m)
+#pragma unroll
+              for (int v = 0; v < C::VEC; ++v) {
+                colp[m][v][0] =
+                    fma(nxx[v], xi[m][r][0], fma(nxy[v], xi[m][r][1], fma(nxz[v], xi[m][r][2], colp[m][v][0])));
+                colp[m][v][1] =
+                    fma(nxy[v], xi[m][r][0], fma(nyy[v], xi[m][r][1], fma(nyz[v], xi[m][r][2], colp[m][v][1])));
+                colp[m][v][2] =
+                    fma(nxz[v], xi[m][r][0], fma(nyz[v], xi[m][r][1], fma(nzz[v], xi[m][r][2], colp[m][v][2])));
+              }
+          }
+        }
       }
     }
     __syncwarp();
     if (lane == 0) mtd::mbar_arrive(&empty[s]);
+    if constexpr (HALF) {
+      if (strict) {
+        // column sums of the chunk: each warp's partial (its rows) to shared
+        // memory, then thread t sums column t % TC, components t / TC,
+        // t / TC + NCW 32 / TC, ..., over the warps in order, and writes them
+        // to the chunk's slot of the work area
+        const int buf = strict_it & 1;
+        ++strict_it;
+        Acc *mine = cb + (size_t)((buf * S::NCW + warp) * SB) * 3 * C::TC;
+#pragma unroll
+        for (int m = 0; m < SB; ++m)
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            *reinterpret_cast<float4 *>(mine + (m * 3 + c) * C::TC + lane * C::VEC) =
+                make_float4(colp[m][0][c], colp[m][1][c], colp[m][2][c], colp[m][3][c]);
+        asm volatile("bar.sync 1, %0;" ::"r"(S::NCW * 32) : "memory");
+        constexpr int NT = S::NCW * 32 / C::TC;  // thread sets over the columns
+        const int t = warp * 32 + lane, col = t % C::TC;
+        const int64_t uu = cu.g * A.CH + cu.c;
+#pragma unroll
+        for (int m = 0; m < SB; ++m) {
+          if (g * SB + m >= A.B) continue;
+#pragma unroll
+          for (int c0 = 0; c0 < 3; c0 += NT) {
+            const int c = c0 + t / C::TC;
+            if (c >= 3) break;
+            Acc tot = 0;
+#pragma unroll
+            for (int w = 0; w < S::NCW; ++w) tot += cb[((size_t)((buf * S::NCW + w) * SB + m) * 3 + c) * C::TC + col];
+            A.colpart[((uu * SB + m) * 3 + c) * C::TC + col] = tot;
+          }
+        }
+      }
+    }
   }
   if (gp_cur >= 0) flush(gp_cur);
+}
+
+// Half storage: the transposed part of the product.  Column j of chunk q
+// received, from every panel p whose chunk (p, q) lies above the diagonal
+// (p < K q), the column sums that chunk left in the work area.  CTA (q, s, b)
+// sums the panels of slice s of that range (NS slices, in increasing p) and
+// parks its sums; the last CTA of (q, b) to arrive adds the NS slice sums in
+// slice order (a fixed order: the result does not depend on timing) and
+// does H_j -= total.  One thread per column of the chunk.
+__global__ void __launch_bounds__(128) k_half_cols(MvArgs A, int SB, int TC, int K, int NS, float *slice_sum) {
+  mtd::pdl_enter();
+  const int64_t q = blockIdx.x;
+  const int sl = blockIdx.y, b = blockIdx.z;
+  const int t = threadIdx.x;
+  const int64_t np = K * q;  // panels above the diagonal of chunk q
+  const int64_t len = (np + NS - 1) / NS;
+  const int64_t pa = sl * len, pb = np < pa + len ? np : pa + len;
+  const int64_t g = b / SB, m = b - g * SB;
+  float tot[3] = {0.0f, 0.0f, 0.0f};
+  // walk the panels with the chunk (p, q)'s unit index kept up to date:
+  // panel p holds chunks q0(p) .. Q-1, q0 growing by one every K panels
+  int64_t q0 = pa / K, cum = g * A.CH + half_cum(pa, A.Q, K);
+  int kk = (int)(pa - q0 * K);
+  const float *base = A.colpart + m * 3 * TC + t;
+  const int64_t ustride = (int64_t)SB * 3 * TC;
+  auto next = [&] {
+    cum += A.Q - q0;
+    if (++kk == K) {
+      kk = 0;
+      ++q0;
+    }
+  };
+  int64_t p = pa;
+  for (; p + 4 <= pb; p += 4) {  // four panels' loads in flight
+    float v[4][3];
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      const float *cp = base + (cum + (q - q0)) * ustride;
+      v[k2][0] = __ldcg(cp);
+      v[k2][1] = __ldcg(cp + TC);
+      v[k2][2] = __ldcg(cp + 2 * TC);
+      next();
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+      tot[0] += v[k2][0];
+      tot[1] += v[k2][1];
+      tot[2] += v[k2][2];
+    }
+  }
+  for (; p < pb; ++p) {
+    const float *cp = base + (cum + (q - q0)) * ustride;
+    tot[0] += __ldcg(cp);
+    tot[1] += __ldcg(cp + TC);
+    tot[2] += __ldcg(cp + 2 * TC);
+    next();
+  }
+  const int64_t qb = (int64_t)b * A.Q + q;
+  float *mine = slice_sum + ((qb * NS + sl) * 3) * TC + t;
+  mine[0] = tot[0];
+  mine[TC] = tot[1];
+  mine[2 * TC] = tot[2];
+  __threadfence();
+  __syncthreads();
+  __shared__ int last;
+  if (t == 0) last = (atomicAdd(&A.arrive[qb], 1) == NS - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t j = q * TC + t;
+  if (j >= A.n || (A.active && !A.active[b])) return;
+  float v[3] = {0.0f, 0.0f, 0.0f};
+  for (int k2 = 0; k2 < NS; ++k2) {
+    const float *ss = slice_sum + ((qb * NS + k2) * 3) * TC + t;
+    v[0] += __ldcg(ss);
+    v[1] += __ldcg(ss + TC);
+    v[2] += __ldcg(ss + 2 * TC);
+  }
+  float *H = reinterpret_cast<float *>(A.H) + (size_t)b * 3 * A.n + 3 * j;
+  H[0] -= v[0];
+  H[1] -= v[1];
+  H[2] -= v[2];
 }
 
 // xs[b][q][c][t] = Ms_j m_j[c] with j = q*TC + t (0 beyond n)
@@ -612,10 +851,22 @@ __global__ void k_near_v(int64_t n, int B, int Bp, const int32_t *ptr, const int
   }
 }
 
+// half storage is built for FP32 tensors only (6 or 4 planes)
+template <int PREC>
+constexpr bool has_half() {
+  return PREC == MT_F32 || PREC == kF32Planar;
+}
+
 template <int PREC, int SB>
 cudaError_t prepare_mv_one() {
-  return cudaFuncSetAttribute(k_matvec<PREC, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              MvShape<PREC, SB>::SMEM_BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_matvec<PREC, SB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       MvShape<PREC, SB, false>::SMEM_BYTES);
+  if constexpr (has_half<PREC>()) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_matvec<PREC, SB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               MvShape<PREC, SB, true>::SMEM_BYTES);
+  }
+  return e;
 }
 
 template <int PREC>
@@ -635,19 +886,38 @@ inline int mv_group(int B, int prec) {
 }
 
 template <int PREC, int SB>
-void launch_mv_sb(const MvArgs &A, int64_t P, int64_t Q, int grid_cap, cudaStream_t s) {
-  using S = MvShape<PREC, SB>;
+void launch_mv_sb(const MvArgs &A, bool half, int grid_cap, cudaStream_t s) {
   // never more CTAs than units: every CTA then owns at least one unit, which
   // the panel bookkeeping (owners of a panel's first and last unit bound its
   // contributors) relies on
-  const int64_t U = (int64_t)((A.B + SB - 1) / SB) * P * Q;
+  const int64_t U = (int64_t)((A.B + SB - 1) / SB) * A.CH;
   const int grid = (int)std::min<int64_t>(grid_cap, U);
-  mt::launch_pdl(k_matvec<PREC, SB>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
+  if constexpr (has_half<PREC>()) {
+    if (half) {
+      using S = MvShape<PREC, SB, true>;
+      static_assert(MvCfg<PREC>::TC % MvCfg<PREC>::TR == 0, "panels tile a chunk row");
+      // the work area: chunk sums, then the slice sums and arrival counters
+      // of the column pass
+      constexpr int TC = MvCfg<PREC>::TC;
+      const int ns = half_col_slices(A.P);
+      const int64_t ng = (A.B + SB - 1) / SB;
+      float *slice_sum = A.colpart + (size_t)ng * SB * A.CH * 3 * TC;
+      MvArgs A2 = A;
+      A2.arrive = reinterpret_cast<int *>(slice_sum + (size_t)A.B * A.Q * ns * 3 * TC);
+      mt::launch_pdl(k_matvec<PREC, SB, true>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A2);
+      // the transposed part, summed per column
+      mt::launch_pdl(k_half_cols, dim3((unsigned)A.Q, (unsigned)ns, (unsigned)A.B), dim3(TC), 0, s, A2, SB, TC,
+                     TC / MvCfg<PREC>::TR, ns, slice_sum);
+      return;
+    }
+  }
+  using S = MvShape<PREC, SB, false>;
+  mt::launch_pdl(k_matvec<PREC, SB, false>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
 }
 
 template <int PREC>
 void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, int *count, const int *active,
-               int *status, cudaStream_t s) {
+               int *status, float *colpart, cudaStream_t s) {
   MvArgs A;
   A.tensor = T->d_data;
   A.scale = T->d_scale;
@@ -660,13 +930,17 @@ void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, i
   A.n = T->n;
   A.P = T->L.P;
   A.Q = T->L.Q;
+  A.CH = T->L.CH;
+  A.colpart = colpart;
+  A.arrive = nullptr;
   A.B = B;
   const int cap = mt::matvec_grid(T);
+  const bool half = T->L.half;
   switch (mv_group(B, PREC)) {
-    case 1: launch_mv_sb<PREC, 1>(A, T->L.P, T->L.Q, cap, s); break;
-    case 2: launch_mv_sb<PREC, 2>(A, T->L.P, T->L.Q, cap, s); break;
+    case 1: launch_mv_sb<PREC, 1>(A, half, cap, s); break;
+    case 2: launch_mv_sb<PREC, 2>(A, half, cap, s); break;
     default:
-      if constexpr (PREC != MT_BF16_SCALED && PREC != kBF16Planar) launch_mv_sb<PREC, 4>(A, T->L.P, T->L.Q, cap, s);
+      if constexpr (PREC != MT_BF16_SCALED && PREC != kBF16Planar) launch_mv_sb<PREC, 4>(A, half, cap, s);
       break;
   }
 }
@@ -735,6 +1009,19 @@ size_t matvec_part_bytes(const mt_tensor *T) {
 
 size_t matvec_count_bytes(const mt_tensor *T, int B) { return (size_t)B * T->L.P * 8 /*W<=8*/ * sizeof(int); }
 
+// half storage: the column sums of every stored chunk for B simulations
+// (groups of up to 4 share a chunk read; a partial group keeps its slots),
+// then the slice sums of k_half_cols and its arrival counters (a call with
+// fewer simulations uses a prefix of each part)
+size_t matvec_colpart_bytes(const mt_tensor *T, int B) {
+  if (!T->L.half) return 0;
+  const int sb = mv_group(B, T->L.nplane == 4 ? kF32Planar : MT_F32);
+  const int64_t ng = (B + sb - 1) / sb;
+  const int ns = half_col_slices(T->L.P);
+  return (size_t)ng * sb * T->L.CH * 3 * T->L.TC * sizeof(float) +
+         (size_t)B * T->L.Q * ns * 3 * T->L.TC * sizeof(float) + (size_t)B * T->L.Q * sizeof(int);
+}
+
 void launch_prep_xs(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
   if (T->layout == MT_LAYOUT_SPARSE) {
     launch_prep_sparse_x(T, m, B, xs, s);
@@ -756,20 +1043,20 @@ void launch_prep_xs_f64(const mt_tensor *T, const double *m, int B, double *xs, 
 }
 
 void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *part, int *count,
-                   const int *active, int *status, cudaStream_t s) {
+                   const int *active, int *status, cudaStream_t s, float *colpart) {
   switch (T->prec) {
     case MT_F32:
-      if (T->L.nplane == 4) launch_mv<kF32Planar>(T, xs, B, H, part, count, active, status, s);
-      else launch_mv<MT_F32>(T, xs, B, H, part, count, active, status, s);
+      if (T->L.nplane == 4) launch_mv<kF32Planar>(T, xs, B, H, part, count, active, status, colpart, s);
+      else launch_mv<MT_F32>(T, xs, B, H, part, count, active, status, colpart, s);
       break;
-    case MT_F64: launch_mv<MT_F64>(T, xs, B, H, part, count, active, status, s); break;
+    case MT_F64: launch_mv<MT_F64>(T, xs, B, H, part, count, active, status, nullptr, s); break;
     case MT_BF16_SCALED:
-      if (T->L.nplane == 4) launch_mv<kBF16Planar>(T, xs, B, H, part, count, active, status, s);
-      else launch_mv<MT_BF16_SCALED>(T, xs, B, H, part, count, active, status, s);
+      if (T->L.nplane == 4) launch_mv<kBF16Planar>(T, xs, B, H, part, count, active, status, nullptr, s);
+      else launch_mv<MT_BF16_SCALED>(T, xs, B, H, part, count, active, status, nullptr, s);
       break;
     case MT_BF16_SPLIT:
-      if (T->L.nplane == 8) launch_mv<kSplitPlanar>(T, xs, B, H, part, count, active, status, s);
-      else launch_mv<MT_BF16_SPLIT>(T, xs, B, H, part, count, active, status, s);
+      if (T->L.nplane == 8) launch_mv<kSplitPlanar>(T, xs, B, H, part, count, active, status, nullptr, s);
+      else launch_mv<MT_BF16_SPLIT>(T, xs, B, H, part, count, active, status, nullptr, s);
       break;
   }
 }

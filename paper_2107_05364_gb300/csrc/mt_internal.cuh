@@ -143,10 +143,34 @@ struct mt_layout {
   int nplane = 6;           // 6 unique entries (12 for split hi/lo)
   int elem_bytes = 4;
   int64_t P = 0, Q = 0;     // panels, chunks per panel
+  bool half = false;        // only the upper triangle of chunks (see half_cum)
+  int64_t CH = 0;           // stored chunks (P * Q, or half_cum(P) when half)
   int64_t chunk_elems() const { return (int64_t)nplane * TR * TC; }
   int64_t chunk_bytes() const { return chunk_elems() * elem_bytes; }
   int64_t scale_bytes_per_chunk = 0;  // BF16 scaled: TR x TC int8 exponents
 };
+
+// Half storage (Sec. 3.2: the tensor is symmetric).  For tiles of one shape
+// the point tensor is even in the offset of the two centres, so N_ij = N_ji
+// (and every block is symmetric): panel p (rows p TR ...) keeps only its
+// column chunks q >= q0(p) = p / K, K = TC / TR, the chunk holding its own
+// rows.  That diagonal chunk is used as stored (for its rows only); every
+// higher chunk serves its rows and, transposed, its columns.  Stored chunks
+// are consecutive in (p, q) order: chunk (p, q) is number
+// half_cum(p) + q - q0(p), half_cum(p) counting the chunks of panels < p.
+__host__ __device__ __forceinline__ int64_t half_q0(int64_t p, int K) { return p / K; }
+__host__ __device__ __forceinline__ int64_t half_cum(int64_t p, int64_t Q, int K) {
+  const int64_t R = p / K;  // chunk row of p: every panel of chunk row r keeps Q - r chunks
+  return p * Q - ((int64_t)K * R * (R - 1) / 2 + R * (p - (int64_t)K * R));
+}
+// stored chunk of (panel p, column chunk q), -1 if the half storage omits it
+__host__ __device__ __forceinline__ int64_t stream_chunk(int64_t p, int64_t q, int64_t Q, int TR, int TC,
+                                                         bool half) {
+  if (!half) return p * Q + q;
+  const int K = TC / TR;
+  const int64_t q0 = half_q0(p, K);
+  return q < q0 ? -1 : half_cum(p, Q, K) + (q - q0);
+}
 
 struct mt_tensor {
   std::atomic<int> refs{1};
@@ -173,6 +197,8 @@ struct mt_tensor {
   int count_B = 0;
   float *d_Hd = nullptr;
   int Hd_B = 0;
+  float *d_colpart = nullptr;  // half storage: column work area of the standalone calls
+  int colpart_B = 0;
   int gemm_stages[4] = {0, 0, 0, 0};  // tuned ring depth per padded batch 16/32/64/128
   int gemm_kps[4] = {0, 0, 0, 0};     // tuned K blocks per ring stage (tile shape along K)
   // thresholded layout: block-sparse rows (kept blocks, 6 FP32 entries each)
@@ -195,6 +221,9 @@ __host__ __device__ __forceinline__ int stream_plane(int e, int nplane) {
 // bound on |N_xz|, |N_yz| of a single-layer tile set (FP64 round-off of
 // entries that vanish by mirror symmetry)
 constexpr double kPlanarTol = 1e-12;
+// half storage from this many tiles on (smaller FP32 tensors are read from
+// L2 or shared memory by the one-kernel integrator path, which wants rows)
+constexpr int64_t kHalfMinTiles = 2048;
 
 // Index of entry e of block (i, j) in the tile-blocked streaming layout.
 __host__ __device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, int e, int TR, int TC, int nplane,
@@ -202,6 +231,16 @@ __host__ __device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, i
   const int64_t p = i / TR, q = j / TC;
   const int r = (int)(i - p * TR), c = (int)(j - q * TC);
   return (((p * Q + q) * nplane + e) * TR + r) * (int64_t)TC + c;
+}
+// The same for either storage; -1 where the half storage omits block (i, j)
+// (it is block (j, i), stored: N_ij = N_ji for tiles of one shape).
+__host__ __device__ __forceinline__ int64_t layout_index_h(int64_t i, int64_t j, int e, int TR, int TC, int nplane,
+                                                           int64_t Q, bool half) {
+  const int64_t p = i / TR, q = j / TC;
+  const int64_t ch = stream_chunk(p, q, Q, TR, TC, half);
+  if (ch < 0) return -1;
+  const int r = (int)(i - p * TR), c = (int)(j - q * TC);
+  return ((ch * nplane + e) * TR + r) * (int64_t)TC + c;
 }
 
 // Operand of the thresholded product: a float4 (Ms m, 0) per tile and
@@ -252,9 +291,13 @@ size_t matvec_count_bytes(const mt_tensor *T, int B);
 // xs[b] = Ms * m[b] in the padded chunked layout ([Q][3][TC], zero padded)
 void launch_prep_xs(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s);
 void launch_prep_xs_f64(const mt_tensor *T, const double *m, int B, double *xs, cudaStream_t s);
-// H[b] = -N xs[b]; active (may be null) skips finished simulations
+// bytes of the column work area of a half-stored tensor for B sims (0 if
+// the tensor stores every block)
+size_t matvec_colpart_bytes(const mt_tensor *T, int B);
+// H[b] = -N xs[b]; active (may be null) skips finished simulations; colpart:
+// the column work area (matvec_colpart_bytes) of a half-stored tensor
 void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *part, int *count,
-                   const int *active, int *status, cudaStream_t s);
+                   const int *active, int *status, cudaStream_t s, float *colpart = nullptr);
 // H[b] -= near-field blocks applied to Ms m (BF16 precisions); element
 // (b, j, c) of m at m[b * sb + (3 j + c) * se]
 void launch_near(const mt_tensor *T, const float *m, int64_t sb, int64_t se, int B, float *H, const int *active,

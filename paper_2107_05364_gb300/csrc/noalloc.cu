@@ -52,6 +52,9 @@ extern "C" mt_status mt_demag_field_noalloc(mt_tensor *T, const float *m, int B,
   MT_CHECK(T->prec != MT_F64, MT_EINVAL, "mt_demag_field_noalloc: FP64 tensors are not supported");
   MT_CHECK(T->layout == MT_LAYOUT_STREAM, MT_EINVAL,
            "mt_demag_field_noalloc: only streaming-layout tensors are supported");
+  MT_CHECK(!T->L.half, MT_EINVAL,
+           "mt_demag_field_noalloc: a half-stored tensor needs a column work area of 1.5 KB per stored chunk; "
+           "assemble with MT_LAYOUT_STREAM_FULL or use mt_demag_field");
   const size_t count_bytes = align256(mt::matvec_count_bytes(T, B));
   const size_t part_bytes = align256(mt::matvec_part_bytes(T));
   const size_t xs_bytes = align256(sizeof(float) * (size_t)mt::xs_floats(T) * (size_t)B);

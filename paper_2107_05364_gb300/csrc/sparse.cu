@@ -364,6 +364,8 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   MT_CHECK(T->prec == MT_F32 && T->layout == MT_LAYOUT_STREAM, MT_EINVAL,
            "mt_tensor_threshold: needs an FP32 tensor of the streaming layout");
   MT_CHECK(fraction >= 0.0 && fraction < 1.0, MT_EINVAL, "mt_tensor_threshold: fraction in [0, 1)");
+  MT_CHECK(!T->L.half, MT_EINVAL,
+           "mt_tensor_threshold: needs every block stored; assemble with MT_LAYOUT_STREAM_FULL");
   MT_CUDA(cudaSetDevice(T->tiles->ctx->device));
   const int64_t n = T->n;
   const mt_layout &L = T->L;

@@ -1,0 +1,144 @@
+"""Half storage of the tensor of a tile set of one shape (Sec. 3.2: the
+tensor is symmetric), through the C ABI.
+
+For cuboids of equal edges the point tensor of tile j at the centre of tile
+i is a function of c_i - c_j that is even in it, so N_ij = N_ji.  An FP32
+streaming tensor of more than 2,048 such tiles stores only the upper
+triangle of column chunks; the product applies each off-diagonal chunk to
+its rows and, transposed, to its columns.  Checked here against the FP64
+oracle (fields at the FP32 tolerance 1e-6, relative L2; stored entries at
+FP32 rounding), against the same tensor stored in full, for batches that
+exercise every group width of the product (1, 2, 3, 5 simulations), on a
+single-layer film (4 entry planes) and a prism (6 planes) whose tile counts
+leave ragged panels and chunks; and in the integrator (fixed steps).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_05364_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2107_05364_gb300 import build
+    build.build()
+    from paper_2107_05364_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(mt):
+    return mt.mt_ctx_create(0)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+GEOMS = {
+    # n = 2,800: 175 panels of 16 rows, 22 chunks of 128 columns (the last ragged)
+    "film70x40": lambda: wl.film(70, 40, 1, size=(350e-9, 200e-9, 3e-9)),
+    # n = 2,520: 157.5 panels (ragged), 6 entry planes
+    "prism15x14x12": lambda: wl.grid_tiles(np.linspace(0, 75e-9, 16), np.linspace(0, 70e-9, 15),
+                                           np.linspace(0, 60e-9, 13), 8e5, 1.3e-11, 0.0),
+}
+
+
+@pytest.fixture(scope="module", params=list(GEOMS))
+def case(mt, ctx, request):
+    t = GEOMS[request.param]()
+    tiles = mt.mt_tiles_create(ctx, t)
+    Th = mt.mt_demag_assemble(tiles, "f32")
+    Tf = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)
+    return request.param, t, tiles, Th, Tf, oracle.Model.from_tiles(t)
+
+
+def test_half_storage_is_chosen_and_smaller(mt, case):
+    name, t, tiles, Th, Tf, md = case
+    ih, ifu = Th.info(), Tf.info()
+    assert ih["half"] == 1 and ifu["half"] == 0
+    assert ih["planes"] == ifu["planes"] == (4 if name.startswith("film") else 6)
+    # the upper triangle of chunks: a bit more than half of the full tensor
+    assert 0.5 < ih["bytes"] / ifu["bytes"] < 0.56
+
+
+def test_half_stored_rows_are_the_tensor(mt, case):
+    # rows read from the half storage (lower blocks taken from their upper
+    # partners) against the oracle's FP64 blocks, at FP32 rounding
+    name, t, tiles, Th, Tf, md = case
+    rows = [0, 15, 16, 127, 128, t.n // 2, t.n - 1]
+    for i in rows:
+        h = mt.mt_tensor_read_rows(Th, i, i + 1)[0]
+        ref = md.N[i]
+        assert np.abs(h - ref).max() <= 2e-7 * np.abs(ref).max(), i
+        f = mt.mt_tensor_read_rows(Tf, i, i + 1)[0]
+        assert np.abs(h - f).max() <= 2e-7 * np.abs(ref).max(), i
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 5])
+def test_half_field_matches_oracle_and_full(mt, case, B):
+    import torch
+    name, t, tiles, Th, Tf, md = case
+    m = np.stack([wl.m_random(t.n, seed=60 + b) for b in range(B)]).astype(np.float32)
+    mg = torch.tensor(m.ravel(), device="cuda")
+    Hh = torch.full_like(mg, float("nan"))
+    Hf = torch.full_like(mg, float("nan"))
+    mt.mt_demag_field(Th, mg, Hh, B=B)
+    mt.mt_demag_field(Tf, mg, Hf, B=B)
+    torch.cuda.synchronize()
+    hh = Hh.cpu().numpy().reshape(B, t.n, 3)
+    hf = Hf.cpu().numpy().reshape(B, t.n, 3)
+    assert np.isfinite(hh).all()
+    for b in range(B):
+        ref = oracle.demag_field(md, m[b].astype(np.float64))
+        assert _rel(hh[b], ref) <= 1e-6, (name, B, b, _rel(hh[b], ref))
+        assert _rel(hh[b], hf[b]) <= 1e-6, (name, B, b)
+    # deterministic: the same bits on a second call
+    H2 = torch.full_like(mg, float("nan"))
+    mt.mt_demag_field(Th, mg, H2, B=B)
+    torch.cuda.synchronize()
+    assert torch.equal(Hh, H2)
+
+
+def test_half_integrator_steps_match_oracle(mt, case):
+    name, t, tiles, Th, Tf, md = case
+    h = 1e-13
+    m0 = wl.m_noisy(t.n, (1, 1, 1), 1e-2, seed=3).astype(np.float32)
+    p, keep = mt.llg_params(1, alpha=0.05, Ha=(1e4, -2e4, 5e3))
+    out = {}
+    for key, T in (("half", Th), ("full", Tf)):
+        I = mt.Integrator(T, p, mt.ode_opts(fixed_h=h))
+        assert I.path() == mt.MT_PATH_GRAPH
+        I.set_state(m0.ravel())
+        I.step(8)
+        out[key] = I.get_state()[0].copy()
+        I.close()
+    so, mo, _, _ = oracle.integrate(md, m0.astype(np.float64), oracle.llg_params(alpha=0.05, Ha=(1e4, -2e4, 5e3)),
+                                    oracle.ode_opts(fixed_h=h), 0.0, 8 * h, 1)
+    assert so == oracle.OK
+    assert np.abs(out["half"] - mo).max() <= 3e-6
+    assert np.abs(out["half"] - out["full"]).max() <= 3e-6
+
+
+def test_half_storage_limits(mt, ctx, case):
+    import torch
+    name, t, tiles, Th, Tf, md = case
+    # thresholding and the allocation-free product need every block
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_tensor_threshold(Th, 0.3)
+    assert e.value.status == mt.MT_EINVAL
+    mg = torch.zeros(3 * t.n, device="cuda")
+    with pytest.raises(mt.MtError) as e:
+        mt.mt_demag_field_noalloc(Th, mg, torch.zeros_like(mg))
+    assert e.value.status == mt.MT_EINVAL
+    # tiles of different shapes, or few tiles, keep every block
+    g = wl.graded_film(60, 40, 1, (300e-9, 200e-9, 3e-9), seed=8)  # n = 2,400, graded
+    assert mt.mt_demag_assemble(mt.mt_tiles_create(ctx, g), "f32").info()["half"] == 0
+    s = wl.film(40, 40, 1)  # 1,600 tiles: the one-kernel integrator path reads rows
+    assert mt.mt_demag_assemble(mt.mt_tiles_create(ctx, s), "f32").info()["half"] == 0

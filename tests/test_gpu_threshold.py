@@ -107,7 +107,7 @@ def test_threshold_full_size_sampled_rows(mt, ctx):
     import torch
     t = wl.film(160, 40, 1)
     tiles = mt.mt_tiles_create(ctx, t)
-    T = mt.mt_demag_assemble(tiles, "f32")
+    T = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)  # thresholding reads every block
     _, _, nz = mt.mt_tensor_threshold(T, 0.0)
     S, thr, kept = mt.mt_tensor_threshold(T, 0.4)
     k = int(0.4 * nz)

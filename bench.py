@@ -710,7 +710,9 @@ def run_hysteresis(args):
     m0 = np.tile(wl.m_noisy(t.n, wl.SP2_DIR, 1e-3, seed=0).astype(np.float32).ravel(), B)
     K = args.values
     rows = []
-    for prec, layout in (("f32", 0), ("split", 1), ("bf16", 1)):
+    # (8 simulations per pass: the FP32 tensor stores every block, the half
+    # storage's product being faster for 1 or 2 simulations only)
+    for prec, layout in (("f32", mt.MT_LAYOUT_STREAM_FULL), ("split", 1), ("bf16", 1)):
         T = mt.mt_demag_assemble_ex(tiles, prec, layout)
         p, keep = mt.llg_params(B, alpha=4000.0, form=mt.MT_FORM_LL, precess=0, exch_scale=(10.0 / d_lex) ** 2)
         I = mt.Integrator(T, p, opts, B=B)
@@ -722,7 +724,8 @@ def run_hysteresis(args):
         mavg, tau, hc, mr, st = I.hysteresis(wl.SP2_DIR, H[:K], 40e-9)
         wall = time.perf_counter() - t0
         rhs = sum(x["n_rhs"] for x in st)
-        rows.append({"product": "%s_%s" % (prec, "dense" if layout else "stream"), "wall_s": wall,
+        rows.append({"product": "%s_%s" % (prec, "dense" if layout == mt.MT_LAYOUT_DENSE else "stream"),
+                     "wall_s": wall,
                      "values_x_sims_per_s": K * B / wall, "rhs_evals_per_s": rhs / wall,
                      "attempts_stiffest": st[0]["n_accept"] + st[0]["n_reject"],
                      "full_loop_hours": wall / K * len(H) / 3600.0})
@@ -1269,9 +1272,10 @@ def run_profile(args):
     """One kernel family on a chosen film, for profiler captures: the
     2.5 x 2.5 x 3 nm cell film of nx x ny x nz tiles; --what field (the
     product, `--reps` calls), step (RK(4,5) attempts through the integrator,
-    on --path), or assemble; --layout stream / stream6 / dense; --threshold F
-    applies the Sec. 4.3.1 sparse tensor.  Prints the average time per call
-    from CUDA events (meaningless under a profiler)."""
+    on --path), or assemble; --layout stream / full (stream without the
+    half storage) / stream6 / dense; --threshold F applies the Sec. 4.3.1
+    sparse tensor.  Prints the average time per call from CUDA events
+    (meaningless under a profiler)."""
     import torch
     torch.cuda.set_device(0)
     from paper_2107_05364_gb300 import binding as mt
@@ -1289,7 +1293,8 @@ def run_profile(args):
         torch.cuda.synchronize()
         print("assemble n=%d: %.3f ms" % (t.n, e0.elapsed_time(e1) / args.reps))
         return
-    layout = {"stream": mt.MT_LAYOUT_STREAM, "dense": mt.MT_LAYOUT_DENSE, "stream6": mt.MT_LAYOUT_STREAM6}[args.layout]
+    layout = {"stream": mt.MT_LAYOUT_STREAM, "full": mt.MT_LAYOUT_STREAM_FULL, "dense": mt.MT_LAYOUT_DENSE,
+              "stream6": mt.MT_LAYOUT_STREAM6}[args.layout]
     T = mt.mt_demag_assemble_ex(tiles, prec, layout)
     if args.threshold is not None:
         S, thr, kept = mt.mt_tensor_threshold(T, args.threshold)
@@ -1368,7 +1373,7 @@ def main():
     ap.add_argument("--what", default="field", choices=["field", "step", "assemble"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sims", type=int, default=1)
-    ap.add_argument("--layout", default="stream", choices=["stream", "dense", "stream6"])
+    ap.add_argument("--layout", default="stream", choices=["stream", "full", "dense", "stream6"])
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--path", default="auto", choices=["auto", "graph", "persistent"])
     args = ap.parse_args()

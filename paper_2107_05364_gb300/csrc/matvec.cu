@@ -91,11 +91,12 @@ struct MvCfg<MT_BF16_SPLIT> {
 template <int PREC, int SB, bool HALF = false>
 struct MvShape {
   using C = MvCfg<PREC>;
-  // consumer warps: W, or 2 W for a half-stored tensor and one simulation
-  // (its chunks carry twice the arithmetic per byte, the row and the column
-  // product, and one warp per SM sub-partition left the issue slots idle on
-  // latency)
-  static constexpr int NCW = (HALF && SB == 1) ? 2 * C::W : C::W;
+  // consumer warps: W, or 2 W for a half-stored tensor and up to two
+  // simulations per chunk read (its chunks carry twice the arithmetic per
+  // byte, the row and the column product, and one warp per SM sub-partition
+  // left the issue slots idle on latency; with four simulations the halved
+  // register budget spills)
+  static constexpr int NCW = (HALF && SB <= 2) ? 2 * C::W : C::W;
   static constexpr int RPW = C::TR / NCW;  // rows per consumer warp
   static constexpr int DATA_BYTES = C::NPLANE * C::TR * C::TC * (int)sizeof(typename C::T);
   static constexpr int SCALE_BYTES = C::SCALED ? C::TR * C::TC : 0;

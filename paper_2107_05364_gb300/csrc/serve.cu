@@ -195,7 +195,11 @@ bool make_resident(mt_server *S, Geometry &g, const std::vector<Geometry *> &all
   e->B = S->o.max_batch;
   e->n = g.n;
   e->slot.resize(e->B);
-  mt_status st = mt_demag_assemble_ex(g.tiles, (mt_prec)S->o.prec, S->o.layout, &e->T);
+  // the half storage (tiles of one shape) pays for one or two simulations
+  // per pass; an engine of 3 or more slots streams every block
+  const int layout =
+      (S->o.layout == MT_LAYOUT_STREAM && e->B >= 3) ? (int)MT_LAYOUT_STREAM_FULL : (int)S->o.layout;
+  mt_status st = mt_demag_assemble_ex(g.tiles, (mt_prec)S->o.prec, layout, &e->T);
   if (st == MT_OK) {
     std::vector<double> alpha(e->B, 0.5), Ha(3 * e->B, 0.0);
     mt_llg_params p{S->o.gamma, alpha.data(), Ha.data(), S->o.form, 1, nullptr};

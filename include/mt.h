@@ -83,8 +83,11 @@ typedef enum {
                         /* (made by mt_tensor_threshold, Sec. 4.3.1)            */
   MT_LAYOUT_STREAM6 = 3, /* MT_LAYOUT_STREAM with all 6 entry planes and every  */
                         /* block stored (see mt_demag_assemble)                */
-  MT_LAYOUT_STREAM_FULL = 4 /* MT_LAYOUT_STREAM with every block stored (no use  */
+  MT_LAYOUT_STREAM_FULL = 4, /* MT_LAYOUT_STREAM with every block stored (no use */
                         /* of N_ij = N_ji; planes as for MT_LAYOUT_STREAM)      */
+  MT_LAYOUT_STREAM_HALF = 5 /* MT_LAYOUT_STREAM with the half storage of tiles  */
+                        /* of one shape at any size (FP32 cuboids of one shape */
+                        /* only, else MT_EINVAL; see mt_demag_assemble)         */
 } mt_layout_kind;
 
 /* Equation-of-motion form. */
@@ -240,8 +243,9 @@ MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **ou
  * Tiles of one shape.  When every cuboid has the same edges, the point
  * tensor of tile j at the centre of tile i depends only on c_i - c_j and is
  * even in it, so N_ij = N_ji and the whole tensor is symmetric (Sec. 3.2).
- * An FP32 streaming tensor of more than 2,048 such tiles then stores only
- * the upper triangle: 16-row panel p keeps its 128-column chunks from the
+ * An FP32 streaming tensor of more than 4,096 such tiles (any number with
+ * MT_LAYOUT_STREAM_HALF; below ~3,600 tiles the full storage's product is
+ * the faster one, one simulation) then stores only the upper triangle: 16-row panel p keeps its 128-column chunks from the
  * one holding its own rows on (about n^2 / 2 blocks); the product applies
  * each off-diagonal chunk to its rows and, transposed, to its columns (a
  * column work area of 1.5 KB per stored chunk and simulation, held by the

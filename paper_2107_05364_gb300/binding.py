@@ -19,7 +19,8 @@ from . import build as _build
 MT_OK, MT_EINVAL, MT_ENOMEM, MT_EOVERLAP, MT_ENOCONV, MT_ETIMEOUT, MT_ENONFINITE, MT_ECUDA, MT_EBUSY = range(9)
 MT_F64, MT_F32, MT_BF16_SCALED, MT_BF16_SPLIT = range(4)
 MT_FORM_GILBERT, MT_FORM_LL = 0, 1
-MT_LAYOUT_STREAM, MT_LAYOUT_DENSE, MT_LAYOUT_SPARSE, MT_LAYOUT_STREAM6, MT_LAYOUT_STREAM_FULL = 0, 1, 2, 3, 4
+(MT_LAYOUT_STREAM, MT_LAYOUT_DENSE, MT_LAYOUT_SPARSE, MT_LAYOUT_STREAM6, MT_LAYOUT_STREAM_FULL,
+ MT_LAYOUT_STREAM_HALF) = 0, 1, 2, 3, 4, 5
 MT_PATH_GRAPH, MT_PATH_PERSISTENT = 1, 2
 PREC_NAMES = {"f64": MT_F64, "f32": MT_F32, "bf16": MT_BF16_SCALED, "bf16_scaled": MT_BF16_SCALED,
               "split": MT_BF16_SPLIT, "bf16_split": MT_BF16_SPLIT}

@@ -457,11 +457,15 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
   MT_CHECK(tiles && out, MT_EINVAL, "mt_demag_assemble: NULL argument");
   MT_CHECK(prec >= MT_F64 && prec <= MT_BF16_SPLIT, MT_EINVAL, "mt_demag_assemble: bad precision %d", (int)prec);
   MT_CHECK(layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_DENSE || layout == MT_LAYOUT_STREAM6 ||
-               layout == MT_LAYOUT_STREAM_FULL,
+               layout == MT_LAYOUT_STREAM_FULL || layout == MT_LAYOUT_STREAM_HALF,
            MT_EINVAL, "mt_demag_assemble: bad layout %d", layout);
-  const bool allow_planar = layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_STREAM_FULL;
-  const bool allow_half = layout == MT_LAYOUT_STREAM;
-  if (layout == MT_LAYOUT_STREAM6 || layout == MT_LAYOUT_STREAM_FULL) layout = MT_LAYOUT_STREAM;
+  const bool allow_planar =
+      layout == MT_LAYOUT_STREAM || layout == MT_LAYOUT_STREAM_FULL || layout == MT_LAYOUT_STREAM_HALF;
+  const bool force_half = layout == MT_LAYOUT_STREAM_HALF;
+  const bool allow_half = layout == MT_LAYOUT_STREAM || force_half;
+  MT_CHECK(!force_half || (prec == MT_F32 && tiles->kind == MT_TILE_CUBOID), MT_EINVAL,
+           "mt_demag_assemble: MT_LAYOUT_STREAM_HALF stores FP32 tensors of cuboid tiles only");
+  if (layout != MT_LAYOUT_DENSE) layout = MT_LAYOUT_STREAM;
   MT_CHECK(layout == MT_LAYOUT_STREAM || prec == MT_BF16_SCALED || prec == MT_BF16_SPLIT, MT_EINVAL,
            "mt_demag_assemble: the dense layout stores BF16 or split BF16 only");
   mt_ctx *ctx = tiles->ctx;
@@ -495,10 +499,10 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
     }
     T->L.P = (T->n + T->L.TR - 1) / T->L.TR;
     T->L.Q = (T->n + T->L.TC - 1) / T->L.TC;
-    // FP32 tiles of one shape beyond the one-kernel path's range: the
-    // tensor is symmetric (N_ij = N_ji), so only the upper triangle of
-    // chunks is stored (Sec. 3.2)
-    if (allow_half && prec == MT_F32 && tiles->kind == MT_TILE_CUBOID && T->n > kHalfMinTiles) {
+    // FP32 tiles of one shape: the tensor is symmetric (N_ij = N_ji), so
+    // only the upper triangle of chunks is stored (Sec. 3.2); by default
+    // from kHalfMinTiles tiles on, where the half product is the faster one
+    if (allow_half && prec == MT_F32 && tiles->kind == MT_TILE_CUBOID && (force_half || T->n > kHalfMinTiles)) {
       // one shape: equal edges to 1e-12 (as for the lattice test; the
       // tensor then differs from a symmetric one far below FP32 rounding)
       bool same = true;
@@ -506,6 +510,11 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
         for (int a = 0; a < 3; ++a)
           same = same && std::fabs(tiles->edge[3 * i + a] - tiles->edge[a]) <= 1e-12 * tiles->edge[a];
       T->L.half = same;
+    }
+    if (force_half && !T->L.half) {
+      delete T;
+      mt::tiles_release(tiles);
+      MT_CHECK(false, MT_EINVAL, "mt_demag_assemble: MT_LAYOUT_STREAM_HALF needs tiles of one shape");
     }
     T->L.CH = T->L.half ? half_cum(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
     data_bytes = (size_t)T->L.CH * T->L.chunk_bytes();

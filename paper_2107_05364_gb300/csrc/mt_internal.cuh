@@ -221,9 +221,12 @@ __host__ __device__ __forceinline__ int stream_plane(int e, int nplane) {
 // bound on |N_xz|, |N_yz| of a single-layer tile set (FP64 round-off of
 // entries that vanish by mirror symmetry)
 constexpr double kPlanarTol = 1e-12;
-// half storage from this many tiles on (smaller FP32 tensors are read from
-// L2 or shared memory by the one-kernel integrator path, which wants rows)
-constexpr int64_t kHalfMinTiles = 2048;
+// MT_LAYOUT_STREAM stores a tensor of tiles of one shape half from this many
+// tiles on: measured on single-layer films, one simulation, per attempted
+// integrator step, half against full storage 0.178 / 0.140 ms at 2,500 tiles,
+// 0.255 / 0.253 at 3,600, 0.384 / 0.413 at 4,900, 0.516 / 0.646 at 6,400
+// (the column pass costs a fixed ~15 us that a small tensor does not repay)
+constexpr int64_t kHalfMinTiles = 4096;
 
 // Index of entry e of block (i, j) in the tile-blocked streaming layout.
 __host__ __device__ __forceinline__ int64_t layout_index(int64_t i, int64_t j, int e, int TR, int TC, int nplane,

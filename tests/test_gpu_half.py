@@ -3,9 +3,11 @@ tensor is symmetric), through the C ABI.
 
 For cuboids of equal edges the point tensor of tile j at the centre of tile
 i is a function of c_i - c_j that is even in it, so N_ij = N_ji.  An FP32
-streaming tensor of more than 2,048 such tiles stores only the upper
-triangle of column chunks; the product applies each off-diagonal chunk to
-its rows and, transposed, to its columns.  Checked here against the FP64
+streaming tensor of such tiles stores only the upper triangle of column
+chunks (by default from 4,096 tiles on; at any size with
+MT_LAYOUT_STREAM_HALF, used here to keep the oracle's tensors small); the
+product applies each off-diagonal chunk to its rows and, transposed, to its
+columns.  Checked here against the FP64
 oracle (fields at the FP32 tolerance 1e-6, relative L2; stored entries at
 FP32 rounding), against the same tensor stored in full, for batches that
 exercise every group width of the product (1, 2, 3, 5 simulations), on a
@@ -54,7 +56,7 @@ GEOMS = {
 def case(mt, ctx, request):
     t = GEOMS[request.param]()
     tiles = mt.mt_tiles_create(ctx, t)
-    Th = mt.mt_demag_assemble(tiles, "f32")
+    Th = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_HALF)
     Tf = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)
     return request.param, t, tiles, Th, Tf, oracle.Model.from_tiles(t)
 
@@ -137,8 +139,16 @@ def test_half_storage_limits(mt, ctx, case):
     with pytest.raises(mt.MtError) as e:
         mt.mt_demag_field_noalloc(Th, mg, torch.zeros_like(mg))
     assert e.value.status == mt.MT_EINVAL
-    # tiles of different shapes, or few tiles, keep every block
-    g = wl.graded_film(60, 40, 1, (300e-9, 200e-9, 3e-9), seed=8)  # n = 2,400, graded
-    assert mt.mt_demag_assemble(mt.mt_tiles_create(ctx, g), "f32").info()["half"] == 0
-    s = wl.film(40, 40, 1)  # 1,600 tiles: the one-kernel integrator path reads rows
-    assert mt.mt_demag_assemble(mt.mt_tiles_create(ctx, s), "f32").info()["half"] == 0
+    # tiles of different shapes keep every block; the explicit half layout
+    # refuses them and other precisions
+    g = mt.mt_tiles_create(ctx, wl.graded_film(60, 40, 1, (300e-9, 200e-9, 3e-9), seed=8))  # n = 2,400
+    assert mt.mt_demag_assemble(g, "f32").info()["half"] == 0
+    for tl, prec in ((g, "f32"), (tiles, "split"), (tiles, "bf16"), (tiles, "f64")):
+        with pytest.raises(mt.MtError) as e:
+            mt.mt_demag_assemble_ex(tl, prec, mt.MT_LAYOUT_STREAM_HALF)
+        assert e.value.status == mt.MT_EINVAL
+    # the default layout: full storage up to 4,096 tiles of one shape, half above
+    assert mt.mt_demag_assemble(tiles, "f32").info()["half"] == 0
+    big = mt.mt_tiles_create(ctx, wl.film(80, 52, 1, size=(400e-9, 260e-9, 3e-9)))  # n = 4,160
+    assert mt.mt_demag_assemble(big, "f32").info()["half"] == 1
+    assert mt.mt_demag_assemble_ex(big, "f32", mt.MT_LAYOUT_STREAM_FULL).info()["half"] == 0

@@ -516,7 +516,7 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
       mt::tiles_release(tiles);
       MT_CHECK(false, MT_EINVAL, "mt_demag_assemble: MT_LAYOUT_STREAM_HALF needs tiles of one shape");
     }
-    T->L.CH = T->L.half ? half_cum(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
+    T->L.CH = T->L.half ? half_chunks(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
     data_bytes = (size_t)T->L.CH * T->L.chunk_bytes();
     scale_bytes = (size_t)T->L.CH * T->L.scale_bytes_per_chunk;
   }

@@ -618,7 +618,7 @@ mt_status assemble(mt_tensor *T) {
     T->L.P = (n + T->L.TR - 1) / T->L.TR;
     T->L.Q = (n + T->L.TC - 1) / T->L.TC;
     T->L.half = half;
-    T->L.CH = half ? half_cum(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
+    T->L.CH = half ? half_chunks(T->L.P, T->L.Q, T->L.TC / T->L.TR) : T->L.P * T->L.Q;
     const size_t bytes = (size_t)T->L.CH * (T->L.chunk_bytes() + T->L.scale_bytes_per_chunk);
     {
       std::lock_guard<std::mutex> lk(ctx->mu);

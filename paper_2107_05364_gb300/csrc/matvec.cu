@@ -21,6 +21,7 @@
 //     order, so the result does not depend on timing.
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "mt_internal.cuh"
 
@@ -88,32 +89,24 @@ struct MvCfg<MT_BF16_SPLIT> {
   static constexpr bool SCALED = false, PLANAR = false;
 };
 
-template <int PREC, int SB, bool HALF = false>
+template <int PREC, int SB>
 struct MvShape {
   using C = MvCfg<PREC>;
-  // consumer warps: W, or 2 W for a half-stored tensor and up to two
-  // simulations per chunk read (its chunks carry twice the arithmetic per
-  // byte, the row and the column product, and one warp per SM sub-partition
-  // left the issue slots idle on latency; with four simulations the halved
-  // register budget spills)
-  static constexpr int NCW = (HALF && SB <= 2) ? 2 * C::W : C::W;
+  static constexpr int NCW = C::W;         // consumer warps
   static constexpr int RPW = C::TR / NCW;  // rows per consumer warp
   static constexpr int DATA_BYTES = C::NPLANE * C::TR * C::TC * (int)sizeof(typename C::T);
   static constexpr int SCALE_BYTES = C::SCALED ? C::TR * C::TC : 0;
   static constexpr int XS_BYTES = 3 * C::TC * (int)sizeof(typename C::Acc);  // one simulation's slice
   static constexpr int STAGE_BYTES = DATA_BYTES + SCALE_BYTES + SB * XS_BYTES;
-  // half storage: the consumer warps' column sums of a chunk, double buffered
-  static constexpr int CB_BYTES = HALF ? 2 * NCW * SB * 3 * C::TC * (int)sizeof(typename C::Acc) : 0;
   // ring depth: up to C::STAGES within 226 KB of shared memory (the
   // barriers and the abort flag fill the rest of the 227 KB a CTA may have)
-  static constexpr int STAGES = (C::STAGES * STAGE_BYTES + CB_BYTES <= 226 * 1024)
-                                    ? C::STAGES
-                                    : (226 * 1024 - CB_BYTES) / STAGE_BYTES;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + CB_BYTES + 2 * STAGES * 8 + 16;
+  static constexpr int STAGES =
+      (C::STAGES * STAGE_BYTES <= 226 * 1024) ? C::STAGES : (226 * 1024) / STAGE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16;
   static_assert(SMEM_BYTES <= 227 * 1024, "shared memory of one CTA");
   static constexpr int THREADS = (NCW + 1) * 32;
   static_assert(STAGES >= 2, "at least a double-buffered ring");
-  static_assert(C::TR % NCW == 0 && (!HALF || (NCW * 32) % C::TC == 0), "whole rows per warp, whole column sets");
+  static_assert(C::TR % NCW == 0, "whole rows per warp");
   static_assert(C::TC == 32 * C::VEC, "a warp covers one chunk row");
   static_assert(3 * RPW <= 32, "one lane per (row, component) in the flush");
   static_assert(DATA_BYTES % 16 == 0 && SCALE_BYTES % 16 == 0 && XS_BYTES % 16 == 0, "bulk copy sizes");
@@ -182,57 +175,33 @@ struct MvArgs {
   const int *active;
   int *status;
   int64_t n, P, Q;
-  int64_t CH;     // stored chunks per group of simulations
-  float *colpart; // half storage: column sums [unit][SB][3][TC]
-  int *arrive;    // half storage: k_half_cols arrival counters [B][Q], zeroed by k_matvec
+  int64_t CH;  // stored chunks
   int B;
 };
 
-// slices of a column chunk's panel range in k_half_cols: about 32 panels each
-inline int half_col_slices(int64_t P) { return (int)std::max<int64_t>(1, std::min<int64_t>(64, (P + 31) / 32)); }
 
 // Units in storage order: (group of simulations g, stored chunk c) with c
-// the chunk (panel p, column chunk q).  Without half storage c = p Q + q;
-// with it panel p holds chunks q0(p) .. Q-1 (see half_cum).
+// the chunk (panel p, column chunk q) = p Q + q.
 struct UnitCursor {
   int64_t g, p, q, c;
 };
-template <int K, bool HALF>
 __device__ __forceinline__ void unit_decode(const MvArgs &A, int64_t u, UnitCursor &cu) {
   cu.g = u / A.CH;
   cu.c = u - cu.g * A.CH;
-  if (!HALF) {
-    cu.p = cu.c / A.Q;
-    cu.q = cu.c - cu.p * A.Q;
-    return;
-  }
-  int64_t lo = 0, hi = A.P - 1;  // the last panel whose first chunk is <= c
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (half_cum(mid, A.Q, K) <= cu.c) lo = mid;
-    else hi = mid - 1;
-  }
-  cu.p = lo;
-  cu.q = half_q0(lo, K) + (cu.c - half_cum(lo, A.Q, K));
+  cu.p = cu.c / A.Q;
+  cu.q = cu.c - cu.p * A.Q;
 }
-template <int K, bool HALF>
 __device__ __forceinline__ void unit_next(const MvArgs &A, UnitCursor &cu) {
   ++cu.c;
   if (++cu.q == A.Q) {
     ++cu.p;
-    cu.q = HALF ? half_q0(cu.p, K) : 0;
+    cu.q = 0;
   }
   if (cu.c == A.CH) {
     cu.c = 0;
     ++cu.g;
     cu.p = 0;
-    cu.q = 0;
   }
-}
-// first unit of panel p of group g
-template <int K, bool HALF>
-__device__ __forceinline__ int64_t panel_first_unit(const MvArgs &A, int64_t g, int64_t p) {
-  return g * A.CH + (HALF ? half_cum(p, A.Q, K) : p * A.Q);
 }
 
 // SB simulations share every chunk read: unit = (group of SB simulations,
@@ -248,21 +217,14 @@ __device__ __forceinline__ bool group_live(const MvArgs &A, int64_t g, int SB) {
   return false;
 }
 
-template <int PREC, int SB, bool HALF>
-__global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(MvArgs A) {
+template <int PREC, int SB>
+__global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs A) {
   mtd::pdl_enter();
   using C = MvCfg<PREC>;
-  using S = MvShape<PREC, SB, HALF>;
-  if constexpr (HALF) {  // the column pass that follows counts its arrivals from zero
-    for (int64_t k = blockIdx.x * (int64_t)S::THREADS + threadIdx.x; k < (int64_t)A.B * A.Q;
-         k += (int64_t)gridDim.x * S::THREADS)
-      A.arrive[k] = 0;
-  }
+  using S = MvShape<PREC, SB>;
   using Acc = typename C::Acc;
-  constexpr int K = C::TC / C::TR;  // panels per column chunk
   extern __shared__ __align__(128) unsigned char smem[];
-  Acc *cb = reinterpret_cast<Acc *>(smem + S::STAGES * S::STAGE_BYTES);  // half: column sums
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES + S::CB_BYTES);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES);
   uint64_t *empty = full + S::STAGES;
   volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + S::STAGES);
 
@@ -291,8 +253,8 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
       const unsigned char *xs = reinterpret_cast<const unsigned char *>(A.xs);
       int it = 0;
       UnitCursor cu;
-      unit_decode<K, HALF>(A, u0, cu);
-      for (int64_t u = u0; u < u1; ++u, unit_next<K, HALF>(A, cu)) {
+      unit_decode(A, u0, cu);
+      for (int64_t u = u0; u < u1; ++u, unit_next(A, cu)) {
         const int64_t g = cu.g, q = cu.q;
         if (!group_live(A, g, SB)) continue;
         const int s = it % S::STAGES;
@@ -328,9 +290,8 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
 
   // ---------------- consumers ----------------
   Acc acc[SB][S::RPW][3];
-  Acc xi[HALF ? SB : 1][S::RPW][3];  // half: the operand of this warp's rows (the transposed product)
   int64_t gp_cur = -1;
-  int it = 0, strict_it = 0;
+  int it = 0;
   bool aborted = false;
 
   auto flush = [&](int64_t gp) {
@@ -342,7 +303,7 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[m][r][c] = mtd::warp_sum(acc[m][r][c]);
     const int64_t g = gp / A.P, p = gp - g * A.P;
-    const int64_t pu0 = panel_first_unit<K, HALF>(A, g, p), pu1 = panel_first_unit<K, HALF>(A, g, p + 1);
+    const int64_t pu0 = g * A.CH + p * A.Q, pu1 = pu0 + A.Q;  // the panel's units
     const int64_t kf = mtd::sk_owner(pu0, U, G), kl = mtd::sk_owner(pu1 - 1, U, G);
     // this lane's (row, component)
     const int lr = lane / 3, lc = lane - 3 * (lane / 3);
@@ -401,8 +362,8 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
   };
 
   UnitCursor cu;
-  unit_decode<K, HALF>(A, u0, cu);
-  for (int64_t u = u0; u < u1; ++u, unit_next<K, HALF>(A, cu)) {
+  unit_decode(A, u0, cu);
+  for (int64_t u = u0; u < u1; ++u, unit_next(A, cu)) {
     const int64_t g = cu.g, gp = g * A.P + cu.p;
     if (!group_live(A, g, SB)) continue;
     if (gp != gp_cur) {
@@ -412,30 +373,6 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
       for (int m = 0; m < SB; ++m)
 #pragma unroll
         for (int r = 0; r < S::RPW; ++r) acc[m][r][0] = acc[m][r][1] = acc[m][r][2] = 0;
-      if constexpr (HALF) {
-        // the operand of this warp's rows, for the transposed product
-        const Acc *xsg = reinterpret_cast<const Acc *>(A.xs);
-#pragma unroll
-        for (int m = 0; m < SB; ++m) {
-          const int64_t b = g * SB + m < A.B ? g * SB + m : 0;
-#pragma unroll
-          for (int r = 0; r < S::RPW; ++r) {
-            const int64_t i = cu.p * C::TR + warp * S::RPW + r;
-            const int64_t qi = i / C::TC, ti = i - qi * C::TC;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) xi[m][r][c] = __ldg(&xsg[((b * A.Q + qi) * 3 + c) * C::TC + ti]);
-          }
-        }
-      }
-    }
-    // an off-diagonal chunk of the half storage also serves its columns
-    const bool strict = HALF && cu.q > half_q0(cu.p, K);
-    Acc colp[HALF ? SB : 1][C::VEC][3];
-    if constexpr (HALF) {
-#pragma unroll
-      for (int m = 0; m < SB; ++m)
-#pragma unroll
-        for (int v = 0; v < C::VEC; ++v) colp[m][v][0] = colp[m][v][1] = colp[m][v][2] = 0;
     }
     const int s = it % S::STAGES;
     const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
@@ -491,19 +428,6 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
             acc[m][r][1] += sy;
             acc[m][r][2] += sz;
           }
-          if constexpr (HALF) {
-            if (strict) {
-              // block (row, v) transposed: the same symmetric block times this row's operand
-#pragma unroll
-              for (int m = 0; m < SB; ++m)
-#pragma unroll
-                for (int v = 0; v < C::VEC; ++v) {
-                  colp[m][v][0] = fma(nxx[v], xi[m][r][0], fma(nxy[v], xi[m][r][1], colp[m][v][0]));
-                  colp[m][v][1] = fma(nxy[v], xi[m][r][0], fma(nyy[v], xi[m][r][1], colp[m][v][1]));
-                  colp[m][v][2] = fma(nzz[v], xi[m][r][2], colp[m][v][2]);
-                }
-            }
-          }
           continue;
         }
         Acc nxx[C::VEC], nxy[C::VEC], nxz[C::VEC], nyy[C::VEC], nyz[C::VEC], nzz[C::VEC];
@@ -541,103 +465,505 @@ __global__ void __launch_bounds__(MvShape<PREC, SB, HALF>::THREADS, 1) k_matvec(
           acc[m][r][1] += sy;
           acc[m][r][2] += sz;
         }
-        if constexpr (HALF) {
-          if (strict) {
-#pragma unroll
-            for (int m = 0; m < SB; ++m)
-#pragma unroll
-              for (int v = 0; v < C::VEC; ++v) {
-                colp[m][v][0] =
-                    fma(nxx[v], xi[m][r][0], fma(nxy[v], xi[m][r][1], fma(nxz[v], xi[m][r][2], colp[m][v][0])));
-                colp[m][v][1] =
-                    fma(nxy[v], xi[m][r][0], fma(nyy[v], xi[m][r][1], fma(nyz[v], xi[m][r][2], colp[m][v][1])));
-                colp[m][v][2] =
-                    fma(nxz[v], xi[m][r][0], fma(nyz[v], xi[m][r][1], fma(nzz[v], xi[m][r][2], colp[m][v][2])));
-              }
-          }
-        }
       }
     }
     __syncwarp();
     if (lane == 0) mtd::mbar_arrive(&empty[s]);
-    if constexpr (HALF) {
-      if (strict) {
-        // column sums of the chunk: each warp's partial (its rows) to shared
-        // memory, then thread t sums column t % TC, components t / TC,
-        // t / TC + NCW 32 / TC, ..., over the warps in order, and writes them
-        // to the chunk's slot of the work area
-        const int buf = strict_it & 1;
-        ++strict_it;
-        Acc *mine = cb + (size_t)((buf * S::NCW + warp) * SB) * 3 * C::TC;
-#pragma unroll
-        for (int m = 0; m < SB; ++m)
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            *reinterpret_cast<float4 *>(mine + (m * 3 + c) * C::TC + lane * C::VEC) =
-                make_float4(colp[m][0][c], colp[m][1][c], colp[m][2][c], colp[m][3][c]);
-        asm volatile("bar.sync 1, %0;" ::"r"(S::NCW * 32) : "memory");
-        constexpr int NT = S::NCW * 32 / C::TC;  // thread sets over the columns
-        const int t = warp * 32 + lane, col = t % C::TC;
-        const int64_t uu = cu.g * A.CH + cu.c;
-#pragma unroll
-        for (int m = 0; m < SB; ++m) {
-          if (g * SB + m >= A.B) continue;
-#pragma unroll
-          for (int c0 = 0; c0 < 3; c0 += NT) {
-            const int c = c0 + t / C::TC;
-            if (c >= 3) break;
-            Acc tot = 0;
-#pragma unroll
-            for (int w = 0; w < S::NCW; ++w) tot += cb[((size_t)((buf * S::NCW + w) * SB + m) * 3 + c) * C::TC + col];
-            A.colpart[((uu * SB + m) * 3 + c) * C::TC + col] = tot;
-          }
-        }
-      }
-    }
   }
   if (gp_cur >= 0) flush(gp_cur);
 }
 
-// Half storage: the transposed part of the product.  Column j of chunk q
-// received, from every panel p whose chunk (p, q) lies above the diagonal
-// (p < K q), the column sums that chunk left in the work area.  CTA (q, s, b)
-// sums the panels of slice s of that range (NS slices, in increasing p) and
-// parks its sums; the last CTA of (q, b) to arrive adds the NS slice sums in
+// ===========================================================================
+// Half-stored tensors (tiles of one shape, N_ij = N_ji; order: half_gbase).
+// k_matvec_half streams the stored chunks in order, a group of K chunks at a
+// time: the K panels of super-row R against column chunk q.  Each chunk is
+// applied to its rows; a group above the diagonal (q > R) is applied,
+// transposed, to its columns too.  Its K chunks arrive one after the other,
+// so a thread keeps its columns' sums over the whole group in registers, and
+// the consumer warps meet once per group (not per chunk) to add them.  A
+// group's column sums go to the work area (a group split between two CTAs
+// is finished by the last of them to arrive, adding the parts in CTA
+// order); k_half_cols then adds, for each column chunk q, the sums of the
+// groups (R, q), R < q, in order of R and subtracts them from H.  Up to 2
+// simulations share a chunk read (more take several passes: their row
+// sums would not fit the registers).
+template <int PREC, int SB>
+struct HalfShape {
+  using C = MvCfg<PREC>;
+  static constexpr int K = C::TC / C::TR;  // panels per super-row
+  static constexpr int NCW = 2 * C::W;     // consumer warps
+  static constexpr int RPW = C::TR / NCW;  // rows of each panel per warp
+  static constexpr int DATA_BYTES = C::NPLANE * C::TR * C::TC * 4;
+  static constexpr int XS_BYTES = 3 * C::TC * 4;
+  static constexpr int STAGE_BYTES = DATA_BYTES + SB * XS_BYTES;
+  static constexpr int CB_BYTES = NCW * SB * 3 * C::TC * 4;  // the warps' column sums of a group
+  static constexpr int XI_BYTES = NCW * SB * K * RPW * 16;   // each warp's row operand (x, y, z, 0)
+  static constexpr int STAGES = (C::STAGES * STAGE_BYTES + CB_BYTES + XI_BYTES <= 226 * 1024)
+                                    ? C::STAGES
+                                    : (226 * 1024 - CB_BYTES - XI_BYTES) / STAGE_BYTES;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + CB_BYTES + XI_BYTES + 2 * STAGES * 8 + 16;
+  static constexpr int THREADS = (NCW + 1) * 32;
+  static constexpr int NV = K * RPW * 3;  // row values a warp holds per simulation
+  static_assert(SB == 1 || SB == 2, "one or two simulations per chunk read");
+  static_assert(C::VEC == 4 && C::TC == 32 * C::VEC && C::TR % NCW == 0, "float4 columns, whole rows per warp");
+  static_assert((NCW * 32) % C::TC == 0 && NV <= 64 && 16 * SB <= 32, "flush and operand lanes");
+  static_assert(STAGES >= 2 && SMEM_BYTES <= 227 * 1024, "ring within one CTA's shared memory");
+};
+
+struct HalfArgs {
+  const float *tensor;
+  const float *xs;   // [b][q][3][TC], Ms m
+  float *H;
+  float *part;       // row partials of super-rows shared by CTAs [2 G][SB][K TR][3]
+  int *count;        // arrival counters per (simulation group, super-row, warp)
+  int *gcount;       // arrival counters per (simulation group, group)
+  float *colpart;    // column sums of every group above the diagonal [NG][NGR][SB][3][TC]
+  float *colsplit;   // parts of the groups shared by CTAs [2 G][SB][3][TC]
+  int *arrive;       // k_half_cols arrival counters [B][Q], zeroed by k_matvec_half
+  const int *active;
+  int *status;
+  int64_t n, P, Q, CH, NGR;  // NGR = Q (Q + 1) / 2 groups
+  int B;
+};
+
+__device__ __forceinline__ bool half_live(const HalfArgs &A, int64_t g, int SB) {
+  if (!A.active) return true;
+  for (int s = 0; s < SB; ++s) {
+    const int64_t b = g * SB + s;
+    if (b < A.B && A.active[b]) return true;
+  }
+  return false;
+}
+
+// (simulation group g, group gi = (super-row R, column chunk q)) in storage
+// order; a group's first unit is g CH + K gi, its length K except for the
+// last group (the last super-row's diagonal), CH - K (NGR - 1)
+struct GroupCursor {
+  int64_t g, R, q, gi;
+};
+template <int K>
+__device__ __forceinline__ int64_t group_decode(const HalfArgs &A, int64_t u, GroupCursor &gc) {
+  gc.g = u / A.CH;
+  const int64_t c = u - gc.g * A.CH;
+  gc.gi = c / K;
+  int64_t lo = 0, hi = A.Q - 1;  // the last super-row whose first group is <= gi
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (half_gbase(mid, A.Q) <= gc.gi) lo = mid;
+    else hi = mid - 1;
+  }
+  gc.R = lo;
+  gc.q = lo + (gc.gi - half_gbase(lo, A.Q));
+  return u - (c - K * gc.gi);  // the group's first unit
+}
+__device__ __forceinline__ void group_next(const HalfArgs &A, GroupCursor &gc) {
+  ++gc.gi;
+  if (++gc.q == A.Q) {
+    ++gc.R;
+    gc.q = gc.R;
+  }
+  if (gc.gi == A.NGR) {
+    gc.gi = 0;
+    ++gc.g;
+    gc.R = 0;
+    gc.q = 0;
+  }
+}
+template <int K>
+__device__ __forceinline__ int group_len(const HalfArgs &A, const GroupCursor &gc) {
+  return gc.gi == A.NGR - 1 ? (int)(A.CH - (int64_t)K * (A.NGR - 1)) : K;
+}
+
+template <int PREC, int SB>
+__global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half(HalfArgs A) {
+  mtd::pdl_enter();
+  using C = MvCfg<PREC>;
+  using S = HalfShape<PREC, SB>;
+  constexpr int K = S::K, TR = C::TR, TC = C::TC;
+  // the column pass that follows counts its arrivals from zero
+  for (int64_t i = blockIdx.x * (int64_t)S::THREADS + threadIdx.x; i < (int64_t)A.B * A.Q;
+       i += (int64_t)gridDim.x * S::THREADS)
+    A.arrive[i] = 0;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *cb = reinterpret_cast<float *>(smem + S::STAGES * S::STAGE_BYTES);
+  float4 *xi_all = reinterpret_cast<float4 *>(smem + S::STAGES * S::STAGE_BYTES + S::CB_BYTES);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES + S::CB_BYTES + S::XI_BYTES);
+  uint64_t *empty = full + S::STAGES;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + S::STAGES);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t G = gridDim.x, kcta = blockIdx.x;
+  const int64_t NG = (A.B + SB - 1) / SB;
+  const int64_t U = NG * A.CH;
+  const int64_t u0 = mtd::sk_begin(kcta, U, G), u1 = mtd::sk_begin(kcta + 1, U, G);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S::STAGES; ++s) {
+      mtd::mbar_init(&full[s], 1);
+      mtd::mbar_init(&empty[s], S::NCW);
+    }
+    *abort_flag = 0;
+    mtd::fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == S::NCW) {
+    // ---------------- producer: the CTA's units in storage order ----------------
+    if (lane == 0) {
+      const uint64_t pol_stream = mtd::policy_evict_first();
+      const uint64_t pol_keep = mtd::policy_evict_last();
+      const unsigned char *tens = reinterpret_cast<const unsigned char *>(A.tensor);
+      const unsigned char *xs = reinterpret_cast<const unsigned char *>(A.xs);
+      int it = 0;
+      GroupCursor gc;
+      bool stop = false;
+      for (int64_t gs = group_decode<K>(A, u0, gc); gs < u1 && !stop; gs += group_len<K>(A, gc), group_next(A, gc)) {
+        if (!half_live(A, gc.g, SB)) continue;
+        const int len = group_len<K>(A, gc);
+        const int kb = (int)(u0 > gs ? u0 - gs : 0), ke = (int)(u1 - gs < len ? u1 - gs : len);
+        for (int k = kb; k < ke; ++k) {
+          const int s = it % S::STAGES;
+          const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
+          if (it >= S::STAGES) {
+            if (*abort_flag || !mtd::mbar_wait_bounded(&empty[s], ph ^ 1u, A.status)) {
+              *abort_flag = 1;
+              stop = true;
+              break;
+            }
+          }
+          unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
+          const int64_t c = gs - gc.g * A.CH + k;  // stored chunk
+          mtd::mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+          mtd::bulk_g2s(st, tens + (size_t)c * S::DATA_BYTES, S::DATA_BYTES, &full[s], pol_stream);
+#pragma unroll
+          for (int m = 0; m < SB; ++m) {
+            const int64_t b = gc.g * SB + m < A.B ? gc.g * SB + m : 0;
+            mtd::bulk_g2s(st + S::DATA_BYTES + m * S::XS_BYTES, xs + (size_t)(b * A.Q + gc.q) * S::XS_BYTES,
+                          S::XS_BYTES, &full[s], pol_keep);
+          }
+          ++it;
+        }
+      }
+      // drain: every copy issued must have landed before the CTA may exit
+      for (int s = 0; s < S::STAGES && s < it; ++s) {
+        const int last = it - 1 - ((it - 1 - s) % S::STAGES);  // last issue on stage s
+        mtd::mbar_wait_bounded(&full[s], (uint32_t)(last / S::STAGES) & 1u, A.status);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  // warp w holds rows w RPW + r (r < RPW) of each of the K panels of the
+  // current super-row; lane l holds columns 4 l .. 4 l + 3
+  float acc[SB][K][S::RPW][3];
+  float4 *xi = xi_all + warp * SB * K * S::RPW;  // [m][k RPW + r]
+  int64_t sr_cur = -1;  // current (simulation group, super-row) = g Q + R
+  int it = 0;
+  bool aborted = false;
+  const int ct = threadIdx.x;  // consumer thread 0 .. 32 NCW - 1
+  __shared__ int split_last;
+
+  auto out = [&](int64_t b) -> float * {
+    return (b < A.B && (!A.active || A.active[b])) ? A.H + (size_t)b * 3 * A.n : nullptr;
+  };
+
+  // rows of super-row sr: warp totals, then written (or, for a super-row
+  // shared by CTAs, parked and added in CTA order by the last to arrive)
+  auto flush_rows = [&](int64_t sr) {
+#pragma unroll
+    for (int m = 0; m < SB; ++m)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int r = 0; r < S::RPW; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[m][k][r][c] = mtd::warp_sum(acc[m][k][r][c]);
+    const int64_t g = sr / A.Q, R = sr - g * A.Q;
+    const int64_t su0 = g * A.CH + (int64_t)K * half_gbase(R, A.Q);
+    const int64_t su1 = (R == A.Q - 1) ? (g + 1) * A.CH : g * A.CH + (int64_t)K * half_gbase(R + 1, A.Q);
+    const int64_t kf = mtd::sk_owner(su0, U, G), kl = mtd::sk_owner(su1 - 1, U, G);
+    // lane l holds values v = l and l + 32 (v = (k RPW + r) 3 + c)
+    float mine[SB][2];
+#pragma unroll
+    for (int m = 0; m < SB; ++m) {
+      mine[m][0] = mine[m][1] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int r = 0; r < S::RPW; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int v = (k * S::RPW + r) * 3 + c;
+            if (v == lane) mine[m][0] = acc[m][k][r][c];
+            if (v == lane + 32) mine[m][1] = acc[m][k][r][c];
+          }
+    }
+    auto row_of = [&](int v) {  // row within the super-row
+      const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
+      return k * TR + warp * S::RPW + r;
+    };
+    const int64_t row0 = R * K * TR;
+    if (kf == kl) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int v = lane + 32 * h;
+        if (v >= S::NV) continue;
+        const int64_t row = row0 + row_of(v);
+        if (row >= A.n) continue;
+#pragma unroll
+        for (int m = 0; m < SB; ++m)
+          if (float *H = out(g * SB + m)) H[3 * row + v % 3] = -mine[m][h];
+      }
+      return;
+    }
+    const int64_t slot = (u0 >= su0) ? 2 * kcta : 2 * kcta + 1;  // the super-row is this CTA's first or last
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int v = lane + 32 * h;
+      if (v >= S::NV) continue;
+#pragma unroll
+      for (int m = 0; m < SB; ++m) A.part[((slot * SB + m) * K * TR + row_of(v)) * 3 + v % 3] = mine[m][h];
+    }
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) last = (atomicAdd(&A.count[sr * S::NCW + warp], 1) == (int)(kl - kf));
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int v = lane + 32 * h;
+      if (v >= S::NV) continue;
+      const int64_t row = row0 + row_of(v);
+#pragma unroll
+      for (int m = 0; m < SB; ++m) {
+        float tot = 0.0f;
+        for (int64_t kk = kf; kk <= kl; ++kk) {
+          const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
+          tot += __ldcg(&A.part[((sl * SB + m) * K * TR + row_of(v)) * 3 + v % 3]);
+        }
+        float *H = out(g * SB + m);
+        if (H && row < A.n) H[3 * row + v % 3] = -tot;
+      }
+    }
+    if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
+  };
+
+  // the chunks kb .. ke - 1 of one group; STRICT: also its column sums
+  auto run_group = [&](auto strict_c, const GroupCursor &gc, int kb, int ke, float colp[SB][4][3]) {
+    constexpr bool STRICT = decltype(strict_c)::value;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (k < kb || k >= ke) continue;
+      const int s = it % S::STAGES;
+      const uint32_t ph = (uint32_t)(it / S::STAGES) & 1u;
+      ++it;
+      if (!aborted) {
+        if (*abort_flag || !mtd::mbar_wait_bounded(&full[s], ph, A.status)) {
+          aborted = true;
+          *abort_flag = 1;
+        }
+      }
+      if (!aborted) {
+        const unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
+        float X[SB][4], Y[SB][4], Z[SB][4];
+#pragma unroll
+        for (int m = 0; m < SB; ++m) {
+          const unsigned char *xsm = st + S::DATA_BYTES + m * S::XS_BYTES;
+          load_xs<PREC>(xsm, 0, lane, X[m]);
+          load_xs<PREC>(xsm, 1, lane, Y[m]);
+          load_xs<PREC>(xsm, 2, lane, Z[m]);
+        }
+#pragma unroll
+        for (int r = 0; r < S::RPW; ++r) {
+          const int row = warp * S::RPW + r;
+          float4 xr[SB];
+          if constexpr (STRICT) {
+#pragma unroll
+            for (int m = 0; m < SB; ++m) xr[m] = xi[m * K * S::RPW + k * S::RPW + r];
+          }
+          if constexpr (C::PLANAR) {
+            float nxx[4], nxy[4], nyy[4], nzz[4];
+            load_vals<PREC>(st, 0, row, lane, nxx);
+            load_vals<PREC>(st, 1, row, lane, nxy);
+            load_vals<PREC>(st, 2, row, lane, nyy);
+            load_vals<PREC>(st, 3, row, lane, nzz);
+#pragma unroll
+            for (int m = 0; m < SB; ++m) {
+              float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                sx = fmaf(nxx[v], X[m][v], fmaf(nxy[v], Y[m][v], sx));
+                sy = fmaf(nxy[v], X[m][v], fmaf(nyy[v], Y[m][v], sy));
+                sz = fmaf(nzz[v], Z[m][v], sz);
+                if constexpr (STRICT) {
+                  colp[m][v][0] = fmaf(nxx[v], xr[m].x, fmaf(nxy[v], xr[m].y, colp[m][v][0]));
+                  colp[m][v][1] = fmaf(nxy[v], xr[m].x, fmaf(nyy[v], xr[m].y, colp[m][v][1]));
+                  colp[m][v][2] = fmaf(nzz[v], xr[m].z, colp[m][v][2]);
+                }
+              }
+              acc[m][k][r][0] += sx;
+              acc[m][k][r][1] += sy;
+              acc[m][k][r][2] += sz;
+            }
+          } else {
+            float nxx[4], nxy[4], nxz[4], nyy[4], nyz[4], nzz[4];
+            load_vals<PREC>(st, 0, row, lane, nxx);
+            load_vals<PREC>(st, 1, row, lane, nxy);
+            load_vals<PREC>(st, 2, row, lane, nxz);
+            load_vals<PREC>(st, 3, row, lane, nyy);
+            load_vals<PREC>(st, 4, row, lane, nyz);
+            load_vals<PREC>(st, 5, row, lane, nzz);
+#pragma unroll
+            for (int m = 0; m < SB; ++m) {
+              float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                sx = fmaf(nxx[v], X[m][v], fmaf(nxy[v], Y[m][v], fmaf(nxz[v], Z[m][v], sx)));
+                sy = fmaf(nxy[v], X[m][v], fmaf(nyy[v], Y[m][v], fmaf(nyz[v], Z[m][v], sy)));
+                sz = fmaf(nxz[v], X[m][v], fmaf(nyz[v], Y[m][v], fmaf(nzz[v], Z[m][v], sz)));
+                if constexpr (STRICT) {
+                  colp[m][v][0] = fmaf(nxx[v], xr[m].x, fmaf(nxy[v], xr[m].y, fmaf(nxz[v], xr[m].z, colp[m][v][0])));
+                  colp[m][v][1] = fmaf(nxy[v], xr[m].x, fmaf(nyy[v], xr[m].y, fmaf(nyz[v], xr[m].z, colp[m][v][1])));
+                  colp[m][v][2] = fmaf(nxz[v], xr[m].x, fmaf(nyz[v], xr[m].y, fmaf(nzz[v], xr[m].z, colp[m][v][2])));
+                }
+              }
+              acc[m][k][r][0] += sx;
+              acc[m][k][r][1] += sy;
+              acc[m][k][r][2] += sz;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mtd::mbar_arrive(&empty[s]);
+    }
+  };
+
+  GroupCursor gc;
+  for (int64_t gs = group_decode<K>(A, u0, gc); gs < u1; gs += group_len<K>(A, gc), group_next(A, gc)) {
+    if (!half_live(A, gc.g, SB)) continue;
+    const int len = group_len<K>(A, gc);
+    const int kb = (int)(u0 > gs ? u0 - gs : 0), ke = (int)(u1 - gs < len ? u1 - gs : len);
+    const int64_t sr = gc.g * A.Q + gc.R;
+    if (sr != sr_cur) {
+      if (sr_cur >= 0) flush_rows(sr_cur);
+      sr_cur = sr;
+#pragma unroll
+      for (int m = 0; m < SB; ++m)
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+#pragma unroll
+          for (int r = 0; r < S::RPW; ++r) acc[m][k][r][0] = acc[m][k][r][1] = acc[m][k][r][2] = 0.0f;
+      // the operand of this warp's rows of the super-row (column chunk R of
+      // the operand): lane l < 16 SB takes simulation l / 16, row slot l % 16
+      __syncwarp();
+      if (lane < SB * K * S::RPW) {
+        const int m = lane / (K * S::RPW), kr = lane % (K * S::RPW);
+        const int k = kr / S::RPW, r = kr % S::RPW;
+        const int64_t b = gc.g * SB + m < A.B ? gc.g * SB + m : 0;
+        const float *x = A.xs + (size_t)(b * A.Q + gc.R) * 3 * TC + k * TR + warp * S::RPW + r;
+        xi[m * K * S::RPW + kr] = make_float4(__ldg(x), __ldg(x + TC), __ldg(x + 2 * TC), 0.0f);
+      }
+      __syncwarp();
+    }
+    if (gc.q == gc.R) {  // the diagonal group: rows only
+      run_group(std::false_type{}, gc, kb, ke, nullptr);
+      continue;
+    }
+    float colp[SB][4][3];
+#pragma unroll
+    for (int m = 0; m < SB; ++m)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) colp[m][v][0] = colp[m][v][1] = colp[m][v][2] = 0.0f;
+    run_group(std::true_type{}, gc, kb, ke, colp);
+    // column sums of the group: each warp's (its rows) to shared memory,
+    // then thread t adds column t % TC, components t / TC, t / TC + 2, ...,
+    // over the warps in order
+#pragma unroll
+    for (int m = 0; m < SB; ++m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        *reinterpret_cast<float4 *>(cb + ((warp * SB + m) * 3 + c) * TC + lane * 4) =
+            make_float4(colp[m][0][c], colp[m][1][c], colp[m][2][c], colp[m][3][c]);
+    asm volatile("bar.sync 1, %0;" ::"r"(S::NCW * 32) : "memory");
+    constexpr int NT = S::NCW * 32 / TC;  // thread sets over the columns
+    const int col = ct % TC;
+    const bool whole = (kb == 0 && ke == len);
+    const int64_t slot = (u0 >= gs) ? 2 * kcta : 2 * kcta + 1;  // a split group: this CTA's first or last
+#pragma unroll
+    for (int c0 = 0; c0 < 3; c0 += NT) {
+      const int c = c0 + ct / TC;
+      if (c >= 3) break;
+#pragma unroll
+      for (int m = 0; m < SB; ++m) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int w = 0; w < S::NCW; ++w) tot += cb[((w * SB + m) * 3 + c) * TC + col];
+        if (whole) A.colpart[(((gc.g * A.NGR + gc.gi) * SB + m) * 3 + c) * TC + col] = tot;
+        else A.colsplit[((slot * SB + m) * 3 + c) * TC + col] = tot;
+      }
+    }
+    if (!whole) __threadfence();
+    asm volatile("bar.sync 1, %0;" ::"r"(S::NCW * 32) : "memory");  // CB free; a split part is out
+    if (whole) continue;
+    // a group split between CTAs: the last to arrive adds the parts in CTA order
+    const int64_t kf = mtd::sk_owner(gs, U, G), kl = mtd::sk_owner(gs + len - 1, U, G);
+    int *gcount = &A.gcount[gc.g * A.NGR + gc.gi];
+    if (ct == 0) split_last = (atomicAdd(gcount, 1) == (int)(kl - kf));
+    asm volatile("bar.sync 1, %0;" ::"r"(S::NCW * 32) : "memory");
+    if (!split_last) continue;
+    __threadfence();
+#pragma unroll
+    for (int c0 = 0; c0 < 3; c0 += NT) {
+      const int c = c0 + ct / TC;
+      if (c >= 3) break;
+#pragma unroll
+      for (int m = 0; m < SB; ++m) {
+        float tot = 0.0f;
+        for (int64_t kk = kf; kk <= kl; ++kk) {
+          const int64_t sl = (mtd::sk_begin(kk, U, G) >= gs) ? 2 * kk : 2 * kk + 1;
+          tot += __ldcg(&A.colsplit[((sl * SB + m) * 3 + c) * TC + col]);
+        }
+        A.colpart[(((gc.g * A.NGR + gc.gi) * SB + m) * 3 + c) * TC + col] = tot;
+      }
+    }
+    if (ct == 0) *gcount = 0;  // ready for the next launch
+  }
+  if (sr_cur >= 0) flush_rows(sr_cur);
+}
+
+// The transposed part of a half-stored product.  Column j of column chunk q
+// gets sum over the groups (R, q), R < q, of their column sums.  CTA
+// (q, s, b) adds the groups of slice s of R (NS slices, R increasing) and
+// parks the sum; the last CTA of (q, b) to arrive adds the NS slice sums in
 // slice order (a fixed order: the result does not depend on timing) and
 // does H_j -= total.  One thread per column of the chunk.
-__global__ void __launch_bounds__(128) k_half_cols(MvArgs A, int SB, int TC, int K, int NS, float *slice_sum) {
+__global__ void __launch_bounds__(128) k_half_cols(HalfArgs A, int SB, int TC, int NS, float *slice_sum) {
   mtd::pdl_enter();
   const int64_t q = blockIdx.x;
   const int sl = blockIdx.y, b = blockIdx.z;
   const int t = threadIdx.x;
-  const int64_t np = K * q;  // panels above the diagonal of chunk q
-  const int64_t len = (np + NS - 1) / NS;
-  const int64_t pa = sl * len, pb = np < pa + len ? np : pa + len;
+  const int64_t len = (q + NS - 1) / NS;
+  const int64_t Ra = sl * len, Rb = q < Ra + len ? q : Ra + len;
   const int64_t g = b / SB, m = b - g * SB;
   float tot[3] = {0.0f, 0.0f, 0.0f};
-  // walk the panels with the chunk (p, q)'s unit index kept up to date:
-  // panel p holds chunks q0(p) .. Q-1, q0 growing by one every K panels
-  int64_t q0 = pa / K, cum = g * A.CH + half_cum(pa, A.Q, K);
-  int kk = (int)(pa - q0 * K);
-  const float *base = A.colpart + m * 3 * TC + t;
-  const int64_t ustride = (int64_t)SB * 3 * TC;
-  auto next = [&] {
-    cum += A.Q - q0;
-    if (++kk == K) {
-      kk = 0;
-      ++q0;
-    }
-  };
-  int64_t p = pa;
-  for (; p + 4 <= pb; p += 4) {  // four panels' loads in flight
+  // group (R, q) is number half_gbase(R) + q - R; the next R's is Q - R - 1 on
+  const float *base = A.colpart + ((g * A.NGR * SB + m) * 3) * TC + t;
+  const int64_t gstride = (int64_t)SB * 3 * TC;
+  int64_t gi = half_gbase(Ra, A.Q) + q - Ra;
+  int64_t R = Ra;
+  for (; R + 4 <= Rb; R += 4) {  // four groups' loads in flight
     float v[4][3];
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) {
-      const float *cp = base + (cum + (q - q0)) * ustride;
+      const float *cp = base + gi * gstride;
       v[k2][0] = __ldcg(cp);
       v[k2][1] = __ldcg(cp + TC);
       v[k2][2] = __ldcg(cp + 2 * TC);
-      next();
+      gi += A.Q - (R + k2) - 1;
     }
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) {
@@ -646,12 +972,12 @@ __global__ void __launch_bounds__(128) k_half_cols(MvArgs A, int SB, int TC, int
       tot[2] += v[k2][2];
     }
   }
-  for (; p < pb; ++p) {
-    const float *cp = base + (cum + (q - q0)) * ustride;
+  for (; R < Rb; ++R) {
+    const float *cp = base + gi * gstride;
     tot[0] += __ldcg(cp);
     tot[1] += __ldcg(cp + TC);
     tot[2] += __ldcg(cp + 2 * TC);
-    next();
+    gi += A.Q - R - 1;
   }
   const int64_t qb = (int64_t)b * A.Q + q;
   float *mine = slice_sum + ((qb * NS + sl) * 3) * TC + t;
@@ -674,7 +1000,7 @@ __global__ void __launch_bounds__(128) k_half_cols(MvArgs A, int SB, int TC, int
     v[1] += __ldcg(ss + TC);
     v[2] += __ldcg(ss + 2 * TC);
   }
-  float *H = reinterpret_cast<float *>(A.H) + (size_t)b * 3 * A.n + 3 * j;
+  float *H = A.H + (size_t)b * 3 * A.n + 3 * j;
   H[0] -= v[0];
   H[1] -= v[1];
   H[2] -= v[2];
@@ -860,12 +1186,12 @@ constexpr bool has_half() {
 
 template <int PREC, int SB>
 cudaError_t prepare_mv_one() {
-  cudaError_t e = cudaFuncSetAttribute(k_matvec<PREC, SB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       MvShape<PREC, SB, false>::SMEM_BYTES);
-  if constexpr (has_half<PREC>()) {
+  cudaError_t e = cudaFuncSetAttribute(k_matvec<PREC, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       MvShape<PREC, SB>::SMEM_BYTES);
+  if constexpr (has_half<PREC>() && SB <= 2) {
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_matvec<PREC, SB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               MvShape<PREC, SB, true>::SMEM_BYTES);
+      e = cudaFuncSetAttribute(k_matvec_half<PREC, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               HalfShape<PREC, SB>::SMEM_BYTES);
   }
   return e;
 }
@@ -880,45 +1206,91 @@ cudaError_t prepare_mv() {
 
 // simulations per chunk read: 1, 2 or 4 (2 at most for the scaled BF16
 // tensor, whose 8-wide rows with 4 operands spill registers: measured 0.56 ms
-// for 4 simulations at n = 10,000 against 0.21 ms for one)
-inline int mv_group(int B, int prec) {
-  const int cap = (prec == MT_BF16_SCALED || prec == kBF16Planar) ? 2 : 4;
+// for 4 simulations at n = 10,000 against 0.21 ms for one; 2 at most for a
+// half-stored tensor, whose threads hold the sums of 16 rows per simulation)
+inline int mv_group(int B, int prec, bool half) {
+  const int cap = (half || prec == MT_BF16_SCALED || prec == kBF16Planar) ? 2 : 4;
   return B <= 1 ? 1 : (B == 2 || cap == 2) ? 2 : 4;
 }
 
+// slices of a column chunk's range of super-rows in k_half_cols (about 8
+// groups each)
+inline int half_col_slices(int64_t Q) { return (int)std::max<int64_t>(1, std::min<int64_t>(16, (Q + 7) / 8)); }
+
 template <int PREC, int SB>
-void launch_mv_sb(const MvArgs &A, bool half, int grid_cap, cudaStream_t s) {
+void launch_mv_sb(const MvArgs &A, int grid_cap, cudaStream_t s) {
   // never more CTAs than units: every CTA then owns at least one unit, which
   // the panel bookkeeping (owners of a panel's first and last unit bound its
   // contributors) relies on
   const int64_t U = (int64_t)((A.B + SB - 1) / SB) * A.CH;
   const int grid = (int)std::min<int64_t>(grid_cap, U);
-  if constexpr (has_half<PREC>()) {
-    if (half) {
-      using S = MvShape<PREC, SB, true>;
-      static_assert(MvCfg<PREC>::TC % MvCfg<PREC>::TR == 0, "panels tile a chunk row");
-      // the work area: chunk sums, then the slice sums and arrival counters
-      // of the column pass
-      constexpr int TC = MvCfg<PREC>::TC;
-      const int ns = half_col_slices(A.P);
-      const int64_t ng = (A.B + SB - 1) / SB;
-      float *slice_sum = A.colpart + (size_t)ng * SB * A.CH * 3 * TC;
-      MvArgs A2 = A;
-      A2.arrive = reinterpret_cast<int *>(slice_sum + (size_t)A.B * A.Q * ns * 3 * TC);
-      mt::launch_pdl(k_matvec<PREC, SB, true>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A2);
-      // the transposed part, summed per column
-      mt::launch_pdl(k_half_cols, dim3((unsigned)A.Q, (unsigned)ns, (unsigned)A.B), dim3(TC), 0, s, A2, SB, TC,
-                     TC / MvCfg<PREC>::TR, ns, slice_sum);
-      return;
-    }
-  }
-  using S = MvShape<PREC, SB, false>;
-  mt::launch_pdl(k_matvec<PREC, SB, false>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
+  using S = MvShape<PREC, SB>;
+  mt::launch_pdl(k_matvec<PREC, SB>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
+}
+
+// work area of a half-stored product over B simulations, SB per chunk read
+// (floats unless noted): the column sums of every group [NG][NGR][SB][3][TC];
+// the parts of groups split between CTAs [2 grid_cap][SB][3][TC]; the slice
+// sums of k_half_cols [B][Q][NS][3][TC]; its arrival counters [B][Q] (int)
+struct HalfArea {
+  size_t colpart, colsplit, slice, arrive, bytes;
+};
+inline HalfArea half_area(int64_t Q, int64_t B, int SB, int grid_cap, int TC) {
+  const int64_t NG = (B + SB - 1) / SB, NGR = half_groups(Q);
+  HalfArea h;
+  h.colpart = 0;
+  h.colsplit = h.colpart + (size_t)NG * NGR * SB * 3 * TC;
+  h.slice = h.colsplit + (size_t)2 * grid_cap * SB * 3 * TC;
+  h.arrive = h.slice + (size_t)B * Q * half_col_slices(Q) * 3 * TC;
+  h.bytes = h.arrive * sizeof(float) + (size_t)B * Q * sizeof(int);
+  return h;
+}
+
+template <int PREC, int SB>
+void launch_half(const mt_tensor *T, const float *xs, int B, float *H, float *part, int *count, const int *active,
+                 int *status, float *work, cudaStream_t s) {
+  using S = HalfShape<PREC, SB>;
+  constexpr int TC = MvCfg<PREC>::TC;
+  const int cap = mt::matvec_grid(T);
+  const HalfArea h = half_area(T->L.Q, B, SB, cap, TC);
+  HalfArgs A;
+  A.tensor = reinterpret_cast<const float *>(T->d_data);
+  A.xs = xs;
+  A.H = H;
+  A.part = part;
+  A.count = count;
+  A.gcount = count + (size_t)B * T->L.P * 8;  // after the row counters (all counters rest at zero)
+  A.colpart = work + h.colpart;
+  A.colsplit = work + h.colsplit;
+  A.arrive = reinterpret_cast<int *>(work + h.arrive);
+  A.active = active;
+  A.status = status;
+  A.n = T->n;
+  A.P = T->L.P;
+  A.Q = T->L.Q;
+  A.CH = T->L.CH;
+  A.NGR = half_groups(T->L.Q);
+  A.B = B;
+  const int64_t U = (int64_t)((B + SB - 1) / SB) * A.CH;
+  const int grid = (int)std::min<int64_t>(cap, U);
+  mt::launch_pdl(k_matvec_half<PREC, SB>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
+  const int ns = half_col_slices(A.Q);
+  mt::launch_pdl(k_half_cols, dim3((unsigned)A.Q, (unsigned)ns, (unsigned)B), dim3(TC), 0, s, A, SB, TC, ns,
+                 work + h.slice);
 }
 
 template <int PREC>
 void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, int *count, const int *active,
                int *status, float *colpart, cudaStream_t s) {
+  if constexpr (has_half<PREC>()) {
+    if (T->L.half) {
+      if (mv_group(B, PREC, true) == 1)
+        launch_half<PREC, 1>(T, (const float *)xs, B, (float *)H, (float *)part, count, active, status, colpart, s);
+      else
+        launch_half<PREC, 2>(T, (const float *)xs, B, (float *)H, (float *)part, count, active, status, colpart, s);
+      return;
+    }
+  }
   MvArgs A;
   A.tensor = T->d_data;
   A.scale = T->d_scale;
@@ -932,16 +1304,13 @@ void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, i
   A.P = T->L.P;
   A.Q = T->L.Q;
   A.CH = T->L.CH;
-  A.colpart = colpart;
-  A.arrive = nullptr;
   A.B = B;
   const int cap = mt::matvec_grid(T);
-  const bool half = T->L.half;
-  switch (mv_group(B, PREC)) {
-    case 1: launch_mv_sb<PREC, 1>(A, half, cap, s); break;
-    case 2: launch_mv_sb<PREC, 2>(A, half, cap, s); break;
+  switch (mv_group(B, PREC, false)) {
+    case 1: launch_mv_sb<PREC, 1>(A, cap, s); break;
+    case 2: launch_mv_sb<PREC, 2>(A, cap, s); break;
     default:
-      if constexpr (PREC != MT_BF16_SCALED && PREC != kBF16Planar) launch_mv_sb<PREC, 4>(A, half, cap, s);
+      if constexpr (PREC != MT_BF16_SCALED && PREC != kBF16Planar) launch_mv_sb<PREC, 4>(A, cap, s);
       break;
   }
 }
@@ -1005,22 +1374,24 @@ int64_t xs_floats(const mt_tensor *T) {
 
 size_t matvec_part_bytes(const mt_tensor *T) {
   const size_t el = T->prec == MT_F64 ? 8 : 4;
+  if (T->L.half)  // super-rows of K panels, up to 2 simulations per chunk read
+    return (size_t)2 * matvec_grid(T) * 2 * (T->L.TC / T->L.TR) * T->L.TR * 3 * el;
   return (size_t)2 * matvec_grid(T) * 4 /*simulations per chunk read, at most*/ * T->L.TR * 3 * el;
 }
 
-size_t matvec_count_bytes(const mt_tensor *T, int B) { return (size_t)B * T->L.P * 8 /*W<=8*/ * sizeof(int); }
+// per (simulation, panel) up to 8 warp counters; a half-stored tensor adds
+// one counter per (simulation, group)
+size_t matvec_count_bytes(const mt_tensor *T, int B) {
+  const size_t rows = (size_t)B * T->L.P * 8;
+  return (rows + (T->L.half ? (size_t)B * half_groups(T->L.Q) : 0)) * sizeof(int);
+}
 
-// half storage: the column sums of every stored chunk for B simulations
-// (groups of up to 4 share a chunk read; a partial group keeps its slots),
-// then the slice sums of k_half_cols and its arrival counters (a call with
-// fewer simulations uses a prefix of each part)
+// half storage: the work area of the product over B simulations (a call
+// with fewer simulations uses less of each part)
 size_t matvec_colpart_bytes(const mt_tensor *T, int B) {
   if (!T->L.half) return 0;
-  const int sb = mv_group(B, T->L.nplane == 4 ? kF32Planar : MT_F32);
-  const int64_t ng = (B + sb - 1) / sb;
-  const int ns = half_col_slices(T->L.P);
-  return (size_t)ng * sb * T->L.CH * 3 * T->L.TC * sizeof(float) +
-         (size_t)B * T->L.Q * ns * 3 * T->L.TC * sizeof(float) + (size_t)B * T->L.Q * sizeof(int);
+  const int sb = mv_group(B, MT_F32, true);
+  return half_area(T->L.Q, B, sb, matvec_grid(T), T->L.TC).bytes;
 }
 
 void launch_prep_xs(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {

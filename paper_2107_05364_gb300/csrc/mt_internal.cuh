@@ -143,8 +143,8 @@ struct mt_layout {
   int nplane = 6;           // 6 unique entries (12 for split hi/lo)
   int elem_bytes = 4;
   int64_t P = 0, Q = 0;     // panels, chunks per panel
-  bool half = false;        // only the upper triangle of chunks (see half_cum)
-  int64_t CH = 0;           // stored chunks (P * Q, or half_cum(P) when half)
+  bool half = false;        // only the upper triangle of chunks (see half_gbase)
+  int64_t CH = 0;           // stored chunks (P * Q, or half_chunks(P, Q) when half)
   int64_t chunk_elems() const { return (int64_t)nplane * TR * TC; }
   int64_t chunk_bytes() const { return chunk_elems() * elem_bytes; }
   int64_t scale_bytes_per_chunk = 0;  // BF16 scaled: TR x TC int8 exponents
@@ -152,24 +152,30 @@ struct mt_layout {
 
 // Half storage (Sec. 3.2: the tensor is symmetric).  For tiles of one shape
 // the point tensor is even in the offset of the two centres, so N_ij = N_ji
-// (and every block is symmetric): panel p (rows p TR ...) keeps only its
-// column chunks q >= q0(p) = p / K, K = TC / TR, the chunk holding its own
-// rows.  That diagonal chunk is used as stored (for its rows only); every
-// higher chunk serves its rows and, transposed, its columns.  Stored chunks
-// are consecutive in (p, q) order: chunk (p, q) is number
-// half_cum(p) + q - q0(p), half_cum(p) counting the chunks of panels < p.
+// (and every block is symmetric).  With K = TC / TR panels per chunk row,
+// super-row R (panels K R .. K R + K - 1: the rows of column chunk R; there
+// are Q super-rows, as K TR = TC) keeps its chunks of column chunks q >= R.
+// The diagonal group (q = R) is used as stored, for its rows; every higher
+// chunk serves its rows and, transposed, its columns.  Stored order: super-row
+// by super-row, in each the column chunks in turn, and for each column chunk
+// its K panels one after the other (a "group" of K chunks): chunk (p, q) with
+// R = p / K is number K (half_gbase(R) + q - R) + p - K R, half_gbase(R)
+// counting the groups of the super-rows above R.  (A group's K chunks come
+// one after the other, so the product keeps a column's sums over K panels.)
 __host__ __device__ __forceinline__ int64_t half_q0(int64_t p, int K) { return p / K; }
-__host__ __device__ __forceinline__ int64_t half_cum(int64_t p, int64_t Q, int K) {
-  const int64_t R = p / K;  // chunk row of p: every panel of chunk row r keeps Q - r chunks
-  return p * Q - ((int64_t)K * R * (R - 1) / 2 + R * (p - (int64_t)K * R));
+__host__ __device__ __forceinline__ int64_t half_gbase(int64_t R, int64_t Q) { return R * Q - R * (R - 1) / 2; }
+// groups and stored chunks of a half-stored P x Q chunk grid
+__host__ __device__ __forceinline__ int64_t half_groups(int64_t Q) { return half_gbase(Q, Q); }
+__host__ __device__ __forceinline__ int64_t half_chunks(int64_t P, int64_t Q, int K) {
+  return (int64_t)K * half_gbase(Q - 1, Q) + (P - (int64_t)K * (Q - 1));  // the last super-row: one group
 }
 // stored chunk of (panel p, column chunk q), -1 if the half storage omits it
 __host__ __device__ __forceinline__ int64_t stream_chunk(int64_t p, int64_t q, int64_t Q, int TR, int TC,
                                                          bool half) {
   if (!half) return p * Q + q;
   const int K = TC / TR;
-  const int64_t q0 = half_q0(p, K);
-  return q < q0 ? -1 : half_cum(p, Q, K) + (q - q0);
+  const int64_t R = p / K;
+  return q < R ? -1 : (int64_t)K * (half_gbase(R, Q) + q - R) + (p - (int64_t)K * R);
 }
 
 struct mt_tensor {

@@ -46,12 +46,13 @@ MU0 = 4e-7 * math.pi
 # 1,618,193,152 + 2,841,856 (1.0131 x 1.6e9).  Valid while k_matvec<f32> is
 # unchanged.
 MATVEC_F32_N10000_TRAFFIC = {6: 2427094016 + 2980864, 4: 1618193152 + 2841856}  # tensors storing every block
-# The same film with the tensor stored half (upper triangle of chunks), one
-# ncu capture of each kernel of a product: k_matvec<f32, 4 planes, half> read
-# 828,331,520 and wrote 6,757,632 bytes, k_half_cols read 38,003,712 (the
-# column sums of the stored chunks) -- 1.091 x the 0.80 GB algorithmic bytes.
-# Valid while both kernels are unchanged.
-MATVEC_F32_HALF_N10000_TRAFFIC = {4: 828331520 + 6757632 + 38003712}
+# The same film with the tensor stored half (upper triangle of chunks, in
+# super-row order), one ncu capture of each kernel of a product:
+# k_matvec_half<f32, 4 planes> read 828,401,408 and wrote 4,751,104 bytes,
+# k_half_cols read 4,875,264 (the column sums of the groups above the
+# diagonal) -- 1.047 x the 0.80 GB algorithmic bytes.  Valid while both
+# kernels are unchanged.
+MATVEC_F32_HALF_N10000_TRAFFIC = {4: 828401408 + 4751104 + 4875264}
 
 
 def f32_alg_bytes(info, n):
@@ -362,8 +363,9 @@ def run_ours(args):
                      "frac": achieved / peak,
                      "traffic": None if n != 10000 else (MATVEC_F32_HALF_N10000_TRAFFIC if info["half"]
                                                          else MATVEC_F32_N10000_TRAFFIC).get(planes),
-                     "kernel": ("k_matvec<f32" + (", 4 planes" if planes == 4 else "") +
-                                (", half> + k_half_cols" if info["half"] else ">")),
+                     "kernel": (("k_matvec_half<f32" if info["half"] else "k_matvec<f32") +
+                                (", 4 planes" if planes == 4 else "") +
+                                ("> + k_half_cols" if info["half"] else ">")),
                      "stored": "upper triangle of blocks (N_ij = N_ji: tiles of one shape)" if info["half"]
                      else "every block",
                      "peak_kind": kind, "algorithmic_bytes_per_launch": alg_bytes,
@@ -1177,7 +1179,7 @@ def run_cube(args):
             "assemble_s": t_asm,
             "roofline": {"bound": "hbm", "achieved": alg / (launch * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / (launch * 1e-3) / 1e9 / peak, "traffic": None,
-                         "kernel": "k_matvec<f32, half> + k_half_cols" if info["half"] else "k_matvec<f32>",
+                         "kernel": "k_matvec_half<f32> + k_half_cols" if info["half"] else "k_matvec<f32>",
                          "stored": "upper triangle of blocks (N_ij = N_ji: tiles of one shape)" if info["half"]
                          else "every block",
                          "algorithmic_bytes_per_launch": alg, "launch_ms": launch,

@@ -548,11 +548,14 @@ typedef struct {
   size_t hbm_budget_bytes;  /* tensors + batch state (0: the context budget) */
   int32_t max_batch;        /* slots per resident geometry, 1..128          */
   int32_t prec;             /* mt_prec of cached tensors (not MT_F64)       */
-  int32_t layout;           /* mt_layout_kind of cached tensors; with       */
-                            /* MT_LAYOUT_STREAM and max_batch >= 3 every    */
-                            /* block is stored (MT_LAYOUT_STREAM_FULL): the */
-                            /* half storage's product is faster for one or  */
-                            /* two simulations per pass only                */
+  int32_t layout;           /* mt_layout_kind of cached tensors (not        */
+                            /* MT_LAYOUT_SPARSE; MT_LAYOUT_STREAM_HALF      */
+                            /* fails the jobs of geometries whose tiles     */
+                            /* differ in shape); with MT_LAYOUT_STREAM and  */
+                            /* max_batch >= 3 every block is stored         */
+                            /* (MT_LAYOUT_STREAM_FULL): the half storage's  */
+                            /* product is faster for one or two simulations */
+                            /* per pass only                                */
   int32_t form;             /* mt_form of every job                         */
   double gamma;             /* m/(A s)                                      */
   mt_ode_opts ode;          /* integrator options; max_steps caps each job  */

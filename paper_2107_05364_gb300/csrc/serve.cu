@@ -421,7 +421,10 @@ mt_status mt_server_create(mt_ctx *ctx, const mt_server_opts *opts, mt_server **
   MT_CHECK(opts->max_batch >= 1 && opts->max_batch <= 128, MT_EINVAL, "mt_server_create: max_batch in 1..128");
   MT_CHECK(opts->prec >= MT_F32 && opts->prec <= MT_BF16_SPLIT, MT_EINVAL,
            "mt_server_create: precision must be FP32, BF16 or split BF16");
-  MT_CHECK(opts->layout == MT_LAYOUT_STREAM || opts->prec != MT_F32, MT_EINVAL,
+  MT_CHECK(opts->layout == MT_LAYOUT_STREAM || opts->layout == MT_LAYOUT_DENSE || opts->layout == MT_LAYOUT_STREAM6 ||
+               opts->layout == MT_LAYOUT_STREAM_FULL || opts->layout == MT_LAYOUT_STREAM_HALF,
+           MT_EINVAL, "mt_server_create: bad layout %d", (int)opts->layout);
+  MT_CHECK(opts->layout != MT_LAYOUT_DENSE || opts->prec != MT_F32, MT_EINVAL,
            "mt_server_create: the dense layout stores BF16 or split BF16");
   MT_CHECK(opts->max_running >= 0, MT_EINVAL, "mt_server_create: max_running must be >= 0");
   mt_server *S = new mt_server();

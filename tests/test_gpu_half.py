@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
+from _observe import observe
 from paper_2107_05364_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -126,6 +127,35 @@ def test_half_integrator_steps_match_oracle(mt, case):
     assert so == oracle.OK
     assert np.abs(out["half"] - mo).max() <= 3e-6
     assert np.abs(out["half"] - out["full"]).max() <= 3e-6
+
+
+def test_half_relax_of_two_simulations_with_active_masks(mt, case):
+    # two simulations relaxed together at different damping: the faster one
+    # stops first and leaves the slot inactive while the other runs on (the
+    # product then skips the finished simulation's field).  Relaxed to a
+    # torque of 1e-5 (rtol = atol = 1e-7 keeps the integrator's torque floor
+    # below that), the states of the half and the full storage -- the same
+    # sums in another rounding order, so other stopping points -- agree to
+    # 1e-4 (at a torque of 1e-4 they differed by 1.1e-4)
+    name, t, tiles, Th, Tf, md = case
+    m0 = np.stack([wl.m_noisy(t.n, (1, 0.2, 0), 0.2, seed=11), wl.m_noisy(t.n, (0, 1, 0.1), 0.2, seed=12)])
+    # fields of 0.1 and 0.075 T: relaxation times (1 + a^2) / (a gamma H) of
+    # 0.1 and 0.4 ns, so both reach the torque well inside the 10 ns cap
+    p, keep = mt.llg_params(2, alpha=np.array([0.8, 0.3]), Ha=np.array([[8e4, 0, 0], [0, -6e4, 0]]))
+    out = {}
+    for key, T in (("half", Th), ("full", Tf)):
+        I = mt.Integrator(T, p, mt.ode_opts(rtol=1e-7, atol=1e-7), B=2)
+        I.set_state(m0.astype(np.float32).ravel())
+        st, stats = I.relax(1e-5, 1e-8, check=False)
+        assert st == mt.MT_OK, (key, stats)
+        out[key] = (I.get_state().reshape(2, t.n, 3).copy(), [x["t"] for x in stats], [x["tau"] for x in stats])
+        I.close()
+    (mh, th, tauh), (mf, tf, tauf) = out["half"], out["full"]
+    assert max(tauh) < 1e-5 and max(tauf) < 1e-5
+    assert th[0] != th[1]  # the two simulations stopped at different times
+    observe("half_vs_full_relaxed_two_sims_" + name, float(np.abs(mh - mf).max()), 1e-4)
+    assert np.abs(mh - mf).max() <= 1e-4
+    np.testing.assert_allclose(np.linalg.norm(mh, axis=2), 1.0, atol=1e-5)
 
 
 def test_half_storage_limits(mt, ctx, case):

@@ -146,3 +146,25 @@ def test_one_job_at_a_time_in_arrival_order(mt, ctx):
     assert all(r["status"] == 0 for r in res)
     for a, b in zip(res, res[1:]):
         assert b["t_start"] >= a["t_done"], (a, b)  # no overlap, in submission order
+
+
+def test_half_storage_engines(mt, ctx):
+    # engines on half-stored tensors (MT_LAYOUT_STREAM_HALF: tiles of one
+    # shape, the upper triangle of chunks) relax the same states as engines
+    # that store every block; a geometry whose tiles differ in shape fails
+    # its jobs on half-storage engines with MT_EINVAL
+    geoms = [wl.film(70, 40, 1, size=(350e-9, 200e-9, 3e-9)), wl.film(30, 6, 1, size=(150e-9, 30e-9, 3e-9))]
+    jobs = _jobs(geoms, 4, seed=21)
+    half, st = _run(mt, ctx, geoms, jobs, max_batch=2, rtol=1e-6, layout=mt.MT_LAYOUT_STREAM_HALF)
+    full, _ = _run(mt, ctx, geoms, jobs, max_batch=2, rtol=1e-6, layout=mt.MT_LAYOUT_STREAM_FULL)
+    assert st["failed"] == 0
+    for (s1, r1, m1), (s2, r2, m2) in zip(half, full):
+        assert s1 == 0 and s2 == 0 and r1["status"] == 0 and r2["status"] == 0
+        assert np.abs(m1 - m2).max() <= 1e-4
+    graded = wl.graded_film(20, 10, 1, (100e-9, 50e-9, 3e-9), seed=4)
+    S = mt.Server(ctx, max_batch=2, layout=mt.MT_LAYOUT_STREAM_HALF, opts=mt.ode_opts(rtol=1e-5, atol=1e-5))
+    g = S.add_geometry(graded)
+    j = S.submit(g, wl.m_noisy(graded.n), tol=1e-4, t_max=1e-9)
+    s, r, _ = S.wait(j, 60.0)
+    S.close()
+    assert s == 0 and r["status"] == mt.MT_EINVAL

@@ -219,10 +219,20 @@ __device__ __forceinline__ bool group_live(const MvArgs &A, int64_t g, int SB) {
 
 template <int PREC, int SB>
 __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs A) {
-  mtd::pdl_enter();
   using C = MvCfg<PREC>;
   using S = MvShape<PREC, SB>;
   using Acc = typename C::Acc;
+  {
+    // before waiting on the previous kernel (which writes the operand, not
+    // the tensor): the CTA's first ring-full of tensor chunks into L2
+    const int64_t G = gridDim.x, NG = (A.B + SB - 1) / SB, U = NG * A.CH;
+    const int64_t u0 = mtd::sk_begin(blockIdx.x, U, G), u1 = mtd::sk_begin(blockIdx.x + 1, U, G);
+    const int64_t c0 = u0 % A.CH;
+    if (threadIdx.x < S::STAGES && u0 + threadIdx.x < u1 && c0 + threadIdx.x < A.CH)
+      mtd::bulk_prefetch_l2(reinterpret_cast<const unsigned char *>(A.tensor) + (size_t)(c0 + threadIdx.x) * S::DATA_BYTES,
+                            S::DATA_BYTES);
+  }
+  mtd::pdl_enter();
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + S::STAGES * S::STAGE_BYTES);
   uint64_t *empty = full + S::STAGES;
@@ -576,10 +586,20 @@ __device__ __forceinline__ int group_len(const HalfArgs &A, const GroupCursor &g
 
 template <int PREC, int SB>
 __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half(HalfArgs A) {
-  mtd::pdl_enter();
   using C = MvCfg<PREC>;
   using S = HalfShape<PREC, SB>;
   constexpr int K = S::K, TR = C::TR, TC = C::TC;
+  {
+    // before waiting on the previous kernel (which writes the operand, not
+    // the tensor): the CTA's first ring-full of tensor chunks into L2
+    const int64_t G = gridDim.x, NG = (A.B + SB - 1) / SB, U = NG * A.CH;
+    const int64_t u0 = mtd::sk_begin(blockIdx.x, U, G), u1 = mtd::sk_begin(blockIdx.x + 1, U, G);
+    const int64_t c0 = u0 % A.CH;
+    if (threadIdx.x < S::STAGES && u0 + threadIdx.x < u1 && c0 + threadIdx.x < A.CH)
+      mtd::bulk_prefetch_l2(reinterpret_cast<const unsigned char *>(A.tensor) + (size_t)(c0 + threadIdx.x) * S::DATA_BYTES,
+                            S::DATA_BYTES);
+  }
+  mtd::pdl_enter();
   // the column pass that follows counts its arrivals from zero
   for (int64_t i = blockIdx.x * (int64_t)S::THREADS + threadIdx.x; i < (int64_t)A.B * A.Q;
        i += (int64_t)gridDim.x * S::THREADS)

@@ -497,6 +497,9 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
 // groups (R, q), R < q, in order of R and subtracts them from H.  Up to 2
 // simulations share a chunk read (more take several passes: their row
 // sums would not fit the registers).
+// chunks a half-product CTA prefetches into L2 before the PDL wait
+constexpr int kHalfPrefetch = 18;
+
 template <int PREC, int SB>
 struct HalfShape {
   using C = MvCfg<PREC>;
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
     const int64_t G = gridDim.x, NG = (A.B + SB - 1) / SB, U = NG * A.CH;
     const int64_t u0 = mtd::sk_begin(blockIdx.x, U, G), u1 = mtd::sk_begin(blockIdx.x + 1, U, G);
     const int64_t c0 = u0 % A.CH;
-    if (threadIdx.x < S::STAGES && u0 + threadIdx.x < u1 && c0 + threadIdx.x < A.CH)
+    if (threadIdx.x < kHalfPrefetch && u0 + threadIdx.x < u1 && c0 + threadIdx.x < A.CH)
       mtd::bulk_prefetch_l2(reinterpret_cast<const unsigned char *>(A.tensor) + (size_t)(c0 + threadIdx.x) * S::DATA_BYTES,
                             S::DATA_BYTES);
   }

@@ -40,19 +40,18 @@ from paper_2107_05364_gb300 import workloads as wl  # noqa: E402
 MU0 = 4e-7 * math.pi
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the streaming FP32 product at the film workload below (n = 10,000), from one
-# ncu capture of a full launch, by stored entry planes: 6 planes 2,427,094,016
-# read + 2,980,864 written (1.0125 x the 2.4e9 algorithmic bytes: the zero
-# padding of the last chunk row); 4 planes (the single-layer film)
-# 1,618,193,152 + 2,841,856 (1.0131 x 1.6e9).  Valid while k_matvec<f32> is
-# unchanged.
-MATVEC_F32_N10000_TRAFFIC = {6: 2427094016 + 2980864, 4: 1618193152 + 2841856}  # tensors storing every block
+# ncu capture of a full launch of the current kernels.  Every block stored, 4
+# planes (the single-layer film): 1,618,117,632 read + 2,918,912 written
+# (1.0132 x the 1.6e9 algorithmic bytes: the zero padding of the last chunk
+# row).  Valid while k_matvec<f32> is unchanged.
+MATVEC_F32_N10000_TRAFFIC = {4: 1618117632 + 2918912}  # tensors storing every block
 # The same film with the tensor stored half (upper triangle of chunks, in
 # super-row order), one ncu capture of each kernel of a product:
-# k_matvec_half<f32, 4 planes> read 828,401,408 and wrote 4,751,104 bytes,
-# k_half_cols read 4,875,264 (the column sums of the groups above the
+# k_matvec_half<f32, 4 planes> read 828,403,456 and wrote 4,449,792 bytes,
+# k_half_cols read 4,875,520 (the column sums of the groups above the
 # diagonal) -- 1.047 x the 0.80 GB algorithmic bytes.  Valid while both
 # kernels are unchanged.
-MATVEC_F32_HALF_N10000_TRAFFIC = {4: 828401408 + 4751104 + 4875264}
+MATVEC_F32_HALF_N10000_TRAFFIC = {4: 828403456 + 4449792 + 4875520}
 
 
 def f32_alg_bytes(info, n):

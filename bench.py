@@ -1306,6 +1306,8 @@ def run_profile(args):
         return
     layout = {"stream": mt.MT_LAYOUT_STREAM, "full": mt.MT_LAYOUT_STREAM_FULL, "dense": mt.MT_LAYOUT_DENSE,
               "stream6": mt.MT_LAYOUT_STREAM6}[args.layout]
+    if args.threshold is not None and layout == mt.MT_LAYOUT_STREAM:
+        layout = mt.MT_LAYOUT_STREAM_FULL  # thresholding needs every block stored
     T = mt.mt_demag_assemble_ex(tiles, prec, layout)
     if args.threshold is not None:
         S, thr, kept = mt.mt_tensor_threshold(T, args.threshold)

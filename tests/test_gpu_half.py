@@ -182,3 +182,51 @@ def test_half_storage_limits(mt, ctx, case):
     big = mt.mt_tiles_create(ctx, wl.film(80, 52, 1, size=(400e-9, 260e-9, 3e-9)))  # n = 4,160
     assert mt.mt_demag_assemble(big, "f32").info()["half"] == 1
     assert mt.mt_demag_assemble_ex(big, "f32", mt.MT_LAYOUT_STREAM_FULL).info()["half"] == 0
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (17, 1), (16, 8), (43, 3), (30, 10)])
+def test_half_edge_shapes_match_oracle(mt, ctx, nx, ny):
+    # forced half storage on tile counts at the layout's edges: one tile,
+    # one ragged chunk (17), exactly one super-row (128), one tile into the
+    # second super-row (129) and a ragged 300; fields at the FP32 tolerance
+    import torch
+    t = wl.film(nx, ny, 1, size=(5e-9 * nx, 4e-9 * ny, 3e-9))
+    tiles = mt.mt_tiles_create(ctx, t)
+    Th = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_HALF)
+    assert Th.info()["half"] == 1
+    md = oracle.Model.from_tiles(t)
+    for B in (1, 2):
+        m = np.stack([wl.m_random(t.n, seed=70 + b) for b in range(B)]).astype(np.float32)
+        mg = torch.tensor(m.ravel(), device="cuda")
+        H = torch.full_like(mg, float("nan"))
+        mt.mt_demag_field(Th, mg, H, B=B)
+        torch.cuda.synchronize()
+        h = H.cpu().numpy().reshape(B, t.n, 3)
+        for b in range(B):
+            ref = oracle.demag_field(md, m[b].astype(np.float64))
+            assert _rel(h[b], ref) <= 1e-6, (t.n, B, b, _rel(h[b], ref))
+
+
+def test_default_half_above_the_threshold(mt, ctx):
+    # 4,160 tiles of one shape: stored half by default; the field equals the
+    # full storage's and the oracle's matrix-free rows on sampled rows
+    import torch
+    t = wl.film(80, 52, 1, size=(400e-9, 260e-9, 3e-9))
+    tiles = mt.mt_tiles_create(ctx, t)
+    Th = mt.mt_demag_assemble(tiles, "f32")
+    Tf = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)
+    assert Th.info()["half"] == 1 and Tf.info()["half"] == 0
+    for B in (1, 2, 3):
+        m = np.stack([wl.m_random(t.n, seed=80 + b) for b in range(B)]).astype(np.float32)
+        mg = torch.tensor(m.ravel(), device="cuda")
+        Hh, Hf = torch.empty_like(mg), torch.empty_like(mg)
+        mt.mt_demag_field(Th, mg, Hh, B=B)
+        mt.mt_demag_field(Tf, mg, Hf, B=B)
+        torch.cuda.synchronize()
+        hh = Hh.cpu().numpy().reshape(B, t.n, 3)
+        hf = Hf.cpu().numpy().reshape(B, t.n, 3)
+        assert _rel(hh, hf) <= 1e-6, B
+    rows = np.unique(np.concatenate([[0, 127, 128, 4095, t.n - 1],
+                                     np.random.default_rng(5).integers(0, t.n, 40)]))
+    ref = oracle.demag_field_rows(t.centre, t.edge, t.Ms, m[0].astype(np.float64), rows)
+    assert _rel(hh[0][rows], ref) <= 1e-6

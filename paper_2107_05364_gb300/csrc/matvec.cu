@@ -18,7 +18,12 @@
 //     tensor value is read from shared memory once, as a 16-byte vector;
 //   * a panel split between two CTAs is finished by whichever warp arrives
 //     last (counter per panel and warp): it sums the partial rows in CTA
-//     order, so the result does not depend on timing.
+//     order, so the result does not depend on timing;
+//   * before waiting on the kernel ahead of it (which writes the operand,
+//     never the tensor), each CTA prefetches its first chunks into L2.
+// A tensor of tiles of one shape is symmetric and stored as its upper
+// triangle (Sec. 3.2); k_matvec_half and k_half_cols below apply it, each
+// stored chunk above the diagonal also to its columns.
 #include <algorithm>
 #include <cstdio>
 #include <type_traits>

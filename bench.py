@@ -363,7 +363,7 @@ def run_ours(args):
                      "traffic": None if n != 10000 else (MATVEC_F32_HALF_N10000_TRAFFIC if info["half"]
                                                          else MATVEC_F32_N10000_TRAFFIC).get(planes),
                      "kernel": (("k_matvec_half<f32" if info["half"] else "k_matvec<f32") +
-                                (", 4 planes" if planes == 4 else "") +
+                                (", %d planes" % planes if planes != 6 else "") +
                                 ("> + k_half_cols" if info["half"] else ">")),
                      "stored": "upper triangle of blocks (N_ij = N_ji: tiles of one shape)" if info["half"]
                      else "every block",

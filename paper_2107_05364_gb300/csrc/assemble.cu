@@ -264,7 +264,8 @@ struct AsmArgs {
   void *data;
   int8_t *scale;
   int *bad;           // set to 1 on overlap
-  int *planar_bad;    // set to 1 if a 4-plane (single-layer) tensor meets |N_xz| or |N_yz| > kPlanarTol
+  int *planar_bad;    // set to 1 if a 4- or 3-plane (single-layer) tensor meets |N_xz| or |N_yz| >
+                      // kPlanarTol, or (3 planes) a block's trace off delta_ij by more than kTraceTol
   int dense;          // 1: 9-entry row-major matrix (Kp x Kp), else tile-blocked
   int half;           // 1: streaming FP32 tensor of one tile shape, upper triangle of chunks only
   int64_t Kp;
@@ -369,7 +370,12 @@ __global__ void k_assemble(AsmArgs A) {
         for (int e = 0; e < 6; ++e) {
           const int pl = stream_plane(e, A.nplane);
           if (pl >= 0) D[layout_index_h(i, j, pl, A.TR, A.TC, A.nplane, A.Q, A.half)] = (float)N6[e];
-          else if (!(fabs(N6[e]) <= kPlanarTol)) *A.planar_bad = 1;
+          else if (A.nplane == 3 && e == 5) {
+            // zz is not stored: the identity that gives it must hold here
+            const double tr = N6[0] + N6[3] + N6[5] - (i == j ? 1.0 : 0.0);
+            if (!(fabs(tr) <= kTraceTol * (fabs(N6[0]) + fabs(N6[3]) + fabs(N6[5])) + kPlanarTol))
+              *A.planar_bad = 1;
+          } else if (!(fabs(N6[e]) <= kPlanarTol)) *A.planar_bad = 1;
         }
       } break;
       case MT_BF16_SCALED: {
@@ -467,10 +473,16 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
     switch (prec) {
       case MT_F64: v = ((const double *)data)[layout_index(i, j, e, TR, TC, 6, Q)]; break;
       case MT_F32: {
-        const int pl = stream_plane(e, nplane);
-        int64_t at = pl < 0 ? -1 : layout_index_h(i, j, pl, TR, TC, nplane, Q, hs);
-        if (pl >= 0 && at < 0) at = layout_index_h(j, i, pl, TR, TC, nplane, Q, hs);  // N_ij = N_ji
-        v = pl < 0 ? 0.0 : ((const float *)data)[at];
+        auto stored = [&](int ee) {
+          const int pl = stream_plane(ee, nplane);
+          int64_t at = pl < 0 ? -1 : layout_index_h(i, j, pl, TR, TC, nplane, Q, hs);
+          if (pl >= 0 && at < 0) at = layout_index_h(j, i, pl, TR, TC, nplane, Q, hs);  // N_ij = N_ji
+          return pl < 0 ? 0.0 : (double)((const float *)data)[at];
+        };
+        if (nplane == 3 && e == 5)  // zz from the trace: delta_ij - xx - yy of the stored values, in FP32
+          v = (double)((i == j ? 1.0f : 0.0f) - ((float)stored(0) + (float)stored(3)));
+        else
+          v = stored(e);
       } break;
       case MT_BF16_SCALED: {
         const int pl = stream_plane(e, nplane);
@@ -609,9 +621,10 @@ mt_status assemble(mt_tensor *T) {
   int bad[2] = {0, 0};
   MT_CUDA(cudaMemcpy(bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost));
   MT_CHECK(!bad[0], MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
-  if (bad[1] && T->L.nplane == 4) {
-    // an xz or yz entry of the single-layer set is not round-off: store all
-    // 6 planes after all (within the budget reserved for them)
+  if (bad[1] && (T->L.nplane == 4 || T->L.nplane == 3)) {
+    // an xz or yz entry of the single-layer set is not round-off, or (3
+    // planes) a block's trace is off its identity: store all 6 planes after
+    // all (within the budget reserved for them)
     mt_ctx *ctx = t->ctx;
     const bool half = T->L.half;
     layout_for(T->prec, &T->L);

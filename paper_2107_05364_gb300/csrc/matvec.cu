@@ -38,6 +38,9 @@ namespace {
 constexpr int kF32Planar = 4;
 constexpr int kBF16Planar = 5;
 constexpr int kSplitPlanar = 6;  // hi planes xx, xy, yy, zz, then the lo planes
+// FP32 tensor of a single-layer tile set stored half: planes xx, xy, yy
+// (zz = delta_ij - xx - yy, the trace; see traceless in mt_internal.cuh)
+constexpr int kF32Traceless = 7;
 
 template <int PREC>
 struct MvCfg;
@@ -56,6 +59,14 @@ struct MvCfg<kF32Planar> {
   // chunks) timed faster alone (0.234 against 0.248 ms at n = 10,000) but
   // slower inside the step graph (1.450 against 1.397 ms per attempt)
   static constexpr int TR = 16, TC = 128, NPLANE = 4, VEC = 4, W = 4, STAGES = 6;
+  static constexpr bool SCALED = false, PLANAR = true;
+};
+template <>
+struct MvCfg<kF32Traceless> {
+  using T = float;
+  using Acc = float;
+  // 24 KB chunks: 8 in the ring
+  static constexpr int TR = 16, TC = 128, NPLANE = 3, VEC = 4, W = 4, STAGES = 8;
   static constexpr bool SCALED = false, PLANAR = true;
 };
 template <>
@@ -122,7 +133,7 @@ template <int PREC>
 __device__ __forceinline__ void load_vals(const unsigned char *stage, int plane, int row, int lane,
                                           typename MvCfg<PREC>::Acc v[MvCfg<PREC>::VEC]) {
   using C = MvCfg<PREC>;
-  if constexpr (PREC == MT_F32 || PREC == kF32Planar) {
+  if constexpr (PREC == MT_F32 || PREC == kF32Planar || PREC == kF32Traceless) {
     const float4 a = reinterpret_cast<const float4 *>(stage)[(plane * C::TR + row) * (C::TC / 4) + lane];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   } else if constexpr (PREC == MT_F64) {
@@ -731,6 +742,17 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
       const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
       return k * TR + warp * S::RPW + r;
     };
+    // traceless storage: the self block's N_zz is 1 - xx - yy, the stream
+    // gave -(xx + yy), so the row's z sum lacks Ms_i m_i,z (its operand)
+    auto self_z = [&](int m, int v) -> float {
+      if constexpr (C::NPLANE == 3) {
+        if (v % 3 != 2) return 0.0f;
+        const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
+        return xi[m * K * S::RPW + k * S::RPW + r].z;
+      } else {
+        return 0.0f;
+      }
+    };
     const int64_t row0 = R * K * TR;
     if (kf == kl) {
 #pragma unroll
@@ -741,7 +763,7 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
         if (row >= A.n) continue;
 #pragma unroll
         for (int m = 0; m < SB; ++m)
-          if (float *H = out(g * SB + m)) H[3 * row + v % 3] = -mine[m][h];
+          if (float *H = out(g * SB + m)) H[3 * row + v % 3] = -(mine[m][h] + self_z(m, v));
       }
       return;
     }
@@ -773,7 +795,7 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
           tot += __ldcg(&A.part[((sl * SB + m) * K * TR + row_of(v)) * 3 + v % 3]);
         }
         float *H = out(g * SB + m);
-        if (H && row < A.n) H[3 * row + v % 3] = -tot;
+        if (H && row < A.n) H[3 * row + v % 3] = -(tot + self_z(m, v));
       }
     }
     if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
@@ -812,7 +834,33 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
 #pragma unroll
             for (int m = 0; m < SB; ++m) xr[m] = xi[m * K * S::RPW + k * S::RPW + r];
           }
-          if constexpr (C::PLANAR) {
+          if constexpr (C::NPLANE == 3) {
+            // zz = -(xx + yy) (trace 0; the self blocks' +1 is added in
+            // flush_rows)
+            float nxx[4], nxy[4], nyy[4];
+            load_vals<PREC>(st, 0, row, lane, nxx);
+            load_vals<PREC>(st, 1, row, lane, nxy);
+            load_vals<PREC>(st, 2, row, lane, nyy);
+#pragma unroll
+            for (int m = 0; m < SB; ++m) {
+              float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                const float nzz = -(nxx[v] + nyy[v]);
+                sx = fmaf(nxx[v], X[m][v], fmaf(nxy[v], Y[m][v], sx));
+                sy = fmaf(nxy[v], X[m][v], fmaf(nyy[v], Y[m][v], sy));
+                sz = fmaf(nzz, Z[m][v], sz);
+                if constexpr (STRICT) {
+                  colp[m][v][0] = fmaf(nxx[v], xr[m].x, fmaf(nxy[v], xr[m].y, colp[m][v][0]));
+                  colp[m][v][1] = fmaf(nxy[v], xr[m].x, fmaf(nyy[v], xr[m].y, colp[m][v][1]));
+                  colp[m][v][2] = fmaf(nzz, xr[m].z, colp[m][v][2]);
+                }
+              }
+              acc[m][k][r][0] += sx;
+              acc[m][k][r][1] += sy;
+              acc[m][k][r][2] += sz;
+            }
+          } else if constexpr (C::PLANAR) {
             float nxx[4], nxy[4], nyy[4], nzz[4];
             load_vals<PREC>(st, 0, row, lane, nxx);
             load_vals<PREC>(st, 1, row, lane, nxy);
@@ -1209,7 +1257,7 @@ __global__ void k_near_v(int64_t n, int B, int Bp, const int32_t *ptr, const int
 // half storage is built for FP32 tensors only (6 or 4 planes)
 template <int PREC>
 constexpr bool has_half() {
-  return PREC == MT_F32 || PREC == kF32Planar;
+  return PREC == MT_F32 || PREC == kF32Planar || PREC == kF32Traceless;
 }
 
 template <int PREC, int SB>
@@ -1307,6 +1355,16 @@ void launch_half(const mt_tensor *T, const float *xs, int B, float *H, float *pa
                  work + h.slice);
 }
 
+// a layout that exists only stored half (3 planes)
+template <int PREC>
+void launch_half_only(const mt_tensor *T, const void *xs, int B, void *H, void *part, int *count,
+                      const int *active, int *status, float *colpart, cudaStream_t s) {
+  if (mv_group(B, PREC, true) == 1)
+    launch_half<PREC, 1>(T, (const float *)xs, B, (float *)H, (float *)part, count, active, status, colpart, s);
+  else
+    launch_half<PREC, 2>(T, (const float *)xs, B, (float *)H, (float *)part, count, active, status, colpart, s);
+}
+
 template <int PREC>
 void launch_mv(const mt_tensor *T, const void *xs, int B, void *H, void *part, int *count, const int *active,
                int *status, float *colpart, cudaStream_t s) {
@@ -1353,6 +1411,13 @@ cudaError_t matvec_prepare() {
   cudaError_t e;
   if ((e = prepare_mv<MT_F32>()) != cudaSuccess) return e;
   if ((e = prepare_mv<kF32Planar>()) != cudaSuccess) return e;
+  // the traceless layout is always stored half: its half kernels only
+  if ((e = cudaFuncSetAttribute(k_matvec_half<kF32Traceless, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                HalfShape<kF32Traceless, 1>::SMEM_BYTES)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_matvec_half<kF32Traceless, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                HalfShape<kF32Traceless, 2>::SMEM_BYTES)) != cudaSuccess)
+    return e;
   if ((e = prepare_mv<kBF16Planar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<kSplitPlanar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<MT_F64>()) != cudaSuccess) return e;
@@ -1380,6 +1445,14 @@ void layout_for_planar(int prec, mt_layout *L) {
     L->elem_bytes = 4;
     L->scale_bytes_per_chunk = 0;
   }
+}
+
+void layout_for_traceless(mt_layout *L) {
+  L->TR = MvCfg<kF32Traceless>::TR;
+  L->TC = MvCfg<kF32Traceless>::TC;
+  L->nplane = MvCfg<kF32Traceless>::NPLANE;
+  L->elem_bytes = 4;
+  L->scale_bytes_per_chunk = 0;
 }
 
 void layout_for(int prec, mt_layout *L) {
@@ -1446,7 +1519,8 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
                    const int *active, int *status, cudaStream_t s, float *colpart) {
   switch (T->prec) {
     case MT_F32:
-      if (T->L.nplane == 4) launch_mv<kF32Planar>(T, xs, B, H, part, count, active, status, colpart, s);
+      if (T->L.nplane == 3) launch_half_only<kF32Traceless>(T, xs, B, H, part, count, active, status, colpart, s);
+      else if (T->L.nplane == 4) launch_mv<kF32Planar>(T, xs, B, H, part, count, active, status, colpart, s);
       else launch_mv<MT_F32>(T, xs, B, H, part, count, active, status, colpart, s);
       break;
     case MT_F64: launch_mv<MT_F64>(T, xs, B, H, part, count, active, status, nullptr, s); break;

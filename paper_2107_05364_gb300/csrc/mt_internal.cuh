@@ -218,15 +218,27 @@ struct mt_tensor {
 
 // Plane of entry e (xx, xy, xz, yy, yz, zz) in a streaming layout of
 // nplane planes: the identity for 6, -1 for the xz and yz entries of a
-// single-layer tensor (planes xx, xy, yy, zz).  The split precision holds
-// two such sets (hi, then lo): call it with half its planes.
+// single-layer tensor (planes xx, xy, yy, zz), and with 3 planes (xx, xy,
+// yy: a single-layer FP32 tensor stored half) -1 for zz as well, which the
+// trace gives (see traceless).  The split precision holds two such sets (hi,
+// then lo): call it with half its planes.
 __host__ __device__ __forceinline__ int stream_plane(int e, int nplane) {
-  if (nplane != 4) return e;
-  return e < 2 ? e : e == 3 ? 2 : e == 5 ? 3 : -1;
+  if (nplane == 4) return e < 2 ? e : e == 3 ? 2 : e == 5 ? 3 : -1;
+  if (nplane == 3) return e < 2 ? e : e == 3 ? 2 : -1;
+  return e;
 }
 // bound on |N_xz|, |N_yz| of a single-layer tile set (FP64 round-off of
 // entries that vanish by mirror symmetry)
 constexpr double kPlanarTol = 1e-12;
+// Traceless storage.  The potential of a uniformly magnetised tile is
+// harmonic outside it, so the point tensor of tile j at the centre of any
+// other tile i has trace 0, and a self block trace 1: N_zz = delta_ij -
+// N_xx - N_yy.  A 3-plane tensor stores xx, xy, yy only; assembly checks the
+// identity on every block, |trace - delta_ij| <= kTraceTol (|N_xx| + |N_yy| +
+// |N_zz|) + kPlanarTol (the FP64 round-off of the corner sums, which for
+// distant tiles is absolute: their small entries are differences of O(1)
+// terms); else all 6 planes are stored.
+constexpr double kTraceTol = 1e-9;
 // MT_LAYOUT_STREAM stores a tensor of tiles of one shape half from this many
 // tiles on: measured on single-layer films, one simulation, per attempted
 // integrator step, half against full storage 0.178 / 0.140 ms at 2,500 tiles,
@@ -291,6 +303,9 @@ cudaError_t matvec_prepare();
 // Panel/chunk shape of the storage for a precision (P, Q left to the caller).
 void layout_for(int prec, mt_layout *L);
 void layout_for_planar(int prec, mt_layout *L);  // single-layer tile set: 4 entry planes (split: 4 hi + 4 lo)
+// single-layer FP32 tile set stored half: 3 entry planes (xx, xy, yy; zz
+// from the trace)
+void layout_for_traceless(mt_layout *L);
 // floats of the padded, Ms-scaled operand of one simulation: Q * 3 * TC
 int64_t xs_floats(const mt_tensor *T);
 // bytes of the partial-sum workspace and of the panel counters for B sims

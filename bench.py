@@ -46,12 +46,12 @@ MU0 = 4e-7 * math.pi
 # row).  Valid while k_matvec<f32> is unchanged.
 MATVEC_F32_N10000_TRAFFIC = {4: 1618117632 + 2918912}  # tensors storing every block
 # The same film with the tensor stored half (upper triangle of chunks, in
-# super-row order), one ncu capture of each kernel of a product:
-# k_matvec_half<f32, 4 planes> read 828,403,456 and wrote 4,449,792 bytes,
-# k_half_cols read 4,875,520 (the column sums of the groups above the
-# diagonal) -- 1.047 x the 0.80 GB algorithmic bytes.  Valid while both
-# kernels are unchanged.
-MATVEC_F32_HALF_N10000_TRAFFIC = {4: 828403456 + 4449792 + 4875520}
+# super-row order) and traceless (3 planes: xx, xy, yy), one ncu capture of
+# each kernel of a product: k_matvec_half<f32, 3 planes> read 621,362,176 and
+# wrote 4,646,912 bytes, k_half_cols read 4,875,008 (the column sums of the
+# groups above the diagonal) -- 1.051 x the 0.60 GB algorithmic bytes.  Valid
+# while both kernels are unchanged.
+MATVEC_F32_HALF_N10000_TRAFFIC = {3: 621362176 + 4646912 + 4875008}
 
 
 def f32_alg_bytes(info, n):

@@ -511,9 +511,10 @@ mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout, mt_ten
           same = same && std::fabs(tiles->edge[3 * i + a] - tiles->edge[a]) <= 1e-12 * tiles->edge[a];
       T->L.half = same;
     }
-    // a single-layer FP32 tensor stored half keeps 3 planes: zz from the
-    // trace (traceless; checked on every block at assembly)
-    if (T->L.half && T->L.nplane == 4 && prec == MT_F32) mt::layout_for_traceless(&T->L);
+    // an FP32 tensor stored half leaves out zz, which the trace gives
+    // (traceless; checked on every block at assembly): 3 planes for a single
+    // layer, 5 otherwise
+    if (T->L.half && prec == MT_F32) mt::layout_for_traceless(&T->L, T->L.nplane == 4);
     if (force_half && !T->L.half) {
       delete T;
       mt::tiles_release(tiles);

@@ -265,7 +265,7 @@ struct AsmArgs {
   int8_t *scale;
   int *bad;           // set to 1 on overlap
   int *planar_bad;    // set to 1 if a 4- or 3-plane (single-layer) tensor meets |N_xz| or |N_yz| >
-                      // kPlanarTol, or (3 planes) a block's trace off delta_ij by more than kTraceTol
+                      // kPlanarTol, or (3 or 5 planes) a block's trace off delta_ij by more than kTraceTol
   int dense;          // 1: 9-entry row-major matrix (Kp x Kp), else tile-blocked
   int half;           // 1: streaming FP32 tensor of one tile shape, upper triangle of chunks only
   int64_t Kp;
@@ -370,7 +370,7 @@ __global__ void k_assemble(AsmArgs A) {
         for (int e = 0; e < 6; ++e) {
           const int pl = stream_plane(e, A.nplane);
           if (pl >= 0) D[layout_index_h(i, j, pl, A.TR, A.TC, A.nplane, A.Q, A.half)] = (float)N6[e];
-          else if (A.nplane == 3 && e == 5) {
+          else if (traceless(A.nplane) && e == 5) {
             // zz is not stored: the identity that gives it must hold here
             const double tr = N6[0] + N6[3] + N6[5] - (i == j ? 1.0 : 0.0);
             if (!(fabs(tr) <= kTraceTol * (fabs(N6[0]) + fabs(N6[3]) + fabs(N6[5])) + kPlanarTol))
@@ -479,7 +479,7 @@ __global__ void k_read_rows(const void *data, const int8_t *scale, int prec, int
           if (pl >= 0 && at < 0) at = layout_index_h(j, i, pl, TR, TC, nplane, Q, hs);  // N_ij = N_ji
           return pl < 0 ? 0.0 : (double)((const float *)data)[at];
         };
-        if (nplane == 3 && e == 5)  // zz from the trace: delta_ij - xx - yy of the stored values, in FP32
+        if (traceless(nplane) && e == 5)  // zz from the trace: delta_ij - xx - yy of the stored values, in FP32
           v = (double)((i == j ? 1.0f : 0.0f) - ((float)stored(0) + (float)stored(3)));
         else
           v = stored(e);
@@ -621,7 +621,7 @@ mt_status assemble(mt_tensor *T) {
   int bad[2] = {0, 0};
   MT_CUDA(cudaMemcpy(bad, d_bad, 2 * sizeof(int), cudaMemcpyDeviceToHost));
   MT_CHECK(!bad[0], MT_EOVERLAP, "mt_demag_assemble: tiles overlap or a tile centre lies on another tile");
-  if (bad[1] && (T->L.nplane == 4 || T->L.nplane == 3)) {
+  if (bad[1] && (T->L.nplane == 4 || traceless(T->L.nplane))) {
     // an xz or yz entry of the single-layer set is not round-off, or (3
     // planes) a block's trace is off its identity: store all 6 planes after
     // all (within the budget reserved for them)

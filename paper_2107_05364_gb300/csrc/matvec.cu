@@ -41,6 +41,9 @@ constexpr int kSplitPlanar = 6;  // hi planes xx, xy, yy, zz, then the lo planes
 // FP32 tensor of a single-layer tile set stored half: planes xx, xy, yy
 // (zz = delta_ij - xx - yy, the trace; see traceless in mt_internal.cuh)
 constexpr int kF32Traceless = 7;
+// FP32 tensor of a tile set of one shape stored half, not single-layer:
+// planes xx, xy, xz, yy, yz (zz from the trace)
+constexpr int kF32Traceless5 = 8;
 
 template <int PREC>
 struct MvCfg;
@@ -68,6 +71,14 @@ struct MvCfg<kF32Traceless> {
   // 24 KB chunks: 8 in the ring
   static constexpr int TR = 16, TC = 128, NPLANE = 3, VEC = 4, W = 4, STAGES = 8;
   static constexpr bool SCALED = false, PLANAR = true;
+};
+template <>
+struct MvCfg<kF32Traceless5> {
+  using T = float;
+  using Acc = float;
+  // 40 KB chunks: 5 in the ring
+  static constexpr int TR = 16, TC = 128, NPLANE = 5, VEC = 4, W = 4, STAGES = 5;
+  static constexpr bool SCALED = false, PLANAR = false;
 };
 template <>
 struct MvCfg<MT_F64> {
@@ -133,7 +144,7 @@ template <int PREC>
 __device__ __forceinline__ void load_vals(const unsigned char *stage, int plane, int row, int lane,
                                           typename MvCfg<PREC>::Acc v[MvCfg<PREC>::VEC]) {
   using C = MvCfg<PREC>;
-  if constexpr (PREC == MT_F32 || PREC == kF32Planar || PREC == kF32Traceless) {
+  if constexpr (PREC == MT_F32 || PREC == kF32Planar || PREC == kF32Traceless || PREC == kF32Traceless5) {
     const float4 a = reinterpret_cast<const float4 *>(stage)[(plane * C::TR + row) * (C::TC / 4) + lane];
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
   } else if constexpr (PREC == MT_F64) {
@@ -745,7 +756,7 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
     // traceless storage: the self block's N_zz is 1 - xx - yy, the stream
     // gave -(xx + yy), so the row's z sum lacks Ms_i m_i,z (its operand)
     auto self_z = [&](int m, int v) -> float {
-      if constexpr (C::NPLANE == 3) {
+      if constexpr (C::NPLANE == 3 || C::NPLANE == 5) {
         if (v % 3 != 2) return 0.0f;
         const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
         return xi[m * K * S::RPW + k * S::RPW + r].z;
@@ -854,6 +865,34 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
                   colp[m][v][0] = fmaf(nxx[v], xr[m].x, fmaf(nxy[v], xr[m].y, colp[m][v][0]));
                   colp[m][v][1] = fmaf(nxy[v], xr[m].x, fmaf(nyy[v], xr[m].y, colp[m][v][1]));
                   colp[m][v][2] = fmaf(nzz, xr[m].z, colp[m][v][2]);
+                }
+              }
+              acc[m][k][r][0] += sx;
+              acc[m][k][r][1] += sy;
+              acc[m][k][r][2] += sz;
+            }
+          } else if constexpr (C::NPLANE == 5) {
+            // zz = -(xx + yy) (trace 0; the self blocks' +1 is added in
+            // flush_rows)
+            float nxx[4], nxy[4], nxz[4], nyy[4], nyz[4];
+            load_vals<PREC>(st, 0, row, lane, nxx);
+            load_vals<PREC>(st, 1, row, lane, nxy);
+            load_vals<PREC>(st, 2, row, lane, nxz);
+            load_vals<PREC>(st, 3, row, lane, nyy);
+            load_vals<PREC>(st, 4, row, lane, nyz);
+#pragma unroll
+            for (int m = 0; m < SB; ++m) {
+              float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                const float nzz = -(nxx[v] + nyy[v]);
+                sx = fmaf(nxx[v], X[m][v], fmaf(nxy[v], Y[m][v], fmaf(nxz[v], Z[m][v], sx)));
+                sy = fmaf(nxy[v], X[m][v], fmaf(nyy[v], Y[m][v], fmaf(nyz[v], Z[m][v], sy)));
+                sz = fmaf(nxz[v], X[m][v], fmaf(nyz[v], Y[m][v], fmaf(nzz, Z[m][v], sz)));
+                if constexpr (STRICT) {
+                  colp[m][v][0] = fmaf(nxx[v], xr[m].x, fmaf(nxy[v], xr[m].y, fmaf(nxz[v], xr[m].z, colp[m][v][0])));
+                  colp[m][v][1] = fmaf(nxy[v], xr[m].x, fmaf(nyy[v], xr[m].y, fmaf(nyz[v], xr[m].z, colp[m][v][1])));
+                  colp[m][v][2] = fmaf(nxz[v], xr[m].x, fmaf(nyz[v], xr[m].y, fmaf(nzz, xr[m].z, colp[m][v][2])));
                 }
               }
               acc[m][k][r][0] += sx;
@@ -1257,7 +1296,7 @@ __global__ void k_near_v(int64_t n, int B, int Bp, const int32_t *ptr, const int
 // half storage is built for FP32 tensors only (6 or 4 planes)
 template <int PREC>
 constexpr bool has_half() {
-  return PREC == MT_F32 || PREC == kF32Planar || PREC == kF32Traceless;
+  return PREC == MT_F32 || PREC == kF32Planar || PREC == kF32Traceless || PREC == kF32Traceless5;
 }
 
 template <int PREC, int SB>
@@ -1418,6 +1457,12 @@ cudaError_t matvec_prepare() {
   if ((e = cudaFuncSetAttribute(k_matvec_half<kF32Traceless, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 HalfShape<kF32Traceless, 2>::SMEM_BYTES)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(k_matvec_half<kF32Traceless5, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                HalfShape<kF32Traceless5, 1>::SMEM_BYTES)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_matvec_half<kF32Traceless5, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                HalfShape<kF32Traceless5, 2>::SMEM_BYTES)) != cudaSuccess)
+    return e;
   if ((e = prepare_mv<kBF16Planar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<kSplitPlanar>()) != cudaSuccess) return e;
   if ((e = prepare_mv<MT_F64>()) != cudaSuccess) return e;
@@ -1447,10 +1492,10 @@ void layout_for_planar(int prec, mt_layout *L) {
   }
 }
 
-void layout_for_traceless(mt_layout *L) {
+void layout_for_traceless(mt_layout *L, bool planar) {
   L->TR = MvCfg<kF32Traceless>::TR;
   L->TC = MvCfg<kF32Traceless>::TC;
-  L->nplane = MvCfg<kF32Traceless>::NPLANE;
+  L->nplane = planar ? MvCfg<kF32Traceless>::NPLANE : MvCfg<kF32Traceless5>::NPLANE;
   L->elem_bytes = 4;
   L->scale_bytes_per_chunk = 0;
 }
@@ -1520,6 +1565,8 @@ void launch_matvec(const mt_tensor *T, const float *xs, int B, float *H, float *
   switch (T->prec) {
     case MT_F32:
       if (T->L.nplane == 3) launch_half_only<kF32Traceless>(T, xs, B, H, part, count, active, status, colpart, s);
+      else if (T->L.nplane == 5)
+        launch_half_only<kF32Traceless5>(T, xs, B, H, part, count, active, status, colpart, s);
       else if (T->L.nplane == 4) launch_mv<kF32Planar>(T, xs, B, H, part, count, active, status, colpart, s);
       else launch_mv<MT_F32>(T, xs, B, H, part, count, active, status, colpart, s);
       break;

@@ -225,15 +225,19 @@ struct mt_tensor {
 __host__ __device__ __forceinline__ int stream_plane(int e, int nplane) {
   if (nplane == 4) return e < 2 ? e : e == 3 ? 2 : e == 5 ? 3 : -1;
   if (nplane == 3) return e < 2 ? e : e == 3 ? 2 : -1;
+  if (nplane == 5) return e < 5 ? e : -1;  // xx, xy, xz, yy, yz (zz from the trace)
   return e;
 }
+// zz is given by the trace (not stored) in a 3- or 5-plane layout
+__host__ __device__ __forceinline__ bool traceless(int nplane) { return nplane == 3 || nplane == 5; }
 // bound on |N_xz|, |N_yz| of a single-layer tile set (FP64 round-off of
 // entries that vanish by mirror symmetry)
 constexpr double kPlanarTol = 1e-12;
 // Traceless storage.  The potential of a uniformly magnetised tile is
 // harmonic outside it, so the point tensor of tile j at the centre of any
 // other tile i has trace 0, and a self block trace 1: N_zz = delta_ij -
-// N_xx - N_yy.  A 3-plane tensor stores xx, xy, yy only; assembly checks the
+// N_xx - N_yy.  A 3-plane tensor stores xx, xy, yy only (a single layer,
+// whose xz and yz vanish), a 5-plane one xx, xy, xz, yy, yz; assembly checks the
 // identity on every block, |trace - delta_ij| <= kTraceTol (|N_xx| + |N_yy| +
 // |N_zz|) + kPlanarTol (the FP64 round-off of the corner sums, which for
 // distant tiles is absolute: their small entries are differences of O(1)
@@ -303,9 +307,9 @@ cudaError_t matvec_prepare();
 // Panel/chunk shape of the storage for a precision (P, Q left to the caller).
 void layout_for(int prec, mt_layout *L);
 void layout_for_planar(int prec, mt_layout *L);  // single-layer tile set: 4 entry planes (split: 4 hi + 4 lo)
-// single-layer FP32 tile set stored half: 3 entry planes (xx, xy, yy; zz
-// from the trace)
-void layout_for_traceless(mt_layout *L);
+// FP32 tile set stored half: zz from the trace, 3 entry planes (xx, xy, yy)
+// for a single layer (planar), else 5 (xx, xy, xz, yy, yz)
+void layout_for_traceless(mt_layout *L, bool planar);
 // floats of the padded, Ms-scaled operand of one simulation: Q * 3 * TC
 int64_t xs_floats(const mt_tensor *T);
 // bytes of the partial-sum workspace and of the panel counters for B sims

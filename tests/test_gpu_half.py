@@ -66,19 +66,20 @@ def test_half_storage_is_chosen_and_smaller(mt, case):
     name, t, tiles, Th, Tf, md = case
     ih, ifu = Th.info(), Tf.info()
     assert ih["half"] == 1 and ifu["half"] == 0
-    # a single-layer film stored half keeps xx, xy, yy (zz from the trace)
+    # stored half, zz is left to the trace: a single-layer film keeps xx, xy,
+    # yy, the prism xx, xy, xz, yy, yz
     film = name.startswith("film")
-    assert ifu["planes"] == (4 if film else 6) and ih["planes"] == (3 if film else 6)
-    # the upper triangle of chunks: a bit more than half of the full tensor
-    # (times 3/4 for the film's third plane)
-    lo, hi = (0.375, 0.42) if film else (0.5, 0.56)
+    assert ifu["planes"] == (4 if film else 6) and ih["planes"] == (3 if film else 5)
+    # the upper triangle of chunks: a bit more than half of the full tensor,
+    # times 3/4 (film) or 5/6 (prism) for the planes
+    lo, hi = (0.375, 0.42) if film else (0.416, 0.467)
     assert lo < ih["bytes"] / ifu["bytes"] < hi
 
 
 def test_half_stored_rows_are_the_tensor(mt, case):
     # rows read from the half storage (lower blocks taken from their upper
-    # partners; on the film zz = delta_ij - xx - yy) against the oracle's FP64
-    # blocks, at FP32 rounding
+    # partners; zz = delta_ij - xx - yy) against the oracle's FP64 blocks, at
+    # FP32 rounding
     name, t, tiles, Th, Tf, md = case
     rows = [0, 15, 16, 127, 128, t.n // 2, t.n - 1]
     for i in rows:

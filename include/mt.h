@@ -249,11 +249,12 @@ MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **ou
  * one holding its own rows on (about n^2 / 2 blocks); the product applies
  * each off-diagonal chunk to its rows and, transposed, to its columns (a
  * column work area of 1.5 KB per stored chunk and simulation, held by the
- * tensor or the integrator).  A single-layer set stored half keeps 3 planes,
- * xx, xy, yy: a tile's potential is harmonic outside it, so every block of
- * two different tiles has trace 0 (a self block trace 1), and the product
- * forms N_zz = delta_ij - N_xx - N_yy (assembly checks the identity on every
- * block and otherwise stores all 6 planes; mt_tensor_info.planes tells).
+ * tensor or the integrator).  Stored half, the tensor leaves out zz: a
+ * tile's potential is harmonic outside it, so every block of two different
+ * tiles has trace 0 (a self block trace 1), and the product forms N_zz =
+ * delta_ij - N_xx - N_yy.  A single-layer set keeps 3 planes (xx, xy, yy),
+ * others 5 (xx, xy, xz, yy, yz); assembly checks the identity on every block
+ * and otherwise stores all 6 planes (mt_tensor_info.planes tells).
  * mt_tensor_info.half tells;
  * MT_LAYOUT_STREAM_FULL stores every block.  The half storage's product is
  * the faster one for products over 1 or 2 simulations (n = 10,000 film:

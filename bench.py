@@ -653,7 +653,8 @@ def run_threshold(args):
         err = float(np.linalg.norm(H.cpu().numpy() - H0n) / np.linalg.norm(H0n))
         trace, wall, nrhs = dynamics(S)
         info = S.info()
-        rows.append({"fraction": f, "kept_elements": kept, "sparse_bytes": info["bytes"], "product_ms": ms,
+        rows.append({"fraction": f, "kept_elements": kept, "sparse_bytes": info["bytes"],
+                     "row_warps": info["row_warps"], "product_ms": ms,
                      "field_rel_err": err, "mavg_max_dev": float(np.abs(trace - ref_trace).max()),
                      "dynamics_s": wall, "rhs": nrhs})
         S.close()

@@ -157,7 +157,9 @@ typedef struct {
   int64_t near_blocks; /* FP64 near-field blocks kept apart (0 if none)       */
   int32_t half;        /* 1: only the upper triangle of blocks is stored      */
                        /* (N_ij = N_ji, see mt_demag_assemble)                */
-  int32_t pad;
+  int32_t row_warps;   /* sparse layout: warps that share a row of the        */
+                       /* product (1, 2, 4 or 8; see mt_tensor_threshold);    */
+                       /* 0 for the other layouts                             */
 } mt_tensor_info;
 
 /* ---------------------------------------------------------------------- */
@@ -283,7 +285,10 @@ MT_API mt_status mt_demag_assemble_ex(mt_tiles *tiles, mt_prec prec, int layout,
  * columns of a row are stored as runs of consecutive tiles (gaps of up to 3
  * blocks filled with zeros, runs padded to 4 blocks), so the product reads
  * 24 B per stored block (6 FP32 entries; 16 B for a single-layer tile set)
- * plus 8 B per run, and sums in compensated FP32.  The
+ * plus 8 B per run, and sums in compensated FP32.  A row's blocks are split
+ * among 1, 2, 4 or 8 warps (mt_tensor_info.row_warps), fixed per tensor from
+ * its size and row lengths, so a simulation's field does not depend on the
+ * batch it is computed in.  The
  * new tensor works with mt_demag_field, mt_llg_rhs, mt_energy and the
  * integrator; it keeps the tile set alive.  threshold (may be NULL) gets t,
  * kept_elements (may be NULL) the number of kept nonzero elements.

@@ -55,7 +55,7 @@ class TensorInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("prec", ctypes.c_int32), ("rows_per_panel", ctypes.c_int32),
                 ("cols_per_chunk", ctypes.c_int32), ("layout", ctypes.c_int32), ("planes", ctypes.c_int32),
                 ("bytes", ctypes.c_int64), ("near_blocks", ctypes.c_int64), ("half", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("row_warps", ctypes.c_int32)]
 
 
 class ServerOpts(ctypes.Structure):

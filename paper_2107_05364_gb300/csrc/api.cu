@@ -86,6 +86,7 @@ void free_tensor_mem(mt_tensor *T) {
   cudaFree(T->d_sp_rptr);
   cudaFree(T->d_sp_col);
   cudaFree(T->d_sp_val);
+  cudaFree(T->d_sp_seg);
 }
 
 // workspace of the standalone field/rhs calls for B simulations
@@ -572,7 +573,7 @@ mt_status mt_tensor_get_info(const mt_tensor *T, mt_tensor_info *info) {
   info->bytes = (int64_t)T->bytes;
   info->near_blocks = T->near_count;
   info->half = T->L.half ? 1 : 0;
-  info->pad = 0;
+  info->row_warps = T->layout == MT_LAYOUT_SPARSE ? T->sp_split : 0;
   return MT_OK;
 }
 

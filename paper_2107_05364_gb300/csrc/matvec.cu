@@ -559,7 +559,6 @@ struct HalfArgs {
   int *gcount;       // arrival counters per (simulation group, group)
   float *colpart;    // column sums of every group above the diagonal [NG][NGR][SB][3][TC]
   float *colsplit;   // parts of the groups shared by CTAs [2 G][SB][3][TC]
-  int *arrive;       // k_half_cols arrival counters [B][Q], zeroed by k_matvec_half
   const int *active;
   int *status;
   int64_t n, P, Q, CH, NGR;  // NGR = Q (Q + 1) / 2 groups
@@ -630,10 +629,6 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
                             S::DATA_BYTES);
   }
   mtd::pdl_enter();
-  // the column pass that follows counts its arrivals from zero
-  for (int64_t i = blockIdx.x * (int64_t)S::THREADS + threadIdx.x; i < (int64_t)A.B * A.Q;
-       i += (int64_t)gridDim.x * S::THREADS)
-    A.arrive[i] = 0;
   extern __shared__ __align__(128) unsigned char smem[];
   float *cb = reinterpret_cast<float *>(smem + S::STAGES * S::STAGE_BYTES);
   float4 *xi_all = reinterpret_cast<float4 *>(smem + S::STAGES * S::STAGE_BYTES + S::CB_BYTES);
@@ -1051,34 +1046,36 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
 }
 
 // The transposed part of a half-stored product.  Column j of column chunk q
-// gets sum over the groups (R, q), R < q, of their column sums.  CTA
-// (q, s, b) adds the groups of slice s of R (NS slices, R increasing) and
-// parks the sum; the last CTA of (q, b) to arrive adds the NS slice sums in
-// slice order (a fixed order: the result does not depend on timing) and
-// does H_j -= total.  One thread per column of the chunk.
-__global__ void __launch_bounds__(128) k_half_cols(HalfArgs A, int SB, int TC, int NS, float *slice_sum) {
+// gets the sum over the groups (R, q), R < q, of their column sums.  One CTA
+// per (q, simulation), kHalfColLanes threads per column: thread (r, t) adds
+// column t of the groups R = r, r + kHalfColLanes, ... in increasing R, and
+// the lanes' sums are added in order of r (a fixed order: the result does
+// not depend on timing) before H_j -= total.  Every load of a CTA is issued
+// in one round (the group sums were just written and sit in L2), and no
+// CTA waits on another.
+constexpr int kHalfColLanes = 8;
+template <int TC>
+__global__ void __launch_bounds__(kHalfColLanes *TC) k_half_cols(HalfArgs A, int SB) {
   mtd::pdl_enter();
   const int64_t q = blockIdx.x;
-  const int sl = blockIdx.y, b = blockIdx.z;
-  const int t = threadIdx.x;
-  const int64_t len = (q + NS - 1) / NS;
-  const int64_t Ra = sl * len, Rb = q < Ra + len ? q : Ra + len;
+  const int b = blockIdx.y;
+  const int t = threadIdx.x % TC, r = threadIdx.x / TC;
   const int64_t g = b / SB, m = b - g * SB;
-  float tot[3] = {0.0f, 0.0f, 0.0f};
-  // group (R, q) is number half_gbase(R) + q - R; the next R's is Q - R - 1 on
+  // group (R, q) is number half_gbase(R) + q - R
   const float *base = A.colpart + ((g * A.NGR * SB + m) * 3) * TC + t;
   const int64_t gstride = (int64_t)SB * 3 * TC;
-  int64_t gi = half_gbase(Ra, A.Q) + q - Ra;
-  int64_t R = Ra;
-  for (; R + 4 <= Rb; R += 4) {  // four groups' loads in flight
+  constexpr int L = kHalfColLanes;
+  float tot[3] = {0.0f, 0.0f, 0.0f};
+  int64_t R = r;
+  for (; R + 3 * L < q; R += 4 * L) {  // four groups' loads in flight
     float v[4][3];
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) {
-      const float *cp = base + gi * gstride;
+      const int64_t Rk = R + k2 * L;
+      const float *cp = base + (half_gbase(Rk, A.Q) + q - Rk) * gstride;
       v[k2][0] = __ldcg(cp);
       v[k2][1] = __ldcg(cp + TC);
       v[k2][2] = __ldcg(cp + 2 * TC);
-      gi += A.Q - (R + k2) - 1;
     }
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) {
@@ -1087,33 +1084,27 @@ __global__ void __launch_bounds__(128) k_half_cols(HalfArgs A, int SB, int TC, i
       tot[2] += v[k2][2];
     }
   }
-  for (; R < Rb; ++R) {
-    const float *cp = base + gi * gstride;
+  for (; R < q; R += L) {
+    const float *cp = base + (half_gbase(R, A.Q) + q - R) * gstride;
     tot[0] += __ldcg(cp);
     tot[1] += __ldcg(cp + TC);
     tot[2] += __ldcg(cp + 2 * TC);
-    gi += A.Q - R - 1;
   }
-  const int64_t qb = (int64_t)b * A.Q + q;
-  float *mine = slice_sum + ((qb * NS + sl) * 3) * TC + t;
-  mine[0] = tot[0];
-  mine[TC] = tot[1];
-  mine[2 * TC] = tot[2];
-  __threadfence();
+  __shared__ float lane_sum[L][3][TC];
+  lane_sum[r][0][t] = tot[0];
+  lane_sum[r][1][t] = tot[1];
+  lane_sum[r][2][t] = tot[2];
   __syncthreads();
-  __shared__ int last;
-  if (t == 0) last = (atomicAdd(&A.arrive[qb], 1) == NS - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
+  if (r != 0) return;
   const int64_t j = q * TC + t;
   if (j >= A.n || (A.active && !A.active[b])) return;
-  float v[3] = {0.0f, 0.0f, 0.0f};
-  for (int k2 = 0; k2 < NS; ++k2) {
-    const float *ss = slice_sum + ((qb * NS + k2) * 3) * TC + t;
-    v[0] += __ldcg(ss);
-    v[1] += __ldcg(ss + TC);
-    v[2] += __ldcg(ss + 2 * TC);
+  float v[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k2 = 0; k2 < L; ++k2) s += lane_sum[k2][c][t];
+    v[c] = s;
   }
   float *H = A.H + (size_t)b * 3 * A.n + 3 * j;
   H[0] -= v[0];
@@ -1328,10 +1319,6 @@ inline int mv_group(int B, int prec, bool half) {
   return B <= 1 ? 1 : (B == 2 || cap == 2) ? 2 : 4;
 }
 
-// slices of a column chunk's range of super-rows in k_half_cols (about 8
-// groups each)
-inline int half_col_slices(int64_t Q) { return (int)std::max<int64_t>(1, std::min<int64_t>(16, (Q + 7) / 8)); }
-
 template <int PREC, int SB>
 void launch_mv_sb(const MvArgs &A, int grid_cap, cudaStream_t s) {
   // never more CTAs than units: every CTA then owns at least one unit, which
@@ -1344,20 +1331,17 @@ void launch_mv_sb(const MvArgs &A, int grid_cap, cudaStream_t s) {
 }
 
 // work area of a half-stored product over B simulations, SB per chunk read
-// (floats unless noted): the column sums of every group [NG][NGR][SB][3][TC];
-// the parts of groups split between CTAs [2 grid_cap][SB][3][TC]; the slice
-// sums of k_half_cols [B][Q][NS][3][TC]; its arrival counters [B][Q] (int)
+// (floats): the column sums of every group [NG][NGR][SB][3][TC]; the parts of
+// groups split between CTAs [2 grid_cap][SB][3][TC]
 struct HalfArea {
-  size_t colpart, colsplit, slice, arrive, bytes;
+  size_t colpart, colsplit, bytes;
 };
 inline HalfArea half_area(int64_t Q, int64_t B, int SB, int grid_cap, int TC) {
   const int64_t NG = (B + SB - 1) / SB, NGR = half_groups(Q);
   HalfArea h;
   h.colpart = 0;
   h.colsplit = h.colpart + (size_t)NG * NGR * SB * 3 * TC;
-  h.slice = h.colsplit + (size_t)2 * grid_cap * SB * 3 * TC;
-  h.arrive = h.slice + (size_t)B * Q * half_col_slices(Q) * 3 * TC;
-  h.bytes = h.arrive * sizeof(float) + (size_t)B * Q * sizeof(int);
+  h.bytes = (h.colsplit + (size_t)2 * grid_cap * SB * 3 * TC) * sizeof(float);
   return h;
 }
 
@@ -1377,7 +1361,6 @@ void launch_half(const mt_tensor *T, const float *xs, int B, float *H, float *pa
   A.gcount = count + (size_t)B * T->L.P * 8;  // after the row counters (all counters rest at zero)
   A.colpart = work + h.colpart;
   A.colsplit = work + h.colsplit;
-  A.arrive = reinterpret_cast<int *>(work + h.arrive);
   A.active = active;
   A.status = status;
   A.n = T->n;
@@ -1389,9 +1372,7 @@ void launch_half(const mt_tensor *T, const float *xs, int B, float *H, float *pa
   const int64_t U = (int64_t)((B + SB - 1) / SB) * A.CH;
   const int grid = (int)std::min<int64_t>(cap, U);
   mt::launch_pdl(k_matvec_half<PREC, SB>, dim3(grid), dim3(S::THREADS), S::SMEM_BYTES, s, A);
-  const int ns = half_col_slices(A.Q);
-  mt::launch_pdl(k_half_cols, dim3((unsigned)A.Q, (unsigned)ns, (unsigned)B), dim3(TC), 0, s, A, SB, TC, ns,
-                 work + h.slice);
+  mt::launch_pdl(k_half_cols<TC>, dim3((unsigned)A.Q, (unsigned)B), dim3(kHalfColLanes * TC), 0, s, A, SB);
 }
 
 // a layout that exists only stored half (3 planes)

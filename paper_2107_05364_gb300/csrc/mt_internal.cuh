@@ -214,6 +214,8 @@ struct mt_tensor {
   int64_t *d_sp_rptr = nullptr;  // n + 1: first run of each row
   int32_t *d_sp_col = nullptr;   // 2 per run: (first block within the row, first column)
   float *d_sp_val = nullptr;
+  int32_t *d_sp_seg = nullptr;   // n x 8: the run holding each eighth of a row's steps
+  int sp_split = 1;              // warps per row of the sparse product (1, 2, 4 or 8)
 };
 
 // Plane of entry e (xx, xy, xz, yy, yz, zz) in a streaming layout of

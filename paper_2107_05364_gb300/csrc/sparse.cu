@@ -233,34 +233,78 @@ __device__ __forceinline__ void warp_sum2_pair(float &s, float &c) {
 }
 
 
-// H_i = -sum_kept N_ij Ms_j m_j; one warp per (row, simulation), rows of one
-// simulation consecutive; xs = float4 (Ms m, 0) per tile, n + 4 per
-// simulation; each lane takes 4 consecutive blocks of one run per step (NP
-// vector loads of the values and 4 contiguous operands) and follows the
-// row's runs with a cursor of its own.  (Lanes on interleaved blocks, for
-// wider contiguous loads, needed a cursor walk per block and measured 2.4x
-// slower.)
-template <int NP>
-__global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
-                                             const int64_t *__restrict__ rptr, const int2 *__restrict__ run,
-                                             const float *__restrict__ val, const float4 *__restrict__ xs, float *H,
-                                             const int *active) {
+// A row's blocks are taken 128 at a time (a step: 4 consecutive blocks of one
+// run per lane).  The product may give a row to S = 1, 2, 4 or 8 warps, warp
+// k taking steps floor(k st / S) .. floor((k + 1) st / S) - 1 of the row's
+// st steps; seg[8 i + k'] holds the run (from the row's first) that contains
+// the first block of eighth k', so a warp starts its cursor there.
+constexpr int kSpSegMax = 8;
+
+__global__ void k_seg_runs(int64_t n, const int64_t *__restrict__ ptr, const int64_t *__restrict__ rptr,
+                           const int2 *__restrict__ run, int32_t *seg) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * kSpSegMax) return;
+  const int64_t i = t / kSpSegMax;
+  const int k = (int)(t - i * kSpSegMax);
+  const int64_t st = (ptr[i + 1] - ptr[i] + 127) / 128;
+  const int64_t a = 128 * ((k * st) / kSpSegMax);
+  int64_t lo = rptr[i], hi = rptr[i + 1] - 1;  // the last run starting at or before block a
+  if (hi < lo) {
+    seg[t] = 0;
+    return;
+  }
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (run[mid].x <= a) lo = mid;
+    else hi = mid - 1;
+  }
+  seg[t] = (int32_t)(lo - rptr[i]);
+}
+
+// H_i = -sum_kept N_ij Ms_j m_j, rows of one simulation consecutive; xs =
+// float4 (Ms m, 0) per tile, n + 4 per simulation.  S = 1: one warp per
+// (row, simulation), two per CTA.  S > 1: one CTA per (row, simulation), its
+// S warps on consecutive step ranges, their compensated sums added in warp
+// order in shared memory.  Each lane takes 4 consecutive blocks of one run
+// per step (NP vector loads of the values and 4 contiguous operands) and
+// follows the row's runs with a cursor of its own.  (Lanes on interleaved
+// blocks, for wider contiguous loads, needed a cursor walk per block and
+// measured 2.4x slower.)
+template <int NP, int S>
+__global__ void __launch_bounds__(S == 1 ? 64 : 32 * S) k_spmv(int64_t n, int B, const int64_t *__restrict__ ptr,
+                                                               const int64_t *__restrict__ rptr,
+                                                               const int2 *__restrict__ run,
+                                                               const int32_t *__restrict__ seg,
+                                                               const float *__restrict__ val,
+                                                               const float4 *__restrict__ xs, float *H,
+                                                               const int *active) {
   mtd::pdl_enter();
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (wid >= n * B) return;
-  const int64_t i = wid % n;
-  const int b = (int)(wid / n);
-  if (active && !active[b]) return;
+  int64_t rid;  // b n + i
+  int k;        // this warp's part of the row
+  if constexpr (S == 1) {
+    rid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    k = 0;
+    if (rid >= n * B) return;
+  } else {
+    rid = blockIdx.x;
+    k = threadIdx.x >> 5;
+  }
+  const int64_t i = rid % n;
+  const int b = (int)(rid / n);
+  if (active && !active[b]) return;  // the whole CTA when S > 1
   const float4 *xb = xs + (size_t)b * sparse_x_stride(n);
   const int64_t o = ptr[i], K4 = ptr[i + 1] - o;
+  const int64_t st = (K4 + 127) / 128;
+  const int64_t a_lo = 128 * ((k * st) / S);
+  const int64_t a_e = 128 * (((k + 1) * st) / S), a_hi = a_e < K4 ? a_e : K4;
   const float *rv = val + NP * o;
   const int64_t r1 = rptr[i + 1];
-  int64_t rc = rptr[i];  // this lane's run
+  int64_t rc = rptr[i] + (S == 1 ? 0 : seg[i * kSpSegMax + k * (kSpSegMax / S)]);  // this lane's run
   int2 cur = rc < r1 ? run[rc] : make_int2(0, 0);
   int64_t next = rc + 1 < r1 ? run[rc + 1].x : INT64_MAX;  // first block of the following run
   float sx = 0, cx = 0, sy = 0, cy = 0, sz = 0, cz = 0;
-  for (int64_t a = 4 * (int64_t)lane; a < K4; a += 128) {
+  for (int64_t a = a_lo + 4 * (int64_t)lane; a < a_hi; a += 128) {
     // the values stream past (read once: no L1 allocation); the operands,
     // read by every row, stay cached
     float4 v[NP];
@@ -297,11 +341,37 @@ __global__ void __launch_bounds__(64) k_spmv(int64_t n, int B, const int64_t *__
   warp_sum2_pair(sx, cx);
   warp_sum2_pair(sy, cy);
   warp_sum2_pair(sz, cz);
-  if (lane == 0) {
-    float *Hb = H + (size_t)b * 3 * n + 3 * i;
-    Hb[0] = -(sx + cx);
-    Hb[1] = -(sy + cy);
-    Hb[2] = -(sz + cz);
+  float *Hb = H + (size_t)b * 3 * n + 3 * i;
+  if constexpr (S == 1) {
+    if (lane == 0) {
+      Hb[0] = -(sx + cx);
+      Hb[1] = -(sy + cy);
+      Hb[2] = -(sz + cz);
+    }
+  } else {
+    __shared__ float part[S][6];
+    if (lane == 0) {
+      part[k][0] = sx;
+      part[k][1] = cx;
+      part[k][2] = sy;
+      part[k][3] = cy;
+      part[k][4] = sz;
+      part[k][5] = cz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < S; ++w) {
+        cx += part[w][1];
+        sum2_add(sx, cx, part[w][0]);
+        cy += part[w][3];
+        sum2_add(sy, cy, part[w][2]);
+        cz += part[w][5];
+        sum2_add(sz, cz, part[w][4]);
+      }
+      Hb[0] = -(sx + cx);
+      Hb[1] = -(sy + cy);
+      Hb[2] = -(sz + cz);
+    }
   }
 }
 
@@ -314,6 +384,20 @@ __global__ void k_prep_sparse_x(const float *m, const float *Ms, int64_t n, int 
     const float *mj = m + 3 * t;
     xs[b * sparse_x_stride(n) + j] = make_float4(ms * mj[0], ms * mj[1], ms * mj[2], 0.0f);
   }
+}
+
+// Warps per row of the sparse product, a property of the tensor (so that a
+// simulation's field does not depend on the batch it runs in): doubled while
+// one simulation's rows give fewer than 4 waves of resident warps (32 per SM)
+// and every warp keeps at least 6 steps of 128 blocks.  With one warp per row
+// the last, partial wave runs a whole row's chain of dependent steps on
+// mostly idle SMs.
+int sparse_split(int64_t n, int64_t nnzb, int sms) {
+  const double steps = n > 0 ? (double)nnzb / (double)n / 128.0 : 0.0;
+  const int64_t resident = (int64_t)std::max(1, sms) * 32;
+  int S = 1;
+  while (S < kSpSegMax && n * S < 4 * resident && steps / (2 * S) >= 6.0) S *= 2;
+  return S;
 }
 
 // position of rank k in a 65536-bin histogram: bin and rank within it
@@ -337,17 +421,29 @@ void select_bin(const std::vector<unsigned long long> &h, unsigned long long k, 
 namespace mt {
 
 void launch_spmv(const mt_tensor *T, const float *xs, int B, float *H, const int *active, cudaStream_t s) {
-  const int64_t warps = T->n * (int64_t)B;
-  const dim3 grid((unsigned)((warps + 1) / 2));
+  const int64_t rows = T->n * (int64_t)B;
   const int64_t *ptr = (const int64_t *)T->d_sp_ptr;
   const int64_t *rptr = (const int64_t *)T->d_sp_rptr;
   const int2 *run = reinterpret_cast<const int2 *>(T->d_sp_col);
+  const int32_t *seg = T->d_sp_seg;
   const float *val = (const float *)T->d_sp_val;
   const float4 *x4 = reinterpret_cast<const float4 *>(xs);
-  if (T->L.nplane == 4)
-    mt::launch_pdl(k_spmv<4>, grid, dim3(64), 0, s, T->n, B, ptr, rptr, run, val, x4, H, active);
-  else
-    mt::launch_pdl(k_spmv<6>, grid, dim3(64), 0, s, T->n, B, ptr, rptr, run, val, x4, H, active);
+  const int S = T->sp_split;
+  const dim3 grid((unsigned)(S == 1 ? (rows + 1) / 2 : rows)), block(S == 1 ? 64 : 32 * S);
+#define MT_SPMV(NP, SS) \
+  mt::launch_pdl(k_spmv<NP, SS>, grid, block, 0, s, T->n, B, ptr, rptr, run, seg, val, x4, H, active)
+  if (T->L.nplane == 4) {
+    if (S == 8) MT_SPMV(4, 8);
+    else if (S == 4) MT_SPMV(4, 4);
+    else if (S == 2) MT_SPMV(4, 2);
+    else MT_SPMV(4, 1);
+  } else {
+    if (S == 8) MT_SPMV(6, 8);
+    else if (S == 4) MT_SPMV(6, 4);
+    else if (S == 2) MT_SPMV(6, 2);
+    else MT_SPMV(6, 1);
+  }
+#undef MT_SPMV
 }
 
 void launch_prep_sparse_x(const mt_tensor *T, const float *m, int B, float *xs, cudaStream_t s) {
@@ -446,9 +542,10 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   S->L = T->L;
   S->sp_blocks = nnzb;
   S->sp_runs = nruns;
+  S->sp_split = sparse_split(n, nnzb, ctx->num_sms);
   const int np = T->L.nplane;  // value planes: those the source stores (6, or 4 for a single layer)
   S->bytes = 2 * sizeof(int64_t) * (n + 1) + 2 * sizeof(int32_t) * (size_t)std::max<int64_t>(1, nruns) +
-             np * sizeof(float) * (size_t)std::max<int64_t>(1, nnzb);
+             np * sizeof(float) * (size_t)std::max<int64_t>(1, nnzb) + sizeof(int32_t) * kSpSegMax * (size_t)n;
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->in_use + S->bytes > ctx->budget) {
@@ -464,6 +561,7 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_rptr, sizeof(int64_t) * (n + 1));
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_col, 2 * sizeof(int32_t) * std::max<int64_t>(1, nruns));
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_val, np * sizeof(float) * std::max<int64_t>(1, nnzb));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sp_seg, sizeof(int32_t) * kSpSegMax * (size_t)n);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_ptr, ptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(S->d_sp_rptr, rptr.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
   // gap and padding blocks are zero
@@ -475,6 +573,10 @@ extern "C" mt_status mt_tensor_threshold(mt_tensor *T, double fraction, mt_tenso
   k_rows<true><<<(unsigned)n, 32>>>(D, n, L.TR, L.TC, L.nplane, L.Q, tbits, d_tie, r, nullptr, nullptr,
                                     S->d_sp_ptr, S->d_sp_rptr, S->d_sp_col, S->d_sp_val);
   e = cudaGetLastError();
+  if (e == cudaSuccess)
+    k_seg_runs<<<(unsigned)((n * kSpSegMax + 255) / 256), 256>>>(
+        n, S->d_sp_ptr, S->d_sp_rptr, reinterpret_cast<const int2 *>(S->d_sp_col), S->d_sp_seg);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     mt::tensor_release(S);

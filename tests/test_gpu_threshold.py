@@ -158,3 +158,43 @@ def test_single_layer_sparse_stores_four_planes(mt, ctx):
     mt.mt_demag_field(S6, mg, H6)
     torch.cuda.synchronize()
     assert torch.equal(H4, H6)
+
+
+@pytest.mark.parametrize("nx,ny,fraction,warps", [(64, 32, 0.3, 2), (80, 40, 0.0, 4)])
+def test_rows_split_among_warps(mt, ctx, nx, ny, fraction, warps):
+    # rows of ~14 and 25 steps of 128 blocks: the product gives each row to 2
+    # and 4 warps, each starting from the run that holds its first block
+    import torch
+    t = wl.film(nx, ny, 1)
+    tiles = mt.mt_tiles_create(ctx, t)
+    T = mt.mt_demag_assemble_ex(tiles, "f32", mt.MT_LAYOUT_STREAM_FULL)
+    S, thr, kept = mt.mt_tensor_threshold(T, fraction)
+    assert S.info()["row_warps"] == warps and T.info()["row_warps"] == 0
+    N = oracle.demag_tensor(t.centre, t.edge)
+    if fraction == 0.0:
+        # nothing dropped: the oracle's tensor rounded to FP32 is the stored one
+        # to an ulp here and there
+        md32 = oracle.Model.from_tiles(t, N=N.astype(np.float32).astype(np.float64))
+    else:
+        # the selection on the stored FP32 values (see test_threshold_matches_oracle)
+        N32 = mt.mt_tensor_read_rows(T, 0, t.n)
+        Nt32, thr_o, kept_o = oracle.threshold_tensor(N32, fraction)
+        assert np.float32(thr) == np.float32(thr_o) and kept == kept_o
+        md32 = oracle.Model.from_tiles(t, N=Nt32.astype(np.float64))
+    Nt, _, _ = oracle.threshold_tensor(N, fraction)
+    md = oracle.Model.from_tiles(t, N=Nt)
+    ms = [wl.m_random(t.n, seed=11), np.tile(np.array([[0.6, 0.48, 0.64]]), (t.n, 1))]
+    mg = torch.tensor(np.concatenate([m.astype(np.float32).ravel() for m in ms]), device="cuda")
+    H = torch.full_like(mg, float("nan"))
+    mt.mt_demag_field(S, mg, H, B=2)
+    torch.cuda.synchronize()
+    for b, m in enumerate(ms):
+        Hg = H[b * 3 * t.n:(b + 1) * 3 * t.n].cpu().numpy().reshape(-1, 3)
+        m64 = m.astype(np.float32).astype(np.float64)
+        assert _rel(Hg, oracle.demag_field(md32, m64)) <= 1e-6
+        assert _rel(Hg, oracle.demag_field(md, m64)) <= 1e-4
+        # a simulation's field does not depend on the batch it is computed in
+        H1 = torch.full((3 * t.n,), float("nan"), device="cuda")
+        mt.mt_demag_field(S, mg[b * 3 * t.n:(b + 1) * 3 * t.n].contiguous(), H1)
+        torch.cuda.synchronize()
+        assert torch.equal(H1, H[b * 3 * t.n:(b + 1) * 3 * t.n])

@@ -47,11 +47,11 @@ MU0 = 4e-7 * math.pi
 MATVEC_F32_N10000_TRAFFIC = {4: 1618117632 + 2918912}  # tensors storing every block
 # The same film with the tensor stored half (upper triangle of chunks, in
 # super-row order) and traceless (3 planes: xx, xy, yy), one ncu capture of
-# each kernel of a product: k_matvec_half<f32, 3 planes> read 621,362,176 and
-# wrote 4,646,912 bytes, k_half_cols read 4,875,008 (the column sums of the
-# groups above the diagonal) -- 1.051 x the 0.60 GB algorithmic bytes.  Valid
-# while both kernels are unchanged.
-MATVEC_F32_HALF_N10000_TRAFFIC = {3: 621362176 + 4646912 + 4875008}
+# each kernel of a product: k_matvec_half<f32, 3 planes> read 621,361,920 and
+# wrote 4,856,320 bytes, the single-phase k_half_cols read 4,863,744 (the
+# column sums of the groups above the diagonal) -- 1.052 x the 0.60 GB
+# algorithmic bytes.  Valid while both kernels are unchanged.
+MATVEC_F32_HALF_N10000_TRAFFIC = {3: 621361920 + 4856320 + 4863744}
 
 
 def f32_alg_bytes(info, n):
@@ -1305,8 +1305,8 @@ def run_profile(args):
         torch.cuda.synchronize()
         print("assemble n=%d: %.3f ms" % (t.n, e0.elapsed_time(e1) / args.reps))
         return
-    layout = {"stream": mt.MT_LAYOUT_STREAM, "full": mt.MT_LAYOUT_STREAM_FULL, "dense": mt.MT_LAYOUT_DENSE,
-              "stream6": mt.MT_LAYOUT_STREAM6}[args.layout]
+    layout = {"stream": mt.MT_LAYOUT_STREAM, "full": mt.MT_LAYOUT_STREAM_FULL, "half": mt.MT_LAYOUT_STREAM_HALF,
+              "dense": mt.MT_LAYOUT_DENSE, "stream6": mt.MT_LAYOUT_STREAM6}[args.layout]
     if args.threshold is not None and layout == mt.MT_LAYOUT_STREAM:
         layout = mt.MT_LAYOUT_STREAM_FULL  # thresholding needs every block stored
     T = mt.mt_demag_assemble_ex(tiles, prec, layout)
@@ -1387,7 +1387,7 @@ def main():
     ap.add_argument("--what", default="field", choices=["field", "step", "assemble"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sims", type=int, default=1)
-    ap.add_argument("--layout", default="stream", choices=["stream", "full", "dense", "stream6"])
+    ap.add_argument("--layout", default="stream", choices=["stream", "full", "half", "dense", "stream6"])
     ap.add_argument("--threshold", type=float, default=None)
     ap.add_argument("--path", default="auto", choices=["auto", "graph", "persistent"])
     args = ap.parse_args()

@@ -544,11 +544,37 @@ struct HalfShape {
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + CB_BYTES + XI_BYTES + 2 * STAGES * 8 + 16;
   static constexpr int THREADS = (NCW + 1) * 32;
   static constexpr int NV = K * RPW * 3;  // row values a warp holds per simulation
+  static constexpr int NVAL = SB * RPW * 3;        // a warp's row values per chunk
+  static constexpr int NSLOT = NVAL <= 8 ? 8 : 16;  // padded for the reduce-scatter
   static_assert(SB == 1 || SB == 2, "one or two simulations per chunk read");
   static_assert(C::VEC == 4 && C::TC == 32 * C::VEC && C::TR % NCW == 0, "float4 columns, whole rows per warp");
   static_assert((NCW * 32) % C::TC == 0 && NV <= 64 && 16 * SB <= 32, "flush and operand lanes");
   static_assert(STAGES >= 2 && SMEM_BYTES <= 227 * 1024, "ring within one CTA's shared memory");
 };
+
+// Sums over the warp's lanes of NS values (NS a power of two <= 32), scattered:
+// lane l returns the total of value l / (32 / NS).  Recursive halving: at the
+// step with offset o a lane keeps the upper half of its values if (l & o),
+// else the lower half, and adds its partner's copy of them; once one value is
+// left the remaining offsets add it whole.
+template <int NS>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NS], int lane) {
+  static_assert(NS >= 1 && NS <= 32 && (NS & (NS - 1)) == 0, "a power of two up to 32");
+  int o = 16;
+#pragma unroll
+  for (int cnt = NS / 2; cnt >= 1; cnt /= 2, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < cnt; ++i) {
+      const float send = up ? v[i] : v[cnt + i];
+      const float keep = up ? v[cnt + i] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+#pragma unroll
+  for (; o > 0; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+  return v[0];
+}
 
 struct HalfArgs {
   const float *tensor;
@@ -700,8 +726,21 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
 
   // ---------------- consumers ----------------
   // warp w holds rows w RPW + r (r < RPW) of each of the K panels of the
-  // current super-row; lane l holds columns 4 l .. 4 l + 3
-  float acc[SB][K][S::RPW][3];
+  // current super-row; lane l holds columns 4 l .. 4 l + 3.
+  // - One simulation: lane l keeps the running sums of its part of every row
+  //   value of every panel (acc, K RPW 3 registers) and the warp adds them
+  //   over its lanes at the super-row's flush.
+  // - Two (twice those sums spilled registers): after each chunk the warp's
+  //   NVAL row values (value (m RPW + r) 3 + c: simulation m, row r,
+  //   component c) are added over the lanes by a reduce-scatter that leaves
+  //   value l / LPS in lane l, which keeps its running sum for the chunk's
+  //   panel k in accs[k].  A simulation's sums then run in another order
+  //   than alone (each chunk's warp total first): equal to rounding.
+  constexpr bool SCATTER = SB == 2;
+  constexpr int NVAL = S::NVAL, NSLOT = S::NSLOT, LPS = 32 / NSLOT;
+  float acc[SCATTER ? 1 : SB][SCATTER ? 1 : K][S::RPW][3];
+  float accs[SCATTER ? K : 1];
+  const int my_val = lane / LPS;
   float4 *xi = xi_all + warp * SB * K * S::RPW;  // [m][k RPW + r]
   int64_t sr_cur = -1;  // current (simulation group, super-row) = g Q + R
   int it = 0;
@@ -715,96 +754,160 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
 
   // rows of super-row sr: warp totals, then written (or, for a super-row
   // shared by CTAs, parked and added in CTA order by the last to arrive)
-  auto flush_rows = [&](int64_t sr) {
+  auto flush_lane = [&](int64_t sr) {
+    if constexpr (!SCATTER) {
 #pragma unroll
-    for (int m = 0; m < SB; ++m)
+      for (int m = 0; m < SB; ++m)
 #pragma unroll
-      for (int k = 0; k < K; ++k)
+        for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int r = 0; r < S::RPW; ++r)
+          for (int r = 0; r < S::RPW; ++r)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) acc[m][k][r][c] = mtd::warp_sum(acc[m][k][r][c]);
-    const int64_t g = sr / A.Q, R = sr - g * A.Q;
-    const int64_t su0 = g * A.CH + (int64_t)K * half_gbase(R, A.Q);
-    const int64_t su1 = (R == A.Q - 1) ? (g + 1) * A.CH : g * A.CH + (int64_t)K * half_gbase(R + 1, A.Q);
-    const int64_t kf = mtd::sk_owner(su0, U, G), kl = mtd::sk_owner(su1 - 1, U, G);
-    // lane l holds values v = l and l + 32 (v = (k RPW + r) 3 + c)
-    float mine[SB][2];
+            for (int c = 0; c < 3; ++c) acc[m][k][r][c] = mtd::warp_sum(acc[m][k][r][c]);
+      const int64_t g = sr / A.Q, R = sr - g * A.Q;
+      const int64_t su0 = g * A.CH + (int64_t)K * half_gbase(R, A.Q);
+      const int64_t su1 = (R == A.Q - 1) ? (g + 1) * A.CH : g * A.CH + (int64_t)K * half_gbase(R + 1, A.Q);
+      const int64_t kf = mtd::sk_owner(su0, U, G), kl = mtd::sk_owner(su1 - 1, U, G);
+      // lane l holds values v = l and l + 32 (v = (k RPW + r) 3 + c)
+      float mine[SB][2];
 #pragma unroll
-    for (int m = 0; m < SB; ++m) {
-      mine[m][0] = mine[m][1] = 0.0f;
+      for (int m = 0; m < SB; ++m) {
+        mine[m][0] = mine[m][1] = 0.0f;
 #pragma unroll
-      for (int k = 0; k < K; ++k)
+        for (int k = 0; k < K; ++k)
 #pragma unroll
-        for (int r = 0; r < S::RPW; ++r)
+          for (int r = 0; r < S::RPW; ++r)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            const int v = (k * S::RPW + r) * 3 + c;
-            if (v == lane) mine[m][0] = acc[m][k][r][c];
-            if (v == lane + 32) mine[m][1] = acc[m][k][r][c];
-          }
-    }
-    auto row_of = [&](int v) {  // row within the super-row
-      const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
-      return k * TR + warp * S::RPW + r;
-    };
-    // traceless storage: the self block's N_zz is 1 - xx - yy, the stream
-    // gave -(xx + yy), so the row's z sum lacks Ms_i m_i,z (its operand)
-    auto self_z = [&](int m, int v) -> float {
-      if constexpr (C::NPLANE == 3 || C::NPLANE == 5) {
-        if (v % 3 != 2) return 0.0f;
-        const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
-        return xi[m * K * S::RPW + k * S::RPW + r].z;
-      } else {
-        return 0.0f;
+            for (int c = 0; c < 3; ++c) {
+              const int v = (k * S::RPW + r) * 3 + c;
+              if (v == lane) mine[m][0] = acc[m][k][r][c];
+              if (v == lane + 32) mine[m][1] = acc[m][k][r][c];
+            }
       }
-    };
-    const int64_t row0 = R * K * TR;
-    if (kf == kl) {
+      auto row_of = [&](int v) {  // row within the super-row
+        const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
+        return k * TR + warp * S::RPW + r;
+      };
+      // traceless storage: the self block's N_zz is 1 - xx - yy, the stream
+      // gave -(xx + yy), so the row's z sum lacks Ms_i m_i,z (its operand)
+      auto self_z = [&](int m, int v) -> float {
+        if constexpr (C::NPLANE == 3 || C::NPLANE == 5) {
+          if (v % 3 != 2) return 0.0f;
+          const int k = v / (S::RPW * 3), r = (v / 3) % S::RPW;
+          return xi[m * K * S::RPW + k * S::RPW + r].z;
+        } else {
+          return 0.0f;
+        }
+      };
+      const int64_t row0 = R * K * TR;
+      if (kf == kl) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int v = lane + 32 * h;
+          if (v >= S::NV) continue;
+          const int64_t row = row0 + row_of(v);
+          if (row >= A.n) continue;
+#pragma unroll
+          for (int m = 0; m < SB; ++m)
+            if (float *H = out(g * SB + m)) H[3 * row + v % 3] = -(mine[m][h] + self_z(m, v));
+        }
+        return;
+      }
+      const int64_t slot = (u0 >= su0) ? 2 * kcta : 2 * kcta + 1;  // the super-row is this CTA's first or last
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int v = lane + 32 * h;
+        if (v >= S::NV) continue;
+#pragma unroll
+        for (int m = 0; m < SB; ++m) A.part[((slot * SB + m) * K * TR + row_of(v)) * 3 + v % 3] = mine[m][h];
+      }
+      __threadfence();
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) last = (atomicAdd(&A.count[sr * S::NCW + warp], 1) == (int)(kl - kf));
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (!last) return;
+      __threadfence();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int v = lane + 32 * h;
         if (v >= S::NV) continue;
         const int64_t row = row0 + row_of(v);
-        if (row >= A.n) continue;
 #pragma unroll
-        for (int m = 0; m < SB; ++m)
-          if (float *H = out(g * SB + m)) H[3 * row + v % 3] = -(mine[m][h] + self_z(m, v));
+        for (int m = 0; m < SB; ++m) {
+          float tot = 0.0f;
+          for (int64_t kk = kf; kk <= kl; ++kk) {
+            const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
+            tot += __ldcg(&A.part[((sl * SB + m) * K * TR + row_of(v)) * 3 + v % 3]);
+          }
+          float *H = out(g * SB + m);
+          if (H && row < A.n) H[3 * row + v % 3] = -(tot + self_z(m, v));
+        }
       }
-      return;
-    }
-    const int64_t slot = (u0 >= su0) ? 2 * kcta : 2 * kcta + 1;  // the super-row is this CTA's first or last
+      if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
+        }
+  };
+
+  // the same for SCATTER: lane l holds value j = l / LPS of every panel; the
+  // LPS lanes of a value share the panels (lane l takes k = l % LPS,
+  // l % LPS + LPS, ...)
+  auto flush_scatter = [&](int64_t sr) {
+    if constexpr (SCATTER) {
+      const int64_t g = sr / A.Q, R = sr - g * A.Q;
+      const int64_t su0 = g * A.CH + (int64_t)K * half_gbase(R, A.Q);
+      const int64_t su1 = (R == A.Q - 1) ? (g + 1) * A.CH : g * A.CH + (int64_t)K * half_gbase(R + 1, A.Q);
+      const int64_t kf = mtd::sk_owner(su0, U, G), kl = mtd::sk_owner(su1 - 1, U, G);
+      const bool valid = my_val < NVAL;
+      const int m = my_val / (S::RPW * 3), r = (my_val / 3) % S::RPW, c = my_val % 3;
+      const int row_in = warp * S::RPW + r;  // row within each panel
+      auto self_z = [&](int k) -> float {  // as in flush_lane
+        if constexpr (C::NPLANE == 3 || C::NPLANE == 5) {
+          return c == 2 ? xi[m * K * S::RPW + k * S::RPW + r].z : 0.0f;
+        } else {
+          return 0.0f;
+        }
+      };
+      const int64_t row0 = R * K * TR;
+      float *H = valid ? out(g * SB + m) : nullptr;
+      if (kf == kl) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int v = lane + 32 * h;
-      if (v >= S::NV) continue;
+        for (int k = 0; k < K; ++k) {
+          if (!valid || k % LPS != lane % LPS) continue;
+          const int64_t row = row0 + k * TR + row_in;
+          if (H && row < A.n) H[3 * row + c] = -(accs[k] + self_z(k));
+        }
+        return;
+      }
+      const int64_t slot = (u0 >= su0) ? 2 * kcta : 2 * kcta + 1;  // the super-row is this CTA's first or last
 #pragma unroll
-      for (int m = 0; m < SB; ++m) A.part[((slot * SB + m) * K * TR + row_of(v)) * 3 + v % 3] = mine[m][h];
-    }
-    __threadfence();
-    __syncwarp();
-    int last = 0;
-    if (lane == 0) last = (atomicAdd(&A.count[sr * S::NCW + warp], 1) == (int)(kl - kf));
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last) return;
-    __threadfence();
+      for (int k = 0; k < K; ++k) {
+        if (!valid || k % LPS != lane % LPS) continue;
+        A.part[((slot * SB + m) * K * TR + k * TR + row_in) * 3 + c] = accs[k];
+      }
+      __threadfence();
+      __syncwarp();
+      int last = 0;
+      if (lane == 0) last = (atomicAdd(&A.count[sr * S::NCW + warp], 1) == (int)(kl - kf));
+      last = __shfl_sync(0xffffffffu, last, 0);
+      if (!last) return;
+      __threadfence();
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int v = lane + 32 * h;
-      if (v >= S::NV) continue;
-      const int64_t row = row0 + row_of(v);
-#pragma unroll
-      for (int m = 0; m < SB; ++m) {
+      for (int k = 0; k < K; ++k) {
+        if (!valid || k % LPS != lane % LPS) continue;
         float tot = 0.0f;
         for (int64_t kk = kf; kk <= kl; ++kk) {
           const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
-          tot += __ldcg(&A.part[((sl * SB + m) * K * TR + row_of(v)) * 3 + v % 3]);
+          tot += __ldcg(&A.part[((sl * SB + m) * K * TR + k * TR + row_in) * 3 + c]);
         }
-        float *H = out(g * SB + m);
-        if (H && row < A.n) H[3 * row + v % 3] = -(tot + self_z(m, v));
+        const int64_t row = row0 + k * TR + row_in;
+        if (H && row < A.n) H[3 * row + c] = -(tot + self_z(k));
       }
-    }
-    if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
+      if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
+        }
+  };
+  auto flush_rows = [&](int64_t sr) {
+    if constexpr (SCATTER) flush_scatter(sr);
+    else flush_lane(sr);
   };
 
   // the chunks kb .. ke - 1 of one group; STRICT: also its column sums
@@ -821,6 +924,11 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
           aborted = true;
           *abort_flag = 1;
         }
+      }
+      float rv[SCATTER ? NSLOT : 1];  // SCATTER: this chunk's row values (zero if the wait gave up)
+      if constexpr (SCATTER) {
+#pragma unroll
+        for (int j = 0; j < NSLOT; ++j) rv[j] = 0.0f;
       }
       if (!aborted) {
         const unsigned char *st = smem + (size_t)s * S::STAGE_BYTES;
@@ -862,9 +970,15 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
                   colp[m][v][2] = fmaf(nzz, xr[m].z, colp[m][v][2]);
                 }
               }
-              acc[m][k][r][0] += sx;
-              acc[m][k][r][1] += sy;
-              acc[m][k][r][2] += sz;
+              if constexpr (SCATTER) {
+                rv[(m * S::RPW + r) * 3 + 0] = sx;
+                rv[(m * S::RPW + r) * 3 + 1] = sy;
+                rv[(m * S::RPW + r) * 3 + 2] = sz;
+              } else {
+                acc[m][k][r][0] += sx;
+                acc[m][k][r][1] += sy;
+                acc[m][k][r][2] += sz;
+              }
             }
           } else if constexpr (C::NPLANE == 5) {
             // zz = -(xx + yy) (trace 0; the self blocks' +1 is added in
@@ -890,9 +1004,15 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
                   colp[m][v][2] = fmaf(nxz[v], xr[m].x, fmaf(nyz[v], xr[m].y, fmaf(nzz, xr[m].z, colp[m][v][2])));
                 }
               }
-              acc[m][k][r][0] += sx;
-              acc[m][k][r][1] += sy;
-              acc[m][k][r][2] += sz;
+              if constexpr (SCATTER) {
+                rv[(m * S::RPW + r) * 3 + 0] = sx;
+                rv[(m * S::RPW + r) * 3 + 1] = sy;
+                rv[(m * S::RPW + r) * 3 + 2] = sz;
+              } else {
+                acc[m][k][r][0] += sx;
+                acc[m][k][r][1] += sy;
+                acc[m][k][r][2] += sz;
+              }
             }
           } else if constexpr (C::PLANAR) {
             float nxx[4], nxy[4], nyy[4], nzz[4];
@@ -914,9 +1034,15 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
                   colp[m][v][2] = fmaf(nzz[v], xr[m].z, colp[m][v][2]);
                 }
               }
-              acc[m][k][r][0] += sx;
-              acc[m][k][r][1] += sy;
-              acc[m][k][r][2] += sz;
+              if constexpr (SCATTER) {
+                rv[(m * S::RPW + r) * 3 + 0] = sx;
+                rv[(m * S::RPW + r) * 3 + 1] = sy;
+                rv[(m * S::RPW + r) * 3 + 2] = sz;
+              } else {
+                acc[m][k][r][0] += sx;
+                acc[m][k][r][1] += sy;
+                acc[m][k][r][2] += sz;
+              }
             }
           } else {
             float nxx[4], nxy[4], nxz[4], nyy[4], nyz[4], nzz[4];
@@ -940,15 +1066,22 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
                   colp[m][v][2] = fmaf(nxz[v], xr[m].x, fmaf(nyz[v], xr[m].y, fmaf(nzz[v], xr[m].z, colp[m][v][2])));
                 }
               }
-              acc[m][k][r][0] += sx;
-              acc[m][k][r][1] += sy;
-              acc[m][k][r][2] += sz;
+              if constexpr (SCATTER) {
+                rv[(m * S::RPW + r) * 3 + 0] = sx;
+                rv[(m * S::RPW + r) * 3 + 1] = sy;
+                rv[(m * S::RPW + r) * 3 + 2] = sz;
+              } else {
+                acc[m][k][r][0] += sx;
+                acc[m][k][r][1] += sy;
+                acc[m][k][r][2] += sz;
+              }
             }
           }
         }
       }
       __syncwarp();
       if (lane == 0) mtd::mbar_arrive(&empty[s]);
+      if constexpr (SCATTER) accs[k] += warp_reduce_scatter<NSLOT>(rv, lane);  // every lane, aborted or not
     }
   };
 
@@ -961,12 +1094,17 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
     if (sr != sr_cur) {
       if (sr_cur >= 0) flush_rows(sr_cur);
       sr_cur = sr;
+      if constexpr (SCATTER) {
 #pragma unroll
-      for (int m = 0; m < SB; ++m)
+        for (int k = 0; k < K; ++k) accs[k] = 0.0f;
+      } else {
 #pragma unroll
-        for (int k = 0; k < K; ++k)
+        for (int m = 0; m < SB; ++m)
 #pragma unroll
-          for (int r = 0; r < S::RPW; ++r) acc[m][k][r][0] = acc[m][k][r][1] = acc[m][k][r][2] = 0.0f;
+          for (int k = 0; k < K; ++k)
+#pragma unroll
+            for (int r = 0; r < S::RPW; ++r) acc[m][k][r][0] = acc[m][k][r][1] = acc[m][k][r][2] = 0.0f;
+      }
       // the operand of this warp's rows of the super-row (column chunk R of
       // the operand): lane l < 16 SB takes simulation l / 16, row slot l % 16
       __syncwarp();

@@ -828,6 +828,23 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
       last = __shfl_sync(0xffffffffu, last, 0);
       if (!last) return;
       __threadfence();
+      // the parts in CTA order, each CTA's values loaded together
+      float tot[2][SB];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int m = 0; m < SB; ++m) tot[h][m] = 0.0f;
+      for (int64_t kk = kf; kk <= kl; ++kk) {
+        const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int v = lane + 32 * h;
+          if (v >= S::NV) continue;
+#pragma unroll
+          for (int m = 0; m < SB; ++m)
+            tot[h][m] += __ldcg(&A.part[((sl * SB + m) * K * TR + row_of(v)) * 3 + v % 3]);
+        }
+      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int v = lane + 32 * h;
@@ -835,13 +852,8 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
         const int64_t row = row0 + row_of(v);
 #pragma unroll
         for (int m = 0; m < SB; ++m) {
-          float tot = 0.0f;
-          for (int64_t kk = kf; kk <= kl; ++kk) {
-            const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
-            tot += __ldcg(&A.part[((sl * SB + m) * K * TR + row_of(v)) * 3 + v % 3]);
-          }
           float *H = out(g * SB + m);
-          if (H && row < A.n) H[3 * row + v % 3] = -(tot + self_z(m, v));
+          if (H && row < A.n) H[3 * row + v % 3] = -(tot[h][m] + self_z(m, v));
         }
       }
       if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
@@ -891,16 +903,23 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
       last = __shfl_sync(0xffffffffu, last, 0);
       if (!last) return;
       __threadfence();
+      // the parts in CTA order, each CTA's values loaded together
+      float tot[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) tot[k] = 0.0f;
+      for (int64_t kk = kf; kk <= kl; ++kk) {
+        const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          if (!valid || k % LPS != lane % LPS) continue;
+          tot[k] += __ldcg(&A.part[((sl * SB + m) * K * TR + k * TR + row_in) * 3 + c]);
+        }
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         if (!valid || k % LPS != lane % LPS) continue;
-        float tot = 0.0f;
-        for (int64_t kk = kf; kk <= kl; ++kk) {
-          const int64_t sl = (mtd::sk_begin(kk, U, G) >= su0) ? 2 * kk : 2 * kk + 1;
-          tot += __ldcg(&A.part[((sl * SB + m) * K * TR + k * TR + row_in) * 3 + c]);
-        }
         const int64_t row = row0 + k * TR + row_in;
-        if (H && row < A.n) H[3 * row + c] = -(tot + self_z(k));
+        if (H && row < A.n) H[3 * row + c] = -(tot[k] + self_z(k));
       }
       if (lane == 0) A.count[sr * S::NCW + warp] = 0;  // ready for the next launch
         }
@@ -1164,19 +1183,28 @@ __global__ void __launch_bounds__(HalfShape<PREC, SB>::THREADS, 1) k_matvec_half
     asm volatile("bar.sync 1, %0;" ::"r"(S::NCW * 32) : "memory");
     if (!split_last) continue;
     __threadfence();
+    constexpr int NC = (3 + NT - 1) / NT;  // components per thread
+    float tot[NC][SB];
 #pragma unroll
-    for (int c0 = 0; c0 < 3; c0 += NT) {
-      const int c = c0 + ct / TC;
+    for (int i = 0; i < NC; ++i)
+#pragma unroll
+      for (int m = 0; m < SB; ++m) tot[i][m] = 0.0f;
+    for (int64_t kk = kf; kk <= kl; ++kk) {  // the parts in CTA order, each CTA's loaded together
+      const int64_t sl = (mtd::sk_begin(kk, U, G) >= gs) ? 2 * kk : 2 * kk + 1;
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const int c = i * NT + ct / TC;
+        if (c >= 3) break;
+#pragma unroll
+        for (int m = 0; m < SB; ++m) tot[i][m] += __ldcg(&A.colsplit[((sl * SB + m) * 3 + c) * TC + col]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int c = i * NT + ct / TC;
       if (c >= 3) break;
 #pragma unroll
-      for (int m = 0; m < SB; ++m) {
-        float tot = 0.0f;
-        for (int64_t kk = kf; kk <= kl; ++kk) {
-          const int64_t sl = (mtd::sk_begin(kk, U, G) >= gs) ? 2 * kk : 2 * kk + 1;
-          tot += __ldcg(&A.colsplit[((sl * SB + m) * 3 + c) * TC + col]);
-        }
-        A.colpart[(((gc.g * A.NGR + gc.gi) * SB + m) * 3 + c) * TC + col] = tot;
-      }
+      for (int m = 0; m < SB; ++m) A.colpart[(((gc.g * A.NGR + gc.gi) * SB + m) * 3 + c) * TC + col] = tot[i][m];
     }
     if (ct == 0) *gcount = 0;  // ready for the next launch
   }

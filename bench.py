@@ -47,11 +47,11 @@ MU0 = 4e-7 * math.pi
 MATVEC_F32_N10000_TRAFFIC = {4: 1618117632 + 2918912}  # tensors storing every block
 # The same film with the tensor stored half (upper triangle of chunks, in
 # super-row order) and traceless (3 planes: xx, xy, yy), one ncu capture of
-# each kernel of a product: k_matvec_half<f32, 3 planes> read 621,361,920 and
-# wrote 4,856,320 bytes, the single-phase k_half_cols read 4,863,744 (the
-# column sums of the groups above the diagonal) -- 1.052 x the 0.60 GB
+# each kernel of a product: k_matvec_half<f32, 3 planes> read 621,368,064 and
+# wrote 4,680,192 bytes, k_half_cols read 4,864,000 (the column sums of the
+# groups above the diagonal) and wrote 15,360 -- 1.051 x the 0.60 GB
 # algorithmic bytes.  Valid while both kernels are unchanged.
-MATVEC_F32_HALF_N10000_TRAFFIC = {3: 621361920 + 4856320 + 4863744}
+MATVEC_F32_HALF_N10000_TRAFFIC = {3: 621368064 + 4680192 + 4864000 + 15360}
 
 
 def f32_alg_bytes(info, n):

@@ -374,14 +374,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       last = __shfl_sync(0xffffffffu, last, 0);
       if (last) {
         __threadfence();
-        for (int b = 0; b < P.B; ++b) {
-          float tot = 0.0f;
+        // 16 simulations at a time: all their parts loaded (in CTA order per
+        // simulation) before their stores to H, which the compiler cannot
+        // move loads across
+        for (int b0 = 0; b0 < P.B; b0 += 16) {
+          float tot[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) tot[j] = 0.0f;
           for (int64_t kk = kf; kk <= kl; ++kk) {
             const int64_t fm = mtd::sk_begin(kk, U, G) / P.KBU;
             const int64_t sl = (mt == fm) ? 2 * kk : 2 * kk + 1;
-            tot += __ldcg(&P.part[((size_t)sl * BP + b) * GM + row]);
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (b0 + j < P.B) tot[j] += __ldcg(&P.part[((size_t)sl * BP + b0 + j) * GM + row]);
           }
-          if (r < P.n3) P.H[(size_t)b * P.n3 + r] = -tot;
+          if (r < P.n3)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (b0 + j < P.B) P.H[(size_t)(b0 + j) * P.n3 + r] = -tot[j];
         }
         if (lane == 0) P.count[mt * EPI_WARPS + g] = 0;
       }

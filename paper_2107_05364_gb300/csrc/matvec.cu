@@ -383,17 +383,23 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
     last = __shfl_sync(0xffffffffu, last, 0);
     if (last) {
       __threadfence();
-      if (writer)
-        for (int m = 0; m < SB; ++m) {
-          Acc tot = 0;
-          for (int64_t kk = kf; kk <= kl; ++kk) {
-            // slot of CTA kk: 2 kk if this panel is its first, else 2 kk + 1
-            const int64_t sl = (mtd::sk_begin(kk, U, G) >= pu0) ? 2 * kk : 2 * kk + 1;
-            tot += __ldcg(&part[((sl * SB + m) * C::TR + row_in_panel) * 3 + lc]);
-          }
-          Acc *H = out(m);
-          if (H && row < A.n) H[3 * row + lc] = -tot;
+      if (writer) {
+        // the parts in CTA order, each CTA's simulations loaded together
+        Acc tot[SB];
+#pragma unroll
+        for (int m = 0; m < SB; ++m) tot[m] = 0;
+        for (int64_t kk = kf; kk <= kl; ++kk) {
+          // slot of CTA kk: 2 kk if this panel is its first, else 2 kk + 1
+          const int64_t sl = (mtd::sk_begin(kk, U, G) >= pu0) ? 2 * kk : 2 * kk + 1;
+#pragma unroll
+          for (int m = 0; m < SB; ++m) tot[m] += __ldcg(&part[((sl * SB + m) * C::TR + row_in_panel) * 3 + lc]);
         }
+#pragma unroll
+        for (int m = 0; m < SB; ++m) {
+          Acc *H = out(m);
+          if (H && row < A.n) H[3 * row + lc] = -tot[m];
+        }
+      }
       if (lane == 0) A.count[gp * S::NCW + warp] = 0;  // ready for the next launch
     }
   };

@@ -260,9 +260,13 @@ MT_API mt_status mt_demag_assemble(mt_tiles *tiles, mt_prec prec, mt_tensor **ou
  * mt_tensor_info.half tells;
  * MT_LAYOUT_STREAM_FULL stores every block.  The half storage's product is
  * the faster one for products over 1 or 2 simulations (n = 10,000 film:
- * 0.16 against 0.25 ms for one, 0.21 against 0.26 ms for two); over 3 or
- * more simulations the full storage is (0.36 against 0.24 ms for four), so
- * a caller that batches 3 or more should assemble MT_LAYOUT_STREAM_FULL.
+ * 0.11 against 0.25 ms for one, 0.15 against 0.26 ms for two); over 3 or
+ * more simulations the full storage is (two passes, 0.31 against 0.24 ms
+ * for four), so a caller that batches 3 or more should assemble
+ * MT_LAYOUT_STREAM_FULL.  A pass over two simulations forms the row sums in
+ * another order than a pass over one (each chunk's warp total first), so a
+ * simulation's field from a half-stored tensor in a pair and alone agree to
+ * rounding, not bit for bit.
  * Thresholding and the allocation-free product need every block stored. */
 /* As mt_demag_assemble, with an explicit storage layout (mt_layout_kind).
  * MT_LAYOUT_DENSE turns every product over a batch of B simulations into a

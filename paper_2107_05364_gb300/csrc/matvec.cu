@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(MvShape<PREC, SB>::THREADS, 1) k_matvec(MvArgs
 // simulations share a chunk read (more take several passes: their row
 // sums would not fit the registers).
 // chunks a half-product CTA prefetches into L2 before the PDL wait
-constexpr int kHalfPrefetch = 24;
+constexpr int kHalfPrefetch = 18;
 
 template <int PREC, int SB>
 struct HalfShape {

@@ -43,7 +43,8 @@ MU0 = 4e-7 * math.pi
 # ncu capture of a full launch of the current kernels.  Every block stored, 4
 # planes (the single-layer film): 1,618,117,632 read + 2,918,912 written
 # (1.0132 x the 1.6e9 algorithmic bytes: the zero padding of the last chunk
-# row).  Valid while k_matvec<f32> is unchanged.
+# row).  Valid while k_matvec<f32> reads the same bytes (since the capture,
+# only the order of the split panels' loads of their parked parts changed).
 MATVEC_F32_N10000_TRAFFIC = {4: 1618117632 + 2918912}  # tensors storing every block
 # The same film with the tensor stored half (upper triangle of chunks, in
 # super-row order) and traceless (3 planes: xx, xy, yy), one ncu capture of
